@@ -1,0 +1,290 @@
+"""ctypes front end of the plain FP64 CPU oracle (``pic_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module; the library under
+``paper_2411_09605_gb300`` never does.  It shares no code with the CUDA path.
+
+Every function works on numpy float64 arrays in place (positions and
+velocities of each species, the grid fields), mirroring the C functions one to
+one; the C source states, next to each function, which part of the paper it
+restates and what pins it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pic_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, FP64, no FMA contraction, one thread)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)) or (
+        os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+_dp = C.POINTER(C.c_double)
+_lp = C.POINTER(C.c_long)
+
+
+class _EsCfg(C.Structure):
+    _fields_ = [("nc", C.c_long), ("L", C.c_double), ("order", C.c_int), ("dt", C.c_double),
+                ("scheme", C.c_int), ("remove_mean", C.c_int), ("gamma_on", C.c_int)]
+
+
+class _Species(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("n", C.c_long), ("x", _dp), ("v", _dp),
+                ("w", _dp), ("w0", C.c_double)]
+
+
+class _EmCfg(C.Structure):
+    _fields_ = [("nx", C.c_long), ("ny", C.c_long), ("Lx", C.c_double), ("Ly", C.c_double),
+                ("order", C.c_int), ("dt", C.c_double), ("c", C.c_double), ("scheme", C.c_int),
+                ("gamma_on", C.c_int)]
+
+
+class _Species2d(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("n", C.c_long), ("x", _dp), ("y", _dp),
+                ("vx", _dp), ("vy", _dp), ("vz", _dp), ("w", _dp), ("w0", C.c_double)]
+
+
+def _declare(L):
+    L.orc_shape_weights.argtypes = [C.c_int, C.c_double, C.c_long, _lp, _dp]
+    L.orc_shape_weights.restype = C.c_int
+    L.orc_deposit_1d.argtypes = [C.c_int, C.c_long, C.c_double, C.c_long, _dp, _dp, _dp]
+    L.orc_gather_1d.argtypes = [C.c_int, C.c_long, C.c_double, C.c_long, _dp, _dp, _dp]
+    L.orc_es1d_step.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp, _lp,
+                                C.POINTER(_dp)]
+    L.orc_es1d_step.restype = C.c_int
+    L.orc_es1d_energy.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp, _dp, _dp]
+    L.orc_es1d_run.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp, C.c_long,
+                               _dp, _dp, _lp]
+    L.orc_es1d_run.restype = C.c_int
+    L.orc_poisson_e0_1d.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp]
+    L.orc_yee_curl_e.argtypes = [C.c_long, C.c_long, C.c_double, C.c_double] + [_dp] * 6
+    L.orc_yee_curl_b.argtypes = [C.c_long, C.c_long, C.c_double, C.c_double] + [_dp] * 6
+    L.orc_vstar_solve.argtypes = [_dp, _dp, _dp]
+    L.orc_em2d_step.argtypes = [C.POINTER(_EmCfg), C.POINTER(_Species2d), C.c_int, _dp, _dp, _lp]
+    L.orc_em2d_step.restype = C.c_int
+    L.orc_em2d_energy.argtypes = [C.POINTER(_EmCfg), C.POINTER(_Species2d), C.c_int, _dp, _dp,
+                                  _dp, _dp, _dp]
+
+
+def _ptr(a: Optional[np.ndarray]):
+    if a is None:
+        return C.cast(None, _dp)
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+# ----------------------------------------------------------------------------- 1D
+
+
+@dataclass
+class ES1DConfig:
+    nc: int
+    L: float
+    order: int = 1
+    dt: float = 0.1
+    scheme: int = 2
+    remove_mean: bool = True
+    gamma_on: bool = True
+
+    def _c(self):
+        return _EsCfg(self.nc, self.L, self.order, self.dt, self.scheme, int(self.remove_mean),
+                      int(self.gamma_on))
+
+
+@dataclass
+class Species:
+    """Markers of one species; x and v are float64 arrays updated in place."""
+    q: float
+    m: float
+    x: np.ndarray
+    v: np.ndarray
+    w: Optional[np.ndarray] = None
+    w0: float = 0.0
+
+    def _c(self):
+        return _Species(self.q, self.m, len(self.x), _ptr(self.x), _ptr(self.v), _ptr(self.w),
+                        self.w0)
+
+
+def _sp_array(species: Sequence[Species]):
+    arr = (_Species * len(species))()
+    for i, s in enumerate(species):
+        arr[i] = s._c()
+    return arr
+
+
+def shape_weights(order: int, xi: float, nc: int):
+    idx = (C.c_long * 3)()
+    wt = (C.c_double * 3)()
+    k = lib().orc_shape_weights(order, xi, nc, idx, wt)
+    return np.array(idx[:k], dtype=np.int64), np.array(wt[:k])
+
+
+def deposit_1d(order, nc, L, x, c, J=None):
+    J = np.zeros(nc) if J is None else J
+    lib().orc_deposit_1d(order, nc, L, len(x), _ptr(x), _ptr(c), _ptr(J))
+    return J
+
+
+def gather_1d(order, nc, L, x, E):
+    Ep = np.zeros(len(x))
+    lib().orc_gather_1d(order, nc, L, len(x), _ptr(x), _ptr(E), _ptr(Ep))
+    return Ep
+
+
+def es1d_step(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray, want_gamma=False):
+    """One step; returns (fallback counts per species, Gamma arrays or None)."""
+    sp = _sp_array(species)
+    nfb = (C.c_long * len(species))()
+    gam = None
+    gptr = C.cast(None, C.POINTER(_dp))
+    if want_gamma:
+        gam = [np.zeros(len(s.x)) for s in species]
+        garr = (_dp * len(species))(*[_ptr(g) for g in gam])
+        gptr = C.cast(garr, C.POINTER(_dp))
+    rc = lib().orc_es1d_step(C.byref(cfg._c()), sp, len(species), _ptr(E), nfb, gptr)
+    assert rc == 0
+    return list(nfb), gam
+
+
+def es1d_energy(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray):
+    """Returns (KE per species, W_E)."""
+    sp = _sp_array(species)
+    ke = (C.c_double * len(species))()
+    we = C.c_double()
+    lib().orc_es1d_energy(C.byref(cfg._c()), sp, len(species), _ptr(E), ke, C.byref(we))
+    return list(ke), we.value
+
+
+def es1d_run(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray, nsteps: int):
+    """Runs nsteps; returns (TE[nsteps+1], W_E[nsteps+1], fallbacks[nsteps])."""
+    sp = _sp_array(species)
+    te = np.zeros(nsteps + 1)
+    we = np.zeros(nsteps + 1)
+    nfb = np.zeros(nsteps, dtype=np.int64)
+    rc = lib().orc_es1d_run(C.byref(cfg._c()), sp, len(species), _ptr(E), nsteps, _ptr(te),
+                            _ptr(we), nfb.ctypes.data_as(_lp))
+    assert rc == 0
+    return te, we, nfb
+
+
+def poisson_e0_1d(cfg: ES1DConfig, species: Sequence[Species]):
+    E = np.zeros(cfg.nc)
+    lib().orc_poisson_e0_1d(C.byref(cfg._c()), _sp_array(species), len(species), _ptr(E))
+    return E
+
+
+# ----------------------------------------------------------------------------- 2D3V
+
+
+@dataclass
+class EM2DConfig:
+    nx: int
+    ny: int
+    Lx: float
+    Ly: float
+    order: int = 1
+    dt: float = 0.05
+    c: float = 1.0
+    scheme: int = 2
+    gamma_on: bool = True
+
+    def _c(self):
+        return _EmCfg(self.nx, self.ny, self.Lx, self.Ly, self.order, self.dt, self.c,
+                      self.scheme, int(self.gamma_on))
+
+
+@dataclass
+class Species2D:
+    q: float
+    m: float
+    x: np.ndarray
+    y: np.ndarray
+    vx: np.ndarray
+    vy: np.ndarray
+    vz: np.ndarray
+    w: Optional[np.ndarray] = None
+    w0: float = 0.0
+
+    def _c(self):
+        return _Species2d(self.q, self.m, len(self.x), _ptr(self.x), _ptr(self.y), _ptr(self.vx),
+                          _ptr(self.vy), _ptr(self.vz), _ptr(self.w), self.w0)
+
+
+def _sp2_array(species):
+    arr = (_Species2d * len(species))()
+    for i, s in enumerate(species):
+        arr[i] = s._c()
+    return arr
+
+
+def yee_curl_e(nx, ny, hx, hy, E):
+    """E: [3, ny, nx] -> curl at the B locations, [3, ny, nx]."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    out = np.zeros_like(E)
+    lib().orc_yee_curl_e(nx, ny, hx, hy, _ptr(E[0]), _ptr(E[1]), _ptr(E[2]), _ptr(out[0]),
+                         _ptr(out[1]), _ptr(out[2]))
+    return out
+
+
+def yee_curl_b(nx, ny, hx, hy, B):
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    out = np.zeros_like(B)
+    lib().orc_yee_curl_b(nx, ny, hx, hy, _ptr(B[0]), _ptr(B[1]), _ptr(B[2]), _ptr(out[0]),
+                         _ptr(out[1]), _ptr(out[2]))
+    return out
+
+
+def vstar_solve(u, t):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    out = np.zeros(3)
+    lib().orc_vstar_solve(_ptr(u), _ptr(t), _ptr(out))
+    return out
+
+
+def em2d_step(cfg: EM2DConfig, species: Sequence[Species2D], E: np.ndarray, B: np.ndarray):
+    """E, B: float64 [3, ny, nx] (B holds B^{n-1/2}); updated in place."""
+    assert E.flags.c_contiguous and B.flags.c_contiguous
+    nfb = (C.c_long * len(species))()
+    rc = lib().orc_em2d_step(C.byref(cfg._c()), _sp2_array(species), len(species), _ptr(E),
+                             _ptr(B), nfb)
+    assert rc == 0
+    return list(nfb)
+
+
+def em2d_energy(cfg: EM2DConfig, species: Sequence[Species2D], E, B):
+    """Returns (KE per species, W_E, W_B)."""
+    ke = (C.c_double * len(species))()
+    we, wb = C.c_double(), C.c_double()
+    lib().orc_em2d_energy(C.byref(cfg._c()), _sp2_array(species), len(species), _ptr(E), _ptr(B),
+                          ke, C.byref(we), C.byref(wb))
+    return list(ke), we.value, wb.value

@@ -1,0 +1,708 @@
+/*
+ * Plain FP64 CPU oracle for the explicit energy-conserving PIC scheme of
+ * Ricketson & Hu, "An explicit, energy-conserving particle-in-cell scheme".
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * restatement of the paper's particle and field updates that the CUDA
+ * library is checked against.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code, header,
+ * table or constant with the CUDA library, and never calls it.
+ *
+ * Conventions (every function below follows them):
+ *   - all arithmetic in IEEE double, compiled with -ffp-contract=off so that
+ *     no fused multiply-add changes the rounding;
+ *   - plain loops over particles and grid nodes, in the order the paper
+ *     writes the steps, no blocking, fusion or reordering;
+ *   - per-species charge q and mass m: acceleration (q/m)(E + v x B),
+ *     current (1/|h|) sum q w v S, kinetic energy (1/2) m sum w |v|^2
+ *     (Sec. 2.1 writes the normalised single-species case q = m = 1; the
+ *     energy proofs of Eq. (exp_econs_simple) carry over term by term);
+ *   - grid nodes x_i = i h, periodic; E and J collocated on the nodes (1D).
+ *
+ * Parity status of each function is stated next to it; the pins live in
+ * tests/test_oracle_*.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Shape functions (Sec. 2.2: B-spline shapes; tent S(z) = max(0, 1-|z|/h)) */
+/* ------------------------------------------------------------------------ */
+
+static long imod(long a, long n) {
+  long r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+/*
+ * Weights of the particle at xi = x/h (in cell units) on the nodes it
+ * touches.  order 1: the tent function of Sec. 2.2 -> nodes floor(xi) and
+ * floor(xi)+1 with weights (1-f, f).  order 2: the quadratic B-spline (the
+ * next B-spline, an extension the paper allows but does not test) -> nodes
+ * i0-1, i0, i0+1 with i0 = floor(xi + 1/2), d = xi - i0 and weights
+ * (1/2 (1/2 - d)^2, 3/4 - d^2, 1/2 (1/2 + d)^2).
+ * Returns the number of nodes (order + 1); idx is reduced modulo nc.
+ * Pinned: partition of unity, linear-field reproduction, symmetry, and the
+ * B-spline as the convolution of tents (test_oracle_shapes.py).
+ */
+int orc_shape_weights(int order, double xi, long nc, long *idx, double *wt) {
+  if (order == 1) {
+    double fl = floor(xi);
+    double f = xi - fl;
+    long i = (long)fl;
+    idx[0] = imod(i, nc);
+    idx[1] = imod(i + 1, nc);
+    wt[0] = 1.0 - f;
+    wt[1] = f;
+    return 2;
+  }
+  if (order == 2) {
+    double fl = floor(xi + 0.5);
+    double d = xi - fl;
+    long i0 = (long)fl;
+    idx[0] = imod(i0 - 1, nc);
+    idx[1] = imod(i0, nc);
+    idx[2] = imod(i0 + 1, nc);
+    wt[0] = 0.5 * (0.5 - d) * (0.5 - d);
+    wt[1] = 0.75 - d * d;
+    wt[2] = 0.5 * (0.5 + d) * (0.5 + d);
+    return 3;
+  }
+  return 0;
+}
+
+/* Periodic wrap of a position into [0, L). */
+static double wrap(double x, double L) {
+  double y = x - L * floor(x / L);
+  if (y >= L) y -= L;
+  if (y < 0.0) y = 0.0;
+  return y;
+}
+
+/*
+ * Deposition, Sec. 2.2: j_h += (1/h) sum_p c_p S(x_h - x_p), where the
+ * caller passes c_p = q w_p v_p (current) or c_p = q w_p (charge).
+ * Accumulates into J (nc nodes), does not clear it.
+ */
+void orc_deposit_1d(int order, long nc, double L, long n, const double *x,
+                    const double *c, double *J) {
+  double h = L / (double)nc;
+  for (long p = 0; p < n; p++) {
+    long idx[3];
+    double wt[3];
+    int k = orc_shape_weights(order, x[p] / h, nc, idx, wt);
+    for (int j = 0; j < k; j++) J[idx[j]] += c[p] * wt[j] / h;
+  }
+}
+
+/* Interpolation, Sec. 2.2: E_p = sum_h E_h S(x_p - x_h). */
+void orc_gather_1d(int order, long nc, double L, long n, const double *x,
+                   const double *E, double *Ep) {
+  double h = L / (double)nc;
+  for (long p = 0; p < n; p++) {
+    long idx[3];
+    double wt[3];
+    int k = orc_shape_weights(order, x[p] / h, nc, idx, wt);
+    double s = 0.0;
+    for (int j = 0; j < k; j++) s += E[idx[j]] * wt[j];
+    Ep[p] = s;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* 1D1V electrostatic scheme, Ampere form (Secs. 3.2-3.3)                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  long nc;          /* grid nodes */
+  double L;         /* periodic length */
+  int order;        /* shape order 1 | 2 */
+  double dt;
+  int scheme;       /* 1 = ESEC1 (Eq. naivetranslation + Eq. PICmodification),
+                       2 = ESEC2 (Eq. good_translation) */
+  int remove_mean;  /* 1: E -= dt (J - <J>)  (only div j drives E in the
+                       Ampere form, Eq. ampere); 0: E -= dt J literally */
+  int gamma_on;     /* 1: energy correction of Eq. opt_solution;
+                       0: naive scheme, v^{n+1} = v^dagger (ablation) */
+} orc_es1d_cfg;
+
+typedef struct {
+  double q, m;
+  long n;
+  double *x;        /* [n] positions, updated in place */
+  double *v;        /* [n] velocities, updated in place */
+  const double *w;  /* [n] weights or NULL for uniform w0 */
+  double w0;
+} orc_species;
+
+static double weight_of(const orc_species *s, long p) {
+  return s->w ? s->w[p] : s->w0;
+}
+
+/* Ampere update of the grid field: Eout = Ein - tau (J - <J>) (Eq. ampere;
+ * the mean of J is removed when cfg->remove_mean). */
+static void ampere_update(const orc_es1d_cfg *cfg, const double *Ein,
+                          const double *J, double tau, double *Eout) {
+  double mean = 0.0;
+  if (cfg->remove_mean) {
+    for (long i = 0; i < cfg->nc; i++) mean += J[i];
+    mean /= (double)cfg->nc;
+  }
+  for (long i = 0; i < cfg->nc; i++) Eout[i] = Ein[i] - tau * (J[i] - mean);
+}
+
+/*
+ * One time step of ESEC1 / ESEC2 (1D1V, B = 0), in the paper's order:
+ *
+ *   x*      = x^n + dt/2 v^n                                   (both)
+ *   j^{n,*} = deposit of v^n at x*;  E* = E^n - dt/2 j^{n,*}   (ESEC2 only,
+ *                                                    Eq. doublestardef)
+ *   E**_p   = gather of E* at x*  (ESEC1: E^{n,*}_p = gather of E^n at x*)
+ *   v*      = v^n + dt/2 (q/m) E**_p
+ *   x^{n+1} = x^n + dt v*;   x^{n+1/2} = x^n + dt/2 v*
+ *   j^{*,n+1/2} = deposit of v* at x^{n+1/2}
+ *   E^{n+1} = E^n - dt j^{*,n+1/2};   E^{n+1/2} = (E^n + E^{n+1})/2
+ *   E^{n+1/2}_p = gather of E^{n+1/2} at x^{n+1/2}
+ *   v^dag   = v^n + dt (q/m) E^{n+1/2}_p                  (Eq. PICmodification)
+ *   R       = |v^n|^2 + 2 v* . (v^dag - v^n)
+ *   v^{n+1} = Gamma v^dag, Gamma = sqrt(R) / |v^dag|      (Eq. opt_solution,
+ *                                               rearranged form of Sec. 3.2)
+ *   If R < 0 (imaginary Gamma) or |v^dag| = 0, Gamma := 1 and the particle is
+ *   counted (Sec. 3.2 and Sec. 5.1).
+ *
+ * E is updated in place.  nfallback[s] receives the per-species count.
+ * gamma_out: NULL or nsp pointers (each NULL or [n]) receiving Gamma (1 for
+ * fallbacks).  Returns 0.
+ * Pinned: energy identity Eq. (exp_econs_simple), uniform-field closed form,
+ * Gamma = 1 + O(dt^3) / O(dt^4), cold plasma frequency, Landau and
+ * two-stream rates, brute force (test_oracle_es1d.py).
+ */
+int orc_es1d_step(const orc_es1d_cfg *cfg, orc_species *sp, int nsp,
+                  double *E, long *nfallback, double *const *gamma_out) {
+  if (nsp <= 0 || cfg->nc <= 0) return -1;
+  long nc = cfg->nc;
+  double L = cfg->L, dt = cfg->dt, h = L / (double)nc;
+  double *Estar = (double *)calloc((size_t)nc, sizeof(double));
+  double *J = (double *)calloc((size_t)nc, sizeof(double));
+  double *Enew = (double *)calloc((size_t)nc, sizeof(double));
+  double *Ehalf = (double *)calloc((size_t)nc, sizeof(double));
+  double **xs = (double **)calloc((size_t)nsp, sizeof(double *));
+  double **vs = (double **)calloc((size_t)nsp, sizeof(double *));
+  double **xh = (double **)calloc((size_t)nsp, sizeof(double *));
+  for (int s = 0; s < nsp; s++) {
+    xs[s] = (double *)calloc((size_t)sp[s].n + 1, sizeof(double));
+    vs[s] = (double *)calloc((size_t)sp[s].n + 1, sizeof(double));
+    xh[s] = (double *)calloc((size_t)sp[s].n + 1, sizeof(double));
+  }
+
+  /* x* = x^n + dt/2 v^n */
+  for (int s = 0; s < nsp; s++)
+    for (long p = 0; p < sp[s].n; p++)
+      xs[s][p] = wrap(sp[s].x[p] + 0.5 * dt * sp[s].v[p], L);
+
+  if (cfg->scheme == 2) {
+    /* j^{n,*}: v^n deposited at x*, then E* = E^n - dt/2 j^{n,*} */
+    for (long i = 0; i < nc; i++) J[i] = 0.0;
+    for (int s = 0; s < nsp; s++)
+      for (long p = 0; p < sp[s].n; p++) {
+        long idx[3];
+        double wt[3];
+        int k = orc_shape_weights(cfg->order, xs[s][p] / h, nc, idx, wt);
+        double c = sp[s].q * weight_of(&sp[s], p) * sp[s].v[p];
+        for (int j = 0; j < k; j++) J[idx[j]] += c * wt[j] / h;
+      }
+    ampere_update(cfg, E, J, 0.5 * dt, Estar);
+  } else {
+    for (long i = 0; i < nc; i++) Estar[i] = E[i];
+  }
+
+  /* v* from the field gathered at x*; then x^{n+1/2} */
+  for (int s = 0; s < nsp; s++) {
+    double qm = sp[s].q / sp[s].m;
+    for (long p = 0; p < sp[s].n; p++) {
+      long idx[3];
+      double wt[3];
+      int k = orc_shape_weights(cfg->order, xs[s][p] / h, nc, idx, wt);
+      double Ess = 0.0;
+      for (int j = 0; j < k; j++) Ess += Estar[idx[j]] * wt[j];
+      vs[s][p] = sp[s].v[p] + 0.5 * dt * qm * Ess;
+      xh[s][p] = wrap(sp[s].x[p] + 0.5 * dt * vs[s][p], L);
+    }
+  }
+
+  /* j^{*,n+1/2}: v* deposited at x^{n+1/2}; E^{n+1}, E^{n+1/2} */
+  for (long i = 0; i < nc; i++) J[i] = 0.0;
+  for (int s = 0; s < nsp; s++)
+    for (long p = 0; p < sp[s].n; p++) {
+      long idx[3];
+      double wt[3];
+      int k = orc_shape_weights(cfg->order, xh[s][p] / h, nc, idx, wt);
+      double c = sp[s].q * weight_of(&sp[s], p) * vs[s][p];
+      for (int j = 0; j < k; j++) J[idx[j]] += c * wt[j] / h;
+    }
+  ampere_update(cfg, E, J, dt, Enew);
+  for (long i = 0; i < nc; i++) Ehalf[i] = 0.5 * (E[i] + Enew[i]);
+
+  /* v^dag, Gamma, v^{n+1}; x^{n+1} */
+  for (int s = 0; s < nsp; s++) {
+    double qm = sp[s].q / sp[s].m;
+    long count = 0;
+    for (long p = 0; p < sp[s].n; p++) {
+      long idx[3];
+      double wt[3];
+      int k = orc_shape_weights(cfg->order, xh[s][p] / h, nc, idx, wt);
+      double Ep = 0.0;
+      for (int j = 0; j < k; j++) Ep += Ehalf[idx[j]] * wt[j];
+      double vn = sp[s].v[p];
+      double vstar = vs[s][p];
+      double vdag = vn + dt * qm * Ep;
+      double R = vn * vn + 2.0 * vstar * (vdag - vn);
+      double vd2 = vdag * vdag;
+      double gamma = 1.0;
+      if (cfg->gamma_on) {
+        if (R < 0.0 || vd2 == 0.0) {
+          count++;
+        } else {
+          gamma = sqrt(R) / sqrt(vd2);
+        }
+      }
+      if (gamma_out && gamma_out[s]) gamma_out[s][p] = gamma;
+      sp[s].v[p] = gamma == 1.0 ? vdag : vdag * gamma;
+      sp[s].x[p] = wrap(sp[s].x[p] + dt * vstar, L);
+    }
+    if (nfallback) nfallback[s] = count;
+  }
+  for (long i = 0; i < nc; i++) E[i] = Enew[i];
+
+  for (int s = 0; s < nsp; s++) {
+    free(xs[s]);
+    free(vs[s]);
+    free(xh[s]);
+  }
+  free(xs);
+  free(vs);
+  free(xh);
+  free(Estar);
+  free(J);
+  free(Enew);
+  free(Ehalf);
+  return 0;
+}
+
+/*
+ * Energies of Sec. 5.1: KE_s = (1/2) m_s sum_p w_p v_p^2 per species and
+ * W_E = (1/2) h sum_h E_h^2.  Pinned through the energy identity tests.
+ */
+void orc_es1d_energy(const orc_es1d_cfg *cfg, const orc_species *sp, int nsp,
+                     const double *E, double *KE, double *WE) {
+  double h = cfg->L / (double)cfg->nc;
+  for (int s = 0; s < nsp; s++) {
+    double acc = 0.0;
+    for (long p = 0; p < sp[s].n; p++)
+      acc += weight_of(&sp[s], p) * sp[s].v[p] * sp[s].v[p];
+    KE[s] = 0.5 * sp[s].m * acc;
+  }
+  double we = 0.0;
+  for (long i = 0; i < cfg->nc; i++) we += E[i] * E[i];
+  *WE = 0.5 * h * we;
+}
+
+/*
+ * nsteps steps; TE[k] = total energy after k steps (TE[0] initial),
+ * nfb[k] = fallback count (all species) of step k.  Returns 0.
+ */
+int orc_es1d_run(const orc_es1d_cfg *cfg, orc_species *sp, int nsp, double *E,
+                 long nsteps, double *TE, double *WE_hist, long *nfb) {
+  double *KE = (double *)calloc((size_t)nsp, sizeof(double));
+  long *cnt = (long *)calloc((size_t)nsp, sizeof(long));
+  double we;
+  orc_es1d_energy(cfg, sp, nsp, E, KE, &we);
+  double te = we;
+  for (int s = 0; s < nsp; s++) te += KE[s];
+  if (TE) TE[0] = te;
+  if (WE_hist) WE_hist[0] = we;
+  for (long k = 0; k < nsteps; k++) {
+    orc_es1d_step(cfg, sp, nsp, E, cnt, NULL);
+    long c = 0;
+    for (int s = 0; s < nsp; s++) c += cnt[s];
+    if (nfb) nfb[k] = c;
+    if (TE || WE_hist) {
+      orc_es1d_energy(cfg, sp, nsp, E, KE, &we);
+      te = we;
+      for (int s = 0; s < nsp; s++) te += KE[s];
+      if (TE) TE[k + 1] = te;
+      if (WE_hist) WE_hist[k + 1] = we;
+    }
+  }
+  free(KE);
+  free(cnt);
+  return 0;
+}
+
+/*
+ * Initial field from Gauss's law in the Poisson form, Eq. (poisson):
+ * dE/dx = rho - rho_background, rho deposited with the same shape.  Solved
+ * spectrally (the paper's test code is pseudospectral, Sec. 5): with the
+ * discrete Fourier transform rho_k = sum_j rho_j exp(-2 pi i j k / N),
+ * E_k = rho_k / (i kappa_k), kappa_k = 2 pi k / L; the k = 0 mode (the
+ * neutralising background) and, for even N, the Nyquist mode are zeroed.
+ * Plain O(N^2) transform.  Pinned: a single cosine density gives the exact
+ * sine field; the discrete derivative of E reproduces rho - <rho>.
+ */
+void orc_poisson_e0_1d(const orc_es1d_cfg *cfg, const orc_species *sp,
+                       int nsp, double *E) {
+  long nc = cfg->nc;
+  double L = cfg->L, h = L / (double)nc;
+  double *rho = (double *)calloc((size_t)nc, sizeof(double));
+  for (int s = 0; s < nsp; s++)
+    for (long p = 0; p < sp[s].n; p++) {
+      long idx[3];
+      double wt[3];
+      int k = orc_shape_weights(cfg->order, sp[s].x[p] / h, nc, idx, wt);
+      double c = sp[s].q * weight_of(&sp[s], p);
+      for (int j = 0; j < k; j++) rho[idx[j]] += c * wt[j] / h;
+    }
+  const double twopi = 6.283185307179586476925286766559;
+  for (long j = 0; j < nc; j++) E[j] = 0.0;
+  for (long k = 1; k < nc; k++) {
+    if (nc % 2 == 0 && k == nc / 2) continue;
+    double re = 0.0, im = 0.0;
+    for (long j = 0; j < nc; j++) {
+      double ang = -twopi * (double)((j * k) % nc) / (double)nc;
+      re += rho[j] * cos(ang);
+      im += rho[j] * sin(ang);
+    }
+    long ks = k < nc - k ? k : k - nc; /* signed frequency */
+    double kappa = twopi * (double)ks / L;
+    /* E_k = rho_k / (i kappa) = (im - i re) / kappa */
+    double ere = im / kappa, eim = -re / kappa;
+    for (long j = 0; j < nc; j++) {
+      double ang = twopi * (double)((j * k) % nc) / (double)nc;
+      E[j] += (ere * cos(ang) - eim * sin(ang)) / (double)nc;
+    }
+  }
+  free(rho);
+}
+
+/* ------------------------------------------------------------------------ */
+/* 2D3V electromagnetic scheme with the leapfrog / Yee field step (Sec. 4.1) */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Yee lattice on a periodic nx x ny grid (Sec. 2.2.2): field components are
+ * stored as [ny][nx] arrays; component c of E (and of J) sits at
+ * ((i + ox) hx, (j + oy) hy) and component c of B at the face centre:
+ *   Ex (1/2, 0)   Ey (0, 1/2)   Ez (0, 0)
+ *   Bx (0, 1/2)   By (1/2, 0)   Bz (1/2, 1/2)
+ * Gather of E_c and deposit of J_c use the same tensor-product B-spline
+ * shape centred on component c's nodes, so the pairing of Eq.
+ * (exp_econs_simple) holds component by component.
+ */
+typedef struct {
+  long nx, ny;
+  double Lx, Ly;
+  int order;   /* 1 | 2 */
+  double dt;
+  double c;    /* speed of light (dimensionless) */
+  int scheme;  /* 1 = ESEC1-type v*, 2 = the j^{n,*} / E* stage of Eq.
+                  (EMleapfrog) */
+  int gamma_on;
+} orc_em2d_cfg;
+
+typedef struct {
+  double q, m;
+  long n;
+  double *x, *y;          /* [n] */
+  double *vx, *vy, *vz;   /* [n] */
+  const double *w;
+  double w0;
+} orc_species2d;
+
+static const double OFFX_E[3] = {0.5, 0.0, 0.0}, OFFY_E[3] = {0.0, 0.5, 0.0};
+static const double OFFX_B[3] = {0.0, 0.5, 0.5}, OFFY_B[3] = {0.5, 0.0, 0.5};
+
+/* Tensor-product weights of component with offsets (ox, oy). */
+static int shape2d(const orc_em2d_cfg *g, double x, double y, double ox,
+                   double oy, long *idx, double *wt) {
+  long ix[3], iy[3];
+  double wx[3], wy[3];
+  double hx = g->Lx / (double)g->nx, hy = g->Ly / (double)g->ny;
+  int kx = orc_shape_weights(g->order, x / hx - ox, g->nx, ix, wx);
+  int ky = orc_shape_weights(g->order, y / hy - oy, g->ny, iy, wy);
+  int k = 0;
+  for (int b = 0; b < ky; b++)
+    for (int a = 0; a < kx; a++) {
+      idx[k] = iy[b] * g->nx + ix[a];
+      wt[k] = wx[a] * wy[b];
+      k++;
+    }
+  return k;
+}
+
+#define AT(F, i, j) (F)[imod((j), ny) * nx + imod((i), nx)]
+
+/* Discrete curl of E, evaluated on the B locations (Yee differences). */
+void orc_yee_curl_e(long nx, long ny, double hx, double hy, const double *Ex,
+                    const double *Ey, const double *Ez, double *cx, double *cy,
+                    double *cz) {
+  for (long j = 0; j < ny; j++)
+    for (long i = 0; i < nx; i++) {
+      cx[j * nx + i] = (AT(Ez, i, j + 1) - AT(Ez, i, j)) / hy;
+      cy[j * nx + i] = -(AT(Ez, i + 1, j) - AT(Ez, i, j)) / hx;
+      cz[j * nx + i] = (AT(Ey, i + 1, j) - AT(Ey, i, j)) / hx -
+                       (AT(Ex, i, j + 1) - AT(Ex, i, j)) / hy;
+    }
+}
+
+/* Discrete curl of B, evaluated on the E locations (Yee differences). */
+void orc_yee_curl_b(long nx, long ny, double hx, double hy, const double *Bx,
+                    const double *By, const double *Bz, double *cx, double *cy,
+                    double *cz) {
+  for (long j = 0; j < ny; j++)
+    for (long i = 0; i < nx; i++) {
+      cx[j * nx + i] = (AT(Bz, i, j) - AT(Bz, i, j - 1)) / hy;
+      cy[j * nx + i] = -(AT(Bz, i, j) - AT(Bz, i - 1, j)) / hx;
+      cz[j * nx + i] = (AT(By, i, j) - AT(By, i - 1, j)) / hx -
+                       (AT(Bx, i, j) - AT(Bx, i, j - 1)) / hy;
+    }
+}
+#undef AT
+
+static double wt2d(const orc_species2d *s, long p) {
+  return s->w ? s->w[p] : s->w0;
+}
+
+/* Deposit q w v_c at (px, py) for the three components into J[3][ncell]. */
+static void deposit_em(const orc_em2d_cfg *g, const orc_species2d *s, long n,
+                       const double *px, const double *py, const double *ux,
+                       const double *uy, const double *uz, double *J) {
+  long ncell = g->nx * g->ny;
+  double area = (g->Lx / (double)g->nx) * (g->Ly / (double)g->ny);
+  for (long p = 0; p < n; p++) {
+    const double u[3] = {ux[p], uy[p], uz[p]};
+    double qw = s->q * wt2d(s, p);
+    for (int c = 0; c < 3; c++) {
+      long idx[9];
+      double wt[9];
+      int k = shape2d(g, px[p], py[p], OFFX_E[c], OFFY_E[c], idx, wt);
+      for (int a = 0; a < k; a++) J[c * ncell + idx[a]] += qw * u[c] * wt[a] / area;
+    }
+  }
+}
+
+static void gather3(const orc_em2d_cfg *g, const double *F, const double *ox,
+                    const double *oy, double x, double y, double out[3]) {
+  long ncell = g->nx * g->ny;
+  for (int c = 0; c < 3; c++) {
+    long idx[9];
+    double wt[9];
+    int k = shape2d(g, x, y, ox[c], oy[c], idx, wt);
+    double s = 0.0;
+    for (int a = 0; a < k; a++) s += F[c * ncell + idx[a]] * wt[a];
+    out[c] = s;
+  }
+}
+
+static void cross(const double a[3], const double b[3], double r[3]) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/*
+ * v* of v* = v^n + dt/2 (q/m)(E** + v* x B): linear in v*; with
+ * u = v^n + (q/m)(dt/2) E** and t = (q/m)(dt/2) B the solution is
+ * v* = (u + u x t + (u.t) t) / (1 + |t|^2).  Pinned: it satisfies the
+ * implicit relation, and with E = 0 the push is the symmetric Boris
+ * rotation of Sec. 2.2.1 (test_oracle_em2d.py).
+ */
+void orc_vstar_solve(const double u[3], const double t[3], double out[3]) {
+  double uxt[3];
+  cross(u, t, uxt);
+  double ut = u[0] * t[0] + u[1] * t[1] + u[2] * t[2];
+  double tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  for (int c = 0; c < 3; c++) out[c] = (u[c] + uxt[c] + ut * t[c]) / (1.0 + tt);
+}
+
+/*
+ * One step of Eq. (EMleapfrog):
+ *   x*          = x^n + dt/2 v^n
+ *   B^{n+1/2}   = B^{n-1/2} - dt curl_h E^n
+ *   E*          = E^n + dt/2 (c^2 curl_h B^{n+1/2} - j^{n,*})   (scheme 2;
+ *                 scheme 1 uses E^n)
+ *   v*          = v^n + dt/2 (q/m)(E**_p + v* x B^{n+1/2}_p(x*))
+ *   x^{n+1}     = x^n + dt v*,   x^{n+1/2} = x^n + dt/2 v*
+ *   E^{n+1}     = E^n + dt (c^2 curl_h B^{n+1/2} - j^{*,n+1/2})
+ *   v^dag       = v^n + dt (q/m)(E^{n+1/2}_p + v* x B^{n+1/2}_p)
+ *   v^{n+1}     = Gamma v^dag  (Eq. opt_solution; fallback Gamma := 1)
+ * The B in v^dag is gathered at x^{n+1/2}, as in the electromagnetic
+ * schemes of Secs. 3.4 and 4.1.  E (3 x ncell) and B (3 x ncell, holding
+ * B^{n-1/2} on entry and B^{n+1/2} on exit) are updated in place.
+ */
+int orc_em2d_step(const orc_em2d_cfg *g, orc_species2d *sp, int nsp, double *E,
+                  double *B, long *nfallback) {
+  if (nsp <= 0 || g->nx <= 0 || g->ny <= 0) return -1;
+  long nx = g->nx, ny = g->ny, ncell = nx * ny;
+  double dt = g->dt, c2 = g->c * g->c;
+  double hx = g->Lx / (double)nx, hy = g->Ly / (double)ny;
+  double *cE = (double *)calloc((size_t)(3 * ncell), sizeof(double));
+  double *cB = (double *)calloc((size_t)(3 * ncell), sizeof(double));
+  double *Bh = (double *)calloc((size_t)(3 * ncell), sizeof(double));
+  double *Es = (double *)calloc((size_t)(3 * ncell), sizeof(double));
+  double *J = (double *)calloc((size_t)(3 * ncell), sizeof(double));
+  double *En = (double *)calloc((size_t)(3 * ncell), sizeof(double));
+  double *Eh = (double *)calloc((size_t)(3 * ncell), sizeof(double));
+
+  /* B^{n+1/2} = B^{n-1/2} - dt curl E^n */
+  orc_yee_curl_e(nx, ny, hx, hy, E, E + ncell, E + 2 * ncell, cE, cE + ncell,
+                 cE + 2 * ncell);
+  for (long a = 0; a < 3 * ncell; a++) Bh[a] = B[a] - dt * cE[a];
+  orc_yee_curl_b(nx, ny, hx, hy, Bh, Bh + ncell, Bh + 2 * ncell, cB, cB + ncell,
+                 cB + 2 * ncell);
+
+  for (int s = 0; s < nsp; s++) {
+    orc_species2d *S = &sp[s];
+    long n = S->n;
+    double qm = S->q / S->m;
+    double *xs = (double *)calloc((size_t)n + 1, sizeof(double));
+    double *ys = (double *)calloc((size_t)n + 1, sizeof(double));
+    (void)qm;
+    for (long p = 0; p < n; p++) {
+      xs[p] = wrap(S->x[p] + 0.5 * dt * S->vx[p], g->Lx);
+      ys[p] = wrap(S->y[p] + 0.5 * dt * S->vy[p], g->Ly);
+    }
+    if (g->scheme == 2) deposit_em(g, S, n, xs, ys, S->vx, S->vy, S->vz, J);
+    free(xs);
+    free(ys);
+  }
+  for (long a = 0; a < 3 * ncell; a++)
+    Es[a] = g->scheme == 2 ? E[a] + 0.5 * dt * (c2 * cB[a] - J[a]) : E[a];
+
+  /* per species: v*, x^{n+1/2}, x^{n+1}; deposit j^{*,n+1/2} */
+  double **vsx = (double **)calloc((size_t)nsp, sizeof(double *));
+  double **vsy = (double **)calloc((size_t)nsp, sizeof(double *));
+  double **vsz = (double **)calloc((size_t)nsp, sizeof(double *));
+  double **xh = (double **)calloc((size_t)nsp, sizeof(double *));
+  double **yh = (double **)calloc((size_t)nsp, sizeof(double *));
+  for (long a = 0; a < 3 * ncell; a++) J[a] = 0.0;
+  for (int s = 0; s < nsp; s++) {
+    orc_species2d *S = &sp[s];
+    long n = S->n;
+    double qm = S->q / S->m;
+    vsx[s] = (double *)calloc((size_t)n + 1, sizeof(double));
+    vsy[s] = (double *)calloc((size_t)n + 1, sizeof(double));
+    vsz[s] = (double *)calloc((size_t)n + 1, sizeof(double));
+    xh[s] = (double *)calloc((size_t)n + 1, sizeof(double));
+    yh[s] = (double *)calloc((size_t)n + 1, sizeof(double));
+    for (long p = 0; p < n; p++) {
+      double xs = wrap(S->x[p] + 0.5 * dt * S->vx[p], g->Lx);
+      double ys = wrap(S->y[p] + 0.5 * dt * S->vy[p], g->Ly);
+      double Ess[3], Bs[3], u[3], t[3], vst[3];
+      gather3(g, Es, OFFX_E, OFFY_E, xs, ys, Ess);
+      gather3(g, Bh, OFFX_B, OFFY_B, xs, ys, Bs);
+      const double vn[3] = {S->vx[p], S->vy[p], S->vz[p]};
+      for (int c = 0; c < 3; c++) {
+        u[c] = vn[c] + qm * 0.5 * dt * Ess[c];
+        t[c] = qm * 0.5 * dt * Bs[c];
+      }
+      orc_vstar_solve(u, t, vst);
+      vsx[s][p] = vst[0];
+      vsy[s][p] = vst[1];
+      vsz[s][p] = vst[2];
+      xh[s][p] = wrap(S->x[p] + 0.5 * dt * vst[0], g->Lx);
+      yh[s][p] = wrap(S->y[p] + 0.5 * dt * vst[1], g->Ly);
+    }
+    deposit_em(g, S, n, xh[s], yh[s], vsx[s], vsy[s], vsz[s], J);
+  }
+  for (long a = 0; a < 3 * ncell; a++) {
+    En[a] = E[a] + dt * (c2 * cB[a] - J[a]);
+    Eh[a] = 0.5 * (E[a] + En[a]);
+  }
+
+  for (int s = 0; s < nsp; s++) {
+    orc_species2d *S = &sp[s];
+    double qm = S->q / S->m;
+    long count = 0;
+    for (long p = 0; p < S->n; p++) {
+      double Ep[3], Bp[3], vxb[3], vdag[3];
+      gather3(g, Eh, OFFX_E, OFFY_E, xh[s][p], yh[s][p], Ep);
+      gather3(g, Bh, OFFX_B, OFFY_B, xh[s][p], yh[s][p], Bp);
+      const double vn[3] = {S->vx[p], S->vy[p], S->vz[p]};
+      const double vst[3] = {vsx[s][p], vsy[s][p], vsz[s][p]};
+      cross(vst, Bp, vxb);
+      for (int c = 0; c < 3; c++) vdag[c] = vn[c] + dt * qm * (Ep[c] + vxb[c]);
+      double R = vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2] +
+                 2.0 * (vst[0] * (vdag[0] - vn[0]) + vst[1] * (vdag[1] - vn[1]) +
+                        vst[2] * (vdag[2] - vn[2]));
+      double vd2 = vdag[0] * vdag[0] + vdag[1] * vdag[1] + vdag[2] * vdag[2];
+      double gamma = 1.0;
+      if (g->gamma_on) {
+        if (R < 0.0 || vd2 == 0.0)
+          count++;
+        else
+          gamma = sqrt(R) / sqrt(vd2);
+      }
+      S->vx[p] = gamma == 1.0 ? vdag[0] : vdag[0] * gamma;
+      S->vy[p] = gamma == 1.0 ? vdag[1] : vdag[1] * gamma;
+      S->vz[p] = gamma == 1.0 ? vdag[2] : vdag[2] * gamma;
+      S->x[p] = wrap(S->x[p] + dt * vst[0], g->Lx);
+      S->y[p] = wrap(S->y[p] + dt * vst[1], g->Ly);
+    }
+    if (nfallback) nfallback[s] = count;
+    free(vsx[s]);
+    free(vsy[s]);
+    free(vsz[s]);
+    free(xh[s]);
+    free(yh[s]);
+  }
+  for (long a = 0; a < 3 * ncell; a++) {
+    E[a] = En[a];
+    B[a] = Bh[a];
+  }
+  free(vsx);
+  free(vsy);
+  free(vsz);
+  free(xh);
+  free(yh);
+  free(cE);
+  free(cB);
+  free(Bh);
+  free(Es);
+  free(J);
+  free(En);
+  free(Eh);
+  return 0;
+}
+
+/*
+ * Energies of Sec. 4.1 for the state (x^n, v^n, E^n, B^{n-1/2}):
+ *   KE   = (1/2) m sum w |v|^2 per species,
+ *   W_E  = (1/2) |h| sum |E^n|^2,
+ *   W_B  = (c^2/2) |h| sum B^{n+1/2} . B^{n-1/2},
+ * with B^{n+1/2} = B^{n-1/2} - dt curl_h E^n (the next leapfrog half).
+ */
+void orc_em2d_energy(const orc_em2d_cfg *g, const orc_species2d *sp, int nsp,
+                     const double *E, const double *B, double *KE, double *WE,
+                     double *WB) {
+  long nx = g->nx, ny = g->ny, ncell = nx * ny;
+  double hx = g->Lx / (double)nx, hy = g->Ly / (double)ny, area = hx * hy;
+  for (int s = 0; s < nsp; s++) {
+    double acc = 0.0;
+    for (long p = 0; p < sp[s].n; p++)
+      acc += wt2d(&sp[s], p) * (sp[s].vx[p] * sp[s].vx[p] + sp[s].vy[p] * sp[s].vy[p] +
+                                sp[s].vz[p] * sp[s].vz[p]);
+    KE[s] = 0.5 * sp[s].m * acc;
+  }
+  double we = 0.0;
+  for (long a = 0; a < 3 * ncell; a++) we += E[a] * E[a];
+  *WE = 0.5 * area * we;
+  double *cE = (double *)calloc((size_t)(3 * ncell), sizeof(double));
+  orc_yee_curl_e(nx, ny, hx, hy, E, E + ncell, E + 2 * ncell, cE, cE + ncell,
+                 cE + 2 * ncell);
+  double wb = 0.0;
+  for (long a = 0; a < 3 * ncell; a++) wb += (B[a] - g->dt * cE[a]) * B[a];
+  *WB = 0.5 * g->c * g->c * area * wb;
+  free(cE);
+}
