@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Throughput of the explicit energy-conserving PIC step on one GB300.
+
+Workload: the 1D1V two-stream instability, 2^23 electron markers, 512 cells,
+quadratic shapes, dt = 0.05, ESEC2 (Sec. 3.3), synthetic and seeded.  A "step"
+is one full time step of the scheme (both particle passes, the field updates
+and the per-step energy and fallback reduction).  The metric is particle-steps
+per second (markers x steps / time); each form of the library is reported with
+its energy error max_n |TE^n - TE^0| / TE^0 over the run.
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
+(independent seed): weak scaling, no data-path collective.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s on 1 GB300 (plain FP64 vs chosen form) at |dW/W| <= 1e-11"
+UNIT = "particle-steps/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20          # > 2x the 126.5 MB L2
+# Algorithmic bytes per marker per launch (state that must cross HBM once per
+# barrier-separated pass; v* is recomputed in pass E, never stored).
+ALGO_BYTES = {  # (precision, kind) -> bytes per marker
+    ("fp64", 0): 16, ("fp64", 1): 32,      # pass C reads x, v; pass E reads + writes
+    ("mixed", 0): 12, ("mixed", 1): 24,    # 4 B position + 8 B velocity pair
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--markers", type=int, default=1 << 23)
+    ap.add_argument("--forms", default="mixed,fp64",
+                    help="library forms to time; the first available is the headline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Max of a scalar over all ranks (identity for one rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def workload(markers: int, seed: int):
+    from paper_2411_09605_gb300 import workloads as W
+    return W.two_stream(n=markers, seed=seed)
+
+
+def config_dict(prob, extra=None):
+    d = {"workload": "two_stream_1d1v", "markers": prob.n_markers, "cells": prob.nc,
+         "shape_order": prob.order, "dt": prob.dt, "L": round(prob.L, 6), "scheme": "ESEC2",
+         "v0": 3.0, "vth": 0.1, "seed_amplitude": 1e-3,
+         "l2": "flushed (512 MiB write) before every timed step"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# --------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, enabled: bool = True):
+        self.index, self.enabled, self.proc = index, enabled, None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def __enter__(self):
+        if self.enabled:
+            try:
+                self.f = open(self.path, "w")
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                     "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                    stderr=subprocess.DEVNULL)
+            except OSError:
+                self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- our arm
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def time_form(prob, precision_name: str, steps: int, warmup: int, profile_steps: int, stream,
+              flush_buf):
+    """Device-timed throughput of one library form on the resident workload."""
+    import torch
+    from paper_2411_09605_gb300 import pic
+    prec = pic.PIC_PREC_MIXED if precision_name == "mixed" else pic.PIC_PREC_FP64
+    s = prob.species[0]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x_d = torch.from_numpy(s.x).to(dev)
+    v_d = torch.from_numpy(s.v).to(dev)
+    cfg = pic.make_config(prob.nc, prob.L, prob.dt, prob.order, pic.PIC_SCHEME_ESEC2, prec,
+                          ptr_on_device=1, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    h = pic.pic_init(cfg, [dict(q=s.q, m=s.m, x=x_d, v=v_d, w=None, w0=s.w0)])
+    del x_d, v_d
+    try:
+        te_dev = torch.zeros(max(1, warmup), dtype=torch.float64, device=dev)
+        fb_dev = torch.zeros(max(1, warmup), dtype=torch.int64, device=dev)
+        if warmup:
+            pic.pic_step(h, warmup, fb_dev, te_dev)
+        _, _, _, te0 = pic.pic_energy(h, 1)
+        torch.cuda.synchronize()
+        launches0 = pic.pic_launch_count(h)
+        evs = []
+        fbs, tes = [], []
+        for k in range(steps):
+            flush_buf.zero_()                          # L2 flush, outside the timed region
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pic.pic_step_async(h, 1)
+            b.record(stream)
+            evs.append((a, b))
+            if (k + 1) % 1000 == 0:
+                fb, te = pic.pic_read_stats(h)
+                fbs.append(fb)
+                tes.append(te)
+        fb, te = pic.pic_read_stats(h)
+        fbs.append(fb)
+        tes.append(te)
+        torch.cuda.synchronize()
+        launches = pic.pic_launch_count(h) - launches0
+        step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+        fb = np.concatenate(fbs)
+        te = np.concatenate(tes)
+        # per-kernel durations for the roofline (separate, profiled steps)
+        pic.pic_set_profiling(h, True)
+        for k in range(profile_steps):
+            flush_buf.zero_()
+            pic.pic_step_async(h, 1)
+        pic.pic_read_stats(h)
+        kern = {}
+        for kind, name in ((0, "pass_c"), (1, "pass_e"), (2, "finalize"), (3, "sort")):
+            n, ms = pic.pic_profile(h, kind)
+            if n:
+                kern[name] = {"kind": kind, "launches": n, "avg_us": 1e3 * ms / n}
+        pic.pic_set_profiling(h, False)
+    finally:
+        pic.pic_free(h)
+    allte = np.concatenate([[te0], te])
+    return {"step_ms": step_ms, "fallbacks": int(fb.sum()),
+            "max_rel_dTE": float(np.max(np.abs(allte - allte[0])) / abs(allte[0])),
+            "launches": int(launches), "kernels": kern}
+
+
+def e2e_form(prob, precision_name: str, steps: int, warmup: int):
+    """End to end through the C ABI with host buffers: every step uploads the
+    marker state from pinned host memory, steps once and reads the state and the
+    step's energy/fallback back to pinned host memory."""
+    import torch
+    from paper_2411_09605_gb300 import pic
+    prec = pic.PIC_PREC_MIXED if precision_name == "mixed" else pic.PIC_PREC_FP64
+    s = prob.species[0]
+    n = len(s.x)
+    xh = torch.from_numpy(s.x.copy()).pin_memory()
+    vh = torch.from_numpy(s.v.copy()).pin_memory()
+    fb = torch.zeros(1, dtype=torch.int64).pin_memory()
+    te = torch.zeros(1, dtype=torch.float64).pin_memory()
+    cfg = pic.make_config(prob.nc, prob.L, prob.dt, prob.order, pic.PIC_SCHEME_ESEC2, prec)
+    h = pic.pic_init(cfg, [dict(q=s.q, m=s.m, x=xh.numpy(), v=vh.numpy(), w=None, w0=s.w0)])
+    try:
+        times = []
+        for k in range(warmup + steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pic.pic_set_particles(h, 0, xh.numpy(), vh.numpy())
+            pic.pic_step(h, 1, fb.numpy(), te.numpy())
+            pic.pic_get_particles(h, 0, xh.numpy(), vh.numpy())
+            t1 = time.perf_counter()
+            if k >= warmup:
+                times.append(t1 - t0)
+    finally:
+        pic.pic_free(h)
+    return {"s_per_step": float(np.mean(times)), "h2d": 16 * n, "d2h": 16 * n + 16}
+
+
+def cpu_baseline_oracle(markers: int, seed: int, budget_s: float = 12.0, max_steps: int = 40):
+    """The FP64 C oracle, as it stands, on a bounded sample of the workload."""
+    from oracle import oracle as O
+    prob = workload(markers, seed)
+    s = prob.species[0]
+    cfg = O.ES1DConfig(nc=prob.nc, L=prob.L, order=prob.order, dt=prob.dt, scheme=2)
+    sp = [O.Species(s.q, s.m, s.x.copy(), s.v.copy(), None, s.w0)]
+    E = O.poisson_e0_1d(cfg, sp)
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_steps and (time.perf_counter() - t0) < budget_s:
+        O.es1d_step(cfg, sp, E)
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": markers * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{markers} markers of the same two-stream workload x {k} steps "
+                      f"({dt:.1f} s, single-threaded FP64 C oracle)"}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    from paper_2411_09605_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2411_09605_gb300 import pic
+    pic.lib()
+
+    prob = workload(args.markers, seed=rank)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    forms = {}
+    sampler = ClockSampler(local, enabled=not args.no_clocks)
+    wall0 = time.perf_counter()
+    with sampler:
+        for name in [f.strip() for f in args.forms.split(",") if f.strip()]:
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            try:
+                forms[name] = time_form(prob, name, args.steps, args.warmup, args.profile_steps,
+                                        stream, flush)
+            except pic.PicError as e:
+                if e.code == -7:      # form not built in this library version
+                    forms[name] = {"unavailable": str(e)}
+                    continue
+                raise
+            torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.summary()
+    avail = [k for k, v in forms.items() if "unavailable" not in v]
+    head = avail[0]
+    peak, peak_src = hbm_peak()
+
+    out_forms = {}
+    for name in avail:
+        f = forms[name]
+        t_local = float(f["step_ms"].sum()) / 1e3
+        t_max = max_over_ranks(t_local, world, dev)
+        units = sum_over_ranks(float(prob.n_markers * args.steps), world, dev)
+        kern = f["kernels"]
+        dom = max(kern.items(), key=lambda kv: kv[1]["avg_us"] * kv[1]["launches"])
+        dname, d = dom
+        algo = ALGO_BYTES.get((name, d["kind"]), 0) * prob.n_markers
+        ach = algo / (d["avg_us"] * 1e-6) / 1e9
+        out_forms[name] = {
+            "value": units / t_max, "ms_per_step": 1e3 * t_max / args.steps,
+            "max_rel_dTE": f["max_rel_dTE"], "fallbacks": f["fallbacks"],
+            "gpu_launches": f["launches"],
+            "kernels_us": {k: round(v["avg_us"], 2) for k, v in kern.items()},
+            "roofline": {"bound": "hbm", "kernel": dname, "achieved": round(ach, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                         "traffic": None, "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": algo},
+        }
+    hf = out_forms[head]
+    line = {
+        "metric": METRIC, "value": hf["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": hf["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+i32+i64 (energy in f64)" if head == "mixed" else "f64",
+        "data": "synthetic (seeded two-stream markers)",
+        "config": config_dict(prob, {"form": head, "parallelism": f"replicas{world}"}),
+        "roofline": hf["roofline"], "gpu_launches": hf["gpu_launches"], "clocks": clocks,
+        "energy": {"max_rel_dTE": hf["max_rel_dTE"], "fallbacks": hf["fallbacks"],
+                   "steps": args.warmup + args.steps},
+        "forms": {k: {kk: vv for kk, vv in v.items()} for k, v in out_forms.items()},
+        "unavailable_forms": {k: v["unavailable"] for k, v in forms.items() if k not in avail},
+    }
+    if not args.no_e2e:
+        e = e2e_form(prob, head, max(2, min(args.steps, 10)), 1)
+        t = max_over_ranks(e["s_per_step"], world, dev)
+        line["e2e"] = {"value": sum_over_ranks(prob.n_markers, world, dev) / t, "unit": UNIT,
+                       "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_oracle(1 << 21, 0)
+    line["wall_s_timed_forms"] = round(wall, 2)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is one oracle step of a bounded
+    sample (2^18 markers) of the same workload, on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    markers = 1 << 18
+    prob = workload(markers, 0)
+    s = prob.species[0]
+    cfg = O.ES1DConfig(nc=prob.nc, L=prob.L, order=prob.order, dt=prob.dt, scheme=2)
+    sp = [O.Species(s.q, s.m, s.x.copy(), s.v.copy(), None, s.w0)]
+    E = O.poisson_e0_1d(cfg, sp)
+    for _ in range(args.warmup):
+        O.es1d_step(cfg, sp, E)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.es1d_step(cfg, sp, E)
+    dt = time.perf_counter() - t0
+    value = markers * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded two-stream markers)",
+        "config": config_dict(prob, {"form": "oracle", "sample_of_markers": 1 << 23}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{markers} of the 2^23 markers per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * pic.h -- C ABI of the GB300 library for the explicit, energy-conserving
+ * particle-in-cell scheme of Ricketson & Hu ("An explicit, energy-conserving
+ * particle-in-cell scheme").
+ *
+ * What one call of pic_step() computes, per time step (Sec. 3.3, Eq.
+ * good_translation; Sec. 4.1, Eq. EMleapfrog):
+ *   x*          = x^n + dt/2 v^n
+ *   j^{n,*}     = deposit of v^n at x*            (ESEC2 only, Eq. doublestardef)
+ *   E*          = E^n - dt/2 j^{n,*}              (ES; EM adds c^2 curl B^{n+1/2})
+ *   v*          = v^n + dt/2 (q/m)(E**_p + v* x B)  (E** gathered at x*)
+ *   x^{n+1}     = x^n + dt v*,  x^{n+1/2} = x^n + dt/2 v*
+ *   j^{*,n+1/2} = deposit of v* at x^{n+1/2}
+ *   E^{n+1}     = E^n - dt j^{*,n+1/2}            (Eq. ampere; EM: Eq. EMleapfrog)
+ *   v^dag       = v^n + dt (q/m)(E^{n+1/2}_p + v* x B)  (Eq. PICmodification)
+ *   v^{n+1}     = Gamma v^dag, Gamma = sqrt(|v^n|^2 + 2 v*.(v^dag - v^n)) / |v^dag|
+ *                 (Eq. opt_solution); where the radicand is negative (or
+ *                 v^dag = 0) Gamma := 1 and the particle is counted (Sec. 3.2,
+ *                 Sec. 5.1).
+ * The shape function S is the same B-spline for gather and deposit (Sec. 2.2),
+ * of order 1 (the paper's tent) or 2 (quadratic B-spline, an extension).
+ *
+ * Conventions
+ *   - Every function returns an int status: PIC_OK (0) or a negative PIC_ERR_*
+ *     code; nothing aborts, throws or exits across this boundary.  After a
+ *     nonzero status pic_last_error() describes it (thread-local string).
+ *   - Units are the dimensionless ones of Sec. 2.1.  Species have charge q and
+ *     mass m: acceleration (q/m)(E + v x B), current (1/|h|) sum q w v S,
+ *     kinetic energy (1/2) m sum w |v|^2.  A fixed neutralising background is
+ *     implied (it only enters the initial Poisson solve).
+ *   - Grid: 1D periodic, nodes x_i = i h, h = L / n[0], E and J collocated on
+ *     the nodes (solver PIC_SOLVER_AMPERE_ES, dim_x = dim_v = 1); or 2D periodic
+ *     Yee lattice n[0] x n[1] (solver PIC_SOLVER_YEE_LEAPFROG, dim_x = 2,
+ *     dim_v = 3) with components Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j),
+ *     Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2); grid arrays are
+ *     component-major [3][n[1]][n[0]].
+ *   - Particle arrays are SoA: x is [dim_x][n], v is [dim_v][n], w is [n].
+ *   - Ownership: the library copies everything it is given at pic_init /
+ *     pic_set_* and owns all device memory it allocates until pic_free.  Output
+ *     pointers are written, never retained.
+ *   - Pointers are host pointers unless the config sets ptr_on_device = 1, in
+ *     which case every array argument of every call on that handle is a device
+ *     pointer on the current device.
+ *   - All GPU work is issued on cfg.cuda_stream (a cudaStream_t, or NULL for
+ *     the legacy default stream); calls return after that work completes.
+ *   - A handle is not thread-safe: one thread at a time per handle.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PIC_OK = 0,
+  PIC_ERR_ARG = -1,        /* invalid argument (sizes, enum values, NULL)   */
+  PIC_ERR_CUDA = -2,       /* a CUDA runtime call failed                    */
+  PIC_ERR_OOM = -3,        /* device allocation failed                      */
+  PIC_ERR_NONFINITE = -4,  /* a non-finite value reached the state          */
+  PIC_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up            */
+  PIC_ERR_BOUNDS = -6,     /* an input position lies outside [0, L)         */
+  PIC_ERR_UNSUPPORTED = -7 /* a valid combination this build does not run   */
+};
+
+typedef enum { PIC_SOLVER_AMPERE_ES = 0, PIC_SOLVER_YEE_LEAPFROG = 1 } pic_solver;
+/* ESEC1: Eq. (naivetranslation) with the correction of Eq. (PICmodification);
+ * ESEC2: Eq. (good_translation), one extra deposit per step, Gamma closer to 1. */
+typedef enum { PIC_SCHEME_ESEC1 = 1, PIC_SCHEME_ESEC2 = 2 } pic_scheme;
+/* FP64: positions and velocities in double, all arithmetic in double.
+ * MIXED: positions as 32-bit fixed point (cell and fraction in one word),
+ * velocities as unevaluated float pairs (48-bit significand), shape weights in
+ * FP32, current accumulated exactly in 64-bit integers, Gamma from an exact
+ * difference; energy reductions in double.  Conserves energy to the same
+ * bound (the pairing of Eq. exp_econs_simple is exact by construction). */
+typedef enum { PIC_PREC_FP64 = 0, PIC_PREC_MIXED = 1 } pic_precision;
+
+typedef struct {
+  int dim_x;      /* 1 (with dim_v = 1) or 2 (with dim_v = 3)            */
+  int dim_v;
+  int64_t n[2];   /* nodes per dimension (n[1] ignored when dim_x = 1)  */
+  double L[2];    /* periodic lengths                                   */
+} pic_grid;
+
+typedef struct {
+  double q, m;        /* charge and mass (electrons: -1, 1)                  */
+  int64_t n;          /* markers                                             */
+  const double *x;    /* [dim_x][n], each coordinate in [0, L)               */
+  const double *v;    /* [dim_v][n]                                          */
+  const double *w;    /* [n] weights, or NULL for the uniform weight w0      */
+  double w0;
+} pic_species;
+
+typedef struct {
+  pic_grid grid;
+  int shape_order;          /* 1 | 2                                          */
+  double dt;
+  double c;                 /* speed of light (Yee solver only)               */
+  pic_solver solver;
+  pic_scheme scheme;
+  pic_precision precision;
+  int sort_period;          /* cell-sort the markers every sort_period steps  */
+                            /* (0 = never; sorting only reorders markers)     */
+  int remove_mean;          /* ES: 1 -> E -= dt (J - <J>), 0 -> E -= dt J     */
+  int gamma_on;             /* 1 = energy correction; 0 = naive scheme        */
+  int ptr_on_device;        /* see Conventions                                */
+  void *cuda_stream;        /* cudaStream_t or NULL                           */
+} pic_config;
+
+typedef struct pic_handle pic_handle;
+
+/*
+ * Creates a simulation.  species: nspecies entries (1..8).  E0: initial field,
+ * [nodes] (ES) or [3][ny][nx] (Yee), or NULL: ES solves Gauss's law in the
+ * Poisson form (Eq. poisson, dE/dx = rho - <rho>) spectrally from the
+ * deposited charge, Yee starts from E = 0.  B0 (Yee only): B^{-1/2}
+ * [3][ny][nx] or NULL for zero.  Positions outside [0, L) -> PIC_ERR_BOUNDS;
+ * non-finite input -> PIC_ERR_NONFINITE.  On success *out owns the state.
+ */
+int pic_init(const pic_config *cfg, const pic_species *species, int nspecies,
+             const double *E0, const double *B0, pic_handle **out);
+
+/*
+ * Advances nsteps steps (see the header comment).  Optional outputs (host
+ * arrays, or device arrays when ptr_on_device), each of length nsteps or
+ * NULL: nfallback_per_step[k] = number of particles (all species) whose Gamma
+ * fell back to 1 in step k; te_per_step[k] = total energy after step k
+ * (KE + W_E + W_B, reduced in double on the device every step).
+ * A non-finite total energy stops the call with PIC_ERR_NONFINITE.
+ */
+int pic_step(pic_handle *h, int nsteps, int64_t *nfallback_per_step, double *te_per_step);
+
+/*
+ * Asynchronous form of pic_step: enqueues nsteps steps on the handle's stream
+ * and returns without waiting.  The per-step fallback counts and total
+ * energies stay on the device (at most 1024 pending steps) until
+ * pic_read_stats, which waits for the work, copies them out (arrays of
+ * capacity >= pending steps, or NULL), sets *nread to the number of steps
+ * read, clears them and reports device-side error flags.  pic_step discards
+ * any stats still pending from earlier asynchronous calls.
+ */
+int pic_step_async(pic_handle *h, int nsteps);
+int pic_read_stats(pic_handle *h, int capacity, int64_t *nfallback_per_step, double *te_per_step,
+                   int *nread);
+
+/* Number of CUDA kernels this handle has launched so far (all entry points). */
+int pic_launch_count(pic_handle *h, int64_t *launches);
+
+/*
+ * Per-kernel timing for measurement.  pic_set_profiling(h, 1) clears the
+ * totals and brackets every later launch of h with CUDA events on its stream
+ * (a few microseconds of overhead per launch); 0 stops.  pic_profile returns
+ * the number of launches and their summed device time (ms) of one kind:
+ * 0 = pass C (gather at x*, push to v*, deposit of j^{*,n+1/2}),
+ * 1 = pass E (gather at x^{n+1/2}, Gamma, state update, next j^{n,*}),
+ * 2 = per-step energy/fallback finalisation, 3 = cell sort.
+ */
+int pic_set_profiling(pic_handle *h, int on);
+int pic_profile(pic_handle *h, int kind, int64_t *launches, double *total_ms);
+
+/*
+ * Energies of the current state (Sec. 5.1; W_B of Sec. 4.1):
+ * KE_per_species [nspecies], W_E = (1/2)|h| sum |E|^2,
+ * W_B = (c^2/2)|h| sum B^{n+1/2} . B^{n-1/2} (0 for the ES solver), TE = sum.
+ * Any output may be NULL.  Always host pointers.
+ */
+int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, double *TE);
+
+/* Copies species s out as FP64 SoA ([dim_x][n] positions, [dim_v][n]
+ * velocities).  Marker order is the library's current (possibly sorted)
+ * order; pic_get_ids returns, for each slot, the marker's index at init. */
+int pic_get_particles(pic_handle *h, int s, double *x, double *v);
+int pic_get_ids(pic_handle *h, int s, int64_t *ids);
+/* Replaces species s (same n; resets its ids to 0..n-1). */
+int pic_set_particles(pic_handle *h, int s, const double *x, const double *v);
+/* Fields: E^n and (Yee) B^{n-1/2}; B may be NULL for the ES solver. */
+int pic_get_fields(pic_handle *h, double *E, double *B);
+int pic_set_fields(pic_handle *h, const double *E, const double *B);
+
+/* Number of steps taken since pic_init. */
+int pic_step_count(pic_handle *h, int64_t *steps);
+
+/* Releases every resource of h (NULL is a no-op). */
+void pic_free(pic_handle *h);
+
+/* Message for the last nonzero status returned on this thread. */
+const char *pic_last_error(void);
+
+/* Library version string. */
+const char *pic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

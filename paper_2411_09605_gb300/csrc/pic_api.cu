@@ -1,0 +1,556 @@
+// Host runtime behind the C ABI of include/pic.h: argument checks, device
+// memory, the per-step launch sequence and the state/energy accessors.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "pic_internal.cuh"
+
+using namespace pic;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA,           \
+                  "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,       \
+                  __LINE__);                                                              \
+  } while (0)
+
+constexpr int kStepsCap = 1024;  // per-step stats slots per chunk of pic_step
+constexpr int kProfKinds = 8;    // 0 pass C, 1 pass E, 2 stats finalize, 3 sort
+
+// Validates positions in [0, L) and finite velocities of a 1D state.
+__global__ void validate_1d_kernel(const double *x, const double *v, int64_t n, double L,
+                                   unsigned *err) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    double a = x[p], b = v[p];
+    if (!(a >= 0.0 && a < L)) atomicOr(err, kErrBounds);
+    if (!isfinite(b)) atomicOr(err, kErrNonfinite);
+  }
+}
+
+}  // namespace
+
+struct pic_handle {
+  pic_config cfg;
+  cudaStream_t st = nullptr;
+  int nsp = 0;
+  SpeciesInfo sp[kMaxSpecies];
+  int64_t N = 0;
+  int64_t steps_done = 0;
+  int pending = 0;          // asynchronous steps whose stats are not read yet
+  int64_t launches = 0;     // kernels launched on behalf of this handle
+  bool weighted = false;
+  // optional per-launch timing (pic_set_profiling): events around each launch
+  bool profiling = false;
+  struct Timed { int kind; cudaEvent_t a, b; };
+  std::vector<Timed> timed;
+  double prof_ms[kProfKinds] = {0};
+  int64_t prof_n[kProfKinds] = {0};
+  LaunchShape ls{1, 512};
+  // 1D FP64 state
+  Es1dConst c1{};
+  Es1dFp64Bufs b1{};
+  int64_t *ids = nullptr;
+  std::vector<void *> allocs;
+
+  template <typename T>
+  int alloc(T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+    if (e != cudaSuccess)
+      return fail(PIC_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", sizeof(T) * count,
+                  cudaGetErrorString(e));
+    allocs.push_back(q);
+    *p = (T *)q;
+    return PIC_OK;
+  }
+  ~pic_handle() {
+    for (Timed &t : timed) {
+      cudaEventDestroy(t.a);
+      cudaEventDestroy(t.b);
+    }
+    for (void *p : allocs) cudaFree(p);
+  }
+  // Brackets the launches issued by f with timing events when profiling.
+  template <typename F>
+  cudaError_t timed_launch(int kind, F f) {
+    if (!profiling) {
+      f();
+      return cudaGetLastError();
+    }
+    Timed t{kind, nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&t.a);
+    if (e == cudaSuccess) e = cudaEventCreate(&t.b);
+    if (e != cudaSuccess) return e;
+    cudaEventRecord(t.a, st);
+    f();
+    cudaEventRecord(t.b, st);
+    timed.push_back(t);
+    return cudaGetLastError();
+  }
+  cudaError_t collect_profile() {
+    for (Timed &t : timed) {
+      cudaError_t e = cudaEventSynchronize(t.b);
+      if (e != cudaSuccess) return e;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t.a, t.b);
+      prof_ms[t.kind] += ms;
+      prof_n[t.kind] += 1;
+      cudaEventDestroy(t.a);
+      cudaEventDestroy(t.b);
+    }
+    timed.clear();
+    return cudaSuccess;
+  }
+};
+
+namespace {
+
+int check_flags(pic_handle *h, const char *where) {
+  unsigned flags = 0;
+  CUDA_TRY(cudaMemcpyAsync(&flags, h->b1.err, sizeof flags, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  if (flags) {
+    CUDA_TRY(cudaMemsetAsync(h->b1.err, 0, sizeof(unsigned), h->st));
+    if (flags & kErrNonfinite) return fail(PIC_ERR_NONFINITE, "%s: non-finite value in the state", where);
+    if (flags & kErrBounds)
+      return fail(PIC_ERR_BOUNDS, "%s: a position left [0, L) (input out of range, or a "
+                                  "particle crossed more than one period in a step)", where);
+    if (flags & kErrTimeout) return fail(PIC_ERR_TIMEOUT, "%s: device wait timed out", where);
+    return fail(PIC_ERR_CUDA, "%s: device error flags 0x%x", where, flags);
+  }
+  return PIC_OK;
+}
+
+// Spectral solve of dE/dx = rho - <rho> on the 1D grid (Eq. poisson in field
+// form): E_k = rho_k / (i kappa_k), k = 0 and (even n) the Nyquist mode set to 0.
+void poisson_1d_host(const std::vector<double> &rho, double L, std::vector<double> &E) {
+  const int n = (int)rho.size();
+  const double twopi = 6.283185307179586476925286766559;
+  std::vector<double> cs(n), sn(n);
+  for (int j = 0; j < n; j++) {
+    cs[j] = cos(twopi * j / n);
+    sn[j] = sin(twopi * j / n);
+  }
+  E.assign(n, 0.0);
+  for (int k = 1; k < n; k++) {
+    if (n % 2 == 0 && k == n / 2) continue;
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < n; j++) {
+      int t = (int)(((int64_t)j * k) % n);
+      re += rho[j] * cs[t];
+      im -= rho[j] * sn[t];
+    }
+    int ks = k < n - k ? k : k - n;
+    double kappa = twopi * ks / L;
+    double er = im / kappa, ei = -re / kappa;  // rho_k / (i kappa)
+    for (int j = 0; j < n; j++) {
+      int t = (int)(((int64_t)j * k) % n);
+      E[j] += (er * cs[t] - ei * sn[t]) / n;
+    }
+  }
+}
+
+int init_es1d(pic_handle *h, const pic_species *species, const double *E0) {
+  const pic_config &cfg = h->cfg;
+  int nc = (int)cfg.grid.n[0];
+  Es1dConst &c = h->c1;
+  c.nc = nc;
+  c.order = cfg.shape_order;
+  c.scheme = cfg.scheme;
+  c.remove_mean = cfg.remove_mean;
+  c.gamma_on = cfg.gamma_on;
+  c.nsp = h->nsp;
+  c.n_total = h->N;
+  c.L = cfg.grid.L[0];
+  c.h = c.L / nc;
+  c.inv_h = nc / c.L;
+  c.dt = cfg.dt;
+  for (int s = 0; s < h->nsp; s++) {
+    const SpeciesInfo &S = h->sp[s];
+    c.sp_end[s] = S.offset + S.n;
+    c.qm[s] = S.q / S.m;
+    c.qw_h[s] = S.q * S.w0 / c.h;
+    c.q_h[s] = S.q / c.h;
+    c.half_mw[s] = 0.5 * S.m * S.w0;
+    c.half_m[s] = 0.5 * S.m;
+  }
+  for (int s = h->nsp; s < kMaxSpecies; s++) c.sp_end[s] = h->N;
+
+  CUDA_TRY(es1d_fp64_prepare(c));
+  Es1dFp64Bufs &b = h->b1;
+  int rc;
+  if ((rc = h->alloc(&b.x, h->N)) || (rc = h->alloc(&b.v, h->N))) return rc;
+  b.w = nullptr;
+  if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;
+  for (int k = 0; k < 2; k++)
+    if ((rc = h->alloc(&b.E[k], nc)) || (rc = h->alloc(&b.J1[k], nc)) ||
+        (rc = h->alloc(&b.J2[k], nc)))
+      return rc;
+  if ((rc = h->alloc(&b.ke_part, h->ls.grid)) || (rc = h->alloc(&b.fallback, kStepsCap)) ||
+      (rc = h->alloc(&b.te, kStepsCap)) || (rc = h->alloc(&b.we, 1)) ||
+      (rc = h->alloc(&b.err, 1)) || (rc = h->alloc(&h->ids, h->N)))
+    return rc;
+  CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(unsigned), h->st));
+  for (int s = 0; s < h->nsp; s++) {
+    const SpeciesInfo &S = h->sp[s];
+    const pic_species &in = species[s];
+    CUDA_TRY(cudaMemcpyAsync(b.x + S.offset, in.x, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaMemcpyAsync(b.v + S.offset, in.v, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+    if (h->weighted) {
+      if (in.w) {
+        CUDA_TRY(cudaMemcpyAsync(b.w + S.offset, in.w, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+      } else {
+        std::vector<double> tmp((size_t)S.n, S.w0);
+        CUDA_TRY(cudaMemcpyAsync(b.w + S.offset, tmp.data(), sizeof(double) * S.n,
+                                 cudaMemcpyHostToDevice, h->st));
+        CUDA_TRY(cudaStreamSynchronize(h->st));
+      }
+    }
+  }
+  std::vector<int64_t> ids((size_t)h->N);
+  for (int64_t s = 0; s < h->nsp; s++)
+    for (int64_t p = 0; p < h->sp[s].n; p++) ids[(size_t)(h->sp[s].offset + p)] = p;
+  CUDA_TRY(cudaMemcpyAsync(h->ids, ids.data(), sizeof(int64_t) * h->N, cudaMemcpyHostToDevice, h->st));
+  validate_1d_kernel<<<h->ls.grid, 256, 0, h->st>>>(b.x, b.v, h->N, c.L, b.err);
+  CUDA_TRY(cudaGetLastError());
+  if ((rc = check_flags(h, "pic_init"))) return rc;
+
+  for (int k = 0; k < 2; k++) {
+    CUDA_TRY(cudaMemsetAsync(b.J1[k], 0, sizeof(double) * nc, h->st));
+    CUDA_TRY(cudaMemsetAsync(b.J2[k], 0, sizeof(double) * nc, h->st));
+    CUDA_TRY(cudaMemsetAsync(b.E[k], 0, sizeof(double) * nc, h->st));
+  }
+  if (E0) {
+    std::vector<double> e(nc);
+    CUDA_TRY(cudaMemcpyAsync(e.data(), E0, sizeof(double) * nc, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    for (int i = 0; i < nc; i++)
+      if (!std::isfinite(e[i])) return fail(PIC_ERR_NONFINITE, "pic_init: E0[%d] is not finite", i);
+    CUDA_TRY(cudaMemcpyAsync(b.E[0], e.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, h->st));
+  } else {
+    double *rho = b.J2[1];  // scratch, cleared again below
+    es1d_fp64_charge(c, b.x, b.w, rho, h->ls, h->st);
+    CUDA_TRY(cudaGetLastError());
+    std::vector<double> r(nc), e;
+    CUDA_TRY(cudaMemcpyAsync(r.data(), rho, sizeof(double) * nc, cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    poisson_1d_host(r, c.L, e);
+    CUDA_TRY(cudaMemcpyAsync(b.E[0], e.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(cudaMemsetAsync(rho, 0, sizeof(double) * nc, h->st));
+  }
+  if (c.scheme == 2) {
+    es1d_fp64_deposit_initial(c, b, 0, h->ls, h->st);
+    CUDA_TRY(cudaGetLastError());
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return check_flags(h, "pic_init");
+}
+
+// Re-establishes the invariants of the step sequence after a state change:
+// zero currents and, for ESEC2, j^{n,*} of the new state.
+int restart_es1d(pic_handle *h) {
+  Es1dFp64Bufs &b = h->b1;
+  int par = (int)(h->steps_done & 1);
+  for (int k = 0; k < 2; k++) {
+    CUDA_TRY(cudaMemsetAsync(b.J1[k], 0, sizeof(double) * h->c1.nc, h->st));
+    CUDA_TRY(cudaMemsetAsync(b.J2[k], 0, sizeof(double) * h->c1.nc, h->st));
+  }
+  if (h->c1.scheme == 2) es1d_fp64_deposit_initial(h->c1, b, par, h->ls, h->st);
+  CUDA_TRY(cudaGetLastError());
+  validate_1d_kernel<<<h->ls.grid, 256, 0, h->st>>>(b.x, b.v, h->N, h->c1.L, b.err);
+  CUDA_TRY(cudaGetLastError());
+  return check_flags(h, "pic_set_*");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pic_last_error(void) { return g_last_error.c_str(); }
+
+const char *pic_version(void) { return "gb300-ecpic 0.1 (sm_103a)"; }
+
+int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, const double *E0,
+             const double *B0, pic_handle **out) {
+  if (!out) return fail(PIC_ERR_ARG, "pic_init: out is NULL");
+  *out = nullptr;
+  if (!cfg || !species) return fail(PIC_ERR_ARG, "pic_init: cfg or species is NULL");
+  if (nspecies < 1 || nspecies > kMaxSpecies)
+    return fail(PIC_ERR_ARG, "pic_init: nspecies must be in [1, %d]", kMaxSpecies);
+  if (cfg->shape_order != 1 && cfg->shape_order != 2)
+    return fail(PIC_ERR_ARG, "pic_init: shape_order must be 1 or 2");
+  if (cfg->scheme != PIC_SCHEME_ESEC1 && cfg->scheme != PIC_SCHEME_ESEC2)
+    return fail(PIC_ERR_ARG, "pic_init: scheme must be PIC_SCHEME_ESEC1 or PIC_SCHEME_ESEC2");
+  if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return fail(PIC_ERR_ARG, "pic_init: dt must be > 0");
+  if (cfg->precision != PIC_PREC_FP64 && cfg->precision != PIC_PREC_MIXED)
+    return fail(PIC_ERR_ARG, "pic_init: unknown precision");
+  if (cfg->solver == PIC_SOLVER_AMPERE_ES) {
+    if (cfg->grid.dim_x != 1 || cfg->grid.dim_v != 1)
+      return fail(PIC_ERR_ARG, "pic_init: the Ampere solver runs 1D1V (dim_x = dim_v = 1)");
+    if (cfg->grid.n[0] < 4 || cfg->grid.n[0] > kMaxNodes1D)
+      return fail(PIC_ERR_ARG, "pic_init: 1D grid needs 4..%d nodes", kMaxNodes1D);
+    if (!(cfg->grid.L[0] > 0.0)) return fail(PIC_ERR_ARG, "pic_init: L must be > 0");
+    if (B0) return fail(PIC_ERR_ARG, "pic_init: B0 given for the electrostatic solver");
+  } else if (cfg->solver == PIC_SOLVER_YEE_LEAPFROG) {
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: Yee solver not built in this library version");
+  } else {
+    return fail(PIC_ERR_ARG, "pic_init: unknown solver");
+  }
+  if (cfg->precision == PIC_PREC_MIXED)
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: mixed precision not built in this library version");
+  int64_t N = 0;
+  bool weighted = false;
+  for (int s = 0; s < nspecies; s++) {
+    const pic_species &S = species[s];
+    if (S.n < 0) return fail(PIC_ERR_ARG, "pic_init: species %d has n < 0", s);
+    if (S.n > 0 && (!S.x || !S.v)) return fail(PIC_ERR_ARG, "pic_init: species %d x or v is NULL", s);
+    if (!(S.m > 0.0) || !std::isfinite(S.q)) return fail(PIC_ERR_ARG, "pic_init: species %d needs m > 0 and finite q", s);
+    if (S.w) weighted = true;
+    N += S.n;
+  }
+  if (N > ((int64_t)1 << 40)) return fail(PIC_ERR_ARG, "pic_init: too many markers");
+
+  pic_handle *h = new pic_handle();
+  h->cfg = *cfg;
+  h->st = (cudaStream_t)cfg->cuda_stream;
+  h->nsp = nspecies;
+  h->weighted = weighted;
+  int64_t off = 0;
+  for (int s = 0; s < nspecies; s++) {
+    h->sp[s] = SpeciesInfo{species[s].q, species[s].m, species[s].w0, species[s].n, off,
+                           species[s].w != nullptr};
+    off += species[s].n;
+  }
+  h->N = N;
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(PIC_ERR_CUDA, "pic_init: no usable CUDA device: %s", cudaGetErrorString(e));
+  }
+  int64_t want = (N + 511) / 512;
+  h->ls.block = 512;
+  h->ls.grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 2));
+  int rc = init_es1d(h, species, E0);
+  if (rc) {
+    std::string msg = g_last_error;
+    delete h;
+    g_last_error = msg;
+    return rc;
+  }
+  *out = h;
+  return PIC_OK;
+}
+
+int pic_step_async(pic_handle *h, int nsteps) {
+  if (!h) return fail(PIC_ERR_ARG, "pic_step_async: NULL handle");
+  if (nsteps < 0) return fail(PIC_ERR_ARG, "pic_step_async: nsteps < 0");
+  if (h->pending + nsteps > kStepsCap)
+    return fail(PIC_ERR_ARG, "pic_step_async: more than %d steps pending; call pic_read_stats",
+                kStepsCap);
+  Es1dFp64Bufs &b = h->b1;
+  if (h->pending == 0 && nsteps > 0) {
+    CUDA_TRY(cudaMemsetAsync(b.fallback, 0, sizeof(unsigned long long) * kStepsCap, h->st));
+  }
+  for (int k = 0; k < nsteps; k++) {
+    CUDA_TRY(h->timed_launch(0, [&] {
+      es1d_fp64_pass_c(h->c1, b, h->steps_done, h->pending, h->ls, h->st);
+    }));
+    CUDA_TRY(h->timed_launch(1, [&] {
+      es1d_fp64_pass_e(h->c1, b, h->steps_done, h->pending, h->ls, h->st);
+    }));
+    h->launches += 2;
+    h->steps_done++;
+    h->pending++;
+  }
+  return PIC_OK;
+}
+
+int pic_read_stats(pic_handle *h, int capacity, int64_t *nfallback_per_step, double *te_per_step,
+                   int *nread) {
+  if (!h) return fail(PIC_ERR_ARG, "pic_read_stats: NULL handle");
+  int n = h->pending;
+  if (nread) *nread = n;
+  if (n == 0) return check_flags(h, "pic_read_stats");
+  if ((nfallback_per_step || te_per_step) && capacity < n)
+    return fail(PIC_ERR_ARG, "pic_read_stats: %d steps pending, capacity %d", n, capacity);
+  Es1dFp64Bufs &b = h->b1;
+  CUDA_TRY(h->timed_launch(2, [&] { es1d_fp64_finalize(h->c1, b, n - 1, h->ls.grid, h->st); }));
+  h->launches += 1;
+  std::vector<unsigned long long> fb(n);
+  std::vector<double> te(n);
+  CUDA_TRY(cudaMemcpyAsync(fb.data(), b.fallback, sizeof(unsigned long long) * n,
+                           cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaMemcpyAsync(te.data(), b.te, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  h->pending = 0;
+  if (nfallback_per_step) {
+    std::vector<int64_t> f64(fb.begin(), fb.end());
+    CUDA_TRY(cudaMemcpyAsync(nfallback_per_step, f64.data(), sizeof(int64_t) * n,
+                             cudaMemcpyDefault, h->st));
+  }
+  if (te_per_step)
+    CUDA_TRY(cudaMemcpyAsync(te_per_step, te.data(), sizeof(double) * n, cudaMemcpyDefault, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return check_flags(h, "pic_read_stats");
+}
+
+int pic_step(pic_handle *h, int nsteps, int64_t *nfallback_per_step, double *te_per_step) {
+  if (!h) return fail(PIC_ERR_ARG, "pic_step: NULL handle");
+  if (nsteps < 0) return fail(PIC_ERR_ARG, "pic_step: nsteps < 0");
+  int rc = PIC_OK;
+  if (h->pending) {  // stats of earlier asynchronous steps are discarded
+    if ((rc = pic_read_stats(h, 0, nullptr, nullptr, nullptr))) return rc;
+  }
+  int done = 0;
+  while (done < nsteps) {
+    int chunk = std::min(kStepsCap, nsteps - done);
+    if ((rc = pic_step_async(h, chunk))) return rc;
+    if ((rc = pic_read_stats(h, chunk, nfallback_per_step ? nfallback_per_step + done : nullptr,
+                             te_per_step ? te_per_step + done : nullptr, nullptr)))
+      return rc;
+    done += chunk;
+  }
+  return PIC_OK;
+}
+
+int pic_set_profiling(pic_handle *h, int on) {
+  if (!h) return fail(PIC_ERR_ARG, "pic_set_profiling: NULL handle");
+  CUDA_TRY(h->collect_profile());
+  for (int k = 0; k < kProfKinds; k++) {
+    h->prof_ms[k] = 0.0;
+    h->prof_n[k] = 0;
+  }
+  h->profiling = on != 0;
+  return PIC_OK;
+}
+
+int pic_profile(pic_handle *h, int kind, int64_t *launches, double *total_ms) {
+  if (!h || kind < 0 || kind >= kProfKinds) return fail(PIC_ERR_ARG, "pic_profile: bad arguments");
+  CUDA_TRY(h->collect_profile());
+  if (launches) *launches = h->prof_n[kind];
+  if (total_ms) *total_ms = h->prof_ms[kind];
+  return PIC_OK;
+}
+
+int pic_launch_count(pic_handle *h, int64_t *launches) {
+  if (!h || !launches) return fail(PIC_ERR_ARG, "pic_launch_count: bad arguments");
+  *launches = h->launches;
+  return PIC_OK;
+}
+
+int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, double *TE) {
+  if (!h) return fail(PIC_ERR_ARG, "pic_energy: NULL handle");
+  const Es1dConst &c = h->c1;
+  double *ke_d = h->b1.ke_part;  // reuse: nsp <= grid entries are needed
+  if (h->ls.grid < h->nsp) return fail(PIC_ERR_ARG, "pic_energy: internal size");
+  // ke_part is only consumed during pic_step; it is safe to reuse between calls.
+  es1d_fp64_kinetic(c, h->b1.v, h->b1.w, ke_d, h->st);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<double> ke(h->nsp), e(c.nc);
+  CUDA_TRY(cudaMemcpyAsync(ke.data(), ke_d, sizeof(double) * h->nsp, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaMemcpyAsync(e.data(), h->b1.E[h->steps_done & 1], sizeof(double) * c.nc,
+                           cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  double we = 0.0;
+  for (int i = 0; i < c.nc; i++) we += e[i] * e[i];
+  we *= 0.5 * c.h;
+  double te = we;
+  for (int s = 0; s < h->nsp; s++) {
+    te += ke[s];
+    if (KE_per_species) KE_per_species[s] = ke[s];
+  }
+  if (W_E) *W_E = we;
+  if (W_B) *W_B = 0.0;
+  if (TE) *TE = te;
+  if (!std::isfinite(te)) return fail(PIC_ERR_NONFINITE, "pic_energy: non-finite energy");
+  return PIC_OK;
+}
+
+int pic_get_particles(pic_handle *h, int s, double *x, double *v) {
+  if (!h || s < 0 || s >= h->nsp) return fail(PIC_ERR_ARG, "pic_get_particles: bad handle or species");
+  const SpeciesInfo &S = h->sp[s];
+  if (x) CUDA_TRY(cudaMemcpyAsync(x, h->b1.x + S.offset, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+  if (v) CUDA_TRY(cudaMemcpyAsync(v, h->b1.v + S.offset, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return PIC_OK;
+}
+
+int pic_get_ids(pic_handle *h, int s, int64_t *ids) {
+  if (!h || s < 0 || s >= h->nsp || !ids) return fail(PIC_ERR_ARG, "pic_get_ids: bad arguments");
+  const SpeciesInfo &S = h->sp[s];
+  CUDA_TRY(cudaMemcpyAsync(ids, h->ids + S.offset, sizeof(int64_t) * S.n, cudaMemcpyDefault, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return PIC_OK;
+}
+
+int pic_set_particles(pic_handle *h, int s, const double *x, const double *v) {
+  if (!h || s < 0 || s >= h->nsp || !x || !v) return fail(PIC_ERR_ARG, "pic_set_particles: bad arguments");
+  const SpeciesInfo &S = h->sp[s];
+  CUDA_TRY(cudaMemcpyAsync(h->b1.x + S.offset, x, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+  CUDA_TRY(cudaMemcpyAsync(h->b1.v + S.offset, v, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+  std::vector<int64_t> ids((size_t)S.n);
+  for (int64_t p = 0; p < S.n; p++) ids[(size_t)p] = p;
+  CUDA_TRY(cudaMemcpyAsync(h->ids + S.offset, ids.data(), sizeof(int64_t) * S.n,
+                           cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return restart_es1d(h);
+}
+
+int pic_get_fields(pic_handle *h, double *E, double *B) {
+  if (!h) return fail(PIC_ERR_ARG, "pic_get_fields: NULL handle");
+  (void)B;
+  if (E)
+    CUDA_TRY(cudaMemcpyAsync(E, h->b1.E[h->steps_done & 1], sizeof(double) * h->c1.nc,
+                             cudaMemcpyDefault, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return PIC_OK;
+}
+
+int pic_set_fields(pic_handle *h, const double *E, const double *B) {
+  if (!h || !E) return fail(PIC_ERR_ARG, "pic_set_fields: bad arguments");
+  if (B) return fail(PIC_ERR_ARG, "pic_set_fields: B given for the electrostatic solver");
+  CUDA_TRY(cudaMemcpyAsync(h->b1.E[h->steps_done & 1], E, sizeof(double) * h->c1.nc,
+                           cudaMemcpyDefault, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return restart_es1d(h);
+}
+
+int pic_step_count(pic_handle *h, int64_t *steps) {
+  if (!h || !steps) return fail(PIC_ERR_ARG, "pic_step_count: bad arguments");
+  *steps = h->steps_done;
+  return PIC_OK;
+}
+
+void pic_free(pic_handle *h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of the C ABI in include/pic.h (argument marshalling only).
+
+Every function here forwards to the function of the same name in libpic.so;
+all arithmetic of the method runs in the library's CUDA kernels.  The library
+must have been built (``paper_2411_09605_gb300.build.build()``); importing this
+module without it raises, there is no fallback.
+
+Arrays may be numpy float64 arrays (host) or, with ``ptr_on_device=1`` in the
+config, torch CUDA tensors (their ``data_ptr()`` is passed through).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic.so")
+
+PIC_OK = 0
+ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_OOM", -4: "PIC_ERR_NONFINITE",
+          -5: "PIC_ERR_TIMEOUT", -6: "PIC_ERR_BOUNDS", -7: "PIC_ERR_UNSUPPORTED"}
+PIC_SOLVER_AMPERE_ES, PIC_SOLVER_YEE_LEAPFROG = 0, 1
+PIC_SCHEME_ESEC1, PIC_SCHEME_ESEC2 = 1, 2
+PIC_PREC_FP64, PIC_PREC_MIXED = 0, 1
+
+# every function declared in include/pic.h
+EXPORTS = ["pic_init", "pic_step", "pic_step_async", "pic_read_stats", "pic_launch_count",
+           "pic_set_profiling", "pic_profile",
+           "pic_energy", "pic_get_particles", "pic_get_ids",
+           "pic_set_particles", "pic_get_fields", "pic_set_fields", "pic_step_count", "pic_free",
+           "pic_last_error", "pic_version"]
+
+
+class PicError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class pic_grid(C.Structure):
+    _fields_ = [("dim_x", C.c_int), ("dim_v", C.c_int), ("n", C.c_int64 * 2),
+                ("L", C.c_double * 2)]
+
+
+class pic_species(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("n", C.c_int64), ("x", C.c_void_p),
+                ("v", C.c_void_p), ("w", C.c_void_p), ("w0", C.c_double)]
+
+
+class pic_config(C.Structure):
+    _fields_ = [("grid", pic_grid), ("shape_order", C.c_int), ("dt", C.c_double),
+                ("c", C.c_double), ("solver", C.c_int), ("scheme", C.c_int),
+                ("precision", C.c_int), ("sort_period", C.c_int), ("remove_mean", C.c_int),
+                ("gamma_on", C.c_int), ("ptr_on_device", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Loads libpic.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "paper_2411_09605_gb300.build.build() (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        vp, i64p, dp = C.c_void_p, C.POINTER(C.c_int64), C.c_void_p
+        L.pic_init.argtypes = [C.POINTER(pic_config), C.POINTER(pic_species), C.c_int, dp, dp,
+                               C.POINTER(vp)]
+        L.pic_step.argtypes = [vp, C.c_int, vp, vp]
+        L.pic_step_async.argtypes = [vp, C.c_int]
+        L.pic_read_stats.argtypes = [vp, C.c_int, vp, vp, C.POINTER(C.c_int)]
+        L.pic_launch_count.argtypes = [vp, i64p]
+        L.pic_set_profiling.argtypes = [vp, C.c_int]
+        L.pic_profile.argtypes = [vp, C.c_int, i64p, C.POINTER(C.c_double)]
+        L.pic_energy.argtypes = [vp, vp, vp, vp, vp]
+        L.pic_get_particles.argtypes = [vp, C.c_int, vp, vp]
+        L.pic_get_ids.argtypes = [vp, C.c_int, vp]
+        L.pic_set_particles.argtypes = [vp, C.c_int, vp, vp]
+        L.pic_get_fields.argtypes = [vp, vp, vp]
+        L.pic_set_fields.argtypes = [vp, vp, vp]
+        L.pic_step_count.argtypes = [vp, i64p]
+        L.pic_free.argtypes = [vp]
+        L.pic_free.restype = None
+        L.pic_last_error.restype = C.c_char_p
+        L.pic_version.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("pic_free", "pic_last_error", "pic_version"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != PIC_OK:
+        raise PicError(rc, lib().pic_last_error().decode())
+
+
+def _addr(a) -> Optional[int]:
+    """Address of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous, "arrays must be contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensors must be contiguous"
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def make_config(nc, L, dt, order=1, scheme=PIC_SCHEME_ESEC2, precision=PIC_PREC_FP64,
+                solver=PIC_SOLVER_AMPERE_ES, dim_x=1, dim_v=1, ny=0, Ly=0.0, c=1.0,
+                sort_period=0, remove_mean=1, gamma_on=1, ptr_on_device=0, stream=None):
+    g = pic_grid(dim_x, dim_v, (C.c_int64 * 2)(nc, ny), (C.c_double * 2)(L, Ly))
+    return pic_config(g, order, dt, c, solver, scheme, precision, sort_period, int(remove_mean),
+                      int(gamma_on), int(ptr_on_device), stream)
+
+
+def pic_init(cfg: pic_config, species: Sequence[dict], E0=None, B0=None) -> int:
+    """species: dicts with q, m, x, v, w (or None), w0.  Returns the handle."""
+    arr = (pic_species * len(species))()
+    keep = []
+    for i, s in enumerate(species):
+        n = s["n"] if "n" in s else (s["x"].shape[-1] if s["x"] is not None else 0)
+        arr[i] = pic_species(s["q"], s["m"], n, _addr(s["x"]), _addr(s["v"]),
+                             _addr(s.get("w")), s.get("w0", 0.0))
+        keep.append(s)
+    h = C.c_void_p()
+    _check(lib().pic_init(C.byref(cfg), arr, len(species), _addr(E0), _addr(B0), C.byref(h)))
+    return h.value
+
+
+def pic_step(h: int, nsteps: int, nfallback_per_step=None, te_per_step=None):
+    _check(lib().pic_step(h, nsteps, _addr(nfallback_per_step), _addr(te_per_step)))
+
+
+def pic_step_async(h: int, nsteps: int):
+    _check(lib().pic_step_async(h, nsteps))
+
+
+def pic_read_stats(h: int, capacity: int = 1024):
+    """Returns (fallbacks, total energies) of the steps pending since the last read."""
+    fb = np.zeros(capacity, dtype=np.int64)
+    te = np.zeros(capacity)
+    n = C.c_int()
+    _check(lib().pic_read_stats(h, capacity, fb.ctypes.data, te.ctypes.data, C.byref(n)))
+    return fb[:n.value], te[:n.value]
+
+
+def pic_launch_count(h: int) -> int:
+    n = C.c_int64()
+    _check(lib().pic_launch_count(h, C.byref(n)))
+    return n.value
+
+
+def pic_set_profiling(h: int, on: bool):
+    _check(lib().pic_set_profiling(h, int(on)))
+
+
+def pic_profile(h: int, kind: int):
+    """(launches, total device ms) of one kernel kind since profiling was enabled."""
+    n = C.c_int64()
+    ms = C.c_double()
+    _check(lib().pic_profile(h, kind, C.byref(n), C.byref(ms)))
+    return n.value, ms.value
+
+
+def pic_energy(h: int, nspecies: int):
+    ke = np.zeros(nspecies)
+    we, wb, te = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().pic_energy(h, ke.ctypes.data, C.addressof(we), C.addressof(wb),
+                            C.addressof(te)))
+    return ke, we.value, wb.value, te.value
+
+
+def pic_get_particles(h: int, s: int, x, v):
+    _check(lib().pic_get_particles(h, s, _addr(x), _addr(v)))
+
+
+def pic_get_ids(h: int, s: int, ids):
+    _check(lib().pic_get_ids(h, s, _addr(ids)))
+
+
+def pic_set_particles(h: int, s: int, x, v):
+    _check(lib().pic_set_particles(h, s, _addr(x), _addr(v)))
+
+
+def pic_get_fields(h: int, E, B=None):
+    _check(lib().pic_get_fields(h, _addr(E), _addr(B)))
+
+
+def pic_set_fields(h: int, E, B=None):
+    _check(lib().pic_set_fields(h, _addr(E), _addr(B)))
+
+
+def pic_step_count(h: int) -> int:
+    n = C.c_int64()
+    _check(lib().pic_step_count(h, C.byref(n)))
+    return n.value
+
+
+def pic_free(h: int):
+    lib().pic_free(h)
+
+
+def pic_version() -> str:
+    return lib().pic_version().decode()
+
+
+class Simulation:
+    """Convenience owner of one handle built from a ``workloads.Problem1D``."""
+
+    def __init__(self, prob, scheme=PIC_SCHEME_ESEC2, precision=PIC_PREC_FP64, E0=None,
+                 sort_period=0, remove_mean=True, gamma_on=True):
+        self.prob = prob
+        self.cfg = make_config(prob.nc, prob.L, prob.dt, prob.order, scheme, precision,
+                               sort_period=sort_period, remove_mean=remove_mean,
+                               gamma_on=gamma_on)
+        self.species = [dict(q=s.q, m=s.m, x=np.ascontiguousarray(s.x, dtype=np.float64),
+                             v=np.ascontiguousarray(s.v, dtype=np.float64),
+                             w=None if s.w is None else np.ascontiguousarray(s.w, np.float64),
+                             w0=s.w0) for s in prob.species]
+        self.h = pic_init(self.cfg, self.species, E0)
+
+    def step(self, nsteps: int):
+        fb = np.zeros(nsteps, dtype=np.int64)
+        te = np.zeros(nsteps)
+        pic_step(self.h, nsteps, fb, te)
+        return fb, te
+
+    def particles(self, s: int = 0):
+        n = len(self.species[s]["x"])
+        x, v = np.zeros(n), np.zeros(n)
+        pic_get_particles(self.h, s, x, v)
+        ids = np.zeros(n, dtype=np.int64)
+        pic_get_ids(self.h, s, ids)
+        xo, vo = np.zeros(n), np.zeros(n)
+        xo[ids], vo[ids] = x, v
+        return xo, vo
+
+    def field(self):
+        E = np.zeros(self.prob.nc)
+        pic_get_fields(self.h, E)
+        return E
+
+    def energy(self):
+        return pic_energy(self.h, len(self.species))
+
+    def close(self):
+        if self.h:
+            pic_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

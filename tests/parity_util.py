@@ -1,0 +1,57 @@
+"""Helpers that run one workload through the oracle and through the C ABI and
+compare them (used by the -m gpu parity tests and by smoke())."""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import oracle as O
+
+
+def oracle_run(prob, scheme=2, steps=10, remove_mean=True, gamma_on=True, E0=None):
+    cfg = O.ES1DConfig(nc=prob.nc, L=prob.L, order=prob.order, dt=prob.dt, scheme=scheme,
+                       remove_mean=remove_mean, gamma_on=gamma_on)
+    sp = [O.Species(s.q, s.m, s.x.copy(), s.v.copy(), None if s.w is None else s.w.copy(), s.w0)
+          for s in prob.species]
+    E = O.poisson_e0_1d(cfg, sp) if E0 is None else E0.copy()
+    E_init = E.copy()
+    te, we, nfb = O.es1d_run(cfg, sp, E, steps)
+    return dict(x=[s.x for s in sp], v=[s.v for s in sp], E=E, nfb=nfb, te=te, E0=E_init)
+
+
+def gpu_run(prob, scheme=2, steps=10, precision=0, remove_mean=True, gamma_on=True, E0=None,
+            sort_period=0):
+    from paper_2411_09605_gb300 import pic
+    sim = pic.Simulation(prob, scheme=scheme, precision=precision, E0=E0,
+                         sort_period=sort_period, remove_mean=remove_mean, gamma_on=gamma_on)
+    try:
+        E_init = sim.field()
+        ke0, we0, wb0, te0 = sim.energy()
+        fb, te = sim.step(steps) if steps else (np.zeros(0, np.int64), np.zeros(0))
+        xs, vs = [], []
+        for s in range(len(prob.species)):
+            x, v = sim.particles(s)
+            xs.append(x)
+            vs.append(v)
+        E = sim.field()
+        ke, we, wb, te_now = sim.energy()
+    finally:
+        sim.close()
+    return dict(x=xs, v=vs, E=E, nfb=fb, te=np.concatenate([[te0], te]), E0=E_init,
+                te_now=te_now)
+
+
+def periodic_dist(a, b, L):
+    d = np.abs(a - b) % L
+    return np.minimum(d, L - d)
+
+
+def compare(prob, ref, got):
+    """Scale-normalised maximum differences (x over L, v over max|v|, E in 2-norm)."""
+    out = {}
+    out["x"] = max(np.max(periodic_dist(r, g, prob.L), initial=0.0) / prob.L
+                   for r, g in zip(ref["x"], got["x"]))
+    vmax = max(np.max(np.abs(r), initial=0.0) for r in ref["v"]) or 1.0
+    out["v"] = max(np.max(np.abs(r - g), initial=0.0) for r, g in zip(ref["v"], got["v"])) / vmax
+    En = np.linalg.norm(ref["E"]) or 1.0
+    out["E"] = np.linalg.norm(ref["E"] - got["E"]) / En
+    return out
