@@ -179,6 +179,27 @@ int pic_set_particles(pic_handle *h, int s, const double *x, const double *v);
 int pic_get_fields(pic_handle *h, double *E, double *B);
 int pic_set_fields(pic_handle *h, const double *E, const double *B);
 
+/*
+ * One-species 1D1V step in the FP64 form on caller-owned device buffers that
+ * allocates no device memory (the paper has no counterpart: this is a
+ * deployment entry point).  For callers that may not allocate: a framework
+ * that owns the whole device heap through its own pool and forbids plugins to
+ * call cudaMalloc/cudaFree, or a service whose memory is fixed at start-up.
+ * x, v [n] and E [nodes] are device pointers, updated in place over nsteps
+ * steps of cfg's scheme (solver PIC_SOLVER_AMPERE_ES, precision
+ * PIC_PREC_FP64; uniform weight w0; E is E^n on entry, no Poisson solve).
+ * Optional outputs (host or device, length nsteps): per-step fallback counts
+ * and total energies, as pic_step.  Limits: at most 8192 nodes and 1024 steps
+ * per call, else PIC_ERR_ARG.  Its scratch is one static device array of
+ * 352,576 bytes that every GPU which loads the library holds until exit; all
+ * calls on a device share it, so calls that overlap on the GPU race and must
+ * be serialised.  The first call on a device looks the array up
+ * (cudaGetSymbolAddress): make it before any stream capture.
+ */
+int pic_es1d_step_noalloc(const pic_config *cfg, double q, double m, double w0, int64_t n,
+                          double *x, double *v, double *E, int nsteps,
+                          int64_t *nfallback_per_step, double *te_per_step);
+
 /* Number of steps taken since pic_init. */
 int pic_step_count(pic_handle *h, int64_t *steps);
 

@@ -52,6 +52,11 @@ __global__ void validate_1d_kernel(const double *x, const double *v, int64_t n, 
 
 }  // namespace
 
+namespace pic {
+// Lets other translation units of the library report through pic_last_error.
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace pic
+
 struct pic_handle {
   pic_config cfg;
   cudaStream_t st = nullptr;

@@ -62,6 +62,9 @@ struct LaunchShape {
   int block;
 };
 
+// Sets the message returned by pic_last_error (pic_api.cu).
+void set_last_error(const std::string &msg);
+
 // 1D FP64 path (es1d_fp64.cu)
 cudaError_t es1d_fp64_prepare(const Es1dConst &c);
 void es1d_fp64_deposit_initial(const Es1dConst &c, const Es1dFp64Bufs &b, int parity,

@@ -31,7 +31,7 @@ EXPORTS = ["pic_init", "pic_step", "pic_step_async", "pic_read_stats", "pic_laun
            "pic_set_profiling", "pic_profile",
            "pic_energy", "pic_get_particles", "pic_get_ids",
            "pic_set_particles", "pic_get_fields", "pic_set_fields", "pic_step_count", "pic_free",
-           "pic_last_error", "pic_version"]
+           "pic_last_error", "pic_version", "pic_es1d_step_noalloc"]
 
 
 class PicError(RuntimeError):
@@ -84,6 +84,8 @@ def lib() -> C.CDLL:
         L.pic_get_fields.argtypes = [vp, vp, vp]
         L.pic_set_fields.argtypes = [vp, vp, vp]
         L.pic_step_count.argtypes = [vp, i64p]
+        L.pic_es1d_step_noalloc.argtypes = [C.POINTER(pic_config), C.c_double, C.c_double,
+                                             C.c_double, C.c_int64, vp, vp, vp, C.c_int, vp, vp]
         L.pic_free.argtypes = [vp]
         L.pic_free.restype = None
         L.pic_last_error.restype = C.c_char_p
@@ -208,6 +210,13 @@ def pic_step_count(h: int) -> int:
 
 def pic_free(h: int):
     lib().pic_free(h)
+
+
+def pic_es1d_step_noalloc(cfg: pic_config, q: float, m: float, w0: float, n: int, x, v, E,
+                          nsteps: int, nfallback_per_step=None, te_per_step=None):
+    """Steps caller-owned device arrays without any device allocation (see pic.h)."""
+    _check(lib().pic_es1d_step_noalloc(C.byref(cfg), q, m, w0, n, _addr(x), _addr(v), _addr(E),
+                                       nsteps, _addr(nfallback_per_step), _addr(te_per_step)))
 
 
 def pic_version() -> str:
