@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 512 << 20          # > 2x the 126.5 MB L2
 # barrier-separated pass; v* is recomputed in pass E, never stored).
 ALGO_BYTES = {  # (precision, kind) -> bytes per marker
     ("fp64", 0): 16, ("fp64", 1): 32,      # pass C reads x, v; pass E reads + writes
-    ("mixed", 0): 12, ("mixed", 1): 24,    # 4 B position + 8 B velocity pair
+    ("mixed", 0): 8, ("mixed", 1): 24,     # pass C reads X and vh; pass E X, vh, vl both ways
 }
 
 
@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--sort-period", type=int, default=8,
+                    help="cell sort of the mixed form every this many steps (0 = never)")
     return ap.parse_args()
 
 
@@ -168,7 +170,7 @@ def hbm_peak():
 
 
 def time_form(prob, precision_name: str, steps: int, warmup: int, profile_steps: int, stream,
-              flush_buf):
+              flush_buf, sort_period: int = 0):
     """Device-timed throughput of one library form on the resident workload."""
     import torch
     from paper_2411_09605_gb300 import pic
@@ -178,7 +180,8 @@ def time_form(prob, precision_name: str, steps: int, warmup: int, profile_steps:
     x_d = torch.from_numpy(s.x).to(dev)
     v_d = torch.from_numpy(s.v).to(dev)
     cfg = pic.make_config(prob.nc, prob.L, prob.dt, prob.order, pic.PIC_SCHEME_ESEC2, prec,
-                          ptr_on_device=1, stream=stream.cuda_stream)
+                          ptr_on_device=1, stream=stream.cuda_stream,
+                          sort_period=sort_period if precision_name == "mixed" else 0)
     torch.cuda.synchronize()
     h = pic.pic_init(cfg, [dict(q=s.q, m=s.m, x=x_d, v=v_d, w=None, w0=s.w0)])
     del x_d, v_d
@@ -232,7 +235,7 @@ def time_form(prob, precision_name: str, steps: int, warmup: int, profile_steps:
             "launches": int(launches), "kernels": kern}
 
 
-def e2e_form(prob, precision_name: str, steps: int, warmup: int):
+def e2e_form(prob, precision_name: str, steps: int, warmup: int, sort_period: int = 0):
     """End to end through the C ABI with host buffers: every step uploads the
     marker state from pinned host memory, steps once and reads the state and the
     step's energy/fallback back to pinned host memory."""
@@ -245,7 +248,8 @@ def e2e_form(prob, precision_name: str, steps: int, warmup: int):
     vh = torch.from_numpy(s.v.copy()).pin_memory()
     fb = torch.zeros(1, dtype=torch.int64).pin_memory()
     te = torch.zeros(1, dtype=torch.float64).pin_memory()
-    cfg = pic.make_config(prob.nc, prob.L, prob.dt, prob.order, pic.PIC_SCHEME_ESEC2, prec)
+    cfg = pic.make_config(prob.nc, prob.L, prob.dt, prob.order, pic.PIC_SCHEME_ESEC2, prec,
+                          sort_period=sort_period if precision_name == "mixed" else 0)
     h = pic.pic_init(cfg, [dict(q=s.q, m=s.m, x=xh.numpy(), v=vh.numpy(), w=None, w0=s.w0)])
     try:
         times = []
@@ -311,7 +315,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             try:
                 forms[name] = time_form(prob, name, args.steps, args.warmup, args.profile_steps,
-                                        stream, flush)
+                                        stream, flush, args.sort_period)
             except pic.PicError as e:
                 if e.code == -7:      # form not built in this library version
                     forms[name] = {"unavailable": str(e)}
@@ -352,7 +356,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+i32+i64 (energy in f64)" if head == "mixed" else "f64",
         "data": "synthetic (seeded two-stream markers)",
-        "config": config_dict(prob, {"form": head, "parallelism": f"replicas{world}"}),
+        "config": config_dict(prob, {"form": head, "parallelism": f"replicas{world}",
+                                     "sort_period": args.sort_period if head == "mixed" else 0}),
         "roofline": hf["roofline"], "gpu_launches": hf["gpu_launches"], "clocks": clocks,
         "energy": {"max_rel_dTE": hf["max_rel_dTE"], "fallbacks": hf["fallbacks"],
                    "steps": args.warmup + args.steps},
@@ -360,7 +365,7 @@ def run_ours(args):
         "unavailable_forms": {k: v["unavailable"] for k, v in forms.items() if k not in avail},
     }
     if not args.no_e2e:
-        e = e2e_form(prob, head, max(2, min(args.steps, 10)), 1)
+        e = e2e_form(prob, head, max(2, min(args.steps, 10)), 1, args.sort_period)
         t = max_over_ranks(e["s_per_step"], world, dev)
         line["e2e"] = {"value": sum_over_ranks(prob.n_markers, world, dev) / t, "unit": UNIT,
                        "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"]}

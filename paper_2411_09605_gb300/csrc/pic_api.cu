@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -74,9 +75,18 @@ struct pic_handle {
   double prof_ms[kProfKinds] = {0};
   int64_t prof_n[kProfKinds] = {0};
   LaunchShape ls{1, 512};
-  // 1D FP64 state
+  // 1D FP64 state (in the mixed form x, v serve as FP64 staging for get/set)
   Es1dConst c1{};
   Es1dFp64Bufs b1{};
+  // 1D mixed-precision state
+  bool mixed = false;
+  Es1dMixConst cm{};
+  Es1dMixBufs bm{};
+  Es1dMixBufs bm_alt{};     // the counting sort's destination (swapped after a sort)
+  int64_t *ids_alt = nullptr;
+  uint32_t *sort_hist = nullptr;
+  int sort_blocks = 0;
+  int nsm = 0;
   int64_t *ids = nullptr;
   std::vector<void *> allocs;
 
@@ -144,6 +154,9 @@ int check_flags(pic_handle *h, const char *where) {
       return fail(PIC_ERR_BOUNDS, "%s: a position left [0, L) (input out of range, or a "
                                   "particle crossed more than one period in a step)", where);
     if (flags & kErrTimeout) return fail(PIC_ERR_TIMEOUT, "%s: device wait timed out", where);
+    if (flags & kErrVelocityRange)
+      return fail(PIC_ERR_BOUNDS, "%s: a velocity left the mixed form's fixed-point range "
+                                  "(8 times the largest initial speed)", where);
     return fail(PIC_ERR_CUDA, "%s: device error flags 0x%x", where, flags);
   }
   return PIC_OK;
@@ -176,6 +189,124 @@ void poisson_1d_host(const std::vector<double> &rho, double L, std::vector<doubl
       E[j] += (er * cs[t] - ei * sn[t]) / n;
     }
   }
+}
+
+// Cell-sorts the mixed-form markers (and their ids) into the alternate
+// buffers and swaps them in.
+int sort_mixed(pic_handle *h) {
+  CUDA_TRY(h->timed_launch(3, [&] {
+    es1d_mix_sort(h->cm, h->bm, h->bm_alt, h->ids, h->ids_alt, h->sort_hist, h->sort_blocks,
+                  h->st);
+  }));
+  h->launches += 3;
+  std::swap(h->bm.X, h->bm_alt.X);
+  std::swap(h->bm.vh, h->bm_alt.vh);
+  std::swap(h->bm.vl, h->bm_alt.vl);
+  std::swap(h->ids, h->ids_alt);
+  return PIC_OK;
+}
+
+// Mixed form: constants, integer/float-pair state converted from the FP64
+// staging arrays, j^{n,*} of the initial state.
+int init_mixed(pic_handle *h, bool solve_e0) {
+  const Es1dConst &c = h->c1;
+  const SpeciesInfo &S = h->sp[0];
+  const Es1dFp64Bufs &b = h->b1;
+  Es1dMixConst &m = h->cm;
+  m.nc = c.nc;
+  m.order = c.order;
+  m.scheme = c.scheme;
+  m.remove_mean = c.remove_mean;
+  m.gamma_on = c.gamma_on;
+  m.n = h->N;
+  m.L = c.L;
+  m.h = c.h;
+  m.dt = c.dt;
+  // velocity scale: V units of (dt 2^31 / L) 2^kv, with room for 8x the
+  // largest initial speed inside the 31-bit range
+  unsigned long long *mx = nullptr;
+  int rc;
+  if ((rc = h->alloc(&mx, 1))) return rc;
+  CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), h->st));
+  es1d_absmax(b.v, h->N, mx, h->ls, h->st);
+  CUDA_TRY(cudaGetLastError());
+  unsigned long long bits = 0;
+  CUDA_TRY(cudaMemcpyAsync(&bits, mx, sizeof bits, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  double vmax;
+  memcpy(&vmax, &bits, sizeof vmax);
+  double cx = c.dt * 2147483648.0 / c.L;
+  double vcap = std::max(8.0 * vmax, 1e-6 * c.L / c.dt);
+  int kv = (int)std::floor(std::log2(1073741824.0 / (cx * vcap)));
+  m.kv = std::min(24, std::max(0, kv));
+  m.cxk = std::ldexp(cx, m.kv);
+  int bitlen = 0;
+  while (bitlen < 62 && ((int64_t)1 << bitlen) <= h->N) bitlen++;
+  m.rshift = std::max(17, bitlen - 8);  // |term| < 2^37, N * 2^(54-r) <= 2^62
+  m.jscale = S.q * S.w0 * std::ldexp(1.0, m.rshift) / (c.h * m.cxk * 8388608.0);
+  m.ke_scale = 0.5 * S.m * S.w0 / (m.cxk * m.cxk);
+  m.e_scale = (float)(0.5 * c.dt * S.q / S.m * m.cxk);
+  m.agg = h->cfg.sort_period > 0 ? 1 : 0;
+  m.cd = ff_from_double(c.dt * S.q / S.m * m.cxk);
+  CUDA_TRY(es1d_mix_prepare(m));
+  Es1dMixBufs &bm = h->bm;
+  size_t npad = (size_t)((h->N + 3) / 4 * 4);
+  if ((rc = h->alloc(&bm.X, npad)) || (rc = h->alloc(&bm.vh, npad)) || (rc = h->alloc(&bm.vl, npad)) ||
+      (rc = h->alloc(&bm.Vs, npad)))
+    return rc;
+  for (int k = 0; k < 2; k++)
+    if ((rc = h->alloc(&bm.J1[k], c.nc)) || (rc = h->alloc(&bm.J2[k], c.nc))) return rc;
+  CUDA_TRY(cudaMemsetAsync(bm.X, 0, sizeof(uint32_t) * npad, h->st));
+  CUDA_TRY(cudaMemsetAsync(bm.vh, 0, sizeof(float) * npad, h->st));
+  CUDA_TRY(cudaMemsetAsync(bm.vl, 0, sizeof(float) * npad, h->st));
+  for (int k = 0; k < 2; k++) {
+    bm.E[k] = b.E[k];
+    CUDA_TRY(cudaMemsetAsync(bm.J1[k], 0, sizeof(long long) * c.nc, h->st));
+    CUDA_TRY(cudaMemsetAsync(bm.J2[k], 0, sizeof(long long) * c.nc, h->st));
+  }
+  bm.ke_part = b.ke_part;
+  bm.fallback = b.fallback;
+  bm.te = b.te;
+  bm.we = b.we;
+  bm.err = b.err;
+  if (h->cfg.sort_period > 0) {
+    Es1dMixBufs &alt = h->bm_alt;
+    alt = bm;
+    if ((rc = h->alloc(&alt.X, npad)) || (rc = h->alloc(&alt.vh, npad)) ||
+        (rc = h->alloc(&alt.vl, npad)) || (rc = h->alloc(&h->ids_alt, (size_t)h->N)))
+      return rc;
+    CUDA_TRY(cudaMemsetAsync(alt.X, 0, sizeof(uint32_t) * npad, h->st));
+    CUDA_TRY(cudaMemsetAsync(alt.vh, 0, sizeof(float) * npad, h->st));
+    CUDA_TRY(cudaMemsetAsync(alt.vl, 0, sizeof(float) * npad, h->st));
+    h->sort_blocks = es1d_mix_sort_blocks(m, h->nsm);
+    if ((rc = h->alloc(&h->sort_hist, (size_t)c.nc * (h->sort_blocks + 1)))) return rc;
+  }
+  es1d_mix_from_fp64(m, b.x, b.v, bm, h->ls, h->st);
+  CUDA_TRY(cudaGetLastError());
+  if (solve_e0) {
+    // Gauss's law from the exact integer charge of the stored markers (the
+    // same weights every later deposit uses; independent of marker order)
+    long long *cnt = bm.J2[1];
+    es1d_mix_charge(m, bm, cnt, h->ls, h->st);
+    CUDA_TRY(cudaGetLastError());
+    std::vector<long long> ci(c.nc);
+    CUDA_TRY(cudaMemcpyAsync(ci.data(), cnt, sizeof(long long) * c.nc, cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    std::vector<double> r(c.nc), e;
+    for (int i = 0; i < c.nc; i++) r[i] = S.q * S.w0 / c.h * std::ldexp((double)ci[i], -23);
+    poisson_1d_host(r, c.L, e);
+    CUDA_TRY(cudaMemcpyAsync(b.E[0], e.data(), sizeof(double) * c.nc, cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(long long) * c.nc, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+  }
+  if (h->cfg.sort_period > 0) {
+    if ((rc = sort_mixed(h))) return rc;
+  }
+  if (m.scheme == 2) {
+    es1d_mix_deposit_initial(m, bm, (int)(h->steps_done & 1), h->ls, h->st);
+    CUDA_TRY(cudaGetLastError());
+  }
+  return PIC_OK;
 }
 
 int init_es1d(pic_handle *h, const pic_species *species, const double *E0) {
@@ -248,12 +379,14 @@ int init_es1d(pic_handle *h, const pic_species *species, const double *E0) {
     CUDA_TRY(cudaMemsetAsync(b.J2[k], 0, sizeof(double) * nc, h->st));
     CUDA_TRY(cudaMemsetAsync(b.E[k], 0, sizeof(double) * nc, h->st));
   }
-  if (E0) {
-    std::vector<double> e(nc);
+  if (E0 || h->mixed) {
+    std::vector<double> e(nc, 0.0);
+    if (E0) {
     CUDA_TRY(cudaMemcpyAsync(e.data(), E0, sizeof(double) * nc, cudaMemcpyDefault, h->st));
     CUDA_TRY(cudaStreamSynchronize(h->st));
     for (int i = 0; i < nc; i++)
       if (!std::isfinite(e[i])) return fail(PIC_ERR_NONFINITE, "pic_init: E0[%d] is not finite", i);
+    }
     CUDA_TRY(cudaMemcpyAsync(b.E[0], e.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, h->st));
   } else {
     double *rho = b.J2[1];  // scratch, cleared again below
@@ -266,7 +399,9 @@ int init_es1d(pic_handle *h, const pic_species *species, const double *E0) {
     CUDA_TRY(cudaMemcpyAsync(b.E[0], e.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, h->st));
     CUDA_TRY(cudaMemsetAsync(rho, 0, sizeof(double) * nc, h->st));
   }
-  if (c.scheme == 2) {
+  if (h->mixed) {
+    if ((rc = init_mixed(h, E0 == nullptr))) return rc;
+  } else if (c.scheme == 2) {
     es1d_fp64_deposit_initial(c, b, 0, h->ls, h->st);
     CUDA_TRY(cudaGetLastError());
   }
@@ -276,9 +411,21 @@ int init_es1d(pic_handle *h, const pic_species *species, const double *E0) {
 
 // Re-establishes the invariants of the step sequence after a state change:
 // zero currents and, for ESEC2, j^{n,*} of the new state.
-int restart_es1d(pic_handle *h) {
+int restart_es1d(pic_handle *h, bool particles_changed) {
   Es1dFp64Bufs &b = h->b1;
   int par = (int)(h->steps_done & 1);
+  if (h->mixed) {
+    Es1dMixBufs &bm = h->bm;
+    for (int k = 0; k < 2; k++) {
+      CUDA_TRY(cudaMemsetAsync(bm.J1[k], 0, sizeof(long long) * h->cm.nc, h->st));
+      CUDA_TRY(cudaMemsetAsync(bm.J2[k], 0, sizeof(long long) * h->cm.nc, h->st));
+    }
+    // the FP64 staging arrays hold the new markers only after pic_set_particles
+    if (particles_changed) es1d_mix_from_fp64(h->cm, b.x, b.v, bm, h->ls, h->st);
+    if (h->cm.scheme == 2) es1d_mix_deposit_initial(h->cm, bm, par, h->ls, h->st);
+    CUDA_TRY(cudaGetLastError());
+    return check_flags(h, "pic_set_*");
+  }
   for (int k = 0; k < 2; k++) {
     CUDA_TRY(cudaMemsetAsync(b.J1[k], 0, sizeof(double) * h->c1.nc, h->st));
     CUDA_TRY(cudaMemsetAsync(b.J2[k], 0, sizeof(double) * h->c1.nc, h->st));
@@ -324,8 +471,6 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
   } else {
     return fail(PIC_ERR_ARG, "pic_init: unknown solver");
   }
-  if (cfg->precision == PIC_PREC_MIXED)
-    return fail(PIC_ERR_UNSUPPORTED, "pic_init: mixed precision not built in this library version");
   int64_t N = 0;
   bool weighted = false;
   for (int s = 0; s < nspecies; s++) {
@@ -337,12 +482,16 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
     N += S.n;
   }
   if (N > ((int64_t)1 << 40)) return fail(PIC_ERR_ARG, "pic_init: too many markers");
+  if (cfg->precision == PIC_PREC_MIXED && (nspecies != 1 || weighted))
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: the mixed form runs one species with a uniform "
+                                     "weight (use PIC_PREC_FP64 for several species or weighted markers)");
 
   pic_handle *h = new pic_handle();
   h->cfg = *cfg;
   h->st = (cudaStream_t)cfg->cuda_stream;
   h->nsp = nspecies;
   h->weighted = weighted;
+  h->mixed = cfg->precision == PIC_PREC_MIXED;
   int64_t off = 0;
   for (int s = 0; s < nspecies; s++) {
     h->sp[s] = SpeciesInfo{species[s].q, species[s].m, species[s].w0, species[s].n, off,
@@ -360,6 +509,7 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
   int64_t want = (N + 511) / 512;
   h->ls.block = 512;
   h->ls.grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 2));
+  h->nsm = nsm;
   int rc = init_es1d(h, species, E0);
   if (rc) {
     std::string msg = g_last_error;
@@ -382,12 +532,25 @@ int pic_step_async(pic_handle *h, int nsteps) {
     CUDA_TRY(cudaMemsetAsync(b.fallback, 0, sizeof(unsigned long long) * kStepsCap, h->st));
   }
   for (int k = 0; k < nsteps; k++) {
-    CUDA_TRY(h->timed_launch(0, [&] {
-      es1d_fp64_pass_c(h->c1, b, h->steps_done, h->pending, h->ls, h->st);
-    }));
-    CUDA_TRY(h->timed_launch(1, [&] {
-      es1d_fp64_pass_e(h->c1, b, h->steps_done, h->pending, h->ls, h->st);
-    }));
+    if (h->mixed) {
+      if (h->cfg.sort_period > 0 && h->steps_done > 0 && h->steps_done % h->cfg.sort_period == 0) {
+        int rc = sort_mixed(h);
+        if (rc) return rc;
+      }
+      CUDA_TRY(h->timed_launch(0, [&] {
+        es1d_mix_pass_c(h->cm, h->bm, h->steps_done, h->pending, h->ls, h->st);
+      }));
+      CUDA_TRY(h->timed_launch(1, [&] {
+        es1d_mix_pass_e(h->cm, h->bm, h->steps_done, h->pending, h->ls, h->st);
+      }));
+    } else {
+      CUDA_TRY(h->timed_launch(0, [&] {
+        es1d_fp64_pass_c(h->c1, b, h->steps_done, h->pending, h->ls, h->st);
+      }));
+      CUDA_TRY(h->timed_launch(1, [&] {
+        es1d_fp64_pass_e(h->c1, b, h->steps_done, h->pending, h->ls, h->st);
+      }));
+    }
     h->launches += 2;
     h->steps_done++;
     h->pending++;
@@ -404,7 +567,12 @@ int pic_read_stats(pic_handle *h, int capacity, int64_t *nfallback_per_step, dou
   if ((nfallback_per_step || te_per_step) && capacity < n)
     return fail(PIC_ERR_ARG, "pic_read_stats: %d steps pending, capacity %d", n, capacity);
   Es1dFp64Bufs &b = h->b1;
-  CUDA_TRY(h->timed_launch(2, [&] { es1d_fp64_finalize(h->c1, b, n - 1, h->ls.grid, h->st); }));
+  CUDA_TRY(h->timed_launch(2, [&] {
+    if (h->mixed)
+      es1d_mix_finalize(h->bm, n - 1, h->ls.grid, h->st);
+    else
+      es1d_fp64_finalize(h->c1, b, n - 1, h->ls.grid, h->st);
+  }));
   h->launches += 1;
   std::vector<unsigned long long> fb(n);
   std::vector<double> te(n);
@@ -474,10 +642,22 @@ int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, 
   double *ke_d = h->b1.ke_part;  // reuse: nsp <= grid entries are needed
   if (h->ls.grid < h->nsp) return fail(PIC_ERR_ARG, "pic_energy: internal size");
   // ke_part is only consumed during pic_step; it is safe to reuse between calls.
-  es1d_fp64_kinetic(c, h->b1.v, h->b1.w, ke_d, h->st);
-  CUDA_TRY(cudaGetLastError());
   std::vector<double> ke(h->nsp), e(c.nc);
-  CUDA_TRY(cudaMemcpyAsync(ke.data(), ke_d, sizeof(double) * h->nsp, cudaMemcpyDeviceToHost, h->st));
+  if (h->mixed) {
+    es1d_mix_kinetic(h->cm, h->bm, ke_d, h->ls.grid, h->st);
+    CUDA_TRY(cudaGetLastError());
+    std::vector<double> part(h->ls.grid);
+    CUDA_TRY(cudaMemcpyAsync(part.data(), ke_d, sizeof(double) * h->ls.grid, cudaMemcpyDeviceToHost,
+                             h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    double acc = 0.0;
+    for (double p : part) acc += p;
+    ke[0] = acc;
+  } else {
+    es1d_fp64_kinetic(c, h->b1.v, h->b1.w, ke_d, h->st);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(ke.data(), ke_d, sizeof(double) * h->nsp, cudaMemcpyDeviceToHost, h->st));
+  }
   CUDA_TRY(cudaMemcpyAsync(e.data(), h->b1.E[h->steps_done & 1], sizeof(double) * c.nc,
                            cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(cudaStreamSynchronize(h->st));
@@ -499,6 +679,10 @@ int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, 
 int pic_get_particles(pic_handle *h, int s, double *x, double *v) {
   if (!h || s < 0 || s >= h->nsp) return fail(PIC_ERR_ARG, "pic_get_particles: bad handle or species");
   const SpeciesInfo &S = h->sp[s];
+  if (h->mixed) {
+    es1d_mix_to_fp64(h->cm, h->bm, h->b1.x, h->b1.v, h->ls, h->st);
+    CUDA_TRY(cudaGetLastError());
+  }
   if (x) CUDA_TRY(cudaMemcpyAsync(x, h->b1.x + S.offset, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
   if (v) CUDA_TRY(cudaMemcpyAsync(v, h->b1.v + S.offset, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
   CUDA_TRY(cudaStreamSynchronize(h->st));
@@ -523,7 +707,7 @@ int pic_set_particles(pic_handle *h, int s, const double *x, const double *v) {
   CUDA_TRY(cudaMemcpyAsync(h->ids + S.offset, ids.data(), sizeof(int64_t) * S.n,
                            cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(cudaStreamSynchronize(h->st));
-  return restart_es1d(h);
+  return restart_es1d(h, true);
 }
 
 int pic_get_fields(pic_handle *h, double *E, double *B) {
@@ -542,7 +726,7 @@ int pic_set_fields(pic_handle *h, const double *E, const double *B) {
   CUDA_TRY(cudaMemcpyAsync(h->b1.E[h->steps_done & 1], E, sizeof(double) * h->c1.nc,
                            cudaMemcpyDefault, h->st));
   CUDA_TRY(cudaStreamSynchronize(h->st));
-  return restart_es1d(h);
+  return restart_es1d(h, false);
 }
 
 int pic_step_count(pic_handle *h, int64_t *steps) {

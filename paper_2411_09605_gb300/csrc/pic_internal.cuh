@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "ff.cuh"
 #include "pic.h"
 
 namespace pic {
@@ -42,6 +43,39 @@ struct Es1dConst {
   double q_h[kMaxSpecies];       // q / h (weighted markers: times w_p)
   double half_mw[kMaxSpecies];   // m w0 / 2 (uniform weights)
   double half_m[kMaxSpecies];    // m / 2
+};
+
+// Per-launch constants of the 1D mixed-precision kernels (one species, uniform
+// weight).  Velocities are stored in "V units": v * cxk.
+struct Es1dMixConst {
+  int nc;
+  int order;
+  int scheme;
+  int remove_mean;
+  int gamma_on;
+  int rshift;          // deposit term = round(V* s_k / 2^rshift)
+  int kv;              // one V unit = 2^-kv position units per half step
+  int agg;             // warp-aggregated deposits (markers kept cell-sorted)
+  int64_t n;
+  double L, h, dt;
+  double cxk;          // (dt 2^31 / L) 2^kv
+  double jscale;       // J_h = jscale * (integer node sum)
+  double ke_scale;     // (m w / 2) / cxk^2
+  float e_scale;       // dt/2 (q/m) cxk: E** -> increment of v* in V units
+  ff cd;               // dt (q/m) cxk as a float pair
+};
+
+struct Es1dMixBufs {
+  uint32_t *X;              // [N padded to 4] positions, x = X L / 2^32
+  float *vh, *vl;           // [N padded to 4] velocity pairs
+  int *Vs;                  // [N padded to 4] V* of the current step (pass C -> pass E)
+  double *E[2];
+  long long *J1[2], *J2[2]; // integer current sums
+  double *ke_part;
+  unsigned long long *fallback;
+  double *te;
+  double *we;
+  unsigned *err;
 };
 
 // Everything the 1D FP64 kernels touch.
@@ -79,5 +113,29 @@ void es1d_fp64_charge(const Es1dConst &c, const double *x, const double *w, doub
                       LaunchShape ls, cudaStream_t st);
 void es1d_fp64_kinetic(const Es1dConst &c, const double *v, const double *w, double *ke_sp,
                        cudaStream_t st);
+
+// 1D mixed path (es1d_mixed.cu)
+cudaError_t es1d_mix_prepare(const Es1dMixConst &c);
+void es1d_mix_pass_c(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_index, int slot,
+                     LaunchShape ls, cudaStream_t st);
+void es1d_mix_pass_e(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_index, int slot,
+                     LaunchShape ls, cudaStream_t st);
+void es1d_mix_deposit_initial(const Es1dMixConst &c, const Es1dMixBufs &b, int parity,
+                              LaunchShape ls, cudaStream_t st);
+void es1d_mix_finalize(const Es1dMixBufs &b, int slot, int nblocks, cudaStream_t st);
+void es1d_mix_charge(const Es1dMixConst &c, const Es1dMixBufs &b, long long *count,
+                     LaunchShape ls, cudaStream_t st);
+void es1d_mix_from_fp64(const Es1dMixConst &c, const double *x, const double *v, Es1dMixBufs &b,
+                        LaunchShape ls, cudaStream_t st);
+void es1d_mix_to_fp64(const Es1dMixConst &c, const Es1dMixBufs &b, double *x, double *v,
+                      LaunchShape ls, cudaStream_t st);
+void es1d_mix_kinetic(const Es1dMixConst &c, const Es1dMixBufs &b, double *part, int nblocks,
+                      cudaStream_t st);
+void es1d_absmax(const double *v, int64_t n, unsigned long long *out, LaunchShape ls,
+                 cudaStream_t st);
+int es1d_mix_sort_blocks(const Es1dMixConst &c, int nsm);
+cudaError_t es1d_mix_sort(const Es1dMixConst &c, const Es1dMixBufs &src, const Es1dMixBufs &dst,
+                          const int64_t *ids_in, int64_t *ids_out, uint32_t *H, int G,
+                          cudaStream_t st);
 
 }  // namespace pic
