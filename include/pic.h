@@ -155,7 +155,8 @@ int pic_launch_count(pic_handle *h, int64_t *launches);
  * the number of launches and their summed device time (ms) of one kind:
  * 0 = pass C (gather at x*, push to v*, deposit of j^{*,n+1/2}),
  * 1 = pass E (gather at x^{n+1/2}, Gamma, state update, next j^{n,*}),
- * 2 = per-step energy/fallback finalisation, 3 = cell sort.
+ * 2 = per-step energy/fallback finalisation, 3 = cell sort,
+ * 4 = grid field updates (Yee solver).
  */
 int pic_set_profiling(pic_handle *h, int on);
 int pic_profile(pic_handle *h, int kind, int64_t *launches, double *total_ms);
@@ -175,7 +176,9 @@ int pic_get_particles(pic_handle *h, int s, double *x, double *v);
 int pic_get_ids(pic_handle *h, int s, int64_t *ids);
 /* Replaces species s (same n; resets its ids to 0..n-1). */
 int pic_set_particles(pic_handle *h, int s, const double *x, const double *v);
-/* Fields: E^n and (Yee) B^{n-1/2}; B may be NULL for the ES solver. */
+/* Fields: E^n and (Yee) B^{n-1/2}; B may be NULL for the ES solver and is
+ * required by pic_set_fields for the Yee solver (B^{n+1/2} is then rebuilt as
+ * B^{n-1/2} - dt curl E^n). */
 int pic_get_fields(pic_handle *h, double *E, double *B);
 int pic_set_fields(pic_handle *h, const double *E, const double *B);
 

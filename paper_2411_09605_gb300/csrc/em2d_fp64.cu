@@ -1,0 +1,434 @@
+// 2D3V electromagnetic step with the leapfrog / Yee field update (Sec. 4.1,
+// Eq. EMleapfrog), FP64 form.
+//
+// Yee lattice on a periodic nx x ny grid, component-major [3][ny][nx] arrays:
+//   Ex (i+1/2, j)  Ey (i, j+1/2)  Ez (i, j)      (J the same)
+//   Bx (i, j+1/2)  By (i+1/2, j)  Bz (i+1/2, j+1/2)
+// Gather of E_c and deposit of J_c use the same tensor-product B-spline
+// centred on component c's nodes, so Eq. exp_econs_simple holds per component.
+//
+// Per step (the state is E^n, B^{n-1/2}, Bp = B^{n+1/2} and, for ESEC2,
+// j^{n,*} deposited at the end of the previous step):
+//   K1 grid     E* = E^n + dt/2 (c^2 curl Bp - j^{n,*}); clear j^{*,n+1/2}
+//   K2 markers  x*, E**, B at x*, v* (closed form of the implicit relation),
+//               x^{n+1/2}, deposit of j^{*,n+1/2}
+//   K3 grid     E^{n+1} = E^n + dt (c^2 curl Bp - j^{*,n+1/2}), E^{n+1/2}
+//   K4 markers  recompute v*, x^{n+1/2}; gather E^{n+1/2}, B at x^{n+1/2};
+//               v^dag, Gamma (fallback counted), x^{n+1}, v^{n+1}, KE, next j^{n+1,*}
+//   K5 grid     B^{n+3/2} = Bp - dt curl E^{n+1}; W_E^{n+1}, W_B^{n+1} =
+//               (c^2/2)|h| sum Bp . B^{n+3/2} (the energy of the new state)
+// Fields stay in global memory (0.8 MB at 128 x 128, L2-resident); the
+// current is accumulated with FP64 global atomics.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  if ((unsigned)i < (unsigned)n) return i;
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ double wrapd(double y, double L, unsigned *err) {
+  if (y < 0.0) y += L;
+  if (y >= L) y -= L;
+  if (!(y >= 0.0 && y < L)) atomicOr(err, kErrBounds);
+  return y;
+}
+
+// 1D B-spline weights of coordinate xi (cell units) on nodes i0 .. i0+ORDER
+template <int ORDER>
+struct W1 {
+  int i0;
+  double w[ORDER + 1];
+  __device__ __forceinline__ void set(double xi) {
+    if (ORDER == 1) {
+      double fl = floor(xi);
+      double f = __dadd_rn(xi, -fl);
+      i0 = (int)fl;
+      w[0] = __dadd_rn(1.0, -f);
+      w[1] = f;
+    } else {
+      double fl = floor(__dadd_rn(xi, 0.5));
+      double d = __dadd_rn(xi, -fl);
+      i0 = (int)fl - 1;
+      double a = __dadd_rn(0.5, -d), b = __dadd_rn(0.5, d);
+      w[0] = __dmul_rn(0.5, __dmul_rn(a, a));
+      w[1] = __fma_rn(-d, d, 0.75);
+      w[ORDER] = __dmul_rn(0.5, __dmul_rn(b, b));
+    }
+  }
+};
+
+// Weights of a point for integer-node (I) and half-node (H) components in x, y.
+template <int ORDER>
+struct Shape2 {
+  W1<ORDER> xI, xH, yI, yH;
+  __device__ __forceinline__ Shape2(const Em2dConst &c, double x, double y) {
+    const double xi = __dmul_rn(x, c.inv_hx), yi = __dmul_rn(y, c.inv_hy);
+    xI.set(xi);
+    xH.set(__dadd_rn(xi, -0.5));
+    yI.set(yi);
+    yH.set(__dadd_rn(yi, -0.5));
+  }
+};
+
+template <int ORDER>
+__device__ __forceinline__ double gather_c(const double *F, int nx, int ny, const W1<ORDER> &wx,
+                                           const W1<ORDER> &wy) {
+  double s = 0.0;
+#pragma unroll
+  for (int b = 0; b <= ORDER; b++) {
+    const int row = wrapi(wy.i0 + b, ny) * nx;
+    double r = 0.0;
+#pragma unroll
+    for (int a = 0; a <= ORDER; a++) r = fma(__ldg(&F[row + wrapi(wx.i0 + a, nx)]), wx.w[a], r);
+    s = fma(r, wy.w[b], s);
+  }
+  return s;
+}
+
+template <int ORDER>
+__device__ __forceinline__ void deposit_c(double *J, int nx, int ny, const W1<ORDER> &wx,
+                                          const W1<ORDER> &wy, double coef) {
+#pragma unroll
+  for (int b = 0; b <= ORDER; b++) {
+    const int row = wrapi(wy.i0 + b, ny) * nx;
+    const double cb = coef * wy.w[b];
+#pragma unroll
+    for (int a = 0; a <= ORDER; a++) atomicAdd(&J[row + wrapi(wx.i0 + a, nx)], cb * wx.w[a]);
+  }
+}
+
+// E (Ex: H,I; Ey: I,H; Ez: I,I) and B (Bx: I,H; By: H,I; Bz: H,H) at a point
+template <int ORDER>
+__device__ __forceinline__ void gather_eb(const Em2dConst &c, const double *E, const double *B,
+                                          const Shape2<ORDER> &S, double e[3], double bb[3]) {
+  const int nx = c.nx, ny = c.ny, nc = c.nx * c.ny;
+  if (E) {
+    e[0] = gather_c<ORDER>(E, nx, ny, S.xH, S.yI);
+    e[1] = gather_c<ORDER>(E + nc, nx, ny, S.xI, S.yH);
+    e[2] = gather_c<ORDER>(E + 2 * nc, nx, ny, S.xI, S.yI);
+  }
+  bb[0] = gather_c<ORDER>(B, nx, ny, S.xI, S.yH);
+  bb[1] = gather_c<ORDER>(B + nc, nx, ny, S.xH, S.yI);
+  bb[2] = gather_c<ORDER>(B + 2 * nc, nx, ny, S.xH, S.yH);
+}
+
+template <int ORDER>
+__device__ __forceinline__ void deposit_j(const Em2dConst &c, double *J, const Shape2<ORDER> &S,
+                                          double coef, const double u[3]) {
+  const int nx = c.nx, ny = c.ny, nc = c.nx * c.ny;
+  deposit_c<ORDER>(J, nx, ny, S.xH, S.yI, coef * u[0]);
+  deposit_c<ORDER>(J + nc, nx, ny, S.xI, S.yH, coef * u[1]);
+  deposit_c<ORDER>(J + 2 * nc, nx, ny, S.xI, S.yI, coef * u[2]);
+}
+
+__device__ __forceinline__ int species_of2(const Em2dConst &c, int64_t p) {
+  int s = 0;
+  while (s < c.nsp - 1 && p >= c.sp_end[s]) s++;
+  return s;
+}
+
+// x*, E**, B at x*, v* and x^{n+1/2}, bit for bit the same in K2 and K4.
+template <int ORDER>
+__device__ __forceinline__ void half_push_em(const Em2dConst &c, const Em2dBufs &b, int s,
+                                             double x, double y, const double v[3], double vs[3],
+                                             double &xh, double &yh) {
+  const double hdt = 0.5 * c.dt;
+  const double xs = wrapd(__fma_rn(hdt, v[0], x), c.Lx, b.err);
+  const double ys = wrapd(__fma_rn(hdt, v[1], y), c.Ly, b.err);
+  Shape2<ORDER> S(c, xs, ys);
+  double e[3], bb[3];
+  gather_eb<ORDER>(c, b.Es, b.Bp, S, e, bb);
+  const double k = __dmul_rn(hdt, c.qm[s]);
+  double u[3], t[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    u[d] = __fma_rn(k, e[d], v[d]);
+    t[d] = __dmul_rn(k, bb[d]);
+  }
+  // v* - v* x t = u  ->  v* = (u + u x t + (u.t) t) / (1 + |t|^2)
+  const double uxt0 = __dadd_rn(__dmul_rn(u[1], t[2]), -__dmul_rn(u[2], t[1]));
+  const double uxt1 = __dadd_rn(__dmul_rn(u[2], t[0]), -__dmul_rn(u[0], t[2]));
+  const double uxt2 = __dadd_rn(__dmul_rn(u[0], t[1]), -__dmul_rn(u[1], t[0]));
+  const double ut = __fma_rn(u[2], t[2], __fma_rn(u[1], t[1], __dmul_rn(u[0], t[0])));
+  const double tt = __fma_rn(t[2], t[2], __fma_rn(t[1], t[1], __dmul_rn(t[0], t[0])));
+  const double inv = __drcp_rn(__dadd_rn(1.0, tt));
+  vs[0] = __dmul_rn(__fma_rn(ut, t[0], __dadd_rn(u[0], uxt0)), inv);
+  vs[1] = __dmul_rn(__fma_rn(ut, t[1], __dadd_rn(u[1], uxt1)), inv);
+  vs[2] = __dmul_rn(__fma_rn(ut, t[2], __dadd_rn(u[2], uxt2)), inv);
+  xh = wrapd(__fma_rn(hdt, vs[0], x), c.Lx, b.err);
+  yh = wrapd(__fma_rn(hdt, vs[1], y), c.Ly, b.err);
+}
+
+__device__ double block_sum2(double s, double *red) {
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[k];
+  return t;
+}
+
+// curl of B on the E locations at (i, j), component d
+__device__ __forceinline__ double curl_b(const Em2dConst &c, const double *B, int i, int j, int d) {
+  const int nx = c.nx, ny = c.ny, nc = nx * ny;
+  const double *Bx = B, *By = B + nc, *Bz = B + 2 * nc;
+  const int im = i == 0 ? nx - 1 : i - 1, jm = j == 0 ? ny - 1 : j - 1;
+  if (d == 0) return (Bz[j * nx + i] - Bz[jm * nx + i]) * c.inv_hy;
+  if (d == 1) return -(Bz[j * nx + i] - Bz[j * nx + im]) * c.inv_hx;
+  return (By[j * nx + i] - By[j * nx + im]) * c.inv_hx - (Bx[j * nx + i] - Bx[jm * nx + i]) * c.inv_hy;
+}
+
+// curl of E on the B locations at (i, j), component d
+__device__ __forceinline__ double curl_e(const Em2dConst &c, const double *E, int i, int j, int d) {
+  const int nx = c.nx, ny = c.ny, nc = nx * ny;
+  const double *Ex = E, *Ey = E + nc, *Ez = E + 2 * nc;
+  const int ip = i + 1 == nx ? 0 : i + 1, jp = j + 1 == ny ? 0 : j + 1;
+  if (d == 0) return (Ez[jp * nx + i] - Ez[j * nx + i]) * c.inv_hy;
+  if (d == 1) return -(Ez[j * nx + ip] - Ez[j * nx + i]) * c.inv_hx;
+  return (Ey[j * nx + ip] - Ey[j * nx + i]) * c.inv_hx - (Ex[jp * nx + i] - Ex[j * nx + i]) * c.inv_hy;
+}
+
+// K1: E* (ESEC2: with j^{n,*}; ESEC1: E^n), clear J2
+__global__ void em_k1_kernel(Em2dConst c, Em2dBufs b) {
+  const int nc = c.nx * c.ny;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < 3 * nc; a += gridDim.x * blockDim.x) {
+    const int d = a / nc, ij = a % nc, i = ij % c.nx, j = ij / c.nx;
+    double es = b.E[a];
+    if (c.scheme == 2) es = es + 0.5 * c.dt * (c.c2 * curl_b(c, b.Bp, i, j, d) - b.J1[a]);
+    b.Es[a] = es;
+    b.J2[a] = 0.0;
+  }
+}
+
+// K3: E^{n+1}, E^{n+1/2}; clear J1 (it receives j^{n+1,*})
+__global__ void em_k3_kernel(Em2dConst c, Em2dBufs b) {
+  const int nc = c.nx * c.ny;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < 3 * nc; a += gridDim.x * blockDim.x) {
+    const int d = a / nc, ij = a % nc, i = ij % c.nx, j = ij / c.nx;
+    const double en = b.E[a] + c.dt * (c.c2 * curl_b(c, b.Bp, i, j, d) - b.J2[a]);
+    b.Eh[a] = 0.5 * (b.E[a] + en);
+    b.En[a] = en;
+    b.J1[a] = 0.0;
+  }
+}
+
+// K5: B^{n+3/2} = Bp - dt curl E^{n+1}, block partials of W_E and W_B
+__global__ void __launch_bounds__(256) em_k5_kernel(Em2dConst c, Em2dBufs b) {
+  __shared__ double red[33];
+  const int nc = c.nx * c.ny;
+  double we = 0.0, wb = 0.0;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < 3 * nc; a += gridDim.x * blockDim.x) {
+    const int d = a / nc, ij = a % nc, i = ij % c.nx, j = ij / c.nx;
+    const double bpp = b.Bp[a] - c.dt * curl_e(c, b.En, i, j, d);
+    b.Bpp[a] = bpp;
+    we += b.En[a] * b.En[a];
+    wb += b.Bp[a] * bpp;
+  }
+  double t = block_sum2(we, red);
+  if (threadIdx.x == 0) b.wf_part[2 * blockIdx.x] = t;
+  t = block_sum2(wb, red);
+  if (threadIdx.x == 0) b.wf_part[2 * blockIdx.x + 1] = t;
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(256) em_pass_c_kernel(Em2dConst c, Em2dBufs b) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n_total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int s = species_of2(c, p);
+    const double v[3] = {b.vx[p], b.vy[p], b.vz[p]};
+    double vs[3], xh, yh;
+    half_push_em<ORDER>(c, b, s, b.x[p], b.y[p], v, vs, xh, yh);
+    Shape2<ORDER> S(c, xh, yh);
+    deposit_j<ORDER>(c, b.J2, S, b.w ? c.q_a[s] * b.w[p] : c.qw_a[s], vs);
+  }
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(256) em_pass_e_kernel(Em2dConst c, Em2dBufs b, int slot) {
+  __shared__ double red[33];
+  double ke = 0.0;
+  unsigned nfb = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n_total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int s = species_of2(c, p);
+    const double x = b.x[p], y = b.y[p];
+    const double v[3] = {b.vx[p], b.vy[p], b.vz[p]};
+    double vs[3], xh, yh;
+    half_push_em<ORDER>(c, b, s, x, y, v, vs, xh, yh);
+    Shape2<ORDER> S(c, xh, yh);
+    double e[3], bb[3];
+    gather_eb<ORDER>(c, b.Eh, b.Bp, S, e, bb);
+    const double k = c.dt * c.qm[s];
+    const double vxb[3] = {vs[1] * bb[2] - vs[2] * bb[1], vs[2] * bb[0] - vs[0] * bb[2],
+                           vs[0] * bb[1] - vs[1] * bb[0]};
+    double vd[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) vd[d] = v[d] + k * (e[d] + vxb[d]);
+    const double R = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] +
+                     2.0 * (vs[0] * (vd[0] - v[0]) + vs[1] * (vd[1] - v[1]) + vs[2] * (vd[2] - v[2]));
+    const double vd2 = vd[0] * vd[0] + vd[1] * vd[1] + vd[2] * vd[2];
+    double g = 1.0;
+    if (c.gamma_on) {
+      if (R < 0.0 || vd2 == 0.0)
+        nfb++;
+      else
+        g = sqrt(R) / sqrt(vd2);
+    }
+    double vn[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) vn[d] = vd[d] * g;
+    const double xn = wrapd(x + c.dt * vs[0], c.Lx, b.err);
+    const double yn = wrapd(y + c.dt * vs[1], c.Ly, b.err);
+    const double wp = b.w ? b.w[p] : 1.0;
+    ke += (b.w ? c.half_m[s] * wp : c.half_mw[s]) * (vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
+    if (c.scheme == 2) {
+      const double xs2 = wrapd(xn + 0.5 * c.dt * vn[0], c.Lx, b.err);
+      const double ys2 = wrapd(yn + 0.5 * c.dt * vn[1], c.Ly, b.err);
+      Shape2<ORDER> S2(c, xs2, ys2);
+      deposit_j<ORDER>(c, b.J1, S2, b.w ? c.q_a[s] * wp : c.qw_a[s], vn);
+    }
+    b.x[p] = xn;
+    b.y[p] = yn;
+    b.vx[p] = vn[0];
+    b.vy[p] = vn[1];
+    b.vz[p] = vn[2];
+    if (!isfinite(vn[0] + vn[1] + vn[2])) atomicOr(b.err, kErrNonfinite);
+  }
+  for (int o = 16; o > 0; o >>= 1) nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
+  if ((threadIdx.x & 31) == 0 && nfb) atomicAdd(&b.fallback[slot], (unsigned long long)nfb);
+  double t = block_sum2(ke, red);
+  if (threadIdx.x == 0) b.ke_part[blockIdx.x] = t;
+}
+
+// j^{n,*} of the current state (start-up and after a state change)
+template <int ORDER>
+__global__ void __launch_bounds__(256) em_deposit_initial_kernel(Em2dConst c, Em2dBufs b) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n_total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int s = species_of2(c, p);
+    const double v[3] = {b.vx[p], b.vy[p], b.vz[p]};
+    const double xs = wrapd(b.x[p] + 0.5 * c.dt * v[0], c.Lx, b.err);
+    const double ys = wrapd(b.y[p] + 0.5 * c.dt * v[1], c.Ly, b.err);
+    Shape2<ORDER> S(c, xs, ys);
+    deposit_j<ORDER>(c, b.J1, S, b.w ? c.q_a[s] * b.w[p] : c.qw_a[s], v);
+  }
+}
+
+// Bp = B0 - dt curl E0 (the state's B^{n+1/2})
+__global__ void em_bhalf_kernel(Em2dConst c, const double *B, const double *E, double *Bp) {
+  const int nc = c.nx * c.ny;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < 3 * nc; a += gridDim.x * blockDim.x) {
+    const int d = a / nc, ij = a % nc, i = ij % c.nx, j = ij / c.nx;
+    Bp[a] = B[a] - c.dt * curl_e(c, E, i, j, d);
+  }
+}
+
+// TE of the step in slot: KE partials + field partials
+__global__ void em_finalize_kernel(Em2dBufs b, int slot, int nkb, int nfb, double we_scale,
+                                   double wb_scale) {
+  __shared__ double red[33];
+  double ke = 0.0, we = 0.0, wb = 0.0;
+  for (int i = threadIdx.x; i < nkb; i += blockDim.x) ke += b.ke_part[i];
+  for (int i = threadIdx.x; i < nfb; i += blockDim.x) {
+    we += b.wf_part[2 * i];
+    wb += b.wf_part[2 * i + 1];
+  }
+  double k = block_sum2(ke, red);
+  double e = block_sum2(we, red);
+  double m = block_sum2(wb, red);
+  if (threadIdx.x == 0) {
+    double te = k + we_scale * e + wb_scale * m;
+    b.te[slot] = te;
+    if (!isfinite(te)) atomicOr(b.err, kErrNonfinite);
+  }
+}
+
+__global__ void __launch_bounds__(256) em_kinetic_kernel(Em2dConst c, Em2dBufs b, double *out) {
+  __shared__ double red[33];
+  const int s = blockIdx.y;
+  int64_t beg = s == 0 ? 0 : c.sp_end[s - 1], end = c.sp_end[s];
+  double acc = 0.0;
+  for (int64_t p = beg + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < end;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    double v2 = b.vx[p] * b.vx[p] + b.vy[p] * b.vy[p] + b.vz[p] * b.vz[p];
+    acc += b.w ? c.half_m[s] * b.w[p] * v2 : c.half_mw[s] * v2;
+  }
+  double t = block_sum2(acc, red);
+  if (threadIdx.x == 0) out[s * gridDim.x + blockIdx.x] = t;
+}
+
+}  // namespace
+
+void em2d_k1(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st) {
+  em_k1_kernel<<<lg.grid, lg.block, 0, st>>>(c, b);
+}
+
+void em2d_pass_c(const Em2dConst &c, const Em2dBufs &b, LaunchShape lp, cudaStream_t st) {
+  if (c.order == 1)
+    em_pass_c_kernel<1><<<lp.grid, lp.block, 0, st>>>(c, b);
+  else
+    em_pass_c_kernel<2><<<lp.grid, lp.block, 0, st>>>(c, b);
+}
+
+void em2d_k3(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st) {
+  em_k3_kernel<<<lg.grid, lg.block, 0, st>>>(c, b);
+}
+
+void em2d_pass_e(const Em2dConst &c, const Em2dBufs &b, int slot, LaunchShape lp,
+                 cudaStream_t st) {
+  if (c.order == 1)
+    em_pass_e_kernel<1><<<lp.grid, lp.block, 0, st>>>(c, b, slot);
+  else
+    em_pass_e_kernel<2><<<lp.grid, lp.block, 0, st>>>(c, b, slot);
+}
+
+void em2d_k5(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st) {
+  em_k5_kernel<<<lg.grid, 256, 0, st>>>(c, b);
+}
+
+void em2d_finalize(const Em2dConst &c, const Em2dBufs &b, int slot, LaunchShape lp,
+                   LaunchShape lg, cudaStream_t st) {
+  em_finalize_kernel<<<1, 256, 0, st>>>(b, slot, lp.grid, lg.grid, 0.5 * c.area,
+                                        0.5 * c.c2 * c.area);
+}
+
+__global__ void em2d_validate_kernel(const double *x, const double *y, const double *vx,
+                                     const double *vy, const double *vz, int64_t n, double Lx,
+                                     double Ly, unsigned *err) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    if (!(x[p] >= 0.0 && x[p] < Lx) || !(y[p] >= 0.0 && y[p] < Ly)) atomicOr(err, kErrBounds);
+    if (!isfinite(vx[p]) || !isfinite(vy[p]) || !isfinite(vz[p])) atomicOr(err, kErrNonfinite);
+  }
+}
+
+void em2d_fp64_deposit_initial(const Em2dConst &c, const Em2dBufs &b, LaunchShape lp,
+                               cudaStream_t st) {
+  if (c.order == 1)
+    em_deposit_initial_kernel<1><<<lp.grid, lp.block, 0, st>>>(c, b);
+  else
+    em_deposit_initial_kernel<2><<<lp.grid, lp.block, 0, st>>>(c, b);
+}
+
+void em2d_fp64_bhalf(const Em2dConst &c, const double *B, const double *E, double *Bp,
+                     LaunchShape lg, cudaStream_t st) {
+  em_bhalf_kernel<<<lg.grid, lg.block, 0, st>>>(c, B, E, Bp);
+}
+
+void em2d_fp64_kinetic(const Em2dConst &c, const Em2dBufs &b, double *out, int nblocks,
+                       cudaStream_t st) {
+  em_kinetic_kernel<<<dim3(nblocks, c.nsp), 256, 0, st>>>(c, b, out);
+}
+
+}  // namespace pic

@@ -38,7 +38,7 @@ int fail(int code, const char *fmt, ...) {
   } while (0)
 
 constexpr int kStepsCap = 1024;  // per-step stats slots per chunk of pic_step
-constexpr int kProfKinds = 8;    // 0 pass C, 1 pass E, 2 stats finalize, 3 sort
+constexpr int kProfKinds = 8;    // 0 pass C, 1 pass E, 2 stats finalize, 3 sort, 4 field
 
 // Validates positions in [0, L) and finite velocities of a 1D state.
 __global__ void validate_1d_kernel(const double *x, const double *v, int64_t n, double L,
@@ -78,6 +78,11 @@ struct pic_handle {
   // 1D FP64 state (in the mixed form x, v serve as FP64 staging for get/set)
   Es1dConst c1{};
   Es1dFp64Bufs b1{};
+  // 2D3V Yee state
+  bool em = false;
+  Em2dConst ce{};
+  Em2dBufs be{};
+  LaunchShape lp{1, 256}, lg{1, 256};
   // 1D mixed-precision state
   bool mixed = false;
   Es1dMixConst cm{};
@@ -437,6 +442,108 @@ int restart_es1d(pic_handle *h, bool particles_changed) {
   return check_flags(h, "pic_set_*");
 }
 
+// Yee state change: validate markers, B^{n+1/2} from (E^n, B^{n-1/2}), j^{n,*}.
+int restart_em2d(pic_handle *h) {
+  Em2dBufs &b = h->be;
+  const int64_t nc3 = 3 * (int64_t)h->ce.nx * h->ce.ny;
+  em2d_validate_kernel<<<h->lp.grid, 256, 0, h->st>>>(b.x, b.y, b.vx, b.vy, b.vz, h->N, h->ce.Lx,
+                                                       h->ce.Ly, b.err);
+  CUDA_TRY(cudaGetLastError());
+  em2d_fp64_bhalf(h->ce, b.B, b.E, b.Bp, h->lg, h->st);
+  CUDA_TRY(cudaMemsetAsync(b.J1, 0, sizeof(double) * nc3, h->st));
+  CUDA_TRY(cudaMemsetAsync(b.J2, 0, sizeof(double) * nc3, h->st));
+  if (h->ce.scheme == 2) em2d_fp64_deposit_initial(h->ce, b, h->lp, h->st);
+  CUDA_TRY(cudaGetLastError());
+  return check_flags(h, "pic_init/pic_set_*");
+}
+
+
+// 2D3V Yee: constants, SoA markers, fields E^0, B^{-1/2} and B^{1/2}, j^{0,*}.
+int init_em2d(pic_handle *h, const pic_species *species, const double *E0, const double *B0) {
+  const pic_config &cfg = h->cfg;
+  Em2dConst &c = h->ce;
+  Em2dBufs &b = h->be;
+  c.nx = (int)cfg.grid.n[0];
+  c.ny = (int)cfg.grid.n[1];
+  c.order = cfg.shape_order;
+  c.scheme = cfg.scheme;
+  c.gamma_on = cfg.gamma_on;
+  c.nsp = h->nsp;
+  c.n_total = h->N;
+  c.Lx = cfg.grid.L[0];
+  c.Ly = cfg.grid.L[1];
+  c.inv_hx = c.nx / c.Lx;
+  c.inv_hy = c.ny / c.Ly;
+  c.dt = cfg.dt;
+  c.c2 = cfg.c * cfg.c;
+  c.area = (c.Lx / c.nx) * (c.Ly / c.ny);
+  for (int s = 0; s < h->nsp; s++) {
+    const SpeciesInfo &S = h->sp[s];
+    c.sp_end[s] = S.offset + S.n;
+    c.qm[s] = S.q / S.m;
+    c.qw_a[s] = S.q * S.w0 / c.area;
+    c.q_a[s] = S.q / c.area;
+    c.half_mw[s] = 0.5 * S.m * S.w0;
+    c.half_m[s] = 0.5 * S.m;
+  }
+  for (int s = h->nsp; s < kMaxSpecies; s++) c.sp_end[s] = h->N;
+  const int64_t nc3 = 3 * (int64_t)c.nx * c.ny;
+  h->lp.block = 256;
+  h->lp.grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->N + 255) / 256, (int64_t)h->nsm * 4));
+  h->lg.block = 256;
+  h->lg.grid = (int)std::max<int64_t>(1, std::min<int64_t>((nc3 + 255) / 256, (int64_t)h->nsm * 4));
+  int rc;
+  if ((rc = h->alloc(&b.x, h->N)) || (rc = h->alloc(&b.y, h->N)) || (rc = h->alloc(&b.vx, h->N)) ||
+      (rc = h->alloc(&b.vy, h->N)) || (rc = h->alloc(&b.vz, h->N)))
+    return rc;
+  b.w = nullptr;
+  if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;
+  double **fields[] = {&b.E, &b.En, &b.Eh, &b.Es, &b.B, &b.Bp, &b.Bpp, &b.J1, &b.J2};
+  for (double **f : fields)
+    if ((rc = h->alloc(f, nc3))) return rc;
+  if ((rc = h->alloc(&b.ke_part, (size_t)h->lp.grid * kMaxSpecies)) ||
+      (rc = h->alloc(&b.wf_part, 2 * (size_t)h->lg.grid)) || (rc = h->alloc(&b.fallback, kStepsCap)) ||
+      (rc = h->alloc(&b.te, kStepsCap)) || (rc = h->alloc(&b.err, 1)) ||
+      (rc = h->alloc(&h->ids, h->N)))
+    return rc;
+  // the 1D bookkeeping fields shared by the step/stats/error paths
+  h->b1.err = b.err;
+  h->b1.fallback = b.fallback;
+  h->b1.te = b.te;
+  CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(unsigned), h->st));
+  for (int s = 0; s < h->nsp; s++) {
+    const SpeciesInfo &S = h->sp[s];
+    const pic_species &in = species[s];
+    double *dst[5] = {b.x, b.y, b.vx, b.vy, b.vz};
+    for (int d = 0; d < 2; d++)
+      CUDA_TRY(cudaMemcpyAsync(dst[d] + S.offset, in.x + d * S.n, sizeof(double) * S.n,
+                               cudaMemcpyDefault, h->st));
+    for (int d = 0; d < 3; d++)
+      CUDA_TRY(cudaMemcpyAsync(dst[2 + d] + S.offset, in.v + d * S.n, sizeof(double) * S.n,
+                               cudaMemcpyDefault, h->st));
+    if (h->weighted) {
+      if (in.w) {
+        CUDA_TRY(cudaMemcpyAsync(b.w + S.offset, in.w, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+      } else {
+        std::vector<double> tmp((size_t)S.n, S.w0);
+        CUDA_TRY(cudaMemcpyAsync(b.w + S.offset, tmp.data(), sizeof(double) * S.n,
+                                 cudaMemcpyHostToDevice, h->st));
+        CUDA_TRY(cudaStreamSynchronize(h->st));
+      }
+    }
+  }
+  std::vector<int64_t> ids((size_t)h->N);
+  for (int s = 0; s < h->nsp; s++)
+    for (int64_t p = 0; p < h->sp[s].n; p++) ids[(size_t)(h->sp[s].offset + p)] = p;
+  CUDA_TRY(cudaMemcpyAsync(h->ids, ids.data(), sizeof(int64_t) * h->N, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(cudaMemsetAsync(b.E, 0, sizeof(double) * nc3, h->st));
+  CUDA_TRY(cudaMemsetAsync(b.B, 0, sizeof(double) * nc3, h->st));
+  if (E0) CUDA_TRY(cudaMemcpyAsync(b.E, E0, sizeof(double) * nc3, cudaMemcpyDefault, h->st));
+  if (B0) CUDA_TRY(cudaMemcpyAsync(b.B, B0, sizeof(double) * nc3, cudaMemcpyDefault, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return restart_em2d(h);
+}
+
 }  // namespace
 
 extern "C" {
@@ -467,7 +574,14 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
     if (!(cfg->grid.L[0] > 0.0)) return fail(PIC_ERR_ARG, "pic_init: L must be > 0");
     if (B0) return fail(PIC_ERR_ARG, "pic_init: B0 given for the electrostatic solver");
   } else if (cfg->solver == PIC_SOLVER_YEE_LEAPFROG) {
-    return fail(PIC_ERR_UNSUPPORTED, "pic_init: Yee solver not built in this library version");
+    if (cfg->grid.dim_x != 2 || cfg->grid.dim_v != 3)
+      return fail(PIC_ERR_ARG, "pic_init: the Yee solver runs 2D3V (dim_x = 2, dim_v = 3)");
+    if (cfg->grid.n[0] < 4 || cfg->grid.n[1] < 4 || cfg->grid.n[0] > 8192 || cfg->grid.n[1] > 8192)
+      return fail(PIC_ERR_ARG, "pic_init: Yee grid needs 4..8192 nodes per dimension");
+    if (!(cfg->grid.L[0] > 0.0) || !(cfg->grid.L[1] > 0.0) || !(cfg->c > 0.0))
+      return fail(PIC_ERR_ARG, "pic_init: Yee solver needs L > 0 and c > 0");
+    if (cfg->precision == PIC_PREC_MIXED)
+      return fail(PIC_ERR_UNSUPPORTED, "pic_init: the Yee solver runs in the FP64 form");
   } else {
     return fail(PIC_ERR_ARG, "pic_init: unknown solver");
   }
@@ -510,7 +624,9 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
   h->ls.block = 512;
   h->ls.grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 2));
   h->nsm = nsm;
-  int rc = init_es1d(h, species, E0);
+  h->nsm = nsm;
+  h->em = cfg->solver == PIC_SOLVER_YEE_LEAPFROG;
+  int rc = h->em ? init_em2d(h, species, E0, B0) : init_es1d(h, species, E0);
   if (rc) {
     std::string msg = g_last_error;
     delete h;
@@ -531,7 +647,25 @@ int pic_step_async(pic_handle *h, int nsteps) {
   if (h->pending == 0 && nsteps > 0) {
     CUDA_TRY(cudaMemsetAsync(b.fallback, 0, sizeof(unsigned long long) * kStepsCap, h->st));
   }
-  for (int k = 0; k < nsteps; k++) {
+  for (int k = 0; k < nsteps && h->em; k++) {
+    Em2dBufs &e = h->be;
+    const int slot = h->pending;
+    CUDA_TRY(h->timed_launch(4, [&] { em2d_k1(h->ce, e, h->lg, h->st); }));
+    CUDA_TRY(h->timed_launch(0, [&] { em2d_pass_c(h->ce, e, h->lp, h->st); }));
+    CUDA_TRY(h->timed_launch(4, [&] { em2d_k3(h->ce, e, h->lg, h->st); }));
+    CUDA_TRY(h->timed_launch(1, [&] { em2d_pass_e(h->ce, e, slot, h->lp, h->st); }));
+    CUDA_TRY(h->timed_launch(4, [&] { em2d_k5(h->ce, e, h->lg, h->st); }));
+    CUDA_TRY(h->timed_launch(2, [&] { em2d_finalize(h->ce, e, slot, h->lp, h->lg, h->st); }));
+    h->launches += 6;
+    std::swap(e.E, e.En);
+    double *old = e.B;
+    e.B = e.Bp;
+    e.Bp = e.Bpp;
+    e.Bpp = old;
+    h->steps_done++;
+    h->pending++;
+  }
+  for (int k = 0; k < nsteps && !h->em; k++) {
     if (h->mixed) {
       if (h->cfg.sort_period > 0 && h->steps_done > 0 && h->steps_done % h->cfg.sort_period == 0) {
         int rc = sort_mixed(h);
@@ -567,13 +701,15 @@ int pic_read_stats(pic_handle *h, int capacity, int64_t *nfallback_per_step, dou
   if ((nfallback_per_step || te_per_step) && capacity < n)
     return fail(PIC_ERR_ARG, "pic_read_stats: %d steps pending, capacity %d", n, capacity);
   Es1dFp64Bufs &b = h->b1;
-  CUDA_TRY(h->timed_launch(2, [&] {
-    if (h->mixed)
-      es1d_mix_finalize(h->bm, n - 1, h->ls.grid, h->st);
-    else
-      es1d_fp64_finalize(h->c1, b, n - 1, h->ls.grid, h->st);
-  }));
-  h->launches += 1;
+  if (!h->em) {
+    CUDA_TRY(h->timed_launch(2, [&] {
+      if (h->mixed)
+        es1d_mix_finalize(h->bm, n - 1, h->ls.grid, h->st);
+      else
+        es1d_fp64_finalize(h->c1, b, n - 1, h->ls.grid, h->st);
+    }));
+    h->launches += 1;
+  }
   std::vector<unsigned long long> fb(n);
   std::vector<double> te(n);
   CUDA_TRY(cudaMemcpyAsync(fb.data(), b.fallback, sizeof(unsigned long long) * n,
@@ -636,8 +772,45 @@ int pic_launch_count(pic_handle *h, int64_t *launches) {
   return PIC_OK;
 }
 
+static int energy_em2d(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, double *TE) {
+  const Em2dConst &c = h->ce;
+  Em2dBufs &b = h->be;
+  const int nb = h->lp.grid;
+  em2d_fp64_kinetic(c, b, b.ke_part, nb, h->st);
+  CUDA_TRY(cudaGetLastError());
+  const size_t nc3 = 3 * (size_t)c.nx * c.ny;
+  std::vector<double> part((size_t)nb * h->nsp), e(nc3), bo(nc3), bp(nc3);
+  CUDA_TRY(cudaMemcpyAsync(part.data(), b.ke_part, sizeof(double) * part.size(),
+                           cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaMemcpyAsync(e.data(), b.E, sizeof(double) * nc3, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaMemcpyAsync(bo.data(), b.B, sizeof(double) * nc3, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaMemcpyAsync(bp.data(), b.Bp, sizeof(double) * nc3, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  double te = 0.0;
+  for (int s = 0; s < h->nsp; s++) {
+    double k = 0.0;
+    for (int i = 0; i < nb; i++) k += part[(size_t)s * nb + i];
+    if (KE_per_species) KE_per_species[s] = k;
+    te += k;
+  }
+  double we = 0.0, wb = 0.0;
+  for (size_t a = 0; a < nc3; a++) {
+    we += e[a] * e[a];
+    wb += bp[a] * bo[a];
+  }
+  we *= 0.5 * c.area;
+  wb *= 0.5 * c.c2 * c.area;  // W_B^n = (c^2/2)|h| sum B^{n+1/2} . B^{n-1/2}
+  te += we + wb;
+  if (W_E) *W_E = we;
+  if (W_B) *W_B = wb;
+  if (TE) *TE = te;
+  if (!std::isfinite(te)) return fail(PIC_ERR_NONFINITE, "pic_energy: non-finite energy");
+  return PIC_OK;
+}
+
 int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, double *TE) {
   if (!h) return fail(PIC_ERR_ARG, "pic_energy: NULL handle");
+  if (h->em) return energy_em2d(h, KE_per_species, W_E, W_B, TE);
   const Es1dConst &c = h->c1;
   double *ke_d = h->b1.ke_part;  // reuse: nsp <= grid entries are needed
   if (h->ls.grid < h->nsp) return fail(PIC_ERR_ARG, "pic_energy: internal size");
@@ -679,6 +852,17 @@ int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, 
 int pic_get_particles(pic_handle *h, int s, double *x, double *v) {
   if (!h || s < 0 || s >= h->nsp) return fail(PIC_ERR_ARG, "pic_get_particles: bad handle or species");
   const SpeciesInfo &S = h->sp[s];
+  if (h->em) {
+    const double *src[5] = {h->be.x, h->be.y, h->be.vx, h->be.vy, h->be.vz};
+    for (int d = 0; d < 2 && x; d++)
+      CUDA_TRY(cudaMemcpyAsync(x + d * S.n, src[d] + S.offset, sizeof(double) * S.n,
+                               cudaMemcpyDefault, h->st));
+    for (int d = 0; d < 3 && v; d++)
+      CUDA_TRY(cudaMemcpyAsync(v + d * S.n, src[2 + d] + S.offset, sizeof(double) * S.n,
+                               cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    return PIC_OK;
+  }
   if (h->mixed) {
     es1d_mix_to_fp64(h->cm, h->bm, h->b1.x, h->b1.v, h->ls, h->st);
     CUDA_TRY(cudaGetLastError());
@@ -700,6 +884,21 @@ int pic_get_ids(pic_handle *h, int s, int64_t *ids) {
 int pic_set_particles(pic_handle *h, int s, const double *x, const double *v) {
   if (!h || s < 0 || s >= h->nsp || !x || !v) return fail(PIC_ERR_ARG, "pic_set_particles: bad arguments");
   const SpeciesInfo &S = h->sp[s];
+  if (h->em) {
+    double *dst[5] = {h->be.x, h->be.y, h->be.vx, h->be.vy, h->be.vz};
+    for (int d = 0; d < 2; d++)
+      CUDA_TRY(cudaMemcpyAsync(dst[d] + S.offset, x + d * S.n, sizeof(double) * S.n,
+                               cudaMemcpyDefault, h->st));
+    for (int d = 0; d < 3; d++)
+      CUDA_TRY(cudaMemcpyAsync(dst[2 + d] + S.offset, v + d * S.n, sizeof(double) * S.n,
+                               cudaMemcpyDefault, h->st));
+    std::vector<int64_t> ids((size_t)S.n);
+    for (int64_t p = 0; p < S.n; p++) ids[(size_t)p] = p;
+    CUDA_TRY(cudaMemcpyAsync(h->ids + S.offset, ids.data(), sizeof(int64_t) * S.n,
+                             cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    return restart_em2d(h);
+  }
   CUDA_TRY(cudaMemcpyAsync(h->b1.x + S.offset, x, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
   CUDA_TRY(cudaMemcpyAsync(h->b1.v + S.offset, v, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
   std::vector<int64_t> ids((size_t)S.n);
@@ -712,6 +911,13 @@ int pic_set_particles(pic_handle *h, int s, const double *x, const double *v) {
 
 int pic_get_fields(pic_handle *h, double *E, double *B) {
   if (!h) return fail(PIC_ERR_ARG, "pic_get_fields: NULL handle");
+  if (h->em) {
+    const size_t nc3 = 3 * (size_t)h->ce.nx * h->ce.ny;
+    if (E) CUDA_TRY(cudaMemcpyAsync(E, h->be.E, sizeof(double) * nc3, cudaMemcpyDefault, h->st));
+    if (B) CUDA_TRY(cudaMemcpyAsync(B, h->be.B, sizeof(double) * nc3, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    return PIC_OK;
+  }
   (void)B;
   if (E)
     CUDA_TRY(cudaMemcpyAsync(E, h->b1.E[h->steps_done & 1], sizeof(double) * h->c1.nc,
@@ -722,6 +928,14 @@ int pic_get_fields(pic_handle *h, double *E, double *B) {
 
 int pic_set_fields(pic_handle *h, const double *E, const double *B) {
   if (!h || !E) return fail(PIC_ERR_ARG, "pic_set_fields: bad arguments");
+  if (h->em) {
+    if (!B) return fail(PIC_ERR_ARG, "pic_set_fields: the Yee solver needs B^{n-1/2}");
+    const size_t nc3 = 3 * (size_t)h->ce.nx * h->ce.ny;
+    CUDA_TRY(cudaMemcpyAsync(h->be.E, E, sizeof(double) * nc3, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaMemcpyAsync(h->be.B, B, sizeof(double) * nc3, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    return restart_em2d(h);
+  }
   if (B) return fail(PIC_ERR_ARG, "pic_set_fields: B given for the electrostatic solver");
   CUDA_TRY(cudaMemcpyAsync(h->b1.E[h->steps_done & 1], E, sizeof(double) * h->c1.nc,
                            cudaMemcpyDefault, h->st));

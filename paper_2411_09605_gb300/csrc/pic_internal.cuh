@@ -78,6 +78,41 @@ struct Es1dMixBufs {
   unsigned *err;
 };
 
+// Per-launch constants of the 2D3V Yee kernels (FP64 form).
+struct Em2dConst {
+  int nx, ny;
+  int order;
+  int scheme;
+  int gamma_on;
+  int nsp;
+  int64_t n_total;
+  double Lx, Ly, inv_hx, inv_hy, dt, c2, area;
+  int64_t sp_end[kMaxSpecies];
+  double qm[kMaxSpecies];
+  double qw_a[kMaxSpecies];     // q w0 / |h|
+  double q_a[kMaxSpecies];      // q / |h| (weighted markers)
+  double half_mw[kMaxSpecies];
+  double half_m[kMaxSpecies];
+};
+
+struct Em2dBufs {
+  double *x, *y, *vx, *vy, *vz, *w;   // [N] SoA (w may be null)
+  double *E;      // E^n            [3][ny][nx]
+  double *En;     // E^{n+1}
+  double *Eh;     // E^{n+1/2}
+  double *Es;     // E*
+  double *B;      // B^{n-1/2}
+  double *Bp;     // B^{n+1/2}
+  double *Bpp;    // B^{n+3/2} (computed at the end of a step)
+  double *J1;     // j^{n,*}
+  double *J2;     // j^{*,n+1/2}
+  double *ke_part;             // [particle blocks]
+  double *wf_part;             // [2 x grid blocks] W_E, W_B partials
+  unsigned long long *fallback;
+  double *te;
+  unsigned *err;
+};
+
 // Everything the 1D FP64 kernels touch.
 struct Es1dFp64Bufs {
   double *x, *v, *w;        // [N] SoA (w may be null)
@@ -113,6 +148,24 @@ void es1d_fp64_charge(const Es1dConst &c, const double *x, const double *w, doub
                       LaunchShape ls, cudaStream_t st);
 void es1d_fp64_kinetic(const Es1dConst &c, const double *v, const double *w, double *ke_sp,
                        cudaStream_t st);
+
+// 2D3V Yee path (em2d_fp64.cu)
+void em2d_k1(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st);
+void em2d_pass_c(const Em2dConst &c, const Em2dBufs &b, LaunchShape lp, cudaStream_t st);
+void em2d_k3(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st);
+void em2d_pass_e(const Em2dConst &c, const Em2dBufs &b, int slot, LaunchShape lp, cudaStream_t st);
+void em2d_k5(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st);
+void em2d_finalize(const Em2dConst &c, const Em2dBufs &b, int slot, LaunchShape lp,
+                   LaunchShape lg, cudaStream_t st);
+void em2d_fp64_deposit_initial(const Em2dConst &c, const Em2dBufs &b, LaunchShape lp,
+                               cudaStream_t st);
+void em2d_fp64_bhalf(const Em2dConst &c, const double *B, const double *E, double *Bp,
+                     LaunchShape lg, cudaStream_t st);
+void em2d_fp64_kinetic(const Em2dConst &c, const Em2dBufs &b, double *out, int nblocks,
+                       cudaStream_t st);
+__global__ void em2d_validate_kernel(const double *x, const double *y, const double *vx,
+                                     const double *vy, const double *vz, int64_t n, double Lx,
+                                     double Ly, unsigned *err);
 
 // 1D mixed path (es1d_mixed.cu)
 cudaError_t es1d_mix_prepare(const Es1dMixConst &c);

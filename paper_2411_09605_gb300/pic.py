@@ -272,3 +272,55 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+class Simulation2D:
+    """Owner of one Yee-solver handle built from a ``workloads.Problem2D``."""
+
+    def __init__(self, prob, scheme=PIC_SCHEME_ESEC2, E0=None, B0=None, gamma_on=True):
+        self.prob = prob
+        self.cfg = make_config(prob.nx, prob.Lx, prob.dt, prob.order, scheme, PIC_PREC_FP64,
+                               solver=PIC_SOLVER_YEE_LEAPFROG, dim_x=2, dim_v=3, ny=prob.ny,
+                               Ly=prob.Ly, c=prob.c, gamma_on=gamma_on)
+        self.species = []
+        for s in prob.species:
+            x = np.ascontiguousarray(np.stack([s.x, s.y]), dtype=np.float64)
+            v = np.ascontiguousarray(np.stack([s.vx, s.vy, s.vz]), dtype=np.float64)
+            self.species.append(dict(q=s.q, m=s.m, x=x, v=v, n=len(s.x),
+                                     w=None if s.w is None else np.ascontiguousarray(s.w),
+                                     w0=s.w0))
+        self.h = pic_init(self.cfg, self.species,
+                          None if E0 is None else np.ascontiguousarray(E0, dtype=np.float64),
+                          None if B0 is None else np.ascontiguousarray(B0, dtype=np.float64))
+
+    def step(self, nsteps: int):
+        fb = np.zeros(nsteps, dtype=np.int64)
+        te = np.zeros(nsteps)
+        pic_step(self.h, nsteps, fb, te)
+        return fb, te
+
+    def particles(self, s: int = 0):
+        n = self.species[s]["n"]
+        x, v = np.zeros((2, n)), np.zeros((3, n))
+        pic_get_particles(self.h, s, x, v)
+        return x, v
+
+    def fields(self):
+        shape = (3, self.prob.ny, self.prob.nx)
+        E, B = np.zeros(shape), np.zeros(shape)
+        pic_get_fields(self.h, E, B)
+        return E, B
+
+    def energy(self):
+        return pic_energy(self.h, len(self.species))
+
+    def close(self):
+        if self.h:
+            pic_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
