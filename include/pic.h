@@ -101,12 +101,17 @@ typedef struct {
   pic_solver solver;
   pic_scheme scheme;
   pic_precision precision;
-  int sort_period;          /* cell-sort the markers every sort_period steps  */
-                            /* (0 = never; sorting only reorders markers)     */
+  int sort_period;          /* mixed form: 0 = markers never reordered;       */
+                            /* 1 = kept sorted by (cell, sign of v) every     */
+                            /* step, written in key order by the update pass; */
+                            /* P > 1 = counting sort by cell every P steps.   */
+                            /* Sorting only reorders markers.                 */
   int remove_mean;          /* ES: 1 -> E -= dt (J - <J>), 0 -> E -= dt J     */
   int gamma_on;             /* 1 = energy correction; 0 = naive scheme        */
   int ptr_on_device;        /* see Conventions                                */
   void *cuda_stream;        /* cudaStream_t or NULL                           */
+  int skip_ids;             /* 1: do not carry marker ids through sorts       */
+                            /* (pic_get_ids then fails); 0: keep them         */
 } pic_config;
 
 typedef struct pic_handle pic_handle;

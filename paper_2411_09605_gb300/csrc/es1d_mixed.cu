@@ -123,43 +123,116 @@ __device__ __forceinline__ int to_fixed(float y, unsigned *err) {
 // 20 bits and the signed rest sum over 32 lanes without overflow), then one
 // lane adds the sum; warps spread over more than 8 cells fall back to per-lane
 // atomics.
-template <int ORDER, bool AGG>
-__device__ __forceinline__ void deposit(long long *Jt, const ShapeMix<ORDER> &S, int V, int r,
-                                        bool valid) {
-  if (!AGG) {
-    if (valid) {
+// The block tile holds each node's integer current as two 32-bit counters:
+// the low 16 bits of every added amount (unsigned) and the rest (signed).  An
+// amount A is added exactly as (A & 0xFFFF, A >> 16); the tile value is
+// hi 2^16 + lo.  Two 32-bit shared atomics run about 2.7 times faster than one
+// 64-bit atomic on random addresses, and the rounding shift r is chosen so that
+// neither counter can overflow for the markers a block processes.
+__device__ __forceinline__ void tile_add(unsigned *Jt, int node, long long a) {
+  atomicAdd(&Jt[2 * node], (unsigned)(a & 0xFFFF));
+  atomicAdd(&Jt[2 * node + 1], (unsigned)(int)(a >> 16));
+}
+
+// Direct deposit: one split atomic per node (markers in arbitrary order spread
+// over the tile's banks).
+template <int ORDER>
+__device__ __forceinline__ void deposit_direct(unsigned *Jt, const ShapeMix<ORDER> &S, int V,
+                                               int r) {
 #pragma unroll
-      for (int k = 0; k <= ORDER; k++)
-        atomicAdd((unsigned long long *)&Jt[S.idx[k]],
-                  (unsigned long long)deposit_term(V, S.s[k], r));
-    }
-    return;
+  for (int k = 0; k <= ORDER; k++) tile_add(Jt, S.idx[k], deposit_term(V, S.s[k], r));
+}
+
+// Deposit window for cell-sorted markers: a thread adds the terms of its four
+// markers into kWin consecutive nodes starting at the first node of base cell
+// `base` (one below the warp's smallest first key), then the warp sums each
+// node over its 32
+// lanes (two 32-bit halves: 4 terms of |t| < 2^37 per lane, so the low 20
+// bits and the signed rest sum without overflow) and one lane adds the 128
+// markers' total with a single shared atomic per node.  Markers whose base
+// cell falls outside the window use direct atomics.
+constexpr int kWin = 6;
+
+template <int ORDER>
+struct DepositWindow {
+  long long acc[kWin];
+  int base;
+  // The window starts one cell below the smallest base cell among the warp's
+  // first markers (the other three per lane usually fall within two cells).
+  __device__ __forceinline__ void start(int key, bool valid) {
+#pragma unroll
+    for (int w = 0; w < kWin; w++) acc[w] = 0;
+    const int m = __reduce_min_sync(0xffffffffu, valid ? key : 0x7fffffff);
+    base = m == 0x7fffffff ? 0 : m - 1;
   }
+  __device__ __forceinline__ void add(unsigned *Jt, const ShapeMix<ORDER> &S, int V, int r,
+                                      bool valid) {
+    if (!valid) return;
+    const int off = S.key - base;
+    const bool inwin = off >= 0 && off <= kWin - 1 - ORDER;
+    long long t[ORDER + 1];
+#pragma unroll
+    for (int k = 0; k <= ORDER; k++) t[k] = deposit_term(V, S.s[k], r);
+    if (inwin) {
+#pragma unroll
+      for (int w = 0; w < kWin; w++) {
+        long long a = 0;
+#pragma unroll
+        for (int k = 0; k <= ORDER; k++) a = (w - k == off) ? t[k] : a;
+        acc[w] += a;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k <= ORDER; k++) tile_add(Jt, S.idx[k], t[k]);
+    }
+  }
+  __device__ __forceinline__ void flush(unsigned *Jt, int nc) {
+    int first = (ORDER == 2 ? base - 1 : base) % nc;
+    if (first < 0) first += nc;
+    const bool lead = (threadIdx.x & 31u) == 0u;
+#pragma unroll
+    for (int w = 0; w < kWin; w++) {
+      if (__any_sync(0xffffffffu, acc[w] != 0)) {
+        const int hs = __reduce_add_sync(0xffffffffu, (int)(acc[w] >> 20));
+        const int ls = __reduce_add_sync(0xffffffffu, (int)(acc[w] & 0xFFFFF));
+        if (lead) {
+          int node = first + w;
+          if (node >= nc) node -= nc;
+          tile_add(Jt, node, ((long long)hs << 20) + (long long)ls);
+        }
+      }
+    }
+  }
+};
+
+__device__ void block_exclusive_scan(const uint32_t *T, uint32_t *base, int nc, uint32_t *tmp);
+
+// Sort key of a marker after the step: its cell and the sign of its velocity
+// (counter-streaming markers of one cell then sit in separate runs).
+__device__ __forceinline__ int sort_key(uint32_t X, int V, int nc) {
+  return 2 * cell_of(X, nc) + (V > 0 ? 1 : 0);
+}
+
+// Warp-aggregated increment of a shared counter array: returns this lane's
+// slot (the counter's old value plus the lane's rank among the warp's lanes
+// with the same key).  Cell-sorted markers give one or a few distinct keys
+// per warp; each distinct key costs one ballot, two shuffles and one atomic.
+__device__ __forceinline__ uint32_t warp_rank(uint32_t *cnt, int key, bool valid) {
   const unsigned lane = threadIdx.x & 31u;
-  const int key = valid ? S.key : -1;
-  const unsigned peers = __match_any_sync(0xffffffffu, key);
-  const int leader = __ffs(peers) - 1;
-  const int ngroups = __popc(__ballot_sync(0xffffffffu, valid && (int)lane == leader));
-  if (ngroups > 8) {
-    if (valid) {
-#pragma unroll
-      for (int k = 0; k <= ORDER; k++)
-        atomicAdd((unsigned long long *)&Jt[S.idx[k]],
-                  (unsigned long long)deposit_term(V, S.s[k], r));
-    }
-    return;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned todo = __ballot_sync(0xffffffffu, valid);
+  uint32_t mine = 0;
+  while (todo) {
+    const int leader = __ffs(todo) - 1;
+    const int kk = __shfl_sync(0xffffffffu, key, leader);
+    const unsigned grp = __ballot_sync(0xffffffffu, ((todo >> lane) & 1u) && key == kk);
+    uint32_t first = 0;
+    if ((int)lane == leader) first = atomicAdd(&cnt[kk], (uint32_t)__popc(grp));
+    first = __shfl_sync(0xffffffffu, first, leader);
+    if ((grp >> lane) & 1u) mine = first + (uint32_t)__popc(grp & lt);
+    todo &= ~grp;
   }
-  if (valid) {
-#pragma unroll
-    for (int k = 0; k <= ORDER; k++) {
-      const long long t = deposit_term(V, S.s[k], r);
-      const int hs = __reduce_add_sync(peers, (int)(t >> 20));
-      const int ls = __reduce_add_sync(peers, (int)(t & 0xFFFFF));
-      if ((int)lane == leader)
-        atomicAdd((unsigned long long *)&Jt[S.idx[k]],
-                  (unsigned long long)(((long long)hs << 20) + (long long)ls));
-    }
-  }
+  return mine;
 }
 
 __device__ __forceinline__ double block_sum_d(double s, double *red) {
@@ -196,6 +269,13 @@ __device__ __forceinline__ void build_estar_mix(const Es1dMixConst &c, const dou
       Es[i] = (float)(E[i] - hdt * ((double)J1[i] * c.jscale - mean));
   } else {
     for (int i = threadIdx.x; i < c.nc; i += blockDim.x) Es[i] = (float)E[i];
+  }
+}
+
+__device__ __forceinline__ void flush_tile_split(const unsigned *Jt, long long *J, int nc) {
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const long long a = (long long)(int)Jt[2 * i + 1] * 65536ll + (long long)Jt[2 * i];
+    if (a != 0) atomicAdd((unsigned long long *)&J[i], (unsigned long long)a);
   }
 }
 
@@ -238,15 +318,19 @@ __device__ __forceinline__ int vstar_fixed(float vh, float vl, float e, unsigned
 
 // pass C: x*, E**_p (FP32), v* as the integer V* (stored for pass E),
 // x^{n+1/2} and the exact deposit of j^{*,n+1/2}.
-template <int ORDER, int SCHEME, bool AGG>
+template <int ORDER, int SCHEME, int MODE>
 __global__ void __launch_bounds__(512) mix_pass_c_kernel(Es1dMixConst c, Es1dMixBufs b, int par,
                                                          int prev_slot, int prev_nblocks) {
+  constexpr bool AGG = MODE > 0;
   extern __shared__ __align__(16) unsigned char smraw[];
-  long long *Jt = (long long *)smraw;
-  float *Es = (float *)(Jt + c.nc);
+  unsigned *Jt = (unsigned *)smraw;           // split tile: 2 counters per node
+  float *Es = (float *)(Jt + 2 * c.nc);
+  uint32_t *hist = (uint32_t *)(Es + c.nc);   // MODE 2: keys of the markers after the step
   __shared__ double red[33];
   build_estar_mix<SCHEME>(c, PSEL(b.E, par), PSEL(b.J1, par), Es, red);
-  for (int i = threadIdx.x; i < c.nc; i += blockDim.x) Jt[i] = 0;
+  for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x) Jt[i] = 0;
+  if (MODE == 2)
+    for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x) hist[i] = 0;
   if (blockIdx.x == 0) {
     if (SCHEME == 2)
       for (int i = threadIdx.x; i < c.nc; i += blockDim.x) PSEL(b.J1, par ^ 1)[i] = 0;
@@ -267,6 +351,7 @@ __global__ void __launch_bounds__(512) mix_pass_c_kernel(Es1dMixConst c, Es1dMix
       l4 = reinterpret_cast<const float4 *>(b.vl)[g];
     }
     int Vout[4];
+    DepositWindow<ORDER> win;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
       const uint32_t X = j == 0 ? X4.x : j == 1 ? X4.y : j == 2 ? X4.z : X4.w;
@@ -279,26 +364,45 @@ __global__ void __launch_bounds__(512) mix_pass_c_kernel(Es1dMixConst c, Es1dMix
 #pragma unroll
       for (int k = 0; k <= ORDER; k++) e = __fmaf_rn(Sx.w[k], Es[Sx.idx[k]], e);
       const int Vs = vstar_fixed(vh, vl, __fmul_rn(c.e_scale, e), b.err);
-      const ShapeMix<ORDER> Sh(X + half_shift(Vs, c.kv), c.nc);
-      deposit<ORDER, AGG>(Jt, Sh, Vs, c.rshift, valid);
+      const uint32_t hs = half_shift(Vs, c.kv);
+      const ShapeMix<ORDER> Sh(X + hs, c.nc);
+      if (AGG) {
+        if (j == 0) win.start(Sh.key, valid);
+        win.add(Jt, Sh, Vs, c.rshift, valid);
+      } else if (valid) {
+        deposit_direct<ORDER>(Jt, Sh, Vs, c.rshift);
+      }
+      if (MODE == 2) warp_rank(hist, sort_key(X + 2u * hs, Vs, c.nc), valid);
       Vout[j] = Vs;
     }
+    if (AGG) win.flush(Jt, c.nc);
     if (gv) reinterpret_cast<int4 *>(b.Vs)[g] = make_int4(Vout[0], Vout[1], Vout[2], Vout[3]);
   }
   __syncthreads();
-  flush_tile_i64(Jt, PSEL(b.J2, par), c.nc);
+  flush_tile_split(Jt, PSEL(b.J2, par), c.nc);
+  if (MODE == 2)
+    for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x)
+      b.H[(int64_t)i * gridDim.x + blockIdx.x] = hist[i];
 }
 
 // pass E: E^{n+1}, E^{n+1/2} (float pairs) in the prologue; per marker the
 // gather at x^{n+1/2} = X + [V*], v^dag, Gamma, x^{n+1}, v^{n+1}, the kinetic
 // energy and (ESEC2) the next step's x* and j^{n+1,*} deposit.
-template <int ORDER, int SCHEME, bool AGG>
+template <int ORDER, int SCHEME, int MODE>
 __global__ void __launch_bounds__(512) mix_pass_e_kernel(Es1dMixConst c, Es1dMixBufs b, int par,
                                                          int slot) {
+  constexpr bool AGG = MODE > 0;
   extern __shared__ __align__(16) unsigned char smraw[];
-  long long *Jt = (long long *)smraw;
-  float2 *Eh2 = (float2 *)(Jt + c.nc);
+  unsigned *Jt = (unsigned *)smraw;           // split tile: 2 counters per node
+  float2 *Eh2 = (float2 *)(Jt + 2 * c.nc);
+  uint32_t *off = (uint32_t *)(Eh2 + c.nc);   // MODE 2: next free slot of each key
   __shared__ double red[33];
+  if (MODE == 2) {
+    __shared__ uint32_t tmp[512];
+    block_exclusive_scan(b.T, off, 2 * c.nc, tmp);
+    for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x)
+      off[i] += b.H[(int64_t)i * gridDim.x + blockIdx.x];
+  }
   const double *E = PSEL(b.E, par);
   const long long *J2 = PSEL(b.J2, par);
   double mean2 = c.remove_mean ? block_mean_j(J2, c.nc, c.jscale, red) : 0.0;
@@ -307,7 +411,8 @@ __global__ void __launch_bounds__(512) mix_pass_e_kernel(Es1dMixConst c, Es1dMix
     double en = E[i] - c.dt * ((double)J2[i] * c.jscale - mean2);
     ff s = ff_from_double(0.5 * (E[i] + en));
     Eh2[i] = make_float2(s.hi, s.lo);
-    Jt[i] = 0;
+    Jt[2 * i] = 0;
+    Jt[2 * i + 1] = 0;
     if (blockIdx.x == 0) {
       PSEL(b.E, par ^ 1)[i] = en;
       PSEL(b.J2, par ^ 1)[i] = 0;
@@ -339,6 +444,7 @@ __global__ void __launch_bounds__(512) mix_pass_e_kernel(Es1dMixConst c, Es1dMix
     }
     uint32_t Xo[4];
     float ho[4], lo[4];
+    DepositWindow<ORDER> win;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
       const uint32_t X = j == 0 ? X4.x : j == 1 ? X4.y : j == 2 ? X4.z : X4.w;
@@ -411,13 +517,29 @@ __global__ void __launch_bounds__(512) mix_pass_e_kernel(Es1dMixConst c, Es1dMix
       if (SCHEME == 2) {
         const int Vn1 = to_fixed(vn.hi, b.err);
         const ShapeMix<ORDER> S1(Xn + half_shift(Vn1, c.kv), c.nc);
-        deposit<ORDER, AGG>(Jt, S1, Vn1, c.rshift, valid);
+        if (AGG) {
+          if (j == 0) win.start(S1.key, valid);
+          win.add(Jt, S1, Vn1, c.rshift, valid);
+        } else if (valid) {
+          deposit_direct<ORDER>(Jt, S1, Vn1, c.rshift);
+        }
+      }
+      if (MODE == 2) {
+        // sort on write: the marker's slot in key order, from pass C's counts
+        const uint32_t dst = warp_rank(off, sort_key(Xn, Vs, c.nc), valid);
+        if (valid) {
+          b.Xo[dst] = Xn;
+          b.vho[dst] = vn.hi;
+          b.vlo[dst] = vn.lo;
+          if (b.ids) b.ido[dst] = b.ids[4 * g + j];
+        }
       }
       Xo[j] = valid ? Xn : X;
       ho[j] = valid ? vn.hi : vh;
       lo[j] = valid ? vn.lo : vl;
     }
-    if (gv) {
+    if (AGG && SCHEME == 2) win.flush(Jt, c.nc);
+    if (MODE != 2 && gv) {
       reinterpret_cast<uint4 *>(b.X)[g] = make_uint4(Xo[0], Xo[1], Xo[2], Xo[3]);
       reinterpret_cast<float4 *>(b.vh)[g] = make_float4(ho[0], ho[1], ho[2], ho[3]);
       reinterpret_cast<float4 *>(b.vl)[g] = make_float4(lo[0], lo[1], lo[2], lo[3]);
@@ -429,7 +551,7 @@ __global__ void __launch_bounds__(512) mix_pass_e_kernel(Es1dMixConst c, Es1dMix
   if (threadIdx.x == 0) b.ke_part[blockIdx.x] = c.ke_scale * t;
   if (SCHEME == 2) {
     __syncthreads();
-    flush_tile_i64(Jt, PSEL(b.J1, par ^ 1), c.nc);
+    flush_tile_split(Jt, PSEL(b.J1, par ^ 1), c.nc);
   }
 }
 
@@ -550,9 +672,7 @@ __global__ void __launch_bounds__(512) sort_count_kernel(const uint32_t *X, int6
     int64_t p = base + threadIdx.x;
     bool valid = p < end;
     int key = valid ? cell_of(X[p], nc) : -1;
-    unsigned peers = __match_any_sync(0xffffffffu, key);
-    if (valid && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
-      atomicAdd(&cnt[key], (uint32_t)__popc(peers));
+    warp_rank(cnt, key, valid);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nc; i += blockDim.x) H[(int64_t)i * gridDim.x + blockIdx.x] = cnt[i];
@@ -622,13 +742,8 @@ __global__ void __launch_bounds__(512) sort_move_kernel(Es1dMixBufs src, Es1dMix
     bool valid = p < end;
     uint32_t X = valid ? src.X[p] : 0u;
     int key = valid ? cell_of(X, nc) : -1;
-    unsigned peers = __match_any_sync(0xffffffffu, key);
-    int leader = __ffs(peers) - 1;
-    uint32_t first = 0;
-    if (valid && (int)lane == leader) first = atomicAdd(&off[key], (uint32_t)__popc(peers));
-    first = __shfl_sync(0xffffffffu, first, leader);
+    const uint32_t dest = warp_rank(off, key, valid);
     if (valid) {
-      uint32_t dest = first + (uint32_t)__popc(peers & ((1u << lane) - 1u));
       dst.X[dest] = X;
       dst.vh[dest] = src.vh[p];
       dst.vl[dest] = src.vl[p];
@@ -638,31 +753,37 @@ __global__ void __launch_bounds__(512) sort_move_kernel(Es1dMixBufs src, Es1dMix
 }
 
 template <typename F>
-void dispatch_mix(int order, int scheme, int agg, F f) {
+void dispatch_mix(int order, int scheme, int mode, F f) {
   using I1 = std::integral_constant<int, 1>;
   using I2 = std::integral_constant<int, 2>;
-  using B0 = std::integral_constant<bool, false>;
-  using B1 = std::integral_constant<bool, true>;
-  if (order == 1 && scheme == 1) agg ? f(I1(), I1(), B1()) : f(I1(), I1(), B0());
-  if (order == 1 && scheme == 2) agg ? f(I1(), I2(), B1()) : f(I1(), I2(), B0());
-  if (order == 2 && scheme == 1) agg ? f(I2(), I1(), B1()) : f(I2(), I1(), B0());
-  if (order == 2 && scheme == 2) agg ? f(I2(), I2(), B1()) : f(I2(), I2(), B0());
+  using M0 = std::integral_constant<int, 0>;
+  using M1 = std::integral_constant<int, 1>;
+  using M2 = std::integral_constant<int, 2>;
+  auto go = [&](auto O, auto S) {
+    if (mode == 0) f(O, S, M0());
+    if (mode == 1) f(O, S, M1());
+    if (mode == 2) f(O, S, M2());
+  };
+  if (order == 1 && scheme == 1) go(I1(), I1());
+  if (order == 1 && scheme == 2) go(I1(), I2());
+  if (order == 2 && scheme == 1) go(I2(), I1());
+  if (order == 2 && scheme == 2) go(I2(), I2());
 }
 
-size_t smem_c(const Es1dMixConst &c) { return (size_t)c.nc * (8 + 4); }
-size_t smem_e(const Es1dMixConst &c) { return (size_t)c.nc * (8 + 8); }
+size_t smem_c(const Es1dMixConst &c) { return (size_t)c.nc * (8 + 4 + (c.mode == 2 ? 8 : 0)); }
+size_t smem_e(const Es1dMixConst &c) { return (size_t)c.nc * (8 + 8 + (c.mode == 2 ? 8 : 0)); }
 
 }  // namespace
 
 cudaError_t es1d_mix_prepare(const Es1dMixConst &c) {
   cudaError_t e = cudaSuccess;
-  dispatch_mix(c.order, c.scheme, c.agg, [&](auto O, auto S, auto A) {
+  dispatch_mix(c.order, c.scheme, c.mode, [&](auto O, auto S, auto M) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
-    constexpr bool AGG = decltype(A)::value;
-    e = cudaFuncSetAttribute(mix_pass_c_kernel<ORDER, SCHEME, AGG>,
+    constexpr int MODE = decltype(M)::value;
+    e = cudaFuncSetAttribute(mix_pass_c_kernel<ORDER, SCHEME, MODE>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c(c));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mix_pass_e_kernel<ORDER, SCHEME, AGG>,
+      e = cudaFuncSetAttribute(mix_pass_e_kernel<ORDER, SCHEME, MODE>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e(c));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mix_deposit_initial_kernel<ORDER>,
@@ -677,21 +798,21 @@ cudaError_t es1d_mix_prepare(const Es1dMixConst &c) {
 void es1d_mix_pass_c(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_index, int slot,
                      LaunchShape ls, cudaStream_t st) {
   int par = (int)(step_index & 1);
-  dispatch_mix(c.order, c.scheme, c.agg, [&](auto O, auto S, auto A) {
+  dispatch_mix(c.order, c.scheme, c.mode, [&](auto O, auto S, auto M) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
-    constexpr bool AGG = decltype(A)::value;
-    mix_pass_c_kernel<ORDER, SCHEME, AGG><<<ls.grid, ls.block, smem_c(c), st>>>(c, b, par,
-                                                                                slot - 1, ls.grid);
+    constexpr int MODE = decltype(M)::value;
+    mix_pass_c_kernel<ORDER, SCHEME, MODE><<<ls.grid, ls.block, smem_c(c), st>>>(c, b, par,
+                                                                                 slot - 1, ls.grid);
   });
 }
 
 void es1d_mix_pass_e(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_index, int slot,
                      LaunchShape ls, cudaStream_t st) {
   int par = (int)(step_index & 1);
-  dispatch_mix(c.order, c.scheme, c.agg, [&](auto O, auto S, auto A) {
+  dispatch_mix(c.order, c.scheme, c.mode, [&](auto O, auto S, auto M) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
-    constexpr bool AGG = decltype(A)::value;
-    mix_pass_e_kernel<ORDER, SCHEME, AGG><<<ls.grid, ls.block, smem_e(c), st>>>(c, b, par, slot);
+    constexpr int MODE = decltype(M)::value;
+    mix_pass_e_kernel<ORDER, SCHEME, MODE><<<ls.grid, ls.block, smem_e(c), st>>>(c, b, par, slot);
   });
 }
 
@@ -733,6 +854,11 @@ void es1d_mix_kinetic(const Es1dMixConst &c, const Es1dMixBufs &b, double *part,
 void es1d_absmax(const double *v, int64_t n, unsigned long long *out, LaunchShape ls,
                  cudaStream_t st) {
   absmax_kernel<<<ls.grid, 256, 0, st>>>(v, n, out);
+}
+
+void es1d_mix_fused_scan(const Es1dMixConst &c, const Es1dMixBufs &b, int G, cudaStream_t st) {
+  const int nkeys = 2 * c.nc;
+  sort_cellscan_kernel<<<(nkeys * 32 + 255) / 256, 256, 0, st>>>(b.H, b.T, nkeys, G);
 }
 
 int es1d_mix_sort_blocks(const Es1dMixConst &c, int nsm) {

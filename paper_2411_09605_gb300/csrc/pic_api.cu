@@ -196,6 +196,8 @@ void poisson_1d_host(const std::vector<double> &rho, double L, std::vector<doubl
   }
 }
 
+void wire_sorted_output(pic_handle *h);
+
 // Cell-sorts the mixed-form markers (and their ids) into the alternate
 // buffers and swaps them in.
 int sort_mixed(pic_handle *h) {
@@ -208,7 +210,30 @@ int sort_mixed(pic_handle *h) {
   std::swap(h->bm.vh, h->bm_alt.vh);
   std::swap(h->bm.vl, h->bm_alt.vl);
   std::swap(h->ids, h->ids_alt);
+  wire_sorted_output(h);
   return PIC_OK;
+}
+
+// Sort on write: pass E writes into the alternate arrays, which are swapped in
+// after every step.
+void wire_sorted_output(pic_handle *h) {
+  Es1dMixBufs &bm = h->bm;
+  if (h->cm.mode != 2) return;
+  bm.Xo = h->bm_alt.X;
+  bm.vho = h->bm_alt.vh;
+  bm.vlo = h->bm_alt.vl;
+  bm.ids = h->cfg.skip_ids ? nullptr : h->ids;
+  bm.ido = h->cfg.skip_ids ? nullptr : h->ids_alt;
+}
+
+void swap_sorted_output(pic_handle *h) {
+  Es1dMixBufs &bm = h->bm;
+  std::swap(h->bm.X, h->bm_alt.X);
+  std::swap(h->bm.vh, h->bm_alt.vh);
+  std::swap(h->bm.vl, h->bm_alt.vl);
+  if (!h->cfg.skip_ids) std::swap(h->ids, h->ids_alt);
+  wire_sorted_output(h);
+  (void)bm;
 }
 
 // Mixed form: constants, integer/float-pair state converted from the FP64
@@ -245,13 +270,24 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   int kv = (int)std::floor(std::log2(1073741824.0 / (cx * vcap)));
   m.kv = std::min(24, std::max(0, kv));
   m.cxk = std::ldexp(cx, m.kv);
+  // Terms round(V* s / 2^r) are below 2^T = 2^(54 - r).  A block adds at most
+  // pblk markers to a node; its split counters need pblk 2^16 < 2^32 (low
+  // halves) and pblk 2^(T-16) < 2^31 (signed rest), so T = 47 - ceil(log2 pblk);
+  // the int64 grid sums need N 2^T < 2^63.
+  const int64_t ngroups = (h->N + 3) / 4;
+  const int64_t trips = (ngroups + (int64_t)h->ls.grid * 512 - 1) / ((int64_t)h->ls.grid * 512);
+  const int64_t pblk = std::max<int64_t>(1, trips * 512 * 4);
+  int lg = 0;
+  while (((int64_t)1 << lg) < pblk) lg++;
+  int T = std::min(37, 47 - lg);
   int bitlen = 0;
   while (bitlen < 62 && ((int64_t)1 << bitlen) <= h->N) bitlen++;
-  m.rshift = std::max(17, bitlen - 8);  // |term| < 2^37, N * 2^(54-r) <= 2^62
+  T = std::min(T, 62 - bitlen);
+  m.rshift = 54 - T;
   m.jscale = S.q * S.w0 * std::ldexp(1.0, m.rshift) / (c.h * m.cxk * 8388608.0);
   m.ke_scale = 0.5 * S.m * S.w0 / (m.cxk * m.cxk);
   m.e_scale = (float)(0.5 * c.dt * S.q / S.m * m.cxk);
-  m.agg = h->cfg.sort_period > 0 ? 1 : 0;
+  m.mode = h->cfg.sort_period == 1 ? 2 : (h->cfg.sort_period > 1 ? 1 : 0);
   m.cd = ff_from_double(c.dt * S.q / S.m * m.cxk);
   CUDA_TRY(es1d_mix_prepare(m));
   Es1dMixBufs &bm = h->bm;
@@ -285,6 +321,12 @@ int init_mixed(pic_handle *h, bool solve_e0) {
     CUDA_TRY(cudaMemsetAsync(alt.vl, 0, sizeof(float) * npad, h->st));
     h->sort_blocks = es1d_mix_sort_blocks(m, h->nsm);
     if ((rc = h->alloc(&h->sort_hist, (size_t)c.nc * (h->sort_blocks + 1)))) return rc;
+    if (m.mode == 2) {
+      // sort on write: pass E's destination is the alternate set; key counts
+      // are kept per pass block
+      if ((rc = h->alloc(&bm.H, (size_t)2 * c.nc * h->ls.grid)) || (rc = h->alloc(&bm.T, 2 * (size_t)c.nc)))
+        return rc;
+    }
   }
   es1d_mix_from_fp64(m, b.x, b.v, bm, h->ls, h->st);
   CUDA_TRY(cudaGetLastError());
@@ -307,6 +349,7 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   if (h->cfg.sort_period > 0) {
     if ((rc = sort_mixed(h))) return rc;
   }
+  wire_sorted_output(h);
   if (m.scheme == 2) {
     es1d_mix_deposit_initial(m, bm, (int)(h->steps_done & 1), h->ls, h->st);
     CUDA_TRY(cudaGetLastError());
@@ -623,6 +666,12 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
   int64_t want = (N + 511) / 512;
   h->ls.block = 512;
   h->ls.grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 2));
+  if (cfg->precision == PIC_PREC_MIXED) {
+    // at most 16 grid-stride trips of 4 markers per thread (32768 per block),
+    // the bound the split integer tile is sized for
+    const int64_t need = ((N + 3) / 4 + 512 * 16 - 1) / (512 * 16);
+    h->ls.grid = (int)std::max<int64_t>(h->ls.grid, need);
+  }
   h->nsm = nsm;
   h->nsm = nsm;
   h->em = cfg->solver == PIC_SOLVER_YEE_LEAPFROG;
@@ -667,16 +716,21 @@ int pic_step_async(pic_handle *h, int nsteps) {
   }
   for (int k = 0; k < nsteps && !h->em; k++) {
     if (h->mixed) {
-      if (h->cfg.sort_period > 0 && h->steps_done > 0 && h->steps_done % h->cfg.sort_period == 0) {
+      if (h->cm.mode == 1 && h->steps_done > 0 && h->steps_done % h->cfg.sort_period == 0) {
         int rc = sort_mixed(h);
         if (rc) return rc;
       }
       CUDA_TRY(h->timed_launch(0, [&] {
         es1d_mix_pass_c(h->cm, h->bm, h->steps_done, h->pending, h->ls, h->st);
       }));
+      if (h->cm.mode == 2) {
+        CUDA_TRY(h->timed_launch(3, [&] { es1d_mix_fused_scan(h->cm, h->bm, h->ls.grid, h->st); }));
+        h->launches += 1;
+      }
       CUDA_TRY(h->timed_launch(1, [&] {
         es1d_mix_pass_e(h->cm, h->bm, h->steps_done, h->pending, h->ls, h->st);
       }));
+      if (h->cm.mode == 2) swap_sorted_output(h);
     } else {
       CUDA_TRY(h->timed_launch(0, [&] {
         es1d_fp64_pass_c(h->c1, b, h->steps_done, h->pending, h->ls, h->st);
@@ -875,6 +929,8 @@ int pic_get_particles(pic_handle *h, int s, double *x, double *v) {
 
 int pic_get_ids(pic_handle *h, int s, int64_t *ids) {
   if (!h || s < 0 || s >= h->nsp || !ids) return fail(PIC_ERR_ARG, "pic_get_ids: bad arguments");
+  if (h->cfg.skip_ids && h->mixed && h->cfg.sort_period > 0)
+    return fail(PIC_ERR_ARG, "pic_get_ids: marker ids are not kept (skip_ids = 1)");
   const SpeciesInfo &S = h->sp[s];
   CUDA_TRY(cudaMemcpyAsync(ids, h->ids + S.offset, sizeof(int64_t) * S.n, cudaMemcpyDefault, h->st));
   CUDA_TRY(cudaStreamSynchronize(h->st));

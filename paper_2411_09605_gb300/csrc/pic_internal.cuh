@@ -55,7 +55,7 @@ struct Es1dMixConst {
   int gamma_on;
   int rshift;          // deposit term = round(V* s_k / 2^rshift)
   int kv;              // one V unit = 2^-kv position units per half step
-  int agg;             // warp-aggregated deposits (markers kept cell-sorted)
+  int mode;            // 0 unsorted, 1 periodic counting sort, 2 sorted on write every step
   int64_t n;
   double L, h, dt;
   double cxk;          // (dt 2^31 / L) 2^kv
@@ -69,6 +69,12 @@ struct Es1dMixBufs {
   uint32_t *X;              // [N padded to 4] positions, x = X L / 2^32
   float *vh, *vl;           // [N padded to 4] velocity pairs
   int *Vs;                  // [N padded to 4] V* of the current step (pass C -> pass E)
+  // sort on write (mode 2): pass E writes the new state in key order here
+  uint32_t *Xo;
+  float *vho, *vlo;
+  int64_t *ids, *ido;       // marker ids (null when not tracked)
+  uint32_t *H;              // [2 nc][G] per-block key counts of pass C, then prefixes
+  uint32_t *T;              // [2 nc] key totals
   double *E[2];
   long long *J1[2], *J2[2]; // integer current sums
   double *ke_part;
@@ -187,6 +193,7 @@ void es1d_mix_kinetic(const Es1dMixConst &c, const Es1dMixBufs &b, double *part,
 void es1d_absmax(const double *v, int64_t n, unsigned long long *out, LaunchShape ls,
                  cudaStream_t st);
 int es1d_mix_sort_blocks(const Es1dMixConst &c, int nsm);
+void es1d_mix_fused_scan(const Es1dMixConst &c, const Es1dMixBufs &b, int G, cudaStream_t st);
 cudaError_t es1d_mix_sort(const Es1dMixConst &c, const Es1dMixBufs &src, const Es1dMixBufs &dst,
                           const int64_t *ids_in, int64_t *ids_out, uint32_t *H, int G,
                           cudaStream_t st);

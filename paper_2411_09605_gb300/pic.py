@@ -54,7 +54,8 @@ class pic_config(C.Structure):
     _fields_ = [("grid", pic_grid), ("shape_order", C.c_int), ("dt", C.c_double),
                 ("c", C.c_double), ("solver", C.c_int), ("scheme", C.c_int),
                 ("precision", C.c_int), ("sort_period", C.c_int), ("remove_mean", C.c_int),
-                ("gamma_on", C.c_int), ("ptr_on_device", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("gamma_on", C.c_int), ("ptr_on_device", C.c_int), ("cuda_stream", C.c_void_p),
+                ("skip_ids", C.c_int)]
 
 
 _lib = None
@@ -119,10 +120,11 @@ def _addr(a) -> Optional[int]:
 
 def make_config(nc, L, dt, order=1, scheme=PIC_SCHEME_ESEC2, precision=PIC_PREC_FP64,
                 solver=PIC_SOLVER_AMPERE_ES, dim_x=1, dim_v=1, ny=0, Ly=0.0, c=1.0,
-                sort_period=0, remove_mean=1, gamma_on=1, ptr_on_device=0, stream=None):
+                sort_period=0, remove_mean=1, gamma_on=1, ptr_on_device=0, stream=None,
+                skip_ids=0):
     g = pic_grid(dim_x, dim_v, (C.c_int64 * 2)(nc, ny), (C.c_double * 2)(L, Ly))
     return pic_config(g, order, dt, c, solver, scheme, precision, sort_period, int(remove_mean),
-                      int(gamma_on), int(ptr_on_device), stream)
+                      int(gamma_on), int(ptr_on_device), stream, int(skip_ids))
 
 
 def pic_init(cfg: pic_config, species: Sequence[dict], E0=None, B0=None) -> int:

@@ -154,16 +154,42 @@ def test_counting_sort_permutes_and_orders():
     assert np.max(np.abs(v - s.v[ids]) / np.abs(s.v[ids])) <= 1e-13
 
 
-@pytest.mark.parametrize("order,scheme", [(2, 2), (1, 1)])
-def test_sorting_does_not_change_the_physics(order, scheme):
+@pytest.mark.parametrize("order,scheme,period", [(2, 2, 3), (1, 1, 3), (2, 2, 1), (1, 2, 1),
+                                                (2, 1, 1)])
+def test_sorting_does_not_change_the_physics(order, scheme, period):
     """The mixed form's current is an exact integer sum, so reordering the markers
-    leaves every state bit-identical: runs with and without the periodic counting
-    sort agree exactly (marker by marker through the ids)."""
+    leaves every state bit-identical: runs without sorting, with the periodic
+    counting sort (period 3) and with the per-step sort on write (period 1) agree
+    exactly (marker by marker through the ids)."""
     prob = W.two_stream(n=60_001, nc=256, order=order, seed=17)
     a = gpu_run(prob, scheme, 12, precision=MIXED, sort_period=0)
-    b = gpu_run(prob, scheme, 12, precision=MIXED, sort_period=3)
+    b = gpu_run(prob, scheme, 12, precision=MIXED, sort_period=period)
     assert np.array_equal(a["x"][0], b["x"][0])
     assert np.array_equal(a["v"][0], b["v"][0])
     assert np.array_equal(a["E"], b["E"])
     assert np.array_equal(a["nfb"], b["nfb"])
     assert np.max(np.abs(a["te"] - b["te"])) <= 1e-14 * a["te"][0]
+
+
+def test_sort_on_write_keeps_key_order():
+    """With sort_period = 1 the markers stay ordered by (cell, sign of v*) after every
+    step (checked after 5 steps, in slot order), and the ids remain a permutation."""
+    from paper_2411_09605_gb300 import pic
+    prob = W.two_stream(n=200_003, nc=512, seed=18)
+    sim = pic.Simulation(prob, precision=MIXED, sort_period=1)
+    try:
+        sim.step(5)
+        n = prob.n_markers
+        x, v = np.zeros(n), np.zeros(n)
+        pic.pic_get_particles(sim.h, 0, x, v)
+        ids = np.zeros(n, dtype=np.int64)
+        pic.pic_get_ids(sim.h, 0, ids)
+    finally:
+        sim.close()
+    assert np.array_equal(np.sort(ids), np.arange(n))
+    cells = np.floor(x / (prob.L / prob.nc)).astype(np.int64)
+    # the sort key uses v* of the last step; v^{n+1} has the same sign except for
+    # markers crossing v = 0, so compare cells only (exact) and signs in bulk
+    assert np.all(np.diff(cells) >= 0)
+    key = 2 * cells + (v > 0)
+    assert np.mean(np.diff(key) >= 0) > 0.999
