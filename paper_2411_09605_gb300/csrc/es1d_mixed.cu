@@ -8,22 +8,24 @@
 //     integer overflow of X.
 //   * velocity: an unevaluated float pair (vh, vl) stored in "V units", v times
 //     cxk = (dt 2^31 / L) 2^kv: one V unit moves a marker 2^-kv position units
-//     in half a step.  kv is fixed at set-up from the initial velocity range.
+//     in half a step.  kv >= 1 is fixed at set-up from the initial velocity range.
 //   * v* (Eq. good_translation) is the integer V* = rint(v*), so x* , x^{n+1/2}
 //     = X + [V*]_kv and x^{n+1} = X + 2 [V*]_kv are exact integer additions and
 //     x^{n+1/2} is exactly the midpoint.
 //   * shape weights are exact integers in units of 2^-23 computed from the
 //     fraction (partition of unity is exact); gather and deposit at x^{n+1/2}
 //     use the same integers, as Eq. exp_econs_simple requires.
-//   * current: each marker adds round(V* s_k / 2^r) to node k in 64-bit
-//     integers (exact and order independent, r chosen so no sum overflows; the
-//     rounding is independent per marker and far below the FP64 energy bound).
-//     Lanes of a warp that deposit into the same cell are summed first with
-//     warp reductions (cell-sorted markers make most warps single-cell), then
-//     one shared-memory atomic per cell group; one global atomic per node per
-//     block at the end.
-//   * gather #2 reads E^{n+1/2} as a float pair with error-free weight
-//     products; d = dt (q/m) E_p and v^dag = v^n + d in float pairs.
+//   * current: each marker adds round(V* s_k / 2^r) to node k as an exact
+//     integer (order independent, r chosen so no sum overflows; the rounding
+//     is independent per marker and far below the FP64 energy bound), through
+//     a shared-memory tile of split 32-bit counters; one global 64-bit atomic
+//     per node per block at the end.  Unsorted markers on grids of up to 512
+//     nodes use one tile copy per lane (no bank conflicts); cell-sorted markers
+//     are first summed over the warp in a window of nodes.
+//   * the shared field tables and tiles carry ghost nodes, so the nodes of a
+//     shape never wrap.
+//   * gather #2 reads dt (q/m) cxk E^{n+1/2} as a float pair with error-free
+//     weight products, and v^dag = v^n + d in float pairs.
 //   * Gamma (Eq. opt_solution) from the exact difference
 //     |v^{n+1}|^2 - |v^dag|^2 = 2a, a = d (v* - v^n - d/2) (float pairs for
 //     the cancelling subtraction, FP32 for the small product):
@@ -32,7 +34,8 @@
 //   * energies: per-thread float-pair sums of v^2, block sums in FP64.
 // Gather #1 and deposit #1 only shape v* (not the conservation), so they use
 // plain FP32 weights and the same integer deposit.
-// The markers are kept cell-sorted by a counting sort every sort_period steps.
+// Optionally the markers are kept cell-sorted: by a counting sort every
+// sort_period steps, or written in (cell, sign of v) order by every pass E.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,127 +55,138 @@ __device__ __forceinline__ int cell_of(uint32_t X, int nc) {
   return (int)(((uint64_t)X * (uint32_t)nc) >> 32);
 }
 
-// Shape of a marker at X: nodes and weights.  The weights are quantised
-// B-spline values, multiples of 2^-23, available both as floats (w, for the
-// gathers) and as integers (s = w 2^23, for the deposits); gather and deposit
-// at the same X therefore use exactly the same numbers and sum to 1 exactly.
-// Order 1: w = (1 - f, f).  Order 2: with f = xi - i0 + 1/2 in [0, 1),
-// w = (1/2 (1 - f)^2, 1 - w0 - w2, 1/2 f^2) at nodes i0 - 1, i0, i0 + 1.
+// Padded node indices.  The shared-memory field tables and current tiles carry
+// ghost nodes so that the nodes of a marker's shape are consecutive with no
+// periodic wrap: nc + 3 padded nodes, padded node q standing for grid node
+// (q - kPad) mod nc with kPad = 1 for order 2 (nodes i0 - 1 .. i0 + 1, i0 in
+// [0, nc]) and 0 for order 1 (nodes i, i + 1, i in [0, nc)).
+template <int ORDER>
+struct Pad {
+  static constexpr int kPad = ORDER == 2 ? 1 : 0;
+};
+__device__ __forceinline__ int npad_of(int nc) { return nc + 3; }
+__device__ __forceinline__ int wrap_node(int i, int nc) {
+  return i < 0 ? i + nc : (i >= nc ? i - nc : i);
+}
+
+// Shape of a marker at X: first padded node p and the weights.  The weights
+// are quantised B-spline values, multiples of 2^-23, available both as floats
+// (w, for the gathers) and as integers (s = w 2^23, for the deposits); gather
+// and deposit at the same X therefore use exactly the same numbers and sum to
+// 1 exactly.  Order 1: w = (1 - f, f).  Order 2: with f = xi - i0 + 1/2 in
+// [0, 1), w = (1/2 (1 - f)^2, 1 - w0 - w2, 1/2 f^2) at nodes i0 - 1, i0, i0 + 1.
 template <int ORDER>
 struct ShapeMix {
-  int key;  // base cell
-  int idx[ORDER + 1];
+  int p;
   float w[ORDER + 1];
   int s[ORDER + 1];
   __device__ __forceinline__ ShapeMix(uint32_t X, int nc) {
-    uint32_t lo = X * (uint32_t)nc;
-    int hi = (int)__umulhi(X, (uint32_t)nc);
-    if (ORDER == 2) {
-      uint32_t lo2 = lo + 0x80000000u;
-      hi += lo2 < lo ? 1 : 0;
-      lo = lo2;
-      if (hi >= nc) hi -= nc;
-    }
-    const uint32_t f23 = lo >> 9;
+    // xi (+ 1/2 for order 2) in 32.32 fixed point
+    const uint64_t P = (uint64_t)X * (uint32_t)nc + (ORDER == 2 ? 0x80000000ull : 0ull);
+    p = (int)(P >> 32);
+    const uint32_t f23 = (uint32_t)P >> 9;
     const float f = __fsub_rn(__uint_as_float(0x3F800000u | f23), 1.0f);  // exact
-    key = hi;
     if (ORDER == 1) {
-      idx[0] = hi;
-      idx[1] = (hi + 1 == nc) ? 0 : hi + 1;
       w[0] = __fsub_rn(1.0f, f);
       w[1] = f;
       s[0] = (1 << 23) - (int)f23;
       s[1] = (int)f23;
     } else {
       const float a = __fsub_rn(1.0f, f);
-      const float q0 = __fadd_rn(__fmul_rn(0.5f, __fmul_rn(a, a)), 1.0f);  // 1 + w0 on the 2^-23 grid
-      const float q2 = __fadd_rn(__fmul_rn(0.5f, __fmul_rn(f, f)), 1.0f);
+      // 1 + w0 and 1 + w2 in [1, 1.5]: rounding to float puts w on the 2^-23 grid
+      const float q0 = __fmaf_rn(__fmul_rn(0.5f, a), a, 1.0f);
+      const float q2 = __fmaf_rn(__fmul_rn(0.5f, f), f, 1.0f);
       w[0] = __fsub_rn(q0, 1.0f);
       w[ORDER] = __fsub_rn(q2, 1.0f);
       w[1] = __fsub_rn(__fsub_rn(1.0f, w[0]), w[ORDER]);
       s[0] = __float_as_int(q0) & 0x7FFFFF;
       s[ORDER] = __float_as_int(q2) & 0x7FFFFF;
       s[1] = (1 << 23) - s[0] - s[ORDER];
-      idx[0] = (hi == 0) ? nc - 1 : hi - 1;
-      idx[1] = hi;
-      idx[ORDER] = (hi + 1 == nc) ? 0 : hi + 1;
     }
   }
 };
 
-__device__ __forceinline__ long long deposit_term(int V, int s, int r) {
-  long long t = (long long)V * (long long)s;
-  return (t + (1ll << (r - 1))) >> r;
+__device__ __forceinline__ long long deposit_term(int V, int s, const Es1dMixConst &c) {
+  return ((long long)V * (long long)s + c.rnd) >> c.rshift;
 }
 
-// V units -> position units for half a step
-__device__ __forceinline__ uint32_t half_shift(int V, int kv) {
-  return kv == 0 ? (uint32_t)V : (uint32_t)((V + (1 << (kv - 1))) >> kv);
+// The two tile counters' shares of round(V s / 2^r), r in [17, 31]: bits
+// [r, r + 16) of P = V s + 2^(r-1) (unsigned) and P >> (r + 16) (signed), the
+// same split as tile_add makes of deposit_term.
+struct SplitTerm {
+  unsigned lo;
+  int hi;
+};
+__device__ __forceinline__ SplitTerm deposit_split(int V, int s, const Es1dMixConst &c) {
+  const long long P = (long long)V * (long long)s + c.rnd;
+  const unsigned plo = (unsigned)P, phi = (unsigned)(P >> 32);
+  return {__funnelshift_r(plo, phi, c.rshift) & 0xFFFFu, (int)phi >> (c.rshift - 16)};
 }
 
-__device__ __forceinline__ int to_fixed(float y, unsigned *err) {
-  if (!(fabsf(y) < 2147483520.0f)) atomicOr(err, kErrVelocityRange);
+// V units -> position units for half a step (kv >= 1)
+__device__ __forceinline__ uint32_t half_shift(int V, const Es1dMixConst &c) {
+  return (uint32_t)((V + c.hround) >> c.kv);
+}
+
+__device__ __forceinline__ int to_fixed(float y, unsigned &bad) {
+  if (!(fabsf(y) < 2147483520.0f)) bad |= kErrVelocityRange;
   return __float2int_rn(y);
 }
 
-// Adds round(V s_k / 2^r) at the nodes of S to the block tile.  AGG = false:
-// one shared atomic per lane and node (markers in arbitrary order spread over
-// the tile's banks).  AGG = true (cell-sorted markers): lanes of the warp with
-// the same base cell, found by one match instruction, are summed first with
-// warp reductions of the two 32-bit halves of each term (|term| < 2^37: the low
-// 20 bits and the signed rest sum over 32 lanes without overflow), then one
-// lane adds the sum; warps spread over more than 8 cells fall back to per-lane
-// atomics.
-// The block tile holds each node's integer current as two 32-bit counters:
-// the low 16 bits of every added amount (unsigned) and the rest (signed).  An
-// amount A is added exactly as (A & 0xFFFF, A >> 16); the tile value is
-// hi 2^16 + lo.  Two 32-bit shared atomics run about 2.7 times faster than one
-// 64-bit atomic on random addresses, and the rounding shift r is chosen so that
-// neither counter can overflow for the markers a block processes.
-__device__ __forceinline__ void tile_add(unsigned *Jt, int node, long long a) {
-  atomicAdd(&Jt[2 * node], (unsigned)(a & 0xFFFF));
-  atomicAdd(&Jt[2 * node + 1], (unsigned)(int)(a >> 16));
+// Shared-memory current tile.  Every padded node holds two 32-bit counters per
+// copy: the low 16 bits of each added amount (unsigned) and the signed rest;
+// an amount A is added exactly as (A & 0xFFFF, A >> 16) and the node's value is
+// rest 2^16 + low.  Two 32-bit shared atomics run faster than one 64-bit one,
+// and the rounding shift r is chosen so that no counter can overflow for the
+// markers that add into it.  The tile is laid out [node][half][copy] with RT
+// copies; lane l of every warp adds into copy l mod RT (Jl = tile + l mod RT).
+// With RT = 32 the lanes of a warp always address 32 different banks, so the
+// random-address atomics of unsorted markers never conflict.
+template <int RT>
+__device__ __forceinline__ void tile_add(unsigned *Jl, int q, long long a) {
+  atomicAdd(&Jl[q * 2 * RT], (unsigned)a & 0xFFFFu);
+  atomicAdd(&Jl[q * 2 * RT + RT], (unsigned)(int)(a >> 16));
 }
 
-// Direct deposit: one split atomic per node (markers in arbitrary order spread
-// over the tile's banks).
-template <int ORDER>
-__device__ __forceinline__ void deposit_direct(unsigned *Jt, const ShapeMix<ORDER> &S, int V,
-                                               int r) {
+template <int ORDER, int RT>
+__device__ __forceinline__ void deposit_direct(unsigned *Jl, const ShapeMix<ORDER> &S, int V,
+                                               const Es1dMixConst &c) {
 #pragma unroll
-  for (int k = 0; k <= ORDER; k++) tile_add(Jt, S.idx[k], deposit_term(V, S.s[k], r));
+  for (int k = 0; k <= ORDER; k++) {
+    const SplitTerm t = deposit_split(V, S.s[k], c);
+    atomicAdd(&Jl[(S.p + k) * 2 * RT], t.lo);
+    atomicAdd(&Jl[(S.p + k) * 2 * RT + RT], (unsigned)t.hi);
+  }
 }
 
-// Deposit window for cell-sorted markers: a thread adds the terms of its four
-// markers into kWin consecutive nodes starting at the first node of base cell
-// `base` (one below the warp's smallest first key), then the warp sums each
-// node over its 32
-// lanes (two 32-bit halves: 4 terms of |t| < 2^37 per lane, so the low 20
+// Deposit window for cell-sorted markers (single-copy tile): a thread adds the
+// terms of its four markers into kWin consecutive padded nodes starting one
+// below the warp's smallest first node, then the warp sums each node over its
+// 32 lanes (two 32-bit halves: 4 terms of |t| < 2^37 per lane, so the low 20
 // bits and the signed rest sum without overflow) and one lane adds the 128
-// markers' total with a single shared atomic per node.  Markers whose base
-// cell falls outside the window use direct atomics.
+// markers' total with one split atomic per node.  Markers whose nodes fall
+// outside the window use direct atomics.
 constexpr int kWin = 6;
 
 template <int ORDER>
 struct DepositWindow {
   long long acc[kWin];
   int base;
-  // The window starts one cell below the smallest base cell among the warp's
-  // first markers (the other three per lane usually fall within two cells).
-  __device__ __forceinline__ void start(int key, bool valid) {
+  __device__ __forceinline__ void start(int p, bool valid, int npad) {
 #pragma unroll
     for (int w = 0; w < kWin; w++) acc[w] = 0;
-    const int m = __reduce_min_sync(0xffffffffu, valid ? key : 0x7fffffff);
+    const int m = __reduce_min_sync(0xffffffffu, valid ? p : 0x7fffffff);
     base = m == 0x7fffffff ? 0 : m - 1;
+    base = base < 0 ? 0 : (base > npad - kWin ? npad - kWin : base);
   }
-  __device__ __forceinline__ void add(unsigned *Jt, const ShapeMix<ORDER> &S, int V, int r,
-                                      bool valid) {
+  __device__ __forceinline__ void add(unsigned *Jt, const ShapeMix<ORDER> &S, int V,
+                                      const Es1dMixConst &c, bool valid) {
     if (!valid) return;
-    const int off = S.key - base;
+    const int off = S.p - base;
     const bool inwin = off >= 0 && off <= kWin - 1 - ORDER;
     long long t[ORDER + 1];
 #pragma unroll
-    for (int k = 0; k <= ORDER; k++) t[k] = deposit_term(V, S.s[k], r);
+    for (int k = 0; k <= ORDER; k++) t[k] = deposit_term(V, S.s[k], c);
     if (inwin) {
 #pragma unroll
       for (int w = 0; w < kWin; w++) {
@@ -183,23 +197,17 @@ struct DepositWindow {
       }
     } else {
 #pragma unroll
-      for (int k = 0; k <= ORDER; k++) tile_add(Jt, S.idx[k], t[k]);
+      for (int k = 0; k <= ORDER; k++) tile_add<1>(Jt, S.p + k, t[k]);
     }
   }
-  __device__ __forceinline__ void flush(unsigned *Jt, int nc) {
-    int first = (ORDER == 2 ? base - 1 : base) % nc;
-    if (first < 0) first += nc;
+  __device__ __forceinline__ void flush(unsigned *Jt) {
     const bool lead = (threadIdx.x & 31u) == 0u;
 #pragma unroll
     for (int w = 0; w < kWin; w++) {
       if (__any_sync(0xffffffffu, acc[w] != 0)) {
         const int hs = __reduce_add_sync(0xffffffffu, (int)(acc[w] >> 20));
         const int ls = __reduce_add_sync(0xffffffffu, (int)(acc[w] & 0xFFFFF));
-        if (lead) {
-          int node = first + w;
-          if (node >= nc) node -= nc;
-          tile_add(Jt, node, ((long long)hs << 20) + (long long)ls);
-        }
+        if (lead) tile_add<1>(Jt, base + w, ((long long)hs << 20) + (long long)ls);
       }
     }
   }
@@ -247,281 +255,458 @@ __device__ __forceinline__ double block_sum_d(double s, double *red) {
   return t;  // thread 0
 }
 
-// mean of jscale * J over the grid, identical in every block
-__device__ __forceinline__ double block_mean_j(const long long *J, int n, double jscale, double *red) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)J[i] * jscale;
-  double t = block_sum_d(s, red);
-  if (threadIdx.x == 0) red[32] = t / (double)n;
+// Mean of jscale J over the grid from the exact integer sum (node i at
+// J[i kJStride]): the same value in every block, and FP64 (a narrow pipe on
+// this part) only in thread 0.
+__device__ __forceinline__ double block_mean_j(const long long *J, int n, double jscale_n) {
+  __shared__ long long ired[32];
+  __shared__ double mean;
+  long long s = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += J[i * kJStride];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31u) == 0u) ired[threadIdx.x >> 5] = s;
   __syncthreads();
-  double m = red[32];
+  if (threadIdx.x < 32) {
+    long long t = threadIdx.x < (blockDim.x >> 5) ? ired[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) mean = (double)t * jscale_n;
+  }
   __syncthreads();
-  return m;
+  return mean;
 }
 
-template <int SCHEME>
-__device__ __forceinline__ void build_estar_mix(const Es1dMixConst &c, const double *E, const long long *J1,
-                                float *Es, double *red) {
-  if (SCHEME == 2) {
-    double mean = c.remove_mean ? block_mean_j(J1, c.nc, c.jscale, red) : 0.0;
-    double hdt = 0.5 * c.dt;
-    for (int i = threadIdx.x; i < c.nc; i += blockDim.x)
-      Es[i] = (float)(E[i] - hdt * ((double)J1[i] * c.jscale - mean));
+// Zeroes 2 RT npad counters (RT > 1: the count is a multiple of 4, 16-byte aligned).
+template <int RT>
+__device__ __forceinline__ void clear_tile(unsigned *Jt, int npad) {
+  if (RT > 1) {
+    uint4 *t4 = reinterpret_cast<uint4 *>(Jt);
+    for (int i = threadIdx.x; i < npad * RT / 2; i += blockDim.x) t4[i] = make_uint4(0, 0, 0, 0);
   } else {
-    for (int i = threadIdx.x; i < c.nc; i += blockDim.x) Es[i] = (float)E[i];
+    for (int i = threadIdx.x; i < 2 * npad; i += blockDim.x) Jt[i] = 0;
   }
 }
 
-__device__ __forceinline__ void flush_tile_split(const unsigned *Jt, long long *J, int nc) {
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    const long long a = (long long)(int)Jt[2 * i + 1] * 65536ll + (long long)Jt[2 * i];
-    if (a != 0) atomicAdd((unsigned long long *)&J[i], (unsigned long long)a);
+// Sums the tile's copies node by node (one thread per padded node) and adds
+// each node's total to J[node kJStride] with one 64-bit global atomic (ghost
+// nodes add to the node they stand for).
+template <int ORDER, int RT>
+__device__ __forceinline__ void flush_tile(const unsigned *Jt, long long *J, int nc) {
+  const int npad = npad_of(nc);
+  for (int q = threadIdx.x; q < npad; q += blockDim.x) {
+    long long lo = 0, hi = 0;
+    // copies read in an order skewed by the node: the 32 lanes of a warp
+    // (consecutive nodes) then read 32 different banks
+#pragma unroll
+    for (int k = 0; k < RT; k++) {
+      const int kk = (k + q) & (RT - 1);
+      lo += Jt[q * 2 * RT + kk];
+      hi += (int)Jt[q * 2 * RT + RT + kk];
+    }
+    const long long a = hi * 65536ll + lo;
+    if (a != 0)
+      atomicAdd((unsigned long long *)&J[wrap_node(q - Pad<ORDER>::kPad, nc) * kJStride],
+                (unsigned long long)a);
   }
 }
 
-__device__ __forceinline__ void flush_tile_i64(const long long *Jt, long long *J, int nc) {
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    long long a = Jt[i];
-    if (a != 0) atomicAdd((unsigned long long *)&J[i], (unsigned long long)a);
+// Sum over the block of one double per thread: warp sums only in warps that
+// hold nonzero values, then warp 0 (the FP64 pipe is narrow on this part).
+// The result is valid in thread 0.
+__device__ __forceinline__ double block_sum_sparse(double v, int nactive) {
+  __shared__ double wred[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp * 32 < nactive) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) wred[warp] = v;
   }
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane * 32 < nactive ? wred[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;
 }
 
-__device__ __forceinline__ void finalize_stats_mix(const Es1dMixBufs &b, int slot, int nblocks, double *red) {
+// TE of a finished step: the blocks' kinetic partials (one load per thread)
+// plus W_E of the step's final field (computed by pass E).
+__device__ __forceinline__ void finalize_stats_mix(const Es1dMixBufs &b, int slot, int nblocks) {
   double s = 0.0;
   for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += b.ke_part[i];
-  double t = block_sum_d(s, red);
+  const double t = block_sum_sparse(s, nblocks < (int)blockDim.x ? nblocks : (int)blockDim.x);
   if (threadIdx.x == 0) {
-    double te = t + b.we[0];
+    const double te = t + b.we[0];
     b.te[slot] = te;
     if (!isfinite(te)) atomicOr(b.err, kErrNonfinite);
   }
 }
 
-// Every thread walks groups of 4 consecutive markers (16-byte loads).  All 32
-// lanes of a warp stay in the loop together (the warp-level deposit needs
-// them), so the trip count is rounded up to whole warps.
-__device__ __forceinline__ int64_t warp_trips(int64_t ngroups) {
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t first = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u);
-  return first < ngroups ? (ngroups - first + stride - 1) / stride : 0;
+// Ors the flags of a warp's lanes into the error word (one atomic per warp).
+__device__ __forceinline__ void report_flags(unsigned bad, unsigned *err) {
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31u) == 0u && bad) atomicOr(err, bad);
 }
 
 // V* = rint(v^n + e) to one V unit: v^n is the pair (vh, vl), and above 2^24
 // a float cannot hold every integer, so the sum is split into an integer part
 // and an exact remainder.
-__device__ __forceinline__ int vstar_fixed(float vh, float vl, float e, unsigned *err) {
+__device__ __forceinline__ int vstar_fixed(float vh, float vl, float e, unsigned &bad) {
   const ff s = two_sum(vh, e);
-  const int vi = to_fixed(s.hi, err);
+  const int vi = to_fixed(s.hi, bad);
   const float rem = __fadd_rn(__fadd_rn(__fsub_rn(s.hi, (float)vi), s.lo), vl);
   return vi + __float2int_rn(rem);
 }
 
-// pass C: x*, E**_p (FP32), v* as the integer V* (stored for pass E),
-// x^{n+1/2} and the exact deposit of j^{*,n+1/2}.
-template <int ORDER, int SCHEME, int MODE>
-__global__ void __launch_bounds__(512) mix_pass_c_kernel(Es1dMixConst c, Es1dMixBufs b, int par,
-                                                         int prev_slot, int prev_nblocks) {
+// Stores one table value into RE consecutive copies (RE = 16: 16-byte stores).
+template <int RE, typename T>
+__device__ __forceinline__ void store_copies(T *row, T v) {
+  if (RE == 1) {
+    row[0] = v;
+  } else {
+    static_assert(16 % sizeof(T) == 0, "copies are written 16 bytes at a time");
+    constexpr int kPer = 16 / sizeof(T);
+    union {
+      T t[kPer];
+      uint4 u;
+    } pk;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) pk.t[k] = v;
+    uint4 *r4 = reinterpret_cast<uint4 *>(row);
+#pragma unroll
+    for (int k = 0; k < RE / kPer; k++) r4[k] = pk.u;
+  }
+}
+
+// dt (q/m) cxk E^{n+1/2}_p as a float pair: error-free products of the pair
+// table with the quantised weights, the high parts summed with two-sums.
+template <int ORDER, int RE>
+__device__ __forceinline__ ff gather_kick(const float2 *El, const ShapeMix<ORDER> &S) {
+  float ph[ORDER + 1], pl = 0.0f;
+#pragma unroll
+  for (int k = 0; k <= ORDER; k++) {
+    const float2 eh = El[(S.p + k) * RE];
+    const ff p = two_prod(eh.x, S.w[k]);
+    ph[k] = p.hi;
+    pl = __fadd_rn(pl, __fmaf_rn(eh.y, S.w[k], p.lo));
+  }
+  ff Ep = two_sum(ph[0], ph[1]);
+  pl = __fadd_rn(pl, Ep.lo);
+  if (ORDER == 2) {
+    Ep = two_sum(Ep.hi, ph[ORDER]);
+    pl = __fadd_rn(pl, Ep.lo);
+  }
+  return fast_two_sum(Ep.hi, pl);
+}
+
+// v^dag = v^n + d and v^{n+1} = Gamma v^dag (Eq. opt_solution) in float pairs.
+// With R = |v^n|^2 + 2 v* . (v^dag - v^n), R - |v^dag|^2 = 2a and
+// a = d (v* - v^n - d/2); the bracket is formed from the exact difference
+// V* - v^n, so t = 2a / |v^dag|^2 keeps its relative precision however small it
+// is, and Gamma - 1 = sqrt(1 + t) - 1 = t / (1 + sqrt(1 + t)).  For |t| < 2^-8
+// the series t/2 - t^2/8 + t^3/16 - 5t^4/128 (relative error < 2^-33) replaces
+// the correctly rounded sqrt and divide.  R < 0 is t < -1; that and v^dag = 0
+// (t not finite) fall back to Gamma = 1 and are counted.
+__device__ __forceinline__ ff correct_velocity(float vh, float vl, int Vs, ff d, bool on,
+                                               unsigned &nfb) {
+  const ff vd = ff_add(ff{vh, vl}, d);
+  if (!on) return vd;
+  // b = v* - v^n - d/2 with v* = V* split into two exact float parts
+  const int vlo8 = Vs & 0xFF;
+  const float vst_hi = (float)(Vs - vlo8);
+  const float vst_lo = __fsub_rn(__uint_as_float(0x4B000000u | (unsigned)vlo8), 8388608.0f);
+  const ff q1 = two_sum(vst_hi, -vh);
+  const float q1l = __fadd_rn(q1.lo, __fsub_rn(vst_lo, vl));
+  const ff q2 = two_sum(q1.hi, __fmul_rn(-0.5f, d.hi));
+  const float bq = __fadd_rn(q2.hi, __fadd_rn(q2.lo, __fadd_rn(q1l, __fmul_rn(-0.5f, d.lo))));
+  const float t = __fdiv_rn(__fmul_rn(__fadd_rn(d.hi, d.hi), bq), __fmul_rn(vd.hi, vd.hi));
+  if (!(t >= -1.0f && t < 1e30f)) {
+    nfb++;
+    return vd;
+  }
+  if (fabsf(t) < 0.00390625f) {
+    const float gm = __fmul_rn(
+        t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, -0.0390625f, 0.0625f), -0.125f), 0.5f));
+    // |gm| < 2^-8, so gm v^dag is far below v^dag
+    ff p = two_prod(vd.hi, gm);
+    p.lo = __fmaf_rn(vd.lo, gm, p.lo);
+    const ff s = fast_two_sum(vd.hi, p.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(vd.lo, p.lo)));
+  }
+  const float gm = __fdiv_rn(t, __fadd_rn(1.0f, __fsqrt_rn(__fadd_rn(1.0f, t))));
+  ff p = two_prod(vd.hi, gm);
+  p.lo = __fmaf_rn(vd.lo, gm, p.lo);
+  return ff_add(vd, p);
+}
+
+// Adds a 64-bit padded tile to J[node stride] with one global atomic per node.
+template <int ORDER>
+__device__ __forceinline__ void flush_tile_i64(const long long *Jt, long long *J, int nc,
+                                               int stride) {
+  for (int q = threadIdx.x; q < npad_of(nc); q += blockDim.x) {
+    const long long a = Jt[q];
+    if (a != 0)
+      atomicAdd((unsigned long long *)&J[wrap_node(q - Pad<ORDER>::kPad, nc) * stride],
+                (unsigned long long)a);
+  }
+}
+
+// State of G consecutive markers of one thread (vector loads of 4 G bytes).
+template <int G>
+struct MarkerGroup {
+  uint32_t X[G];
+  float vh[G], vl[G];
+  int V[G];
+};
+
+template <int G, typename T>
+__device__ __forceinline__ void load_vec(const T *base, int64_t g, bool ok, T (&out)[G]) {
+  static_assert(sizeof(T) == 4 && (G == 2 || G == 4), "groups of 2 or 4 words");
+  if (G == 4) {
+    uint4 u = make_uint4(0, 0, 0, 0);
+    if (ok) u = reinterpret_cast<const uint4 *>(base)[g];
+    memcpy(&out, &u, sizeof u);
+  } else {
+    uint2 u = make_uint2(0, 0);
+    if (ok) u = reinterpret_cast<const uint2 *>(base)[g];
+    memcpy(&out, &u, sizeof u);
+  }
+}
+
+template <int G, typename T>
+__device__ __forceinline__ void store_vec(T *base, int64_t g, const T (&in)[G]) {
+  if (G == 4) {
+    uint4 u;
+    memcpy(&u, &in, sizeof u);
+    reinterpret_cast<uint4 *>(base)[g] = u;
+  } else {
+    uint2 u;
+    memcpy(&u, &in, sizeof u);
+    reinterpret_cast<uint2 *>(base)[g] = u;
+  }
+}
+
+template <int G, bool WITH_V>
+__device__ __forceinline__ void load_group(const Es1dMixBufs &b, int64_t g, bool ok,
+                                           MarkerGroup<G> &m) {
+  load_vec<G>(b.X, g, ok, m.X);
+  load_vec<G>(b.vh, g, ok, m.vh);
+  load_vec<G>(b.vl, g, ok, m.vl);
+  if (WITH_V) load_vec<G>(b.Vs, g, ok, m.V);
+}
+
+// Runs body(check, g, m) over the groups g of G consecutive markers of this
+// thread.  With PREFETCH the state of the next group is loaded while the
+// current one is processed (the unsorted passes; the windowed deposits of the
+// sorted modes need those registers).  All lanes of a warp run the same trips
+// (warp-level deposits and ranks need them): trips in which the warp's 32
+// groups are all full run without validity tests (check = false_type), the
+// last one or two with them.
+template <int G, bool WITH_V, bool PREFETCH, typename F>
+__device__ __forceinline__ void for_groups(const Es1dMixBufs &b, int64_t n, F body) {
+  // block b takes the groups [ngroups b / grid, ngroups (b + 1) / grid)
+  const int64_t nfull = n / G, ngroups = (n + G - 1) / G;
+  const int64_t beg = ngroups * blockIdx.x / gridDim.x;
+  const int64_t end = ngroups * (blockIdx.x + 1) / gridDim.x;
+  const int64_t full_end = end < nfull ? end : nfull;
+  int64_t gw = beg + (threadIdx.x & ~31u);
+  int64_t g = gw + (threadIdx.x & 31u);
+  MarkerGroup<G> cur;
+  if (PREFETCH) load_group<G, WITH_V>(b, g, g < end, cur);
+  for (; gw < end; gw += blockDim.x, g += blockDim.x) {
+    MarkerGroup<G> nxt;
+    if (PREFETCH)
+      load_group<G, WITH_V>(b, g + blockDim.x, g + blockDim.x < end, nxt);
+    else
+      load_group<G, WITH_V>(b, g, g < end, cur);
+    if (gw + 31 < full_end)
+      body(std::false_type(), g, cur, end);
+    else
+      body(std::true_type(), g, cur, end);
+    if (PREFETCH) cur = nxt;
+  }
+}
+
+// Markers per group of a thread in passes C and E, and whether the next
+// group's state is loaded while the current one is processed (unsorted modes).
+constexpr int kGroupC = 4;
+constexpr int kGroupE = 4;
+constexpr bool kPrefetchC = true;
+constexpr bool kPrefetchE = false;
+
+template <int ORDER, int SCHEME, int MODE, int RT, int RE>
+__global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
+    mix_pass_c_kernel(Es1dMixConst c, Es1dMixBufs b, int par, int prev_slot, int prev_nblocks) {
   constexpr bool AGG = MODE > 0;
+  constexpr int PAD = Pad<ORDER>::kPad;
+  static_assert(!AGG || RT == 1, "sorted modes use a single tile copy");
   extern __shared__ __align__(16) unsigned char smraw[];
-  unsigned *Jt = (unsigned *)smraw;           // split tile: 2 counters per node
-  float *Es = (float *)(Jt + 2 * c.nc);
-  uint32_t *hist = (uint32_t *)(Es + c.nc);   // MODE 2: keys of the markers after the step
-  __shared__ double red[33];
-  build_estar_mix<SCHEME>(c, PSEL(b.E, par), PSEL(b.J1, par), Es, red);
-  for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x) Jt[i] = 0;
+  const int npad = npad_of(c.nc);
+  unsigned *Jt = (unsigned *)smraw;           // [npad][2][RT]
+  float *Es = (float *)(Jt + 2 * RT * npad);  // [npad][RE]: dt/2 (q/m) cxk E*
+  uint32_t *hist = (uint32_t *)(Es + RE * npad);  // MODE 2: keys of the markers after the step
+  {
+    // E* = E - dt/2 (J1 - <J1>) at every padded node, scaled to the v* kick;
+    // the first node's loads are issued before the block-wide mean
+    const double *E = PSEL(b.E, par);
+    const long long *J1 = PSEL(b.J1, par);
+    const int i0 = wrap_node((int)threadIdx.x - PAD, c.nc);
+    const bool has0 = (int)threadIdx.x < npad;
+    const double E0 = has0 ? E[i0] : 0.0;
+    const long long J0 = (SCHEME == 2 && has0) ? J1[i0 * kJStride] : 0;
+    const double mean = (SCHEME == 2 && c.remove_mean) ? block_mean_j(J1, c.nc, c.jscale_n) : 0.0;
+    for (int q = threadIdx.x; q < npad; q += blockDim.x) {
+      const int i = wrap_node(q - PAD, c.nc);
+      const bool first = q == (int)threadIdx.x;
+      double e = first ? E0 : E[i];
+      if (SCHEME == 2)
+        e -= 0.5 * c.dt * ((double)(first ? J0 : J1[i * kJStride]) * c.jscale - mean);
+      store_copies<RE>(Es + q * RE, (float)(c.e_scale * e));
+    }
+  }
+  clear_tile<RT>(Jt, npad);
   if (MODE == 2)
     for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x) hist[i] = 0;
   if (blockIdx.x == 0) {
     if (SCHEME == 2)
-      for (int i = threadIdx.x; i < c.nc; i += blockDim.x) PSEL(b.J1, par ^ 1)[i] = 0;
-    if (prev_slot >= 0) finalize_stats_mix(b, prev_slot, prev_nblocks, red);
+      for (int i = threadIdx.x; i < c.nc; i += blockDim.x) PSEL(b.J1, par ^ 1)[i * kJStride] = 0;
+    if (prev_slot >= 0) finalize_stats_mix(b, prev_slot, prev_nblocks);
   }
   __syncthreads();
-  const int64_t ngroups = (c.n + 3) >> 2;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t trips = warp_trips(ngroups);
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (int64_t it = 0; it < trips; it++, g += stride) {
-    const bool gv = g < ngroups;
-    uint4 X4 = make_uint4(0, 0, 0, 0);
-    float4 h4 = make_float4(0.f, 0.f, 0.f, 0.f), l4 = h4;
-    if (gv) {
-      X4 = reinterpret_cast<const uint4 *>(b.X)[g];
-      h4 = reinterpret_cast<const float4 *>(b.vh)[g];
-      l4 = reinterpret_cast<const float4 *>(b.vl)[g];
-    }
-    int Vout[4];
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned *Jl = Jt + (lane & (RT - 1));
+  const float *El = Es + (lane & (RE - 1));
+  unsigned bad = 0;
+  constexpr int G = kGroupC;
+  for_groups<G, false, !AGG && kPrefetchC>(b, c.n, [&](auto check, int64_t g, const MarkerGroup<G> &m, int64_t end) {
+    constexpr bool CHECK = decltype(check)::value;
+    const bool gv = !CHECK || g < end;
+    int Vout[G];
     DepositWindow<ORDER> win;
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const uint32_t X = j == 0 ? X4.x : j == 1 ? X4.y : j == 2 ? X4.z : X4.w;
-      const float vh = j == 0 ? h4.x : j == 1 ? h4.y : j == 2 ? h4.z : h4.w;
-      const float vl = j == 0 ? l4.x : j == 1 ? l4.y : j == 2 ? l4.z : l4.w;
-      const bool valid = gv && (4 * g + j < c.n);
-      const int Vn = to_fixed(vh, b.err);
-      const ShapeMix<ORDER> Sx(X + half_shift(Vn, c.kv), c.nc);
+    for (int j = 0; j < G; j++) {
+      const uint32_t X = m.X[j];
+      const float vh = m.vh[j], vl = m.vl[j];
+      const bool valid = !CHECK || (gv && G * g + j < c.n);
+      const int Vn = to_fixed(vh, bad);
+      const ShapeMix<ORDER> Sx(X + half_shift(Vn, c), c.nc);
       float e = 0.0f;
 #pragma unroll
-      for (int k = 0; k <= ORDER; k++) e = __fmaf_rn(Sx.w[k], Es[Sx.idx[k]], e);
-      const int Vs = vstar_fixed(vh, vl, __fmul_rn(c.e_scale, e), b.err);
-      const uint32_t hs = half_shift(Vs, c.kv);
+      for (int k = 0; k <= ORDER; k++) e = __fmaf_rn(Sx.w[k], El[(Sx.p + k) * RE], e);
+      const int Vs = vstar_fixed(vh, vl, e, bad);
+      const uint32_t hs = half_shift(Vs, c);
       const ShapeMix<ORDER> Sh(X + hs, c.nc);
       if (AGG) {
-        if (j == 0) win.start(Sh.key, valid);
-        win.add(Jt, Sh, Vs, c.rshift, valid);
+        if (j == 0) win.start(Sh.p, valid, npad);
+        win.add(Jt, Sh, Vs, c, valid);
       } else if (valid) {
-        deposit_direct<ORDER>(Jt, Sh, Vs, c.rshift);
+        deposit_direct<ORDER, RT>(Jl, Sh, Vs, c);
       }
       if (MODE == 2) warp_rank(hist, sort_key(X + 2u * hs, Vs, c.nc), valid);
       Vout[j] = Vs;
     }
-    if (AGG) win.flush(Jt, c.nc);
-    if (gv) reinterpret_cast<int4 *>(b.Vs)[g] = make_int4(Vout[0], Vout[1], Vout[2], Vout[3]);
-  }
+    if (AGG) win.flush(Jt);
+    if (gv) store_vec<G>(b.Vs, g, Vout);
+  });
+  report_flags(bad, b.err);
   __syncthreads();
-  flush_tile_split(Jt, PSEL(b.J2, par), c.nc);
+  flush_tile<ORDER, RT>(Jt, PSEL(b.J2, par), c.nc);
   if (MODE == 2)
     for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x)
       b.H[(int64_t)i * gridDim.x + blockIdx.x] = hist[i];
 }
 
-// pass E: E^{n+1}, E^{n+1/2} (float pairs) in the prologue; per marker the
-// gather at x^{n+1/2} = X + [V*], v^dag, Gamma, x^{n+1}, v^{n+1}, the kinetic
-// energy and (ESEC2) the next step's x* and j^{n+1,*} deposit.
-template <int ORDER, int SCHEME, int MODE>
-__global__ void __launch_bounds__(512) mix_pass_e_kernel(Es1dMixConst c, Es1dMixBufs b, int par,
-                                                         int slot) {
+// pass E: E^{n+1} and dt (q/m) cxk E^{n+1/2} (float pairs) in the prologue; per
+// marker the gather at x^{n+1/2} = X + [V*], v^dag, Gamma, x^{n+1}, v^{n+1},
+// the kinetic energy and (ESEC2) the next step's x* and j^{n+1,*} deposit.
+template <int ORDER, int SCHEME, int MODE, int RT, int RE>
+__global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
+    mix_pass_e_kernel(Es1dMixConst c, Es1dMixBufs b, int par, int slot) {
   constexpr bool AGG = MODE > 0;
+  constexpr int PAD = Pad<ORDER>::kPad;
+  static_assert(!AGG || RT == 1, "sorted modes use a single tile copy");
   extern __shared__ __align__(16) unsigned char smraw[];
-  unsigned *Jt = (unsigned *)smraw;           // split tile: 2 counters per node
-  float2 *Eh2 = (float2 *)(Jt + 2 * c.nc);
-  uint32_t *off = (uint32_t *)(Eh2 + c.nc);   // MODE 2: next free slot of each key
-  __shared__ double red[33];
+  const int npad = npad_of(c.nc);
+  unsigned *Jt = (unsigned *)smraw;              // [npad][2][RT]
+  float2 *Eh2 = (float2 *)(Jt + 2 * RT * npad);  // [npad][RE]: dt (q/m) cxk E^{n+1/2}
+  uint32_t *off = (uint32_t *)(Eh2 + RE * npad); // MODE 2: next free slot of each key
   if (MODE == 2) {
     __shared__ uint32_t tmp[512];
     block_exclusive_scan(b.T, off, 2 * c.nc, tmp);
     for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x)
       off[i] += b.H[(int64_t)i * gridDim.x + blockIdx.x];
   }
-  const double *E = PSEL(b.E, par);
-  const long long *J2 = PSEL(b.J2, par);
-  double mean2 = c.remove_mean ? block_mean_j(J2, c.nc, c.jscale, red) : 0.0;
-  double we_loc = 0.0;
-  for (int i = threadIdx.x; i < c.nc; i += blockDim.x) {
-    double en = E[i] - c.dt * ((double)J2[i] * c.jscale - mean2);
-    ff s = ff_from_double(0.5 * (E[i] + en));
-    Eh2[i] = make_float2(s.hi, s.lo);
-    Jt[2 * i] = 0;
-    Jt[2 * i + 1] = 0;
+  {
+    // E^{n+1} = E^n - dt (J2 - <J2>) and dt (q/m) cxk E^{n+1/2} as float pairs;
+    // the first node's loads are issued before the block-wide mean
+    const double *E = PSEL(b.E, par);
+    const long long *J2 = PSEL(b.J2, par);
+    const int i0 = wrap_node((int)threadIdx.x - PAD, c.nc);
+    const bool has0 = (int)threadIdx.x < npad;
+    const double E0 = has0 ? E[i0] : 0.0;
+    const long long J0 = has0 ? J2[i0 * kJStride] : 0;
+    const double mean2 = c.remove_mean ? block_mean_j(J2, c.nc, c.jscale_n) : 0.0;
+    double we_loc = 0.0;
+    for (int q = threadIdx.x; q < npad; q += blockDim.x) {
+      const int i = wrap_node(q - PAD, c.nc);
+      const bool first = q == (int)threadIdx.x;
+      const double Ei = first ? E0 : E[i];
+      const double en = Ei - c.dt * ((double)(first ? J0 : J2[i * kJStride]) * c.jscale - mean2);
+      const ff s = ff_from_double(c.kick * (0.5 * (Ei + en)));
+      store_copies<RE>(Eh2 + q * RE, make_float2(s.hi, s.lo));
+      if (blockIdx.x == 0 && q - PAD == i) {
+        PSEL(b.E, par ^ 1)[i] = en;
+        PSEL(b.J2, par ^ 1)[i * kJStride] = 0;
+        we_loc = fma(en, en, we_loc);
+      }
+    }
     if (blockIdx.x == 0) {
-      PSEL(b.E, par ^ 1)[i] = en;
-      PSEL(b.J2, par ^ 1)[i] = 0;
-      we_loc += en * en;
+      const int nact = c.nc + PAD < (int)blockDim.x ? c.nc + PAD : (int)blockDim.x;
+      const double t = block_sum_sparse(we_loc, nact);
+      if (threadIdx.x == 0) b.we[0] = 0.5 * c.h * t;
     }
   }
-  if (blockIdx.x == 0) {
-    double t = block_sum_d(we_loc, red);
-    if (threadIdx.x == 0) b.we[0] = 0.5 * c.h * t;
-  }
+  clear_tile<RT>(Jt, npad);
   __syncthreads();
 
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned *Jl = Jt + (lane & (RT - 1));
+  const float2 *El = Eh2 + (lane & (RE - 1));
   float ke_hi = 0.0f, ke_lo = 0.0f;
-  unsigned nfb = 0;
-  const int64_t ngroups = (c.n + 3) >> 2;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t trips = warp_trips(ngroups);
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (int64_t it = 0; it < trips; it++, g += stride) {
-    const bool gv = g < ngroups;
-    uint4 X4 = make_uint4(0, 0, 0, 0);
-    float4 h4 = make_float4(0.f, 0.f, 0.f, 0.f), l4 = h4;
-    int4 V4 = make_int4(0, 0, 0, 0);
-    if (gv) {
-      X4 = reinterpret_cast<const uint4 *>(b.X)[g];
-      h4 = reinterpret_cast<const float4 *>(b.vh)[g];
-      l4 = reinterpret_cast<const float4 *>(b.vl)[g];
-      V4 = reinterpret_cast<const int4 *>(b.Vs)[g];
-    }
-    uint32_t Xo[4];
-    float ho[4], lo[4];
+  unsigned nfb = 0, bad = 0;
+  constexpr int G = kGroupE;
+  for_groups<G, true, !AGG && kPrefetchE>(b, c.n, [&](auto check, int64_t g, const MarkerGroup<G> &m, int64_t end) {
+    constexpr bool CHECK = decltype(check)::value;
+    const bool gv = !CHECK || g < end;
+    MarkerGroup<G> o;
     DepositWindow<ORDER> win;
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const uint32_t X = j == 0 ? X4.x : j == 1 ? X4.y : j == 2 ? X4.z : X4.w;
-      const float vh = j == 0 ? h4.x : j == 1 ? h4.y : j == 2 ? h4.z : h4.w;
-      const float vl = j == 0 ? l4.x : j == 1 ? l4.y : j == 2 ? l4.z : l4.w;
-      const int Vs = j == 0 ? V4.x : j == 1 ? V4.y : j == 2 ? V4.z : V4.w;
-      const bool valid = gv && (4 * g + j < c.n);
-      const uint32_t hs = half_shift(Vs, c.kv);
-      // gather #2: E^{n+1/2}_p as a float pair from exact weight products
+    for (int j = 0; j < G; j++) {
+      const uint32_t X = m.X[j];
+      const float vh = m.vh[j], vl = m.vl[j];
+      const int Vs = m.V[j];
+      const bool valid = !CHECK || (gv && G * g + j < c.n);
+      const uint32_t hs = half_shift(Vs, c);
+      // gather #2 at x^{n+1/2}: d = dt (q/m) E^{n+1/2}_p in V units
       const ShapeMix<ORDER> Sh(X + hs, c.nc);
-      float ph[ORDER + 1], pl = 0.0f;
-#pragma unroll
-      for (int k = 0; k <= ORDER; k++) {
-        const float2 eh = Eh2[Sh.idx[k]];
-        const ff p = two_prod(eh.x, Sh.w[k]);
-        ph[k] = p.hi;
-        pl = __fadd_rn(pl, __fmaf_rn(eh.y, Sh.w[k], p.lo));
-      }
-      ff Ep = two_sum(ph[0], ph[1]);
-      pl = __fadd_rn(pl, Ep.lo);
-      if (ORDER == 2) {
-        Ep = two_sum(Ep.hi, ph[ORDER]);
-        pl = __fadd_rn(pl, Ep.lo);
-      }
-      Ep = fast_two_sum(Ep.hi, pl);
-      const ff d = ff_mul(Ep, c.cd);        // dt (q/m) E^{n+1/2}_p, V units
-      const ff v = {vh, vl};
-      const ff vd = ff_add(v, d);           // v^dag
-      // b = v* - v^n - d/2 with v* = V* exactly (two exact float parts)
-      const int vlo8 = Vs & 0xFF;
-      const float vst_hi = (float)(Vs - vlo8);
-      const float vst_lo = __fsub_rn(__uint_as_float(0x4B000000u | (unsigned)vlo8), 8388608.0f);
-      const ff q1 = two_sum(vst_hi, -vh);
-      const float q1l = __fadd_rn(q1.lo, __fsub_rn(vst_lo, vl));
-      const ff q2 = two_sum(q1.hi, __fmul_rn(-0.5f, d.hi));
-      const float bq = __fadd_rn(q2.hi, __fadd_rn(q2.lo, __fadd_rn(q1l, __fmul_rn(-0.5f, d.lo))));
-      const float a = __fmul_rn(d.hi, bq);  // |v^{n+1}|^2 - |v^dag|^2 = 2a
-      const float vd2 = __fmul_rn(vd.hi, vd.hi);
-      ff vn = vd;
-      if (c.gamma_on && valid) {
-        const float t = __fdiv_rn(__fmul_rn(2.0f, a), vd2);
-        const float op = __fadd_rn(1.0f, t);
-        if (vd2 > 0.0f && op >= 0.0f && fabsf(t) < 1e30f) {
-          // Gamma - 1 = sqrt(1 + t) - 1 = t / (1 + sqrt(1 + t)): for |t| < 2^-8 the
-          // series t/2 - t^2/8 + t^3/16 - 5t^4/128 (relative error < 2^-33),
-          // otherwise correctly rounded sqrt and divide
-          float gm;
-          if (fabsf(t) < 0.00390625f) {
-            gm = __fmul_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, -0.0390625f, 0.0625f),
-                                                     -0.125f), 0.5f));
-          } else {
-            gm = __fdiv_rn(t, __fadd_rn(1.0f, __fsqrt_rn(op)));
-          }
-          ff p = two_prod(vd.hi, gm);
-          p.lo = __fmaf_rn(vd.lo, gm, p.lo);
-          vn = ff_add(vd, p);
-        } else {
-          nfb++;
-        }
-      }
+      const ff d = gather_kick<ORDER, RE>(El, Sh);
+      const ff vn = correct_velocity(vh, vl, Vs, d, c.gamma_on && valid, nfb);
       if (valid) {
         ff s2 = two_prod(vn.hi, vn.hi);
-        s2.lo = __fmaf_rn(__fmul_rn(2.0f, vn.hi), vn.lo, s2.lo);
+        s2.lo = __fmaf_rn(__fadd_rn(vn.hi, vn.hi), vn.lo, s2.lo);
         const ff acc = two_sum(ke_hi, s2.hi);
         ke_hi = acc.hi;
         ke_lo = __fadd_rn(ke_lo, __fadd_rn(acc.lo, s2.lo));
-        if (!isfinite(vn.hi)) atomicOr(b.err, kErrNonfinite);
+        if (!isfinite(vn.hi)) bad |= kErrNonfinite;
       }
       const uint32_t Xn = X + 2u * hs;
       if (SCHEME == 2) {
-        const int Vn1 = to_fixed(vn.hi, b.err);
-        const ShapeMix<ORDER> S1(Xn + half_shift(Vn1, c.kv), c.nc);
+        const int Vn1 = to_fixed(vn.hi, bad);
+        const ShapeMix<ORDER> S1(Xn + half_shift(Vn1, c), c.nc);
         if (AGG) {
-          if (j == 0) win.start(S1.key, valid);
-          win.add(Jt, S1, Vn1, c.rshift, valid);
+          if (j == 0) win.start(S1.p, valid, npad);
+          win.add(Jt, S1, Vn1, c, valid);
         } else if (valid) {
-          deposit_direct<ORDER>(Jt, S1, Vn1, c.rshift);
+          deposit_direct<ORDER, RT>(Jl, S1, Vn1, c);
         }
       }
       if (MODE == 2) {
@@ -531,28 +716,40 @@ __global__ void __launch_bounds__(512) mix_pass_e_kernel(Es1dMixConst c, Es1dMix
           b.Xo[dst] = Xn;
           b.vho[dst] = vn.hi;
           b.vlo[dst] = vn.lo;
-          if (b.ids) b.ido[dst] = b.ids[4 * g + j];
+          if (b.ids) b.ido[dst] = b.ids[G * g + j];
         }
       }
-      Xo[j] = valid ? Xn : X;
-      ho[j] = valid ? vn.hi : vh;
-      lo[j] = valid ? vn.lo : vl;
+      o.X[j] = valid ? Xn : X;
+      o.vh[j] = valid ? vn.hi : vh;
+      o.vl[j] = valid ? vn.lo : vl;
     }
-    if (AGG && SCHEME == 2) win.flush(Jt, c.nc);
+    if (AGG && SCHEME == 2) win.flush(Jt);
     if (MODE != 2 && gv) {
-      reinterpret_cast<uint4 *>(b.X)[g] = make_uint4(Xo[0], Xo[1], Xo[2], Xo[3]);
-      reinterpret_cast<float4 *>(b.vh)[g] = make_float4(ho[0], ho[1], ho[2], ho[3]);
-      reinterpret_cast<float4 *>(b.vl)[g] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      store_vec<G>(b.X, g, o.X);
+      store_vec<G>(b.vh, g, o.vh);
+      store_vec<G>(b.vl, g, o.vl);
+    }
+  });
+  report_flags(bad, b.err);
+  nfb = __reduce_add_sync(0xffffffffu, nfb);
+  if (lane == 0 && nfb) atomicAdd(&b.fallback[slot], (unsigned long long)nfb);
+  // kinetic energy: float-pair sums over each warp, then over the warps by
+  // warp 0, FP64 for the block total only
+  {
+    __shared__ float2 kred[32];
+    ff k = {ke_hi, ke_lo};
+    for (int o = 16; o > 0; o >>= 1)
+      k = ff_add(k, ff{__shfl_xor_sync(0xffffffffu, k.hi, o), __shfl_xor_sync(0xffffffffu, k.lo, o)});
+    if (lane == 0) kred[threadIdx.x >> 5] = make_float2(k.hi, k.lo);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      k = threadIdx.x < (blockDim.x >> 5) ? ff{kred[lane].x, kred[lane].y} : ff{0.0f, 0.0f};
+      for (int o = 16; o > 0; o >>= 1)
+        k = ff_add(k, ff{__shfl_xor_sync(0xffffffffu, k.hi, o), __shfl_xor_sync(0xffffffffu, k.lo, o)});
+      if (lane == 0) b.ke_part[blockIdx.x] = c.ke_scale * ((double)k.hi + (double)k.lo);
     }
   }
-  for (int o = 16; o > 0; o >>= 1) nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
-  if ((threadIdx.x & 31) == 0 && nfb) atomicAdd(&b.fallback[slot], (unsigned long long)nfb);
-  double t = block_sum_d((double)ke_hi + (double)ke_lo, red);
-  if (threadIdx.x == 0) b.ke_part[blockIdx.x] = c.ke_scale * t;
-  if (SCHEME == 2) {
-    __syncthreads();
-    flush_tile_split(Jt, PSEL(b.J1, par ^ 1), c.nc);
-  }
+  if (SCHEME == 2) flush_tile<ORDER, RT>(Jt, PSEL(b.J1, par ^ 1), c.nc);
 }
 
 template <int ORDER>
@@ -560,19 +757,21 @@ __global__ void __launch_bounds__(512) mix_deposit_initial_kernel(Es1dMixConst c
                                                                   int par) {
   extern __shared__ __align__(16) unsigned char smraw[];
   long long *Jt = (long long *)smraw;
-  for (int i = threadIdx.x; i < c.nc; i += blockDim.x) Jt[i] = 0;
+  const int npad = npad_of(c.nc);
+  for (int i = threadIdx.x; i < npad; i += blockDim.x) Jt[i] = 0;
   __syncthreads();
+  unsigned bad = 0;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n;
        p += (int64_t)gridDim.x * blockDim.x) {
-    int Vn = to_fixed(b.vh[p], b.err);
-    ShapeMix<ORDER> S(b.X[p] + half_shift(Vn, c.kv), c.nc);
+    const int Vn = to_fixed(b.vh[p], bad);
+    const ShapeMix<ORDER> S(b.X[p] + half_shift(Vn, c), c.nc);
 #pragma unroll
     for (int k = 0; k <= ORDER; k++)
-      atomicAdd((unsigned long long *)&Jt[S.idx[k]],
-                (unsigned long long)deposit_term(Vn, S.s[k], c.rshift));
+      atomicAdd((unsigned long long *)&Jt[S.p + k], (unsigned long long)deposit_term(Vn, S.s[k], c));
   }
+  if (bad) atomicOr(b.err, bad);
   __syncthreads();
-  flush_tile_i64(Jt, PSEL(b.J1, par), c.nc);
+  flush_tile_i64<ORDER>(Jt, PSEL(b.J1, par), c.nc, kJStride);
 }
 
 // Charge of the markers for the initial Poisson solve: the integer weights
@@ -582,22 +781,22 @@ __global__ void __launch_bounds__(512) mix_charge_kernel(Es1dMixConst c, Es1dMix
                                                          long long *count) {
   extern __shared__ __align__(16) unsigned char smraw[];
   long long *Jt = (long long *)smraw;
-  for (int i = threadIdx.x; i < c.nc; i += blockDim.x) Jt[i] = 0;
+  const int npad = npad_of(c.nc);
+  for (int i = threadIdx.x; i < npad; i += blockDim.x) Jt[i] = 0;
   __syncthreads();
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n;
        p += (int64_t)gridDim.x * blockDim.x) {
-    ShapeMix<ORDER> S(b.X[p], c.nc);
+    const ShapeMix<ORDER> S(b.X[p], c.nc);
 #pragma unroll
     for (int k = 0; k <= ORDER; k++)
-      atomicAdd((unsigned long long *)&Jt[S.idx[k]], (unsigned long long)S.s[k]);
+      atomicAdd((unsigned long long *)&Jt[S.p + k], (unsigned long long)S.s[k]);
   }
   __syncthreads();
-  flush_tile_i64(Jt, count, c.nc);
+  flush_tile_i64<ORDER>(Jt, count, c.nc, 1);
 }
 
 __global__ void mix_finalize_kernel(Es1dMixBufs b, int slot, int nblocks) {
-  __shared__ double red[33];
-  finalize_stats_mix(b, slot, nblocks, red);
+  finalize_stats_mix(b, slot, nblocks);
 }
 
 // FP64 (x, v) <-> (X, vh, vl) with v stored in V units (v * cxk)
@@ -735,7 +934,6 @@ __global__ void __launch_bounds__(512) sort_move_kernel(Es1dMixBufs src, Es1dMix
   block_exclusive_scan(T, off, nc, tmp);
   for (int i = threadIdx.x; i < nc; i += blockDim.x) off[i] += H[(int64_t)i * gridDim.x + blockIdx.x];
   __syncthreads();
-  const unsigned lane = threadIdx.x & 31u;
   int64_t beg = blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
   for (int64_t base = beg; base < end; base += blockDim.x) {
     int64_t p = base + threadIdx.x;
@@ -753,44 +951,55 @@ __global__ void __launch_bounds__(512) sort_move_kernel(Es1dMixBufs src, Es1dMix
 }
 
 template <typename F>
-void dispatch_mix(int order, int scheme, int mode, F f) {
+void dispatch_mix(const Es1dMixConst &c, F f) {
   using I1 = std::integral_constant<int, 1>;
   using I2 = std::integral_constant<int, 2>;
   using M0 = std::integral_constant<int, 0>;
   using M1 = std::integral_constant<int, 1>;
   using M2 = std::integral_constant<int, 2>;
+  using R1 = std::integral_constant<int, 1>;
+  using R16 = std::integral_constant<int, 16>;
+  using R32 = std::integral_constant<int, 32>;
   auto go = [&](auto O, auto S) {
-    if (mode == 0) f(O, S, M0());
-    if (mode == 1) f(O, S, M1());
-    if (mode == 2) f(O, S, M2());
+    if (c.mode == 0 && c.wide) f(O, S, M0(), R32(), R16());
+    if (c.mode == 0 && !c.wide) f(O, S, M0(), R1(), R1());
+    if (c.mode == 1) f(O, S, M1(), R1(), R1());
+    if (c.mode == 2) f(O, S, M2(), R1(), R1());
   };
-  if (order == 1 && scheme == 1) go(I1(), I1());
-  if (order == 1 && scheme == 2) go(I1(), I2());
-  if (order == 2 && scheme == 1) go(I2(), I1());
-  if (order == 2 && scheme == 2) go(I2(), I2());
+  if (c.order == 1 && c.scheme == 1) go(I1(), I1());
+  if (c.order == 1 && c.scheme == 2) go(I1(), I2());
+  if (c.order == 2 && c.scheme == 1) go(I2(), I1());
+  if (c.order == 2 && c.scheme == 2) go(I2(), I2());
 }
 
-size_t smem_c(const Es1dMixConst &c) { return (size_t)c.nc * (8 + 4 + (c.mode == 2 ? 8 : 0)); }
-size_t smem_e(const Es1dMixConst &c) { return (size_t)c.nc * (8 + 8 + (c.mode == 2 ? 8 : 0)); }
+int tile_copies(const Es1dMixConst &c) { return c.mode == 0 && c.wide ? 32 : 1; }
+int table_copies(const Es1dMixConst &c) { return c.mode == 0 && c.wide ? 16 : 1; }
+size_t npad_host(const Es1dMixConst &c) { return (size_t)c.nc + 3; }
+size_t smem_c(const Es1dMixConst &c) {
+  return npad_host(c) * (8 * tile_copies(c) + 4 * table_copies(c)) + (c.mode == 2 ? 8 * c.nc : 0);
+}
+size_t smem_e(const Es1dMixConst &c) {
+  return npad_host(c) * (8 * tile_copies(c) + 8 * table_copies(c)) + (c.mode == 2 ? 8 * c.nc : 0);
+}
 
 }  // namespace
 
 cudaError_t es1d_mix_prepare(const Es1dMixConst &c) {
   cudaError_t e = cudaSuccess;
-  dispatch_mix(c.order, c.scheme, c.mode, [&](auto O, auto S, auto M) {
+  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
-    constexpr int MODE = decltype(M)::value;
-    e = cudaFuncSetAttribute(mix_pass_c_kernel<ORDER, SCHEME, MODE>,
+    constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
+    e = cudaFuncSetAttribute(mix_pass_c_kernel<ORDER, SCHEME, MODE, NT, NE>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c(c));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mix_pass_e_kernel<ORDER, SCHEME, MODE>,
+      e = cudaFuncSetAttribute(mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e(c));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mix_deposit_initial_kernel<ORDER>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * c.nc));
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * npad_host(c)));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mix_charge_kernel<ORDER>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * c.nc));
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * npad_host(c)));
   });
   return e;
 }
@@ -798,42 +1007,45 @@ cudaError_t es1d_mix_prepare(const Es1dMixConst &c) {
 void es1d_mix_pass_c(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_index, int slot,
                      LaunchShape ls, cudaStream_t st) {
   int par = (int)(step_index & 1);
-  dispatch_mix(c.order, c.scheme, c.mode, [&](auto O, auto S, auto M) {
+  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
-    constexpr int MODE = decltype(M)::value;
-    mix_pass_c_kernel<ORDER, SCHEME, MODE><<<ls.grid, ls.block, smem_c(c), st>>>(c, b, par,
-                                                                                 slot - 1, ls.grid);
+    constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
+    mix_pass_c_kernel<ORDER, SCHEME, MODE, NT, NE>
+        <<<ls.grid, ls.block, smem_c(c), st>>>(c, b, par, slot - 1, ls.grid);
   });
 }
 
 void es1d_mix_pass_e(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_index, int slot,
                      LaunchShape ls, cudaStream_t st) {
   int par = (int)(step_index & 1);
-  dispatch_mix(c.order, c.scheme, c.mode, [&](auto O, auto S, auto M) {
+  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
-    constexpr int MODE = decltype(M)::value;
-    mix_pass_e_kernel<ORDER, SCHEME, MODE><<<ls.grid, ls.block, smem_e(c), st>>>(c, b, par, slot);
+    constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
+    mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE>
+        <<<ls.grid, ls.block, smem_e(c), st>>>(c, b, par, slot);
   });
 }
 
 void es1d_mix_deposit_initial(const Es1dMixConst &c, const Es1dMixBufs &b, int parity,
                               LaunchShape ls, cudaStream_t st) {
+  const size_t sm = 8 * npad_host(c);
   if (c.order == 1)
-    mix_deposit_initial_kernel<1><<<ls.grid, ls.block, 8 * c.nc, st>>>(c, b, parity);
+    mix_deposit_initial_kernel<1><<<ls.grid, 512, sm, st>>>(c, b, parity);
   else
-    mix_deposit_initial_kernel<2><<<ls.grid, ls.block, 8 * c.nc, st>>>(c, b, parity);
+    mix_deposit_initial_kernel<2><<<ls.grid, 512, sm, st>>>(c, b, parity);
 }
 
 void es1d_mix_charge(const Es1dMixConst &c, const Es1dMixBufs &b, long long *count,
                      LaunchShape ls, cudaStream_t st) {
+  const size_t sm = 8 * npad_host(c);
   if (c.order == 1)
-    mix_charge_kernel<1><<<ls.grid, ls.block, 8 * c.nc, st>>>(c, b, count);
+    mix_charge_kernel<1><<<ls.grid, 512, sm, st>>>(c, b, count);
   else
-    mix_charge_kernel<2><<<ls.grid, ls.block, 8 * c.nc, st>>>(c, b, count);
+    mix_charge_kernel<2><<<ls.grid, 512, sm, st>>>(c, b, count);
 }
 
 void es1d_mix_finalize(const Es1dMixBufs &b, int slot, int nblocks, cudaStream_t st) {
-  mix_finalize_kernel<<<1, 256, 0, st>>>(b, slot, nblocks);
+  mix_finalize_kernel<<<1, 1024, 0, st>>>(b, slot, nblocks);
 }
 
 void es1d_mix_from_fp64(const Es1dMixConst &c, const double *x, const double *v, Es1dMixBufs &b,

@@ -86,6 +86,7 @@ struct pic_handle {
   // 1D mixed-precision state
   bool mixed = false;
   Es1dMixConst cm{};
+  LaunchShape lmix{1, 512};  // passes C and E of the mixed form
   Es1dMixBufs bm{};
   Es1dMixBufs bm_alt{};     // the counting sort's destination (swapped after a sort)
   int64_t *ids_alt = nullptr;
@@ -268,27 +269,57 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   double cx = c.dt * 2147483648.0 / c.L;
   double vcap = std::max(8.0 * vmax, 1e-6 * c.L / c.dt);
   int kv = (int)std::floor(std::log2(1073741824.0 / (cx * vcap)));
-  m.kv = std::min(24, std::max(0, kv));
+  // kv >= 1 keeps the half-step shift a plain rounded shift (the range check
+  // on every V* reports speeds that no longer fit 31 bits)
+  m.kv = std::min(24, std::max(1, kv));
+  m.hround = 1 << (m.kv - 1);
   m.cxk = std::ldexp(cx, m.kv);
-  // Terms round(V* s / 2^r) are below 2^T = 2^(54 - r).  A block adds at most
-  // pblk markers to a node; its split counters need pblk 2^16 < 2^32 (low
-  // halves) and pblk 2^(T-16) < 2^31 (signed rest), so T = 47 - ceil(log2 pblk);
-  // the int64 grid sums need N 2^T < 2^63.
+  m.mode = h->cfg.sort_period == 1 ? 2 : (h->cfg.sort_period > 1 ? 1 : 0);
+  m.wide = m.mode == 0 && c.nc <= kWideMaxNodes;
   const int64_t ngroups = (h->N + 3) / 4;
-  const int64_t trips = (ngroups + (int64_t)h->ls.grid * 512 - 1) / ((int64_t)h->ls.grid * 512);
-  const int64_t pblk = std::max<int64_t>(1, trips * 512 * 4);
+  if (m.wide) {
+    // one wave of 1024-thread blocks, one per SM (the per-copy marker count is
+    // checked against the counters' bound below)
+    const int64_t want = std::min<int64_t>((ngroups + 1023) / 1024, h->nsm);
+    h->lmix = LaunchShape{(int)std::max<int64_t>(1, want), 1024};
+  } else {
+    h->lmix = h->ls;
+  }
+  // Terms round(V* s / 2^r) are below 2^T = 2^(54 - r).  At most pcnt markers
+  // add into one tile copy of a block; its split counters need pcnt 2^16 <
+  // 2^32 (low halves) and pcnt 2^(T-16) < 2^31 (signed rest), so T = 47 -
+  // ceil(log2 pcnt); the int64 grid sums need N 2^T < 2^63.  pcnt is the
+  // markers of a 512-thread block of the single-copy launch (at least 2048);
+  // a copy of the wide tile (4 markers per trip from each of 32 threads) is
+  // held to the same count, and one r for every mode keeps the results
+  // independent of the marker order.
+  const int64_t threads = (int64_t)h->ls.grid * 512;
+  const int64_t trips = (ngroups + threads - 1) / threads;
+  const int64_t pcnt = std::max<int64_t>(1, trips * 512 * 4);
+  if (m.wide) {
+    const int64_t wthreads = (int64_t)h->lmix.grid * 1024;
+    const int64_t wtrips = (ngroups + wthreads - 1) / wthreads;
+    if (wtrips * 128 > pcnt) {
+      const int64_t grid = (ngroups * 128 + pcnt * 1024 - 1) / (pcnt * 1024);
+      h->lmix.grid = (int)std::max<int64_t>(h->lmix.grid, grid);
+    }
+  }
   int lg = 0;
-  while (((int64_t)1 << lg) < pblk) lg++;
+  while (((int64_t)1 << lg) < pcnt) lg++;
   int T = std::min(37, 47 - lg);
   int bitlen = 0;
   while (bitlen < 62 && ((int64_t)1 << bitlen) <= h->N) bitlen++;
   T = std::min(T, 62 - bitlen);
   m.rshift = 54 - T;
+  if (m.rshift < 17 || m.rshift > 31)
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: %lld markers need a deposit shift of %d (17..31)",
+                (long long)h->N, m.rshift);
+  m.rnd = 1ll << (m.rshift - 1);
   m.jscale = S.q * S.w0 * std::ldexp(1.0, m.rshift) / (c.h * m.cxk * 8388608.0);
+  m.jscale_n = m.jscale / c.nc;
   m.ke_scale = 0.5 * S.m * S.w0 / (m.cxk * m.cxk);
-  m.e_scale = (float)(0.5 * c.dt * S.q / S.m * m.cxk);
-  m.mode = h->cfg.sort_period == 1 ? 2 : (h->cfg.sort_period > 1 ? 1 : 0);
-  m.cd = ff_from_double(c.dt * S.q / S.m * m.cxk);
+  m.e_scale = 0.5 * c.dt * S.q / S.m * m.cxk;
+  m.kick = c.dt * S.q / S.m * m.cxk;
   CUDA_TRY(es1d_mix_prepare(m));
   Es1dMixBufs &bm = h->bm;
   size_t npad = (size_t)((h->N + 3) / 4 * 4);
@@ -296,14 +327,16 @@ int init_mixed(pic_handle *h, bool solve_e0) {
       (rc = h->alloc(&bm.Vs, npad)))
     return rc;
   for (int k = 0; k < 2; k++)
-    if ((rc = h->alloc(&bm.J1[k], c.nc)) || (rc = h->alloc(&bm.J2[k], c.nc))) return rc;
+    if ((rc = h->alloc(&bm.J1[k], (size_t)c.nc * kJStride)) ||
+        (rc = h->alloc(&bm.J2[k], (size_t)c.nc * kJStride)))
+      return rc;
   CUDA_TRY(cudaMemsetAsync(bm.X, 0, sizeof(uint32_t) * npad, h->st));
   CUDA_TRY(cudaMemsetAsync(bm.vh, 0, sizeof(float) * npad, h->st));
   CUDA_TRY(cudaMemsetAsync(bm.vl, 0, sizeof(float) * npad, h->st));
   for (int k = 0; k < 2; k++) {
     bm.E[k] = b.E[k];
-    CUDA_TRY(cudaMemsetAsync(bm.J1[k], 0, sizeof(long long) * c.nc, h->st));
-    CUDA_TRY(cudaMemsetAsync(bm.J2[k], 0, sizeof(long long) * c.nc, h->st));
+    CUDA_TRY(cudaMemsetAsync(bm.J1[k], 0, sizeof(long long) * c.nc * kJStride, h->st));
+    CUDA_TRY(cudaMemsetAsync(bm.J2[k], 0, sizeof(long long) * c.nc * kJStride, h->st));
   }
   bm.ke_part = b.ke_part;
   bm.fallback = b.fallback;
@@ -465,8 +498,8 @@ int restart_es1d(pic_handle *h, bool particles_changed) {
   if (h->mixed) {
     Es1dMixBufs &bm = h->bm;
     for (int k = 0; k < 2; k++) {
-      CUDA_TRY(cudaMemsetAsync(bm.J1[k], 0, sizeof(long long) * h->cm.nc, h->st));
-      CUDA_TRY(cudaMemsetAsync(bm.J2[k], 0, sizeof(long long) * h->cm.nc, h->st));
+      CUDA_TRY(cudaMemsetAsync(bm.J1[k], 0, sizeof(long long) * h->cm.nc * kJStride, h->st));
+      CUDA_TRY(cudaMemsetAsync(bm.J2[k], 0, sizeof(long long) * h->cm.nc * kJStride, h->st));
     }
     // the FP64 staging arrays hold the new markers only after pic_set_particles
     if (particles_changed) es1d_mix_from_fp64(h->cm, b.x, b.v, bm, h->ls, h->st);
@@ -673,7 +706,6 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
     h->ls.grid = (int)std::max<int64_t>(h->ls.grid, need);
   }
   h->nsm = nsm;
-  h->nsm = nsm;
   h->em = cfg->solver == PIC_SOLVER_YEE_LEAPFROG;
   int rc = h->em ? init_em2d(h, species, E0, B0) : init_es1d(h, species, E0);
   if (rc) {
@@ -721,14 +753,14 @@ int pic_step_async(pic_handle *h, int nsteps) {
         if (rc) return rc;
       }
       CUDA_TRY(h->timed_launch(0, [&] {
-        es1d_mix_pass_c(h->cm, h->bm, h->steps_done, h->pending, h->ls, h->st);
+        es1d_mix_pass_c(h->cm, h->bm, h->steps_done, h->pending, h->lmix, h->st);
       }));
       if (h->cm.mode == 2) {
-        CUDA_TRY(h->timed_launch(3, [&] { es1d_mix_fused_scan(h->cm, h->bm, h->ls.grid, h->st); }));
+        CUDA_TRY(h->timed_launch(3, [&] { es1d_mix_fused_scan(h->cm, h->bm, h->lmix.grid, h->st); }));
         h->launches += 1;
       }
       CUDA_TRY(h->timed_launch(1, [&] {
-        es1d_mix_pass_e(h->cm, h->bm, h->steps_done, h->pending, h->ls, h->st);
+        es1d_mix_pass_e(h->cm, h->bm, h->steps_done, h->pending, h->lmix, h->st);
       }));
       if (h->cm.mode == 2) swap_sorted_output(h);
     } else {
@@ -758,7 +790,7 @@ int pic_read_stats(pic_handle *h, int capacity, int64_t *nfallback_per_step, dou
   if (!h->em) {
     CUDA_TRY(h->timed_launch(2, [&] {
       if (h->mixed)
-        es1d_mix_finalize(h->bm, n - 1, h->ls.grid, h->st);
+        es1d_mix_finalize(h->bm, n - 1, h->lmix.grid, h->st);
       else
         es1d_fp64_finalize(h->c1, b, n - 1, h->ls.grid, h->st);
     }));

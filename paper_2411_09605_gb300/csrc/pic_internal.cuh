@@ -56,14 +56,26 @@ struct Es1dMixConst {
   int rshift;          // deposit term = round(V* s_k / 2^rshift)
   int kv;              // one V unit = 2^-kv position units per half step
   int mode;            // 0 unsorted, 1 periodic counting sort, 2 sorted on write every step
+  int wide;            // unsorted with nc <= kWideMaxNodes: per-lane tile copies, 1024-thread blocks
+  int hround;          // 2^(kv - 1), kv >= 1
+  long long rnd;       // 2^(rshift - 1)
   int64_t n;
   double L, h, dt;
   double cxk;          // (dt 2^31 / L) 2^kv
   double jscale;       // J_h = jscale * (integer node sum)
+  double jscale_n;     // jscale / nc
   double ke_scale;     // (m w / 2) / cxk^2
-  float e_scale;       // dt/2 (q/m) cxk: E** -> increment of v* in V units
-  ff cd;               // dt (q/m) cxk as a float pair
+  double e_scale;      // dt/2 (q/m) cxk: E** -> increment of v* in V units
+  double kick;         // dt (q/m) cxk: E^{n+1/2} -> v^dag - v^n in V units
 };
+
+// Unsorted mixed form: grids up to this many nodes use 32 copies of the
+// current tile and 16 of the field tables per block (one 1024-thread block per
+// SM); larger grids one copy (512-thread blocks).
+constexpr int kWideMaxNodes = 512;
+// Mixed-form integer node sums J1, J2 hold node i at [i * kJStride]: one node
+// per 128-byte line, so the blocks' global atomics spread over the L2 slices.
+constexpr int kJStride = 16;
 
 struct Es1dMixBufs {
   uint32_t *X;              // [N padded to 4] positions, x = X L / 2^32
