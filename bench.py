@@ -33,12 +33,25 @@ UNIT = "particle-steps/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20          # > 2x the 126.5 MB L2
-# Algorithmic bytes per marker per launch (state that must cross HBM once per
-# barrier-separated pass; v* is recomputed in pass E, never stored).
-ALGO_BYTES = {  # (precision, kind) -> bytes per marker
-    ("fp64", 0): 16, ("fp64", 1): 32,      # pass C reads x, v; pass E reads + writes
-    ("mixed", 0): 8, ("mixed", 1): 24,     # pass C reads X and vh; pass E X, vh, vl both ways
+# Algorithmic bytes per marker per launch: the state that must cross HBM once per
+# barrier-separated pass.  FP64 form: pass C reads x, v; pass E reads and writes
+# them (v* is recomputed).  Mixed form: pass C reads X, vh, vl and writes the
+# integer V*; pass E reads X, vh, vl, V* and writes X, vh, vl.
+ALGO_BYTES = {  # (form, kernel kind) -> bytes per marker
+    ("fp64", 0): 16, ("fp64", 1): 32,
+    ("mixed", 0): 16, ("mixed", 1): 28,
 }
+# The FP64 form is bound by the FP64 pipe (2 thread-instructions per SM and
+# clock on this part), not by HBM: its roofline counts FP64-pipe thread
+# instructions per marker, measured once with ncu
+# (sm__thread_inst_executed_pipe_fp64_pred_on.sum / markers) on these kernels.
+FP64_INST_PER_MARKER = {("fp64", 0): 53.5, ("fp64", 1): 115.7}
+FP64_LANES_PER_SM_CLK = 2
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+# ncu capture of the current kernels on this workload (2^23 markers); None where
+# the kernel changed since it was taken.
+TRAFFIC = {("mixed", 0): 111886080, ("mixed", 1): 178013696,
+           ("fp64", 0): 155024384, ("fp64", 1): 226543872}
 
 
 def parse():
@@ -54,7 +67,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=20)
-    ap.add_argument("--sort-period", type=int, default=8,
+    ap.add_argument("--sort-period", type=int, default=0,
                     help="cell sort of the mixed form every this many steps (0 = never)")
     return ap.parse_args()
 
@@ -169,6 +182,29 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def roofline(form, kname, k, markers, hbm_peak, hbm_src, clocks, nsm):
+    """Roofline of the form's dominant kernel: HBM bytes for the mixed form, FP64-
+    pipe thread instructions for the FP64 form (achieved = algorithmic work per
+    launch / average event-timed launch duration)."""
+    t = k["avg_us"] * 1e-6
+    if form == "fp64":
+        inst = FP64_INST_PER_MARKER[(form, k["kind"])] * markers
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak = FP64_LANES_PER_SM_CLK * nsm * mhz * 1e6 / 1e9
+        ach = inst / t / 1e9
+        return {"bound": "alu", "kernel": kname, "achieved": round(ach, 1), "peak": round(peak, 1),
+                "unit": "Ginst/s (FP64 pipe)", "frac": round(ach / peak, 4),
+                "traffic": TRAFFIC.get((form, k["kind"])),
+                "peak_source": f"{FP64_LANES_PER_SM_CLK} FP64 lanes/SM/clk x {nsm} SMs x {mhz:.0f} MHz",
+                "algorithmic_fp64_inst_per_launch": inst}
+    algo = ALGO_BYTES[(form, k["kind"])] * markers
+    ach = algo / t / 1e9
+    return {"bound": "hbm", "kernel": kname, "achieved": round(ach, 1), "peak": hbm_peak,
+            "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+            "traffic": TRAFFIC.get((form, k["kind"])), "peak_source": hbm_src,
+            "algorithmic_bytes_per_launch": algo}
+
+
 def time_form(prob, precision_name: str, steps: int, warmup: int, profile_steps: int, stream,
               flush_buf, sort_period: int = 0):
     """Device-timed throughput of one library form on the resident workload."""
@@ -267,7 +303,7 @@ def e2e_form(prob, precision_name: str, steps: int, warmup: int, sort_period: in
     return {"s_per_step": float(np.mean(times)), "h2d": 16 * n, "d2h": 16 * n + 16}
 
 
-def cpu_baseline_oracle(markers: int, seed: int, budget_s: float = 12.0, max_steps: int = 40):
+def cpu_baseline_oracle(markers: int, seed: int, budget_s: float = 12.0, max_steps: int = 200):
     """The FP64 C oracle, as it stands, on a bounded sample of the workload."""
     from oracle import oracle as O
     prob = workload(markers, seed)
@@ -337,17 +373,17 @@ def run_ours(args):
         kern = f["kernels"]
         dom = max(kern.items(), key=lambda kv: kv[1]["avg_us"] * kv[1]["launches"])
         dname, d = dom
-        algo = ALGO_BYTES.get((name, d["kind"]), 0) * prob.n_markers
-        ach = algo / (d["avg_us"] * 1e-6) / 1e9
         out_forms[name] = {
             "value": units / t_max, "ms_per_step": 1e3 * t_max / args.steps,
             "max_rel_dTE": f["max_rel_dTE"], "fallbacks": f["fallbacks"],
             "gpu_launches": f["launches"],
             "kernels_us": {k: round(v["avg_us"], 2) for k, v in kern.items()},
-            "roofline": {"bound": "hbm", "kernel": dname, "achieved": round(ach, 1),
-                         "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-                         "traffic": None, "peak_source": peak_src,
-                         "algorithmic_bytes_per_launch": algo},
+            "roofline": roofline(name, dname, d, prob.n_markers, peak, peak_src, clocks,
+                                 torch.cuda.get_device_properties(dev).multi_processor_count),
+            "roofline_hbm_by_kernel": {
+                k: round(ALGO_BYTES[(name, v["kind"])] * prob.n_markers / (v["avg_us"] * 1e-6)
+                         / 1e9 / peak, 4)
+                for k, v in kern.items() if (name, v["kind"]) in ALGO_BYTES},
         }
     hf = out_forms[head]
     line = {

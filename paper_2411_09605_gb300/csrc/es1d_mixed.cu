@@ -328,17 +328,24 @@ __device__ __forceinline__ double block_sum_sparse(double v, int nactive) {
   return t;
 }
 
-// TE of a finished step: the blocks' kinetic partials (one load per thread)
-// plus W_E of the step's final field (computed by pass E).
-__device__ __forceinline__ void finalize_stats_mix(const Es1dMixBufs &b, int slot, int nblocks) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += b.ke_part[i];
+// TE of a finished step from the blocks' partials of the kinetic energy and
+// of sum E^2 (pass E); first = this thread's first pair, loaded early by the
+// caller so that its latency overlaps other work.
+__device__ __forceinline__ void finalize_stats_mix(const Es1dMixBufs &b, double h, int slot,
+                                                   int nblocks, double first) {
+  double s = first;
+  for (int i = threadIdx.x + blockDim.x; i < nblocks; i += blockDim.x)
+    s += b.ke_part[i] + 0.5 * h * b.we_part[i];
   const double t = block_sum_sparse(s, nblocks < (int)blockDim.x ? nblocks : (int)blockDim.x);
   if (threadIdx.x == 0) {
-    const double te = t + b.we[0];
-    b.te[slot] = te;
-    if (!isfinite(te)) atomicOr(b.err, kErrNonfinite);
+    b.te[slot] = t;
+    if (!isfinite(t)) atomicOr(b.err, kErrNonfinite);
   }
+}
+
+__device__ __forceinline__ double finalize_first(const Es1dMixBufs &b, double h, int nblocks) {
+  return (int)threadIdx.x < nblocks ? b.ke_part[threadIdx.x] + 0.5 * h * b.we_part[threadIdx.x]
+                                    : 0.0;
 }
 
 // Ors the flags of a warp's lanes into the error word (one atomic per warp).
@@ -544,11 +551,13 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
   unsigned *Jt = (unsigned *)smraw;           // [npad][2][RT]
   float *Es = (float *)(Jt + 2 * RT * npad);  // [npad][RE]: dt/2 (q/m) cxk E*
   uint32_t *hist = (uint32_t *)(Es + RE * npad);  // MODE 2: keys of the markers after the step
+  double fin0 = 0.0;  // block 0: partials of the previous step's TE
   {
     // E* = E - dt/2 (J1 - <J1>) at every padded node, scaled to the v* kick;
     // the first node's loads are issued before the block-wide mean
     const double *E = PSEL(b.E, par);
     const long long *J1 = PSEL(b.J1, par);
+    if (blockIdx.x == 0 && prev_slot >= 0) fin0 = finalize_first(b, c.h, prev_nblocks);
     const int i0 = wrap_node((int)threadIdx.x - PAD, c.nc);
     const bool has0 = (int)threadIdx.x < npad;
     const double E0 = has0 ? E[i0] : 0.0;
@@ -569,7 +578,7 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
   if (blockIdx.x == 0) {
     if (SCHEME == 2)
       for (int i = threadIdx.x; i < c.nc; i += blockDim.x) PSEL(b.J1, par ^ 1)[i * kJStride] = 0;
-    if (prev_slot >= 0) finalize_stats_mix(b, prev_slot, prev_nblocks);
+    if (prev_slot >= 0) finalize_stats_mix(b, c.h, prev_slot, prev_nblocks, fin0);
   }
   __syncthreads();
   const unsigned lane = threadIdx.x & 31u;
@@ -645,7 +654,6 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
     const double E0 = has0 ? E[i0] : 0.0;
     const long long J0 = has0 ? J2[i0 * kJStride] : 0;
     const double mean2 = c.remove_mean ? block_mean_j(J2, c.nc, c.jscale_n) : 0.0;
-    double we_loc = 0.0;
     for (int q = threadIdx.x; q < npad; q += blockDim.x) {
       const int i = wrap_node(q - PAD, c.nc);
       const bool first = q == (int)threadIdx.x;
@@ -656,13 +664,21 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
       if (blockIdx.x == 0 && q - PAD == i) {
         PSEL(b.E, par ^ 1)[i] = en;
         PSEL(b.J2, par ^ 1)[i * kJStride] = 0;
-        we_loc = fma(en, en, we_loc);
       }
     }
-    if (blockIdx.x == 0) {
-      const int nact = c.nc + PAD < (int)blockDim.x ? c.nc + PAD : (int)blockDim.x;
-      const double t = block_sum_sparse(we_loc, nact);
-      if (threadIdx.x == 0) b.we[0] = 0.5 * c.h * t;
+    // sum (E^{n+1})^2 in per-block partials: warp 0 of block b recomputes
+    // E^{n+1} (the same expression) on the nodes [b nc / grid, (b + 1) nc / grid)
+    if (threadIdx.x < 32) {
+      const int n0 = (int)((int64_t)c.nc * blockIdx.x / gridDim.x);
+      const int n1 = (int)((int64_t)c.nc * (blockIdx.x + 1) / gridDim.x);
+      double w = 0.0;
+      for (int i = n0 + (int)threadIdx.x; i < n1; i += 32) {
+        const double en = E[i] - c.dt * ((double)J2[i * kJStride] * c.jscale - mean2);
+        w = fma(en, en, w);
+      }
+      if (n1 > n0)
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      if (threadIdx.x == 0) b.we_part[blockIdx.x] = w;
     }
   }
   clear_tile<RT>(Jt, npad);
@@ -795,8 +811,8 @@ __global__ void __launch_bounds__(512) mix_charge_kernel(Es1dMixConst c, Es1dMix
   flush_tile_i64<ORDER>(Jt, count, c.nc, 1);
 }
 
-__global__ void mix_finalize_kernel(Es1dMixBufs b, int slot, int nblocks) {
-  finalize_stats_mix(b, slot, nblocks);
+__global__ void mix_finalize_kernel(Es1dMixBufs b, double h, int slot, int nblocks) {
+  finalize_stats_mix(b, h, slot, nblocks, finalize_first(b, h, nblocks));
 }
 
 // FP64 (x, v) <-> (X, vh, vl) with v stored in V units (v * cxk)
@@ -1044,8 +1060,9 @@ void es1d_mix_charge(const Es1dMixConst &c, const Es1dMixBufs &b, long long *cou
     mix_charge_kernel<2><<<ls.grid, 512, sm, st>>>(c, b, count);
 }
 
-void es1d_mix_finalize(const Es1dMixBufs &b, int slot, int nblocks, cudaStream_t st) {
-  mix_finalize_kernel<<<1, 1024, 0, st>>>(b, slot, nblocks);
+void es1d_mix_finalize(const Es1dMixConst &c, const Es1dMixBufs &b, int slot, int nblocks,
+                       cudaStream_t st) {
+  mix_finalize_kernel<<<1, 1024, 0, st>>>(b, c.h, slot, nblocks);
 }
 
 void es1d_mix_from_fp64(const Es1dMixConst &c, const double *x, const double *v, Es1dMixBufs &b,

@@ -87,6 +87,7 @@ struct pic_handle {
   bool mixed = false;
   Es1dMixConst cm{};
   LaunchShape lmix{1, 512};  // passes C and E of the mixed form
+  double *energy_part = nullptr;  // pic_energy's kinetic partials (ke_part may be in use)
   Es1dMixBufs bm{};
   Es1dMixBufs bm_alt{};     // the counting sort's destination (swapped after a sort)
   int64_t *ids_alt = nullptr;
@@ -342,6 +343,8 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   bm.fallback = b.fallback;
   bm.te = b.te;
   bm.we = b.we;
+  if ((rc = h->alloc(&bm.we_part, (size_t)h->ls.grid))) return rc;
+  CUDA_TRY(cudaMemsetAsync(bm.we_part, 0, sizeof(double) * h->ls.grid, h->st));
   bm.err = b.err;
   if (h->cfg.sort_period > 0) {
     Es1dMixBufs &alt = h->bm_alt;
@@ -426,7 +429,8 @@ int init_es1d(pic_handle *h, const pic_species *species, const double *E0) {
     if ((rc = h->alloc(&b.E[k], nc)) || (rc = h->alloc(&b.J1[k], nc)) ||
         (rc = h->alloc(&b.J2[k], nc)))
       return rc;
-  if ((rc = h->alloc(&b.ke_part, h->ls.grid)) || (rc = h->alloc(&b.fallback, kStepsCap)) ||
+  if ((rc = h->alloc(&b.ke_part, h->ls.grid)) || (rc = h->alloc(&h->energy_part, h->ls.grid)) ||
+      (rc = h->alloc(&b.fallback, kStepsCap)) ||
       (rc = h->alloc(&b.te, kStepsCap)) || (rc = h->alloc(&b.we, 1)) ||
       (rc = h->alloc(&b.err, 1)) || (rc = h->alloc(&h->ids, h->N)))
     return rc;
@@ -790,7 +794,7 @@ int pic_read_stats(pic_handle *h, int capacity, int64_t *nfallback_per_step, dou
   if (!h->em) {
     CUDA_TRY(h->timed_launch(2, [&] {
       if (h->mixed)
-        es1d_mix_finalize(h->bm, n - 1, h->lmix.grid, h->st);
+        es1d_mix_finalize(h->cm, h->bm, n - 1, h->lmix.grid, h->st);
       else
         es1d_fp64_finalize(h->c1, b, n - 1, h->ls.grid, h->st);
     }));
@@ -898,9 +902,10 @@ int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, 
   if (!h) return fail(PIC_ERR_ARG, "pic_energy: NULL handle");
   if (h->em) return energy_em2d(h, KE_per_species, W_E, W_B, TE);
   const Es1dConst &c = h->c1;
-  double *ke_d = h->b1.ke_part;  // reuse: nsp <= grid entries are needed
+  // own partials: the stepping kernels keep the last step's partials in ke_part
+  // until the next step (or pic_read_stats) has reduced them
+  double *ke_d = h->energy_part;
   if (h->ls.grid < h->nsp) return fail(PIC_ERR_ARG, "pic_energy: internal size");
-  // ke_part is only consumed during pic_step; it is safe to reuse between calls.
   std::vector<double> ke(h->nsp), e(c.nc);
   if (h->mixed) {
     es1d_mix_kinetic(h->cm, h->bm, ke_d, h->ls.grid, h->st);

@@ -93,6 +93,7 @@ struct Es1dMixBufs {
   unsigned long long *fallback;
   double *te;
   double *we;
+  double *we_part;          // [grid] per-block W_E partials of the newest field
   unsigned *err;
 };
 
@@ -193,7 +194,8 @@ void es1d_mix_pass_e(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_i
                      LaunchShape ls, cudaStream_t st);
 void es1d_mix_deposit_initial(const Es1dMixConst &c, const Es1dMixBufs &b, int parity,
                               LaunchShape ls, cudaStream_t st);
-void es1d_mix_finalize(const Es1dMixBufs &b, int slot, int nblocks, cudaStream_t st);
+void es1d_mix_finalize(const Es1dMixConst &c, const Es1dMixBufs &b, int slot, int nblocks,
+                       cudaStream_t st);
 void es1d_mix_charge(const Es1dMixConst &c, const Es1dMixBufs &b, long long *count,
                      LaunchShape ls, cudaStream_t st);
 void es1d_mix_from_fp64(const Es1dMixConst &c, const double *x, const double *v, Es1dMixBufs &b,
