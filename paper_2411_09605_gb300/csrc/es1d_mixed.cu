@@ -255,24 +255,18 @@ __device__ __forceinline__ double block_sum_d(double s, double *red) {
   return t;  // thread 0
 }
 
-// Mean of jscale J over the grid from the exact integer sum (node i at
-// J[i kJStride]): the same value in every block, and FP64 (a narrow pipe on
-// this part) only in thread 0.
-__device__ __forceinline__ double block_mean_j(const long long *J, int n, double jscale_n) {
-  __shared__ long long ired[32];
-  __shared__ double mean;
-  long long s = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += J[i * kJStride];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31u) == 0u) ired[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    long long t = threadIdx.x < (blockDim.x >> 5) ? ired[threadIdx.x] : 0;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) mean = (double)t * jscale_n;
-  }
-  __syncthreads();
-  return mean;
+// An int64 as a float pair (about 48 bits): the rounded value and the exact
+// integer remainder.
+__device__ __forceinline__ ff ff_from_i64(long long J) {
+  const float hi = __ll2float_rn(J);
+  const long long rem = J - __float2ll_rz(hi);  // hi holds an integer value
+  return {hi, __ll2float_rn(rem)};
+}
+
+// Grid mean <J> of integer node sums from their exact total (read by every
+// thread; no block reduction): in J units as a float pair.
+__device__ __forceinline__ ff mean_of_total(long long total, const Es1dMixConst &c) {
+  return ff_mul(ff_from_i64(total), c.inv_nc);
 }
 
 // Zeroes 2 RT npad counters (RT > 1: the count is a multiple of 4, 16-byte aligned).
@@ -286,12 +280,16 @@ __device__ __forceinline__ void clear_tile(unsigned *Jt, int npad) {
   }
 }
 
-// Sums the tile's copies node by node (one thread per padded node) and adds
-// each node's total to J[node kJStride] with one 64-bit global atomic (ghost
-// nodes add to the node they stand for).
+// Sums the tile's copies node by node (one thread per padded node), adds each
+// node's total to J[node kJStride] with one 64-bit global atomic (ghost nodes
+// add to the node they stand for) and the block's total to *total (exact
+// integers, so the grid total does not depend on the order of the blocks).
 template <int ORDER, int RT>
-__device__ __forceinline__ void flush_tile(const unsigned *Jt, long long *J, int nc) {
+__device__ __forceinline__ void flush_tile(const unsigned *Jt, long long *J, long long *total,
+                                           int nc) {
+  __shared__ long long tred[32];
   const int npad = npad_of(nc);
+  long long mine = 0;
   for (int q = threadIdx.x; q < npad; q += blockDim.x) {
     long long lo = 0, hi = 0;
     // copies read in an order skewed by the node: the 32 lanes of a warp
@@ -303,9 +301,18 @@ __device__ __forceinline__ void flush_tile(const unsigned *Jt, long long *J, int
       hi += (int)Jt[q * 2 * RT + RT + kk];
     }
     const long long a = hi * 65536ll + lo;
+    mine += a;
     if (a != 0)
       atomicAdd((unsigned long long *)&J[wrap_node(q - Pad<ORDER>::kPad, nc) * kJStride],
                 (unsigned long long)a);
+  }
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31u) == 0u) tred[threadIdx.x >> 5] = mine;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    long long t = threadIdx.x < (blockDim.x >> 5) ? tred[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0 && t != 0) atomicAdd((unsigned long long *)total, (unsigned long long)t);
   }
 }
 
@@ -346,6 +353,15 @@ __device__ __forceinline__ void finalize_stats_mix(const Es1dMixBufs &b, double 
 __device__ __forceinline__ double finalize_first(const Es1dMixBufs &b, double h, int nblocks) {
   return (int)threadIdx.x < nblocks ? b.ke_part[threadIdx.x] + 0.5 * h * b.we_part[threadIdx.x]
                                     : 0.0;
+}
+
+// Programmatic dependent launch: the passes are launched so that a kernel may
+// start while the previous one finishes; griddepcontrol.wait blocks until the
+// previous kernel has completed and its writes are visible, and
+// launch_dependents lets the next kernel be scheduled early.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Ors the flags of a warp's lanes into the error word (one atomic per warp).
@@ -413,23 +429,34 @@ __device__ __forceinline__ ff gather_kick(const float2 *El, const ShapeMix<ORDER
 // the series t/2 - t^2/8 + t^3/16 - 5t^4/128 (relative error < 2^-33) replaces
 // the correctly rounded sqrt and divide.  R < 0 is t < -1; that and v^dag = 0
 // (t not finite) fall back to Gamma = 1 and are counted.
+// a / b by one correction of the hardware reciprocal estimate r with the
+// exact FMA residual (Markstein's FMA division): q0 = a r, e = a - q0 b,
+// q = q0 + e r.  Before its final rounding q is within about 2^-44 |a/b| of
+// the quotient, so q is the correctly rounded quotient except next to a tie
+// (then one ulp off, either way).  b = 0 or a subnormal b give a non-finite or
+// huge q.
+__device__ __forceinline__ float div_rcp_residual(float a, float b) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(b));
+  const float q0 = __fmul_rn(a, r);
+  const float e = __fmaf_rn(-q0, b, a);
+  return __fmaf_rn(e, r, q0);
+}
+
 __device__ __forceinline__ ff correct_velocity(float vh, float vl, int Vs, ff d, bool on,
                                                unsigned &nfb) {
   const ff vd = ff_add(ff{vh, vl}, d);
   if (!on) return vd;
-  // b = v* - v^n - d/2 with v* = V* split into two exact float parts
-  const int vlo8 = Vs & 0xFF;
-  const float vst_hi = (float)(Vs - vlo8);
-  const float vst_lo = __fsub_rn(__uint_as_float(0x4B000000u | (unsigned)vlo8), 8388608.0f);
-  const ff q1 = two_sum(vst_hi, -vh);
-  const float q1l = __fadd_rn(q1.lo, __fsub_rn(vst_lo, vl));
-  const ff q2 = two_sum(q1.hi, __fmul_rn(-0.5f, d.hi));
-  const float bq = __fadd_rn(q2.hi, __fadd_rn(q2.lo, __fadd_rn(q1l, __fmul_rn(-0.5f, d.lo))));
-  const float t = __fdiv_rn(__fmul_rn(__fadd_rn(d.hi, d.hi), bq), __fmul_rn(vd.hi, vd.hi));
-  if (!(t >= -1.0f && t < 1e30f)) {
-    nfb++;
-    return vd;
-  }
+  // b = v* - v^n - d/2 with v* = V*: vh = ih + fr with ih = rint(vh) (an int,
+  // |vh| < 2^31) and fr exact, so V* - v^n = (V* - ih) - fr - vl where V* - ih
+  // is a small exact integer; its sum with -d/2 is split exactly by a two-sum
+  // and only the small terms are rounded.
+  const int ih = __float2int_rn(vh);
+  const float fr = __fsub_rn(vh, __int2float_rn(ih));
+  const ff q = two_sum(__int2float_rn(Vs - ih), __fmul_rn(-0.5f, d.hi));
+  const float small = __fsub_rn(__fsub_rn(__fsub_rn(q.lo, fr), vl), __fmul_rn(0.5f, d.lo));
+  const float bq = __fadd_rn(q.hi, small);
+  const float t = div_rcp_residual(__fmul_rn(__fadd_rn(d.hi, d.hi), bq), __fmul_rn(vd.hi, vd.hi));
   if (fabsf(t) < 0.00390625f) {
     const float gm = __fmul_rn(
         t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, -0.0390625f, 0.0625f), -0.125f), 0.5f));
@@ -439,21 +466,33 @@ __device__ __forceinline__ ff correct_velocity(float vh, float vl, int Vs, ff d,
     const ff s = fast_two_sum(vd.hi, p.hi);
     return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(vd.lo, p.lo)));
   }
+  if (!(t >= -1.0f && t < 1e30f)) {
+    nfb++;
+    return vd;
+  }
   const float gm = __fdiv_rn(t, __fadd_rn(1.0f, __fsqrt_rn(__fadd_rn(1.0f, t))));
   ff p = two_prod(vd.hi, gm);
   p.lo = __fmaf_rn(vd.lo, gm, p.lo);
   return ff_add(vd, p);
 }
 
-// Adds a 64-bit padded tile to J[node stride] with one global atomic per node.
+// Adds a 64-bit padded tile to J[node stride] with one global atomic per node
+// and, when total is not null, the tile's sum to *total.
 template <int ORDER>
 __device__ __forceinline__ void flush_tile_i64(const long long *Jt, long long *J, int nc,
-                                               int stride) {
+                                               int stride, long long *total) {
+  long long mine = 0;
   for (int q = threadIdx.x; q < npad_of(nc); q += blockDim.x) {
     const long long a = Jt[q];
+    mine += a;
     if (a != 0)
       atomicAdd((unsigned long long *)&J[wrap_node(q - Pad<ORDER>::kPad, nc) * stride],
                 (unsigned long long)a);
+  }
+  if (total) {
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if ((threadIdx.x & 31u) == 0u && mine != 0)
+      atomicAdd((unsigned long long *)total, (unsigned long long)mine);
   }
 }
 
@@ -551,34 +590,37 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
   unsigned *Jt = (unsigned *)smraw;           // [npad][2][RT]
   float *Es = (float *)(Jt + 2 * RT * npad);  // [npad][RE]: dt/2 (q/m) cxk E*
   uint32_t *hist = (uint32_t *)(Es + RE * npad);  // MODE 2: keys of the markers after the step
-  double fin0 = 0.0;  // block 0: partials of the previous step's TE
-  {
-    // E* = E - dt/2 (J1 - <J1>) at every padded node, scaled to the v* kick;
-    // the first node's loads are issued before the block-wide mean
-    const double *E = PSEL(b.E, par);
-    const long long *J1 = PSEL(b.J1, par);
-    if (blockIdx.x == 0 && prev_slot >= 0) fin0 = finalize_first(b, c.h, prev_nblocks);
-    const int i0 = wrap_node((int)threadIdx.x - PAD, c.nc);
-    const bool has0 = (int)threadIdx.x < npad;
-    const double E0 = has0 ? E[i0] : 0.0;
-    const long long J0 = (SCHEME == 2 && has0) ? J1[i0 * kJStride] : 0;
-    const double mean = (SCHEME == 2 && c.remove_mean) ? block_mean_j(J1, c.nc, c.jscale_n) : 0.0;
-    for (int q = threadIdx.x; q < npad; q += blockDim.x) {
-      const int i = wrap_node(q - PAD, c.nc);
-      const bool first = q == (int)threadIdx.x;
-      double e = first ? E0 : E[i];
-      if (SCHEME == 2)
-        e -= 0.5 * c.dt * ((double)(first ? J0 : J1[i * kJStride]) * c.jscale - mean);
-      store_copies<RE>(Es + q * RE, (float)(c.e_scale * e));
-    }
-  }
+  // shared-memory set-up needs nothing from the previous kernel
   clear_tile<RT>(Jt, npad);
   if (MODE == 2)
     for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x) hist[i] = 0;
-  if (blockIdx.x == 0) {
-    if (SCHEME == 2)
-      for (int i = threadIdx.x; i < c.nc; i += blockDim.x) PSEL(b.J1, par ^ 1)[i * kJStride] = 0;
-    if (prev_slot >= 0) finalize_stats_mix(b, c.h, prev_slot, prev_nblocks, fin0);
+  griddep_wait();
+  {
+    // e_scale E* = e_scale E - e_scale dt/2 jscale (J1 - <J1>) at every padded
+    // node in FP32, from the float-pair table kick E (e_scale = kick / 2); the
+    // first node's loads are issued before the grid mean
+    const float2 *Ek = PSEL(b.Ek, par);
+    const long long *J1 = PSEL(b.J1, par);
+    const int i0 = wrap_node((int)threadIdx.x - PAD, c.nc);
+    const bool has0 = (int)threadIdx.x < npad;
+    const float2 E0 = has0 ? Ek[i0] : make_float2(0.0f, 0.0f);
+    const long long J0 = (SCHEME == 2 && has0) ? J1[i0 * kJStride] : 0;
+    const float mean = (SCHEME == 2 && c.remove_mean) ? mean_of_total(b.Jtot[par], c).hi : 0.0f;
+    for (int q = threadIdx.x; q < npad; q += blockDim.x) {
+      const int i = wrap_node(q - PAD, c.nc);
+      const bool first = q == (int)threadIdx.x;
+      const float2 ek = first ? E0 : Ek[i];
+      float e = __fmul_rn(0.5f, __fadd_rn(ek.x, ek.y));
+      if (SCHEME == 2) {
+        const float dj = __fsub_rn(__ll2float_rn(first ? J0 : J1[i * kJStride]), mean);
+        e = __fmaf_rn(-c.c_jstar, dj, e);
+      }
+      store_copies<RE>(Es + q * RE, e);
+    }
+  }
+  if (blockIdx.x == 0 && SCHEME == 2) {
+    for (int i = threadIdx.x; i < c.nc; i += blockDim.x) PSEL(b.J1, par ^ 1)[i * kJStride] = 0;
+    if (threadIdx.x == 0) b.Jtot[par ^ 1] = 0;
   }
   __syncthreads();
   const unsigned lane = threadIdx.x & 31u;
@@ -616,9 +658,13 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
     if (AGG) win.flush(Jt);
     if (gv) store_vec<G>(b.Vs, g, Vout);
   });
+  griddep_launch_dependents();
   report_flags(bad, b.err);
+  // TE of the previous step from pass E's block partials
+  if (blockIdx.x == 0 && prev_slot >= 0)
+    finalize_stats_mix(b, c.h, prev_slot, prev_nblocks, finalize_first(b, c.h, prev_nblocks));
   __syncthreads();
-  flush_tile<ORDER, RT>(Jt, PSEL(b.J2, par), c.nc);
+  flush_tile<ORDER, RT>(Jt, PSEL(b.J2, par), b.Jtot + 2 + par, c.nc);
   if (MODE == 2)
     for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x)
       b.H[(int64_t)i * gridDim.x + blockIdx.x] = hist[i];
@@ -638,6 +684,12 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
   unsigned *Jt = (unsigned *)smraw;              // [npad][2][RT]
   float2 *Eh2 = (float2 *)(Jt + 2 * RT * npad);  // [npad][RE]: dt (q/m) cxk E^{n+1/2}
   uint32_t *off = (uint32_t *)(Eh2 + RE * npad); // MODE 2: next free slot of each key
+  clear_tile<RT>(Jt, npad);  // needs nothing from the previous kernel
+  griddep_wait();
+  const long long *J2 = PSEL(b.J2, par);
+  struct {
+    ff j;
+  } mean2{{0.0f, 0.0f}};
   if (MODE == 2) {
     __shared__ uint32_t tmp[512];
     block_exclusive_scan(b.T, off, 2 * c.nc, tmp);
@@ -645,43 +697,24 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
       off[i] += b.H[(int64_t)i * gridDim.x + blockIdx.x];
   }
   {
-    // E^{n+1} = E^n - dt (J2 - <J2>) and dt (q/m) cxk E^{n+1/2} as float pairs;
-    // the first node's loads are issued before the block-wide mean
-    const double *E = PSEL(b.E, par);
-    const long long *J2 = PSEL(b.J2, par);
+    // kick E^{n+1/2} = kick E^n - kick dt/2 jscale (J2 - <J2>) at every padded
+    // node in float pairs (no FP64 per node); the first node's loads are issued
+    // before the grid mean
+    const float2 *Ek = PSEL(b.Ek, par);
     const int i0 = wrap_node((int)threadIdx.x - PAD, c.nc);
     const bool has0 = (int)threadIdx.x < npad;
-    const double E0 = has0 ? E[i0] : 0.0;
+    const float2 E0 = has0 ? Ek[i0] : make_float2(0.0f, 0.0f);
     const long long J0 = has0 ? J2[i0 * kJStride] : 0;
-    const double mean2 = c.remove_mean ? block_mean_j(J2, c.nc, c.jscale_n) : 0.0;
+    if (c.remove_mean) mean2.j = mean_of_total(b.Jtot[2 + par], c);
     for (int q = threadIdx.x; q < npad; q += blockDim.x) {
       const int i = wrap_node(q - PAD, c.nc);
       const bool first = q == (int)threadIdx.x;
-      const double Ei = first ? E0 : E[i];
-      const double en = Ei - c.dt * ((double)(first ? J0 : J2[i * kJStride]) * c.jscale - mean2);
-      const ff s = ff_from_double(c.kick * (0.5 * (Ei + en)));
-      store_copies<RE>(Eh2 + q * RE, make_float2(s.hi, s.lo));
-      if (blockIdx.x == 0 && q - PAD == i) {
-        PSEL(b.E, par ^ 1)[i] = en;
-        PSEL(b.J2, par ^ 1)[i * kJStride] = 0;
-      }
-    }
-    // sum (E^{n+1})^2 in per-block partials: warp 0 of block b recomputes
-    // E^{n+1} (the same expression) on the nodes [b nc / grid, (b + 1) nc / grid)
-    if (threadIdx.x < 32) {
-      const int n0 = (int)((int64_t)c.nc * blockIdx.x / gridDim.x);
-      const int n1 = (int)((int64_t)c.nc * (blockIdx.x + 1) / gridDim.x);
-      double w = 0.0;
-      for (int i = n0 + (int)threadIdx.x; i < n1; i += 32) {
-        const double en = E[i] - c.dt * ((double)J2[i * kJStride] * c.jscale - mean2);
-        w = fma(en, en, w);
-      }
-      if (n1 > n0)
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      if (threadIdx.x == 0) b.we_part[blockIdx.x] = w;
+      const float2 ek = first ? E0 : Ek[i];
+      const ff dj = ff_sub(ff_from_i64(first ? J0 : J2[i * kJStride]), mean2.j);
+      const ff eh = ff_sub(ff{ek.x, ek.y}, ff_mul(c.kick_jhalf, dj));
+      store_copies<RE>(Eh2 + q * RE, make_float2(eh.hi, eh.lo));
     }
   }
-  clear_tile<RT>(Jt, npad);
   __syncthreads();
 
   const unsigned lane = threadIdx.x & 31u;
@@ -712,7 +745,6 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
         const ff acc = two_sum(ke_hi, s2.hi);
         ke_hi = acc.hi;
         ke_lo = __fadd_rn(ke_lo, __fadd_rn(acc.lo, s2.lo));
-        if (!isfinite(vn.hi)) bad |= kErrNonfinite;
       }
       const uint32_t Xn = X + 2u * hs;
       if (SCHEME == 2) {
@@ -746,6 +778,32 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
       store_vec<G>(b.vl, g, o.vl);
     }
   });
+  griddep_launch_dependents();
+  // E^{n+1} = E^n - dt (jscale J2 - jscale <J2>) in FP64 on the nodes
+  // [b nc / grid, (b + 1) nc / grid) by warp 0 of block b: the field, its
+  // float-pair table for the next step, the cleared J2 of the next step and
+  // this block's part of sum (E^{n+1})^2
+  if (threadIdx.x < 32) {
+    const double *E = PSEL(b.E, par);
+    const double mean_e = c.remove_mean ? (double)b.Jtot[2 + par] * c.jscale / c.nc : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) b.Jtot[2 + (par ^ 1)] = 0;
+    const int n0 = (int)((int64_t)c.nc * blockIdx.x / gridDim.x);
+    const int n1 = (int)((int64_t)c.nc * (blockIdx.x + 1) / gridDim.x);
+    double w = 0.0;
+    for (int i = n0 + (int)threadIdx.x; i < n1; i += 32) {
+      const double en = E[i] - c.dt * ((double)J2[i * kJStride] * c.jscale - mean_e);
+      PSEL(b.E, par ^ 1)[i] = en;
+      const ff k = ff_from_double(c.kick * en);
+      PSEL(b.Ek, par ^ 1)[i] = make_float2(k.hi, k.lo);
+      PSEL(b.J2, par ^ 1)[i * kJStride] = 0;
+      w = fma(en, en, w);
+    }
+    if (n1 > n0)
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) b.we_part[blockIdx.x] = w;
+  }
+  // a non-finite v^{n+1} leaves the thread's kinetic sum non-finite
+  if (!isfinite(ke_hi) || !isfinite(ke_lo)) bad |= kErrNonfinite;
   report_flags(bad, b.err);
   nfb = __reduce_add_sync(0xffffffffu, nfb);
   if (lane == 0 && nfb) atomicAdd(&b.fallback[slot], (unsigned long long)nfb);
@@ -765,7 +823,7 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
       if (lane == 0) b.ke_part[blockIdx.x] = c.ke_scale * ((double)k.hi + (double)k.lo);
     }
   }
-  if (SCHEME == 2) flush_tile<ORDER, RT>(Jt, PSEL(b.J1, par ^ 1), c.nc);
+  if (SCHEME == 2) flush_tile<ORDER, RT>(Jt, PSEL(b.J1, par ^ 1), b.Jtot + (par ^ 1), c.nc);
 }
 
 template <int ORDER>
@@ -787,7 +845,7 @@ __global__ void __launch_bounds__(512) mix_deposit_initial_kernel(Es1dMixConst c
   }
   if (bad) atomicOr(b.err, bad);
   __syncthreads();
-  flush_tile_i64<ORDER>(Jt, PSEL(b.J1, par), c.nc, kJStride);
+  flush_tile_i64<ORDER>(Jt, PSEL(b.J1, par), c.nc, kJStride, b.Jtot + par);
 }
 
 // Charge of the markers for the initial Poisson solve: the integer weights
@@ -808,7 +866,14 @@ __global__ void __launch_bounds__(512) mix_charge_kernel(Es1dMixConst c, Es1dMix
       atomicAdd((unsigned long long *)&Jt[S.p + k], (unsigned long long)S.s[k]);
   }
   __syncthreads();
-  flush_tile_i64<ORDER>(Jt, count, c.nc, 1);
+  flush_tile_i64<ORDER>(Jt, count, c.nc, 1, nullptr);
+}
+
+__global__ void mix_set_ek_kernel(const double *E, float2 *Ek, int nc, double kick) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    const ff k = ff_from_double(kick * E[i]);
+    Ek[i] = make_float2(k.hi, k.lo);
+  }
 }
 
 __global__ void mix_finalize_kernel(Es1dMixBufs b, double h, int slot, int nblocks) {
@@ -1020,14 +1085,33 @@ cudaError_t es1d_mix_prepare(const Es1dMixConst &c) {
   return e;
 }
 
+// Launch with programmatic stream serialization: the kernel may begin (its
+// shared-memory set-up) while the previous kernel in the stream finishes; it
+// waits in griddep_wait() before touching that kernel's results.
+template <typename... P, typename... A>
+void launch_dependent(void (*kern)(P...), LaunchShape ls, size_t smem, cudaStream_t st,
+                      A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ls.grid);
+  cfg.blockDim = dim3(ls.block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);  // errors surface in cudaGetLastError
+}
+
 void es1d_mix_pass_c(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_index, int slot,
                      LaunchShape ls, cudaStream_t st) {
   int par = (int)(step_index & 1);
   dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
     constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
-    mix_pass_c_kernel<ORDER, SCHEME, MODE, NT, NE>
-        <<<ls.grid, ls.block, smem_c(c), st>>>(c, b, par, slot - 1, ls.grid);
+    launch_dependent(mix_pass_c_kernel<ORDER, SCHEME, MODE, NT, NE>, ls, smem_c(c), st, c, b, par,
+                     slot - 1, ls.grid);
   });
 }
 
@@ -1037,8 +1121,8 @@ void es1d_mix_pass_e(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_i
   dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
     constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
-    mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE>
-        <<<ls.grid, ls.block, smem_e(c), st>>>(c, b, par, slot);
+    launch_dependent(mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE>, ls, smem_e(c), st, c, b, par,
+                     slot);
   });
 }
 
@@ -1063,6 +1147,11 @@ void es1d_mix_charge(const Es1dMixConst &c, const Es1dMixBufs &b, long long *cou
 void es1d_mix_finalize(const Es1dMixConst &c, const Es1dMixBufs &b, int slot, int nblocks,
                        cudaStream_t st) {
   mix_finalize_kernel<<<1, 1024, 0, st>>>(b, c.h, slot, nblocks);
+}
+
+void es1d_mix_set_ek(const Es1dMixConst &c, const Es1dMixBufs &b, int parity, cudaStream_t st) {
+  mix_set_ek_kernel<<<(c.nc + 255) / 256, 256, 0, st>>>(PSEL(b.E, parity), PSEL(b.Ek, parity), c.nc,
+                                                         c.kick);
 }
 
 void es1d_mix_from_fp64(const Es1dMixConst &c, const double *x, const double *v, Es1dMixBufs &b,

@@ -317,10 +317,12 @@ int init_mixed(pic_handle *h, bool solve_e0) {
                 (long long)h->N, m.rshift);
   m.rnd = 1ll << (m.rshift - 1);
   m.jscale = S.q * S.w0 * std::ldexp(1.0, m.rshift) / (c.h * m.cxk * 8388608.0);
-  m.jscale_n = m.jscale / c.nc;
   m.ke_scale = 0.5 * S.m * S.w0 / (m.cxk * m.cxk);
   m.e_scale = 0.5 * c.dt * S.q / S.m * m.cxk;
   m.kick = c.dt * S.q / S.m * m.cxk;
+  m.kick_jhalf = ff_from_double(m.kick * 0.5 * c.dt * m.jscale);
+  m.inv_nc = ff_from_double(1.0 / c.nc);
+  m.c_jstar = (float)(m.e_scale * 0.5 * c.dt * m.jscale);
   CUDA_TRY(es1d_mix_prepare(m));
   Es1dMixBufs &bm = h->bm;
   size_t npad = (size_t)((h->N + 3) / 4 * 4);
@@ -336,6 +338,7 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   CUDA_TRY(cudaMemsetAsync(bm.vl, 0, sizeof(float) * npad, h->st));
   for (int k = 0; k < 2; k++) {
     bm.E[k] = b.E[k];
+    if ((rc = h->alloc(&bm.Ek[k], (size_t)c.nc))) return rc;
     CUDA_TRY(cudaMemsetAsync(bm.J1[k], 0, sizeof(long long) * c.nc * kJStride, h->st));
     CUDA_TRY(cudaMemsetAsync(bm.J2[k], 0, sizeof(long long) * c.nc * kJStride, h->st));
   }
@@ -343,6 +346,8 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   bm.fallback = b.fallback;
   bm.te = b.te;
   bm.we = b.we;
+  if ((rc = h->alloc(&bm.Jtot, 4))) return rc;
+  CUDA_TRY(cudaMemsetAsync(bm.Jtot, 0, sizeof(long long) * 4, h->st));
   if ((rc = h->alloc(&bm.we_part, (size_t)h->ls.grid))) return rc;
   CUDA_TRY(cudaMemsetAsync(bm.we_part, 0, sizeof(double) * h->ls.grid, h->st));
   bm.err = b.err;
@@ -386,6 +391,7 @@ int init_mixed(pic_handle *h, bool solve_e0) {
     if ((rc = sort_mixed(h))) return rc;
   }
   wire_sorted_output(h);
+  es1d_mix_set_ek(m, bm, (int)(h->steps_done & 1), h->st);
   if (m.scheme == 2) {
     es1d_mix_deposit_initial(m, bm, (int)(h->steps_done & 1), h->ls, h->st);
     CUDA_TRY(cudaGetLastError());
@@ -505,8 +511,10 @@ int restart_es1d(pic_handle *h, bool particles_changed) {
       CUDA_TRY(cudaMemsetAsync(bm.J1[k], 0, sizeof(long long) * h->cm.nc * kJStride, h->st));
       CUDA_TRY(cudaMemsetAsync(bm.J2[k], 0, sizeof(long long) * h->cm.nc * kJStride, h->st));
     }
+    CUDA_TRY(cudaMemsetAsync(bm.Jtot, 0, sizeof(long long) * 4, h->st));
     // the FP64 staging arrays hold the new markers only after pic_set_particles
     if (particles_changed) es1d_mix_from_fp64(h->cm, b.x, b.v, bm, h->ls, h->st);
+    es1d_mix_set_ek(h->cm, bm, par, h->st);
     if (h->cm.scheme == 2) es1d_mix_deposit_initial(h->cm, bm, par, h->ls, h->st);
     CUDA_TRY(cudaGetLastError());
     return check_flags(h, "pic_set_*");

@@ -63,10 +63,12 @@ struct Es1dMixConst {
   double L, h, dt;
   double cxk;          // (dt 2^31 / L) 2^kv
   double jscale;       // J_h = jscale * (integer node sum)
-  double jscale_n;     // jscale / nc
   double ke_scale;     // (m w / 2) / cxk^2
   double e_scale;      // dt/2 (q/m) cxk: E** -> increment of v* in V units
   double kick;         // dt (q/m) cxk: E^{n+1/2} -> v^dag - v^n in V units
+  ff kick_jhalf;       // kick dt/2 jscale as a float pair: J units -> kick E units
+  ff inv_nc;           // 1 / nc as a float pair
+  float c_jstar;       // e_scale dt/2 jscale: J units -> kick-table units of E*
 };
 
 // Unsorted mixed form: grids up to this many nodes use 32 copies of the
@@ -88,7 +90,9 @@ struct Es1dMixBufs {
   uint32_t *H;              // [2 nc][G] per-block key counts of pass C, then prefixes
   uint32_t *T;              // [2 nc] key totals
   double *E[2];
+  float2 *Ek[2];            // [2][nc] kick E (kick = dt (q/m) cxk) as float pairs, same parity as E
   long long *J1[2], *J2[2]; // integer current sums
+  long long *Jtot;          // [4] grid totals of J1[0], J1[1], J2[0], J2[1] (for <J>)
   double *ke_part;
   unsigned long long *fallback;
   double *te;
@@ -196,6 +200,7 @@ void es1d_mix_deposit_initial(const Es1dMixConst &c, const Es1dMixBufs &b, int p
                               LaunchShape ls, cudaStream_t st);
 void es1d_mix_finalize(const Es1dMixConst &c, const Es1dMixBufs &b, int slot, int nblocks,
                        cudaStream_t st);
+void es1d_mix_set_ek(const Es1dMixConst &c, const Es1dMixBufs &b, int parity, cudaStream_t st);
 void es1d_mix_charge(const Es1dMixConst &c, const Es1dMixBufs &b, long long *count,
                      LaunchShape ls, cudaStream_t st);
 void es1d_mix_from_fp64(const Es1dMixConst &c, const double *x, const double *v, Es1dMixBufs &b,
