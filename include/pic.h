@@ -220,6 +220,48 @@ const char *pic_last_error(void);
 /* Library version string. */
 const char *pic_version(void);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent 1D runs stepped together (a parameter scan or an ensemble
+ * of the scheme of Sec. 3.3 on different problems): each pass of a step is
+ * one launch over a work list of (run, block of the run), instead of one
+ * launch per run.  The method is unchanged; a batched run gives the same
+ * markers, field and fallback counts as the same run stepped alone (its
+ * energies agree to round-off: the kinetic sums are blocked differently).
+ */
+typedef struct pic_batch pic_batch;
+
+/* Creates nruns runs, run r from cfgs[r] and the single species species[r],
+ * as pic_init would (E0 from the Poisson solve).  Every run must use
+ * PIC_SOLVER_AMPERE_ES, PIC_PREC_MIXED, sort_period 0, at most 512 nodes, the
+ * same scheme and the same cuda_stream, else PIC_ERR_UNSUPPORTED.  The batch
+ * owns the runs and frees them in pic_batch_free. */
+int pic_batch_init(const pic_config *cfgs, const pic_species *species, int nruns,
+                   pic_batch **out);
+
+/* Enqueues nsteps steps of every run (asynchronous; at most 1024 steps between
+ * pic_batch_read_stats calls, else PIC_ERR_ARG).  With graphs on
+ * (pic_batch_set_graph) the launches of a call that starts after stats were
+ * read are captured once per (nsteps, step parity) and replayed. */
+int pic_batch_step(pic_batch *b, int nsteps);
+int pic_batch_set_graph(pic_batch *b, int on);
+
+/* Per-step fallback counts and total energies of the steps since the last
+ * call, run by run: nfallback[r * capacity + k], te[r * capacity + k] (host
+ * arrays, either may be NULL); *nread = steps.  Reports device error flags of
+ * any run as pic_read_stats does. */
+int pic_batch_read_stats(pic_batch *b, int capacity, int64_t *nfallback, double *te, int *nread);
+
+/* The handle of run r, for its accessors (pic_get_particles, pic_get_fields,
+ * pic_energy, pic_step_count, ...).  Do not step it, read its stats or free it
+ * directly. */
+int pic_batch_run(pic_batch *b, int run, pic_handle **h);
+
+/* Runs, blocks of the work list, and kernels launched so far. */
+int pic_batch_info(pic_batch *b, int *nruns, int *nblocks, int64_t *launches);
+
+/* Releases the batch and its runs (NULL is a no-op). */
+void pic_batch_free(pic_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

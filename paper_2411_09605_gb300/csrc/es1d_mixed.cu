@@ -496,6 +496,14 @@ __device__ __forceinline__ void flush_tile_i64(const long long *Jt, long long *J
   }
 }
 
+// A block's place among the blocks that share one run's markers: rb of nb.  A
+// single-run launch uses (blockIdx.x, gridDim.x); a batched launch over several
+// runs takes it from its work list.
+struct BlockPlace {
+  int rb, nb;
+};
+__device__ __forceinline__ BlockPlace grid_place() { return {(int)blockIdx.x, (int)gridDim.x}; }
+
 // State of G consecutive markers of one thread (vector loads of 4 G bytes).
 template <int G>
 struct MarkerGroup {
@@ -548,11 +556,11 @@ __device__ __forceinline__ void load_group(const Es1dMixBufs &b, int64_t g, bool
 // groups are all full run without validity tests (check = false_type), the
 // last one or two with them.
 template <int G, bool WITH_V, bool PREFETCH, typename F>
-__device__ __forceinline__ void for_groups(const Es1dMixBufs &b, int64_t n, F body) {
-  // block b takes the groups [ngroups b / grid, ngroups (b + 1) / grid)
+__device__ __forceinline__ void for_groups(const Es1dMixBufs &b, int64_t n, BlockPlace P, F body) {
+  // block rb of nb takes the groups [ngroups rb / nb, ngroups (rb + 1) / nb)
   const int64_t nfull = n / G, ngroups = (n + G - 1) / G;
-  const int64_t beg = ngroups * blockIdx.x / gridDim.x;
-  const int64_t end = ngroups * (blockIdx.x + 1) / gridDim.x;
+  const int64_t beg = ngroups * P.rb / P.nb;
+  const int64_t end = ngroups * (P.rb + 1) / P.nb;
   const int64_t full_end = end < nfull ? end : nfull;
   int64_t gw = beg + (threadIdx.x & ~31u);
   int64_t g = gw + (threadIdx.x & 31u);
@@ -580,8 +588,8 @@ constexpr bool kPrefetchC = true;
 constexpr bool kPrefetchE = false;
 
 template <int ORDER, int SCHEME, int MODE, int RT, int RE>
-__global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
-    mix_pass_c_kernel(Es1dMixConst c, Es1dMixBufs b, int par, int prev_slot, int prev_nblocks) {
+__device__ __forceinline__ void pass_c_body(const Es1dMixConst &c, const Es1dMixBufs &b, int par,
+                                            int prev_slot, int prev_nblocks, BlockPlace P) {
   constexpr bool AGG = MODE > 0;
   constexpr int PAD = Pad<ORDER>::kPad;
   static_assert(!AGG || RT == 1, "sorted modes use a single tile copy");
@@ -618,7 +626,7 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
       store_copies<RE>(Es + q * RE, e);
     }
   }
-  if (blockIdx.x == 0 && SCHEME == 2) {
+  if (P.rb == 0 && SCHEME == 2) {
     for (int i = threadIdx.x; i < c.nc; i += blockDim.x) PSEL(b.J1, par ^ 1)[i * kJStride] = 0;
     if (threadIdx.x == 0) b.Jtot[par ^ 1] = 0;
   }
@@ -628,7 +636,7 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
   const float *El = Es + (lane & (RE - 1));
   unsigned bad = 0;
   constexpr int G = kGroupC;
-  for_groups<G, false, !AGG && kPrefetchC>(b, c.n, [&](auto check, int64_t g, const MarkerGroup<G> &m, int64_t end) {
+  for_groups<G, false, !AGG && kPrefetchC>(b, c.n, P, [&](auto check, int64_t g, const MarkerGroup<G> &m, int64_t end) {
     constexpr bool CHECK = decltype(check)::value;
     const bool gv = !CHECK || g < end;
     int Vout[G];
@@ -661,21 +669,27 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
   griddep_launch_dependents();
   report_flags(bad, b.err);
   // TE of the previous step from pass E's block partials
-  if (blockIdx.x == 0 && prev_slot >= 0)
+  if (P.rb == 0 && prev_slot >= 0)
     finalize_stats_mix(b, c.h, prev_slot, prev_nblocks, finalize_first(b, c.h, prev_nblocks));
   __syncthreads();
   flush_tile<ORDER, RT>(Jt, PSEL(b.J2, par), b.Jtot + 2 + par, c.nc);
   if (MODE == 2)
     for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x)
-      b.H[(int64_t)i * gridDim.x + blockIdx.x] = hist[i];
+      b.H[(int64_t)i * P.nb + P.rb] = hist[i];
+}
+
+template <int ORDER, int SCHEME, int MODE, int RT, int RE>
+__global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
+    mix_pass_c_kernel(Es1dMixConst c, Es1dMixBufs b, int par, int prev_slot, int prev_nblocks) {
+  pass_c_body<ORDER, SCHEME, MODE, RT, RE>(c, b, par, prev_slot, prev_nblocks, grid_place());
 }
 
 // pass E: E^{n+1} and dt (q/m) cxk E^{n+1/2} (float pairs) in the prologue; per
 // marker the gather at x^{n+1/2} = X + [V*], v^dag, Gamma, x^{n+1}, v^{n+1},
 // the kinetic energy and (ESEC2) the next step's x* and j^{n+1,*} deposit.
 template <int ORDER, int SCHEME, int MODE, int RT, int RE>
-__global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
-    mix_pass_e_kernel(Es1dMixConst c, Es1dMixBufs b, int par, int slot) {
+__device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMixBufs &b, int par,
+                                            int slot, BlockPlace P) {
   constexpr bool AGG = MODE > 0;
   constexpr int PAD = Pad<ORDER>::kPad;
   static_assert(!AGG || RT == 1, "sorted modes use a single tile copy");
@@ -694,7 +708,7 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
     __shared__ uint32_t tmp[512];
     block_exclusive_scan(b.T, off, 2 * c.nc, tmp);
     for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x)
-      off[i] += b.H[(int64_t)i * gridDim.x + blockIdx.x];
+      off[i] += b.H[(int64_t)i * P.nb + P.rb];
   }
   {
     // kick E^{n+1/2} = kick E^n - kick dt/2 jscale (J2 - <J2>) at every padded
@@ -723,7 +737,7 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
   float ke_hi = 0.0f, ke_lo = 0.0f;
   unsigned nfb = 0, bad = 0;
   constexpr int G = kGroupE;
-  for_groups<G, true, !AGG && kPrefetchE>(b, c.n, [&](auto check, int64_t g, const MarkerGroup<G> &m, int64_t end) {
+  for_groups<G, true, !AGG && kPrefetchE>(b, c.n, P, [&](auto check, int64_t g, const MarkerGroup<G> &m, int64_t end) {
     constexpr bool CHECK = decltype(check)::value;
     const bool gv = !CHECK || g < end;
     MarkerGroup<G> o;
@@ -786,9 +800,9 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
   if (threadIdx.x < 32) {
     const double *E = PSEL(b.E, par);
     const double mean_e = c.remove_mean ? (double)b.Jtot[2 + par] * c.jscale / c.nc : 0.0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) b.Jtot[2 + (par ^ 1)] = 0;
-    const int n0 = (int)((int64_t)c.nc * blockIdx.x / gridDim.x);
-    const int n1 = (int)((int64_t)c.nc * (blockIdx.x + 1) / gridDim.x);
+    if (P.rb == 0 && threadIdx.x == 0) b.Jtot[2 + (par ^ 1)] = 0;
+    const int n0 = (int)((int64_t)c.nc * P.rb / P.nb);
+    const int n1 = (int)((int64_t)c.nc * (P.rb + 1) / P.nb);
     double w = 0.0;
     for (int i = n0 + (int)threadIdx.x; i < n1; i += 32) {
       const double en = E[i] - c.dt * ((double)J2[i * kJStride] * c.jscale - mean_e);
@@ -800,7 +814,7 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
     }
     if (n1 > n0)
       for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    if (threadIdx.x == 0) b.we_part[blockIdx.x] = w;
+    if (threadIdx.x == 0) b.we_part[P.rb] = w;
   }
   // a non-finite v^{n+1} leaves the thread's kinetic sum non-finite
   if (!isfinite(ke_hi) || !isfinite(ke_lo)) bad |= kErrNonfinite;
@@ -820,10 +834,16 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
       k = threadIdx.x < (blockDim.x >> 5) ? ff{kred[lane].x, kred[lane].y} : ff{0.0f, 0.0f};
       for (int o = 16; o > 0; o >>= 1)
         k = ff_add(k, ff{__shfl_xor_sync(0xffffffffu, k.hi, o), __shfl_xor_sync(0xffffffffu, k.lo, o)});
-      if (lane == 0) b.ke_part[blockIdx.x] = c.ke_scale * ((double)k.hi + (double)k.lo);
+      if (lane == 0) b.ke_part[P.rb] = c.ke_scale * ((double)k.hi + (double)k.lo);
     }
   }
   if (SCHEME == 2) flush_tile<ORDER, RT>(Jt, PSEL(b.J1, par ^ 1), b.Jtot + (par ^ 1), c.nc);
+}
+
+template <int ORDER, int SCHEME, int MODE, int RT, int RE>
+__global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
+    mix_pass_e_kernel(Es1dMixConst c, Es1dMixBufs b, int par, int slot) {
+  pass_e_body<ORDER, SCHEME, MODE, RT, RE>(c, b, par, slot, grid_place());
 }
 
 template <int ORDER>
@@ -867,6 +887,61 @@ __global__ void __launch_bounds__(512) mix_charge_kernel(Es1dMixConst c, Es1dMix
   }
   __syncthreads();
   flush_tile_i64<ORDER>(Jt, count, c.nc, 1, nullptr);
+}
+
+// ------------------------------------------------------------- batched runs
+// One launch per pass over a work list: block i steps block items[i].rb of the
+// items[i].nb blocks of run items[i].run, with that run's constants and
+// buffers (read-only arrays, read before the dependency wait) and the same
+// pass bodies as a single-run launch; the kernel boundaries remain the only
+// barriers between the passes.
+template <int SCHEME>
+__global__ void __launch_bounds__(1024, 1)
+    mix_batch_pass_c_kernel(const Es1dMixConst *__restrict__ cs, const Es1dMixBufs *__restrict__ bs,
+                            const BatchItem *__restrict__ items, int par, int prev_slot) {
+  const BatchItem it = items[blockIdx.x];
+  const Es1dMixConst &c = cs[it.run];
+  const Es1dMixBufs &b = bs[it.run];
+  const BlockPlace P{it.rb, it.nb};
+  if (c.order == 1)
+    pass_c_body<1, SCHEME, 0, 32, 16>(c, b, par, prev_slot, it.nb, P);
+  else
+    pass_c_body<2, SCHEME, 0, 32, 16>(c, b, par, prev_slot, it.nb, P);
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(1024, 1)
+    mix_batch_pass_e_kernel(const Es1dMixConst *__restrict__ cs, const Es1dMixBufs *__restrict__ bs,
+                            const BatchItem *__restrict__ items, int par, int slot) {
+  const BatchItem it = items[blockIdx.x];
+  const Es1dMixConst &c = cs[it.run];
+  const Es1dMixBufs &b = bs[it.run];
+  const BlockPlace P{it.rb, it.nb};
+  if (c.order == 1)
+    pass_e_body<1, SCHEME, 0, 32, 16>(c, b, par, slot, P);
+  else
+    pass_e_body<2, SCHEME, 0, 32, 16>(c, b, par, slot, P);
+}
+
+// TE of step `slot` of every run (one block per run).
+__global__ void mix_batch_finalize_kernel(const Es1dMixConst *cs, const Es1dMixBufs *bs,
+                                          const int *nblocks, int slot) {
+  const Es1dMixBufs &b = bs[blockIdx.x];
+  const double h = cs[blockIdx.x].h;
+  const int nb = nblocks[blockIdx.x];
+  finalize_stats_mix(b, h, slot, nb, finalize_first(b, h, nb));
+}
+
+// Copies the first n per-step counts and energies of every run into one
+// buffer ([run][step]) and clears the counts for the next steps.
+__global__ void mix_batch_gather_kernel(const Es1dMixBufs *bs, int n, unsigned long long *fb,
+                                        double *te) {
+  const Es1dMixBufs &b = bs[blockIdx.x];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    fb[(int64_t)blockIdx.x * n + k] = b.fallback[k];
+    te[(int64_t)blockIdx.x * n + k] = b.te[k];
+    b.fallback[k] = 0;
+  }
 }
 
 __global__ void mix_set_ek_kernel(const double *E, float2 *Ek, int nc, double kick) {
@@ -1152,6 +1227,52 @@ void es1d_mix_finalize(const Es1dMixConst &c, const Es1dMixBufs &b, int slot, in
 void es1d_mix_set_ek(const Es1dMixConst &c, const Es1dMixBufs &b, int parity, cudaStream_t st) {
   mix_set_ek_kernel<<<(c.nc + 255) / 256, 256, 0, st>>>(PSEL(b.E, parity), PSEL(b.Ek, parity), c.nc,
                                                          c.kick);
+}
+
+cudaError_t es1d_batch_prepare(size_t smem) {
+  cudaError_t e = cudaSuccess;
+  for (auto k : {(const void *)mix_batch_pass_c_kernel<1>, (const void *)mix_batch_pass_c_kernel<2>,
+                 (const void *)mix_batch_pass_e_kernel<1>, (const void *)mix_batch_pass_e_kernel<2>})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
+}
+
+size_t es1d_mix_smem_max(const Es1dMixConst &c) {
+  const size_t a = smem_c(c), b = smem_e(c);
+  return a > b ? a : b;
+}
+
+void es1d_batch_pass_c(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,
+                       int nitems, int scheme, size_t smem, int64_t step_index, int slot,
+                       cudaStream_t st) {
+  const int par = (int)(step_index & 1);
+  const LaunchShape ls{nitems, 1024};
+  if (scheme == 1)
+    launch_dependent(mix_batch_pass_c_kernel<1>, ls, smem, st, cs, bs, items, par, slot - 1);
+  else
+    launch_dependent(mix_batch_pass_c_kernel<2>, ls, smem, st, cs, bs, items, par, slot - 1);
+}
+
+void es1d_batch_pass_e(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,
+                       int nitems, int scheme, size_t smem, int64_t step_index, int slot,
+                       cudaStream_t st) {
+  const int par = (int)(step_index & 1);
+  const LaunchShape ls{nitems, 1024};
+  if (scheme == 1)
+    launch_dependent(mix_batch_pass_e_kernel<1>, ls, smem, st, cs, bs, items, par, slot);
+  else
+    launch_dependent(mix_batch_pass_e_kernel<2>, ls, smem, st, cs, bs, items, par, slot);
+}
+
+void es1d_batch_finalize(const Es1dMixConst *cs, const Es1dMixBufs *bs, const int *nblocks,
+                         int nruns, int slot, cudaStream_t st) {
+  mix_batch_finalize_kernel<<<nruns, 1024, 0, st>>>(cs, bs, nblocks, slot);
+}
+
+void es1d_batch_gather_stats(const Es1dMixBufs *bs, int nruns, int n, unsigned long long *fb,
+                             double *te, cudaStream_t st) {
+  mix_batch_gather_kernel<<<nruns, 256, 0, st>>>(bs, n, fb, te);
 }
 
 void es1d_mix_from_fp64(const Es1dMixConst &c, const double *x, const double *v, Es1dMixBufs &b,

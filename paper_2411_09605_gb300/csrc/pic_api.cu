@@ -1058,3 +1058,235 @@ void pic_free(pic_handle *h) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batches
+// Independent 1D runs of the mixed form stepped together: one launch per pass
+// for all runs, over a work list of (run, block of the run).  The runs are
+// ordinary handles (their accessors work); only their stepping and stats go
+// through the batch.
+struct pic_batch {
+  std::vector<pic_handle *> runs;
+  cudaStream_t st = nullptr;
+  cudaStream_t own = nullptr;  // created when the runs were given no stream
+  int scheme = 2;
+  size_t smem = 0;
+  int nitems = 0;
+  Es1dMixConst *d_c = nullptr;
+  Es1dMixBufs *d_b = nullptr;
+  BatchItem *d_items = nullptr;
+  int *d_nb = nullptr;
+  unsigned long long *d_fb = nullptr;  // [runs][kStepsCap] gathered counts
+  double *d_te = nullptr;              // [runs][kStepsCap] gathered energies
+  int64_t steps_done = 0;
+  int pending = 0;
+  int64_t launches = 0;
+  bool use_graph = false;
+  struct Graph {
+    int steps, parity;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  ~pic_batch() {
+    if (st) cudaStreamSynchronize(st);
+    for (Graph &g : graphs) cudaGraphExecDestroy(g.exec);
+    for (void *p : {(void *)d_c, (void *)d_b, (void *)d_items, (void *)d_nb, (void *)d_fb,
+                    (void *)d_te})
+      if (p) cudaFree(p);
+    for (pic_handle *h : runs) pic_free(h);
+    if (own) cudaStreamDestroy(own);
+  }
+  // The launches of nsteps steps from the current step count, on st.
+  void enqueue(int nsteps, int first_slot) {
+    for (int k = 0; k < nsteps; k++) {
+      const int64_t step = steps_done + k;
+      es1d_batch_pass_c(d_c, d_b, d_items, nitems, scheme, smem, step, first_slot + k, st);
+      es1d_batch_pass_e(d_c, d_b, d_items, nitems, scheme, smem, step, first_slot + k, st);
+    }
+  }
+};
+
+namespace {
+// Blocks of 1024 threads per run: about this many 4-marker trips each (at most
+// 16, the bound the runs' integer tiles are sized for).
+constexpr int kBatchTrips = 8;
+}  // namespace
+
+extern "C" {
+
+int pic_batch_init(const pic_config *cfgs, const pic_species *species, int nruns,
+                   pic_batch **out) {
+  if (!cfgs || !species || !out || nruns <= 0)
+    return fail(PIC_ERR_ARG, "pic_batch_init: bad arguments");
+  *out = nullptr;
+  for (int r = 0; r < nruns; r++) {
+    const pic_config &c = cfgs[r];
+    if (c.solver != PIC_SOLVER_AMPERE_ES || c.precision != PIC_PREC_MIXED || c.sort_period != 0 ||
+        c.grid.n[0] > kWideMaxNodes || c.scheme != cfgs[0].scheme ||
+        c.cuda_stream != cfgs[0].cuda_stream)
+      return fail(PIC_ERR_UNSUPPORTED,
+                  "pic_batch_init: run %d: batches take unsorted mixed-form 1D runs with at most "
+                  "%d nodes, one scheme and one stream", r, kWideMaxNodes);
+  }
+  pic_batch *b = new pic_batch();
+  b->scheme = cfgs[0].scheme;
+  std::vector<Es1dMixConst> hc(nruns);
+  std::vector<Es1dMixBufs> hb(nruns);
+  std::vector<BatchItem> items;
+  std::vector<int> nbs(nruns);
+  for (int r = 0; r < nruns; r++) {
+    pic_handle *h = nullptr;
+    int rc = pic_init(&cfgs[r], &species[r], 1, nullptr, nullptr, &h);
+    if (rc) {
+      std::string msg = g_last_error;
+      delete b;
+      return fail(rc, "pic_batch_init: run %d: %s", r, msg.c_str());
+    }
+    b->runs.push_back(h);
+    if (!h->cm.wide) {
+      delete b;
+      return fail(PIC_ERR_UNSUPPORTED, "pic_batch_init: run %d is not in the wide layout", r);
+    }
+    b->st = h->st;
+    hc[r] = h->cm;
+    hb[r] = h->bm;
+    const int64_t ngroups = (h->N + 3) / 4;
+    int nb = (int)std::max<int64_t>(1, (ngroups + 1024 * kBatchTrips - 1) / (1024 * kBatchTrips));
+    nb = std::min(nb, h->ls.grid);  // the run's per-block partials hold ls.grid entries
+    if ((ngroups + (int64_t)nb * 1024 - 1) / ((int64_t)nb * 1024) > 16) {
+      delete b;
+      return fail(PIC_ERR_UNSUPPORTED, "pic_batch_init: run %d is too large for a batch", r);
+    }
+    nbs[r] = nb;
+    for (int k = 0; k < nb; k++) items.push_back(BatchItem{r, k, nb});
+    b->smem = std::max(b->smem, es1d_mix_smem_max(h->cm));
+  }
+  b->nitems = (int)items.size();
+  if (!cfgs[0].cuda_stream) {
+    // the legacy default stream cannot be captured into a graph: the batch and
+    // its runs move to a stream of their own
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete b;
+      return fail(PIC_ERR_CUDA, "pic_batch_init: %s", cudaGetErrorString(e));
+    }
+    b->st = b->own;
+    for (pic_handle *h : b->runs) h->st = b->own;
+  }
+  auto up = [&](auto **dst, const auto &v) -> cudaError_t {
+    cudaError_t e = cudaMalloc((void **)dst, sizeof(v[0]) * v.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(*dst, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice, b->st);
+    return e;
+  };
+  cudaError_t e = up(&b->d_c, hc);
+  if (e == cudaSuccess) e = up(&b->d_b, hb);
+  if (e == cudaSuccess) e = up(&b->d_items, items);
+  if (e == cudaSuccess) e = up(&b->d_nb, nbs);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_fb, sizeof(unsigned long long) * kStepsCap * nruns);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_te, sizeof(double) * kStepsCap * nruns);
+  if (e == cudaSuccess) e = es1d_batch_prepare(b->smem);
+  for (int r = 0; r < nruns && e == cudaSuccess; r++)
+    e = cudaMemsetAsync(hb[r].fallback, 0, sizeof(unsigned long long) * kStepsCap, b->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) {
+    delete b;
+    return fail(e == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA,
+                "pic_batch_init: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return PIC_OK;
+}
+
+int pic_batch_set_graph(pic_batch *b, int on) {
+  if (!b) return fail(PIC_ERR_ARG, "pic_batch_set_graph: NULL batch");
+  b->use_graph = on != 0;
+  return PIC_OK;
+}
+
+int pic_batch_step(pic_batch *b, int nsteps) {
+  if (!b || nsteps < 0) return fail(PIC_ERR_ARG, "pic_batch_step: bad arguments");
+  if (b->pending + nsteps > kStepsCap)
+    return fail(PIC_ERR_ARG, "pic_batch_step: %d steps pending, at most %d before "
+                             "pic_batch_read_stats", b->pending + nsteps, kStepsCap);
+  if (nsteps == 0) return PIC_OK;
+  const int parity = (int)(b->steps_done & 1);
+  if (b->use_graph && b->pending == 0) {
+    // the same launches for the same step count and parity replay one graph
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : b->graphs)
+      if (g.steps == nsteps && g.parity == parity) exec = g.exec;
+    if (!exec) {
+      cudaGraph_t graph = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+      b->enqueue(nsteps, 0);
+      cudaError_t e = cudaStreamEndCapture(b->st, &graph);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      CUDA_TRY(e);
+      b->graphs.push_back({nsteps, parity, exec});
+    }
+    CUDA_TRY(cudaGraphLaunch(exec, b->st));
+  } else {
+    b->enqueue(nsteps, b->pending);
+    CUDA_TRY(cudaGetLastError());
+  }
+  b->launches += 2 * nsteps;
+  b->steps_done += nsteps;
+  b->pending += nsteps;
+  for (pic_handle *h : b->runs) h->steps_done += nsteps;
+  return PIC_OK;
+}
+
+int pic_batch_read_stats(pic_batch *b, int capacity, int64_t *nfallback, double *te, int *nread) {
+  if (!b) return fail(PIC_ERR_ARG, "pic_batch_read_stats: NULL batch");
+  const int n = b->pending, nruns = (int)b->runs.size();
+  if (nread) *nread = n;
+  if (n > 0) {
+    if ((nfallback || te) && capacity < n)
+      return fail(PIC_ERR_ARG, "pic_batch_read_stats: %d steps pending, capacity %d", n,
+                  capacity);
+    es1d_batch_finalize(b->d_c, b->d_b, b->d_nb, nruns, n - 1, b->st);
+    es1d_batch_gather_stats(b->d_b, nruns, n, b->d_fb, b->d_te, b->st);
+    CUDA_TRY(cudaGetLastError());
+    b->launches += 2;
+    std::vector<unsigned long long> fb((size_t)n * nruns);
+    std::vector<double> tv((size_t)n * nruns);
+    CUDA_TRY(cudaMemcpyAsync(fb.data(), b->d_fb, sizeof(unsigned long long) * fb.size(),
+                             cudaMemcpyDeviceToHost, b->st));
+    CUDA_TRY(cudaMemcpyAsync(tv.data(), b->d_te, sizeof(double) * tv.size(),
+                             cudaMemcpyDeviceToHost, b->st));
+    CUDA_TRY(cudaStreamSynchronize(b->st));
+    for (int r = 0; r < nruns; r++)
+      for (int k = 0; k < n; k++) {
+        if (nfallback) nfallback[(size_t)r * capacity + k] = (int64_t)fb[(size_t)r * n + k];
+        if (te) te[(size_t)r * capacity + k] = tv[(size_t)r * n + k];
+      }
+    b->pending = 0;
+  }
+  for (pic_handle *h : b->runs) {
+    int rc = check_flags(h, "pic_batch_read_stats");
+    if (rc) return rc;
+  }
+  return PIC_OK;
+}
+
+int pic_batch_run(pic_batch *b, int run, pic_handle **h) {
+  if (!b || !h || run < 0 || run >= (int)b->runs.size())
+    return fail(PIC_ERR_ARG, "pic_batch_run: bad arguments");
+  *h = b->runs[run];
+  return PIC_OK;
+}
+
+int pic_batch_info(pic_batch *b, int *nruns, int *nblocks, int64_t *launches) {
+  if (!b) return fail(PIC_ERR_ARG, "pic_batch_info: NULL batch");
+  if (nruns) *nruns = (int)b->runs.size();
+  if (nblocks) *nblocks = b->nitems;
+  if (launches) *launches = b->launches;
+  return PIC_OK;
+}
+
+void pic_batch_free(pic_batch *b) { delete b; }
+
+}  // extern "C"

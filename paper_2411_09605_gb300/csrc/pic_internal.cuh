@@ -71,6 +71,12 @@ struct Es1dMixConst {
   float c_jstar;       // e_scale dt/2 jscale: J units -> kick-table units of E*
 };
 
+// One block of a batched launch over several independent runs: block rb of the
+// nb blocks that share run `run`.
+struct BatchItem {
+  int run, rb, nb;
+};
+
 // Unsorted mixed form: grids up to this many nodes use 32 copies of the
 // current tile and 16 of the field tables per block (one 1024-thread block per
 // SM); larger grids one copy (512-thread blocks).
@@ -201,6 +207,20 @@ void es1d_mix_deposit_initial(const Es1dMixConst &c, const Es1dMixBufs &b, int p
 void es1d_mix_finalize(const Es1dMixConst &c, const Es1dMixBufs &b, int slot, int nblocks,
                        cudaStream_t st);
 void es1d_mix_set_ek(const Es1dMixConst &c, const Es1dMixBufs &b, int parity, cudaStream_t st);
+// batched runs (unsorted, nc <= kWideMaxNodes, one scheme): device arrays of the
+// runs' constants and buffers and the work list of nitems blocks
+cudaError_t es1d_batch_prepare(size_t smem);
+void es1d_batch_pass_c(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,
+                       int nitems, int scheme, size_t smem, int64_t step_index, int slot,
+                       cudaStream_t st);
+void es1d_batch_pass_e(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,
+                       int nitems, int scheme, size_t smem, int64_t step_index, int slot,
+                       cudaStream_t st);
+void es1d_batch_finalize(const Es1dMixConst *cs, const Es1dMixBufs *bs, const int *nblocks,
+                         int nruns, int slot, cudaStream_t st);
+void es1d_batch_gather_stats(const Es1dMixBufs *bs, int nruns, int n, unsigned long long *fb,
+                             double *te, cudaStream_t st);
+size_t es1d_mix_smem_max(const Es1dMixConst &c);
 void es1d_mix_charge(const Es1dMixConst &c, const Es1dMixBufs &b, long long *count,
                      LaunchShape ls, cudaStream_t st);
 void es1d_mix_from_fp64(const Es1dMixConst &c, const double *x, const double *v, Es1dMixBufs &b,

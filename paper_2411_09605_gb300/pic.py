@@ -31,7 +31,9 @@ EXPORTS = ["pic_init", "pic_step", "pic_step_async", "pic_read_stats", "pic_laun
            "pic_set_profiling", "pic_profile",
            "pic_energy", "pic_get_particles", "pic_get_ids",
            "pic_set_particles", "pic_get_fields", "pic_set_fields", "pic_step_count", "pic_free",
-           "pic_last_error", "pic_version", "pic_es1d_step_noalloc"]
+           "pic_last_error", "pic_version", "pic_es1d_step_noalloc",
+           "pic_batch_init", "pic_batch_step", "pic_batch_set_graph", "pic_batch_read_stats",
+           "pic_batch_run", "pic_batch_info", "pic_batch_free"]
 
 
 class PicError(RuntimeError):
@@ -89,10 +91,19 @@ def lib() -> C.CDLL:
                                              C.c_double, C.c_int64, vp, vp, vp, C.c_int, vp, vp]
         L.pic_free.argtypes = [vp]
         L.pic_free.restype = None
+        L.pic_batch_init.argtypes = [C.POINTER(pic_config), C.POINTER(pic_species), C.c_int,
+                                     C.POINTER(vp)]
+        L.pic_batch_step.argtypes = [vp, C.c_int]
+        L.pic_batch_set_graph.argtypes = [vp, C.c_int]
+        L.pic_batch_read_stats.argtypes = [vp, C.c_int, vp, vp, C.POINTER(C.c_int)]
+        L.pic_batch_run.argtypes = [vp, C.c_int, C.POINTER(vp)]
+        L.pic_batch_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), i64p]
+        L.pic_batch_free.argtypes = [vp]
+        L.pic_batch_free.restype = None
         L.pic_last_error.restype = C.c_char_p
         L.pic_version.restype = C.c_char_p
         for name in EXPORTS:
-            if name not in ("pic_free", "pic_last_error", "pic_version"):
+            if name not in ("pic_free", "pic_last_error", "pic_version", "pic_batch_free"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -229,11 +240,11 @@ class Simulation:
     """Convenience owner of one handle built from a ``workloads.Problem1D``."""
 
     def __init__(self, prob, scheme=PIC_SCHEME_ESEC2, precision=PIC_PREC_FP64, E0=None,
-                 sort_period=0, remove_mean=True, gamma_on=True):
+                 sort_period=0, remove_mean=True, gamma_on=True, stream=None):
         self.prob = prob
         self.cfg = make_config(prob.nc, prob.L, prob.dt, prob.order, scheme, precision,
                                sort_period=sort_period, remove_mean=remove_mean,
-                               gamma_on=gamma_on)
+                               gamma_on=gamma_on, stream=stream)
         self.species = [dict(q=s.q, m=s.m, x=np.ascontiguousarray(s.x, dtype=np.float64),
                              v=np.ascontiguousarray(s.v, dtype=np.float64),
                              w=None if s.w is None else np.ascontiguousarray(s.w, np.float64),
@@ -326,3 +337,101 @@ class Simulation2D:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ batches
+
+
+def pic_batch_init(cfgs: Sequence[pic_config], species: Sequence[dict]) -> int:
+    """Run r from cfgs[r] and the single species dict species[r]; returns the batch."""
+    n = len(cfgs)
+    ca = (pic_config * n)(*cfgs)
+    sa = (pic_species * n)()
+    for i, s in enumerate(species):
+        sa[i] = pic_species(s["q"], s["m"], s["x"].shape[-1], _addr(s["x"]), _addr(s["v"]),
+                            _addr(s.get("w")), s.get("w0", 0.0))
+    b = C.c_void_p()
+    _check(lib().pic_batch_init(ca, sa, n, C.byref(b)))
+    return b.value
+
+
+def pic_batch_step(b: int, nsteps: int):
+    _check(lib().pic_batch_step(b, nsteps))
+
+
+def pic_batch_set_graph(b: int, on: bool):
+    _check(lib().pic_batch_set_graph(b, int(on)))
+
+
+def pic_batch_read_stats(b: int, nruns: int, capacity: int = 1024):
+    """(fallbacks [runs, steps], total energies [runs, steps]) since the last read."""
+    fb = np.zeros((nruns, capacity), dtype=np.int64)
+    te = np.zeros((nruns, capacity))
+    n = C.c_int()
+    _check(lib().pic_batch_read_stats(b, capacity, fb.ctypes.data, te.ctypes.data, C.byref(n)))
+    return fb[:, :n.value], te[:, :n.value]
+
+
+def pic_batch_run(b: int, run: int) -> int:
+    h = C.c_void_p()
+    _check(lib().pic_batch_run(b, run, C.byref(h)))
+    return h.value
+
+
+def pic_batch_info(b: int):
+    nr, nb, nl = C.c_int(), C.c_int(), C.c_int64()
+    _check(lib().pic_batch_info(b, C.byref(nr), C.byref(nb), C.byref(nl)))
+    return nr.value, nb.value, nl.value
+
+
+def pic_batch_free(b: int):
+    lib().pic_batch_free(b)
+
+
+class Batch:
+    """Independent 1D problems (workloads.Problem1D, one species each) stepped
+    together in the mixed form."""
+
+    def __init__(self, problems, scheme=PIC_SCHEME_ESEC2, graphs=False, stream=None):
+        """stream: a cudaStream_t (int) for every run, or None for a stream the batch
+        creates."""
+        self.problems = problems
+        cfgs = [make_config(p.nc, p.L, p.dt, p.order, scheme, PIC_PREC_MIXED, stream=stream)
+                for p in problems]
+        sp = [dict(q=p.species[0].q, m=p.species[0].m, x=p.species[0].x, v=p.species[0].v,
+                   w=None, w0=p.species[0].w0) for p in problems]
+        self.b = pic_batch_init(cfgs, sp)
+        if graphs:
+            pic_batch_set_graph(self.b, True)
+
+    def step(self, nsteps: int):
+        """Steps every run; returns (fallbacks, total energies), each [runs, steps]."""
+        fbs, tes = [], []
+        done = 0
+        while done < nsteps:
+            k = min(1024, nsteps - done)
+            pic_batch_step(self.b, k)
+            fb, te = pic_batch_read_stats(self.b, len(self.problems))
+            fbs.append(fb)
+            tes.append(te)
+            done += k
+        return np.concatenate(fbs, axis=1), np.concatenate(tes, axis=1)
+
+    def run(self, r: int) -> int:
+        return pic_batch_run(self.b, r)
+
+    def particles(self, r: int):
+        n = self.problems[r].n_markers
+        x, v = np.zeros(n), np.zeros(n)
+        pic_get_particles(self.run(r), 0, x, v)
+        return x, v
+
+    def field(self, r: int):
+        E = np.zeros(self.problems[r].nc)
+        pic_get_fields(self.run(r), E)
+        return E
+
+    def close(self):
+        if self.b:
+            pic_batch_free(self.b)
+            self.b = None

@@ -145,6 +145,25 @@ def two_stream(n: int = 1 << 23, nc: int = 512, k: float = 0.2, v0: float = 3.0,
                      [Markers1D(-1.0, 1.0, x, v, None, L / n)])
 
 
+def ensemble(nruns: int = 256, seed: int = 0, n_min: float = 1e4, n_max: float = 1e6,
+             nc_min: int = 32, nc_max: int = 512):
+    """Independent 1D1V problems for a batched run: per run N_c ~ U{nc_min..nc_max},
+    N ~ log-uniform on [n_min, n_max], seed amplitude alpha ~ U[1e-3, 0.1]; even runs
+    Landau damping (CIC, dt 0.1), odd runs two-stream (quadratic shapes, dt 0.05)."""
+    rng = np.random.default_rng(seed)
+    runs = []
+    for r in range(nruns):
+        nc = int(rng.integers(nc_min, nc_max + 1))
+        n = int(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        alpha = float(rng.uniform(1e-3, 0.1))
+        s = int(rng.integers(0, 2**31 - 1))
+        if r % 2 == 0:
+            runs.append(landau(n=n, nc=nc, alpha=alpha, seed=s))
+        else:
+            runs.append(two_stream(n=n, nc=nc, alpha=alpha, seed=s))
+    return runs
+
+
 def bump_on_tail(n: int = 1 << 20, nc: int = 256, k: float = 0.3, alpha: float = 0.04,
                  beam_frac: float = 0.1, vb: float = 4.5, vtb: float = 0.5,
                  dt: float = 0.1, steps: int = 500, order: int = 2, seed: int = 0) -> Problem1D:

@@ -57,3 +57,34 @@ def test_argument_errors_are_status_codes(lib):
     assert ei.value.code == -1
     assert lib.pic_step(None, 1, None, None) == -1
     lib.pic_free(None)  # no-op
+
+
+def test_batch_argument_errors_are_status_codes(lib):
+    import ctypes as C
+    from paper_2411_09605_gb300 import pic
+    x = np.array([0.5])
+    v = np.array([0.1])
+    sp = [dict(q=-1.0, m=1.0, x=x, v=v, w=None, w0=1.0)]
+    # not batchable: FP64 form, sorted markers, more than 512 nodes, mixed schemes
+    for cfgs in ([pic.make_config(64, 1.0, 0.1)],
+                 [pic.make_config(64, 1.0, 0.1, precision=pic.PIC_PREC_MIXED, sort_period=4)],
+                 [pic.make_config(1024, 1.0, 0.1, precision=pic.PIC_PREC_MIXED)],
+                 [pic.make_config(64, 1.0, 0.1, precision=pic.PIC_PREC_MIXED),
+                  pic.make_config(64, 1.0, 0.1, scheme=pic.PIC_SCHEME_ESEC1,
+                                  precision=pic.PIC_PREC_MIXED)]):
+        with pytest.raises(pic.PicError) as ei:
+            pic.pic_batch_init(cfgs, sp * len(cfgs))
+        assert ei.value.code == -7
+    assert lib.pic_batch_init(None, None, 1, C.byref(C.c_void_p())) == -1
+    assert lib.pic_batch_step(None, 1) == -1
+    lib.pic_batch_free(None)  # no-op
+
+
+def test_every_entry_point_has_argument_types():
+    """ctypes passes undeclared integer arguments as 32-bit ints, which would cut
+    the 64-bit handle pointers."""
+    from paper_2411_09605_gb300 import pic
+    L = pic.lib()
+    for name in pic.EXPORTS:
+        if name not in ("pic_last_error", "pic_version"):
+            assert getattr(L, name).argtypes is not None, name
