@@ -445,6 +445,7 @@ def run_ensemble(args):
     for graphs in (False, True):
         bt = pic.Batch(probs, graphs=graphs, stream=stream.cuda_stream)
         try:
+            trips = pic.pic_batch_autotune(bt.b, 2)
             bt.step(args.warmup)
             t = timed(lambda k: pic.pic_batch_step(bt.b, k), steps)
             fb, te = pic.pic_batch_read_stats(bt.b, len(probs))
@@ -475,7 +476,7 @@ def run_ensemble(args):
         "data": "synthetic (seeded Landau and two-stream runs)",
         "config": {"workload": "ensemble_1d1v", "runs": len(probs), "markers": markers,
                    "cells": "U{32..512}", "markers_per_run": "log-uniform [1e4, 1e6]",
-                   "blocks_per_pass": nblocks,
+                   "blocks_per_pass": nblocks, "trips_per_block (autotuned)": trips,
                    "l2": "not flushed: the batch state (%.0f MB) is larger than L2"
                          % (16e-6 * markers)},
         "forms": out,

@@ -245,6 +245,13 @@ int pic_batch_init(const pic_config *cfgs, const pic_species *species, int nruns
 int pic_batch_step(pic_batch *b, int nsteps);
 int pic_batch_set_graph(pic_batch *b, int on);
 
+/* Chooses the blocks per run (about 4, 8 or 16 trips of 4 markers per thread)
+ * by timing steps_per_trial steps with each work list (these are real steps
+ * of every run: their stats are read with the others), and keeps the fastest.
+ * The choice is remembered for this process per (number of runs, total markers
+ * rounded to a power of two, largest grid); *trips (may be NULL) receives it. */
+int pic_batch_autotune(pic_batch *b, int steps_per_trial, int *trips);
+
 /* Per-step fallback counts and total energies of the steps since the last
  * call, run by run: nfallback[r * capacity + k], te[r * capacity + k] (host
  * arrays, either may be NULL); *nread = steps.  Reports device error flags of

@@ -1244,14 +1244,14 @@ size_t es1d_mix_smem_max(const Es1dMixConst &c) {
 }
 
 void es1d_batch_pass_c(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,
-                       int nitems, int scheme, size_t smem, int64_t step_index, int slot,
+                       int nitems, int scheme, size_t smem, int64_t step_index, int prev_slot,
                        cudaStream_t st) {
   const int par = (int)(step_index & 1);
   const LaunchShape ls{nitems, 1024};
   if (scheme == 1)
-    launch_dependent(mix_batch_pass_c_kernel<1>, ls, smem, st, cs, bs, items, par, slot - 1);
+    launch_dependent(mix_batch_pass_c_kernel<1>, ls, smem, st, cs, bs, items, par, prev_slot);
   else
-    launch_dependent(mix_batch_pass_c_kernel<2>, ls, smem, st, cs, bs, items, par, slot - 1);
+    launch_dependent(mix_batch_pass_c_kernel<2>, ls, smem, st, cs, bs, items, par, prev_slot);
 }
 
 void es1d_batch_pass_e(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,

@@ -6,6 +6,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -1071,6 +1073,8 @@ struct pic_batch {
   int scheme = 2;
   size_t smem = 0;
   int nitems = 0;
+  int trips = 8;  // target 4-marker trips per 1024-thread block of a run
+  bool prev_closed = false;  // the last pending step's TE was reduced already
   Es1dMixConst *d_c = nullptr;
   Es1dMixBufs *d_b = nullptr;
   BatchItem *d_items = nullptr;
@@ -1099,16 +1103,38 @@ struct pic_batch {
   void enqueue(int nsteps, int first_slot) {
     for (int k = 0; k < nsteps; k++) {
       const int64_t step = steps_done + k;
-      es1d_batch_pass_c(d_c, d_b, d_items, nitems, scheme, smem, step, first_slot + k, st);
+      const int prev = (k == 0 && prev_closed) ? -1 : first_slot + k - 1;
+      es1d_batch_pass_c(d_c, d_b, d_items, nitems, scheme, smem, step, prev, st);
       es1d_batch_pass_e(d_c, d_b, d_items, nitems, scheme, smem, step, first_slot + k, st);
     }
+    if (nsteps > 0) prev_closed = false;
   }
 };
 
 namespace {
-// Blocks of 1024 threads per run: about this many 4-marker trips each (at most
+// Blocks of 1024 threads per run: about `trips` 4-marker trips each (at most
 // 16, the bound the runs' integer tiles are sized for).
 constexpr int kBatchTrips = 8;
+
+// Work list of a batch for a trip target; returns the blocks per run.
+std::vector<int> batch_items(const std::vector<pic_handle *> &runs, int trips,
+                             std::vector<BatchItem> &items) {
+  std::vector<int> nbs;
+  items.clear();
+  for (int r = 0; r < (int)runs.size(); r++) {
+    const pic_handle *h = runs[r];
+    const int64_t ngroups = (h->N + 3) / 4;
+    int nb = (int)std::max<int64_t>(1, (ngroups + 1024 * trips - 1) / (1024 * trips));
+    nb = std::min(nb, h->ls.grid);  // the run's per-block partials hold ls.grid entries
+    while ((ngroups + (int64_t)nb * 1024 - 1) / ((int64_t)nb * 1024) > 16 && nb < h->ls.grid) nb++;
+    nbs.push_back(nb);
+    for (int k = 0; k < nb; k++) items.push_back(BatchItem{r, k, nb});
+  }
+  return nbs;
+}
+
+// Tuned trip targets, per (runs, log2 of all markers, largest grid) in this process.
+std::map<std::tuple<int, int, int>, int> g_batch_tuned;
 }  // namespace
 
 extern "C" {
@@ -1149,16 +1175,16 @@ int pic_batch_init(const pic_config *cfgs, const pic_species *species, int nruns
     b->st = h->st;
     hc[r] = h->cm;
     hb[r] = h->bm;
-    const int64_t ngroups = (h->N + 3) / 4;
-    int nb = (int)std::max<int64_t>(1, (ngroups + 1024 * kBatchTrips - 1) / (1024 * kBatchTrips));
-    nb = std::min(nb, h->ls.grid);  // the run's per-block partials hold ls.grid entries
-    if ((ngroups + (int64_t)nb * 1024 - 1) / ((int64_t)nb * 1024) > 16) {
+    b->smem = std::max(b->smem, es1d_mix_smem_max(h->cm));
+  }
+  b->trips = kBatchTrips;
+  nbs = batch_items(b->runs, b->trips, items);
+  for (int r = 0; r < nruns; r++) {
+    const int64_t ngroups = (b->runs[r]->N + 3) / 4;
+    if ((ngroups + (int64_t)nbs[r] * 1024 - 1) / ((int64_t)nbs[r] * 1024) > 16) {
       delete b;
       return fail(PIC_ERR_UNSUPPORTED, "pic_batch_init: run %d is too large for a batch", r);
     }
-    nbs[r] = nb;
-    for (int k = 0; k < nb; k++) items.push_back(BatchItem{r, k, nb});
-    b->smem = std::max(b->smem, es1d_mix_smem_max(h->cm));
   }
   b->nitems = (int)items.size();
   if (!cfgs[0].cuda_stream) {
@@ -1198,9 +1224,92 @@ int pic_batch_init(const pic_config *cfgs, const pic_species *species, int nruns
   return PIC_OK;
 }
 
+// Replaces the work list for a new trip target (the graphs captured with the
+// old list are dropped).
+static int batch_retarget(pic_batch *b, int trips) {
+  std::vector<BatchItem> items;
+  std::vector<int> nbs = batch_items(b->runs, trips, items);
+  for (int r = 0; r < (int)b->runs.size(); r++) {
+    const int64_t ngroups = (b->runs[r]->N + 3) / 4;
+    if ((ngroups + (int64_t)nbs[r] * 1024 - 1) / ((int64_t)nbs[r] * 1024) > 16) return PIC_OK;
+  }
+  CUDA_TRY(cudaStreamSynchronize(b->st));
+  if (b->pending && !b->prev_closed) {
+    // the energy of the last pending step is reduced over the old work list's
+    // block partials now, and not again by the next step's pass C
+    es1d_batch_finalize(b->d_c, b->d_b, b->d_nb, (int)b->runs.size(), b->pending - 1, b->st);
+    CUDA_TRY(cudaGetLastError());
+    b->prev_closed = true;
+  }
+  cudaFree(b->d_items);
+  cudaFree(b->d_nb);
+  b->d_items = nullptr;
+  b->d_nb = nullptr;
+  CUDA_TRY(cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size()));
+  CUDA_TRY(cudaMalloc(&b->d_nb, sizeof(int) * nbs.size()));
+  CUDA_TRY(cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(),
+                      cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->d_nb, nbs.data(), sizeof(int) * nbs.size(), cudaMemcpyHostToDevice));
+  for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+  b->graphs.clear();
+  b->nitems = (int)items.size();
+  b->trips = trips;
+  return PIC_OK;
+}
+
 int pic_batch_set_graph(pic_batch *b, int on) {
   if (!b) return fail(PIC_ERR_ARG, "pic_batch_set_graph: NULL batch");
   b->use_graph = on != 0;
+  return PIC_OK;
+}
+
+int pic_batch_autotune(pic_batch *b, int steps_per_trial, int *trips) {
+  if (!b || steps_per_trial <= 0) return fail(PIC_ERR_ARG, "pic_batch_autotune: bad arguments");
+  int64_t markers = 0;
+  int ncmax = 0;
+  for (pic_handle *h : b->runs) {
+    markers += h->N;
+    ncmax = std::max(ncmax, h->cm.nc);
+  }
+  int lg = 0;
+  while (((int64_t)1 << lg) < markers) lg++;
+  const auto key = std::make_tuple((int)b->runs.size(), lg, ncmax);
+  auto it = g_batch_tuned.find(key);
+  int best = b->trips;
+  if (it != g_batch_tuned.end()) {
+    best = it->second;
+  } else {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    for (int t : {4, 8, 16}) {
+      if (b->pending + steps_per_trial > kStepsCap) break;
+      int rc = batch_retarget(b, t);
+      if (rc) return rc;
+      if (b->trips != t) continue;  // this target would break the tiles' bound
+      CUDA_TRY(cudaEventRecord(e0, b->st));
+      b->enqueue(steps_per_trial, b->pending);
+      CUDA_TRY(cudaEventRecord(e1, b->st));
+      CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      b->launches += 2 * steps_per_trial;
+      b->steps_done += steps_per_trial;
+      b->pending += steps_per_trial;
+      for (pic_handle *h : b->runs) h->steps_done += steps_per_trial;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_batch_tuned[key] = best;
+  }
+  int rc = batch_retarget(b, best);
+  if (rc) return rc;
+  if (trips) *trips = b->trips;
   return PIC_OK;
 }
 
@@ -1247,7 +1356,8 @@ int pic_batch_read_stats(pic_batch *b, int capacity, int64_t *nfallback, double 
     if ((nfallback || te) && capacity < n)
       return fail(PIC_ERR_ARG, "pic_batch_read_stats: %d steps pending, capacity %d", n,
                   capacity);
-    es1d_batch_finalize(b->d_c, b->d_b, b->d_nb, nruns, n - 1, b->st);
+    if (!b->prev_closed) es1d_batch_finalize(b->d_c, b->d_b, b->d_nb, nruns, n - 1, b->st);
+    b->prev_closed = false;
     es1d_batch_gather_stats(b->d_b, nruns, n, b->d_fb, b->d_te, b->st);
     CUDA_TRY(cudaGetLastError());
     b->launches += 2;

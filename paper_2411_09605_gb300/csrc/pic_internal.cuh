@@ -210,8 +210,9 @@ void es1d_mix_set_ek(const Es1dMixConst &c, const Es1dMixBufs &b, int parity, cu
 // batched runs (unsorted, nc <= kWideMaxNodes, one scheme): device arrays of the
 // runs' constants and buffers and the work list of nitems blocks
 cudaError_t es1d_batch_prepare(size_t smem);
+// prev_slot: stats slot of the previous step to reduce (TE), or -1
 void es1d_batch_pass_c(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,
-                       int nitems, int scheme, size_t smem, int64_t step_index, int slot,
+                       int nitems, int scheme, size_t smem, int64_t step_index, int prev_slot,
                        cudaStream_t st);
 void es1d_batch_pass_e(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,
                        int nitems, int scheme, size_t smem, int64_t step_index, int slot,

@@ -33,7 +33,7 @@ EXPORTS = ["pic_init", "pic_step", "pic_step_async", "pic_read_stats", "pic_laun
            "pic_set_particles", "pic_get_fields", "pic_set_fields", "pic_step_count", "pic_free",
            "pic_last_error", "pic_version", "pic_es1d_step_noalloc",
            "pic_batch_init", "pic_batch_step", "pic_batch_set_graph", "pic_batch_read_stats",
-           "pic_batch_run", "pic_batch_info", "pic_batch_free"]
+           "pic_batch_run", "pic_batch_info", "pic_batch_free", "pic_batch_autotune"]
 
 
 class PicError(RuntimeError):
@@ -98,6 +98,7 @@ def lib() -> C.CDLL:
         L.pic_batch_read_stats.argtypes = [vp, C.c_int, vp, vp, C.POINTER(C.c_int)]
         L.pic_batch_run.argtypes = [vp, C.c_int, C.POINTER(vp)]
         L.pic_batch_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), i64p]
+        L.pic_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.pic_batch_free.argtypes = [vp]
         L.pic_batch_free.restype = None
         L.pic_last_error.restype = C.c_char_p
@@ -382,6 +383,14 @@ def pic_batch_info(b: int):
     nr, nb, nl = C.c_int(), C.c_int(), C.c_int64()
     _check(lib().pic_batch_info(b, C.byref(nr), C.byref(nb), C.byref(nl)))
     return nr.value, nb.value, nl.value
+
+
+def pic_batch_autotune(b: int, steps_per_trial: int) -> int:
+    """Times each work list for steps_per_trial real steps and keeps the fastest;
+    returns its trips per block."""
+    t = C.c_int()
+    _check(lib().pic_batch_autotune(b, steps_per_trial, C.byref(t)))
+    return t.value
 
 
 def pic_batch_free(b: int):

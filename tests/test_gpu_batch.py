@@ -86,3 +86,26 @@ def test_batched_run_follows_the_oracle():
     ref = oracle_run(prob, 2, 10)
     d = compare(prob, ref, {"x": [got[0][0]], "v": [got[0][1]], "E": got[0][2]})
     assert d["x"] <= 1e-6 and d["v"] <= 1e-6 and d["E"] <= 3e-6, d
+
+
+def test_autotune_keeps_the_runs_exact():
+    """Tuning runs real steps with three work lists (4, 8 and 16 trips per
+    block), switching between them; the runs and their per-step energies must be
+    those of the runs stepped alone."""
+    from paper_2411_09605_gb300 import pic
+    probs = _problems()[:3]
+    b = pic.Batch(probs)
+    try:
+        trips = pic.pic_batch_autotune(b.b, 2)
+        assert trips in (4, 8, 16)
+        fb, te = b.step(3)        # reads the 6 tuning steps and 3 more
+        assert fb.shape == (3, 9)
+        out = [(*b.particles(r), b.field(r)) for r in range(len(probs))]
+    finally:
+        b.close()
+    for r, p in enumerate(probs):
+        x, v, E, fb1, te1 = _alone(p, 9)
+        assert np.array_equal(out[r][0], x) and np.array_equal(out[r][1], v), r
+        assert np.array_equal(out[r][2], E), r
+        assert np.array_equal(fb[r], fb1), r
+        assert np.max(np.abs(te[r] - te1)) <= 1e-14 * abs(te1[0]), r
