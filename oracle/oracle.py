@@ -85,6 +85,8 @@ def _declare(L):
                                _dp, _dp, _lp]
     L.orc_es1d_run.restype = C.c_int
     L.orc_poisson_e0_1d.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp]
+    L.orc_es1d_grad.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp, C.c_long,
+                                _dp, C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp)]
     L.orc_yee_curl_e.argtypes = [C.c_long, C.c_long, C.c_double, C.c_double] + [_dp] * 6
     L.orc_yee_curl_b.argtypes = [C.c_long, C.c_long, C.c_double, C.c_double] + [_dp] * 6
     L.orc_vstar_solve.argtypes = [_dp, _dp, _dp]
@@ -194,6 +196,24 @@ def es1d_run(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray, nsteps:
                             _ptr(we), nfb.ctypes.data_as(_lp))
     assert rc == 0
     return te, we, nfb
+
+
+def es1d_grad(cfg: ES1DConfig, species: Sequence[Species], E0: np.ndarray, nsteps: int,
+              Ebar: np.ndarray, xbar: Sequence[np.ndarray], vbar: Sequence[np.ndarray]):
+    """Reverse mode of nsteps steps from the state (species, E0), which is left
+    unchanged.  Ebar, xbar, vbar: adjoints of the final field and markers.
+    Returns (Ebar, xbar, vbar, wbar) of the initial state (wbar[s] per marker, or
+    one entry for a uniform w0)."""
+    sp = _sp_array(species)
+    Eb = np.ascontiguousarray(Ebar, dtype=np.float64).copy()
+    xb = [np.ascontiguousarray(a, dtype=np.float64).copy() for a in xbar]
+    vb = [np.ascontiguousarray(a, dtype=np.float64).copy() for a in vbar]
+    wb = [np.zeros(len(s.x) if s.w is not None else 1) for s in species]
+    arr = lambda lst: (_dp * len(lst))(*[_ptr(a) for a in lst])  # noqa: E731
+    rc = lib().orc_es1d_grad(C.byref(cfg._c()), sp, len(species), _ptr(np.ascontiguousarray(E0)),
+                             nsteps, _ptr(Eb), arr(xb), arr(vb), arr(wb))
+    assert rc == 0
+    return Eb, xb, vb, wb
 
 
 def poisson_e0_1d(cfg: ES1DConfig, species: Sequence[Species]):

@@ -291,6 +291,283 @@ int orc_es1d_step(const orc_es1d_cfg *cfg, orc_species *sp, int nsp,
   return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Reverse mode of the 1D1V step (for gradients of a final objective)        */
+/* ------------------------------------------------------------------------ */
+
+/* Shape weights and their derivatives dS/dxi at xi = x/h (order 1: the tent,
+ * piecewise; order 2: the quadratic B-spline, continuously differentiable). */
+static int shape_weights_deriv(int order, double xi, long nc, long *idx, double *wt,
+                               double *dwt) {
+  int k = orc_shape_weights(order, xi, nc, idx, wt);
+  if (order == 1) {
+    dwt[0] = -1.0;
+    dwt[1] = 1.0;
+  } else {
+    double d = xi - floor(xi + 0.5);
+    dwt[0] = -(0.5 - d);
+    dwt[1] = -2.0 * d;
+    dwt[2] = 0.5 + d;
+  }
+  return k;
+}
+
+/* Adjoint of Eout = Ein - tau (J - <J>): Ein_bar += Eout_bar and the
+ * returned Jbar = -tau (Eout_bar - <Eout_bar>) (the mean removal is symmetric). */
+static void ampere_adjoint(const orc_es1d_cfg *cfg, const double *Eout_bar, double tau,
+                           double *Ein_bar, double *Jbar) {
+  double mean = 0.0;
+  if (cfg->remove_mean) {
+    for (long i = 0; i < cfg->nc; i++) mean += Eout_bar[i];
+    mean /= (double)cfg->nc;
+  }
+  for (long i = 0; i < cfg->nc; i++) {
+    Ein_bar[i] += Eout_bar[i];
+    Jbar[i] = -tau * (Eout_bar[i] - mean);
+  }
+}
+
+/*
+ * Gradients through nsteps steps of orc_es1d_step, by reverse mode (the
+ * adjoint of each operation of the step, taken in the reverse order):
+ *   deposit J_h = sum_p c_p S(x_p - x_h)/h  ->  c_bar_p = sum_h J_bar_h S/h,
+ *                                              x_bar_p += c_p sum_h J_bar_h S'/h^2
+ *   gather  a_p = sum_h E_h S(x_p - x_h)    ->  E_bar_h += a_bar_p S,
+ *                                              x_bar_p += a_bar_p sum_h E_h S'/h
+ *   Gamma (Sec. 3.2): v^{n+1} = v^dag sqrt(R)/|v^dag| with R = |v^n|^2 +
+ *   2 v* (v^dag - v^n); in 1D v^{n+1} = sign(v^dag) sqrt(R), so only R
+ *   carries the adjoint: R_bar = v_bar^{n+1} sign(v^dag) / (2 sqrt(R)); a
+ *   fallback (Gamma := 1) passes v_bar^{n+1} to v^dag.
+ * The periodic wrap has derivative 1.
+ * On entry sp and E hold the initial state (unchanged on return), Ebar the
+ * adjoint of the final field, xbar[s], vbar[s] the adjoints of the final
+ * markers; on return Ebar, xbar, vbar hold the adjoints of the initial state
+ * and wbar[s] (if not NULL) the adjoint of each marker's weight (of w0 summed
+ * over the markers of a uniformly weighted species).  Returns 0.
+ * Pinned by central differences of orc_es1d_run (test_oracle_grad.py).
+ */
+int orc_es1d_grad(const orc_es1d_cfg *cfg, const orc_species *sp0, int nsp, const double *E0,
+                  long nsteps, double *Ebar, double *const *xbar, double *const *vbar,
+                  double *const *wbar) {
+  long nc = cfg->nc;
+  double L = cfg->L, dt = cfg->dt, h = L / (double)nc;
+  /* forward, keeping every step's markers and field */
+  double **X = (double **)calloc((size_t)nsp * (nsteps + 1), sizeof(double *));
+  double **V = (double **)calloc((size_t)nsp * (nsteps + 1), sizeof(double *));
+  double *Eh = (double *)calloc((size_t)nc * (nsteps + 1), sizeof(double));
+  orc_species *sp = (orc_species *)calloc((size_t)nsp, sizeof(orc_species));
+  for (long i = 0; i < nc; i++) Eh[i] = E0[i];
+  for (int s = 0; s < nsp; s++) {
+    sp[s] = sp0[s];
+    X[s] = (double *)calloc((size_t)sp0[s].n + 1, sizeof(double));
+    V[s] = (double *)calloc((size_t)sp0[s].n + 1, sizeof(double));
+    for (long p = 0; p < sp0[s].n; p++) {
+      X[s][p] = sp0[s].x[p];
+      V[s][p] = sp0[s].v[p];
+    }
+  }
+  for (long n = 0; n < nsteps; n++) {
+    double *En = Eh + (n + 1) * nc;
+    for (long i = 0; i < nc; i++) En[i] = Eh[n * nc + i];
+    for (int s = 0; s < nsp; s++) {
+      double *xn = (double *)calloc((size_t)sp0[s].n + 1, sizeof(double));
+      double *vn = (double *)calloc((size_t)sp0[s].n + 1, sizeof(double));
+      for (long p = 0; p < sp0[s].n; p++) {
+        xn[p] = X[n * nsp + s][p];
+        vn[p] = V[n * nsp + s][p];
+      }
+      X[(n + 1) * nsp + s] = xn;
+      V[(n + 1) * nsp + s] = vn;
+      sp[s].x = xn;
+      sp[s].v = vn;
+    }
+    orc_es1d_step(cfg, sp, nsp, En, NULL, NULL);
+  }
+
+  /* reverse */
+  double *Estar = (double *)calloc((size_t)nc, sizeof(double));
+  double *J = (double *)calloc((size_t)nc, sizeof(double));
+  double *Ehalf = (double *)calloc((size_t)nc, sizeof(double));
+  double *Jbar = (double *)calloc((size_t)nc, sizeof(double));
+  double *Hbar = (double *)calloc((size_t)nc, sizeof(double));
+  double *Esbar = (double *)calloc((size_t)nc, sizeof(double));
+  double *Enbar = (double *)calloc((size_t)nc, sizeof(double));
+  for (int s = 0; s < nsp; s++)
+    if (wbar && wbar[s])
+      for (long p = 0; p < (sp0[s].w ? sp0[s].n : 1); p++) wbar[s][p] = 0.0;
+  for (long n = nsteps - 1; n >= 0; n--) {
+    const double *En = Eh + n * nc, *Enew = Eh + (n + 1) * nc;
+    /* recompute the step's grid quantities: E*, E^{n+1/2} */
+    if (cfg->scheme == 2) {
+      for (long i = 0; i < nc; i++) J[i] = 0.0;
+      for (int s = 0; s < nsp; s++)
+        for (long p = 0; p < sp0[s].n; p++) {
+          long idx[3];
+          double wt[3];
+          double xs = wrap(X[n * nsp + s][p] + 0.5 * dt * V[n * nsp + s][p], L);
+          int k = orc_shape_weights(cfg->order, xs / h, nc, idx, wt);
+          double c = sp0[s].q * weight_of(&sp0[s], p) * V[n * nsp + s][p];
+          for (int j = 0; j < k; j++) J[idx[j]] += c * wt[j] / h;
+        }
+      ampere_update(cfg, En, J, 0.5 * dt, Estar);
+    } else {
+      for (long i = 0; i < nc; i++) Estar[i] = En[i];
+    }
+    for (long i = 0; i < nc; i++) {
+      Ehalf[i] = 0.5 * (En[i] + Enew[i]);
+      Hbar[i] = 0.0;
+      Esbar[i] = 0.0;
+      Enbar[i] = 0.0;
+    }
+    /* markers, from v^{n+1}, x^{n+1} back to v*, x^{n+1/2}: H_bar and the
+     * adjoints of v*, x^{n+1/2} (kept in ub, yb) */
+    double **ub = (double **)calloc((size_t)nsp, sizeof(double *));
+    double **yb = (double **)calloc((size_t)nsp, sizeof(double *));
+    for (int s = 0; s < nsp; s++) {
+      double qm = sp0[s].q / sp0[s].m;
+      ub[s] = (double *)calloc((size_t)sp0[s].n + 1, sizeof(double));
+      yb[s] = (double *)calloc((size_t)sp0[s].n + 1, sizeof(double));
+      for (long p = 0; p < sp0[s].n; p++) {
+        const double xn = X[n * nsp + s][p], vn = V[n * nsp + s][p];
+        long idx[3];
+        double wt[3], dwt[3];
+        double xs = wrap(xn + 0.5 * dt * vn, L);
+        int k = orc_shape_weights(cfg->order, xs / h, nc, idx, wt);
+        double a = 0.0;
+        for (int j = 0; j < k; j++) a += Estar[idx[j]] * wt[j];
+        double u = vn + 0.5 * dt * qm * a;
+        double y = wrap(xn + 0.5 * dt * u, L);
+        k = shape_weights_deriv(cfg->order, y / h, nc, idx, wt, dwt);
+        double b = 0.0, bp = 0.0;
+        for (int j = 0; j < k; j++) {
+          b += Ehalf[idx[j]] * wt[j];
+          bp += Ehalf[idx[j]] * dwt[j];
+        }
+        double d = vn + dt * qm * b;
+        double R = vn * vn + 2.0 * u * (d - vn);
+        double vb1 = vbar[s][p], xb1 = xbar[s][p];
+        /* x^{n+1} = x^n + dt v* */
+        double xb = xb1, ubar = dt * xb1, vb = 0.0, db = 0.0;
+        /* v^{n+1} */
+        if (cfg->gamma_on && !(R < 0.0 || d * d == 0.0)) {
+          double Rb = vb1 * (d > 0.0 ? 1.0 : -1.0) / (2.0 * sqrt(R));
+          vb += Rb * (2.0 * vn - 2.0 * u);
+          ubar += Rb * 2.0 * (d - vn);
+          db += Rb * 2.0 * u;
+        } else {
+          db += vb1;
+        }
+        /* v^dag = v^n + dt (q/m) b */
+        vb += db;
+        double bb = db * dt * qm;
+        for (int j = 0; j < k; j++) Hbar[idx[j]] += bb * wt[j];
+        double ybar = bb * bp / h;
+        xbar[s][p] = xb;
+        vbar[s][p] = vb;
+        ub[s][p] = ubar;
+        yb[s][p] = ybar;
+      }
+    }
+    /* E^{n+1/2} = (E^n + E^{n+1})/2 and E^{n+1} = E^n - dt (j - <j>) */
+    for (long i = 0; i < nc; i++) {
+      Enbar[i] = Ebar[i] + 0.5 * Hbar[i];  /* adjoint of E^{n+1} */
+      Ebar[i] = 0.5 * Hbar[i];             /* adjoint of E^n so far */
+    }
+    ampere_adjoint(cfg, Enbar, dt, Ebar, Jbar);
+    /* j^{*,n+1/2} = deposit of v* at x^{n+1/2}; v* = v^n + dt/2 (q/m) a;
+     * x^{n+1/2} = x^n + dt/2 v*; a = gather of E* at x* */
+    for (int s = 0; s < nsp; s++) {
+      double qm = sp0[s].q / sp0[s].m;
+      for (long p = 0; p < sp0[s].n; p++) {
+        const double xn = X[n * nsp + s][p], vn = V[n * nsp + s][p];
+        const double w = weight_of(&sp0[s], p);
+        long idx[3];
+        double wt[3], dwt[3];
+        double xs = wrap(xn + 0.5 * dt * vn, L);
+        int k = shape_weights_deriv(cfg->order, xs / h, nc, idx, wt, dwt);
+        double a = 0.0, ap = 0.0;
+        for (int j = 0; j < k; j++) {
+          a += Estar[idx[j]] * wt[j];
+          ap += Estar[idx[j]] * dwt[j];
+        }
+        double u = vn + 0.5 * dt * qm * a;
+        double y = wrap(xn + 0.5 * dt * u, L);
+        long idy[3];
+        double wy[3], dwy[3];
+        int ky = shape_weights_deriv(cfg->order, y / h, nc, idy, wy, dwy);
+        double g = 0.0, gp = 0.0;
+        for (int j = 0; j < ky; j++) {
+          g += Jbar[idy[j]] * wy[j] / h;
+          gp += Jbar[idy[j]] * dwy[j] / (h * h);
+        }
+        double c = sp0[s].q * w * u;
+        double ubar = ub[s][p] + sp0[s].q * w * g;
+        double ybar = yb[s][p] + c * gp;
+        if (wbar && wbar[s]) wbar[s][sp0[s].w ? p : 0] += sp0[s].q * u * g;
+        xbar[s][p] += ybar;
+        ubar += 0.5 * dt * ybar;
+        vbar[s][p] += ubar;
+        double abar = 0.5 * dt * qm * ubar;
+        for (int j = 0; j < k; j++) Esbar[idx[j]] += abar * wt[j];
+        double xsb = abar * ap / h;
+        ub[s][p] = xsb;  /* adjoint of x* so far */
+      }
+    }
+    /* E* = E^n - dt/2 (j^{n,*} - <.>) (ESEC2) or E^n (ESEC1) */
+    if (cfg->scheme == 2) {
+      ampere_adjoint(cfg, Esbar, 0.5 * dt, Ebar, Jbar);
+      for (int s = 0; s < nsp; s++)
+        for (long p = 0; p < sp0[s].n; p++) {
+          const double xn = X[n * nsp + s][p], vn = V[n * nsp + s][p];
+          const double w = weight_of(&sp0[s], p);
+          long idx[3];
+          double wt[3], dwt[3];
+          double xs = wrap(xn + 0.5 * dt * vn, L);
+          int k = shape_weights_deriv(cfg->order, xs / h, nc, idx, wt, dwt);
+          double g = 0.0, gp = 0.0;
+          for (int j = 0; j < k; j++) {
+            g += Jbar[idx[j]] * wt[j] / h;
+            gp += Jbar[idx[j]] * dwt[j] / (h * h);
+          }
+          if (wbar && wbar[s]) wbar[s][sp0[s].w ? p : 0] += sp0[s].q * vn * g;
+          vbar[s][p] += sp0[s].q * w * g;
+          ub[s][p] += sp0[s].q * w * vn * gp;
+        }
+    } else {
+      for (long i = 0; i < nc; i++) Ebar[i] += Esbar[i];
+    }
+    /* x* = x^n + dt/2 v^n */
+    for (int s = 0; s < nsp; s++)
+      for (long p = 0; p < sp0[s].n; p++) {
+        xbar[s][p] += ub[s][p];
+        vbar[s][p] += 0.5 * dt * ub[s][p];
+      }
+    for (int s = 0; s < nsp; s++) {
+      free(ub[s]);
+      free(yb[s]);
+    }
+    free(ub);
+    free(yb);
+  }
+  for (long k = 0; k <= nsteps; k++)
+    for (int s = 0; s < nsp; s++) {
+      free(X[k * nsp + s]);
+      free(V[k * nsp + s]);
+    }
+  free(X);
+  free(V);
+  free(Eh);
+  free(sp);
+  free(Estar);
+  free(J);
+  free(Ehalf);
+  free(Jbar);
+  free(Hbar);
+  free(Esbar);
+  free(Enbar);
+  return 0;
+}
+
 /*
  * Energies of Sec. 5.1: KE_s = (1/2) m_s sum_p w_p v_p^2 per species and
  * W_E = (1/2) h sum_h E_h^2.  Pinned through the energy identity tests.
