@@ -208,6 +208,34 @@ int pic_es1d_step_noalloc(const pic_config *cfg, double q, double m, double w0, 
                           double *x, double *v, double *E, int nsteps,
                           int64_t *nfallback_per_step, double *te_per_step);
 
+/* ------------------------------------------------------------ gradients
+ * Reverse mode of the FP64 1D form (solver PIC_SOLVER_AMPERE_ES, precision
+ * PIC_PREC_FP64, either scheme and shape order): derivatives of an objective
+ * of the state after nsteps steps with respect to the state before them.  The
+ * paper conserves energy exactly but does not differentiate the scheme; the
+ * reverse pass takes the adjoint of every operation of Sec. 3.3 in reverse
+ * order (gather and deposit swap roles; Gamma of Sec. 3.2 is differentiated
+ * through R, and a fallback through v^dag).
+ *
+ * pic_grad_forward steps h forward nsteps steps (as pic_step_async; pending
+ * stats must have been read) and keeps the markers and field every
+ * checkpoint_every steps on the device ((nsteps / checkpoint_every + 1) x
+ * (2 N + nodes) doubles).
+ *
+ * pic_grad_backward takes the adjoints of the state after those steps -
+ * Ebar [nodes], xbar [N], vbar [N] (host or device, NULL = zero) - and writes
+ * the adjoints of the state before them: Ebar0 [nodes], xbar0, vbar0 and wbar0
+ * [N] (the derivative by each marker's weight; for a uniformly weighted
+ * species the derivative by its w0 is the sum over its markers), host or
+ * device, each may be NULL.  Each segment of checkpoint_every steps is
+ * re-run from its checkpoint and reversed; h is left at the state after the
+ * forward steps.  The step sequence must not change in between, else
+ * PIC_ERR_ARG.
+ */
+int pic_grad_forward(pic_handle *h, int nsteps, int checkpoint_every);
+int pic_grad_backward(pic_handle *h, const double *Ebar, const double *xbar, const double *vbar,
+                      double *Ebar0, double *xbar0, double *vbar0, double *wbar0);
+
 /* Number of steps taken since pic_init. */
 int pic_step_count(pic_handle *h, int64_t *steps);
 

@@ -97,6 +97,17 @@ struct pic_handle {
   int sort_blocks = 0;
   int nsm = 0;
   int64_t *ids = nullptr;
+  // reverse mode (pic_grad_forward / pic_grad_backward), FP64 1D form
+  struct Grad {
+    int64_t start = -1;       // step count when pic_grad_forward began
+    int nsteps = 0, every = 0, nck = 0;
+    double *ckpt = nullptr;   // [nck][2N + nc] x, v, E every `every` steps
+    double *seg = nullptr;    // [every + 1][2N + nc] the states of one segment
+    double *fin = nullptr;    // [2N + nc] the state after the forward steps
+    double *grid = nullptr;   // [7][nc] E*, H, J1, H_bar, E*_bar, J_bar, E_bar
+    double *mk = nullptr;     // [5][N] x_bar, v_bar, w_bar and marker scratch
+    size_t ckpt_cap = 0, seg_cap = 0;
+  } grad;
   std::vector<void *> allocs;
 
   template <typename T>
@@ -116,6 +127,9 @@ struct pic_handle {
       cudaEventDestroy(t.b);
     }
     for (void *p : allocs) cudaFree(p);
+    for (void *p : {(void *)grad.ckpt, (void *)grad.seg, (void *)grad.fin, (void *)grad.grid,
+                    (void *)grad.mk})
+      if (p) cudaFree(p);
   }
   // Brackets the launches issued by f with timing events when profiling.
   template <typename F>
@@ -500,6 +514,23 @@ int init_es1d(pic_handle *h, const pic_species *species, const double *E0) {
   }
   CUDA_TRY(cudaStreamSynchronize(h->st));
   return check_flags(h, "pic_init");
+}
+
+// Copies the FP64 1D state (x, v and E of the current step) to or from a
+// packed [2N + nc] device buffer.
+cudaError_t state_copy(pic_handle *h, double *buf, bool save) {
+  const size_t N = (size_t)h->N, nc = (size_t)h->c1.nc;
+  double *E = h->b1.E[h->steps_done & 1];
+  double *dst[3] = {buf, buf + N, buf + 2 * N}, *src[3] = {h->b1.x, h->b1.v, E};
+  const size_t cnt[3] = {N, N, nc};
+  for (int k = 0; k < 3; k++) {
+    cudaError_t e = save ? cudaMemcpyAsync(dst[k], src[k], sizeof(double) * cnt[k],
+                                           cudaMemcpyDeviceToDevice, h->st)
+                         : cudaMemcpyAsync(src[k], dst[k], sizeof(double) * cnt[k],
+                                           cudaMemcpyDeviceToDevice, h->st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Re-establishes the invariants of the step sequence after a state change:
@@ -1044,6 +1075,123 @@ int pic_set_fields(pic_handle *h, const double *E, const double *B) {
                            cudaMemcpyDefault, h->st));
   CUDA_TRY(cudaStreamSynchronize(h->st));
   return restart_es1d(h, false);
+}
+
+int pic_grad_forward(pic_handle *h, int nsteps, int checkpoint_every) {
+  if (!h || nsteps <= 0 || checkpoint_every <= 0)
+    return fail(PIC_ERR_ARG, "pic_grad_forward: bad arguments");
+  if (h->em || h->mixed)
+    return fail(PIC_ERR_UNSUPPORTED, "pic_grad_forward: the reverse mode is built for the FP64 "
+                                     "1D form");
+  if (h->pending) return fail(PIC_ERR_ARG, "pic_grad_forward: read the pending stats first");
+  if (checkpoint_every > kStepsCap) checkpoint_every = kStepsCap;
+  pic_handle::Grad &g = h->grad;
+  const size_t N = (size_t)h->N, nc = (size_t)h->c1.nc, len = 2 * N + nc;
+  const int nck = (nsteps + checkpoint_every - 1) / checkpoint_every;
+  if ((size_t)nck * len > g.ckpt_cap) {
+    if (g.ckpt) cudaFree(g.ckpt);
+    g.ckpt = nullptr;
+    g.ckpt_cap = 0;
+    CUDA_TRY(cudaMalloc(&g.ckpt, sizeof(double) * nck * len));
+    g.ckpt_cap = (size_t)nck * len;
+  }
+  g.start = h->steps_done;
+  g.nsteps = nsteps;
+  g.every = checkpoint_every;
+  g.nck = nck;
+  for (int k = 0; k < nsteps; k++) {
+    if (k % checkpoint_every == 0)
+      CUDA_TRY(state_copy(h, g.ckpt + (size_t)(k / checkpoint_every) * len, true));
+    if (h->pending == kStepsCap) {
+      int rc = pic_read_stats(h, 0, nullptr, nullptr, nullptr);
+      if (rc) return rc;
+    }
+    int rc = pic_step_async(h, 1);
+    if (rc) return rc;
+  }
+  return PIC_OK;
+}
+
+int pic_grad_backward(pic_handle *h, const double *Ebar, const double *xbar, const double *vbar,
+                      double *Ebar0, double *xbar0, double *vbar0, double *wbar0) {
+  if (!h) return fail(PIC_ERR_ARG, "pic_grad_backward: NULL handle");
+  pic_handle::Grad &g = h->grad;
+  if (g.start < 0 || h->steps_done != g.start + g.nsteps)
+    return fail(PIC_ERR_ARG, "pic_grad_backward: no pic_grad_forward ends at the current step");
+  int rc = pic_read_stats(h, 0, nullptr, nullptr, nullptr);
+  if (rc) return rc;
+  const size_t N = (size_t)h->N, nc = (size_t)h->c1.nc, len = 2 * N + nc;
+  const int every = g.every;
+  if (!g.fin) {
+    CUDA_TRY(cudaMalloc(&g.fin, sizeof(double) * len));
+    CUDA_TRY(cudaMalloc(&g.grid, sizeof(double) * 7 * nc));
+    CUDA_TRY(cudaMalloc(&g.mk, sizeof(double) * 5 * N));
+  }
+  if ((size_t)(every + 1) * len > g.seg_cap) {
+    if (g.seg) cudaFree(g.seg);
+    g.seg = nullptr;
+    g.seg_cap = 0;
+    CUDA_TRY(cudaMalloc(&g.seg, sizeof(double) * (every + 1) * len));
+    g.seg_cap = (size_t)(every + 1) * len;
+  }
+  CUDA_TRY(es1d_grad_prepare(h->c1));
+  Es1dGradBufs gb{};
+  gb.w = h->b1.w;
+  for (int s = 0; s < h->nsp; s++) gb.w0[s] = h->sp[s].w0;
+  gb.Estar = g.grid;
+  gb.H = g.grid + nc;
+  gb.J1 = g.grid + 2 * nc;
+  gb.Hbar = g.grid + 3 * nc;
+  gb.Esbar = g.grid + 4 * nc;
+  gb.Jbar = g.grid + 5 * nc;
+  gb.Ebar = g.grid + 6 * nc;
+  gb.xbar = g.mk;
+  gb.vbar = g.mk + N;
+  gb.wbar = g.mk + 2 * N;
+  gb.ub = g.mk + 3 * N;
+  gb.yb = g.mk + 4 * N;
+  gb.err = h->b1.err;
+  // adjoints of the final state (NULL = 0)
+  CUDA_TRY(cudaMemsetAsync(g.mk, 0, sizeof(double) * 5 * N, h->st));
+  CUDA_TRY(cudaMemsetAsync(g.grid, 0, sizeof(double) * 7 * nc, h->st));
+  if (Ebar) CUDA_TRY(cudaMemcpyAsync(gb.Ebar, Ebar, sizeof(double) * nc, cudaMemcpyDefault, h->st));
+  if (xbar) CUDA_TRY(cudaMemcpyAsync(gb.xbar, xbar, sizeof(double) * N, cudaMemcpyDefault, h->st));
+  if (vbar) CUDA_TRY(cudaMemcpyAsync(gb.vbar, vbar, sizeof(double) * N, cudaMemcpyDefault, h->st));
+  CUDA_TRY(state_copy(h, g.fin, true));
+  const int64_t fin_step = h->steps_done;
+  for (int seg = g.nck - 1; seg >= 0; seg--) {
+    const int s0 = seg * every, s1 = std::min(g.nsteps, s0 + every);
+    // re-run the segment from its checkpoint, keeping every step's state
+    h->steps_done = g.start + s0;
+    CUDA_TRY(state_copy(h, g.ckpt + (size_t)seg * len, false));
+    if ((rc = restart_es1d(h, false))) return rc;
+    for (int k = s0; k < s1; k++) {
+      CUDA_TRY(state_copy(h, g.seg + (size_t)(k - s0) * len, true));
+      if ((rc = pic_step_async(h, 1))) return rc;
+    }
+    CUDA_TRY(state_copy(h, g.seg + (size_t)(s1 - s0) * len, true));
+    if ((rc = pic_read_stats(h, 0, nullptr, nullptr, nullptr))) return rc;
+    // reverse the segment's steps
+    for (int k = s1 - 1; k >= s0; k--) {
+      const double *st = g.seg + (size_t)(k - s0) * len, *nx = st + len;
+      gb.x = st;
+      gb.v = st + N;
+      es1d_grad_step(h->c1, gb, st + 2 * N, nx + 2 * N, h->ls, h->st);
+      CUDA_TRY(cudaGetLastError());
+      h->launches += h->c1.scheme == 2 ? 7 : 6;
+    }
+  }
+  // adjoints of the initial state
+  if (Ebar0) CUDA_TRY(cudaMemcpyAsync(Ebar0, gb.Ebar, sizeof(double) * nc, cudaMemcpyDefault, h->st));
+  if (xbar0) CUDA_TRY(cudaMemcpyAsync(xbar0, gb.xbar, sizeof(double) * N, cudaMemcpyDefault, h->st));
+  if (vbar0) CUDA_TRY(cudaMemcpyAsync(vbar0, gb.vbar, sizeof(double) * N, cudaMemcpyDefault, h->st));
+  if (wbar0) CUDA_TRY(cudaMemcpyAsync(wbar0, gb.wbar, sizeof(double) * N, cudaMemcpyDefault, h->st));
+  // back to the state after the forward steps
+  h->steps_done = fin_step;
+  CUDA_TRY(state_copy(h, g.fin, false));
+  if ((rc = restart_es1d(h, false))) return rc;
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return check_flags(h, "pic_grad_backward");
 }
 
 int pic_step_count(pic_handle *h, int64_t *steps) {

@@ -155,6 +155,21 @@ struct Es1dFp64Bufs {
   unsigned *err;            // device error flags
 };
 
+// Reverse mode of the FP64 1D form (es1d_grad.cu): the markers and weights of
+// the forward step being reversed, grid scratch and the running adjoints.
+struct Es1dGradBufs {
+  const double *x, *v;      // [N] markers at the start of the step
+  const double *w;          // [N] weights, or null for uniform weights w0[s]
+  double w0[kMaxSpecies];
+  double *Estar, *H, *J1;   // [nc] E*, E^{n+1/2}, j^{n,*} of the step
+  double *Hbar, *Esbar, *Jbar;  // [nc] adjoint scratch
+  double *Ebar;             // [nc] adjoint of the field (E^{n+1} in, E^n out)
+  double *xbar, *vbar;      // [N] adjoints of the markers (after the step in, before out)
+  double *wbar;             // [N] adjoints of the weights, accumulated
+  double *ub, *yb;          // [N] marker scratch
+  unsigned *err;
+};
+
 struct LaunchShape {
   int grid;
   int block;
@@ -162,6 +177,12 @@ struct LaunchShape {
 
 // Sets the message returned by pic_last_error (pic_api.cu).
 void set_last_error(const std::string &msg);
+
+// reverse mode of one FP64 1D step, from the step's starting field E and its
+// result Enew (es1d_grad.cu)
+cudaError_t es1d_grad_prepare(const Es1dConst &c);
+void es1d_grad_step(const Es1dConst &c, const Es1dGradBufs &g, const double *E,
+                    const double *Enew, LaunchShape ls, cudaStream_t st);
 
 // 1D FP64 path (es1d_fp64.cu)
 cudaError_t es1d_fp64_prepare(const Es1dConst &c);

@@ -33,7 +33,8 @@ EXPORTS = ["pic_init", "pic_step", "pic_step_async", "pic_read_stats", "pic_laun
            "pic_set_particles", "pic_get_fields", "pic_set_fields", "pic_step_count", "pic_free",
            "pic_last_error", "pic_version", "pic_es1d_step_noalloc",
            "pic_batch_init", "pic_batch_step", "pic_batch_set_graph", "pic_batch_read_stats",
-           "pic_batch_run", "pic_batch_info", "pic_batch_free", "pic_batch_autotune"]
+           "pic_batch_run", "pic_batch_info", "pic_batch_free", "pic_batch_autotune",
+           "pic_grad_forward", "pic_grad_backward"]
 
 
 class PicError(RuntimeError):
@@ -89,6 +90,8 @@ def lib() -> C.CDLL:
         L.pic_step_count.argtypes = [vp, i64p]
         L.pic_es1d_step_noalloc.argtypes = [C.POINTER(pic_config), C.c_double, C.c_double,
                                              C.c_double, C.c_int64, vp, vp, vp, C.c_int, vp, vp]
+        L.pic_grad_forward.argtypes = [vp, C.c_int, C.c_int]
+        L.pic_grad_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         L.pic_free.argtypes = [vp]
         L.pic_free.restype = None
         L.pic_batch_init.argtypes = [C.POINTER(pic_config), C.POINTER(pic_species), C.c_int,
@@ -444,3 +447,57 @@ class Batch:
         if self.b:
             pic_batch_free(self.b)
             self.b = None
+
+
+# ------------------------------------------------------------------ gradients
+
+
+def pic_grad_forward(h: int, nsteps: int, checkpoint_every: int = 50):
+    _check(lib().pic_grad_forward(h, nsteps, checkpoint_every))
+
+
+def pic_grad_backward(h: int, Ebar=None, xbar=None, vbar=None, Ebar0=None, xbar0=None,
+                      vbar0=None, wbar0=None):
+    """Adjoints of the state before the forward steps into the given arrays."""
+    _check(lib().pic_grad_backward(h, _addr(Ebar), _addr(xbar), _addr(vbar), _addr(Ebar0),
+                                   _addr(xbar0), _addr(vbar0), _addr(wbar0)))
+
+
+def differentiable_steps(h: int, nsteps: int, x0, v0, E0, w=None, checkpoint_every: int = 50):
+    """Steps the FP64 1D handle h (one species) nsteps steps from (x0, v0, E0)
+    and returns (x, v, E) after them as torch tensors whose gradients flow back
+    to x0, v0, E0 and w through pic_grad_backward.  w, when given, must be the
+    marker weights h was created with (the steps use those); its gradient is
+    returned all the same.  Inputs are float64 tensors on the CPU or the GPU."""
+    import torch
+
+    class _Steps(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x0, v0, E0, w):
+            ctx.dev, ctx.n, ctx.nc = x0.device, x0.numel(), E0.numel()
+            xs, vs, Es = (t.detach().contiguous().to(torch.float64) for t in (x0, v0, E0))
+            if ctx.dev.type == "cuda":
+                torch.cuda.synchronize(ctx.dev)
+            pic_set_particles(h, 0, xs, vs)
+            pic_set_fields(h, Es)
+            pic_grad_forward(h, nsteps, checkpoint_every)
+            x, v, E = torch.empty_like(xs), torch.empty_like(vs), torch.empty_like(Es)
+            pic_get_particles(h, 0, x, v)
+            pic_get_fields(h, E)
+            return x, v, E
+
+        @staticmethod
+        def backward(ctx, gx, gv, gE):
+            gx, gv, gE = (None if t is None else t.detach().contiguous().to(torch.float64)
+                          for t in (gx, gv, gE))
+            xb0 = torch.zeros(ctx.n, dtype=torch.float64, device=ctx.dev)
+            vb0, wb0 = torch.zeros_like(xb0), torch.zeros_like(xb0)
+            Eb0 = torch.zeros(ctx.nc, dtype=torch.float64, device=ctx.dev)
+            if ctx.dev.type == "cuda":
+                torch.cuda.synchronize(ctx.dev)
+            pic_grad_backward(h, gE, gx, gv, Eb0, xb0, vb0, wb0)
+            return xb0, vb0, Eb0, wb0
+
+    if w is None:
+        w = torch.zeros(x0.numel(), dtype=torch.float64, device=x0.device)
+    return _Steps.apply(x0, v0, E0, w)
