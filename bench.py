@@ -50,7 +50,7 @@ FP64_LANES_PER_SM_CLK = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu capture of the current kernels on this workload (2^23 markers); None where
 # the kernel changed since it was taken.
-TRAFFIC = {("mixed", 0): 111886080, ("mixed", 1): 178013696,
+TRAFFIC = {("mixed", 0): 111929344, ("mixed", 1): 178150912,
            ("fp64", 0): 155024384, ("fp64", 1): 226543872}
 
 
@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--sort-period", type=int, default=0,
                     help="cell sort of the mixed form every this many steps (0 = never)")
+    ap.add_argument("--grad", action="store_true",
+                    help="time the reverse mode on the bump-on-tail workload instead (not the "
+                         "default line), with the finite-difference agreement vs horizon")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="time a batch of this many independent runs instead (not the default "
                          "line): batched launches vs the same runs stepped one by one")
@@ -456,7 +459,8 @@ def run_ensemble(args):
         out["graphs" if graphs else "launches"] = {"value": markers * steps / t,
                                                    "ms_per_step": 1e3 * t / steps,
                                                    "max_rel_dTE": drift,
-                                                   "fallbacks": int(fb.sum())}
+                                                   "fallbacks": int(fb.sum()),
+                                                   "steps_in_stats": int(fb.shape[1])}
     # the same runs, each stepped alone (one pair of launches per run and step)
     t_single = 0.0
     for p in probs:
@@ -483,6 +487,83 @@ def run_ensemble(args):
         "runs_one_by_one": {"value": markers * steps / t_single,
                             "ms_per_step": 1e3 * t_single / steps},
         "speedup_vs_one_by_one": head["value"] / (markers * steps / t_single),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_grad(args):
+    """Reverse mode of the FP64 form on the bump-on-tail workload (2^20 weighted
+    markers, 256 cells, dt 0.1, 500 steps, checkpoints every 50): throughput of
+    the forward + reverse pass, and for several horizons the derivative of the
+    final W_E by the seed amplitude alpha (through the weights, the initial field
+    held at its alpha = 0.04 value) against central differences."""
+    import torch
+    from paper_2411_09605_gb300 import build as B, pic, workloads as W
+    B.build()
+    torch.cuda.set_device(0)
+    n, nc, k, a0 = 1 << 20, 256, 0.3, 0.04
+    nsteps, every = 500, 50
+    base = W.bump_on_tail(n=n, nc=nc, k=k, alpha=a0, seed=0)
+    sim0 = pic.Simulation(base)
+    E0 = sim0.field()
+    sim0.close()
+    s = base.species[0]
+    dw = (base.L / n) * np.cos(k * s.x)
+
+    def objective_and_grad(steps, alpha, want_grad):
+        sim = pic.Simulation(W.bump_on_tail(n=n, nc=nc, k=k, alpha=alpha, seed=0), E0=E0)
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if want_grad:
+                pic.pic_grad_forward(sim.h, steps, every)
+                fb, _ = pic.pic_read_stats(sim.h)
+            else:
+                fb, _ = sim.step(steps)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            E = sim.field()
+            h = base.L / nc
+            L = 0.5 * h * float(np.sum(E * E))
+            g = None
+            if want_grad:
+                wb = np.zeros(n)
+                pic.pic_grad_backward(sim.h, h * E, None, None, None, None, None, wb)
+                torch.cuda.synchronize()
+                g = float(np.dot(wb, dw))
+            t2 = time.perf_counter()
+        finally:
+            sim.close()
+        return L, g, t1 - t0, t2 - t1, int(np.sum(fb))
+
+    objective_and_grad(20, a0, True)                    # warm-up
+    L, g, t_fwd, t_bwd, nfb = objective_and_grad(nsteps, a0, True)
+    # central differences at two step sizes: where they disagree with each other
+    # the objective is not smooth on that scale (a marker switching between Gamma
+    # and its fallback makes W_E jump), and no derivative can match them
+    horizons = []
+    for H in (10, 20, 50, 100, 200, 500):
+        _, gh, _, _, fb_h = objective_and_grad(H, a0, True)
+        fd = {}
+        for eps in (1e-6, 1e-7):
+            lp = objective_and_grad(H, a0 + eps, False)[0]
+            lm = objective_and_grad(H, a0 - eps, False)[0]
+            fd[eps] = (lp - lm) / (2 * eps)
+        horizons.append({"steps": H, "ad": gh, "fd_eps_1e-6": fd[1e-6], "fd_eps_1e-7": fd[1e-7],
+                         "rel_diff_ad_fd": abs(fd[1e-6] - gh) / max(abs(fd[1e-6]), 1e-300),
+                         "rel_diff_fd_fd": abs(fd[1e-6] - fd[1e-7]) / max(abs(fd[1e-6]), 1e-300),
+                         "fallbacks": fb_h})
+    line = {
+        "metric": "particle-steps/s of forward + reverse (bump-on-tail, FP64 form)",
+        "value": n * nsteps / (t_fwd + t_bwd), "unit": UNIT, "n_gpus": 1, "steps": nsteps,
+        "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded bump-on-tail, weighted markers)",
+        "config": {"workload": "bump_on_tail_1d1v", "markers": n, "cells": nc, "dt": 0.1,
+                   "checkpoint_every": every, "objective": "W_E after the steps",
+                   "timing": "wall clock around forward and reverse (host synchronised; the "
+                             "reverse includes the download of the weight adjoints)"},
+        "forward_s": t_fwd, "reverse_s": t_bwd, "fallbacks": nfb,
+        "dWE_dalpha": g, "horizons": horizons,
     }
     print(json.dumps(line), flush=True)
 
@@ -530,6 +611,8 @@ def main():
         run_reference(args)
     elif args.ensemble:
         run_ensemble(args)
+    elif args.grad:
+        run_grad(args)
     else:
         run_ours(args)
 
