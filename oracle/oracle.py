@@ -72,6 +72,16 @@ class _Species2d(C.Structure):
                 ("vx", _dp), ("vy", _dp), ("vz", _dp), ("w", _dp), ("w0", C.c_double)]
 
 
+class _Em1Cfg(C.Structure):
+    _fields_ = [("n", C.c_long), ("L", C.c_double), ("order", C.c_int), ("dt", C.c_double),
+                ("c", C.c_double), ("solver", C.c_int), ("scheme", C.c_int), ("gamma_on", C.c_int)]
+
+
+class _Species1d2v(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("n", C.c_long), ("y", _dp), ("vx", _dp),
+                ("vy", _dp), ("w", _dp), ("w0", C.c_double)]
+
+
 def _declare(L):
     L.orc_shape_weights.argtypes = [C.c_int, C.c_double, C.c_long, _lp, _dp]
     L.orc_shape_weights.restype = C.c_int
@@ -93,6 +103,14 @@ def _declare(L):
     L.orc_em2d_step.argtypes = [C.POINTER(_EmCfg), C.POINTER(_Species2d), C.c_int, _dp, _dp, _lp]
     L.orc_em2d_step.restype = C.c_int
     L.orc_em2d_energy.argtypes = [C.POINTER(_EmCfg), C.POINTER(_Species2d), C.c_int, _dp, _dp,
+                                  _dp, _dp, _dp]
+    L.orc_spectral_deriv.argtypes = [C.c_long, C.c_double, _dp, _dp]
+    L.orc_em1d_field_advance.argtypes = [C.POINTER(_Em1Cfg), C.c_int, C.c_double, _dp, _dp, _dp,
+                                         _dp, _dp, _dp]
+    L.orc_em1d_step.argtypes = [C.POINTER(_Em1Cfg), C.POINTER(_Species1d2v), C.c_int, _dp, _dp,
+                                _lp]
+    L.orc_em1d_step.restype = C.c_int
+    L.orc_em1d_energy.argtypes = [C.POINTER(_Em1Cfg), C.POINTER(_Species1d2v), C.c_int, _dp, _dp,
                                   _dp, _dp, _dp]
 
 
@@ -308,3 +326,99 @@ def em2d_energy(cfg: EM2DConfig, species: Sequence[Species2D], E, B):
     lib().orc_em2d_energy(C.byref(cfg._c()), _sp2_array(species), len(species), _ptr(E), _ptr(B),
                           ke, C.byref(we), C.byref(wb))
     return list(ke), we.value, wb.value
+
+
+# ----------------------------------------------------------------------------- 1D2V spectral EM
+
+CN, PSATD = 1, 2
+
+
+@dataclass
+class EM1DConfig:
+    """1D2V geometry of the Weibel test: coordinate y, velocities (vx, vy),
+    fields E = (Ex, Ey) [2, n] and Bz [n]; solver CN (Eq. EMbasic) or PSATD
+    (Eq. EM_PSATD)."""
+    n: int
+    L: float
+    order: int = 1
+    dt: float = 0.1
+    c: float = 1.0
+    solver: int = CN
+    scheme: int = 2
+    gamma_on: bool = True
+
+    def _c(self):
+        return _Em1Cfg(self.n, self.L, self.order, self.dt, self.c, self.solver, self.scheme,
+                       int(self.gamma_on))
+
+
+@dataclass
+class Species1D2V:
+    q: float
+    m: float
+    y: np.ndarray
+    vx: np.ndarray
+    vy: np.ndarray
+    w: Optional[np.ndarray] = None
+    w0: float = 0.0
+
+    def _c(self):
+        return _Species1d2v(self.q, self.m, len(self.y), _ptr(self.y), _ptr(self.vx),
+                            _ptr(self.vy), _ptr(self.w), self.w0)
+
+
+def _sp12_array(species):
+    arr = (_Species1d2v * len(species))()
+    for i, s in enumerate(species):
+        arr[i] = s._c()
+    return arr
+
+
+def spectral_deriv(n: int, L: float, f: np.ndarray) -> np.ndarray:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(n)
+    lib().orc_spectral_deriv(n, L, _ptr(f), _ptr(out))
+    return out
+
+
+def em1d_field_advance(cfg: EM1DConfig, kind: int, tau: float, E, B, j):
+    """kind 0 explicit Euler, 1 Crank-Nicolson, 2 PSATD, over tau with j fixed.
+    Returns (E', B', Eavg)."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    j = np.ascontiguousarray(j, dtype=np.float64)
+    Eo, Bo, Ea = np.zeros_like(E), np.zeros_like(B), np.zeros_like(E)
+    lib().orc_em1d_field_advance(C.byref(cfg._c()), kind, tau, _ptr(E), _ptr(B), _ptr(j),
+                                 _ptr(Eo), _ptr(Bo), _ptr(Ea))
+    return Eo, Bo, Ea
+
+
+def em1d_step(cfg: EM1DConfig, species: Sequence[Species1D2V], E: np.ndarray, B: np.ndarray):
+    """E [2, n], B [n] float64, updated in place with the species."""
+    assert E.flags.c_contiguous and B.flags.c_contiguous
+    nfb = (C.c_long * len(species))()
+    rc = lib().orc_em1d_step(C.byref(cfg._c()), _sp12_array(species), len(species), _ptr(E),
+                             _ptr(B), nfb)
+    assert rc == 0
+    return list(nfb)
+
+
+def em1d_energy(cfg: EM1DConfig, species: Sequence[Species1D2V], E, B):
+    """Returns (KE per species, W_E, W_B)."""
+    ke = (C.c_double * len(species))()
+    we, wb = C.c_double(), C.c_double()
+    lib().orc_em1d_energy(C.byref(cfg._c()), _sp12_array(species), len(species), _ptr(E), _ptr(B),
+                          ke, C.byref(we), C.byref(wb))
+    return list(ke), we.value, wb.value
+
+
+def em1d_run(cfg: EM1DConfig, species: Sequence[Species1D2V], E, B, nsteps: int):
+    """Runs nsteps; returns (TE[nsteps+1], W_E[nsteps+1], W_B[nsteps+1], fallbacks[nsteps])."""
+    te, we, wb = np.zeros(nsteps + 1), np.zeros(nsteps + 1), np.zeros(nsteps + 1)
+    fb = np.zeros(nsteps, dtype=np.int64)
+    for k in range(nsteps + 1):
+        ke, we[k], wb[k] = em1d_energy(cfg, species, E, B)
+        te[k] = sum(ke) + we[k] + wb[k]
+        if k < nsteps:
+            fb[k] = sum(em1d_step(cfg, species, E, B))
+    return te, we, wb, fb

@@ -22,6 +22,7 @@
  * Parity status of each function is stated next to it; the pins live in
  * tests/test_oracle_*.py.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -982,4 +983,328 @@ void orc_em2d_energy(const orc_em2d_cfg *g, const orc_species2d *sp, int nsp,
   for (long a = 0; a < 3 * ncell; a++) wb += (B[a] - g->dt * cE[a]) * B[a];
   *WB = 0.5 * g->c * g->c * area * wb;
   free(cE);
+}
+
+/* ------------------------------------------------------------------------ */
+/* 1D2V electromagnetic schemes with a pseudospectral field solve:          */
+/* EMEC(LI), Eq. (EMbasic), and EMEC(PSATD), Eq. (EM_PSATD)                 */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Geometry of the paper's Weibel test (Sec. 5): one periodic coordinate y of
+ * length L with n collocated nodes y_j = j h; velocities (vx, vy); fields
+ * E = (Ex, Ey, 0) and B = (0, 0, Bz).  With only d/dy non-zero the curls are
+ *   (curl B)_x = dBz/dy,  (curl B)_y = 0,  (curl E)_z = -dEx/dy,
+ * so Maxwell's equations of Eq. (EMbasic) read
+ *   dEx/dt = c^2 dBz/dy - jx,   dEy/dt = -jy,   dBz/dt = dEx/dy.
+ * d/dy is pseudospectral (Sec. 2.2.3): mode m of the discrete Fourier
+ * transform is multiplied by i kk with kk = 2 pi m / L for the signed mode
+ * number m in (-n/2, n/2); the Nyquist mode of an even n (which has no real
+ * i kk) gets kk = 0.  The matrix of d/dy is then real and antisymmetric, which
+ * is the discrete curl identity Eq. (curlIdentity) the energy proofs use.
+ * Everything below is a direct O(n^2) discrete Fourier transform.
+ */
+
+typedef struct {
+  long n;        /* nodes */
+  double L;      /* periodic length */
+  int order;     /* 1 | 2 */
+  double dt;
+  double c;      /* speed of light */
+  int solver;    /* 1 = CN (Eq. EMbasic), 2 = PSATD (Eq. EM_PSATD) */
+  int scheme;    /* 2 = the E*, B* half step with j^{n,*}; 1 = E* = E^n, B* = B^n */
+  int gamma_on;
+} orc_em1d_cfg;
+
+typedef struct {
+  double q, m;
+  long n;
+  double *y;          /* [n] */
+  double *vx, *vy;    /* [n] */
+  const double *w;    /* [n] or NULL */
+  double w0;
+} orc_species1d2v;
+
+/* Signed wavenumber of DFT mode k (0 for the Nyquist mode of an even n). */
+static double em1d_kk(long k, long n, double L) {
+  long m = k <= n / 2 ? k : k - n;
+  if (2 * k == n) m = 0;
+  return 2.0 * M_PI * (double)m / L;
+}
+
+static void em1d_dft(long n, const double *f, double complex *F) {
+  for (long k = 0; k < n; k++) {
+    double complex s = 0.0;
+    for (long j = 0; j < n; j++) {
+      double ang = -2.0 * M_PI * (double)((j * k) % n) / (double)n;
+      s += f[j] * (cos(ang) + I * sin(ang));
+    }
+    F[k] = s;
+  }
+}
+
+/* Inverse DFT of a Hermitian spectrum; returns the real part. */
+static void em1d_idft(long n, const double complex *F, double *f) {
+  for (long j = 0; j < n; j++) {
+    double complex s = 0.0;
+    for (long k = 0; k < n; k++) {
+      double ang = 2.0 * M_PI * (double)((j * k) % n) / (double)n;
+      s += F[k] * (cos(ang) + I * sin(ang));
+    }
+    f[j] = creal(s) / (double)n;
+  }
+}
+
+/* Pseudospectral d/dy of f (pinned against the analytic derivative of band-
+ * limited fields and by antisymmetry, test_oracle_em1d.py). */
+void orc_spectral_deriv(long n, double L, const double *f, double *df) {
+  double complex *F = (double complex *)calloc((size_t)n, sizeof(double complex));
+  em1d_dft(n, f, F);
+  for (long k = 0; k < n; k++) F[k] *= I * em1d_kk(k, n, L);
+  em1d_idft(n, F, df);
+  free(F);
+}
+
+/*
+ * Field advance over tau with the current j held fixed (E = [2][n] as Ex, Ey;
+ * B = [n] as Bz; j = [2][n]).  kind:
+ *   0 explicit Euler (the E*, B* half step of Eq. EMbasic):
+ *       E' = E + tau (c^2 curl B - j),  B' = B - tau curl E;
+ *   1 Crank-Nicolson (the full step of Eq. EMbasic):
+ *       E' = E + tau (c^2 curl (B + B')/2 - j),  B' = B - tau curl (E + E')/2,
+ *     solved exactly mode by mode (a 2 x 2 linear system for Ex, Bz);
+ *   2 PSATD (Eq. PSATDformula with Delta t -> tau): the exact solution of
+ *     the ODE system Eq. (PSATDconstruction).  Eavg (may be NULL) receives
+ *     the time average of E over [0, tau] (the closed form given after Eq.
+ *     EM_PSATD).
+ * For kind 0 and 1 Eavg, if given, receives (E + E')/2.
+ * Pinned: vacuum standing waves against cos(kc t) (PSATD) and the CN phase
+ * 2 atan(kc tau/2) per step; a fine Runge-Kutta integration of the ODE with
+ * its quadrature of E (PSATD, Eavg); the residual of the CN relations.
+ */
+void orc_em1d_field_advance(const orc_em1d_cfg *g, int kind, double tau,
+                            const double *E, const double *B, const double *j,
+                            double *Eout, double *Bout, double *Eavg) {
+  long n = g->n;
+  double c = g->c, c2 = c * c;
+  double complex *Fx = (double complex *)calloc((size_t)n, sizeof(double complex));
+  double complex *Fy = (double complex *)calloc((size_t)n, sizeof(double complex));
+  double complex *Fb = (double complex *)calloc((size_t)n, sizeof(double complex));
+  double complex *Jx = (double complex *)calloc((size_t)n, sizeof(double complex));
+  double complex *Jy = (double complex *)calloc((size_t)n, sizeof(double complex));
+  double complex *Ox = (double complex *)calloc((size_t)n, sizeof(double complex));
+  double complex *Oy = (double complex *)calloc((size_t)n, sizeof(double complex));
+  double complex *Ob = (double complex *)calloc((size_t)n, sizeof(double complex));
+  double complex *Ax = (double complex *)calloc((size_t)n, sizeof(double complex));
+  double complex *Ay = (double complex *)calloc((size_t)n, sizeof(double complex));
+  em1d_dft(n, E, Fx);
+  em1d_dft(n, E + n, Fy);
+  em1d_dft(n, B, Fb);
+  em1d_dft(n, j, Jx);
+  em1d_dft(n, j + n, Jy);
+  for (long k = 0; k < n; k++) {
+    double kk = em1d_kk(k, n, g->L);
+    if (kind == 0) {
+      Ox[k] = Fx[k] + tau * (c2 * I * kk * Fb[k] - Jx[k]);
+      Ob[k] = Fb[k] + tau * I * kk * Fx[k];
+    } else if (kind == 1) {
+      double complex a = I * kk * tau / 2.0;
+      double complex r1 = Fx[k] + c2 * a * Fb[k] - tau * Jx[k];
+      double complex r2 = Fb[k] + a * Fx[k];
+      double complex det = 1.0 - c2 * a * a;
+      Ox[k] = (r1 + c2 * a * r2) / det;
+      Ob[k] = (r2 + a * r1) / det;
+    } else {
+      double kabs = fabs(kk), s = kk > 0.0 ? 1.0 : -1.0;
+      if (kabs == 0.0) {
+        Ox[k] = Fx[k] - tau * Jx[k];
+        Ob[k] = Fb[k];
+        Ax[k] = Fx[k] - 0.5 * tau * Jx[k];
+      } else {
+        double C = cos(kabs * c * tau), S = sin(kabs * c * tau);
+        Ox[k] = C * Fx[k] + I * s * S * c * Fb[k] - S / (kabs * c) * Jx[k];
+        Ob[k] = C * Fb[k] + I * s * (S / c) * Fx[k] - I * s * (1.0 - C) / (kabs * c2) * Jx[k];
+        Ax[k] = S / (kabs * c * tau) * Fx[k] + I * s * (1.0 - C) / (kabs * tau) * Fb[k] -
+                (1.0 - C) / (kabs * kabs * c2 * tau) * Jx[k];
+      }
+      Ay[k] = Fy[k] - 0.5 * tau * Jy[k];
+    }
+    /* the longitudinal component has no curl term in every kind */
+    Oy[k] = Fy[k] - tau * Jy[k];
+  }
+  em1d_idft(n, Ox, Eout);
+  em1d_idft(n, Oy, Eout + n);
+  em1d_idft(n, Ob, Bout);
+  if (Eavg) {
+    if (kind == 2) {
+      em1d_idft(n, Ax, Eavg);
+      em1d_idft(n, Ay, Eavg + n);
+    } else {
+      for (long a = 0; a < 2 * n; a++) Eavg[a] = 0.5 * (E[a] + Eout[a]);
+    }
+  }
+  free(Fx); free(Fy); free(Fb); free(Jx); free(Jy);
+  free(Ox); free(Oy); free(Ob); free(Ax); free(Ay);
+}
+
+static double wt1d2v(const orc_species1d2v *s, long p) {
+  return s->w ? s->w[p] : s->w0;
+}
+
+/* jx, jy += (1/h) q w (ux, uy) S(y_h - y_p) at the positions py. */
+static void deposit_1d2v(const orc_em1d_cfg *g, const orc_species1d2v *s,
+                         const double *py, const double *ux, const double *uy,
+                         double *J) {
+  double h = g->L / (double)g->n;
+  for (long p = 0; p < s->n; p++) {
+    long idx[3];
+    double wt[3];
+    int k = orc_shape_weights(g->order, py[p] / h, g->n, idx, wt);
+    double qw = s->q * wt1d2v(s, p) / h;
+    for (int a = 0; a < k; a++) {
+      J[idx[a]] += qw * ux[p] * wt[a];
+      J[g->n + idx[a]] += qw * uy[p] * wt[a];
+    }
+  }
+}
+
+static double gather_at(const orc_em1d_cfg *g, const double *F, double y) {
+  double h = g->L / (double)g->n;
+  long idx[3];
+  double wt[3];
+  int k = orc_shape_weights(g->order, y / h, g->n, idx, wt);
+  double s = 0.0;
+  for (int a = 0; a < k; a++) s += F[idx[a]] * wt[a];
+  return s;
+}
+
+/*
+ * One step of Eq. (EMbasic) (solver 1) or Eq. (EM_PSATD) (solver 2) for the
+ * 1D2V geometry above, E = [2][n] and B = [n] updated in place:
+ *   y*          = y^n + dt/2 vy^n
+ *   j^{n,*}     = (1/h) sum q w v^n S(y_h - y*)                 (scheme 2)
+ *   (E*, B*)    = explicit half step (CN) or PSATD over dt/2 with j^{n,*}
+ *                 (scheme 1: E* = E^n, B* = B^n)
+ *   v*          = v^n + dt/2 (q/m)(E**_p + v* x B**_p), E**, B** gathered at y*
+ *               = (u + u x t)/(1 + t^2) with u = v^n + (q/m)(dt/2) E**_p and
+ *                 t = (q/m)(dt/2) B**_p (u . t = 0 in this geometry)
+ *   y^{n+1}     = y^n + dt vy*,  y^{n+1/2} = y^n + dt/2 vy*
+ *   j^{*,n+1/2} = (1/h) sum q w v* S(y_h - y^{n+1/2})
+ *   (E^{n+1}, B^{n+1}) = CN or PSATD over dt with j^{*,n+1/2}
+ *   Ebar        = (E^n + E^{n+1})/2 (CN) or the time average <E> (PSATD)
+ *   B^{n+1/2}   = (B^n + B^{n+1})/2
+ *   v^dag       = v^n + dt (q/m)(Ebar_p + v* x B^{n+1/2}_p) at y^{n+1/2}
+ *   v^{n+1}     = Gamma v^dag (Eq. opt_solution; fallback Gamma := 1, counted)
+ */
+int orc_em1d_step(const orc_em1d_cfg *g, orc_species1d2v *sp, int nsp,
+                  double *E, double *B, long *nfallback) {
+  if (nsp <= 0 || g->n <= 0 || (g->solver != 1 && g->solver != 2)) return -1;
+  long n = g->n;
+  double dt = g->dt;
+  int full = g->solver == 1 ? 1 : 2;
+  double *J = (double *)calloc((size_t)(2 * n), sizeof(double));
+  double *Es = (double *)calloc((size_t)(2 * n), sizeof(double));
+  double *Bs = (double *)calloc((size_t)n, sizeof(double));
+  double *En = (double *)calloc((size_t)(2 * n), sizeof(double));
+  double *Bn = (double *)calloc((size_t)n, sizeof(double));
+  double *Eb = (double *)calloc((size_t)(2 * n), sizeof(double));
+  double *Bh = (double *)calloc((size_t)n, sizeof(double));
+
+  /* j^{n,*} and the half step */
+  if (g->scheme == 2) {
+    for (int s = 0; s < nsp; s++) {
+      orc_species1d2v *S = &sp[s];
+      double *ys = (double *)calloc((size_t)S->n + 1, sizeof(double));
+      for (long p = 0; p < S->n; p++) ys[p] = wrap(S->y[p] + 0.5 * dt * S->vy[p], g->L);
+      deposit_1d2v(g, S, ys, S->vx, S->vy, J);
+      free(ys);
+    }
+    orc_em1d_field_advance(g, full == 1 ? 0 : 2, 0.5 * dt, E, B, J, Es, Bs, NULL);
+  } else {
+    memcpy(Es, E, sizeof(double) * 2 * n);
+    memcpy(Bs, B, sizeof(double) * n);
+  }
+
+  /* v*, y^{n+1/2}; deposit j^{*,n+1/2} */
+  double **vsx = (double **)calloc((size_t)nsp, sizeof(double *));
+  double **vsy = (double **)calloc((size_t)nsp, sizeof(double *));
+  double **yh = (double **)calloc((size_t)nsp, sizeof(double *));
+  for (long a = 0; a < 2 * n; a++) J[a] = 0.0;
+  for (int s = 0; s < nsp; s++) {
+    orc_species1d2v *S = &sp[s];
+    double qm = S->q / S->m;
+    vsx[s] = (double *)calloc((size_t)S->n + 1, sizeof(double));
+    vsy[s] = (double *)calloc((size_t)S->n + 1, sizeof(double));
+    yh[s] = (double *)calloc((size_t)S->n + 1, sizeof(double));
+    for (long p = 0; p < S->n; p++) {
+      double ys = wrap(S->y[p] + 0.5 * dt * S->vy[p], g->L);
+      double ux = S->vx[p] + qm * 0.5 * dt * gather_at(g, Es, ys);
+      double uy = S->vy[p] + qm * 0.5 * dt * gather_at(g, Es + n, ys);
+      double t = qm * 0.5 * dt * gather_at(g, Bs, ys);
+      vsx[s][p] = (ux + uy * t) / (1.0 + t * t);
+      vsy[s][p] = (uy - ux * t) / (1.0 + t * t);
+      yh[s][p] = wrap(S->y[p] + 0.5 * dt * vsy[s][p], g->L);
+    }
+    deposit_1d2v(g, S, yh[s], vsx[s], vsy[s], J);
+  }
+
+  /* the full field step */
+  orc_em1d_field_advance(g, full, dt, E, B, J, En, Bn, Eb);
+  for (long a = 0; a < n; a++) Bh[a] = 0.5 * (B[a] + Bn[a]);
+
+  /* v^dag, Gamma, y^{n+1}, v^{n+1} */
+  for (int s = 0; s < nsp; s++) {
+    orc_species1d2v *S = &sp[s];
+    double qm = S->q / S->m;
+    long count = 0;
+    for (long p = 0; p < S->n; p++) {
+      double y = yh[s][p];
+      double ex = gather_at(g, Eb, y), ey = gather_at(g, Eb + n, y);
+      double bz = gather_at(g, Bh, y);
+      double vx = S->vx[p], vy = S->vy[p], wx = vsx[s][p], wy = vsy[s][p];
+      double dx = vx + dt * qm * (ex + wy * bz);
+      double dy = vy + dt * qm * (ey - wx * bz);
+      double R = vx * vx + vy * vy + 2.0 * (wx * (dx - vx) + wy * (dy - vy));
+      double vd2 = dx * dx + dy * dy;
+      double gamma = 1.0;
+      if (g->gamma_on) {
+        if (R < 0.0 || vd2 == 0.0)
+          count++;
+        else
+          gamma = sqrt(R) / sqrt(vd2);
+      }
+      S->vx[p] = gamma == 1.0 ? dx : dx * gamma;
+      S->vy[p] = gamma == 1.0 ? dy : dy * gamma;
+      S->y[p] = wrap(S->y[p] + dt * wy, g->L);
+    }
+    if (nfallback) nfallback[s] = count;
+    free(vsx[s]);
+    free(vsy[s]);
+    free(yh[s]);
+  }
+  memcpy(E, En, sizeof(double) * 2 * n);
+  memcpy(B, Bn, sizeof(double) * n);
+  free(vsx); free(vsy); free(yh);
+  free(J); free(Es); free(Bs); free(En); free(Bn); free(Eb); free(Bh);
+  return 0;
+}
+
+/* KE per species, W_E = (h/2) sum (Ex^2 + Ey^2), W_B = (c^2 h/2) sum Bz^2 (the
+ * energies of Eq. EM_econs and Eq. PSATDecons). */
+void orc_em1d_energy(const orc_em1d_cfg *g, const orc_species1d2v *sp, int nsp,
+                     const double *E, const double *B, double *KE, double *WE,
+                     double *WB) {
+  long n = g->n;
+  double h = g->L / (double)n;
+  for (int s = 0; s < nsp; s++) {
+    double acc = 0.0;
+    for (long p = 0; p < sp[s].n; p++)
+      acc += wt1d2v(&sp[s], p) * (sp[s].vx[p] * sp[s].vx[p] + sp[s].vy[p] * sp[s].vy[p]);
+    KE[s] = 0.5 * sp[s].m * acc;
+  }
+  double we = 0.0, wb = 0.0;
+  for (long a = 0; a < 2 * n; a++) we += E[a] * E[a];
+  for (long a = 0; a < n; a++) wb += B[a] * B[a];
+  *WE = 0.5 * h * we;
+  *WB = 0.5 * g->c * g->c * h * wb;
 }

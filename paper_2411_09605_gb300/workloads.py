@@ -248,3 +248,68 @@ def weibel(nx: int = 128, ny: int = 128, ppc: int = 64, L: float = 12.8, vth_par
     vz = rng.standard_normal(n) * vperp
     return Problem2D("weibel", nx, ny, L, L, order, dt, c, steps,
                      [Markers2D(-1.0, 1.0, x, y, vx, vy, vz, None, L * L / n)])
+
+
+@dataclass
+class Markers1D2V:
+    q: float
+    m: float
+    y: np.ndarray          # float64 [n], in [0, L)
+    vx: np.ndarray
+    vy: np.ndarray
+    w: Optional[np.ndarray] = None
+    w0: float = 0.0
+
+
+@dataclass
+class Problem1D2V:
+    """1D2V electromagnetic problem: coordinate y, velocities (vx, vy), fields
+    E = (Ex, Ey) [2, n] and Bz [n] on n collocated nodes."""
+    name: str
+    L: float
+    n: int
+    order: int
+    dt: float
+    c: float
+    steps: int
+    E0: np.ndarray
+    B0: np.ndarray
+    species: List[Markers1D2V] = field(default_factory=list)
+
+    @property
+    def n_markers(self) -> int:
+        return sum(len(s.y) for s in self.species)
+
+
+def weibel_1d2v(n: int = 32, ppc: int = 3200, k0: float = 0.2, beta: float = 0.01,
+                delta: float = 0.5, v01: float = 0.3, v02: float = 0.3, b: float = 0.001,
+                dt: float = 0.1, c: float = 1.0, steps: int = 1000, order: int = 1,
+                mirrored: bool = False, seed: int = 0) -> Problem1D2V:
+    """The Weibel test of Sec. 5 (Exp. 3): L = 2 pi / k0, quiet start (markers
+    evenly spaced in y), f ~ exp(-vy^2/beta) [delta exp(-(vx - v01)^2/beta)
+    + (1 - delta) exp(-(vx + v02)^2/beta)], E = 0, Bz = b sin(k0 y).
+    mirrored: markers come in fours (vx, vy), (-vx, -vy), (vx, -vy), (-vx, vy)
+    at the same y (only for delta = 1/2 and v01 = v02). Free streaming then
+    deposits no jx at any time, so only the seed b drives (Ex, Bz)."""
+    rng = np.random.default_rng(seed)
+    L = 2.0 * np.pi / k0
+    N = n * ppc
+    y = (np.arange(N) + 0.5) * (L / N)
+    sd = np.sqrt(beta / 2.0)
+    if mirrored:
+        assert N % 4 == 0 and delta == 0.5 and v01 == v02
+        q = N // 4
+        ax = np.where(rng.random(q) < delta, v01, -v02) + sd * rng.standard_normal(q)
+        ay = sd * rng.standard_normal(q)
+        vx = np.stack([ax, -ax, ax, -ax], axis=1).ravel()
+        vy = np.stack([ay, -ay, -ay, ay], axis=1).ravel()
+        y = np.repeat((np.arange(q) + 0.5) * (L / q), 4)
+    else:
+        beam = np.where(rng.random(N) < delta, v01, -v02)
+        vx = beam + sd * rng.standard_normal(N)
+        vy = sd * rng.standard_normal(N)
+    nodes = np.arange(n) * (L / n)
+    E0 = np.zeros((2, n))
+    B0 = b * np.sin(k0 * nodes)
+    return Problem1D2V("weibel_1d2v", L, n, order, dt, c, steps, E0, B0,
+                       [Markers1D2V(-1.0, 1.0, y, vx, vy, None, L / N)])
