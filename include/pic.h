@@ -33,7 +33,12 @@
  *     Yee lattice n[0] x n[1] (solver PIC_SOLVER_YEE_LEAPFROG, dim_x = 2,
  *     dim_v = 3) with components Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j),
  *     Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2); grid arrays are
- *     component-major [3][n[1]][n[0]].
+ *     component-major [3][n[1]][n[0]]; or 1D periodic with a pseudospectral
+ *     field solve (solvers PIC_SOLVER_CN_SPECTRAL / PIC_SOLVER_PSATD,
+ *     dim_x = 1, dim_v = 2): the coordinate is y, velocities (vx, vy), fields
+ *     E = [2][n] (Ex, Ey) and B = [n] (Bz) on the nodes y_j = j h, n a power
+ *     of two in [4, 1024].  d/dy multiplies Fourier mode m by 2 pi i m / L,
+ *     and by 0 for the Nyquist mode (Sec. 2.2.3).
  *   - Particle arrays are SoA: x is [dim_x][n], v is [dim_v][n], w is [n].
  *   - Ownership: the library copies everything it is given at pic_init /
  *     pic_set_* and owns all device memory it allocates until pic_free.  Output
@@ -65,7 +70,17 @@ enum {
   PIC_ERR_UNSUPPORTED = -7 /* a valid combination this build does not run   */
 };
 
-typedef enum { PIC_SOLVER_AMPERE_ES = 0, PIC_SOLVER_YEE_LEAPFROG = 1 } pic_solver;
+/* PIC_SOLVER_CN_SPECTRAL: EMEC(LI), the linearly implicit (Crank-Nicolson)
+ * Maxwell step of Eq. (EMbasic); PIC_SOLVER_PSATD: EMEC(PSATD), Eq. (EM_PSATD),
+ * the analytic Fourier-space step of Eq. (PSATDformula) with the time-averaged
+ * E in v^dag.  Both run the 1D2V geometry of the paper's Weibel test (see
+ * Conventions) with a pseudospectral d/dy. */
+typedef enum {
+  PIC_SOLVER_AMPERE_ES = 0,
+  PIC_SOLVER_YEE_LEAPFROG = 1,
+  PIC_SOLVER_CN_SPECTRAL = 2,
+  PIC_SOLVER_PSATD = 3
+} pic_solver;
 /* ESEC1: Eq. (naivetranslation) with the correction of Eq. (PICmodification);
  * ESEC2: Eq. (good_translation), one extra deposit per step, Gamma closer to 1. */
 typedef enum { PIC_SCHEME_ESEC1 = 1, PIC_SCHEME_ESEC2 = 2 } pic_scheme;
@@ -118,10 +133,11 @@ typedef struct pic_handle pic_handle;
 
 /*
  * Creates a simulation.  species: nspecies entries (1..8).  E0: initial field,
- * [nodes] (ES) or [3][ny][nx] (Yee), or NULL: ES solves Gauss's law in the
- * Poisson form (Eq. poisson, dE/dx = rho - <rho>) spectrally from the
- * deposited charge, Yee starts from E = 0.  B0 (Yee only): B^{-1/2}
- * [3][ny][nx] or NULL for zero.  Positions outside [0, L) -> PIC_ERR_BOUNDS;
+ * [nodes] (ES), [3][ny][nx] (Yee) or [2][n] (spectral), or NULL: ES solves
+ * Gauss's law in the Poisson form (Eq. poisson, dE/dx = rho - <rho>)
+ * spectrally from the deposited charge, the electromagnetic solvers start
+ * from E = 0.  B0: B^{-1/2} [3][ny][nx] (Yee) or Bz^0 [n] (spectral), or NULL
+ * for zero; not allowed for the ES solver.  Positions outside [0, L) -> PIC_ERR_BOUNDS;
  * non-finite input -> PIC_ERR_NONFINITE.  On success *out owns the state.
  */
 int pic_init(const pic_config *cfg, const pic_species *species, int nspecies,
@@ -169,7 +185,8 @@ int pic_profile(pic_handle *h, int kind, int64_t *launches, double *total_ms);
 /*
  * Energies of the current state (Sec. 5.1; W_B of Sec. 4.1):
  * KE_per_species [nspecies], W_E = (1/2)|h| sum |E|^2,
- * W_B = (c^2/2)|h| sum B^{n+1/2} . B^{n-1/2} (0 for the ES solver), TE = sum.
+ * W_B = (c^2/2)|h| sum B^{n+1/2} . B^{n-1/2} (Yee), (c^2/2) h sum Bz^2
+ * (spectral solvers, Eq. EM_econs), 0 for the ES solver; TE = sum.
  * Any output may be NULL.  Always host pointers.
  */
 int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, double *TE);

@@ -1,0 +1,489 @@
+// 1D2V electromagnetic step with a pseudospectral field solve, FP64 form:
+// EMEC(LI), the Crank-Nicolson scheme of Sec. 4.1 (Eq. EMbasic), and
+// EMEC(PSATD) of Sec. 4.3 (Eq. EM_PSATD), in the geometry of the paper's
+// Weibel test: one periodic coordinate y, velocities (vx, vy), E = (Ex, Ey),
+// B = Bz, all on n collocated nodes.  With only d/dy non-zero,
+//   dEx/dt = c^2 dBz/dy - jx,   dEy/dt = -jy,   dBz/dt = dEx/dy,
+// so Ey's update is pointwise and only the pair (Ex, Bz) needs a transform.
+// d/dy multiplies Fourier mode m by i kk, kk = 2 pi m / L (m signed); the
+// Nyquist mode gets kk = 0, which keeps the discrete curl antisymmetric
+// (Eq. curlIdentity), so both energy proofs hold exactly.
+//
+// Two launches per step, like the other particle paths:
+//   pass C  every block: E*, B* tables in shared memory; per marker y*,
+//           E**, B**, the closed-form v* of v* = v^n + dt/2 (q/m)(E** + v* x B**),
+//           y^{n+1/2}, deposit of j^{*,n+1/2} (shared tile, then global atomics).
+//           The block that finishes last does the full field step:
+//           (E^{n+1}, B^{n+1}) by Crank-Nicolson or PSATD over dt with
+//           j^{*,n+1/2}, the E that v^dag uses (E^{n+1/2}, or PSATD's time
+//           average <E>) and B^{n+1/2} = (B^n + B^{n+1})/2.
+//   pass E  every block: the same v*, y^{n+1/2} recomputed bit for bit, the
+//           gather of that E and B^{n+1/2}, v^dag, Gamma (Eq. opt_solution;
+//           fallback counted), y^{n+1}, v^{n+1}, the kinetic-energy partial and
+//           (ESEC2 form) the deposit of j^{n+1,*} at y^{n+1} + dt/2 vy^{n+1}.
+//           The block that finishes last writes TE of the new state and the
+//           next step's half step: (E*, B*) from E^{n+1}, B^{n+1}, j^{n+1,*}
+//           by the explicit half step (Crank-Nicolson scheme) or PSATD over
+//           dt/2.
+// "Last block" is a counter taken with one atomic per block after a memory
+// fence; nothing waits.  The field solve is an in-block radix-2 FFT over n
+// (a power of two, 4 <= n <= 1024) in shared memory.
+#include <cuda_runtime.h>
+
+#include "es1d_fp64_common.cuh"
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+constexpr int kEm1Threads = 256;
+
+__device__ __forceinline__ int species_of1(const Em1dConst &c, int64_t p) {
+  int s = 0;
+  while (s < c.nsp - 1 && p >= c.sp_end[s]) s++;
+  return s;
+}
+
+// y*, E**, B**, v*, y^{n+1/2} with explicitly rounded operations: pass C
+// deposits at exactly the y^{n+1/2} and v* that pass E gathers at.
+template <int ORDER>
+__device__ __forceinline__ void em1d_half_push(const Em1dConst &c, const double *Esx,
+                                               const double *Esy, const double *Bs, double y,
+                                               double vx, double vy, double qm, unsigned *err,
+                                               double &vsx, double &vsy, double &yh) {
+  const double hdt = 0.5 * c.dt;
+  const double ys = wrap_periodic(__fma_rn(hdt, vy, y), c.L, err);
+  const Shape64<ORDER> S(__dmul_rn(ys, c.inv_h), c.n);
+  const double ex = S.gather(Esx), ey = S.gather(Esy), bz = S.gather(Bs);
+  const double a = __dmul_rn(hdt, qm);
+  const double ux = __fma_rn(a, ex, vx), uy = __fma_rn(a, ey, vy);
+  const double t = __dmul_rn(a, bz);
+  const double inv = __ddiv_rn(1.0, __fma_rn(t, t, 1.0));
+  vsx = __dmul_rn(__fma_rn(uy, t, ux), inv);
+  vsy = __dmul_rn(__fma_rn(-ux, t, uy), inv);
+  yh = wrap_periodic(__fma_rn(hdt, vsy, y), c.L, err);
+}
+
+// ---------------------------------------------------------------- field solve
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ double2 cscale(double s, double2 a) { return {s * a.x, s * a.y}; }
+__device__ __forceinline__ double2 ctimes_i(double2 a) { return {-a.y, a.x}; }   // i a
+__device__ __forceinline__ double2 cconj(double2 a) { return {a.x, -a.y}; }
+
+// In-place radix-2 transform of n = 2^log2n values in shared memory:
+// a_k <- sum_j a_j exp(sign 2 pi i j k / n) (unnormalised).  Every thread of
+// the block takes part.
+__device__ void block_fft(double2 *a, int n, int log2n, double sign) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int r = (int)(__brev((unsigned)i) >> (32 - log2n));
+    if (r > i) {
+      const double2 t = a[i];
+      a[i] = a[r];
+      a[r] = t;
+    }
+  }
+  __syncthreads();
+  for (int len = 2; len <= n; len <<= 1) {
+    const int half = len >> 1;
+    for (int b = threadIdx.x; b < (n >> 1); b += blockDim.x) {
+      const int grp = b / half, j = b - grp * half;
+      const int i0 = grp * len + j, i1 = i0 + half;
+      double s, co;
+      sincospi(sign * 2.0 * (double)j / (double)len, &s, &co);
+      const double2 u = a[i0], v = a[i1];
+      const double2 t = {v.x * co - v.y * s, v.x * s + v.y * co};
+      a[i0] = cadd(u, t);
+      a[i1] = csub(u, t);
+    }
+    __syncthreads();
+  }
+}
+
+// Signed wavenumber of mode k (0 for the Nyquist mode).
+__device__ __forceinline__ double mode_kk(const Em1dConst &c, int k) {
+  if (2 * k == c.n) return 0.0;
+  const int m = (k <= c.n / 2) ? k : k - c.n;
+  return 2.0 * 3.141592653589793 * (double)m / c.L;
+}
+
+// Field advance over tau with j held fixed; kind 0 explicit Euler (the half
+// step of Eq. EMbasic), 1 Crank-Nicolson (its full step), 2 PSATD (Eq.
+// PSATDformula with Delta t -> tau).  Reads E [2][n], B [n], J [2][n] from
+// global memory (written by other blocks of this kernel: read through L2),
+// writes Eo, Bo and, when non-null, Ea (the E of v^dag: PSATD's <E> over
+// [0, tau], else (E + Eo)/2) and Bh = (B + Bo)/2.  Z1, Z2: 2n double2 of
+// shared memory.
+__device__ void field_advance(const Em1dConst &c, int kind, double tau, const double *E,
+                              const double *B, const double *J, double *Eo, double *Bo,
+                              double *Ea, double *Bh, double2 *Z1, double2 *Z2) {
+  const int n = c.n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    Z1[i] = make_double2(__ldcg(E + i), __ldcg(B + i));
+    Z2[i] = make_double2(__ldcg(J + i), 0.0);
+  }
+  __syncthreads();
+  block_fft(Z1, n, c.log2n, -1.0);
+  block_fft(Z2, n, c.log2n, -1.0);
+  // modes k and n - k by one thread: Z1 holds Ex + i Bz, so
+  // Ex_k = (Z_k + conj Z_{n-k}) / 2 and Bz_k = (Z_k - conj Z_{n-k}) / (2i)
+  const double c2 = c.c2;
+  for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
+    const int k2 = (n - k) & (n - 1);
+    const double2 zk = Z1[k], zm = Z1[k2];
+    const double2 A = cscale(0.5, cadd(zk, cconj(zm)));
+    const double2 Bm = cscale(0.5, {zk.y + zm.y, zm.x - zk.x});   // (zk - conj zm) / (2i)
+    const double2 Jk = Z2[k];
+    const double kk = mode_kk(c, k);
+    double2 Ox, Ob, Ax = {0.0, 0.0};
+    if (kind == 0) {
+      Ox = cadd(A, cscale(tau, csub(cscale(c2 * kk, ctimes_i(Bm)), Jk)));
+      Ob = cadd(Bm, cscale(tau * kk, ctimes_i(A)));
+    } else if (kind == 1) {
+      // a = i alpha, alpha = kk tau / 2: r1 = A + c^2 a B - tau J, r2 = B + a A,
+      // Ex' = (r1 + c^2 a r2) / det, Bz' = (r2 + a r1) / det, det = 1 + c^2 alpha^2
+      const double al = 0.5 * kk * tau;
+      const double2 r1 = csub(cadd(A, cscale(c2 * al, ctimes_i(Bm))), cscale(tau, Jk));
+      const double2 r2 = cadd(Bm, cscale(al, ctimes_i(A)));
+      const double inv_det = 1.0 / (1.0 + c2 * al * al);
+      Ox = cscale(inv_det, cadd(r1, cscale(c2 * al, ctimes_i(r2))));
+      Ob = cscale(inv_det, cadd(r2, cscale(al, ctimes_i(r1))));
+    } else {
+      if (kk == 0.0) {
+        Ox = csub(A, cscale(tau, Jk));
+        Ob = Bm;
+        Ax = csub(A, cscale(0.5 * tau, Jk));
+      } else {
+        const double ka = fabs(kk), sg = kk > 0.0 ? 1.0 : -1.0, cc = c.c;
+        const double x = ka * cc * tau;
+        double S, C, sh, chh;
+        sincos(x, &S, &C);
+        sincos(0.5 * x, &sh, &chh);
+        const double omc = 2.0 * sh * sh;  // 1 - cos x without cancellation
+        Ox = cadd(cadd(cscale(C, A), cscale(sg * S * cc, ctimes_i(Bm))), cscale(-S / (ka * cc), Jk));
+        Ob = cadd(cadd(cscale(C, Bm), cscale(sg * S / cc, ctimes_i(A))),
+                  cscale(-sg * omc / (ka * c2), ctimes_i(Jk)));
+        Ax = cadd(cadd(cscale(S / x, A), cscale(sg * omc / (ka * tau), ctimes_i(Bm))),
+                  cscale(-omc / (ka * ka * c2 * tau), Jk));
+      }
+    }
+    // repack Ex' + i Bz' (and <Ex>) for the inverse transform; mode n - k holds
+    // the conjugates
+    Z1[k] = cadd(Ox, ctimes_i(Ob));
+    Z2[k] = Ax;
+    if (k2 != k) {
+      Z1[k2] = cadd(cconj(Ox), ctimes_i(cconj(Ob)));
+      Z2[k2] = cconj(Ax);
+    }
+  }
+  __syncthreads();
+  block_fft(Z1, n, c.log2n, 1.0);
+  if (kind == 2 && Ea) block_fft(Z2, n, c.log2n, 1.0);
+  const double inv_n = 1.0 / (double)n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double ex = __ldcg(E + i), ey = __ldcg(E + n + i), bz = __ldcg(B + i);
+    const double jy = __ldcg(J + n + i);
+    const double exn = Z1[i].x * inv_n, bzn = Z1[i].y * inv_n;
+    Eo[i] = exn;
+    Eo[n + i] = ey - tau * jy;
+    Bo[i] = bzn;
+    if (Ea) {
+      Ea[i] = kind == 2 ? Z2[i].x * inv_n : 0.5 * (ex + exn);
+      Ea[n + i] = ey - 0.5 * tau * jy;
+    }
+    if (Bh) Bh[i] = 0.5 * (bz + bzn);
+  }
+  __syncthreads();
+}
+
+// True in the one block that arrives last at this counter; every thread first
+// fences its own global writes, so the last block sees all blocks' results.
+// That block resets the counter for the next launch.
+__device__ bool arrive_last(unsigned *counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(counter, 1u);
+    last = prev == gridDim.x - 1;
+    if (last) *counter = 0u;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+__device__ double block_sum_d(double s, double *red) {
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[k];
+  return t;  // valid in thread 0
+}
+
+__device__ __forceinline__ double marker_qw(const Em1dConst &c, const Em1dBufs &b, int s,
+                                            int64_t p) {
+  return b.w ? c.q_h[s] * b.w[p] : c.qw_h[s];
+}
+
+// ---------------------------------------------------------------- passes
+
+template <int ORDER>
+__global__ void __launch_bounds__(kEm1Threads) em1d_pass_c_kernel(Em1dConst c, Em1dBufs b) {
+  extern __shared__ double sm[];
+  const int n = c.n;
+  double *Esx = sm, *Esy = sm + n, *Bs = sm + 2 * n, *Jt = sm + 3 * n;  // Jt [2][n]
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    Esx[i] = b.Es[i];
+    Esy[i] = b.Es[n + i];
+    Bs[i] = b.Bs[i];
+    Jt[i] = 0.0;
+    Jt[n + i] = 0.0;
+  }
+  __syncthreads();
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n_total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int s = species_of1(c, p);
+    double vsx, vsy, yh;
+    em1d_half_push<ORDER>(c, Esx, Esy, Bs, b.y[p], b.vx[p], b.vy[p], c.qm[s], b.err, vsx, vsy, yh);
+    const Shape64<ORDER> S(__dmul_rn(yh, c.inv_h), n);
+    const double qw = marker_qw(c, b, s, p);
+    S.deposit(Jt, qw * vsx);
+    S.deposit(Jt + n, qw * vsy);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x)
+    if (Jt[i] != 0.0) atomicAdd(&b.J2[i], Jt[i]);
+  if (arrive_last(b.done)) {
+    double2 *Z = (double2 *)sm;
+    field_advance(c, c.solver == 1 ? 1 : 2, c.dt, b.E, b.B, b.J2, b.En, b.Bn, b.Ea, b.Bh, Z, Z + n);
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) b.J1[i] = 0.0;
+  }
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kEm1Threads) em1d_pass_e_kernel(Em1dConst c, Em1dBufs b,
+                                                                   int slot) {
+  extern __shared__ double sm[];
+  __shared__ double red[33];
+  const int n = c.n;
+  double *Esx = sm, *Esy = sm + n, *Bs = sm + 2 * n;
+  double *Eax = sm + 3 * n, *Eay = sm + 4 * n, *Bh = sm + 5 * n, *Jt = sm + 6 * n;  // Jt [2][n]
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    Esx[i] = b.Es[i];
+    Esy[i] = b.Es[n + i];
+    Bs[i] = b.Bs[i];
+    Eax[i] = b.Ea[i];
+    Eay[i] = b.Ea[n + i];
+    Bh[i] = b.Bh[i];
+    Jt[i] = 0.0;
+    Jt[n + i] = 0.0;
+  }
+  __syncthreads();
+  const double dt = c.dt, hdt = 0.5 * c.dt;
+  double ke = 0.0;
+  unsigned nfb = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n_total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int s = species_of1(c, p);
+    const double qm = c.qm[s];
+    const double y = b.y[p], vx = b.vx[p], vy = b.vy[p];
+    double vsx, vsy, yh;
+    em1d_half_push<ORDER>(c, Esx, Esy, Bs, y, vx, vy, qm, b.err, vsx, vsy, yh);
+    const Shape64<ORDER> S(__dmul_rn(yh, c.inv_h), n);
+    const double ex = S.gather(Eax), ey = S.gather(Eay), bz = S.gather(Bh);
+    const double a = dt * qm;
+    const double dx = fma(a, fma(vsy, bz, ex), vx);
+    const double dy = fma(a, fma(-vsx, bz, ey), vy);
+    // R = |v^n|^2 + 2 v* . (v^dag - v^n), Gamma = sqrt(R) / |v^dag| (Eq. opt_solution)
+    const double R = fma(vx, vx, vy * vy) + 2.0 * fma(vsx, dx - vx, vsy * (dy - vy));
+    const double vd2 = fma(dx, dx, dy * dy);
+    double g = 1.0;
+    if (c.gamma_on) {
+      if (R < 0.0 || vd2 == 0.0)
+        nfb++;
+      else
+        g = sqrt(R / vd2);
+    }
+    const double v1x = g * dx, v1y = g * dy;
+    const double y1 = wrap_periodic(fma(dt, vsy, y), c.L, b.err);
+    b.y[p] = y1;
+    b.vx[p] = v1x;
+    b.vy[p] = v1y;
+    ke = fma(c.half_m[s] * (b.w ? b.w[p] : c.w0[s]), fma(v1x, v1x, v1y * v1y), ke);
+    if (c.scheme == 2) {
+      const double ys = wrap_periodic(fma(hdt, v1y, y1), c.L, b.err);
+      const Shape64<ORDER> S2(ys * c.inv_h, n);
+      const double qw = marker_qw(c, b, s, p);
+      S2.deposit(Jt, qw * v1x);
+      S2.deposit(Jt + n, qw * v1y);
+    }
+  }
+  if (!isfinite(ke)) atomicOr(b.err, kErrNonfinite);
+  const unsigned fbw = __reduce_add_sync(0xffffffffu, nfb);
+  if ((threadIdx.x & 31) == 0 && fbw) atomicAdd(&b.fallback[slot], (unsigned long long)fbw);
+  const double kb = block_sum_d(ke, red);
+  if (threadIdx.x == 0) b.ke_part[blockIdx.x] = kb;
+  __syncthreads();
+  if (c.scheme == 2)
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x)
+      if (Jt[i] != 0.0) atomicAdd(&b.J1[i], Jt[i]);
+  if (arrive_last(b.done + 1)) {
+    // TE of the new state: KE from the block partials in block order, W_E + W_B
+    double wf = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double ex = __ldcg(b.En + i), ey = __ldcg(b.En + n + i), bz = __ldcg(b.Bn + i);
+      wf += 0.5 * c.h * (ex * ex + ey * ey) + 0.5 * c.c2 * c.h * bz * bz;
+    }
+    const double wsum = block_sum_d(wf, red);
+    if (threadIdx.x == 0) {
+      double k = 0.0;
+      for (int i = 0; i < (int)gridDim.x; i++) k += __ldcg(b.ke_part + i);
+      b.te[slot] = k + wsum;
+    }
+    double2 *Z = (double2 *)sm;
+    if (c.scheme == 2) {
+      field_advance(c, c.solver == 1 ? 0 : 2, hdt, b.En, b.Bn, b.J1, b.Es, b.Bs, nullptr, nullptr,
+                    Z, Z + n);
+    } else {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        b.Es[i] = __ldcg(b.En + i);
+        b.Es[n + i] = __ldcg(b.En + n + i);
+        b.Bs[i] = __ldcg(b.Bn + i);
+      }
+    }
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) b.J2[i] = 0.0;
+  }
+}
+
+// j^{0,*} of the initial state (ESEC2 form): deposit of v^n at y^n + dt/2 vy^n.
+template <int ORDER>
+__global__ void __launch_bounds__(kEm1Threads) em1d_deposit_initial_kernel(Em1dConst c,
+                                                                            Em1dBufs b) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n_total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int s = species_of1(c, p);
+    const double ys = wrap_periodic(fma(0.5 * c.dt, b.vy[p], b.y[p]), c.L, b.err);
+    const Shape64<ORDER> S(ys * c.inv_h, c.n);
+    const double qw = marker_qw(c, b, s, p);
+    S.deposit(b.J1, qw * b.vx[p]);
+    S.deposit(b.J1 + c.n, qw * b.vy[p]);
+  }
+}
+
+// The first half step (E*, B*) from (E^n, B^n, j^{n,*}); one block.
+__global__ void __launch_bounds__(kEm1Threads) em1d_half_kernel(Em1dConst c, Em1dBufs b) {
+  extern __shared__ double sm[];
+  double2 *Z = (double2 *)sm;
+  if (c.scheme == 2) {
+    field_advance(c, c.solver == 1 ? 0 : 2, 0.5 * c.dt, b.E, b.B, b.J1, b.Es, b.Bs, nullptr,
+                  nullptr, Z, Z + c.n);
+  } else {
+    for (int i = threadIdx.x; i < c.n; i += blockDim.x) {
+      b.Es[i] = b.E[i];
+      b.Es[c.n + i] = b.E[c.n + i];
+      b.Bs[i] = b.B[i];
+    }
+  }
+}
+
+// Kinetic energy per species (block partials [nsp][grid]) and, from block 0,
+// W_E and W_B of the current fields (wf[0], wf[1]).
+__global__ void __launch_bounds__(kEm1Threads) em1d_energy_kernel(Em1dConst c, Em1dBufs b,
+                                                                   double *ke_out, double *wf) {
+  __shared__ double red[33];
+  for (int s = 0; s < c.nsp; s++) {
+    const int64_t lo = s == 0 ? 0 : c.sp_end[s - 1], hi = c.sp_end[s];
+    double acc = 0.0;
+    for (int64_t p = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < hi;
+         p += (int64_t)gridDim.x * blockDim.x)
+      acc = fma(b.w ? b.w[p] : c.w0[s], fma(b.vx[p], b.vx[p], b.vy[p] * b.vy[p]), acc);
+    const double t = block_sum_d(acc, red);
+    if (threadIdx.x == 0) ke_out[(size_t)s * gridDim.x + blockIdx.x] = c.half_m[s] * t;
+    __syncthreads();
+  }
+  if (blockIdx.x == 0) {
+    double we = 0.0, wb = 0.0;
+    for (int i = threadIdx.x; i < c.n; i += blockDim.x) {
+      we = fma(b.E[i], b.E[i], fma(b.E[c.n + i], b.E[c.n + i], we));
+      wb = fma(b.B[i], b.B[i], wb);
+    }
+    const double a = block_sum_d(we, red);
+    const double d = block_sum_d(wb, red);
+    if (threadIdx.x == 0) {
+      wf[0] = 0.5 * c.h * a;
+      wf[1] = 0.5 * c.c2 * c.h * d;
+    }
+  }
+}
+
+size_t pass_smem(const Em1dConst &c) { return sizeof(double) * 8 * (size_t)c.n; }
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+__global__ void em1d_validate_kernel(const double *y, const double *vx, const double *vy,
+                                     int64_t n, double L, unsigned *err) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    if (!(y[p] >= 0.0 && y[p] < L)) atomicOr(err, kErrBounds);
+    if (!isfinite(vx[p]) || !isfinite(vy[p])) atomicOr(err, kErrNonfinite);
+  }
+}
+
+cudaError_t em1d_prepare(const Em1dConst &c) {
+  const size_t sm = pass_smem(c);
+  cudaError_t e = cudaSuccess;
+  if (c.order == 1) {
+    if ((e = allow_smem(em1d_pass_c_kernel<1>, sm))) return e;
+    if ((e = allow_smem(em1d_pass_e_kernel<1>, sm))) return e;
+  } else {
+    if ((e = allow_smem(em1d_pass_c_kernel<2>, sm))) return e;
+    if ((e = allow_smem(em1d_pass_e_kernel<2>, sm))) return e;
+  }
+  return allow_smem(em1d_half_kernel, sm);
+}
+
+void em1d_pass_c(const Em1dConst &c, const Em1dBufs &b, LaunchShape lp, cudaStream_t st) {
+  const size_t sm = pass_smem(c);
+  if (c.order == 1)
+    em1d_pass_c_kernel<1><<<lp.grid, kEm1Threads, sm, st>>>(c, b);
+  else
+    em1d_pass_c_kernel<2><<<lp.grid, kEm1Threads, sm, st>>>(c, b);
+}
+
+void em1d_pass_e(const Em1dConst &c, const Em1dBufs &b, int slot, LaunchShape lp,
+                 cudaStream_t st) {
+  const size_t sm = pass_smem(c);
+  if (c.order == 1)
+    em1d_pass_e_kernel<1><<<lp.grid, kEm1Threads, sm, st>>>(c, b, slot);
+  else
+    em1d_pass_e_kernel<2><<<lp.grid, kEm1Threads, sm, st>>>(c, b, slot);
+}
+
+void em1d_start(const Em1dConst &c, const Em1dBufs &b, LaunchShape lp, cudaStream_t st) {
+  if (c.scheme == 2) {
+    if (c.order == 1)
+      em1d_deposit_initial_kernel<1><<<lp.grid, kEm1Threads, 0, st>>>(c, b);
+    else
+      em1d_deposit_initial_kernel<2><<<lp.grid, kEm1Threads, 0, st>>>(c, b);
+  }
+  em1d_half_kernel<<<1, kEm1Threads, pass_smem(c), st>>>(c, b);
+}
+
+void em1d_energy(const Em1dConst &c, const Em1dBufs &b, double *ke_out, double *wf,
+                 LaunchShape lp, cudaStream_t st) {
+  em1d_energy_kernel<<<lp.grid, kEm1Threads, 0, st>>>(c, b, ke_out, wf);
+}
+
+}  // namespace pic

@@ -80,6 +80,12 @@ struct pic_handle {
   // 1D FP64 state (in the mixed form x, v serve as FP64 staging for get/set)
   Es1dConst c1{};
   Es1dFp64Bufs b1{};
+  // 1D2V spectral state (Crank-Nicolson or PSATD field solve)
+  bool em1 = false;
+  Em1dConst c1e{};
+  Em1dBufs b1e{};
+  LaunchShape le{1, 256};
+  double *e1_part = nullptr;  // pic_energy's partials [nsp][le.grid] and W_E, W_B
   // 2D3V Yee state
   bool em = false;
   Em2dConst ce{};
@@ -665,6 +671,105 @@ int init_em2d(pic_handle *h, const pic_species *species, const double *E0, const
   return restart_em2d(h);
 }
 
+// 1D2V spectral state change: validate markers, j^{n,*} and the half step.
+int restart_em1d(pic_handle *h) {
+  Em1dBufs &b = h->b1e;
+  const int n = h->c1e.n;
+  em1d_validate_kernel<<<h->le.grid, 256, 0, h->st>>>(b.y, b.vx, b.vy, h->N, h->c1e.L, b.err);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(b.J1, 0, sizeof(double) * 2 * n, h->st));
+  CUDA_TRY(cudaMemsetAsync(b.J2, 0, sizeof(double) * 2 * n, h->st));
+  CUDA_TRY(cudaMemsetAsync(b.done, 0, sizeof(unsigned) * 2, h->st));
+  em1d_start(h->c1e, b, h->le, h->st);
+  CUDA_TRY(cudaGetLastError());
+  h->launches += 2 + (h->c1e.scheme == 2);
+  return check_flags(h, "pic_init/pic_set_*");
+}
+
+// 1D2V with a spectral field solve: constants, SoA markers (y, vx, vy), fields.
+int init_em1d(pic_handle *h, const pic_species *species, const double *E0, const double *B0) {
+  const pic_config &cfg = h->cfg;
+  Em1dConst &c = h->c1e;
+  Em1dBufs &b = h->b1e;
+  c.n = (int)cfg.grid.n[0];
+  c.log2n = 0;
+  while ((1 << c.log2n) < c.n) c.log2n++;
+  c.order = cfg.shape_order;
+  c.scheme = cfg.scheme;
+  c.solver = cfg.solver == PIC_SOLVER_CN_SPECTRAL ? 1 : 2;
+  c.gamma_on = cfg.gamma_on;
+  c.nsp = h->nsp;
+  c.n_total = h->N;
+  c.L = cfg.grid.L[0];
+  c.h = c.L / c.n;
+  c.inv_h = c.n / c.L;
+  c.dt = cfg.dt;
+  c.c = cfg.c;
+  c.c2 = cfg.c * cfg.c;
+  for (int s = 0; s < h->nsp; s++) {
+    const SpeciesInfo &S = h->sp[s];
+    c.sp_end[s] = S.offset + S.n;
+    c.qm[s] = S.q / S.m;
+    c.qw_h[s] = S.q * S.w0 / c.h;
+    c.q_h[s] = S.q / c.h;
+    c.w0[s] = S.w0;
+    c.half_m[s] = 0.5 * S.m;
+  }
+  for (int s = h->nsp; s < kMaxSpecies; s++) c.sp_end[s] = h->N;
+  h->le.block = 256;
+  h->le.grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->N + 255) / 256, (int64_t)h->nsm * 2));
+  const size_t n = (size_t)c.n;
+  int rc;
+  if ((rc = h->alloc(&b.y, h->N)) || (rc = h->alloc(&b.vx, h->N)) || (rc = h->alloc(&b.vy, h->N)))
+    return rc;
+  b.w = nullptr;
+  if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;
+  double **e2[] = {&b.E, &b.En, &b.Es, &b.Ea, &b.J1, &b.J2};
+  for (double **f : e2)
+    if ((rc = h->alloc(f, 2 * n))) return rc;
+  double **e1[] = {&b.B, &b.Bn, &b.Bs, &b.Bh};
+  for (double **f : e1)
+    if ((rc = h->alloc(f, n))) return rc;
+  if ((rc = h->alloc(&b.ke_part, (size_t)h->le.grid)) || (rc = h->alloc(&b.done, 2)) ||
+      (rc = h->alloc(&b.fallback, kStepsCap)) || (rc = h->alloc(&b.te, kStepsCap)) ||
+      (rc = h->alloc(&b.err, 1)) || (rc = h->alloc(&h->ids, h->N)) ||
+      (rc = h->alloc(&h->e1_part, (size_t)h->le.grid * h->nsp + 2)))
+    return rc;
+  h->b1.err = b.err;
+  h->b1.fallback = b.fallback;
+  h->b1.te = b.te;
+  CUDA_TRY(em1d_prepare(c));
+  CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(unsigned), h->st));
+  for (int s = 0; s < h->nsp; s++) {
+    const SpeciesInfo &S = h->sp[s];
+    const pic_species &in = species[s];
+    CUDA_TRY(cudaMemcpyAsync(b.y + S.offset, in.x, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaMemcpyAsync(b.vx + S.offset, in.v, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaMemcpyAsync(b.vy + S.offset, in.v + S.n, sizeof(double) * S.n, cudaMemcpyDefault,
+                             h->st));
+    if (h->weighted) {
+      if (in.w) {
+        CUDA_TRY(cudaMemcpyAsync(b.w + S.offset, in.w, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+      } else {
+        std::vector<double> tmp((size_t)S.n, S.w0);
+        CUDA_TRY(cudaMemcpyAsync(b.w + S.offset, tmp.data(), sizeof(double) * S.n,
+                                 cudaMemcpyHostToDevice, h->st));
+        CUDA_TRY(cudaStreamSynchronize(h->st));
+      }
+    }
+  }
+  std::vector<int64_t> ids((size_t)h->N);
+  for (int s = 0; s < h->nsp; s++)
+    for (int64_t p = 0; p < h->sp[s].n; p++) ids[(size_t)(h->sp[s].offset + p)] = p;
+  CUDA_TRY(cudaMemcpyAsync(h->ids, ids.data(), sizeof(int64_t) * h->N, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(cudaMemsetAsync(b.E, 0, sizeof(double) * 2 * n, h->st));
+  CUDA_TRY(cudaMemsetAsync(b.B, 0, sizeof(double) * n, h->st));
+  if (E0) CUDA_TRY(cudaMemcpyAsync(b.E, E0, sizeof(double) * 2 * n, cudaMemcpyDefault, h->st));
+  if (B0) CUDA_TRY(cudaMemcpyAsync(b.B, B0, sizeof(double) * n, cudaMemcpyDefault, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return restart_em1d(h);
+}
+
 }  // namespace
 
 extern "C" {
@@ -694,6 +799,17 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
       return fail(PIC_ERR_ARG, "pic_init: 1D grid needs 4..%d nodes", kMaxNodes1D);
     if (!(cfg->grid.L[0] > 0.0)) return fail(PIC_ERR_ARG, "pic_init: L must be > 0");
     if (B0) return fail(PIC_ERR_ARG, "pic_init: B0 given for the electrostatic solver");
+  } else if (cfg->solver == PIC_SOLVER_CN_SPECTRAL || cfg->solver == PIC_SOLVER_PSATD) {
+    if (cfg->grid.dim_x != 1 || cfg->grid.dim_v != 2)
+      return fail(PIC_ERR_ARG, "pic_init: the spectral solvers run 1D2V (dim_x = 1, dim_v = 2)");
+    const int64_t n = cfg->grid.n[0];
+    if (n < 4 || n > kSpecMaxNodes || (n & (n - 1)))
+      return fail(PIC_ERR_ARG, "pic_init: the spectral solvers need a power of two in [4, %d] nodes",
+                  kSpecMaxNodes);
+    if (!(cfg->grid.L[0] > 0.0) || !(cfg->c > 0.0) || !std::isfinite(cfg->c))
+      return fail(PIC_ERR_ARG, "pic_init: the spectral solvers need L > 0 and c > 0");
+    if (cfg->precision == PIC_PREC_MIXED)
+      return fail(PIC_ERR_UNSUPPORTED, "pic_init: the spectral solvers run in the FP64 form");
   } else if (cfg->solver == PIC_SOLVER_YEE_LEAPFROG) {
     if (cfg->grid.dim_x != 2 || cfg->grid.dim_v != 3)
       return fail(PIC_ERR_ARG, "pic_init: the Yee solver runs 2D3V (dim_x = 2, dim_v = 3)");
@@ -752,7 +868,10 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
   }
   h->nsm = nsm;
   h->em = cfg->solver == PIC_SOLVER_YEE_LEAPFROG;
-  int rc = h->em ? init_em2d(h, species, E0, B0) : init_es1d(h, species, E0);
+  h->em1 = cfg->solver == PIC_SOLVER_CN_SPECTRAL || cfg->solver == PIC_SOLVER_PSATD;
+  int rc = h->em    ? init_em2d(h, species, E0, B0)
+           : h->em1 ? init_em1d(h, species, E0, B0)
+                    : init_es1d(h, species, E0);
   if (rc) {
     std::string msg = g_last_error;
     delete h;
@@ -773,6 +892,17 @@ int pic_step_async(pic_handle *h, int nsteps) {
   if (h->pending == 0 && nsteps > 0) {
     CUDA_TRY(cudaMemsetAsync(b.fallback, 0, sizeof(unsigned long long) * kStepsCap, h->st));
   }
+  for (int k = 0; k < nsteps && h->em1; k++) {
+    Em1dBufs &e = h->b1e;
+    const int slot = h->pending;
+    CUDA_TRY(h->timed_launch(0, [&] { em1d_pass_c(h->c1e, e, h->le, h->st); }));
+    CUDA_TRY(h->timed_launch(1, [&] { em1d_pass_e(h->c1e, e, slot, h->le, h->st); }));
+    h->launches += 2;
+    std::swap(e.E, e.En);
+    std::swap(e.B, e.Bn);
+    h->steps_done++;
+    h->pending++;
+  }
   for (int k = 0; k < nsteps && h->em; k++) {
     Em2dBufs &e = h->be;
     const int slot = h->pending;
@@ -791,7 +921,7 @@ int pic_step_async(pic_handle *h, int nsteps) {
     h->steps_done++;
     h->pending++;
   }
-  for (int k = 0; k < nsteps && !h->em; k++) {
+  for (int k = 0; k < nsteps && !h->em && !h->em1; k++) {
     if (h->mixed) {
       if (h->cm.mode == 1 && h->steps_done > 0 && h->steps_done % h->cfg.sort_period == 0) {
         int rc = sort_mixed(h);
@@ -832,7 +962,7 @@ int pic_read_stats(pic_handle *h, int capacity, int64_t *nfallback_per_step, dou
   if ((nfallback_per_step || te_per_step) && capacity < n)
     return fail(PIC_ERR_ARG, "pic_read_stats: %d steps pending, capacity %d", n, capacity);
   Es1dFp64Bufs &b = h->b1;
-  if (!h->em) {
+  if (!h->em && !h->em1) {
     CUDA_TRY(h->timed_launch(2, [&] {
       if (h->mixed)
         es1d_mix_finalize(h->cm, h->bm, n - 1, h->lmix.grid, h->st);
@@ -939,9 +1069,36 @@ static int energy_em2d(pic_handle *h, double *KE_per_species, double *W_E, doubl
   return PIC_OK;
 }
 
+static int energy_em1d(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, double *TE) {
+  const int nb = h->le.grid;
+  double *ke = h->e1_part, *wf = h->e1_part + (size_t)nb * h->nsp;
+  em1d_energy(h->c1e, h->b1e, ke, wf, h->le, h->st);
+  CUDA_TRY(cudaGetLastError());
+  h->launches += 1;
+  std::vector<double> part((size_t)nb * h->nsp + 2);
+  CUDA_TRY(cudaMemcpyAsync(part.data(), h->e1_part, sizeof(double) * part.size(),
+                           cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  double te = 0.0;
+  for (int s = 0; s < h->nsp; s++) {
+    double k = 0.0;
+    for (int i = 0; i < nb; i++) k += part[(size_t)s * nb + i];
+    if (KE_per_species) KE_per_species[s] = k;
+    te += k;
+  }
+  const double we = part[(size_t)nb * h->nsp], wb = part[(size_t)nb * h->nsp + 1];
+  te += we + wb;
+  if (W_E) *W_E = we;
+  if (W_B) *W_B = wb;
+  if (TE) *TE = te;
+  if (!std::isfinite(te)) return fail(PIC_ERR_NONFINITE, "pic_energy: non-finite energy");
+  return PIC_OK;
+}
+
 int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, double *TE) {
   if (!h) return fail(PIC_ERR_ARG, "pic_energy: NULL handle");
   if (h->em) return energy_em2d(h, KE_per_species, W_E, W_B, TE);
+  if (h->em1) return energy_em1d(h, KE_per_species, W_E, W_B, TE);
   const Es1dConst &c = h->c1;
   // own partials: the stepping kernels keep the last step's partials in ke_part
   // until the next step (or pic_read_stats) has reduced them
@@ -984,6 +1141,18 @@ int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, 
 int pic_get_particles(pic_handle *h, int s, double *x, double *v) {
   if (!h || s < 0 || s >= h->nsp) return fail(PIC_ERR_ARG, "pic_get_particles: bad handle or species");
   const SpeciesInfo &S = h->sp[s];
+  if (h->em1) {
+    if (x) CUDA_TRY(cudaMemcpyAsync(x, h->b1e.y + S.offset, sizeof(double) * S.n, cudaMemcpyDefault,
+                                    h->st));
+    if (v) {
+      CUDA_TRY(cudaMemcpyAsync(v, h->b1e.vx + S.offset, sizeof(double) * S.n, cudaMemcpyDefault,
+                               h->st));
+      CUDA_TRY(cudaMemcpyAsync(v + S.n, h->b1e.vy + S.offset, sizeof(double) * S.n,
+                               cudaMemcpyDefault, h->st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    return PIC_OK;
+  }
   if (h->em) {
     const double *src[5] = {h->be.x, h->be.y, h->be.vx, h->be.vy, h->be.vz};
     for (int d = 0; d < 2 && x; d++)
@@ -1018,6 +1187,18 @@ int pic_get_ids(pic_handle *h, int s, int64_t *ids) {
 int pic_set_particles(pic_handle *h, int s, const double *x, const double *v) {
   if (!h || s < 0 || s >= h->nsp || !x || !v) return fail(PIC_ERR_ARG, "pic_set_particles: bad arguments");
   const SpeciesInfo &S = h->sp[s];
+  if (h->em1) {
+    CUDA_TRY(cudaMemcpyAsync(h->b1e.y + S.offset, x, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaMemcpyAsync(h->b1e.vx + S.offset, v, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaMemcpyAsync(h->b1e.vy + S.offset, v + S.n, sizeof(double) * S.n, cudaMemcpyDefault,
+                             h->st));
+    std::vector<int64_t> ids((size_t)S.n);
+    for (int64_t p = 0; p < S.n; p++) ids[(size_t)p] = p;
+    CUDA_TRY(cudaMemcpyAsync(h->ids + S.offset, ids.data(), sizeof(int64_t) * S.n,
+                             cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    return restart_em1d(h);
+  }
   if (h->em) {
     double *dst[5] = {h->be.x, h->be.y, h->be.vx, h->be.vy, h->be.vz};
     for (int d = 0; d < 2; d++)
@@ -1045,6 +1226,13 @@ int pic_set_particles(pic_handle *h, int s, const double *x, const double *v) {
 
 int pic_get_fields(pic_handle *h, double *E, double *B) {
   if (!h) return fail(PIC_ERR_ARG, "pic_get_fields: NULL handle");
+  if (h->em1) {
+    const size_t n = (size_t)h->c1e.n;
+    if (E) CUDA_TRY(cudaMemcpyAsync(E, h->b1e.E, sizeof(double) * 2 * n, cudaMemcpyDefault, h->st));
+    if (B) CUDA_TRY(cudaMemcpyAsync(B, h->b1e.B, sizeof(double) * n, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    return PIC_OK;
+  }
   if (h->em) {
     const size_t nc3 = 3 * (size_t)h->ce.nx * h->ce.ny;
     if (E) CUDA_TRY(cudaMemcpyAsync(E, h->be.E, sizeof(double) * nc3, cudaMemcpyDefault, h->st));
@@ -1062,6 +1250,14 @@ int pic_get_fields(pic_handle *h, double *E, double *B) {
 
 int pic_set_fields(pic_handle *h, const double *E, const double *B) {
   if (!h || !E) return fail(PIC_ERR_ARG, "pic_set_fields: bad arguments");
+  if (h->em1) {
+    if (!B) return fail(PIC_ERR_ARG, "pic_set_fields: the spectral solvers need Bz");
+    const size_t n = (size_t)h->c1e.n;
+    CUDA_TRY(cudaMemcpyAsync(h->b1e.E, E, sizeof(double) * 2 * n, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaMemcpyAsync(h->b1e.B, B, sizeof(double) * n, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    return restart_em1d(h);
+  }
   if (h->em) {
     if (!B) return fail(PIC_ERR_ARG, "pic_set_fields: the Yee solver needs B^{n-1/2}");
     const size_t nc3 = 3 * (size_t)h->ce.nx * h->ce.ny;
@@ -1080,7 +1276,7 @@ int pic_set_fields(pic_handle *h, const double *E, const double *B) {
 int pic_grad_forward(pic_handle *h, int nsteps, int checkpoint_every) {
   if (!h || nsteps <= 0 || checkpoint_every <= 0)
     return fail(PIC_ERR_ARG, "pic_grad_forward: bad arguments");
-  if (h->em || h->mixed)
+  if (h->em || h->em1 || h->mixed)
     return fail(PIC_ERR_UNSUPPORTED, "pic_grad_forward: the reverse mode is built for the FP64 "
                                      "1D form");
   if (h->pending) return fail(PIC_ERR_ARG, "pic_grad_forward: read the pending stats first");

@@ -142,6 +142,41 @@ struct Em2dBufs {
   unsigned *err;
 };
 
+// 1D2V electromagnetic path with a pseudospectral field solve (Crank-Nicolson
+// or PSATD), FP64; n a power of two in [4, kSpecMaxNodes].
+constexpr int kSpecMaxNodes = 1024;
+
+struct Em1dConst {
+  int n, log2n;
+  int order;
+  int scheme;
+  int solver;       // 1 Crank-Nicolson, 2 PSATD
+  int gamma_on;
+  int nsp;
+  int64_t n_total;
+  double L, h, inv_h, dt, c, c2;
+  int64_t sp_end[kMaxSpecies];
+  double qm[kMaxSpecies];
+  double qw_h[kMaxSpecies];     // q w0 / h
+  double q_h[kMaxSpecies];      // q / h (weighted markers)
+  double w0[kMaxSpecies];
+  double half_m[kMaxSpecies];
+};
+
+struct Em1dBufs {
+  double *y, *vx, *vy, *w;   // [N] SoA (w may be null)
+  double *E, *En;            // E^n, E^{n+1}: [2][n] (Ex, Ey); swapped after each step
+  double *B, *Bn;            // Bz^n, Bz^{n+1}: [n]
+  double *Es, *Bs;           // E*, B* of the half step
+  double *Ea, *Bh;           // the E of v^dag (E^{n+1/2} or <E>) and B^{n+1/2}
+  double *J1, *J2;           // j^{n,*}, j^{*,n+1/2}: [2][n]
+  double *ke_part;           // [particle blocks]
+  unsigned *done;            // [2] arrival counters of pass C and pass E
+  unsigned long long *fallback;
+  double *te;
+  unsigned *err;
+};
+
 // Everything the 1D FP64 kernels touch.
 struct Es1dFp64Bufs {
   double *x, *v, *w;        // [N] SoA (w may be null)
@@ -216,6 +251,18 @@ void em2d_fp64_kinetic(const Em2dConst &c, const Em2dBufs &b, double *out, int n
 __global__ void em2d_validate_kernel(const double *x, const double *y, const double *vx,
                                      const double *vy, const double *vz, int64_t n, double Lx,
                                      double Ly, unsigned *err);
+
+// 1D2V spectral path (em1d_spectral.cu)
+cudaError_t em1d_prepare(const Em1dConst &c);
+void em1d_pass_c(const Em1dConst &c, const Em1dBufs &b, LaunchShape lp, cudaStream_t st);
+void em1d_pass_e(const Em1dConst &c, const Em1dBufs &b, int slot, LaunchShape lp, cudaStream_t st);
+// j^{0,*} (ESEC2 form) and the first E*, B*
+void em1d_start(const Em1dConst &c, const Em1dBufs &b, LaunchShape lp, cudaStream_t st);
+// kinetic energy partials ke_out [nsp][lp.grid] and wf = {W_E, W_B}
+void em1d_energy(const Em1dConst &c, const Em1dBufs &b, double *ke_out, double *wf,
+                 LaunchShape lp, cudaStream_t st);
+__global__ void em1d_validate_kernel(const double *y, const double *vx, const double *vy,
+                                     int64_t n, double L, unsigned *err);
 
 // 1D mixed path (es1d_mixed.cu)
 cudaError_t es1d_mix_prepare(const Es1dMixConst &c);

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libpic.so")
 PIC_OK = 0
 ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_OOM", -4: "PIC_ERR_NONFINITE",
           -5: "PIC_ERR_TIMEOUT", -6: "PIC_ERR_BOUNDS", -7: "PIC_ERR_UNSUPPORTED"}
-PIC_SOLVER_AMPERE_ES, PIC_SOLVER_YEE_LEAPFROG = 0, 1
+PIC_SOLVER_AMPERE_ES, PIC_SOLVER_YEE_LEAPFROG, PIC_SOLVER_CN_SPECTRAL, PIC_SOLVER_PSATD = 0, 1, 2, 3
 PIC_SCHEME_ESEC1, PIC_SCHEME_ESEC2 = 1, 2
 PIC_PREC_FP64, PIC_PREC_MIXED = 0, 1
 
@@ -325,6 +325,63 @@ class Simulation2D:
     def fields(self):
         shape = (3, self.prob.ny, self.prob.nx)
         E, B = np.zeros(shape), np.zeros(shape)
+        pic_get_fields(self.h, E, B)
+        return E, B
+
+    def energy(self):
+        return pic_energy(self.h, len(self.species))
+
+    def close(self):
+        if self.h:
+            pic_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Simulation1D2V:
+    """Owner of one spectral-solver handle (Crank-Nicolson or PSATD) built from
+    a ``workloads.Problem1D2V``."""
+
+    def __init__(self, prob, solver=PIC_SOLVER_PSATD, scheme=PIC_SCHEME_ESEC2, E0=None, B0=None,
+                 gamma_on=True, stream=None):
+        self.prob = prob
+        self.cfg = make_config(prob.n, prob.L, prob.dt, prob.order, scheme, PIC_PREC_FP64,
+                               solver=solver, dim_x=1, dim_v=2, c=prob.c, gamma_on=gamma_on,
+                               stream=stream)
+        self.species = []
+        for s in prob.species:
+            self.species.append(dict(q=s.q, m=s.m, x=np.ascontiguousarray(s.y, dtype=np.float64),
+                                     v=np.ascontiguousarray(np.stack([s.vx, s.vy]),
+                                                            dtype=np.float64),
+                                     n=len(s.y),
+                                     w=None if s.w is None else np.ascontiguousarray(s.w),
+                                     w0=s.w0))
+        E0 = prob.E0 if E0 is None else E0
+        B0 = prob.B0 if B0 is None else B0
+        self.h = pic_init(self.cfg, self.species, np.ascontiguousarray(E0, dtype=np.float64),
+                          np.ascontiguousarray(B0, dtype=np.float64))
+
+    def step(self, nsteps: int):
+        fb = np.zeros(nsteps, dtype=np.int64)
+        te = np.zeros(nsteps)
+        pic_step(self.h, nsteps, fb, te)
+        return fb, te
+
+    def particles(self, s: int = 0):
+        """(y, vx, vy) of species s."""
+        n = self.species[s]["n"]
+        y, v = np.zeros(n), np.zeros((2, n))
+        pic_get_particles(self.h, s, y, v)
+        return y, v[0], v[1]
+
+    def fields(self):
+        """(E [2, n], Bz [n])."""
+        E, B = np.zeros((2, self.prob.n)), np.zeros(self.prob.n)
         pic_get_fields(self.h, E, B)
         return E, B
 

@@ -47,6 +47,13 @@ def test_argument_errors_are_status_codes(lib):
         pic.make_config(2, 1.0, 0.1),
         pic.make_config(64, 1.0, 0.1, scheme=3),
         pic.make_config(64, 1.0, 0.1, dim_x=2),
+        # spectral solvers: a power of two in [4, 1024] nodes, dim_v = 2, c > 0
+        pic.make_config(48, 1.0, 0.1, solver=pic.PIC_SOLVER_PSATD, dim_v=2),
+        pic.make_config(2048, 1.0, 0.1, solver=pic.PIC_SOLVER_CN_SPECTRAL, dim_v=2),
+        pic.make_config(2, 1.0, 0.1, solver=pic.PIC_SOLVER_CN_SPECTRAL, dim_v=2),
+        pic.make_config(64, 1.0, 0.1, solver=pic.PIC_SOLVER_PSATD, dim_v=1),
+        pic.make_config(64, 1.0, 0.1, solver=pic.PIC_SOLVER_PSATD, dim_v=2, c=0.0),
+        pic.make_config(64, 1.0, 0.1, solver=4, dim_v=2),
     ]
     for cfg in bad:
         with pytest.raises(pic.PicError) as ei:
@@ -55,6 +62,10 @@ def test_argument_errors_are_status_codes(lib):
     with pytest.raises(pic.PicError) as ei:
         pic.pic_init(pic.make_config(64, 1.0, 0.1), [])
     assert ei.value.code == -1
+    with pytest.raises(pic.PicError) as ei:   # the spectral solvers have no mixed form
+        pic.pic_init(pic.make_config(64, 1.0, 0.1, precision=pic.PIC_PREC_MIXED,
+                                     solver=pic.PIC_SOLVER_PSATD, dim_v=2), sp)
+    assert ei.value.code == -7
     assert lib.pic_step(None, 1, None, None) == -1
     lib.pic_free(None)  # no-op
 
