@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--sort-period", type=int, default=0,
                     help="cell sort of the mixed form every this many steps (0 = never)")
+    ap.add_argument("--weibel1d", action="store_true",
+                    help="time the 1D2V electromagnetic path (Crank-Nicolson and PSATD field "
+                         "solves) on the Weibel workload instead (not the default line)")
     ap.add_argument("--grad", action="store_true",
                     help="time the reverse mode on the bump-on-tail workload instead (not the "
                          "default line), with the finite-difference agreement vs horizon")
@@ -491,6 +494,133 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+# pass C reads y, vx, vy; pass E reads and writes them (v* is recomputed)
+EM1D_ALGO_BYTES = {0: 24, 1: 48}
+# FP64-pipe thread instructions per marker of the 1D2V passes (ncu,
+# sm__thread_inst_executed_pipe_fp64_pred_on.sum / markers at 2^23 markers):
+# like the FP64 1D form these passes are bound by the FP64 pipe, not by HBM
+EM1D_FP64_INST_PER_MARKER = {0: 54.45, 1: 120.34}
+# DRAM bytes per launch at 2^23 markers (dram__bytes_read.sum + dram__bytes_write.sum)
+EM1D_TRAFFIC = {0: 204952064, 1: 341139456}
+
+
+def run_weibel1d(args):
+    """The 1D2V Weibel test of Sec. 5 (32 cells, beta 0.01, beams +-0.3, b 0.001,
+    k0 0.2, dt 0.1, c 1) with both spectral field solves: the paper's size
+    (3200 markers per cell, 102,400 markers) over a long run for the energy
+    error, and 2^23 markers (262,144 per cell) for throughput and the HBM
+    roofline of the passes."""
+    import torch
+    from paper_2411_09605_gb300 import build as B, pic, workloads as W
+    B.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    dev = torch.device("cuda", 0)
+    peak, peak_src = hbm_peak()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    long_steps = max(10, min(args.steps * 10, 4000))
+    out = {}
+    with ClockSampler(0, enabled=not args.no_clocks) as clk:
+        for name, solver in (("cn", pic.PIC_SOLVER_CN_SPECTRAL), ("psatd", pic.PIC_SOLVER_PSATD)):
+            res = {}
+            # the paper's size: state 2.5 MB, L2-resident; chunks of <= 1000 steps
+            prob = W.weibel_1d2v(seed=0)
+            sim = pic.Simulation1D2V(prob, solver=solver, stream=stream.cuda_stream)
+            try:
+                te0 = sim.energy()[3]
+                fbs, tes, ms = [], [], 0.0
+                left = long_steps
+                while left:
+                    k = min(left, 1000)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    a.record(stream)
+                    pic.pic_step_async(sim.h, k)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    ms += a.elapsed_time(b)
+                    fb, te = pic.pic_read_stats(sim.h)
+                    fbs.append(fb)
+                    tes.append(te)
+                    left -= k
+                fb, te = np.concatenate(fbs), np.concatenate(tes)
+                WE = sim.energy()
+            finally:
+                sim.close()
+            res["paper_size"] = {
+                "markers": prob.n_markers, "steps": long_steps, "t_end": long_steps * prob.dt,
+                "value": prob.n_markers * long_steps / (ms / 1e3), "us_per_step": 1e3 * ms / long_steps,
+                "max_rel_dTE": float(np.max(np.abs(te - te0)) / te0), "fallbacks": int(fb.sum()),
+                "W_B_end": WE[2], "l2": "resident (2.5 MB state), not flushed"}
+            # 2^23 markers: per-step events, L2 flushed between steps
+            big = W.weibel_1d2v(ppc=(1 << 23) // 32, seed=1)
+            sim = pic.Simulation1D2V(big, solver=solver, stream=stream.cuda_stream)
+            try:
+                te0 = sim.energy()[3]
+                pic.pic_step_async(sim.h, max(3, args.warmup))
+                pic.pic_read_stats(sim.h)
+                evs = []
+                for _ in range(args.steps):
+                    flush.zero_()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    pic.pic_step_async(sim.h, 1)
+                    b.record(stream)
+                    evs.append((a, b))
+                fb, te = pic.pic_read_stats(sim.h)
+                torch.cuda.synchronize()
+                step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+                pic.pic_set_profiling(sim.h, True)
+                for _ in range(args.profile_steps):
+                    flush.zero_()
+                    pic.pic_step_async(sim.h, 1)
+                pic.pic_read_stats(sim.h)
+                kern = {}
+                nsm = torch.cuda.get_device_properties(0).multi_processor_count
+                fp64_peak = FP64_LANES_PER_SM_CLK * nsm * 2070.0e6 / 1e9   # Ginst/s
+                for kind, kname in ((0, "pass_c"), (1, "pass_e")):
+                    n, tot = pic.pic_profile(sim.h, kind)
+                    if n:
+                        avg = 1e3 * tot / n
+                        ach = EM1D_ALGO_BYTES[kind] * big.n_markers / (avg * 1e-6) / 1e9
+                        inst = EM1D_FP64_INST_PER_MARKER[kind] * big.n_markers / (avg * 1e-6) / 1e9
+                        kern[kname] = {"avg_us": avg, "launches": n, "achieved_GBs": round(ach, 1),
+                                       "frac_hbm": round(ach / peak, 4),
+                                       "fp64_ginst_s": round(inst, 1), "fp64_peak": round(fp64_peak, 1),
+                                       "frac_fp64": round(inst / fp64_peak, 4)}
+                pic.pic_set_profiling(sim.h, False)
+            finally:
+                sim.close()
+            res["2p23"] = {"markers": big.n_markers, "steps": args.steps,
+                           "value": big.n_markers * args.steps / (step_ms.sum() / 1e3),
+                           "us_per_step": 1e3 * float(step_ms.mean()),
+                           "max_rel_dTE": float(np.max(np.abs(te - te0)) / te0),
+                           "fallbacks": int(fb.sum()), "kernels": kern,
+                           "l2": "flushed (512 MiB write) before every timed step"}
+            out[name] = res
+    head = out["psatd"]["2p23"]
+    dom = max(head["kernels"].items(), key=lambda kv: kv[1]["avg_us"])
+    line = {
+        "metric": "particle-steps/s, 1D2V Weibel with spectral EM field solves",
+        "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": head["us_per_step"] / 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Weibel markers, quiet start in y)",
+        "config": {"workload": "weibel_1d2v", "cells": 32, "dt": 0.1, "c": 1.0, "shape_order": 1,
+                   "scheme": "ESEC2", "value_from": "PSATD at 2^23 markers"},
+        "roofline": {"bound": "alu", "kernel": dom[0], "achieved": dom[1]["fp64_ginst_s"],
+                     "peak": dom[1]["fp64_peak"], "unit": "Ginst/s (FP64 pipe)",
+                     "frac": dom[1]["frac_fp64"],
+                     "traffic": EM1D_TRAFFIC[0 if dom[0] == "pass_c" else 1],
+                     "peak_source": f"{FP64_LANES_PER_SM_CLK} FP64 lanes/SM/clk x SMs x 2070 MHz",
+                     "hbm_frac": dom[1]["frac_hbm"]},
+        "solvers": out, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_grad(args):
     """Reverse mode of the FP64 form on the bump-on-tail workload (2^20 weighted
     markers, 256 cells, dt 0.1, 500 steps, checkpoints every 50): throughput of
@@ -613,6 +743,8 @@ def main():
         run_ensemble(args)
     elif args.grad:
         run_grad(args)
+    elif args.weibel1d:
+        run_weibel1d(args)
     else:
         run_ours(args)
 

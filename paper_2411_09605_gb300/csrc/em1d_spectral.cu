@@ -12,11 +12,10 @@
 // Two launches per step, like the other particle paths:
 //   pass C  every block: E*, B* tables in shared memory; per marker y*,
 //           E**, B**, the closed-form v* of v* = v^n + dt/2 (q/m)(E** + v* x B**),
-//           y^{n+1/2}, deposit of j^{*,n+1/2} (shared tile, then global atomics).
-//           The block that finishes last does the full field step:
-//           (E^{n+1}, B^{n+1}) by Crank-Nicolson or PSATD over dt with
-//           j^{*,n+1/2}, the E that v^dag uses (E^{n+1/2}, or PSATD's time
-//           average <E>) and B^{n+1/2} = (B^n + B^{n+1})/2.
+//           y^{n+1/2}, deposit of j^{*,n+1/2}.  The block that finishes last
+//           does the full field step: (E^{n+1}, B^{n+1}) by Crank-Nicolson or
+//           PSATD over dt with j^{*,n+1/2}, the E that v^dag uses (E^{n+1/2},
+//           or PSATD's time average <E>) and B^{n+1/2} = (B^n + B^{n+1})/2.
 //   pass E  every block: the same v*, y^{n+1/2} recomputed bit for bit, the
 //           gather of that E and B^{n+1/2}, v^dag, Gamma (Eq. opt_solution;
 //           fallback counted), y^{n+1}, v^{n+1}, the kinetic-energy partial and
@@ -27,7 +26,15 @@
 //           dt/2.
 // "Last block" is a counter taken with one atomic per block after a memory
 // fence; nothing waits.  The field solve is an in-block radix-2 FFT over n
-// (a power of two, 4 <= n <= 1024) in shared memory.
+// (a power of two, 4 <= n <= 1024) in shared memory, with its twiddles and
+// the PSATD per-mode coefficients tabulated once at set-up.
+//
+// Deposits: each lane of a block adds into its own copy of the block's
+// current tile (rt copies, laid out [node][component][copy], rt up to 32 as
+// shared memory allows), so FP64 shared atomics rarely meet; the flush sums
+// the copies and adds the block's tile into one of kJSlices slices of the
+// global current, which spreads the blocks' global atomics over kJSlices
+// addresses per node; the field solve sums the slices.
 #include <cuda_runtime.h>
 
 #include "es1d_fp64_common.cuh"
@@ -73,9 +80,9 @@ __device__ __forceinline__ double2 ctimes_i(double2 a) { return {-a.y, a.x}; }  
 __device__ __forceinline__ double2 cconj(double2 a) { return {a.x, -a.y}; }
 
 // In-place radix-2 transform of n = 2^log2n values in shared memory:
-// a_k <- sum_j a_j exp(sign 2 pi i j k / n) (unnormalised).  Every thread of
-// the block takes part.
-__device__ void block_fft(double2 *a, int n, int log2n, double sign) {
+// a_k <- sum_j a_j exp(sign 2 pi i j k / n) (unnormalised), sign = -1 or +1.
+// tw[j] = exp(-2 pi i j / n), j < n/2.  Every thread of the block takes part.
+__device__ void block_fft(double2 *a, int n, int log2n, int sign, const double2 *tw) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int r = (int)(__brev((unsigned)i) >> (32 - log2n));
     if (r > i) {
@@ -85,15 +92,15 @@ __device__ void block_fft(double2 *a, int n, int log2n, double sign) {
     }
   }
   __syncthreads();
-  for (int len = 2; len <= n; len <<= 1) {
+  for (int len = 2, step = n >> 1; len <= n; len <<= 1, step >>= 1) {
     const int half = len >> 1;
     for (int b = threadIdx.x; b < (n >> 1); b += blockDim.x) {
       const int grp = b / half, j = b - grp * half;
       const int i0 = grp * len + j, i1 = i0 + half;
-      double s, co;
-      sincospi(sign * 2.0 * (double)j / (double)len, &s, &co);
+      double2 w = tw[j * step];
+      if (sign > 0) w.y = -w.y;
       const double2 u = a[i0], v = a[i1];
-      const double2 t = {v.x * co - v.y * s, v.x * s + v.y * co};
+      const double2 t = {v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x};
       a[i0] = cadd(u, t);
       a[i1] = csub(u, t);
     }
@@ -108,66 +115,100 @@ __device__ __forceinline__ double mode_kk(const Em1dConst &c, int k) {
   return 2.0 * 3.141592653589793 * (double)m / c.L;
 }
 
-// Field advance over tau with j held fixed; kind 0 explicit Euler (the half
-// step of Eq. EMbasic), 1 Crank-Nicolson (its full step), 2 PSATD (Eq.
-// PSATDformula with Delta t -> tau).  Reads E [2][n], B [n], J [2][n] from
-// global memory (written by other blocks of this kernel: read through L2),
-// writes Eo, Bo and, when non-null, Ea (the E of v^dag: PSATD's <E> over
-// [0, tau], else (E + Eo)/2) and Bh = (B + Bo)/2.  Z1, Z2: 2n double2 of
-// shared memory.
-__device__ void field_advance(const Em1dConst &c, int kind, double tau, const double *E,
-                              const double *B, const double *J, double *Eo, double *Bo,
-                              double *Ea, double *Bh, double2 *Z1, double2 *Z2) {
+// Sum of the kJSlices slices of a sliced current at entry i of [2][n].
+__device__ __forceinline__ double jsum(const double *J, int n, int i) {
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kJSlices; k++) s += __ldcg(J + (size_t)k * 2 * n + i);
+  return s;
+}
+
+// Per-mode coefficients of the three field advances over tau with j fixed.
+// Each maps the transverse spectra (Ex, Bz, jx) of mode k to
+//   Ex' = a1 Ex + i a2 Bz - a3 jx,   Bz' = a1 Bz + i a4 Ex - i a5 jx,
+// and PSATD's time average <Ex> = b1 Ex + i b2 Bz - b3 jx:
+//   explicit Euler (the half step of Eq. EMbasic): a = (1, c^2 kk tau, tau, kk tau, 0);
+//   Crank-Nicolson (its full step), al = kk tau / 2, d = 1 + c^2 al^2:
+//     a = ((1 - c^2 al^2)/d, 2 c^2 al / d, tau / d, 2 al / d, al tau / d);
+//   PSATD (Eq. PSATDformula with Delta t -> tau), x = |kk| c tau, s = sign kk:
+//     a = (cos x, s c sin x, sin x / (|kk| c), s sin x / c, s (1 - cos x)/(|kk| c^2)),
+//     b = (sin x / x, s (1 - cos x)/(|kk| tau), (1 - cos x)/(kk^2 c^2 tau)),
+//   and for kk = 0 the limits a = (1, 0, tau, 0, 0), b = (1, 0, tau / 2).
+// 1 - cos x is formed as 2 sin^2 (x/2).
+__device__ void mode_coefficients(const Em1dConst &c, int kind, double tau, int k, double *q) {
+  const double kk = mode_kk(c, k), c2 = c.c2;
+  for (int i = 0; i < kEm1Coef; i++) q[i] = 0.0;
+  if (kind == 0) {
+    q[0] = 1.0;
+    q[1] = c2 * kk * tau;
+    q[2] = tau;
+    q[3] = kk * tau;
+  } else if (kind == 1) {
+    const double al = 0.5 * kk * tau, d = 1.0 + c2 * al * al;
+    q[0] = (1.0 - c2 * al * al) / d;
+    q[1] = 2.0 * c2 * al / d;
+    q[2] = tau / d;
+    q[3] = 2.0 * al / d;
+    q[4] = al * tau / d;
+  } else if (kk == 0.0) {
+    q[0] = 1.0;
+    q[2] = tau;
+    q[5] = 1.0;
+    q[7] = 0.5 * tau;
+  } else {
+    const double ka = fabs(kk), sg = kk > 0.0 ? 1.0 : -1.0, cc = c.c, x = ka * cc * tau;
+    double S, C, sh, ch;
+    sincos(x, &S, &C);
+    sincos(0.5 * x, &sh, &ch);
+    const double omc = 2.0 * sh * sh;
+    q[0] = C;
+    q[1] = sg * S * cc;
+    q[2] = S / (ka * cc);
+    q[3] = sg * S / cc;
+    q[4] = sg * omc / (ka * c2);
+    q[5] = S / x;
+    q[6] = sg * omc / (ka * tau);
+    q[7] = omc / (ka * ka * c2 * tau);
+  }
+}
+
+// Field advance over tau with j held fixed, from the per-mode coefficients cf
+// [n/2 + 1][kEm1Coef] of mode_coefficients; psatd selects <E> (else the
+// average (E + Eo)/2) for Ea.  Reads E [2][n], B [n] and the sliced J
+// [kJSlices][2][n] from global memory (written by other blocks of this
+// kernel: read through L2), writes Eo, Bo and, when non-null, Ea (the E of
+// v^dag) and Bh = (B + Bo)/2.  Z1: shared scratch of at least 9n + 8 doubles
+// (the two transforms, the twiddles and the coefficients, loaded together).
+__device__ void field_advance(const Em1dConst &c, bool psatd, double tau, const double *cf_g,
+                              const double2 *tw_g, const double *E, const double *B,
+                              const double *J, double *Eo, double *Bo, double *Ea, double *Bh,
+                              double2 *Z1) {
   const int n = c.n;
+  double2 *Z2 = Z1 + n, *tw = Z1 + 2 * n;
+  double *cf = (double *)(tw + n / 2);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     Z1[i] = make_double2(__ldcg(E + i), __ldcg(B + i));
-    Z2[i] = make_double2(__ldcg(J + i), 0.0);
+    Z2[i] = make_double2(jsum(J, n, i), 0.0);
   }
+  for (int i = threadIdx.x; i < n / 2; i += blockDim.x) tw[i] = __ldg(tw_g + i);
+  for (int i = threadIdx.x; i < kEm1Coef * (n / 2 + 1); i += blockDim.x) cf[i] = __ldg(cf_g + i);
   __syncthreads();
-  block_fft(Z1, n, c.log2n, -1.0);
-  block_fft(Z2, n, c.log2n, -1.0);
+  block_fft(Z1, n, c.log2n, -1, tw);
+  block_fft(Z2, n, c.log2n, -1, tw);
   // modes k and n - k by one thread: Z1 holds Ex + i Bz, so
   // Ex_k = (Z_k + conj Z_{n-k}) / 2 and Bz_k = (Z_k - conj Z_{n-k}) / (2i)
-  const double c2 = c.c2;
   for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
     const int k2 = (n - k) & (n - 1);
     const double2 zk = Z1[k], zm = Z1[k2];
     const double2 A = cscale(0.5, cadd(zk, cconj(zm)));
     const double2 Bm = cscale(0.5, {zk.y + zm.y, zm.x - zk.x});   // (zk - conj zm) / (2i)
     const double2 Jk = Z2[k];
-    const double kk = mode_kk(c, k);
-    double2 Ox, Ob, Ax = {0.0, 0.0};
-    if (kind == 0) {
-      Ox = cadd(A, cscale(tau, csub(cscale(c2 * kk, ctimes_i(Bm)), Jk)));
-      Ob = cadd(Bm, cscale(tau * kk, ctimes_i(A)));
-    } else if (kind == 1) {
-      // a = i alpha, alpha = kk tau / 2: r1 = A + c^2 a B - tau J, r2 = B + a A,
-      // Ex' = (r1 + c^2 a r2) / det, Bz' = (r2 + a r1) / det, det = 1 + c^2 alpha^2
-      const double al = 0.5 * kk * tau;
-      const double2 r1 = csub(cadd(A, cscale(c2 * al, ctimes_i(Bm))), cscale(tau, Jk));
-      const double2 r2 = cadd(Bm, cscale(al, ctimes_i(A)));
-      const double inv_det = 1.0 / (1.0 + c2 * al * al);
-      Ox = cscale(inv_det, cadd(r1, cscale(c2 * al, ctimes_i(r2))));
-      Ob = cscale(inv_det, cadd(r2, cscale(al, ctimes_i(r1))));
-    } else {
-      if (kk == 0.0) {
-        Ox = csub(A, cscale(tau, Jk));
-        Ob = Bm;
-        Ax = csub(A, cscale(0.5 * tau, Jk));
-      } else {
-        const double ka = fabs(kk), sg = kk > 0.0 ? 1.0 : -1.0, cc = c.c;
-        const double x = ka * cc * tau;
-        double S, C, sh, chh;
-        sincos(x, &S, &C);
-        sincos(0.5 * x, &sh, &chh);
-        const double omc = 2.0 * sh * sh;  // 1 - cos x without cancellation
-        Ox = cadd(cadd(cscale(C, A), cscale(sg * S * cc, ctimes_i(Bm))), cscale(-S / (ka * cc), Jk));
-        Ob = cadd(cadd(cscale(C, Bm), cscale(sg * S / cc, ctimes_i(A))),
-                  cscale(-sg * omc / (ka * c2), ctimes_i(Jk)));
-        Ax = cadd(cadd(cscale(S / x, A), cscale(sg * omc / (ka * tau), ctimes_i(Bm))),
-                  cscale(-omc / (ka * ka * c2 * tau), Jk));
-      }
-    }
+    const double *q = cf + kEm1Coef * k;
+    const double2 Ox = csub(cadd(cscale(q[0], A), cscale(q[1], ctimes_i(Bm))), cscale(q[2], Jk));
+    const double2 Ob = csub(cadd(cscale(q[0], Bm), cscale(q[3], ctimes_i(A))),
+                            cscale(q[4], ctimes_i(Jk)));
+    const double2 Ax =
+        csub(cadd(cscale(q[5], A), cscale(q[6], ctimes_i(Bm))), cscale(q[7], Jk));
     // repack Ex' + i Bz' (and <Ex>) for the inverse transform; mode n - k holds
     // the conjugates
     Z1[k] = cadd(Ox, ctimes_i(Ob));
@@ -178,18 +219,18 @@ __device__ void field_advance(const Em1dConst &c, int kind, double tau, const do
     }
   }
   __syncthreads();
-  block_fft(Z1, n, c.log2n, 1.0);
-  if (kind == 2 && Ea) block_fft(Z2, n, c.log2n, 1.0);
+  block_fft(Z1, n, c.log2n, 1, tw);
+  if (psatd && Ea) block_fft(Z2, n, c.log2n, 1, tw);
   const double inv_n = 1.0 / (double)n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double ex = __ldcg(E + i), ey = __ldcg(E + n + i), bz = __ldcg(B + i);
-    const double jy = __ldcg(J + n + i);
+    const double jy = jsum(J, n, n + i);
     const double exn = Z1[i].x * inv_n, bzn = Z1[i].y * inv_n;
     Eo[i] = exn;
     Eo[n + i] = ey - tau * jy;
     Bo[i] = bzn;
     if (Ea) {
-      Ea[i] = kind == 2 ? Z2[i].x * inv_n : 0.5 * (ex + exn);
+      Ea[i] = psatd ? Z2[i].x * inv_n : 0.5 * (ex + exn);
       Ea[n + i] = ey - 0.5 * tau * jy;
     }
     if (Bh) Bh[i] = 0.5 * (bz + bzn);
@@ -231,20 +272,52 @@ __device__ __forceinline__ double marker_qw(const Em1dConst &c, const Em1dBufs &
   return b.w ? c.q_h[s] * b.w[p] : c.qw_h[s];
 }
 
+// ------------------------------------------------------------ current tiles
+
+__device__ __forceinline__ void clear_tile(double *Jt, int len) {
+  for (int i = threadIdx.x; i < len; i += blockDim.x) Jt[i] = 0.0;
+}
+
+// (ax, ay) S(y_h - y) into this lane's copy of the tile [n][2][rt].
+template <int ORDER>
+__device__ __forceinline__ void tile_deposit(double *Jt, int rt, const Shape64<ORDER> &S,
+                                             double ax, double ay) {
+  const int l = threadIdx.x & (rt - 1);
+#pragma unroll
+  for (int k = 0; k <= ORDER; k++) {
+    double *q = Jt + (size_t)S.idx[k] * 2 * rt + l;
+    atomicAdd(q, ax * S.w[k]);
+    atomicAdd(q + rt, ay * S.w[k]);
+  }
+}
+
+// Sums each (node, component)'s copies (starting at a rotating copy, so the
+// threads of a warp read different banks) and adds the non-zero totals into
+// this block's slice of the global current J [kJSlices][2][n].
+__device__ void flush_tile(const double *Jt, int rt, double *J, int n) {
+  double *Js = J + (size_t)(blockIdx.x & (kJSlices - 1)) * 2 * n;
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
+    const int node = i >> 1, comp = i & 1;
+    const double *q = Jt + (size_t)i * rt;
+    double a = 0.0;
+    for (int r = 0; r < rt; r++) a += q[(r + i) & (rt - 1)];
+    if (a != 0.0) atomicAdd(&Js[comp * n + node], a);
+  }
+}
+
 // ---------------------------------------------------------------- passes
 
 template <int ORDER>
 __global__ void __launch_bounds__(kEm1Threads) em1d_pass_c_kernel(Em1dConst c, Em1dBufs b) {
   extern __shared__ double sm[];
   const int n = c.n;
-  double *Esx = sm, *Esy = sm + n, *Bs = sm + 2 * n, *Jt = sm + 3 * n;  // Jt [2][n]
+  double *Esx = sm, *Esy = sm + n, *Bs = sm + 2 * n, *Jt = sm + 3 * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     Esx[i] = b.Es[i];
     Esy[i] = b.Es[n + i];
     Bs[i] = b.Bs[i];
-    Jt[i] = 0.0;
-    Jt[n + i] = 0.0;
   }
+  clear_tile(Jt, 2 * n * c.rt);
   __syncthreads();
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n_total;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -253,16 +326,14 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_c_kernel(Em1dConst c, E
     em1d_half_push<ORDER>(c, Esx, Esy, Bs, b.y[p], b.vx[p], b.vy[p], c.qm[s], b.err, vsx, vsy, yh);
     const Shape64<ORDER> S(__dmul_rn(yh, c.inv_h), n);
     const double qw = marker_qw(c, b, s, p);
-    S.deposit(Jt, qw * vsx);
-    S.deposit(Jt + n, qw * vsy);
+    tile_deposit<ORDER>(Jt, c.rt, S, qw * vsx, qw * vsy);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x)
-    if (Jt[i] != 0.0) atomicAdd(&b.J2[i], Jt[i]);
+  flush_tile(Jt, c.rt, b.J2, n);
   if (arrive_last(b.done)) {
     double2 *Z = (double2 *)sm;
-    field_advance(c, c.solver == 1 ? 1 : 2, c.dt, b.E, b.B, b.J2, b.En, b.Bn, b.Ea, b.Bh, Z, Z + n);
-    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) b.J1[i] = 0.0;
+    field_advance(c, c.solver == 2, c.dt, b.coef, b.tw, b.E, b.B, b.J2, b.En, b.Bn, b.Ea, b.Bh, Z);
+    for (int i = threadIdx.x; i < kJSlices * 2 * n; i += blockDim.x) b.J1[i] = 0.0;
   }
 }
 
@@ -273,7 +344,7 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_e_kernel(Em1dConst c, E
   __shared__ double red[33];
   const int n = c.n;
   double *Esx = sm, *Esy = sm + n, *Bs = sm + 2 * n;
-  double *Eax = sm + 3 * n, *Eay = sm + 4 * n, *Bh = sm + 5 * n, *Jt = sm + 6 * n;  // Jt [2][n]
+  double *Eax = sm + 3 * n, *Eay = sm + 4 * n, *Bh = sm + 5 * n, *Jt = sm + 6 * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     Esx[i] = b.Es[i];
     Esy[i] = b.Es[n + i];
@@ -281,9 +352,8 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_e_kernel(Em1dConst c, E
     Eax[i] = b.Ea[i];
     Eay[i] = b.Ea[n + i];
     Bh[i] = b.Bh[i];
-    Jt[i] = 0.0;
-    Jt[n + i] = 0.0;
   }
+  clear_tile(Jt, 2 * n * c.rt);
   __syncthreads();
   const double dt = c.dt, hdt = 0.5 * c.dt;
   double ke = 0.0;
@@ -320,8 +390,7 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_e_kernel(Em1dConst c, E
       const double ys = wrap_periodic(fma(hdt, v1y, y1), c.L, b.err);
       const Shape64<ORDER> S2(ys * c.inv_h, n);
       const double qw = marker_qw(c, b, s, p);
-      S2.deposit(Jt, qw * v1x);
-      S2.deposit(Jt + n, qw * v1y);
+      tile_deposit<ORDER>(Jt, c.rt, S2, qw * v1x, qw * v1y);
     }
   }
   if (!isfinite(ke)) atomicOr(b.err, kErrNonfinite);
@@ -330,9 +399,7 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_e_kernel(Em1dConst c, E
   const double kb = block_sum_d(ke, red);
   if (threadIdx.x == 0) b.ke_part[blockIdx.x] = kb;
   __syncthreads();
-  if (c.scheme == 2)
-    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x)
-      if (Jt[i] != 0.0) atomicAdd(&b.J1[i], Jt[i]);
+  if (c.scheme == 2) flush_tile(Jt, c.rt, b.J1, n);
   if (arrive_last(b.done + 1)) {
     // TE of the new state: KE from the block partials in block order, W_E + W_B
     double wf = 0.0;
@@ -340,16 +407,15 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_e_kernel(Em1dConst c, E
       const double ex = __ldcg(b.En + i), ey = __ldcg(b.En + n + i), bz = __ldcg(b.Bn + i);
       wf += 0.5 * c.h * (ex * ex + ey * ey) + 0.5 * c.c2 * c.h * bz * bz;
     }
-    const double wsum = block_sum_d(wf, red);
-    if (threadIdx.x == 0) {
-      double k = 0.0;
-      for (int i = 0; i < (int)gridDim.x; i++) k += __ldcg(b.ke_part + i);
-      b.te[slot] = k + wsum;
-    }
+    // the block partials, each thread a fixed stride of them, then a fixed-order
+    // block reduction: the same sum every step for the same partials
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) wf += __ldcg(b.ke_part + i);
+    const double tsum = block_sum_d(wf, red);
+    if (threadIdx.x == 0) b.te[slot] = tsum;
     double2 *Z = (double2 *)sm;
     if (c.scheme == 2) {
-      field_advance(c, c.solver == 1 ? 0 : 2, hdt, b.En, b.Bn, b.J1, b.Es, b.Bs, nullptr, nullptr,
-                    Z, Z + n);
+      field_advance(c, c.solver == 2, hdt, b.coef + kEm1Coef * (n / 2 + 1), b.tw, b.En, b.Bn,
+                    b.J1, b.Es, b.Bs, nullptr, nullptr, Z);
     } else {
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
         b.Es[i] = __ldcg(b.En + i);
@@ -357,7 +423,7 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_e_kernel(Em1dConst c, E
         b.Bs[i] = __ldcg(b.Bn + i);
       }
     }
-    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) b.J2[i] = 0.0;
+    for (int i = threadIdx.x; i < kJSlices * 2 * n; i += blockDim.x) b.J2[i] = 0.0;
   }
 }
 
@@ -365,14 +431,37 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_e_kernel(Em1dConst c, E
 template <int ORDER>
 __global__ void __launch_bounds__(kEm1Threads) em1d_deposit_initial_kernel(Em1dConst c,
                                                                             Em1dBufs b) {
+  extern __shared__ double sm[];
+  double *Jt = sm;
+  clear_tile(Jt, 2 * c.n * c.rt);
+  __syncthreads();
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n_total;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int s = species_of1(c, p);
     const double ys = wrap_periodic(fma(0.5 * c.dt, b.vy[p], b.y[p]), c.L, b.err);
     const Shape64<ORDER> S(ys * c.inv_h, c.n);
     const double qw = marker_qw(c, b, s, p);
-    S.deposit(b.J1, qw * b.vx[p]);
-    S.deposit(b.J1 + c.n, qw * b.vy[p]);
+    tile_deposit<ORDER>(Jt, c.rt, S, qw * b.vx[p], qw * b.vy[p]);
+  }
+  __syncthreads();
+  flush_tile(Jt, c.rt, b.J1, c.n);
+}
+
+// Twiddles tw[j] = exp(-2 pi i j / n), j < n/2, and the per-mode coefficients
+// of the full step over dt (coef[0 .. n/2]: Crank-Nicolson or PSATD) and of
+// the half step over dt/2 (coef[n/2 + 1 ..]: explicit Euler or PSATD); one
+// block, once per set-up.
+__global__ void em1d_tables_kernel(Em1dConst c, Em1dBufs b) {
+  const int n = c.n;
+  for (int j = threadIdx.x; j < n / 2; j += blockDim.x) {
+    double s, co;
+    sincospi(-2.0 * (double)j / (double)n, &s, &co);
+    b.tw[j] = make_double2(co, s);
+  }
+  for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
+    mode_coefficients(c, c.solver == 1 ? 1 : 2, c.dt, k, b.coef + kEm1Coef * k);
+    mode_coefficients(c, c.solver == 1 ? 0 : 2, 0.5 * c.dt, k,
+                      b.coef + kEm1Coef * (n / 2 + 1 + k));
   }
 }
 
@@ -381,8 +470,8 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_half_kernel(Em1dConst c, Em1
   extern __shared__ double sm[];
   double2 *Z = (double2 *)sm;
   if (c.scheme == 2) {
-    field_advance(c, c.solver == 1 ? 0 : 2, 0.5 * c.dt, b.E, b.B, b.J1, b.Es, b.Bs, nullptr,
-                  nullptr, Z, Z + c.n);
+    field_advance(c, c.solver == 2, 0.5 * c.dt, b.coef + kEm1Coef * (c.n / 2 + 1), b.tw, b.E,
+                  b.B, b.J1, b.Es, b.Bs, nullptr, nullptr, Z);
   } else {
     for (int i = threadIdx.x; i < c.n; i += blockDim.x) {
       b.Es[i] = b.E[i];
@@ -422,7 +511,11 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_energy_kernel(Em1dConst c, E
   }
 }
 
-size_t pass_smem(const Em1dConst &c) { return sizeof(double) * 8 * (size_t)c.n; }
+// the passes' tables and tile copies, or the field solve's 9n + 8 doubles
+size_t pass_smem(const Em1dConst &c) {
+  const size_t a = (6 + 2 * (size_t)c.rt) * c.n, f = 9 * (size_t)c.n + 8;
+  return sizeof(double) * (a > f ? a : f);
+}
 
 template <typename K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
@@ -431,6 +524,12 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 }
 
 }  // namespace
+
+int em1d_tile_copies(int n) {
+  int rt = 32;
+  while (rt > 1 && sizeof(double) * (6 + 2 * (size_t)rt) * n > kEm1TileBudget) rt >>= 1;
+  return rt;
+}
 
 __global__ void em1d_validate_kernel(const double *y, const double *vx, const double *vy,
                                      int64_t n, double L, unsigned *err) {
@@ -441,17 +540,21 @@ __global__ void em1d_validate_kernel(const double *y, const double *vx, const do
   }
 }
 
-cudaError_t em1d_prepare(const Em1dConst &c) {
+cudaError_t em1d_prepare(const Em1dConst &c, const Em1dBufs &b, cudaStream_t st) {
   const size_t sm = pass_smem(c);
   cudaError_t e = cudaSuccess;
   if (c.order == 1) {
     if ((e = allow_smem(em1d_pass_c_kernel<1>, sm))) return e;
     if ((e = allow_smem(em1d_pass_e_kernel<1>, sm))) return e;
+    if ((e = allow_smem(em1d_deposit_initial_kernel<1>, sm))) return e;
   } else {
     if ((e = allow_smem(em1d_pass_c_kernel<2>, sm))) return e;
     if ((e = allow_smem(em1d_pass_e_kernel<2>, sm))) return e;
+    if ((e = allow_smem(em1d_deposit_initial_kernel<2>, sm))) return e;
   }
-  return allow_smem(em1d_half_kernel, sm);
+  if ((e = allow_smem(em1d_half_kernel, sm))) return e;
+  em1d_tables_kernel<<<1, kEm1Threads, 0, st>>>(c, b);
+  return cudaGetLastError();
 }
 
 void em1d_pass_c(const Em1dConst &c, const Em1dBufs &b, LaunchShape lp, cudaStream_t st) {
@@ -472,13 +575,14 @@ void em1d_pass_e(const Em1dConst &c, const Em1dBufs &b, int slot, LaunchShape lp
 }
 
 void em1d_start(const Em1dConst &c, const Em1dBufs &b, LaunchShape lp, cudaStream_t st) {
+  const size_t sm = pass_smem(c);
   if (c.scheme == 2) {
     if (c.order == 1)
-      em1d_deposit_initial_kernel<1><<<lp.grid, kEm1Threads, 0, st>>>(c, b);
+      em1d_deposit_initial_kernel<1><<<lp.grid, kEm1Threads, sm, st>>>(c, b);
     else
-      em1d_deposit_initial_kernel<2><<<lp.grid, kEm1Threads, 0, st>>>(c, b);
+      em1d_deposit_initial_kernel<2><<<lp.grid, kEm1Threads, sm, st>>>(c, b);
   }
-  em1d_half_kernel<<<1, kEm1Threads, pass_smem(c), st>>>(c, b);
+  em1d_half_kernel<<<1, kEm1Threads, sm, st>>>(c, b);
 }
 
 void em1d_energy(const Em1dConst &c, const Em1dBufs &b, double *ke_out, double *wf,

@@ -677,8 +677,8 @@ int restart_em1d(pic_handle *h) {
   const int n = h->c1e.n;
   em1d_validate_kernel<<<h->le.grid, 256, 0, h->st>>>(b.y, b.vx, b.vy, h->N, h->c1e.L, b.err);
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaMemsetAsync(b.J1, 0, sizeof(double) * 2 * n, h->st));
-  CUDA_TRY(cudaMemsetAsync(b.J2, 0, sizeof(double) * 2 * n, h->st));
+  CUDA_TRY(cudaMemsetAsync(b.J1, 0, sizeof(double) * kJSlices * 2 * n, h->st));
+  CUDA_TRY(cudaMemsetAsync(b.J2, 0, sizeof(double) * kJSlices * 2 * n, h->st));
   CUDA_TRY(cudaMemsetAsync(b.done, 0, sizeof(unsigned) * 2, h->st));
   em1d_start(h->c1e, b, h->le, h->st);
   CUDA_TRY(cudaGetLastError());
@@ -699,6 +699,7 @@ int init_em1d(pic_handle *h, const pic_species *species, const double *E0, const
   c.solver = cfg.solver == PIC_SOLVER_CN_SPECTRAL ? 1 : 2;
   c.gamma_on = cfg.gamma_on;
   c.nsp = h->nsp;
+  c.rt = em1d_tile_copies(c.n);
   c.n_total = h->N;
   c.L = cfg.grid.L[0];
   c.h = c.L / c.n;
@@ -724,9 +725,12 @@ int init_em1d(pic_handle *h, const pic_species *species, const double *E0, const
     return rc;
   b.w = nullptr;
   if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;
-  double **e2[] = {&b.E, &b.En, &b.Es, &b.Ea, &b.J1, &b.J2};
+  double **e2[] = {&b.E, &b.En, &b.Es, &b.Ea};
   for (double **f : e2)
     if ((rc = h->alloc(f, 2 * n))) return rc;
+  if ((rc = h->alloc(&b.J1, kJSlices * 2 * n)) || (rc = h->alloc(&b.J2, kJSlices * 2 * n)) ||
+      (rc = h->alloc(&b.tw, n / 2)) || (rc = h->alloc(&b.coef, 2 * kEm1Coef * (n / 2 + 1))))
+    return rc;
   double **e1[] = {&b.B, &b.Bn, &b.Bs, &b.Bh};
   for (double **f : e1)
     if ((rc = h->alloc(f, n))) return rc;
@@ -738,7 +742,8 @@ int init_em1d(pic_handle *h, const pic_species *species, const double *E0, const
   h->b1.err = b.err;
   h->b1.fallback = b.fallback;
   h->b1.te = b.te;
-  CUDA_TRY(em1d_prepare(c));
+  CUDA_TRY(em1d_prepare(c, b, h->st));
+  h->launches += 1;
   CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(unsigned), h->st));
   for (int s = 0; s < h->nsp; s++) {
     const SpeciesInfo &S = h->sp[s];

@@ -145,6 +145,9 @@ struct Em2dBufs {
 // 1D2V electromagnetic path with a pseudospectral field solve (Crank-Nicolson
 // or PSATD), FP64; n a power of two in [4, kSpecMaxNodes].
 constexpr int kSpecMaxNodes = 1024;
+constexpr int kJSlices = 8;                  // slices of the global current (power of two)
+constexpr size_t kEm1TileBudget = 96 * 1024; // shared bytes for field tables + tile copies
+constexpr int kEm1Coef = 8;                  // per-mode field-advance coefficients
 
 struct Em1dConst {
   int n, log2n;
@@ -153,6 +156,7 @@ struct Em1dConst {
   int solver;       // 1 Crank-Nicolson, 2 PSATD
   int gamma_on;
   int nsp;
+  int rt;           // copies of the shared current tile (power of two, <= 32)
   int64_t n_total;
   double L, h, inv_h, dt, c, c2;
   int64_t sp_end[kMaxSpecies];
@@ -169,7 +173,9 @@ struct Em1dBufs {
   double *B, *Bn;            // Bz^n, Bz^{n+1}: [n]
   double *Es, *Bs;           // E*, B* of the half step
   double *Ea, *Bh;           // the E of v^dag (E^{n+1/2} or <E>) and B^{n+1/2}
-  double *J1, *J2;           // j^{n,*}, j^{*,n+1/2}: [2][n]
+  double *J1, *J2;           // j^{n,*}, j^{*,n+1/2}: [kJSlices][2][n], summed over slices
+  double2 *tw;               // [n/2] FFT twiddles exp(-2 pi i j / n)
+  double *coef;              // [2][n/2 + 1][kEm1Coef] per-mode coefficients, full and half step
   double *ke_part;           // [particle blocks]
   unsigned *done;            // [2] arrival counters of pass C and pass E
   unsigned long long *fallback;
@@ -253,7 +259,10 @@ __global__ void em2d_validate_kernel(const double *x, const double *y, const dou
                                      double Ly, unsigned *err);
 
 // 1D2V spectral path (em1d_spectral.cu)
-cudaError_t em1d_prepare(const Em1dConst &c);
+// shared-memory opt-in and the twiddle / coefficient tables (b.tw, b.coef)
+cudaError_t em1d_prepare(const Em1dConst &c, const Em1dBufs &b, cudaStream_t st);
+// copies of the shared current tile for n nodes
+int em1d_tile_copies(int n);
 void em1d_pass_c(const Em1dConst &c, const Em1dBufs &b, LaunchShape lp, cudaStream_t st);
 void em1d_pass_e(const Em1dConst &c, const Em1dBufs &b, int slot, LaunchShape lp, cudaStream_t st);
 // j^{0,*} (ESEC2 form) and the first E*, B*
