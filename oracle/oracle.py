@@ -104,6 +104,12 @@ def _declare(L):
     L.orc_em2d_step.restype = C.c_int
     L.orc_em2d_energy.argtypes = [C.POINTER(_EmCfg), C.POINTER(_Species2d), C.c_int, _dp, _dp,
                                   _dp, _dp, _dp]
+    L.orc_binomial_filter.argtypes = [C.c_long, _dp, _dp]
+    L.orc_std_field.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, C.c_int, _dp]
+    L.orc_std_start.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, C.c_int, _dp]
+    L.orc_std_step.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, C.c_int, _dp, _dp,
+                               _dp]
+    L.orc_std_step.restype = C.c_int
     L.orc_spectral_deriv.argtypes = [C.c_long, C.c_double, _dp, _dp]
     L.orc_em1d_field_advance.argtypes = [C.POINTER(_Em1Cfg), C.c_int, C.c_double, _dp, _dp, _dp,
                                          _dp, _dp, _dp]
@@ -238,6 +244,49 @@ def poisson_e0_1d(cfg: ES1DConfig, species: Sequence[Species]):
     E = np.zeros(cfg.nc)
     lib().orc_poisson_e0_1d(C.byref(cfg._c()), _sp_array(species), len(species), _ptr(E))
     return E
+
+
+# ----------------------------------------------------------------------------- standard PIC
+
+
+def binomial_filter(a: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    out = np.zeros_like(a)
+    lib().orc_binomial_filter(len(a), _ptr(a), _ptr(out))
+    return out
+
+
+def std_field(cfg: ES1DConfig, species: Sequence[Species], passes: int = 1) -> np.ndarray:
+    E = np.zeros(cfg.nc)
+    lib().orc_std_field(C.byref(cfg._c()), _sp_array(species), len(species), passes, _ptr(E))
+    return E
+
+
+def std_start(cfg: ES1DConfig, species: Sequence[Species], passes: int = 1) -> np.ndarray:
+    """E^0 of x^0; turns each species' v^0 into v^{-1/2} in place."""
+    E = np.zeros(cfg.nc)
+    lib().orc_std_start(C.byref(cfg._c()), _sp_array(species), len(species), passes, _ptr(E))
+    return E
+
+
+def std_step(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray, passes: int = 1):
+    """One leapfrog step in place; returns (KE per species, W_E) at the start time."""
+    ke = (C.c_double * len(species))()
+    we = C.c_double()
+    rc = lib().orc_std_step(C.byref(cfg._c()), _sp_array(species), len(species), passes, _ptr(E),
+                            ke, C.byref(we))
+    assert rc == 0
+    return list(ke), we.value
+
+
+def std_run(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray, nsteps: int,
+            passes: int = 1):
+    """nsteps leapfrog steps from a started state; TE[n] and W_E[n] of times 0..nsteps-1."""
+    te, we = np.zeros(nsteps), np.zeros(nsteps)
+    for k in range(nsteps):
+        ke, we[k] = std_step(cfg, species, E, passes)
+        te[k] = sum(ke) + we[k]
+    return te, we
 
 
 # ----------------------------------------------------------------------------- 2D3V

@@ -629,11 +629,14 @@ int orc_es1d_run(const orc_es1d_cfg *cfg, orc_species *sp, int nsp, double *E,
  * Plain O(N^2) transform.  Pinned: a single cosine density gives the exact
  * sine field; the discrete derivative of E reproduces rho - <rho>.
  */
-void orc_poisson_e0_1d(const orc_es1d_cfg *cfg, const orc_species *sp,
-                       int nsp, double *E) {
+static void poisson_spectral(long nc, double L, const double *rho, double *E);
+
+/* Charge density rho_h = (1/h) sum_p q w S(x_h - x_p) of the positions. */
+static void deposit_charge(const orc_es1d_cfg *cfg, const orc_species *sp, int nsp,
+                           double *rho) {
   long nc = cfg->nc;
-  double L = cfg->L, h = L / (double)nc;
-  double *rho = (double *)calloc((size_t)nc, sizeof(double));
+  double h = cfg->L / (double)nc;
+  for (long j = 0; j < nc; j++) rho[j] = 0.0;
   for (int s = 0; s < nsp; s++)
     for (long p = 0; p < sp[s].n; p++) {
       long idx[3];
@@ -642,6 +645,19 @@ void orc_poisson_e0_1d(const orc_es1d_cfg *cfg, const orc_species *sp,
       double c = sp[s].q * weight_of(&sp[s], p);
       for (int j = 0; j < k; j++) rho[idx[j]] += c * wt[j] / h;
     }
+}
+
+void orc_poisson_e0_1d(const orc_es1d_cfg *cfg, const orc_species *sp,
+                       int nsp, double *E) {
+  long nc = cfg->nc;
+  double *rho = (double *)calloc((size_t)nc, sizeof(double));
+  deposit_charge(cfg, sp, nsp, rho);
+  poisson_spectral(nc, cfg->L, rho, E);
+  free(rho);
+}
+
+/* E from dE/dx = rho - <rho> as above (k = 0 and the Nyquist mode zeroed). */
+static void poisson_spectral(long nc, double L, const double *rho, double *E) {
   const double twopi = 6.283185307179586476925286766559;
   for (long j = 0; j < nc; j++) E[j] = 0.0;
   for (long k = 1; k < nc; k++) {
@@ -661,7 +677,88 @@ void orc_poisson_e0_1d(const orc_es1d_cfg *cfg, const orc_species *sp,
       E[j] += (ere * cos(ang) - eim * sin(ang)) / (double)nc;
     }
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Standard explicit PIC, the comparator of Sec. 5                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The paper measures its schemes against Vlasov-Poisson PIC with the
+ * classical leapfrog push (in 1D1V the Boris push without B), with binomial
+ * filtering of the charge density.  State: x^n, v^{n-1/2} and E^n, the field
+ * of the filtered charge of x^n.  One step:
+ *   E^n_p     = sum_h E^n_h S(x_h - x_p^n)
+ *   v^{n+1/2} = v^{n-1/2} + dt (q/m) E^n_p
+ *   x^{n+1}   = x^n + dt v^{n+1/2}
+ *   rho^{n+1} = (1/h) sum q w S(x_h - x^{n+1}), `passes` times through the
+ *               1-2-1 filter, E^{n+1} from dE/dx = rho - <rho> (spectral)
+ * The energy at time n: KE^n = (1/2) m sum w (v^{n-1/2}^2 + v^{n+1/2}^2) / 2 and
+ * W_E^n = (h/2) sum (E^n)^2.  It is not conserved (that is the comparison).
+ */
+
+/* One pass of the binomial filter out_i = (in_{i-1} + 2 in_i + in_{i+1}) / 4,
+ * periodic; its factor on mode k is cos^2(pi k / nc), 0 on the Nyquist mode
+ * (pinned against that transfer function). */
+void orc_binomial_filter(long nc, const double *in, double *out) {
+  for (long i = 0; i < nc; i++)
+    out[i] = 0.25 * (in[imod(i - 1, nc)] + 2.0 * in[i] + in[imod(i + 1, nc)]);
+}
+
+/* E of the positions: charge, `passes` filter passes, spectral Gauss's law. */
+void orc_std_field(const orc_es1d_cfg *cfg, const orc_species *sp, int nsp, int passes,
+                   double *E) {
+  long nc = cfg->nc;
+  double *rho = (double *)calloc((size_t)nc, sizeof(double));
+  double *tmp = (double *)calloc((size_t)nc, sizeof(double));
+  deposit_charge(cfg, sp, nsp, rho);
+  for (int k = 0; k < passes; k++) {
+    orc_binomial_filter(nc, rho, tmp);
+    memcpy(rho, tmp, sizeof(double) * (size_t)nc);
+  }
+  poisson_spectral(nc, cfg->L, rho, E);
   free(rho);
+  free(tmp);
+}
+
+/* Start of the leapfrog from (x^0, v^0): E^0 of x^0 and the usual half kick
+ * back, v^{-1/2} = v^0 - dt/2 (q/m) E^0_p, in place in sp[].v. */
+void orc_std_start(const orc_es1d_cfg *cfg, orc_species *sp, int nsp, int passes, double *E) {
+  orc_std_field(cfg, sp, nsp, passes, E);
+  for (int s = 0; s < nsp; s++) {
+    double qm = sp[s].q / sp[s].m;
+    for (long p = 0; p < sp[s].n; p++) {
+      double Ep;
+      orc_gather_1d(cfg->order, cfg->nc, cfg->L, 1, &sp[s].x[p], E, &Ep);
+      sp[s].v[p] -= 0.5 * cfg->dt * qm * Ep;
+    }
+  }
+}
+
+/* One leapfrog step from (x^n, v^{n-1/2}, E^n) to (x^{n+1}, v^{n+1/2}, E^{n+1})
+ * in place; KE (per species) and WE receive the energies at time n. */
+int orc_std_step(const orc_es1d_cfg *cfg, orc_species *sp, int nsp, int passes, double *E,
+                 double *KE, double *WE) {
+  long nc = cfg->nc;
+  double dt = cfg->dt, h = cfg->L / (double)nc;
+  double we = 0.0;
+  for (long j = 0; j < nc; j++) we += E[j] * E[j];
+  *WE = 0.5 * h * we;
+  for (int s = 0; s < nsp; s++) {
+    double qm = sp[s].q / sp[s].m, acc = 0.0;
+    for (long p = 0; p < sp[s].n; p++) {
+      double Ep;
+      orc_gather_1d(cfg->order, nc, cfg->L, 1, &sp[s].x[p], E, &Ep);
+      double vold = sp[s].v[p];
+      double vnew = vold + dt * qm * Ep;
+      acc += weight_of(&sp[s], p) * 0.5 * (vold * vold + vnew * vnew);
+      sp[s].v[p] = vnew;
+      sp[s].x[p] = wrap(sp[s].x[p] + dt * vnew, cfg->L);
+    }
+    KE[s] = 0.5 * sp[s].m * acc;
+  }
+  orc_std_field(cfg, sp, nsp, passes, E);
+  return 0;
 }
 
 /* ------------------------------------------------------------------------ */
