@@ -40,18 +40,19 @@ L2_FLUSH_BYTES = 512 << 20          # > 2x the 126.5 MB L2
 ALGO_BYTES = {  # (form, kernel kind) -> bytes per marker
     ("fp64", 0): 16, ("fp64", 1): 32,
     ("mixed", 0): 16, ("mixed", 1): 28,
+    ("standard", 1): 32,     # the comparator's one pass reads and writes x, v
 }
 # The FP64 form is bound by the FP64 pipe (2 thread-instructions per SM and
 # clock on this part), not by HBM: its roofline counts FP64-pipe thread
 # instructions per marker, measured once with ncu
 # (sm__thread_inst_executed_pipe_fp64_pred_on.sum / markers) on these kernels.
-FP64_INST_PER_MARKER = {("fp64", 0): 53.5, ("fp64", 1): 115.7}
+FP64_INST_PER_MARKER = {("fp64", 0): 53.5, ("fp64", 1): 115.7, ("standard", 1): 45.39}
 FP64_LANES_PER_SM_CLK = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu capture of the current kernels on this workload (2^23 markers); None where
 # the kernel changed since it was taken.
 TRAFFIC = {("mixed", 0): 111929344, ("mixed", 1): 178150912,
-           ("fp64", 0): 155024384, ("fp64", 1): 226543872}
+           ("fp64", 0): 155024384, ("fp64", 1): 226543872, ("standard", 1): 207165440}
 
 
 def parse():
@@ -61,7 +62,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--markers", type=int, default=1 << 23)
-    ap.add_argument("--forms", default="mixed,fp64",
+    ap.add_argument("--forms", default="mixed,fp64,standard",
                     help="library forms to time; the first available is the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -193,10 +194,11 @@ def hbm_peak():
 
 def roofline(form, kname, k, markers, hbm_peak, hbm_src, clocks, nsm):
     """Roofline of the form's dominant kernel: HBM bytes for the mixed form, FP64-
-    pipe thread instructions for the FP64 form (achieved = algorithmic work per
-    launch / average event-timed launch duration)."""
+    pipe thread instructions for the FP64 form and the standard comparator
+    (achieved = algorithmic work per launch / average event-timed launch
+    duration)."""
     t = k["avg_us"] * 1e-6
-    if form == "fp64":
+    if form in ("fp64", "standard"):
         inst = FP64_INST_PER_MARKER[(form, k["kind"])] * markers
         mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
         peak = FP64_LANES_PER_SM_CLK * nsm * mhz * 1e6 / 1e9
@@ -224,9 +226,14 @@ def time_form(prob, precision_name: str, steps: int, warmup: int, profile_steps:
     dev = torch.device("cuda", torch.cuda.current_device())
     x_d = torch.from_numpy(s.x).to(dev)
     v_d = torch.from_numpy(s.v).to(dev)
+    # "standard": the comparison scheme of Sec. 5 (leapfrog Vlasov-Poisson, one
+    # binomial filter pass on the charge) on the same workload
+    std = precision_name == "standard"
     cfg = pic.make_config(prob.nc, prob.L, prob.dt, prob.order, pic.PIC_SCHEME_ESEC2, prec,
                           ptr_on_device=1, stream=stream.cuda_stream,
-                          sort_period=sort_period if precision_name == "mixed" else 0)
+                          sort_period=sort_period if precision_name == "mixed" else 0,
+                          solver=pic.PIC_SOLVER_STANDARD_LEAPFROG if std else
+                          pic.PIC_SOLVER_AMPERE_ES, binomial_passes=1 if std else 0)
     torch.cuda.synchronize()
     h = pic.pic_init(cfg, [dict(q=s.q, m=s.m, x=x_d, v=v_d, w=None, w0=s.w0)])
     del x_d, v_d

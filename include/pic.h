@@ -75,11 +75,23 @@ enum {
  * the analytic Fourier-space step of Eq. (PSATDformula) with the time-averaged
  * E in v^dag.  Both run the 1D2V geometry of the paper's Weibel test (see
  * Conventions) with a pseudospectral d/dy. */
+/* PIC_SOLVER_STANDARD_LEAPFROG: not the paper's method but the scheme it is
+ * measured against (Sec. 5): Vlasov-Poisson PIC with the leapfrog push and
+ * binomial_passes passes of the 1-2-1 filter on the charge, 1D1V, FP64.  Its
+ * state is x^n, v^{n-1/2} and E^n (the spectral Gauss's-law field of the
+ * filtered charge of x^n): pic_get_particles returns v^{n-1/2};
+ * pic_init and pic_set_particles take v^0 (v^n) and start the leapfrog with
+ * v^{-1/2} = v^0 - dt/2 (q/m) E^0_p; E0, B0 must be NULL and pic_set_fields is
+ * PIC_ERR_UNSUPPORTED (E follows from the charge).  Its energy at step n is
+ * (1/2) m sum w (v^{n-1/2}^2 + v^{n+1/2}^2) / 2 + (h/2) sum (E^n)^2, and it is
+ * not conserved: that is the comparison.  The scheme, gamma_on and
+ * remove_mean fields do not apply; its fallback counts are 0. */
 typedef enum {
   PIC_SOLVER_AMPERE_ES = 0,
   PIC_SOLVER_YEE_LEAPFROG = 1,
   PIC_SOLVER_CN_SPECTRAL = 2,
-  PIC_SOLVER_PSATD = 3
+  PIC_SOLVER_PSATD = 3,
+  PIC_SOLVER_STANDARD_LEAPFROG = 4
 } pic_solver;
 /* ESEC1: Eq. (naivetranslation) with the correction of Eq. (PICmodification);
  * ESEC2: Eq. (good_translation), one extra deposit per step, Gamma closer to 1. */
@@ -127,6 +139,8 @@ typedef struct {
   void *cuda_stream;        /* cudaStream_t or NULL                           */
   int skip_ids;             /* 1: do not carry marker ids through sorts       */
                             /* (pic_get_ids then fails); 0: keep them         */
+  int binomial_passes;      /* standard solver: 1-2-1 filter passes on the    */
+                            /* charge, 0..8; must be 0 for the other solvers  */
 } pic_config;
 
 typedef struct pic_handle pic_handle;

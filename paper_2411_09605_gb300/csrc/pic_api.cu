@@ -80,6 +80,12 @@ struct pic_handle {
   // 1D FP64 state (in the mixed form x, v serve as FP64 staging for get/set)
   Es1dConst c1{};
   Es1dFp64Bufs b1{};
+  // standard-PIC comparator state
+  bool stdp = false;
+  StdConst cs{};
+  StdBufs bs{};
+  LaunchShape lsd{1, 256};
+  double *std_part = nullptr;  // pic_energy's partials [nsp][lsd.grid] and W_E
   // 1D2V spectral state (Crank-Nicolson or PSATD field solve)
   bool em1 = false;
   Em1dConst c1e{};
@@ -671,6 +677,91 @@ int init_em2d(pic_handle *h, const pic_species *species, const double *E0, const
   return restart_em2d(h);
 }
 
+// Standard-PIC state change: validate markers, E^n from the charge and the
+// half kick back to v^{n-1/2} (the velocities given are v^n).
+int restart_std(pic_handle *h) {
+  StdBufs &b = h->bs;
+  validate_1d_kernel<<<h->lsd.grid, 256, 0, h->st>>>(b.x, b.v, h->N, h->cs.L, b.err);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(b.rho, 0, sizeof(double) * kJSlices * h->cs.n, h->st));
+  CUDA_TRY(cudaMemsetAsync(b.done, 0, sizeof(unsigned), h->st));
+  std_start(h->cs, b, h->lsd, h->st);
+  CUDA_TRY(cudaGetLastError());
+  h->launches += 3;
+  return check_flags(h, "pic_init/pic_set_*");
+}
+
+// Standard PIC, 1D1V: constants, SoA markers, tables, E^0 and v^{-1/2}.
+int init_std(pic_handle *h, const pic_species *species) {
+  const pic_config &cfg = h->cfg;
+  StdConst &c = h->cs;
+  StdBufs &b = h->bs;
+  c.n = (int)cfg.grid.n[0];
+  c.log2n = 0;
+  while ((1 << c.log2n) < c.n) c.log2n++;
+  c.order = cfg.shape_order;
+  c.nsp = h->nsp;
+  c.rt = std_tile_copies(c.n);
+  c.passes = cfg.binomial_passes;
+  c.n_total = h->N;
+  c.L = cfg.grid.L[0];
+  c.h = c.L / c.n;
+  c.inv_h = c.n / c.L;
+  c.dt = cfg.dt;
+  for (int s = 0; s < h->nsp; s++) {
+    const SpeciesInfo &S = h->sp[s];
+    c.sp_end[s] = S.offset + S.n;
+    c.qm[s] = S.q / S.m;
+    c.qw_h[s] = S.q * S.w0 / c.h;
+    c.q_h[s] = S.q / c.h;
+    c.w0[s] = S.w0;
+    c.half_m[s] = 0.5 * S.m;
+  }
+  for (int s = h->nsp; s < kMaxSpecies; s++) c.sp_end[s] = h->N;
+  h->lsd.block = 256;
+  h->lsd.grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->N + 255) / 256, (int64_t)h->nsm * 2));
+  const size_t n = (size_t)c.n;
+  int rc;
+  if ((rc = h->alloc(&b.x, h->N)) || (rc = h->alloc(&b.v, h->N))) return rc;
+  b.w = nullptr;
+  if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;
+  if ((rc = h->alloc(&b.E, n)) || (rc = h->alloc(&b.rho, kJSlices * n)) ||
+      (rc = h->alloc(&b.tw, n / 2)) || (rc = h->alloc(&b.g, n / 2 + 1)) ||
+      (rc = h->alloc(&b.ke_part, (size_t)h->lsd.grid)) || (rc = h->alloc(&b.done, 1)) ||
+      (rc = h->alloc(&b.fallback, kStepsCap)) || (rc = h->alloc(&b.te, kStepsCap)) ||
+      (rc = h->alloc(&b.err, 1)) || (rc = h->alloc(&h->ids, h->N)) ||
+      (rc = h->alloc(&h->std_part, (size_t)h->lsd.grid * h->nsp + 1)))
+    return rc;
+  h->b1.err = b.err;
+  h->b1.fallback = b.fallback;
+  h->b1.te = b.te;
+  CUDA_TRY(cudaMemsetAsync(b.err, 0, sizeof(unsigned), h->st));
+  CUDA_TRY(std_prepare(c, b, h->st));
+  h->launches += 1;
+  for (int s = 0; s < h->nsp; s++) {
+    const SpeciesInfo &S = h->sp[s];
+    const pic_species &in = species[s];
+    CUDA_TRY(cudaMemcpyAsync(b.x + S.offset, in.x, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaMemcpyAsync(b.v + S.offset, in.v, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+    if (h->weighted) {
+      if (in.w) {
+        CUDA_TRY(cudaMemcpyAsync(b.w + S.offset, in.w, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+      } else {
+        std::vector<double> tmp((size_t)S.n, S.w0);
+        CUDA_TRY(cudaMemcpyAsync(b.w + S.offset, tmp.data(), sizeof(double) * S.n,
+                                 cudaMemcpyHostToDevice, h->st));
+        CUDA_TRY(cudaStreamSynchronize(h->st));
+      }
+    }
+  }
+  std::vector<int64_t> ids((size_t)h->N);
+  for (int s = 0; s < h->nsp; s++)
+    for (int64_t p = 0; p < h->sp[s].n; p++) ids[(size_t)(h->sp[s].offset + p)] = p;
+  CUDA_TRY(cudaMemcpyAsync(h->ids, ids.data(), sizeof(int64_t) * h->N, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return restart_std(h);
+}
+
 // 1D2V spectral state change: validate markers, j^{n,*} and the half step.
 int restart_em1d(pic_handle *h) {
   Em1dBufs &b = h->b1e;
@@ -797,6 +888,8 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
   if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return fail(PIC_ERR_ARG, "pic_init: dt must be > 0");
   if (cfg->precision != PIC_PREC_FP64 && cfg->precision != PIC_PREC_MIXED)
     return fail(PIC_ERR_ARG, "pic_init: unknown precision");
+  if (cfg->solver != PIC_SOLVER_STANDARD_LEAPFROG && cfg->binomial_passes != 0)
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: binomial_passes is for the standard solver");
   if (cfg->solver == PIC_SOLVER_AMPERE_ES) {
     if (cfg->grid.dim_x != 1 || cfg->grid.dim_v != 1)
       return fail(PIC_ERR_ARG, "pic_init: the Ampere solver runs 1D1V (dim_x = dim_v = 1)");
@@ -804,6 +897,19 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
       return fail(PIC_ERR_ARG, "pic_init: 1D grid needs 4..%d nodes", kMaxNodes1D);
     if (!(cfg->grid.L[0] > 0.0)) return fail(PIC_ERR_ARG, "pic_init: L must be > 0");
     if (B0) return fail(PIC_ERR_ARG, "pic_init: B0 given for the electrostatic solver");
+  } else if (cfg->solver == PIC_SOLVER_STANDARD_LEAPFROG) {
+    if (cfg->grid.dim_x != 1 || cfg->grid.dim_v != 1)
+      return fail(PIC_ERR_ARG, "pic_init: the standard solver runs 1D1V (dim_x = dim_v = 1)");
+    const int64_t n = cfg->grid.n[0];
+    if (n < 4 || n > kStdMaxNodes || (n & (n - 1)))
+      return fail(PIC_ERR_ARG, "pic_init: the standard solver needs a power of two in [4, %d] nodes",
+                  kStdMaxNodes);
+    if (!(cfg->grid.L[0] > 0.0)) return fail(PIC_ERR_ARG, "pic_init: L must be > 0");
+    if (cfg->binomial_passes < 0 || cfg->binomial_passes > 8)
+      return fail(PIC_ERR_ARG, "pic_init: binomial_passes must be in [0, 8]");
+    if (E0 || B0) return fail(PIC_ERR_ARG, "pic_init: the standard solver takes E from the charge");
+    if (cfg->precision == PIC_PREC_MIXED)
+      return fail(PIC_ERR_UNSUPPORTED, "pic_init: the standard solver runs in the FP64 form");
   } else if (cfg->solver == PIC_SOLVER_CN_SPECTRAL || cfg->solver == PIC_SOLVER_PSATD) {
     if (cfg->grid.dim_x != 1 || cfg->grid.dim_v != 2)
       return fail(PIC_ERR_ARG, "pic_init: the spectral solvers run 1D2V (dim_x = 1, dim_v = 2)");
@@ -874,9 +980,11 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
   h->nsm = nsm;
   h->em = cfg->solver == PIC_SOLVER_YEE_LEAPFROG;
   h->em1 = cfg->solver == PIC_SOLVER_CN_SPECTRAL || cfg->solver == PIC_SOLVER_PSATD;
-  int rc = h->em    ? init_em2d(h, species, E0, B0)
-           : h->em1 ? init_em1d(h, species, E0, B0)
-                    : init_es1d(h, species, E0);
+  h->stdp = cfg->solver == PIC_SOLVER_STANDARD_LEAPFROG;
+  int rc = h->em     ? init_em2d(h, species, E0, B0)
+           : h->em1  ? init_em1d(h, species, E0, B0)
+           : h->stdp ? init_std(h, species)
+                     : init_es1d(h, species, E0);
   if (rc) {
     std::string msg = g_last_error;
     delete h;
@@ -896,6 +1004,13 @@ int pic_step_async(pic_handle *h, int nsteps) {
   Es1dFp64Bufs &b = h->b1;
   if (h->pending == 0 && nsteps > 0) {
     CUDA_TRY(cudaMemsetAsync(b.fallback, 0, sizeof(unsigned long long) * kStepsCap, h->st));
+  }
+  for (int k = 0; k < nsteps && h->stdp; k++) {
+    const int slot = h->pending;
+    CUDA_TRY(h->timed_launch(1, [&] { std_step(h->cs, h->bs, slot, h->lsd, h->st); }));
+    h->launches += 1;
+    h->steps_done++;
+    h->pending++;
   }
   for (int k = 0; k < nsteps && h->em1; k++) {
     Em1dBufs &e = h->b1e;
@@ -926,7 +1041,7 @@ int pic_step_async(pic_handle *h, int nsteps) {
     h->steps_done++;
     h->pending++;
   }
-  for (int k = 0; k < nsteps && !h->em && !h->em1; k++) {
+  for (int k = 0; k < nsteps && !h->em && !h->em1 && !h->stdp; k++) {
     if (h->mixed) {
       if (h->cm.mode == 1 && h->steps_done > 0 && h->steps_done % h->cfg.sort_period == 0) {
         int rc = sort_mixed(h);
@@ -967,7 +1082,7 @@ int pic_read_stats(pic_handle *h, int capacity, int64_t *nfallback_per_step, dou
   if ((nfallback_per_step || te_per_step) && capacity < n)
     return fail(PIC_ERR_ARG, "pic_read_stats: %d steps pending, capacity %d", n, capacity);
   Es1dFp64Bufs &b = h->b1;
-  if (!h->em && !h->em1) {
+  if (!h->em && !h->em1 && !h->stdp) {
     CUDA_TRY(h->timed_launch(2, [&] {
       if (h->mixed)
         es1d_mix_finalize(h->cm, h->bm, n - 1, h->lmix.grid, h->st);
@@ -1100,8 +1215,35 @@ static int energy_em1d(pic_handle *h, double *KE_per_species, double *W_E, doubl
   return PIC_OK;
 }
 
+static int energy_std(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, double *TE) {
+  const int nb = h->lsd.grid;
+  double *ke = h->std_part, *we = h->std_part + (size_t)nb * h->nsp;
+  std_energy(h->cs, h->bs, ke, we, h->lsd, h->st);
+  CUDA_TRY(cudaGetLastError());
+  h->launches += 1;
+  std::vector<double> part((size_t)nb * h->nsp + 1);
+  CUDA_TRY(cudaMemcpyAsync(part.data(), h->std_part, sizeof(double) * part.size(),
+                           cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  double te = 0.0;
+  for (int s = 0; s < h->nsp; s++) {
+    double k = 0.0;
+    for (int i = 0; i < nb; i++) k += part[(size_t)s * nb + i];
+    if (KE_per_species) KE_per_species[s] = k;
+    te += k;
+  }
+  const double wev = part[(size_t)nb * h->nsp];
+  te += wev;
+  if (W_E) *W_E = wev;
+  if (W_B) *W_B = 0.0;
+  if (TE) *TE = te;
+  if (!std::isfinite(te)) return fail(PIC_ERR_NONFINITE, "pic_energy: non-finite energy");
+  return PIC_OK;
+}
+
 int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, double *TE) {
   if (!h) return fail(PIC_ERR_ARG, "pic_energy: NULL handle");
+  if (h->stdp) return energy_std(h, KE_per_species, W_E, W_B, TE);
   if (h->em) return energy_em2d(h, KE_per_species, W_E, W_B, TE);
   if (h->em1) return energy_em1d(h, KE_per_species, W_E, W_B, TE);
   const Es1dConst &c = h->c1;
@@ -1146,6 +1288,14 @@ int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, 
 int pic_get_particles(pic_handle *h, int s, double *x, double *v) {
   if (!h || s < 0 || s >= h->nsp) return fail(PIC_ERR_ARG, "pic_get_particles: bad handle or species");
   const SpeciesInfo &S = h->sp[s];
+  if (h->stdp) {
+    if (x) CUDA_TRY(cudaMemcpyAsync(x, h->bs.x + S.offset, sizeof(double) * S.n, cudaMemcpyDefault,
+                                    h->st));
+    if (v) CUDA_TRY(cudaMemcpyAsync(v, h->bs.v + S.offset, sizeof(double) * S.n, cudaMemcpyDefault,
+                                    h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    return PIC_OK;
+  }
   if (h->em1) {
     if (x) CUDA_TRY(cudaMemcpyAsync(x, h->b1e.y + S.offset, sizeof(double) * S.n, cudaMemcpyDefault,
                                     h->st));
@@ -1192,6 +1342,16 @@ int pic_get_ids(pic_handle *h, int s, int64_t *ids) {
 int pic_set_particles(pic_handle *h, int s, const double *x, const double *v) {
   if (!h || s < 0 || s >= h->nsp || !x || !v) return fail(PIC_ERR_ARG, "pic_set_particles: bad arguments");
   const SpeciesInfo &S = h->sp[s];
+  if (h->stdp) {
+    CUDA_TRY(cudaMemcpyAsync(h->bs.x + S.offset, x, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaMemcpyAsync(h->bs.v + S.offset, v, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
+    std::vector<int64_t> ids((size_t)S.n);
+    for (int64_t p = 0; p < S.n; p++) ids[(size_t)p] = p;
+    CUDA_TRY(cudaMemcpyAsync(h->ids + S.offset, ids.data(), sizeof(int64_t) * S.n,
+                             cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    return restart_std(h);
+  }
   if (h->em1) {
     CUDA_TRY(cudaMemcpyAsync(h->b1e.y + S.offset, x, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
     CUDA_TRY(cudaMemcpyAsync(h->b1e.vx + S.offset, v, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
@@ -1231,6 +1391,12 @@ int pic_set_particles(pic_handle *h, int s, const double *x, const double *v) {
 
 int pic_get_fields(pic_handle *h, double *E, double *B) {
   if (!h) return fail(PIC_ERR_ARG, "pic_get_fields: NULL handle");
+  if (h->stdp) {
+    if (B) return fail(PIC_ERR_ARG, "pic_get_fields: B given for an electrostatic solver");
+    if (E) CUDA_TRY(cudaMemcpyAsync(E, h->bs.E, sizeof(double) * h->cs.n, cudaMemcpyDefault, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    return PIC_OK;
+  }
   if (h->em1) {
     const size_t n = (size_t)h->c1e.n;
     if (E) CUDA_TRY(cudaMemcpyAsync(E, h->b1e.E, sizeof(double) * 2 * n, cudaMemcpyDefault, h->st));
@@ -1255,6 +1421,9 @@ int pic_get_fields(pic_handle *h, double *E, double *B) {
 
 int pic_set_fields(pic_handle *h, const double *E, const double *B) {
   if (!h || !E) return fail(PIC_ERR_ARG, "pic_set_fields: bad arguments");
+  if (h->stdp)
+    return fail(PIC_ERR_UNSUPPORTED, "pic_set_fields: the standard solver's E follows from the "
+                                     "charge (Gauss's law)");
   if (h->em1) {
     if (!B) return fail(PIC_ERR_ARG, "pic_set_fields: the spectral solvers need Bz");
     const size_t n = (size_t)h->c1e.n;
@@ -1281,7 +1450,7 @@ int pic_set_fields(pic_handle *h, const double *E, const double *B) {
 int pic_grad_forward(pic_handle *h, int nsteps, int checkpoint_every) {
   if (!h || nsteps <= 0 || checkpoint_every <= 0)
     return fail(PIC_ERR_ARG, "pic_grad_forward: bad arguments");
-  if (h->em || h->em1 || h->mixed)
+  if (h->em || h->em1 || h->stdp || h->mixed)
     return fail(PIC_ERR_UNSUPPORTED, "pic_grad_forward: the reverse mode is built for the FP64 "
                                      "1D form");
   if (h->pending) return fail(PIC_ERR_ARG, "pic_grad_forward: read the pending stats first");

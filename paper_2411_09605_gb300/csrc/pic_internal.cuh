@@ -183,6 +183,39 @@ struct Em1dBufs {
   unsigned *err;
 };
 
+// Standard explicit PIC (the comparison scheme: leapfrog Vlasov-Poisson with a
+// binomially filtered charge), FP64 1D1V; n a power of two in [4, kStdMaxNodes].
+constexpr int kStdMaxNodes = 4096;
+
+struct StdConst {
+  int n, log2n;
+  int order;
+  int nsp;
+  int rt;           // copies of the shared charge tile (power of two, <= 32)
+  int passes;       // 1-2-1 filter passes on the charge
+  int64_t n_total;
+  double L, h, inv_h, dt;
+  int64_t sp_end[kMaxSpecies];
+  double qm[kMaxSpecies];
+  double qw_h[kMaxSpecies];
+  double q_h[kMaxSpecies];
+  double w0[kMaxSpecies];
+  double half_m[kMaxSpecies];
+};
+
+struct StdBufs {
+  double *x, *v, *w;     // x^n and v^{n-1/2} [N] (w may be null)
+  double *E;             // E^n [n]
+  double *rho;           // charge of the next positions [kJSlices][n]
+  double2 *tw;           // [n/2] FFT twiddles
+  double *g;             // [n/2 + 1] filter gain / |kk| per mode (0: k = 0, Nyquist)
+  double *ke_part;       // [particle blocks]
+  unsigned *done;        // arrival counter
+  unsigned long long *fallback;
+  double *te;
+  unsigned *err;
+};
+
 // Everything the 1D FP64 kernels touch.
 struct Es1dFp64Bufs {
   double *x, *v, *w;        // [N] SoA (w may be null)
@@ -257,6 +290,16 @@ void em2d_fp64_kinetic(const Em2dConst &c, const Em2dBufs &b, double *out, int n
 __global__ void em2d_validate_kernel(const double *x, const double *y, const double *vx,
                                      const double *vy, const double *vz, int64_t n, double Lx,
                                      double Ly, unsigned *err);
+
+// standard-PIC comparator (es1d_standard.cu)
+int std_tile_copies(int n);
+cudaError_t std_prepare(const StdConst &c, const StdBufs &b, cudaStream_t st);
+void std_step(const StdConst &c, const StdBufs &b, int slot, LaunchShape lp, cudaStream_t st);
+// E^0 from the charge of x^0, then v^{-1/2} = v^0 - dt/2 (q/m) E^0_p
+void std_start(const StdConst &c, const StdBufs &b, LaunchShape lp, cudaStream_t st);
+// KE^n partials ke_out [nsp][lp.grid] (v^{n+1/2} formed, not stored) and W_E^n
+void std_energy(const StdConst &c, const StdBufs &b, double *ke_out, double *we, LaunchShape lp,
+                cudaStream_t st);
 
 // 1D2V spectral path (em1d_spectral.cu)
 // shared-memory opt-in and the twiddle / coefficient tables (b.tw, b.coef)

@@ -23,6 +23,7 @@ PIC_OK = 0
 ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_OOM", -4: "PIC_ERR_NONFINITE",
           -5: "PIC_ERR_TIMEOUT", -6: "PIC_ERR_BOUNDS", -7: "PIC_ERR_UNSUPPORTED"}
 PIC_SOLVER_AMPERE_ES, PIC_SOLVER_YEE_LEAPFROG, PIC_SOLVER_CN_SPECTRAL, PIC_SOLVER_PSATD = 0, 1, 2, 3
+PIC_SOLVER_STANDARD_LEAPFROG = 4
 PIC_SCHEME_ESEC1, PIC_SCHEME_ESEC2 = 1, 2
 PIC_PREC_FP64, PIC_PREC_MIXED = 0, 1
 
@@ -58,7 +59,7 @@ class pic_config(C.Structure):
                 ("c", C.c_double), ("solver", C.c_int), ("scheme", C.c_int),
                 ("precision", C.c_int), ("sort_period", C.c_int), ("remove_mean", C.c_int),
                 ("gamma_on", C.c_int), ("ptr_on_device", C.c_int), ("cuda_stream", C.c_void_p),
-                ("skip_ids", C.c_int)]
+                ("skip_ids", C.c_int), ("binomial_passes", C.c_int)]
 
 
 _lib = None
@@ -136,10 +137,11 @@ def _addr(a) -> Optional[int]:
 def make_config(nc, L, dt, order=1, scheme=PIC_SCHEME_ESEC2, precision=PIC_PREC_FP64,
                 solver=PIC_SOLVER_AMPERE_ES, dim_x=1, dim_v=1, ny=0, Ly=0.0, c=1.0,
                 sort_period=0, remove_mean=1, gamma_on=1, ptr_on_device=0, stream=None,
-                skip_ids=0):
+                skip_ids=0, binomial_passes=0):
     g = pic_grid(dim_x, dim_v, (C.c_int64 * 2)(nc, ny), (C.c_double * 2)(L, Ly))
     return pic_config(g, order, dt, c, solver, scheme, precision, sort_period, int(remove_mean),
-                      int(gamma_on), int(ptr_on_device), stream, int(skip_ids))
+                      int(gamma_on), int(ptr_on_device), stream, int(skip_ids),
+                      int(binomial_passes))
 
 
 def pic_init(cfg: pic_config, species: Sequence[dict], E0=None, B0=None) -> int:
@@ -244,11 +246,15 @@ class Simulation:
     """Convenience owner of one handle built from a ``workloads.Problem1D``."""
 
     def __init__(self, prob, scheme=PIC_SCHEME_ESEC2, precision=PIC_PREC_FP64, E0=None,
-                 sort_period=0, remove_mean=True, gamma_on=True, stream=None):
+                 sort_period=0, remove_mean=True, gamma_on=True, stream=None,
+                 solver=PIC_SOLVER_AMPERE_ES, binomial_passes=0):
+        """solver PIC_SOLVER_STANDARD_LEAPFROG selects the standard-PIC comparator
+        (its particles() then returns v^{n-1/2})."""
         self.prob = prob
         self.cfg = make_config(prob.nc, prob.L, prob.dt, prob.order, scheme, precision,
                                sort_period=sort_period, remove_mean=remove_mean,
-                               gamma_on=gamma_on, stream=stream)
+                               gamma_on=gamma_on, stream=stream, solver=solver,
+                               binomial_passes=binomial_passes)
         self.species = [dict(q=s.q, m=s.m, x=np.ascontiguousarray(s.x, dtype=np.float64),
                              v=np.ascontiguousarray(s.v, dtype=np.float64),
                              w=None if s.w is None else np.ascontiguousarray(s.w, np.float64),

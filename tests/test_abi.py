@@ -53,7 +53,12 @@ def test_argument_errors_are_status_codes(lib):
         pic.make_config(2, 1.0, 0.1, solver=pic.PIC_SOLVER_CN_SPECTRAL, dim_v=2),
         pic.make_config(64, 1.0, 0.1, solver=pic.PIC_SOLVER_PSATD, dim_v=1),
         pic.make_config(64, 1.0, 0.1, solver=pic.PIC_SOLVER_PSATD, dim_v=2, c=0.0),
-        pic.make_config(64, 1.0, 0.1, solver=4, dim_v=2),
+        pic.make_config(64, 1.0, 0.1, solver=5, dim_v=2),
+        # standard comparator: 1D1V, a power of two in [4, 4096], 0..8 filter passes
+        pic.make_config(48, 1.0, 0.1, solver=pic.PIC_SOLVER_STANDARD_LEAPFROG),
+        pic.make_config(8192, 1.0, 0.1, solver=pic.PIC_SOLVER_STANDARD_LEAPFROG),
+        pic.make_config(64, 1.0, 0.1, solver=pic.PIC_SOLVER_STANDARD_LEAPFROG, binomial_passes=9),
+        pic.make_config(64, 1.0, 0.1, solver=pic.PIC_SOLVER_STANDARD_LEAPFROG, dim_v=2),
     ]
     for cfg in bad:
         with pytest.raises(pic.PicError) as ei:
@@ -66,6 +71,13 @@ def test_argument_errors_are_status_codes(lib):
         pic.pic_init(pic.make_config(64, 1.0, 0.1, precision=pic.PIC_PREC_MIXED,
                                      solver=pic.PIC_SOLVER_PSATD, dim_v=2), sp)
     assert ei.value.code == -7
+    with pytest.raises(pic.PicError) as ei:   # filter passes belong to the standard solver
+        pic.pic_init(pic.make_config(64, 1.0, 0.1, binomial_passes=1), sp)
+    assert ei.value.code == -7
+    with pytest.raises(pic.PicError) as ei:   # its field follows from the charge
+        pic.pic_init(pic.make_config(64, 1.0, 0.1, solver=pic.PIC_SOLVER_STANDARD_LEAPFROG), sp,
+                     np.zeros(64))
+    assert ei.value.code == -1
     assert lib.pic_step(None, 1, None, None) == -1
     lib.pic_free(None)  # no-op
 
