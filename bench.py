@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--sort-period", type=int, default=0,
                     help="cell sort of the mixed form every this many steps (0 = never)")
+    ap.add_argument("--weibel2d", action="store_true",
+                    help="time the 2D3V Yee/leapfrog path on the 128 x 128 Weibel workload "
+                         "instead (not the default line)")
     ap.add_argument("--weibel1d", action="store_true",
                     help="time the 1D2V electromagnetic path (Crank-Nicolson and PSATD field "
                          "solves) on the Weibel workload instead (not the default line)")
@@ -501,6 +504,96 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+# 2D3V Yee path: pass C reads x, y, vx, vy, vz; pass E reads and writes them
+EM2D_ALGO_BYTES = {0: 40, 1: 80}
+# FP64-pipe thread instructions per marker (ncu, 2^20 markers): bound by the FP64 pipe
+EM2D_FP64_INST_PER_MARKER = {0: 163.0, 1: 312.74}
+EM2D_TRAFFIC = {0: 43169536, 1: 43617792}   # dram read + write per launch
+
+
+def run_weibel2d(args):
+    """The 2D3V Weibel workload with the Yee/leapfrog field step (Sec. 4.1):
+    128 x 128 periodic cells, 64 markers per cell (1,048,576), bi-Maxwellian
+    with T_perp / T_par = 10, vth_par = 0.05 c, CFL 0.5, FP64, ESEC2 form."""
+    import torch
+    from paper_2411_09605_gb300 import build as B, pic, workloads as W
+    B.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()          # the handle uses the default stream
+    peak, peak_src = hbm_peak()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    prob = W.weibel()
+    sim = pic.Simulation2D(prob)
+    try:
+        te0 = sim.energy()[3]
+        pic.pic_step_async(sim.h, max(3, args.warmup))
+        pic.pic_read_stats(sim.h)
+        launches0 = pic.pic_launch_count(sim.h)
+        evs = []
+        with ClockSampler(0, enabled=not args.no_clocks) as clk:
+            for _ in range(args.steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pic.pic_step_async(sim.h, 1)
+                b.record(stream)
+                evs.append((a, b))
+            fb, te = pic.pic_read_stats(sim.h)
+            torch.cuda.synchronize()
+        launches = pic.pic_launch_count(sim.h) - launches0
+        step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+        pic.pic_set_profiling(sim.h, True)
+        for _ in range(args.profile_steps):
+            flush.zero_()
+            pic.pic_step_async(sim.h, 1)
+        pic.pic_read_stats(sim.h)
+        kern = {}
+        for kind, kname in ((0, "pass_c"), (1, "pass_e"), (2, "finalize"), (4, "field")):
+            n, tot = pic.pic_profile(sim.h, kind)
+            if n:
+                kern[kname] = {"launches": n, "avg_us": 1e3 * tot / n}
+        pic.pic_set_profiling(sim.h, False)
+    finally:
+        sim.close()
+    n = prob.n_markers
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    fp64_peak = FP64_LANES_PER_SM_CLK * nsm * 2070.0e6 / 1e9
+    for kind, kname in ((0, "pass_c"), (1, "pass_e")):
+        if kname in kern:
+            t = kern[kname]["avg_us"] * 1e-6
+            ach = EM2D_ALGO_BYTES[kind] * n / t / 1e9
+            kern[kname]["achieved_GBs"] = round(ach, 1)
+            kern[kname]["frac_hbm"] = round(ach / peak, 4)
+            kern[kname]["fp64_ginst_s"] = round(EM2D_FP64_INST_PER_MARKER[kind] * n / t / 1e9, 1)
+            kern[kname]["frac_fp64"] = round(kern[kname]["fp64_ginst_s"] / fp64_peak, 4)
+    dom = "pass_e" if "pass_e" in kern else "pass_c"
+    value = n * args.steps / (step_ms.sum() / 1e3)
+    line = {
+        "metric": "particle-steps/s, 2D3V Weibel with the Yee/leapfrog field step",
+        "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": float(step_ms.mean()),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded bi-Maxwellian markers)",
+        "config": {"workload": "weibel_2d3v_yee", "cells": [prob.nx, prob.ny],
+                   "markers": n, "dt": prob.dt, "c": prob.c, "scheme": "ESEC2",
+                   "shape_order": prob.order,
+                   "l2": "flushed (512 MiB write) before every timed step"},
+        "energy": {"max_rel_dTE": float(np.max(np.abs(te - te0)) / te0),
+                   "fallbacks": int(fb.sum())},
+        "gpu_launches": int(launches), "kernels": kern, "clocks": clk.summary(),
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": kern[dom]["fp64_ginst_s"],
+                     "peak": round(fp64_peak, 1), "unit": "Ginst/s (FP64 pipe)",
+                     "frac": kern[dom]["frac_fp64"],
+                     "traffic": EM2D_TRAFFIC[1 if dom == "pass_e" else 0],
+                     "peak_source": f"{FP64_LANES_PER_SM_CLK} FP64 lanes/SM/clk x SMs x 2070 MHz",
+                     "hbm_frac": kern[dom]["frac_hbm"], "hbm_peak": peak,
+                     "hbm_peak_source": peak_src},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # pass C reads y, vx, vy; pass E reads and writes them (v* is recomputed)
 EM1D_ALGO_BYTES = {0: 24, 1: 48}
 # FP64-pipe thread instructions per marker of the 1D2V passes (ncu,
@@ -752,6 +845,8 @@ def main():
         run_grad(args)
     elif args.weibel1d:
         run_weibel1d(args)
+    elif args.weibel2d:
+        run_weibel2d(args)
     else:
         run_ours(args)
 
