@@ -53,7 +53,8 @@ _lp = C.POINTER(C.c_long)
 
 class _EsCfg(C.Structure):
     _fields_ = [("nc", C.c_long), ("L", C.c_double), ("order", C.c_int), ("dt", C.c_double),
-                ("scheme", C.c_int), ("remove_mean", C.c_int), ("gamma_on", C.c_int)]
+                ("scheme", C.c_int), ("remove_mean", C.c_int), ("gamma_on", C.c_int),
+                ("passes", C.c_int)]
 
 
 class _Species(C.Structure):
@@ -139,10 +140,11 @@ class ES1DConfig:
     scheme: int = 2
     remove_mean: bool = True
     gamma_on: bool = True
+    passes: int = 0          # binomial filter passes inside the scheme
 
     def _c(self):
         return _EsCfg(self.nc, self.L, self.order, self.dt, self.scheme, int(self.remove_mean),
-                      int(self.gamma_on))
+                      int(self.gamma_on), int(self.passes))
 
 
 @dataclass

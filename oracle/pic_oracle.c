@@ -127,7 +127,22 @@ typedef struct {
                        Ampere form, Eq. ampere); 0: E -= dt J literally */
   int gamma_on;     /* 1: energy correction of Eq. opt_solution;
                        0: naive scheme, v^{n+1} = v^dagger (ablation) */
+  int passes;       /* binomial filter passes F inside the scheme: Ampere uses
+                       F j and the gathers F E (0: none) */
 } orc_es1d_cfg;
+
+void orc_binomial_filter(long nc, const double *in, double *out);
+
+/* a <- F^passes a (the 1-2-1 filter, periodic), in place */
+static void filter_passes(long nc, double *a, int passes) {
+  if (passes <= 0) return;
+  double *t = (double *)calloc((size_t)nc, sizeof(double));
+  for (int k = 0; k < passes; k++) {
+    orc_binomial_filter(nc, a, t);
+    memcpy(a, t, sizeof(double) * (size_t)nc);
+  }
+  free(t);
+}
 
 typedef struct {
   double q, m;
@@ -173,6 +188,11 @@ static void ampere_update(const orc_es1d_cfg *cfg, const double *Ein,
  *   If R < 0 (imaginary Gamma) or |v^dag| = 0, Gamma := 1 and the particle is
  *   counted (Sec. 3.2 and Sec. 5.1).
  *
+ * With cfg->passes > 0 the binomial filter F (Sec. 5: the paper filters to
+ * remove the Nyquist mode) enters energy-consistently: both Ampere updates use
+ * F j, and both gathers read F E* and F E^{n+1/2}.  F is symmetric, so
+ * sum_h E_h (F j)_h = sum_h (F E)_h j_h and the energy identity stays exact.
+ *
  * E is updated in place.  nfallback[s] receives the per-species count.
  * gamma_out: NULL or nsp pointers (each NULL or [n]) receiving Gamma (1 for
  * fallbacks).  Returns 0.
@@ -214,10 +234,12 @@ int orc_es1d_step(const orc_es1d_cfg *cfg, orc_species *sp, int nsp,
         double c = sp[s].q * weight_of(&sp[s], p) * sp[s].v[p];
         for (int j = 0; j < k; j++) J[idx[j]] += c * wt[j] / h;
       }
+    filter_passes(nc, J, cfg->passes);
     ampere_update(cfg, E, J, 0.5 * dt, Estar);
   } else {
     for (long i = 0; i < nc; i++) Estar[i] = E[i];
   }
+  filter_passes(nc, Estar, cfg->passes);   /* the gathered E* is F E* */
 
   /* v* from the field gathered at x*; then x^{n+1/2} */
   for (int s = 0; s < nsp; s++) {
@@ -243,8 +265,10 @@ int orc_es1d_step(const orc_es1d_cfg *cfg, orc_species *sp, int nsp,
       double c = sp[s].q * weight_of(&sp[s], p) * vs[s][p];
       for (int j = 0; j < k; j++) J[idx[j]] += c * wt[j] / h;
     }
+  filter_passes(nc, J, cfg->passes);
   ampere_update(cfg, E, J, dt, Enew);
   for (long i = 0; i < nc; i++) Ehalf[i] = 0.5 * (E[i] + Enew[i]);
+  filter_passes(nc, Ehalf, cfg->passes);   /* the gathered E^{n+1/2} is F E^{n+1/2} */
 
   /* v^dag, Gamma, v^{n+1}; x^{n+1} */
   for (int s = 0; s < nsp; s++) {
@@ -350,6 +374,7 @@ static void ampere_adjoint(const orc_es1d_cfg *cfg, const double *Eout_bar, doub
 int orc_es1d_grad(const orc_es1d_cfg *cfg, const orc_species *sp0, int nsp, const double *E0,
                   long nsteps, double *Ebar, double *const *xbar, double *const *vbar,
                   double *const *wbar) {
+  if (cfg->passes != 0) return -1;   /* the reverse mode is for the unfiltered scheme */
   long nc = cfg->nc;
   double L = cfg->L, dt = cfg->dt, h = L / (double)nc;
   /* forward, keeping every step's markers and field */
