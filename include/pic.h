@@ -139,8 +139,14 @@ typedef struct {
   void *cuda_stream;        /* cudaStream_t or NULL                           */
   int skip_ids;             /* 1: do not carry marker ids through sorts       */
                             /* (pic_get_ids then fails); 0: keep them         */
-  int binomial_passes;      /* standard solver: 1-2-1 filter passes on the    */
-                            /* charge, 0..8; must be 0 for the other solvers  */
+  int binomial_passes;      /* 1-2-1 filter passes, 0..8.  Standard solver: on */
+                            /* the charge.  Ampere solver, FP64 form: inside  */
+                            /* the scheme, energy-consistently (Ampere uses   */
+                            /* F j, the gathers F E; F is symmetric, so the   */
+                            /* energy identity stays exact), and the initial  */
+                            /* Gauss field is that of F rho.  Other solvers,  */
+                            /* the mixed form and the no-alloc entry point:   */
+                            /* must be 0.                                     */
 } pic_config;
 
 typedef struct pic_handle pic_handle;

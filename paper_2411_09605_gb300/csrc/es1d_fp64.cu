@@ -69,6 +69,48 @@ __device__ void build_estar(const Es1dConst &c, const double *E, const double *J
   }
 }
 
+// a <- F^passes a in shared memory (the 1-2-1 filter, periodic), ping-ponging
+// with tmp; returns the buffer that holds the result.
+__device__ double *smem_filter(double *a, double *tmp, int nc, int passes) {
+  for (int k = 0; k < passes; k++) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+      const int im = i == 0 ? nc - 1 : i - 1, ip = i + 1 == nc ? 0 : i + 1;
+      tmp[i] = 0.25 * (a[im] + 2.0 * a[i] + a[ip]);
+    }
+    double *t = a;
+    a = tmp;
+    tmp = t;
+  }
+  __syncthreads();
+  return a;
+}
+
+// With filtering: Es = F E*, E* = E^n - dt/2 (F J1 - <J1>) (ESEC2) or E^n;
+// T is nc doubles of scratch (the filter keeps the mean, <F J1> = <J1>).
+template <int SCHEME>
+__device__ void build_estar_filtered(const Es1dConst &c, const double *E, const double *J1,
+                                     double *Es, double *T, double *red) {
+  double *o = T;
+  if (SCHEME == 2) {
+    const double mean = c.remove_mean ? block_mean(J1, c.nc, red) : 0.0;
+    for (int i = threadIdx.x; i < c.nc; i += blockDim.x) T[i] = J1[i];
+    double *fj = smem_filter(T, Es, c.nc, c.passes);
+    o = fj == T ? Es : T;
+    const double hdt = 0.5 * c.dt;
+    for (int i = threadIdx.x; i < c.nc; i += blockDim.x) o[i] = E[i] - hdt * (fj[i] - mean);
+    double *r = smem_filter(o, fj, c.nc, c.passes);
+    if (r != Es)
+      for (int i = threadIdx.x; i < c.nc; i += blockDim.x) Es[i] = r[i];
+  } else {
+    for (int i = threadIdx.x; i < c.nc; i += blockDim.x) T[i] = E[i];
+    double *r = smem_filter(T, Es, c.nc, c.passes);
+    if (r != Es)
+      for (int i = threadIdx.x; i < c.nc; i += blockDim.x) Es[i] = r[i];
+  }
+  __syncthreads();
+}
+
 __device__ void flush_tile(const double *Jt, double *J, int nc) {
   for (int i = threadIdx.x; i < nc; i += blockDim.x) {
     double a = Jt[i];
@@ -95,7 +137,10 @@ __global__ void __launch_bounds__(512) pass_c_kernel(Es1dConst c, Es1dFp64Bufs b
   double *Es = sm;
   double *Jt = sm + c.nc;
   __shared__ double red[33];
-  build_estar<SCHEME>(c, b.E[par], b.J1[par], Es, red);
+  if (c.passes > 0)
+    build_estar_filtered<SCHEME>(c, b.E[par], b.J1[par], Es, Jt, red);
+  else
+    build_estar<SCHEME>(c, b.E[par], b.J1[par], Es, red);
   for (int i = threadIdx.x; i < c.nc; i += blockDim.x) Jt[i] = 0.0;
   if (blockIdx.x == 0) {
     if (SCHEME == 2)
@@ -129,17 +174,40 @@ __global__ void __launch_bounds__(512) pass_e_kernel(Es1dConst c, Es1dFp64Bufs b
   const double *J2 = b.J2[par];
   double mean2 = c.remove_mean ? block_mean(J2, c.nc, red) : 0.0;
   double we_loc = 0.0;
-  for (int i = threadIdx.x; i < c.nc; i += blockDim.x) {
-    double en = E[i] - c.dt * (J2[i] - mean2);
-    Eh[i] = 0.5 * (E[i] + en);
-    Jt[i] = 0.0;
-    if (blockIdx.x == 0) {
-      b.E[par ^ 1][i] = en;
-      b.J2[par ^ 1][i] = 0.0;
-      we_loc += en * en;
+  if (c.passes > 0) {
+    // E^{n+1} = E^n - dt (F J2 - <J2>) (the state, unfiltered), gather table
+    // F E^{n+1/2}; Jt and Eh serve as scratch before the tile is cleared
+    for (int i = threadIdx.x; i < c.nc; i += blockDim.x) Jt[i] = J2[i];
+    double *fj = smem_filter(Jt, Eh, c.nc, c.passes);
+    double *o = fj == Jt ? Eh : Jt;
+    for (int i = threadIdx.x; i < c.nc; i += blockDim.x) {
+      double en = E[i] - c.dt * (fj[i] - mean2);
+      o[i] = 0.5 * (E[i] + en);
+      if (blockIdx.x == 0) {
+        b.E[par ^ 1][i] = en;
+        b.J2[par ^ 1][i] = 0.0;
+        we_loc += en * en;
+      }
     }
+    double *r = smem_filter(o, fj, c.nc, c.passes);
+    if (r != Eh)
+      for (int i = threadIdx.x; i < c.nc; i += blockDim.x) Eh[i] = r[i];
+    __syncthreads();
+    build_estar_filtered<SCHEME>(c, E, b.J1[par], Es, Jt, red);
+    for (int i = threadIdx.x; i < c.nc; i += blockDim.x) Jt[i] = 0.0;
+  } else {
+    for (int i = threadIdx.x; i < c.nc; i += blockDim.x) {
+      double en = E[i] - c.dt * (J2[i] - mean2);
+      Eh[i] = 0.5 * (E[i] + en);
+      Jt[i] = 0.0;
+      if (blockIdx.x == 0) {
+        b.E[par ^ 1][i] = en;
+        b.J2[par ^ 1][i] = 0.0;
+        we_loc += en * en;
+      }
+    }
+    build_estar<SCHEME>(c, E, b.J1[par], Es, red);
   }
-  build_estar<SCHEME>(c, E, b.J1[par], Es, red);
   if (blockIdx.x == 0) {
     double t = block_sum(we_loc, red);
     if (threadIdx.x == 0) b.we[0] = 0.5 * c.h * t;

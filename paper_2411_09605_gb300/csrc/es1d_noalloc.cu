@@ -82,9 +82,10 @@ extern "C" int pic_es1d_step_noalloc(const pic_config *cfg, double q, double m, 
                                      int64_t *nfallback_per_step, double *te_per_step) {
   if (!cfg) return noalloc_fail(PIC_ERR_ARG, "pic_es1d_step_noalloc: cfg is NULL");
   if (cfg->solver != PIC_SOLVER_AMPERE_ES || cfg->grid.dim_x != 1 || cfg->grid.dim_v != 1 ||
-      cfg->precision != PIC_PREC_FP64)
+      cfg->precision != PIC_PREC_FP64 || cfg->binomial_passes != 0)
     return noalloc_fail(PIC_ERR_ARG,
-                        "pic_es1d_step_noalloc: needs the 1D1V Ampere solver in FP64 form");
+                        "pic_es1d_step_noalloc: needs the 1D1V Ampere solver in FP64 form, "
+                        "without filtering (binomial_passes = 0)");
   const int64_t nc = cfg->grid.n[0];
   if (nc < 4 || nc > kNoallocMaxNodes)
     return noalloc_fail(PIC_ERR_ARG, "pic_es1d_step_noalloc: grid must have 4..8192 nodes "

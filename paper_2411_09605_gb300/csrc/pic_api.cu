@@ -436,6 +436,7 @@ int init_es1d(pic_handle *h, const pic_species *species, const double *E0) {
   c.scheme = cfg.scheme;
   c.remove_mean = cfg.remove_mean;
   c.gamma_on = cfg.gamma_on;
+  c.passes = cfg.binomial_passes;
   c.nsp = h->nsp;
   c.n_total = h->N;
   c.L = cfg.grid.L[0];
@@ -511,9 +512,16 @@ int init_es1d(pic_handle *h, const pic_species *species, const double *E0) {
     double *rho = b.J2[1];  // scratch, cleared again below
     es1d_fp64_charge(c, b.x, b.w, rho, h->ls, h->st);
     CUDA_TRY(cudaGetLastError());
-    std::vector<double> r(nc), e;
+    std::vector<double> r(nc), e, t(nc);
     CUDA_TRY(cudaMemcpyAsync(r.data(), rho, sizeof(double) * nc, cudaMemcpyDeviceToHost, h->st));
     CUDA_TRY(cudaStreamSynchronize(h->st));
+    // with filtering inside the scheme, Gauss's law of the filtered charge
+    // (the field the filtered Ampere updates keep consistent)
+    for (int k = 0; k < c.passes; k++) {
+      for (int i = 0; i < nc; i++)
+        t[i] = 0.25 * (r[(i + nc - 1) % nc] + 2.0 * r[i] + r[(i + 1) % nc]);
+      r.swap(t);
+    }
     poisson_1d_host(r, c.L, e);
     CUDA_TRY(cudaMemcpyAsync(b.E[0], e.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, h->st));
     CUDA_TRY(cudaMemsetAsync(rho, 0, sizeof(double) * nc, h->st));
@@ -888,8 +896,13 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
   if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return fail(PIC_ERR_ARG, "pic_init: dt must be > 0");
   if (cfg->precision != PIC_PREC_FP64 && cfg->precision != PIC_PREC_MIXED)
     return fail(PIC_ERR_ARG, "pic_init: unknown precision");
-  if (cfg->solver != PIC_SOLVER_STANDARD_LEAPFROG && cfg->binomial_passes != 0)
-    return fail(PIC_ERR_UNSUPPORTED, "pic_init: binomial_passes is for the standard solver");
+  if (cfg->binomial_passes < 0 || cfg->binomial_passes > 8)
+    return fail(PIC_ERR_ARG, "pic_init: binomial_passes must be in [0, 8]");
+  if (cfg->binomial_passes != 0 &&
+      !(cfg->solver == PIC_SOLVER_STANDARD_LEAPFROG ||
+        (cfg->solver == PIC_SOLVER_AMPERE_ES && cfg->precision == PIC_PREC_FP64)))
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: binomial_passes is for the standard solver and "
+                                     "the FP64 form of the Ampere solver");
   if (cfg->solver == PIC_SOLVER_AMPERE_ES) {
     if (cfg->grid.dim_x != 1 || cfg->grid.dim_v != 1)
       return fail(PIC_ERR_ARG, "pic_init: the Ampere solver runs 1D1V (dim_x = dim_v = 1)");
@@ -1450,7 +1463,7 @@ int pic_set_fields(pic_handle *h, const double *E, const double *B) {
 int pic_grad_forward(pic_handle *h, int nsteps, int checkpoint_every) {
   if (!h || nsteps <= 0 || checkpoint_every <= 0)
     return fail(PIC_ERR_ARG, "pic_grad_forward: bad arguments");
-  if (h->em || h->em1 || h->stdp || h->mixed)
+  if (h->em || h->em1 || h->stdp || h->mixed || h->c1.passes != 0)
     return fail(PIC_ERR_UNSUPPORTED, "pic_grad_forward: the reverse mode is built for the FP64 "
                                      "1D form");
   if (h->pending) return fail(PIC_ERR_ARG, "pic_grad_forward: read the pending stats first");

@@ -33,6 +33,7 @@ struct Es1dConst {
   int scheme;
   int remove_mean;
   int gamma_on;
+  int passes;     // binomial filter passes inside the scheme (FP64 form): F j, F E
   int nsp;
   int64_t n_total;
   double L, h, inv_h, dt;

@@ -71,9 +71,13 @@ def test_argument_errors_are_status_codes(lib):
         pic.pic_init(pic.make_config(64, 1.0, 0.1, precision=pic.PIC_PREC_MIXED,
                                      solver=pic.PIC_SOLVER_PSATD, dim_v=2), sp)
     assert ei.value.code == -7
-    with pytest.raises(pic.PicError) as ei:   # filter passes belong to the standard solver
-        pic.pic_init(pic.make_config(64, 1.0, 0.1, binomial_passes=1), sp)
+    with pytest.raises(pic.PicError) as ei:   # no filtering in the mixed form
+        pic.pic_init(pic.make_config(64, 1.0, 0.1, binomial_passes=1,
+                                     precision=pic.PIC_PREC_MIXED), sp)
     assert ei.value.code == -7
+    with pytest.raises(pic.PicError) as ei:
+        pic.pic_init(pic.make_config(64, 1.0, 0.1, binomial_passes=9), sp)
+    assert ei.value.code == -1
     with pytest.raises(pic.PicError) as ei:   # its field follows from the charge
         pic.pic_init(pic.make_config(64, 1.0, 0.1, solver=pic.PIC_SOLVER_STANDARD_LEAPFROG), sp,
                      np.zeros(64))
