@@ -42,6 +42,13 @@ int fail(int code, const char *fmt, ...) {
 constexpr int kStepsCap = 1024;  // per-step stats slots per chunk of pic_step
 constexpr int kProfKinds = 8;    // 0 pass C, 1 pass E, 2 stats finalize, 3 sort, 4 field
 
+// ids[p] = p for one species' slots (marker ids after pic_set_particles).
+__global__ void iota_ids_kernel(int64_t *ids, int64_t n) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x)
+    ids[p] = p;
+}
+
 // Validates positions in [0, L) and finite velocities of a 1D state.
 __global__ void validate_1d_kernel(const double *x, const double *v, int64_t n, double L,
                                    unsigned *err) {
@@ -177,6 +184,15 @@ struct pic_handle {
 };
 
 namespace {
+
+// Marker ids 0..n-1 of species S, set on the device (no host array).
+cudaError_t reset_ids(pic_handle *h, const SpeciesInfo &S) {
+  if (S.n == 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((S.n + 255) / 256, 4096);
+  iota_ids_kernel<<<grid, 256, 0, h->st>>>(h->ids + S.offset, S.n);
+  h->launches += 1;
+  return cudaGetLastError();
+}
 
 int check_flags(pic_handle *h, const char *where) {
   unsigned flags = 0;
@@ -1358,11 +1374,7 @@ int pic_set_particles(pic_handle *h, int s, const double *x, const double *v) {
   if (h->stdp) {
     CUDA_TRY(cudaMemcpyAsync(h->bs.x + S.offset, x, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
     CUDA_TRY(cudaMemcpyAsync(h->bs.v + S.offset, v, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
-    std::vector<int64_t> ids((size_t)S.n);
-    for (int64_t p = 0; p < S.n; p++) ids[(size_t)p] = p;
-    CUDA_TRY(cudaMemcpyAsync(h->ids + S.offset, ids.data(), sizeof(int64_t) * S.n,
-                             cudaMemcpyHostToDevice, h->st));
-    CUDA_TRY(cudaStreamSynchronize(h->st));
+    CUDA_TRY(reset_ids(h, S));
     return restart_std(h);
   }
   if (h->em1) {
@@ -1370,11 +1382,7 @@ int pic_set_particles(pic_handle *h, int s, const double *x, const double *v) {
     CUDA_TRY(cudaMemcpyAsync(h->b1e.vx + S.offset, v, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
     CUDA_TRY(cudaMemcpyAsync(h->b1e.vy + S.offset, v + S.n, sizeof(double) * S.n, cudaMemcpyDefault,
                              h->st));
-    std::vector<int64_t> ids((size_t)S.n);
-    for (int64_t p = 0; p < S.n; p++) ids[(size_t)p] = p;
-    CUDA_TRY(cudaMemcpyAsync(h->ids + S.offset, ids.data(), sizeof(int64_t) * S.n,
-                             cudaMemcpyHostToDevice, h->st));
-    CUDA_TRY(cudaStreamSynchronize(h->st));
+    CUDA_TRY(reset_ids(h, S));
     return restart_em1d(h);
   }
   if (h->em) {
@@ -1385,20 +1393,12 @@ int pic_set_particles(pic_handle *h, int s, const double *x, const double *v) {
     for (int d = 0; d < 3; d++)
       CUDA_TRY(cudaMemcpyAsync(dst[2 + d] + S.offset, v + d * S.n, sizeof(double) * S.n,
                                cudaMemcpyDefault, h->st));
-    std::vector<int64_t> ids((size_t)S.n);
-    for (int64_t p = 0; p < S.n; p++) ids[(size_t)p] = p;
-    CUDA_TRY(cudaMemcpyAsync(h->ids + S.offset, ids.data(), sizeof(int64_t) * S.n,
-                             cudaMemcpyHostToDevice, h->st));
-    CUDA_TRY(cudaStreamSynchronize(h->st));
+    CUDA_TRY(reset_ids(h, S));
     return restart_em2d(h);
   }
   CUDA_TRY(cudaMemcpyAsync(h->b1.x + S.offset, x, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
   CUDA_TRY(cudaMemcpyAsync(h->b1.v + S.offset, v, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
-  std::vector<int64_t> ids((size_t)S.n);
-  for (int64_t p = 0; p < S.n; p++) ids[(size_t)p] = p;
-  CUDA_TRY(cudaMemcpyAsync(h->ids + S.offset, ids.data(), sizeof(int64_t) * S.n,
-                           cudaMemcpyHostToDevice, h->st));
-  CUDA_TRY(cudaStreamSynchronize(h->st));
+  CUDA_TRY(reset_ids(h, S));
   return restart_es1d(h, true);
 }
 
