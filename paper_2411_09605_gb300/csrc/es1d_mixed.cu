@@ -868,6 +868,33 @@ __global__ void __launch_bounds__(512) mix_deposit_initial_kernel(Es1dMixConst c
   flush_tile_i64<ORDER>(Jt, PSEL(b.J1, par), c.nc, kJStride, b.Jtot + par);
 }
 
+// The same j^{n,*} for the wide layout (nc <= kWideMaxNodes, unsorted): 1024-thread
+// blocks of the passes' launch, each lane adding into its own copy of the split
+// tile; the per-copy marker count stays within the bound the rounding shift is
+// chosen for (a thread takes at most 4 markers per trip of the passes), and the
+// integer totals equal the single-tile kernel's.
+template <int ORDER>
+__global__ void __launch_bounds__(1024, 1)
+    mix_deposit_initial_wide_kernel(Es1dMixConst c, Es1dMixBufs b, int par) {
+  constexpr int RT = 32;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned *Jt = (unsigned *)smraw;  // [npad][2][RT]
+  const int npad = npad_of(c.nc);
+  clear_tile<RT>(Jt, npad);
+  __syncthreads();
+  unsigned *Jl = Jt + (threadIdx.x & (RT - 1));
+  unsigned bad = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int Vn = to_fixed(b.vh[p], bad);
+    const ShapeMix<ORDER> S(b.X[p] + half_shift(Vn, c), c.nc);
+    deposit_direct<ORDER, RT>(Jl, S, Vn, c);
+  }
+  if (bad) atomicOr(b.err, bad);
+  __syncthreads();
+  flush_tile<ORDER, RT>(Jt, PSEL(b.J1, par), b.Jtot + par, c.nc);
+}
+
 // Charge of the markers for the initial Poisson solve: the integer weights
 // summed exactly per node (order independent), in units of 2^-23.
 template <int ORDER>
@@ -1156,6 +1183,10 @@ cudaError_t es1d_mix_prepare(const Es1dMixConst &c) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mix_charge_kernel<ORDER>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * npad_host(c)));
+    if (e == cudaSuccess && c.wide)
+      e = cudaFuncSetAttribute(mix_deposit_initial_wide_kernel<ORDER>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(2 * 32 * 4 * npad_host(c)));
   });
   return e;
 }
@@ -1203,6 +1234,14 @@ void es1d_mix_pass_e(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_i
 
 void es1d_mix_deposit_initial(const Es1dMixConst &c, const Es1dMixBufs &b, int parity,
                               LaunchShape ls, cudaStream_t st) {
+  if (c.wide && ls.block == 1024) {
+    const size_t smw = 2 * 32 * 4 * npad_host(c);
+    if (c.order == 1)
+      mix_deposit_initial_wide_kernel<1><<<ls.grid, 1024, smw, st>>>(c, b, parity);
+    else
+      mix_deposit_initial_wide_kernel<2><<<ls.grid, 1024, smw, st>>>(c, b, parity);
+    return;
+  }
   const size_t sm = 8 * npad_host(c);
   if (c.order == 1)
     mix_deposit_initial_kernel<1><<<ls.grid, 512, sm, st>>>(c, b, parity);

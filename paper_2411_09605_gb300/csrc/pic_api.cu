@@ -437,7 +437,7 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   wire_sorted_output(h);
   es1d_mix_set_ek(m, bm, (int)(h->steps_done & 1), h->st);
   if (m.scheme == 2) {
-    es1d_mix_deposit_initial(m, bm, (int)(h->steps_done & 1), h->ls, h->st);
+    es1d_mix_deposit_initial(m, bm, (int)(h->steps_done & 1), m.wide ? h->lmix : h->ls, h->st);
     CUDA_TRY(cudaGetLastError());
   }
   return PIC_OK;
@@ -584,7 +584,8 @@ int restart_es1d(pic_handle *h, bool particles_changed) {
     // the FP64 staging arrays hold the new markers only after pic_set_particles
     if (particles_changed) es1d_mix_from_fp64(h->cm, b.x, b.v, bm, h->ls, h->st);
     es1d_mix_set_ek(h->cm, bm, par, h->st);
-    if (h->cm.scheme == 2) es1d_mix_deposit_initial(h->cm, bm, par, h->ls, h->st);
+    if (h->cm.scheme == 2)
+      es1d_mix_deposit_initial(h->cm, bm, par, h->cm.wide ? h->lmix : h->ls, h->st);
     CUDA_TRY(cudaGetLastError());
     return check_flags(h, "pic_set_*");
   }
