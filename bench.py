@@ -34,11 +34,11 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20          # > 2x the 126.5 MB L2
 # Algorithmic bytes per marker per launch: the state that must cross HBM once per
-# barrier-separated pass.  FP64 form: pass C reads x, v; pass E reads and writes
-# them (v* is recomputed).  Mixed form: pass C reads X, vh, vl and writes the
-# integer V*; pass E reads X, vh, vl, V* and writes X, vh, vl.
+# barrier-separated pass.  FP64 form: pass C reads x, v and writes v*; pass E
+# reads x, v, v* and writes x, v.  Mixed form: pass C reads X, vh, vl and writes
+# the integer V*; pass E reads X, vh, vl, V* and writes X, vh, vl.
 ALGO_BYTES = {  # (form, kernel kind) -> bytes per marker
-    ("fp64", 0): 16, ("fp64", 1): 32,
+    ("fp64", 0): 24, ("fp64", 1): 40,    # pass C also writes v*, pass E reads it
     ("mixed", 0): 16, ("mixed", 1): 28,
     ("standard", 1): 32,     # the comparator's one pass reads and writes x, v
 }
@@ -46,13 +46,13 @@ ALGO_BYTES = {  # (form, kernel kind) -> bytes per marker
 # clock on this part), not by HBM: its roofline counts FP64-pipe thread
 # instructions per marker, measured once with ncu
 # (sm__thread_inst_executed_pipe_fp64_pred_on.sum / markers) on these kernels.
-FP64_INST_PER_MARKER = {("fp64", 0): 53.5, ("fp64", 1): 115.7, ("standard", 1): 45.39}
+FP64_INST_PER_MARKER = {("fp64", 0): 53.5, ("fp64", 1): 92.75, ("standard", 1): 45.39}
 FP64_LANES_PER_SM_CLK = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu capture of the current kernels on this workload (2^23 markers); None where
 # the kernel changed since it was taken.
 TRAFFIC = {("mixed", 0): 111929344, ("mixed", 1): 178150912,
-           ("fp64", 0): 155024384, ("fp64", 1): 226543872, ("standard", 1): 207165440}
+           ("fp64", 0): None, ("fp64", 1): 304729600, ("standard", 1): 207165440}
 
 
 def parse():
@@ -504,11 +504,12 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
-# 2D3V Yee path: pass C reads x, y, vx, vy, vz; pass E reads and writes them
-EM2D_ALGO_BYTES = {0: 40, 1: 80}
+# 2D3V Yee path: pass C reads x, y, vx, vy, vz and writes v*; pass E reads them
+# and v*, and writes x, y, v
+EM2D_ALGO_BYTES = {0: 64, 1: 104}          # pass C also writes v*, pass E reads it
 # FP64-pipe thread instructions per marker (ncu, 2^20 markers): bound by the FP64 pipe
-EM2D_FP64_INST_PER_MARKER = {0: 163.0, 1: 312.74}
-EM2D_TRAFFIC = {0: 43169536, 1: 43617792}   # dram read + write per launch
+EM2D_FP64_INST_PER_MARKER = {0: 163.0, 1: 205.89}
+EM2D_TRAFFIC = {0: None, 1: 68729856}     # dram read + write per launch
 
 
 def run_weibel2d(args):
@@ -594,14 +595,14 @@ def run_weibel2d(args):
     print(json.dumps(line), flush=True)
 
 
-# pass C reads y, vx, vy; pass E reads and writes them (v* is recomputed)
-EM1D_ALGO_BYTES = {0: 24, 1: 48}
+# pass C reads y, vx, vy and writes v*; pass E reads them and v*, writes y, vx, vy
+EM1D_ALGO_BYTES = {0: 40, 1: 64}          # pass C also writes v*, pass E reads it
 # FP64-pipe thread instructions per marker of the 1D2V passes (ncu,
 # sm__thread_inst_executed_pipe_fp64_pred_on.sum / markers at 2^23 markers):
 # like the FP64 1D form these passes are bound by the FP64 pipe, not by HBM
-EM1D_FP64_INST_PER_MARKER = {0: 54.45, 1: 120.34}
+EM1D_FP64_INST_PER_MARKER = {0: 54.45, 1: 85.35}
 # DRAM bytes per launch at 2^23 markers (dram__bytes_read.sum + dram__bytes_write.sum)
-EM1D_TRAFFIC = {0: 204952064, 1: 341139456}
+EM1D_TRAFFIC = {0: None, 1: 487232768}
 
 
 def run_weibel1d(args):

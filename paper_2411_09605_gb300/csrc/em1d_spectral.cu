@@ -16,7 +16,8 @@
 //           does the full field step: (E^{n+1}, B^{n+1}) by Crank-Nicolson or
 //           PSATD over dt with j^{*,n+1/2}, the E that v^dag uses (E^{n+1/2},
 //           or PSATD's time average <E>) and B^{n+1/2} = (B^n + B^{n+1})/2.
-//   pass E  every block: the same v*, y^{n+1/2} recomputed bit for bit, the
+//   pass E  every block: v* as pass C stored it and y^{n+1/2} formed with the
+//           same rounding (cheaper than recomputing on the FP64 pipe), the
 //           gather of that E and B^{n+1/2}, v^dag, Gamma (Eq. opt_solution;
 //           fallback counted), y^{n+1}, v^{n+1}, the kinetic-energy partial and
 //           (ESEC2 form) the deposit of j^{n+1,*} at y^{n+1} + dt/2 vy^{n+1}.
@@ -261,6 +262,8 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_c_kernel(Em1dConst c, E
     const int s = species_of1(c, p);
     double vsx, vsy, yh;
     em1d_half_push<ORDER>(c, Esx, Esy, Bs, b.y[p], b.vx[p], b.vy[p], c.qm[s], b.err, vsx, vsy, yh);
+    b.vsx[p] = vsx;   // pass E forms y^{n+1/2} from v* with the same rounding
+    b.vsy[p] = vsy;
     const Shape64<ORDER> S(__dmul_rn(yh, c.inv_h), n);
     const double qw = marker_qw(c, b, s, p);
     tile_deposit<ORDER>(Jt, c.rt, S, qw * vsx, qw * vsy);
@@ -300,8 +303,8 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_e_kernel(Em1dConst c, E
     const int s = species_of1(c, p);
     const double qm = c.qm[s];
     const double y = b.y[p], vx = b.vx[p], vy = b.vy[p];
-    double vsx, vsy, yh;
-    em1d_half_push<ORDER>(c, Esx, Esy, Bs, y, vx, vy, qm, b.err, vsx, vsy, yh);
+    const double vsx = b.vsx[p], vsy = b.vsy[p];
+    const double yh = wrap_periodic(__fma_rn(hdt, vsy, y), c.L, b.err);
     const Shape64<ORDER> S(__dmul_rn(yh, c.inv_h), n);
     const double ex = S.gather(Eax), ey = S.gather(Eay), bz = S.gather(Bh);
     const double a = dt * qm;

@@ -10,10 +10,10 @@
 // Per step (the state is E^n, B^{n-1/2}, Bp = B^{n+1/2} and, for ESEC2,
 // j^{n,*} deposited at the end of the previous step):
 //   K1 grid     E* = E^n + dt/2 (c^2 curl Bp - j^{n,*}); clear j^{*,n+1/2}
-//   K2 markers  x*, E**, B at x*, v* (closed form of the implicit relation),
-//               x^{n+1/2}, deposit of j^{*,n+1/2}
+//   K2 markers  x*, E**, B at x*, v* (closed form of the implicit relation,
+//               stored), x^{n+1/2}, deposit of j^{*,n+1/2}
 //   K3 grid     E^{n+1} = E^n + dt (c^2 curl Bp - j^{*,n+1/2}), E^{n+1/2}
-//   K4 markers  recompute v*, x^{n+1/2}; gather E^{n+1/2}, B at x^{n+1/2};
+//   K4 markers  v* loaded, x^{n+1/2} with K2's rounding; gather E^{n+1/2}, B at x^{n+1/2};
 //               v^dag, Gamma (fallback counted), x^{n+1}, v^{n+1}, KE, next j^{n+1,*}
 //   K5 grid     B^{n+3/2} = Bp - dt curl E^{n+1}; W_E^{n+1}, W_B^{n+1} =
 //               (c^2/2)|h| sum Bp . B^{n+3/2} (the energy of the new state)
@@ -249,6 +249,9 @@ __global__ void __launch_bounds__(256) em_pass_c_kernel(Em2dConst c, Em2dBufs b)
     const double v[3] = {b.vx[p], b.vy[p], b.vz[p]};
     double vs[3], xh, yh;
     half_push_em<ORDER>(c, b, s, b.x[p], b.y[p], v, vs, xh, yh);
+    b.vsx[p] = vs[0];   // pass E forms x^{n+1/2} from v* with the same rounding
+    b.vsy[p] = vs[1];
+    b.vsz[p] = vs[2];
     Shape2<ORDER> S(c, xh, yh);
     deposit_j<ORDER>(c, b.J2, S, b.w ? c.q_a[s] * b.w[p] : c.qw_a[s], vs);
   }
@@ -264,8 +267,10 @@ __global__ void __launch_bounds__(256) em_pass_e_kernel(Em2dConst c, Em2dBufs b,
     const int s = species_of2(c, p);
     const double x = b.x[p], y = b.y[p];
     const double v[3] = {b.vx[p], b.vy[p], b.vz[p]};
-    double vs[3], xh, yh;
-    half_push_em<ORDER>(c, b, s, x, y, v, vs, xh, yh);
+    const double vs[3] = {b.vsx[p], b.vsy[p], b.vsz[p]};
+    const double hdt = 0.5 * c.dt;
+    const double xh = wrapd(__fma_rn(hdt, vs[0], x), c.Lx, b.err);
+    const double yh = wrapd(__fma_rn(hdt, vs[1], y), c.Ly, b.err);
     Shape2<ORDER> S(c, xh, yh);
     double e[3], bb[3];
     gather_eb<ORDER>(c, b.Eh, b.Bp, S, e, bb);

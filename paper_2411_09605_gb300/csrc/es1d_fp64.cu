@@ -4,9 +4,11 @@
 // of the scheme (Sec. 3.3, Eq. good_translation): the deposited currents.
 //   pass C: E* = E^n - dt/2 (j^{n,*} - <j^{n,*}>) in the prologue (every block,
 //           redundantly, from the tiny grid), then per particle
-//           x* -> E**_p -> v* -> x^{n+1/2} -> deposit j^{*,n+1/2}.
+//           x* -> E**_p -> v* -> x^{n+1/2} -> deposit j^{*,n+1/2}; v* is stored.
 //   pass E: E^{n+1} = E^n - dt (j^{*,n+1/2} - <.>) and E^{n+1/2} in the prologue,
-//           then per particle the same x*, v*, x^{n+1/2} recomputed bit for bit,
+//           then per particle v* loaded and x^{n+1/2} formed with pass C's
+//           rounding (the FP64 pipe, not HBM, bounds this form: a load is
+//           cheaper than recomputing x*, E**_p and v*),
 //           E^{n+1/2}_p, v^dag, Gamma (Eq. opt_solution) with the imaginary-root
 //           fallback of Sec. 3.2, x^{n+1}, v^{n+1}; for ESEC2 the next step's
 //           x* and j^{n+1,*} deposit are fused in (Eq. doublestardef).
@@ -154,6 +156,7 @@ __global__ void __launch_bounds__(512) pass_c_kernel(Es1dConst c, Es1dFp64Bufs b
     double x = b.x[p], v = b.v[p];
     double vs, xh;
     half_push<ORDER>(c, Es, x, v, c.qm[s], b.err, vs, xh);
+    b.vs[p] = vs;   // pass E forms x^{n+1/2} from it with the same rounding
     double coef = (b.w ? c.q_h[s] * b.w[p] : c.qw_h[s]) * vs;
     Shape64<ORDER> S(__dmul_rn(xh, c.inv_h), c.nc);
     S.deposit(Jt, coef);
@@ -221,8 +224,9 @@ __global__ void __launch_bounds__(512) pass_e_kernel(Es1dConst c, Es1dFp64Bufs b
     int s = species_of(c, p);
     double x = b.x[p], v = b.v[p];
     double qm = c.qm[s];
-    double vs, xh;
-    half_push<ORDER>(c, Es, x, v, qm, b.err, vs, xh);
+    // v* from pass C; x^{n+1/2} with the rounding half_push used for the deposit
+    const double vs = b.vs[p];
+    const double xh = wrap_periodic(__fma_rn(hdt, vs, x), c.L, b.err);
     Shape64<ORDER> Sh(__dmul_rn(xh, c.inv_h), c.nc);
     double Ep = Sh.gather(Eh);
     double vd = v + c.dt * qm * Ep;

@@ -473,7 +473,9 @@ int init_es1d(pic_handle *h, const pic_species *species, const double *E0) {
   CUDA_TRY(es1d_fp64_prepare(c));
   Es1dFp64Bufs &b = h->b1;
   int rc;
-  if ((rc = h->alloc(&b.x, h->N)) || (rc = h->alloc(&b.v, h->N))) return rc;
+  if ((rc = h->alloc(&b.x, h->N)) || (rc = h->alloc(&b.v, h->N)) ||
+      (!h->mixed && (rc = h->alloc(&b.vs, h->N))))
+    return rc;
   b.w = nullptr;
   if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;
   for (int k = 0; k < 2; k++)
@@ -652,7 +654,9 @@ int init_em2d(pic_handle *h, const pic_species *species, const double *E0, const
   h->lg.grid = (int)std::max<int64_t>(1, std::min<int64_t>((nc3 + 255) / 256, (int64_t)h->nsm * 4));
   int rc;
   if ((rc = h->alloc(&b.x, h->N)) || (rc = h->alloc(&b.y, h->N)) || (rc = h->alloc(&b.vx, h->N)) ||
-      (rc = h->alloc(&b.vy, h->N)) || (rc = h->alloc(&b.vz, h->N)))
+      (rc = h->alloc(&b.vy, h->N)) || (rc = h->alloc(&b.vz, h->N)) ||
+      (rc = h->alloc(&b.vsx, h->N)) || (rc = h->alloc(&b.vsy, h->N)) ||
+      (rc = h->alloc(&b.vsz, h->N)))
     return rc;
   b.w = nullptr;
   if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;
@@ -837,7 +841,8 @@ int init_em1d(pic_handle *h, const pic_species *species, const double *E0, const
   h->le.grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->N + 255) / 256, (int64_t)h->nsm * 2));
   const size_t n = (size_t)c.n;
   int rc;
-  if ((rc = h->alloc(&b.y, h->N)) || (rc = h->alloc(&b.vx, h->N)) || (rc = h->alloc(&b.vy, h->N)))
+  if ((rc = h->alloc(&b.y, h->N)) || (rc = h->alloc(&b.vx, h->N)) || (rc = h->alloc(&b.vy, h->N)) ||
+      (rc = h->alloc(&b.vsx, h->N)) || (rc = h->alloc(&b.vsy, h->N)))
     return rc;
   b.w = nullptr;
   if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;

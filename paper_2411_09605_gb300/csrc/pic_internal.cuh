@@ -136,6 +136,7 @@ struct Em2dBufs {
   double *Bpp;    // B^{n+3/2} (computed at the end of a step)
   double *J1;     // j^{n,*}
   double *J2;     // j^{*,n+1/2}
+  double *vsx, *vsy, *vsz;     // [N] v* of the current step (pass C -> pass E)
   double *ke_part;             // [particle blocks]
   double *wf_part;             // [2 x grid blocks] W_E, W_B partials
   unsigned long long *fallback;
@@ -170,6 +171,7 @@ struct Em1dConst {
 
 struct Em1dBufs {
   double *y, *vx, *vy, *w;   // [N] SoA (w may be null)
+  double *vsx, *vsy;         // [N] v* of the current step (pass C -> pass E)
   double *E, *En;            // E^n, E^{n+1}: [2][n] (Ex, Ey); swapped after each step
   double *B, *Bn;            // Bz^n, Bz^{n+1}: [n]
   double *Es, *Bs;           // E*, B* of the half step
@@ -220,6 +222,7 @@ struct StdBufs {
 // Everything the 1D FP64 kernels touch.
 struct Es1dFp64Bufs {
   double *x, *v, *w;        // [N] SoA (w may be null)
+  double *vs;               // [N] v* of the current step (pass C -> pass E)
   double *E[2];             // ping-pong E^n / E^{n+1}
   double *J1[2];            // j^{n,*} (ESEC2), indexed by step parity
   double *J2[2];            // j^{*,n+1/2}
