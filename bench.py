@@ -504,45 +504,40 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
-# 2D3V Yee path: pass C reads x, y, vx, vy, vz and writes v*; pass E reads them
-# and v*, and writes x, y, v
-EM2D_ALGO_BYTES = {0: 64, 1: 104}          # pass C also writes v*, pass E reads it
-# FP64-pipe thread instructions per marker (ncu, 2^20 markers): bound by the FP64 pipe
+# 2D3V Yee path, FP64 form: pass C reads x, y, vx, vy, vz and writes v*; pass
+# E reads them and v*, and writes x, y, v.  Mixed form: X, Y (u32), three
+# float pairs and V* (3 x i32): pass C reads 32 bytes and writes 12, pass E
+# reads 44 and writes 32.
+EM2D_ALGO_BYTES = {("fp64", 0): 64, ("fp64", 1): 104, ("mixed", 0): 44, ("mixed", 1): 76}
+# FP64-pipe thread instructions per marker of the FP64 form (ncu, 2^20
+# markers): that form is bound by the FP64 pipe
 EM2D_FP64_INST_PER_MARKER = {0: 163.0, 1: 205.89}
-EM2D_TRAFFIC = {0: None, 1: 68729856}     # dram read + write per launch
+EM2D_TRAFFIC = {("fp64", 0): None, ("fp64", 1): 68729856,   # dram read + write per launch
+                ("mixed", 0): None, ("mixed", 1): None}
 
 
-def run_weibel2d(args):
-    """The 2D3V Weibel workload with the Yee/leapfrog field step (Sec. 4.1):
-    128 x 128 periodic cells, 64 markers per cell (1,048,576), bi-Maxwellian
-    with T_perp / T_par = 10, vth_par = 0.05 c, CFL 0.5, FP64, ESEC2 form."""
+def time_weibel2d(prob, precision, args, stream, flush):
+    """Warm-up, timed steps (one event pair per step, L2 flushed before each)
+    and a profiled run of one form of the 2D3V Yee step."""
     import torch
-    from paper_2411_09605_gb300 import build as B, pic, workloads as W
-    B.build()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.current_stream()          # the handle uses the default stream
-    peak, peak_src = hbm_peak()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    prob = W.weibel()
-    sim = pic.Simulation2D(prob)
+    from paper_2411_09605_gb300 import pic
+    sim = pic.Simulation2D(prob, precision=precision)
     try:
         te0 = sim.energy()[3]
         pic.pic_step_async(sim.h, max(3, args.warmup))
         pic.pic_read_stats(sim.h)
         launches0 = pic.pic_launch_count(sim.h)
         evs = []
-        with ClockSampler(0, enabled=not args.no_clocks) as clk:
-            for _ in range(args.steps):
-                flush.zero_()
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                pic.pic_step_async(sim.h, 1)
-                b.record(stream)
-                evs.append((a, b))
-            fb, te = pic.pic_read_stats(sim.h)
-            torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pic.pic_step_async(sim.h, 1)
+            b.record(stream)
+            evs.append((a, b))
+        fb, te = pic.pic_read_stats(sim.h)
+        torch.cuda.synchronize()
         launches = pic.pic_launch_count(sim.h) - launches0
         step_ms = np.array([a.elapsed_time(b) for a, b in evs])
         pic.pic_set_profiling(sim.h, True)
@@ -558,39 +553,75 @@ def run_weibel2d(args):
         pic.pic_set_profiling(sim.h, False)
     finally:
         sim.close()
+    return {"step_ms": step_ms, "kernels": kern, "launches": int(launches),
+            "max_rel_dTE": float(np.max(np.abs(te - te0)) / te0), "fallbacks": int(fb.sum())}
+
+
+def run_weibel2d(args):
+    """The 2D3V Weibel workload with the Yee/leapfrog field step (Sec. 4.1):
+    128 x 128 periodic cells, 64 markers per cell (1,048,576), bi-Maxwellian
+    with T_perp / T_par = 10, vth_par = 0.05 c, CFL 0.5, ESEC2 form; the FP64
+    and the mixed form on the same markers, the mixed form the headline."""
+    import torch
+    from paper_2411_09605_gb300 import build as B, pic, workloads as W
+    B.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()          # the handle uses the default stream
+    peak, peak_src = hbm_peak()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    prob = W.weibel()
     n = prob.n_markers
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     fp64_peak = FP64_LANES_PER_SM_CLK * nsm * 2070.0e6 / 1e9
-    for kind, kname in ((0, "pass_c"), (1, "pass_e")):
-        if kname in kern:
-            t = kern[kname]["avg_us"] * 1e-6
-            ach = EM2D_ALGO_BYTES[kind] * n / t / 1e9
-            kern[kname]["achieved_GBs"] = round(ach, 1)
-            kern[kname]["frac_hbm"] = round(ach / peak, 4)
-            kern[kname]["fp64_ginst_s"] = round(EM2D_FP64_INST_PER_MARKER[kind] * n / t / 1e9, 1)
-            kern[kname]["frac_fp64"] = round(kern[kname]["fp64_ginst_s"] / fp64_peak, 4)
-    dom = "pass_e" if "pass_e" in kern else "pass_c"
-    value = n * args.steps / (step_ms.sum() / 1e3)
+    forms = {}
+    with ClockSampler(0, enabled=not args.no_clocks) as clk:
+        for name, precision in (("mixed", 1), ("fp64", 0)):
+            forms[name] = time_weibel2d(prob, precision, args, stream, flush)
+    out = {}
+    for name, f in forms.items():
+        kern = f["kernels"]
+        for kind, kname in ((0, "pass_c"), (1, "pass_e")):
+            if kname in kern:
+                t = kern[kname]["avg_us"] * 1e-6
+                ach = EM2D_ALGO_BYTES[(name, kind)] * n / t / 1e9
+                kern[kname]["achieved_GBs"] = round(ach, 1)
+                kern[kname]["frac_hbm"] = round(ach / peak, 4)
+                if name == "fp64":
+                    kern[kname]["fp64_ginst_s"] = round(EM2D_FP64_INST_PER_MARKER[kind] * n / t / 1e9, 1)
+                    kern[kname]["frac_fp64"] = round(kern[kname]["fp64_ginst_s"] / fp64_peak, 4)
+        dom = max(("pass_c", "pass_e"), key=lambda k: kern[k]["avg_us"])
+        dk = 1 if dom == "pass_e" else 0
+        if name == "fp64":
+            roof = {"bound": "alu", "kernel": dom, "achieved": kern[dom]["fp64_ginst_s"],
+                    "peak": round(fp64_peak, 1), "unit": "Ginst/s (FP64 pipe)",
+                    "frac": kern[dom]["frac_fp64"], "traffic": EM2D_TRAFFIC[(name, dk)],
+                    "peak_source": f"{FP64_LANES_PER_SM_CLK} FP64 lanes/SM/clk x SMs x 2070 MHz",
+                    "hbm_frac": kern[dom]["frac_hbm"], "hbm_peak": peak,
+                    "hbm_peak_source": peak_src}
+        else:
+            roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_GBs"],
+                    "peak": peak, "unit": "GB/s", "frac": kern[dom]["frac_hbm"],
+                    "traffic": EM2D_TRAFFIC[(name, dk)], "peak_source": peak_src}
+        out[name] = {"value": n * args.steps / (f["step_ms"].sum() / 1e3),
+                     "ms_per_step": float(f["step_ms"].mean()),
+                     "energy": {"max_rel_dTE": f["max_rel_dTE"], "fallbacks": f["fallbacks"]},
+                     "gpu_launches": f["launches"], "kernels": kern, "roofline": roof}
+    hf = out["mixed"]
     line = {
         "metric": "particle-steps/s, 2D3V Weibel with the Yee/leapfrog field step",
-        "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": float(step_ms.mean()),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "value": hf["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": hf["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+i32+i64 (fields and energy in f64)",
         "data": "synthetic (seeded bi-Maxwellian markers)",
         "config": {"workload": "weibel_2d3v_yee", "cells": [prob.nx, prob.ny],
                    "markers": n, "dt": prob.dt, "c": prob.c, "scheme": "ESEC2",
-                   "shape_order": prob.order,
+                   "shape_order": prob.order, "form": "mixed",
                    "l2": "flushed (512 MiB write) before every timed step"},
-        "energy": {"max_rel_dTE": float(np.max(np.abs(te - te0)) / te0),
-                   "fallbacks": int(fb.sum())},
-        "gpu_launches": int(launches), "kernels": kern, "clocks": clk.summary(),
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": kern[dom]["fp64_ginst_s"],
-                     "peak": round(fp64_peak, 1), "unit": "Ginst/s (FP64 pipe)",
-                     "frac": kern[dom]["frac_fp64"],
-                     "traffic": EM2D_TRAFFIC[1 if dom == "pass_e" else 0],
-                     "peak_source": f"{FP64_LANES_PER_SM_CLK} FP64 lanes/SM/clk x SMs x 2070 MHz",
-                     "hbm_frac": kern[dom]["frac_hbm"], "hbm_peak": peak,
-                     "hbm_peak_source": peak_src},
+        "energy": hf["energy"], "gpu_launches": hf["gpu_launches"],
+        "kernels": hf["kernels"], "clocks": clk.summary(), "roofline": hf["roofline"],
+        "forms": out,
     }
     print(json.dumps(line), flush=True)
 

@@ -1,0 +1,516 @@
+// 2D3V electromagnetic step with the leapfrog / Yee field update (Sec. 4.1,
+// Eq. EMleapfrog), mixed-precision form.
+//
+// The FP64 form of this step is bound by the FP64 pipe (a per-marker v* solve,
+// two gathers of six components and Gamma).  This form keeps FP64 on the grid
+// only (the field update, K5 and the energy sums are those of the FP64 form)
+// and runs the per-marker work in FP32, float pairs and integers, with the
+// energy still conserved to the FP64 bound:
+//   * positions X, Y: 32-bit fixed point, x = X L / 2^32 (Lx = Ly = L); the
+//     cell and in-cell fraction come from X n as a 32.32 number and the
+//     periodic wrap is the integer overflow.
+//   * velocities: float pairs (vh, vl) in V units, v cxk with cxk =
+//     (dt 2^31 / L) 2^kv for all three components; v* is the integer V*, so
+//     x^{n+1/2} = X + [V*_x]_kv and x^{n+1} = X + 2 [V*_x]_kv are exact.
+//   * weights: quantised B-spline values (multiples of 2^-23) per axis; the
+//     gather of E^{n+1/2} and the deposit of j^{*,n+1/2} use the same
+//     integers s_x s_y, as Eq. exp_econs_simple requires.
+//   * current: each marker adds round(V*_c s_x s_y / 2^r) (r >= 32, so no
+//     node sum overflows) to the int64 node sums with global atomics: exact
+//     integer sums, independent of the marker order.
+//   * gather #1 (E*, B at x*) only shapes v*: FP32 tables and FP32 weights;
+//     v* = (u + u x t + (u.t) t) / (1 + |t|^2) as u plus an FP32 correction.
+//   * gather #2: kick E^{n+1/2} as float pairs with error-free products, so
+//     the kick d is the grid's E^{n+1/2} to about 2^-46.
+//   * the magnetic term mu = dt (q/m) V* x B is formed in float pairs from the
+//     exact V*: V* . mu is zero to the pairs' precision, so B does no work
+//     (whatever rounding the B table had).
+//   * Gamma (Eq. opt_solution): with Delta = v^dag - v^n = d + mu,
+//     |v^{n+1}|^2 - |v^dag|^2 = 2 Delta . (V* - v^n - Delta/2), the bracket
+//     from the exact difference V* - v^n per component, then
+//     Gamma - 1 = t / (1 + sqrt(1 + t)), t = 2a / |v^dag|^2, in float pairs.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "em2d_common.cuh"
+#include "ff.cuh"
+#include "mixed_common.cuh"
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+// Quantised B-spline weights of one axis.  X is the position as a 32-bit
+// fraction of the box, n the cells of the axis; half = the component sits on
+// the half nodes (i + 1/2).  i0 is the first node, k[] the periodic node
+// indices, w[] the weights as floats and s[] = w 2^23 as integers (sum 2^23).
+// Order 1: w = (1 - f, f) at floor(xi), floor(xi) + 1.  Order 2: with
+// f = frac(xi + 1/2), w = (1/2 (1 - f)^2, 1 - w0 - w2, 1/2 f^2) at
+// floor(xi + 1/2) - 1 .. + 1.  xi is in cells, less 1/2 for half nodes.
+template <int ORDER>
+struct AxisMix {
+  int k[ORDER + 1];
+  float w[ORDER + 1];
+  uint32_t s[ORDER + 1];
+  __device__ __forceinline__ AxisMix(uint32_t X, int n, bool half) {
+    // xi (+ 1/2 for order 2, - 1/2 for half nodes) + n as a 32.32 number,
+    // kept positive by the offset of n cells
+    const uint64_t P = (uint64_t)X * (uint32_t)n + ((uint64_t)(uint32_t)n << 32) +
+                       (ORDER == 2 ? 0x80000000ull : 0ull) - (half ? 0x80000000ull : 0ull);
+    const int i0 = (int)(P >> 32) - n - (ORDER == 2 ? 1 : 0);
+#pragma unroll
+    for (int a = 0; a <= ORDER; a++) {
+      const int i = i0 + a;
+      k[a] = i < 0 ? i + n : (i >= n ? i - n : i);
+    }
+    const uint32_t f23 = (uint32_t)P >> 9;
+    const float f = __fsub_rn(__uint_as_float(0x3F800000u | f23), 1.0f);  // exact
+    if (ORDER == 1) {
+      w[0] = __fsub_rn(1.0f, f);
+      w[1] = f;
+      s[0] = (1u << 23) - f23;
+      s[1] = f23;
+    } else {
+      const float a = __fsub_rn(1.0f, f);
+      // 1 + w0 and 1 + w2 in [1, 1.5]: rounding to float puts w on the 2^-23 grid
+      const float q0 = __fmaf_rn(__fmul_rn(0.5f, a), a, 1.0f);
+      const float q2 = __fmaf_rn(__fmul_rn(0.5f, f), f, 1.0f);
+      w[0] = __fsub_rn(q0, 1.0f);
+      w[ORDER] = __fsub_rn(q2, 1.0f);
+      w[1] = __fsub_rn(__fsub_rn(1.0f, w[0]), w[ORDER]);
+      s[0] = (uint32_t)__float_as_int(q0) & 0x7FFFFFu;
+      s[ORDER] = (uint32_t)__float_as_int(q2) & 0x7FFFFFu;
+      s[1] = (1u << 23) - s[0] - s[ORDER];
+    }
+  }
+};
+
+// Weights of a point for integer-node (I) and half-node (H) components.
+template <int ORDER>
+struct Shape2Mix {
+  AxisMix<ORDER> xI, xH, yI, yH;
+  __device__ __forceinline__ Shape2Mix(uint32_t X, uint32_t Y, int nx, int ny)
+      : xI(X, nx, false), xH(X, nx, true), yI(Y, ny, false), yH(Y, ny, true) {}
+};
+
+// V units -> position units for half a step (kv >= 1)
+__device__ __forceinline__ uint32_t half_shift(int V, const Em2dMixConst &c) {
+  return (uint32_t)((V + c.hround) >> c.kv);
+}
+
+template <int ORDER>
+__device__ __forceinline__ float gather_f(const float *T, int nx, const AxisMix<ORDER> &ax,
+                                          const AxisMix<ORDER> &ay) {
+  float s = 0.0f;
+#pragma unroll
+  for (int b = 0; b <= ORDER; b++) {
+    const float *row = T + ay.k[b] * nx;
+    float r = 0.0f;
+#pragma unroll
+    for (int a = 0; a <= ORDER; a++) r = __fmaf_rn(__ldg(row + ax.k[a]), ax.w[a], r);
+    s = __fmaf_rn(r, ay.w[b], s);
+  }
+  return s;
+}
+
+// sum_b w_y[b] sum_a w_x[a] T[b][a] of a float-pair table: error-free
+// products with the quantised weights, the large parts summed by two-sums
+template <int ORDER>
+__device__ __forceinline__ ff gather_ff(const float2 *T, int nx, const AxisMix<ORDER> &ax,
+                                        const AxisMix<ORDER> &ay) {
+  ff acc{0.0f, 0.0f};
+#pragma unroll
+  for (int b = 0; b <= ORDER; b++) {
+    const float2 *row = T + ay.k[b] * nx;
+    float ph[ORDER + 1], pl = 0.0f;
+#pragma unroll
+    for (int a = 0; a <= ORDER; a++) {
+      const float2 e = __ldg(row + ax.k[a]);
+      const ff p = two_prod(e.x, ax.w[a]);
+      ph[a] = p.hi;
+      pl = __fadd_rn(pl, __fmaf_rn(e.y, ax.w[a], p.lo));
+    }
+    ff r = two_sum(ph[0], ph[1]);
+    pl = __fadd_rn(pl, r.lo);
+    if (ORDER == 2) {
+      r = two_sum(r.hi, ph[ORDER]);
+      pl = __fadd_rn(pl, r.lo);
+    }
+    acc = ff_add(acc, ff_mul_f(fast_two_sum(r.hi, pl), ay.w[b]));
+  }
+  return acc;
+}
+
+// round(V s_a s_b / 2^r) for r >= 32, given m = |V| s_b (|V| < 2^31, s <= 2^23,
+// so the product is below 2^77): with m = mh 2^32 + ml,
+// (m s_a + 2^(r-1)) >> r = (mh s_a + ((ml s_a + 2^(r-1)) >> 32)) >> (r - 32).
+__device__ __forceinline__ long long deposit_term(uint64_t m, uint32_t sa, bool neg,
+                                                  const Em2dMixConst &c) {
+  const uint64_t lo = (uint64_t)(uint32_t)m * sa + (uint64_t)c.rnd;
+  const uint64_t q = ((uint64_t)(uint32_t)(m >> 32) * sa + (lo >> 32)) >> (c.rshift - 32);
+  return neg ? -(long long)q : (long long)q;
+}
+
+template <int ORDER>
+__device__ __forceinline__ void deposit_c(long long *J, int nx, const AxisMix<ORDER> &ax,
+                                          const AxisMix<ORDER> &ay, int V,
+                                          const Em2dMixConst &c) {
+  if (V == 0) return;
+  const bool neg = V < 0;
+  const uint32_t mag = neg ? 0u - (uint32_t)V : (uint32_t)V;
+#pragma unroll
+  for (int b = 0; b <= ORDER; b++) {
+    const uint64_t m = (uint64_t)mag * ay.s[b];
+    long long *row = J + ay.k[b] * nx;
+#pragma unroll
+    for (int a = 0; a <= ORDER; a++)
+      atomicAdd((unsigned long long *)(row + ax.k[a]),
+                (unsigned long long)deposit_term(m, ax.s[a], neg, c));
+  }
+}
+
+// j of velocity V at the shape's point: Jx on (H, I), Jy on (I, H), Jz on (I, I)
+template <int ORDER>
+__device__ __forceinline__ void deposit_j(const Em2dMixConst &c, long long *J,
+                                          const Shape2Mix<ORDER> &S, const int V[3]) {
+  const int nx = c.nx, nc = c.nx * c.ny;
+  deposit_c<ORDER>(J, nx, S.xH, S.yI, V[0], c);
+  deposit_c<ORDER>(J + nc, nx, S.xI, S.yH, V[1], c);
+  deposit_c<ORDER>(J + 2 * nc, nx, S.xI, S.yI, V[2], c);
+}
+
+__device__ __forceinline__ void report_bad(unsigned bad, unsigned *err) {
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31u) == 0u && bad) atomicOr(err, bad);
+}
+
+// An exact integer as a float pair (|V| < 2^31).
+__device__ __forceinline__ ff ff_from_int(int V) {
+  const float hi = __int2float_rn(V);
+  return {hi, __int2float_rn(V - __float2int_rn(hi))};
+}
+
+// v^dag = v^n + Delta and v^{n+1} = Gamma v^dag (Eq. opt_solution) in float
+// pairs, three components.  R - |v^dag|^2 = 2a with a = Delta . b and
+// b = V* - v^n - Delta/2: each b_i is formed from the exact difference
+// V*_i - rint(vh_i) and the exact remainders, the small product in FP32.
+// Gamma - 1 = t / (1 + sqrt(1 + t)), t = 2a / |v^dag|^2; for |t| < 2^-8 the
+// series t/2 - t^2/8 + t^3/16 - 5t^4/128 (relative error < 2^-33).  R < 0
+// (t < -1) and v^dag = 0 (t not finite) fall back to Gamma = 1, counted.
+__device__ __forceinline__ void correct_velocity3(const float vh[3], const float vl[3],
+                                                  const int Vs[3], const ff D[3], bool on,
+                                                  unsigned &nfb, ff vn[3]) {
+  ff vd[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) vd[d] = ff_add(ff{vh[d], vl[d]}, D[d]);
+  float gm = 0.0f;
+  if (on) {
+    float a2 = 0.0f, vd2 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const int ih = __float2int_rn(vh[d]);
+      const float fr = __fsub_rn(vh[d], __int2float_rn(ih));
+      const ff q = two_sum(__int2float_rn(Vs[d] - ih), __fmul_rn(-0.5f, D[d].hi));
+      const float small =
+          __fsub_rn(__fsub_rn(__fsub_rn(q.lo, fr), vl[d]), __fmul_rn(0.5f, D[d].lo));
+      const float bq = __fadd_rn(q.hi, small);
+      a2 = __fmaf_rn(__fadd_rn(D[d].hi, D[d].hi), bq, a2);
+      vd2 = __fmaf_rn(vd[d].hi, vd[d].hi, vd2);
+    }
+    const float t = div_rcp_residual(a2, vd2);
+    if (fabsf(t) < 0.00390625f) {
+      gm = __fmul_rn(
+          t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, -0.0390625f, 0.0625f), -0.125f), 0.5f));
+    } else if (!(t >= -1.0f && t < 1e30f)) {
+      nfb++;
+    } else {
+      gm = __fdiv_rn(t, __fadd_rn(1.0f, __fsqrt_rn(__fadd_rn(1.0f, t))));
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    ff p = two_prod(vd[d].hi, gm);
+    p.lo = __fmaf_rn(vd[d].lo, gm, p.lo);
+    vn[d] = ff_add(vd[d], p);
+  }
+}
+
+// K1: e_half E* (ESEC2: E^n + dt/2 (c^2 curl B^{n+1/2} - j^{n,*}); ESEC1: E^n)
+// and t_half B^{n+1/2} as FP32 tables; clear J2
+__global__ void mix2_k1_kernel(Em2dConst c, Em2dMixConst m, Em2dMixBufs mb, Em2dBufs b) {
+  const int nc = c.nx * c.ny;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < 3 * nc; a += gridDim.x * blockDim.x) {
+    const int d = a / nc, ij = a % nc, i = ij % c.nx, j = ij / c.nx;
+    double es = b.E[a];
+    if (m.scheme == 2)
+      es = es + 0.5 * c.dt * (c.c2 * curl_b(c, b.Bp, i, j, d) - m.jscale * (double)mb.J1[a]);
+    mb.T1[a] = (float)(m.e_half * es);
+    mb.T1[3 * nc + a] = (float)(m.t_half * b.Bp[a]);
+    mb.J2[a] = 0;
+  }
+}
+
+// K3: E^{n+1} (FP64), kick E^{n+1/2} as float pairs, m_full B^{n+1/2}; clear J1
+__global__ void mix2_k3_kernel(Em2dConst c, Em2dMixConst m, Em2dMixBufs mb, Em2dBufs b) {
+  const int nc = c.nx * c.ny;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < 3 * nc; a += gridDim.x * blockDim.x) {
+    const int d = a / nc, ij = a % nc, i = ij % c.nx, j = ij / c.nx;
+    const double en =
+        b.E[a] + c.dt * (c.c2 * curl_b(c, b.Bp, i, j, d) - m.jscale * (double)mb.J2[a]);
+    const ff k = ff_from_double(m.kick * (0.5 * (b.E[a] + en)));
+    b.En[a] = en;
+    mb.T2[a] = make_float2(k.hi, k.lo);
+    mb.B2[a] = (float)(m.m_full * b.Bp[a]);
+    mb.J1[a] = 0;
+  }
+}
+
+// Pass C: x*, E* and B at x*, v* (integer V*), x^{n+1/2}, deposit of j^{*,n+1/2}
+template <int ORDER>
+__global__ void __launch_bounds__(256) mix2_pass_c_kernel(Em2dMixConst c, Em2dMixBufs b) {
+  const int nx = c.nx, nc = c.nx * c.ny;
+  unsigned bad = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t X = b.X[p], Y = b.Y[p];
+    float vh[3], vl[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      vh[d] = b.vh[d][p];
+      vl[d] = b.vl[d][p];
+    }
+    const Shape2Mix<ORDER> S1(X + half_shift(to_fixed(vh[0], bad), c),
+                              Y + half_shift(to_fixed(vh[1], bad), c), c.nx, c.ny);
+    const float *T = b.T1;
+    float e[3], t[3];
+    e[0] = gather_f<ORDER>(T, nx, S1.xH, S1.yI);
+    e[1] = gather_f<ORDER>(T + nc, nx, S1.xI, S1.yH);
+    e[2] = gather_f<ORDER>(T + 2 * nc, nx, S1.xI, S1.yI);
+    t[0] = gather_f<ORDER>(T + 3 * nc, nx, S1.xI, S1.yH);
+    t[1] = gather_f<ORDER>(T + 4 * nc, nx, S1.xH, S1.yI);
+    t[2] = gather_f<ORDER>(T + 5 * nc, nx, S1.xH, S1.yH);
+    // v* - v* x t = u = v^n + e: v* = u + (u x t + (u.t) t - |t|^2 u) / (1 + |t|^2)
+    float u[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) u[d] = __fadd_rn(vh[d], e[d]);
+    const float ut = __fmaf_rn(u[2], t[2], __fmaf_rn(u[1], t[1], __fmul_rn(u[0], t[0])));
+    const float tt = __fmaf_rn(t[2], t[2], __fmaf_rn(t[1], t[1], __fmul_rn(t[0], t[0])));
+    const float inv = __frcp_rn(__fadd_rn(1.0f, tt));
+    const float r[3] = {__fsub_rn(__fmul_rn(u[1], t[2]), __fmul_rn(u[2], t[1])),
+                        __fsub_rn(__fmul_rn(u[2], t[0]), __fmul_rn(u[0], t[2])),
+                        __fsub_rn(__fmul_rn(u[0], t[1]), __fmul_rn(u[1], t[0]))};
+    int Vs[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const float corr = __fmul_rn(__fmaf_rn(ut, t[d], __fmaf_rn(-tt, u[d], r[d])), inv);
+      Vs[d] = vstar_fixed(vh[d], vl[d], __fadd_rn(e[d], corr), bad);
+    }
+    const Shape2Mix<ORDER> Sh(X + half_shift(Vs[0], c), Y + half_shift(Vs[1], c), c.nx, c.ny);
+    deposit_j<ORDER>(c, b.J2, Sh, Vs);
+#pragma unroll
+    for (int d = 0; d < 3; d++) b.Vs[d][p] = Vs[d];
+  }
+  report_bad(bad, b.err);
+}
+
+// Pass E: gather at x^{n+1/2} = X + [V*], v^dag, Gamma, x^{n+1}, v^{n+1}, the
+// kinetic energy and (ESEC2) the next step's j^{n+1,*}
+template <int ORDER>
+__global__ void __launch_bounds__(256) mix2_pass_e_kernel(Em2dMixConst c, Em2dMixBufs b,
+                                                          int slot) {
+  __shared__ double red[33];
+  const int nx = c.nx, nc = c.nx * c.ny;
+  float ke_hi = 0.0f, ke_lo = 0.0f;
+  unsigned nfb = 0, bad = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t X = b.X[p], Y = b.Y[p];
+    float vh[3], vl[3];
+    int Vs[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      vh[d] = b.vh[d][p];
+      vl[d] = b.vl[d][p];
+      Vs[d] = b.Vs[d][p];
+    }
+    const uint32_t hx = half_shift(Vs[0], c), hy = half_shift(Vs[1], c);
+    const Shape2Mix<ORDER> S(X + hx, Y + hy, c.nx, c.ny);
+    ff D[3];
+    D[0] = gather_ff<ORDER>(b.T2, nx, S.xH, S.yI);
+    D[1] = gather_ff<ORDER>(b.T2 + nc, nx, S.xI, S.yH);
+    D[2] = gather_ff<ORDER>(b.T2 + 2 * nc, nx, S.xI, S.yI);
+    const float bb[3] = {gather_f<ORDER>(b.B2, nx, S.xI, S.yH),
+                         gather_f<ORDER>(b.B2 + nc, nx, S.xH, S.yI),
+                         gather_f<ORDER>(b.B2 + 2 * nc, nx, S.xH, S.yH)};
+    // Delta = d + dt (q/m) V* x B, the cross product in float pairs of the exact V*
+    const ff vs[3] = {ff_from_int(Vs[0]), ff_from_int(Vs[1]), ff_from_int(Vs[2])};
+    D[0] = ff_add(D[0], ff_sub(ff_mul_f(vs[1], bb[2]), ff_mul_f(vs[2], bb[1])));
+    D[1] = ff_add(D[1], ff_sub(ff_mul_f(vs[2], bb[0]), ff_mul_f(vs[0], bb[2])));
+    D[2] = ff_add(D[2], ff_sub(ff_mul_f(vs[0], bb[1]), ff_mul_f(vs[1], bb[0])));
+    ff vn[3];
+    correct_velocity3(vh, vl, Vs, D, c.gamma_on != 0, nfb, vn);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      ff s2 = two_prod(vn[d].hi, vn[d].hi);
+      s2.lo = __fmaf_rn(__fadd_rn(vn[d].hi, vn[d].hi), vn[d].lo, s2.lo);
+      const ff acc = two_sum(ke_hi, s2.hi);
+      ke_hi = acc.hi;
+      ke_lo = __fadd_rn(ke_lo, __fadd_rn(acc.lo, s2.lo));
+    }
+    const uint32_t Xn = X + 2u * hx, Yn = Y + 2u * hy;
+    if (c.scheme == 2) {
+      const int Vn1[3] = {to_fixed(vn[0].hi, bad), to_fixed(vn[1].hi, bad),
+                          to_fixed(vn[2].hi, bad)};
+      const Shape2Mix<ORDER> S1(Xn + half_shift(Vn1[0], c), Yn + half_shift(Vn1[1], c), c.nx,
+                                c.ny);
+      deposit_j<ORDER>(c, b.J1, S1, Vn1);
+    }
+    b.X[p] = Xn;
+    b.Y[p] = Yn;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      b.vh[d][p] = vn[d].hi;
+      b.vl[d][p] = vn[d].lo;
+      if (!isfinite(vn[d].hi)) bad |= kErrNonfinite;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
+  if ((threadIdx.x & 31) == 0 && nfb) atomicAdd(&b.fallback[slot], (unsigned long long)nfb);
+  report_bad(bad, b.err);
+  const double t = block_sum2((double)ke_hi + (double)ke_lo, red);
+  if (threadIdx.x == 0) b.ke_part[blockIdx.x] = c.ke_scale * t;
+}
+
+// j^{n,*} of the current state (start-up and after a state change), the same
+// deposit pass E makes for the next step
+template <int ORDER>
+__global__ void __launch_bounds__(256) mix2_deposit_initial_kernel(Em2dMixConst c,
+                                                                   Em2dMixBufs b) {
+  unsigned bad = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int V[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) V[d] = to_fixed(b.vh[d][p], bad);
+    const Shape2Mix<ORDER> S(b.X[p] + half_shift(V[0], c), b.Y[p] + half_shift(V[1], c), c.nx,
+                             c.ny);
+    deposit_j<ORDER>(c, b.J1, S, V);
+  }
+  report_bad(bad, b.err);
+}
+
+__global__ void mix2_from_fp64_kernel(Em2dMixConst c, Em2dMixBufs mb, Em2dBufs b) {
+  const double *v[3] = {b.vx, b.vy, b.vz};
+  unsigned bad = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    mb.X[p] = (uint32_t)((unsigned long long)llrint(b.x[p] / c.L * 4294967296.0) & 0xFFFFFFFFull);
+    mb.Y[p] = (uint32_t)((unsigned long long)llrint(b.y[p] / c.L * 4294967296.0) & 0xFFFFFFFFull);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const double vv = v[d][p] * c.cxk;
+      if (!isfinite(vv)) bad |= kErrNonfinite;
+      if (!(fabs(vv) < 2147483520.0)) bad |= kErrVelocityRange;
+      const float h = (float)vv;
+      mb.vh[d][p] = h;
+      mb.vl[d][p] = (float)(vv - (double)h);
+    }
+  }
+  report_bad(bad, b.err);
+}
+
+__global__ void mix2_to_fp64_kernel(Em2dMixConst c, Em2dMixBufs mb, Em2dBufs b) {
+  double *v[3] = {b.vx, b.vy, b.vz};
+  const double inv = 1.0 / c.cxk;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    b.x[p] = (double)mb.X[p] * (c.L / 4294967296.0);
+    b.y[p] = (double)mb.Y[p] * (c.L / 4294967296.0);
+#pragma unroll
+    for (int d = 0; d < 3; d++) v[d][p] = ((double)mb.vh[d][p] + (double)mb.vl[d][p]) * inv;
+  }
+}
+
+__global__ void __launch_bounds__(256) mix2_kinetic_kernel(Em2dMixConst c, Em2dMixBufs mb,
+                                                           double *out) {
+  __shared__ double red[33];
+  double acc = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const double v = (double)mb.vh[d][p] + (double)mb.vl[d][p];
+      acc += v * v;
+    }
+  }
+  const double t = block_sum2(acc, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = c.ke_scale * t;
+}
+
+// max |v| over the three staging components (non-negative doubles order like
+// their bit patterns)
+__global__ void mix2_absmax_kernel(Em2dBufs b, int64_t n, unsigned long long *out) {
+  double m = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, fmax(fabs(b.vx[p]), fmax(fabs(b.vy[p]), fabs(b.vz[p]))));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+}  // namespace
+
+void em2dm_k1(const Em2dConst &c, const Em2dMixConst &m, const Em2dMixBufs &mb,
+              const Em2dBufs &b, LaunchShape lg, cudaStream_t st) {
+  mix2_k1_kernel<<<lg.grid, lg.block, 0, st>>>(c, m, mb, b);
+}
+
+void em2dm_k3(const Em2dConst &c, const Em2dMixConst &m, const Em2dMixBufs &mb,
+              const Em2dBufs &b, LaunchShape lg, cudaStream_t st) {
+  mix2_k3_kernel<<<lg.grid, lg.block, 0, st>>>(c, m, mb, b);
+}
+
+void em2dm_pass_c(const Em2dMixConst &m, const Em2dMixBufs &mb, LaunchShape lp, cudaStream_t st) {
+  if (m.order == 1)
+    mix2_pass_c_kernel<1><<<lp.grid, 256, 0, st>>>(m, mb);
+  else
+    mix2_pass_c_kernel<2><<<lp.grid, 256, 0, st>>>(m, mb);
+}
+
+void em2dm_pass_e(const Em2dMixConst &m, const Em2dMixBufs &mb, int slot, LaunchShape lp,
+                  cudaStream_t st) {
+  if (m.order == 1)
+    mix2_pass_e_kernel<1><<<lp.grid, 256, 0, st>>>(m, mb, slot);
+  else
+    mix2_pass_e_kernel<2><<<lp.grid, 256, 0, st>>>(m, mb, slot);
+}
+
+void em2dm_from_fp64(const Em2dMixConst &m, const Em2dMixBufs &mb, const Em2dBufs &b,
+                     LaunchShape lp, cudaStream_t st) {
+  mix2_from_fp64_kernel<<<lp.grid, 256, 0, st>>>(m, mb, b);
+}
+
+void em2dm_to_fp64(const Em2dMixConst &m, const Em2dMixBufs &mb, const Em2dBufs &b,
+                   LaunchShape lp, cudaStream_t st) {
+  mix2_to_fp64_kernel<<<lp.grid, 256, 0, st>>>(m, mb, b);
+}
+
+void em2dm_deposit_initial(const Em2dMixConst &m, const Em2dMixBufs &mb, LaunchShape lp,
+                           cudaStream_t st) {
+  if (m.order == 1)
+    mix2_deposit_initial_kernel<1><<<lp.grid, 256, 0, st>>>(m, mb);
+  else
+    mix2_deposit_initial_kernel<2><<<lp.grid, 256, 0, st>>>(m, mb);
+}
+
+void em2dm_kinetic(const Em2dMixConst &m, const Em2dMixBufs &mb, double *out, LaunchShape lp,
+                   cudaStream_t st) {
+  mix2_kinetic_kernel<<<lp.grid, 256, 0, st>>>(m, mb, out);
+}
+
+void em2dm_absmax(const Em2dBufs &b, int64_t n, unsigned long long *out, LaunchShape lp,
+                  cudaStream_t st) {
+  mix2_absmax_kernel<<<lp.grid, 256, 0, st>>>(b, n, out);
+}
+
+}  // namespace pic

@@ -42,6 +42,7 @@
 #include <type_traits>
 
 #include "ff.cuh"
+#include "mixed_common.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -126,11 +127,6 @@ __device__ __forceinline__ SplitTerm deposit_split(int V, int s, const Es1dMixCo
 // V units -> position units for half a step (kv >= 1)
 __device__ __forceinline__ uint32_t half_shift(int V, const Es1dMixConst &c) {
   return (uint32_t)((V + c.hround) >> c.kv);
-}
-
-__device__ __forceinline__ int to_fixed(float y, unsigned &bad) {
-  if (!(fabsf(y) < 2147483520.0f)) bad |= kErrVelocityRange;
-  return __float2int_rn(y);
 }
 
 // Shared-memory current tile.  Every padded node holds two 32-bit counters per
@@ -370,16 +366,6 @@ __device__ __forceinline__ void report_flags(unsigned bad, unsigned *err) {
   if ((threadIdx.x & 31u) == 0u && bad) atomicOr(err, bad);
 }
 
-// V* = rint(v^n + e) to one V unit: v^n is the pair (vh, vl), and above 2^24
-// a float cannot hold every integer, so the sum is split into an integer part
-// and an exact remainder.
-__device__ __forceinline__ int vstar_fixed(float vh, float vl, float e, unsigned &bad) {
-  const ff s = two_sum(vh, e);
-  const int vi = to_fixed(s.hi, bad);
-  const float rem = __fadd_rn(__fadd_rn(__fsub_rn(s.hi, (float)vi), s.lo), vl);
-  return vi + __float2int_rn(rem);
-}
-
 // Stores one table value into RE consecutive copies (RE = 16: 16-byte stores).
 template <int RE, typename T>
 __device__ __forceinline__ void store_copies(T *row, T v) {
@@ -429,20 +415,6 @@ __device__ __forceinline__ ff gather_kick(const float2 *El, const ShapeMix<ORDER
 // the series t/2 - t^2/8 + t^3/16 - 5t^4/128 (relative error < 2^-33) replaces
 // the correctly rounded sqrt and divide.  R < 0 is t < -1; that and v^dag = 0
 // (t not finite) fall back to Gamma = 1 and are counted.
-// a / b by one correction of the hardware reciprocal estimate r with the
-// exact FMA residual (Markstein's FMA division): q0 = a r, e = a - q0 b,
-// q = q0 + e r.  Before its final rounding q is within about 2^-44 |a/b| of
-// the quotient, so q is the correctly rounded quotient except next to a tie
-// (then one ulp off, either way).  b = 0 or a subnormal b give a non-finite or
-// huge q.
-__device__ __forceinline__ float div_rcp_residual(float a, float b) {
-  float r;
-  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(b));
-  const float q0 = __fmul_rn(a, r);
-  const float e = __fmaf_rn(-q0, b, a);
-  return __fmaf_rn(e, r, q0);
-}
-
 __device__ __forceinline__ ff correct_velocity(float vh, float vl, int Vs, ff d, bool on,
                                                unsigned &nfb) {
   const ff vd = ff_add(ff{vh, vl}, d);

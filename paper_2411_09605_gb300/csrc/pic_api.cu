@@ -103,6 +103,8 @@ struct pic_handle {
   bool em = false;
   Em2dConst ce{};
   Em2dBufs be{};
+  Em2dMixConst cme{};   // mixed form of the 2D3V path (em && mixed)
+  Em2dMixBufs bme{};
   LaunchShape lp{1, 256}, lg{1, 256};
   // 1D mixed-precision state
   bool mixed = false;
@@ -603,18 +605,94 @@ int restart_es1d(pic_handle *h, bool particles_changed) {
 }
 
 // Yee state change: validate markers, B^{n+1/2} from (E^n, B^{n-1/2}), j^{n,*}.
-int restart_em2d(pic_handle *h) {
+// The mixed form takes its markers from the FP64 staging arrays only when
+// they changed (markers_changed); otherwise its own state stays as it is.
+int restart_em2d(pic_handle *h, bool markers_changed = true) {
   Em2dBufs &b = h->be;
   const int64_t nc3 = 3 * (int64_t)h->ce.nx * h->ce.ny;
-  em2d_validate_kernel<<<h->lp.grid, 256, 0, h->st>>>(b.x, b.y, b.vx, b.vy, b.vz, h->N, h->ce.Lx,
-                                                       h->ce.Ly, b.err);
-  CUDA_TRY(cudaGetLastError());
+  if (markers_changed || !h->mixed) {
+    em2d_validate_kernel<<<h->lp.grid, 256, 0, h->st>>>(b.x, b.y, b.vx, b.vy, b.vz, h->N,
+                                                         h->ce.Lx, h->ce.Ly, b.err);
+    CUDA_TRY(cudaGetLastError());
+  }
   em2d_fp64_bhalf(h->ce, b.B, b.E, b.Bp, h->lg, h->st);
-  CUDA_TRY(cudaMemsetAsync(b.J1, 0, sizeof(double) * nc3, h->st));
-  CUDA_TRY(cudaMemsetAsync(b.J2, 0, sizeof(double) * nc3, h->st));
-  if (h->ce.scheme == 2) em2d_fp64_deposit_initial(h->ce, b, h->lp, h->st);
+  if (h->mixed) {
+    Em2dMixBufs &mb = h->bme;
+    if (markers_changed) em2dm_from_fp64(h->cme, mb, b, h->lp, h->st);
+    CUDA_TRY(cudaMemsetAsync(mb.J1, 0, sizeof(long long) * nc3, h->st));
+    CUDA_TRY(cudaMemsetAsync(mb.J2, 0, sizeof(long long) * nc3, h->st));
+    if (h->ce.scheme == 2) em2dm_deposit_initial(h->cme, mb, h->lp, h->st);
+  } else {
+    CUDA_TRY(cudaMemsetAsync(b.J1, 0, sizeof(double) * nc3, h->st));
+    CUDA_TRY(cudaMemsetAsync(b.J2, 0, sizeof(double) * nc3, h->st));
+    if (h->ce.scheme == 2) em2d_fp64_deposit_initial(h->ce, b, h->lp, h->st);
+  }
   CUDA_TRY(cudaGetLastError());
   return check_flags(h, "pic_init/pic_set_*");
+}
+
+// Mixed form of the 2D3V path: the velocity scale from the largest initial
+// speed, the deposit shift from the marker count, the per-marker state and
+// the float tables (the FP64 staging arrays hold the initial markers).
+int init_em2d_mixed(pic_handle *h) {
+  const Em2dConst &c = h->ce;
+  const SpeciesInfo &S = h->sp[0];
+  Em2dMixConst &m = h->cme;
+  Em2dMixBufs &mb = h->bme;
+  m.nx = c.nx;
+  m.ny = c.ny;
+  m.order = c.order;
+  m.scheme = c.scheme;
+  m.gamma_on = c.gamma_on;
+  m.n = h->N;
+  m.L = c.Lx;
+  m.dt = c.dt;
+  unsigned long long *mx = nullptr;
+  int rc;
+  if ((rc = h->alloc(&mx, 1))) return rc;
+  CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), h->st));
+  em2dm_absmax(h->be, h->N, mx, h->lp, h->st);
+  CUDA_TRY(cudaGetLastError());
+  unsigned long long bits = 0;
+  CUDA_TRY(cudaMemcpyAsync(&bits, mx, sizeof bits, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  double vmax;
+  memcpy(&vmax, &bits, sizeof vmax);
+  // V units of (dt 2^31 / L) 2^kv, with room for 8x the largest initial speed
+  // inside the 31-bit range; kv >= 1 keeps the half-step shift a rounded shift
+  const double cx = c.dt * 2147483648.0 / m.L;
+  const double vcap = std::max(8.0 * vmax, 1e-6 * m.L / c.dt);
+  const int kv = (int)std::floor(std::log2(1073741824.0 / (cx * vcap)));
+  m.kv = std::min(24, std::max(1, kv));
+  m.hround = 1 << (m.kv - 1);
+  m.cxk = std::ldexp(cx, m.kv);
+  // terms round(V* s_x s_y / 2^r) are below 2^(77 - r); with N < 2^bitlen
+  // markers every node sum stays below 2^62 for r = bitlen + 15 (and r >= 32
+  // for the split product in the kernels)
+  int bitlen = 0;
+  while (bitlen < 62 && ((int64_t)1 << bitlen) <= h->N) bitlen++;
+  m.rshift = std::max(32, bitlen + 15);
+  m.rnd = 1ll << (m.rshift - 1);
+  const double qm = S.q / S.m;
+  m.jscale = S.q * S.w0 * std::ldexp(1.0, m.rshift - 46) / (c.area * m.cxk);
+  m.ke_scale = 0.5 * S.m * S.w0 / (m.cxk * m.cxk);
+  m.e_half = 0.5 * c.dt * qm * m.cxk;
+  m.t_half = 0.5 * c.dt * qm;
+  m.kick = c.dt * qm * m.cxk;
+  m.m_full = c.dt * qm;
+  const size_t n = (size_t)h->N, nc3 = 3 * (size_t)c.nx * c.ny;
+  if ((rc = h->alloc(&mb.X, n)) || (rc = h->alloc(&mb.Y, n)) || (rc = h->alloc(&mb.J1, nc3)) ||
+      (rc = h->alloc(&mb.J2, nc3)) || (rc = h->alloc(&mb.T1, 2 * nc3)) ||
+      (rc = h->alloc(&mb.T2, nc3)) || (rc = h->alloc(&mb.B2, nc3)))
+    return rc;
+  for (int d = 0; d < 3; d++)
+    if ((rc = h->alloc(&mb.vh[d], n)) || (rc = h->alloc(&mb.vl[d], n)) ||
+        (rc = h->alloc(&mb.Vs[d], n)))
+      return rc;
+  mb.ke_part = h->be.ke_part;
+  mb.fallback = h->be.fallback;
+  mb.err = h->be.err;
+  return PIC_OK;
 }
 
 
@@ -654,9 +732,10 @@ int init_em2d(pic_handle *h, const pic_species *species, const double *E0, const
   h->lg.grid = (int)std::max<int64_t>(1, std::min<int64_t>((nc3 + 255) / 256, (int64_t)h->nsm * 4));
   int rc;
   if ((rc = h->alloc(&b.x, h->N)) || (rc = h->alloc(&b.y, h->N)) || (rc = h->alloc(&b.vx, h->N)) ||
-      (rc = h->alloc(&b.vy, h->N)) || (rc = h->alloc(&b.vz, h->N)) ||
-      (rc = h->alloc(&b.vsx, h->N)) || (rc = h->alloc(&b.vsy, h->N)) ||
-      (rc = h->alloc(&b.vsz, h->N)))
+      (rc = h->alloc(&b.vy, h->N)) || (rc = h->alloc(&b.vz, h->N)))
+    return rc;
+  if (!h->mixed && ((rc = h->alloc(&b.vsx, h->N)) || (rc = h->alloc(&b.vsy, h->N)) ||
+                    (rc = h->alloc(&b.vsz, h->N))))
     return rc;
   b.w = nullptr;
   if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;
@@ -703,6 +782,7 @@ int init_em2d(pic_handle *h, const pic_species *species, const double *E0, const
   if (E0) CUDA_TRY(cudaMemcpyAsync(b.E, E0, sizeof(double) * nc3, cudaMemcpyDefault, h->st));
   if (B0) CUDA_TRY(cudaMemcpyAsync(b.B, B0, sizeof(double) * nc3, cudaMemcpyDefault, h->st));
   CUDA_TRY(cudaStreamSynchronize(h->st));
+  if (h->mixed && (rc = init_em2d_mixed(h))) return rc;
   return restart_em2d(h);
 }
 
@@ -963,8 +1043,9 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
       return fail(PIC_ERR_ARG, "pic_init: Yee grid needs 4..8192 nodes per dimension");
     if (!(cfg->grid.L[0] > 0.0) || !(cfg->grid.L[1] > 0.0) || !(cfg->c > 0.0))
       return fail(PIC_ERR_ARG, "pic_init: Yee solver needs L > 0 and c > 0");
-    if (cfg->precision == PIC_PREC_MIXED)
-      return fail(PIC_ERR_UNSUPPORTED, "pic_init: the Yee solver runs in the FP64 form");
+    if (cfg->precision == PIC_PREC_MIXED && cfg->grid.L[0] != cfg->grid.L[1])
+      return fail(PIC_ERR_UNSUPPORTED, "pic_init: the mixed form of the Yee solver needs a "
+                                       "square domain (L[0] == L[1])");
   } else {
     return fail(PIC_ERR_ARG, "pic_init: unknown solver");
   }
@@ -1061,10 +1142,18 @@ int pic_step_async(pic_handle *h, int nsteps) {
   for (int k = 0; k < nsteps && h->em; k++) {
     Em2dBufs &e = h->be;
     const int slot = h->pending;
-    CUDA_TRY(h->timed_launch(4, [&] { em2d_k1(h->ce, e, h->lg, h->st); }));
-    CUDA_TRY(h->timed_launch(0, [&] { em2d_pass_c(h->ce, e, h->lp, h->st); }));
-    CUDA_TRY(h->timed_launch(4, [&] { em2d_k3(h->ce, e, h->lg, h->st); }));
-    CUDA_TRY(h->timed_launch(1, [&] { em2d_pass_e(h->ce, e, slot, h->lp, h->st); }));
+    if (h->mixed) {
+      const Em2dMixBufs &mb = h->bme;
+      CUDA_TRY(h->timed_launch(4, [&] { em2dm_k1(h->ce, h->cme, mb, e, h->lg, h->st); }));
+      CUDA_TRY(h->timed_launch(0, [&] { em2dm_pass_c(h->cme, mb, h->lp, h->st); }));
+      CUDA_TRY(h->timed_launch(4, [&] { em2dm_k3(h->ce, h->cme, mb, e, h->lg, h->st); }));
+      CUDA_TRY(h->timed_launch(1, [&] { em2dm_pass_e(h->cme, mb, slot, h->lp, h->st); }));
+    } else {
+      CUDA_TRY(h->timed_launch(4, [&] { em2d_k1(h->ce, e, h->lg, h->st); }));
+      CUDA_TRY(h->timed_launch(0, [&] { em2d_pass_c(h->ce, e, h->lp, h->st); }));
+      CUDA_TRY(h->timed_launch(4, [&] { em2d_k3(h->ce, e, h->lg, h->st); }));
+      CUDA_TRY(h->timed_launch(1, [&] { em2d_pass_e(h->ce, e, slot, h->lp, h->st); }));
+    }
     CUDA_TRY(h->timed_launch(4, [&] { em2d_k5(h->ce, e, h->lg, h->st); }));
     CUDA_TRY(h->timed_launch(2, [&] { em2d_finalize(h->ce, e, slot, h->lp, h->lg, h->st); }));
     h->launches += 6;
@@ -1192,7 +1281,10 @@ static int energy_em2d(pic_handle *h, double *KE_per_species, double *W_E, doubl
   const Em2dConst &c = h->ce;
   Em2dBufs &b = h->be;
   const int nb = h->lp.grid;
-  em2d_fp64_kinetic(c, b, b.ke_part, nb, h->st);
+  if (h->mixed)
+    em2dm_kinetic(h->cme, h->bme, b.ke_part, h->lp, h->st);
+  else
+    em2d_fp64_kinetic(c, b, b.ke_part, nb, h->st);
   CUDA_TRY(cudaGetLastError());
   const size_t nc3 = 3 * (size_t)c.nx * c.ny;
   std::vector<double> part((size_t)nb * h->nsp), e(nc3), bo(nc3), bp(nc3);
@@ -1344,6 +1436,10 @@ int pic_get_particles(pic_handle *h, int s, double *x, double *v) {
     return PIC_OK;
   }
   if (h->em) {
+    if (h->mixed) {
+      em2dm_to_fp64(h->cme, h->bme, h->be, h->lp, h->st);
+      CUDA_TRY(cudaGetLastError());
+    }
     const double *src[5] = {h->be.x, h->be.y, h->be.vx, h->be.vy, h->be.vz};
     for (int d = 0; d < 2 && x; d++)
       CUDA_TRY(cudaMemcpyAsync(x + d * S.n, src[d] + S.offset, sizeof(double) * S.n,
@@ -1457,7 +1553,7 @@ int pic_set_fields(pic_handle *h, const double *E, const double *B) {
     CUDA_TRY(cudaMemcpyAsync(h->be.E, E, sizeof(double) * nc3, cudaMemcpyDefault, h->st));
     CUDA_TRY(cudaMemcpyAsync(h->be.B, B, sizeof(double) * nc3, cudaMemcpyDefault, h->st));
     CUDA_TRY(cudaStreamSynchronize(h->st));
-    return restart_em2d(h);
+    return restart_em2d(h, false);
   }
   if (B) return fail(PIC_ERR_ARG, "pic_set_fields: B given for the electrostatic solver");
   CUDA_TRY(cudaMemcpyAsync(h->b1.E[h->steps_done & 1], E, sizeof(double) * h->c1.nc,

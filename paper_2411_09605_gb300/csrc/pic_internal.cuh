@@ -219,6 +219,42 @@ struct StdBufs {
   unsigned *err;
 };
 
+// Mixed form of the 2D3V Yee path (one species, uniform weight, square
+// domain): positions X, Y as 32-bit fixed point (x = X L / 2^32), velocities as
+// float pairs in V units (v cxk; one V unit moves a marker 2^-kv position units
+// in half a step), v* as integers V*, the currents as exact int64 sums of
+// round(V* s_x s_y / 2^rshift) (s: weights in units of 2^-23); the fields stay
+// FP64 on the grid, with float tables for the gathers.
+struct Em2dMixConst {
+  int nx, ny;
+  int order, scheme, gamma_on;
+  int kv, hround;      // V units -> half-step position shift: (V + hround) >> kv
+  int rshift;          // current term = round(V* s_x s_y / 2^rshift), rshift >= 32
+  long long rnd;       // 2^(rshift - 1)
+  int64_t n;
+  double L, dt;
+  double cxk;          // (dt 2^31 / L) 2^kv
+  double jscale;       // J = jscale * (integer node sum)
+  double ke_scale;     // (m w / 2) / cxk^2
+  double e_half;       // dt/2 (q/m) cxk: E* -> V units
+  double t_half;       // dt/2 (q/m): B -> the rotation vector t of v*
+  double kick;         // dt (q/m) cxk: E^{n+1/2} -> V units
+  double m_full;       // dt (q/m): (V* x B) -> V units
+};
+
+struct Em2dMixBufs {
+  uint32_t *X, *Y;                 // [N]
+  float *vh[3], *vl[3];            // [N] velocity pairs in V units
+  int *Vs[3];                      // [N] V* (pass C -> pass E)
+  long long *J1, *J2;              // [3][ny][nx] integer current sums
+  float *T1;                       // [6][ny][nx]: e_half E*, then t_half B^{n+1/2}
+  float2 *T2;                      // [3][ny][nx]: kick E^{n+1/2} as float pairs
+  float *B2;                       // [3][ny][nx]: m_full B^{n+1/2}
+  double *ke_part;                 // [particle blocks]
+  unsigned long long *fallback;
+  unsigned *err;
+};
+
 // Everything the 1D FP64 kernels touch.
 struct Es1dFp64Bufs {
   double *x, *v, *w;        // [N] SoA (w may be null)
@@ -304,6 +340,30 @@ void std_start(const StdConst &c, const StdBufs &b, LaunchShape lp, cudaStream_t
 // KE^n partials ke_out [nsp][lp.grid] (v^{n+1/2} formed, not stored) and W_E^n
 void std_energy(const StdConst &c, const StdBufs &b, double *ke_out, double *we, LaunchShape lp,
                 cudaStream_t st);
+
+// 2D3V Yee path, mixed form (em2d_mixed.cu); the FP64 fields live in Em2dBufs
+// and K5 / the finalize kernel of the FP64 form are shared.
+void em2dm_k1(const Em2dConst &c, const Em2dMixConst &m, const Em2dMixBufs &mb,
+              const Em2dBufs &b, LaunchShape lg, cudaStream_t st);
+void em2dm_k3(const Em2dConst &c, const Em2dMixConst &m, const Em2dMixBufs &mb,
+              const Em2dBufs &b, LaunchShape lg, cudaStream_t st);
+void em2dm_pass_c(const Em2dMixConst &m, const Em2dMixBufs &mb, LaunchShape lp, cudaStream_t st);
+void em2dm_pass_e(const Em2dMixConst &m, const Em2dMixBufs &mb, int slot, LaunchShape lp,
+                  cudaStream_t st);
+// FP64 staging (x, y, vx, vy, vz) <-> the mixed state
+void em2dm_from_fp64(const Em2dMixConst &m, const Em2dMixBufs &mb, const Em2dBufs &b,
+                     LaunchShape lp, cudaStream_t st);
+void em2dm_to_fp64(const Em2dMixConst &m, const Em2dMixBufs &mb, const Em2dBufs &b,
+                   LaunchShape lp, cudaStream_t st);
+// j^{n,*} of the current state into mb.J1 (cleared first by the caller)
+void em2dm_deposit_initial(const Em2dMixConst &m, const Em2dMixBufs &mb, LaunchShape lp,
+                           cudaStream_t st);
+// kinetic energy block partials (physical units) into out[lp.grid]
+void em2dm_kinetic(const Em2dMixConst &m, const Em2dMixBufs &mb, double *out, LaunchShape lp,
+                   cudaStream_t st);
+// largest |v| component of the FP64 staging velocities (bits of a double)
+void em2dm_absmax(const Em2dBufs &b, int64_t n, unsigned long long *out, LaunchShape lp,
+                  cudaStream_t st);
 
 // 1D2V spectral path (em1d_spectral.cu)
 // shared-memory opt-in and the twiddle / coefficient tables (b.tw, b.coef)

@@ -300,9 +300,10 @@ class Simulation:
 class Simulation2D:
     """Owner of one Yee-solver handle built from a ``workloads.Problem2D``."""
 
-    def __init__(self, prob, scheme=PIC_SCHEME_ESEC2, E0=None, B0=None, gamma_on=True):
+    def __init__(self, prob, scheme=PIC_SCHEME_ESEC2, E0=None, B0=None, gamma_on=True,
+                 precision=PIC_PREC_FP64):
         self.prob = prob
-        self.cfg = make_config(prob.nx, prob.Lx, prob.dt, prob.order, scheme, PIC_PREC_FP64,
+        self.cfg = make_config(prob.nx, prob.Lx, prob.dt, prob.order, scheme, precision,
                                solver=PIC_SOLVER_YEE_LEAPFROG, dim_x=2, dim_v=3, ny=prob.ny,
                                Ly=prob.Ly, c=prob.c, gamma_on=gamma_on)
         self.species = []

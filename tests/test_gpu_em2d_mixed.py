@@ -1,0 +1,192 @@
+"""Parity of the mixed-precision form of the 2D3V Yee path (Sec. 4.1, Eq.
+EMleapfrog) with the FP64 oracle and with the FP64 form, through the C ABI.
+
+The mixed form stores positions as 32-bit fixed point (L / 2^32), v* as an
+integer in units of 1 / cxk (cxk = 2^kv dt 2^31 / L), shape weights as
+integers of 2^-23 per axis and runs gather #1 (E*, B at x*) in FP32, so it
+follows the oracle to about 1e-7 of the scale per step, not 1e-11.  Bar (the
+same quanta as the 1D mixed form, over 10 steps): positions / L and velocities
+/ max|v| within 1e-6, except markers slower than 1% of max|v| (Gamma - 1 is as
+sensitive to v* as 1 / |v^dag|^2), held to 1e-4; E and B (2-norm relative)
+within 3e-6, since they integrate the weight quanta of every deposit.  Energy
+is conserved to the FP64 bound: runs without imaginary-Gamma fallbacks stay
+within max_n |TE^n - TE^0| / TE^0 <= 1e-11."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_09605_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-6
+TOL_F = 3e-6
+MIXED = 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2411_09605_gb300 import build
+    build.build()
+
+
+def _fields(prob, seed, amp=1e-3):
+    rng = np.random.default_rng(seed)
+    shape = (3, prob.ny, prob.nx)
+    return (np.ascontiguousarray(amp * rng.standard_normal(shape)),
+            np.ascontiguousarray(amp * rng.standard_normal(shape)))
+
+
+def _oracle(prob, scheme, steps, E0, B0):
+    cfg = O.EM2DConfig(nx=prob.nx, ny=prob.ny, Lx=prob.Lx, Ly=prob.Ly, order=prob.order,
+                       dt=prob.dt, c=prob.c, scheme=scheme)
+    sp = [O.Species2D(s.q, s.m, s.x.copy(), s.y.copy(), s.vx.copy(), s.vy.copy(), s.vz.copy(),
+                      None, s.w0) for s in prob.species]
+    E, B = E0.copy(), B0.copy()
+    nfb = []
+    for _ in range(steps):
+        nfb.append(sum(O.em2d_step(cfg, sp, E, B)))
+    s = sp[0]
+    return np.stack([s.x, s.y]), np.stack([s.vx, s.vy, s.vz]), E, B, np.array(nfb)
+
+
+def _gpu(prob, scheme, steps, E0, B0, precision=MIXED):
+    from paper_2411_09605_gb300 import pic
+    sim = pic.Simulation2D(prob, scheme=scheme, E0=E0, B0=B0, precision=precision)
+    try:
+        te0 = sim.energy()[3]
+        fb, te = sim.step(steps)
+        x, v = sim.particles(0)
+        E, B = sim.fields()
+        energy = sim.energy()
+    finally:
+        sim.close()
+    return x, v, E, B, fb, te, te0, energy
+
+
+def _diff(prob, ref, got):
+    (xr, vr, Er, Br), (xg, vg, Eg, Bg) = ref, got
+    d = np.abs(xr - xg) % prob.Lx
+    vmax = np.max(np.abs(vr))
+    slow = np.sqrt(np.sum(vr ** 2, axis=0)) < 0.01 * vmax
+    dv = np.max(np.abs(vr - vg), axis=0)
+    return {"x": np.max(np.minimum(d, prob.Lx - d)) / prob.Lx,
+            "v": np.max(dv[~slow], initial=0.0) / vmax,
+            "v_slow": np.max(dv[slow], initial=0.0) / vmax,
+            "E": np.linalg.norm(Er - Eg) / np.linalg.norm(Er),
+            "B": np.linalg.norm(Br - Bg) / np.linalg.norm(Br)}
+
+
+def _check(prob, scheme, steps=10, seed=0, fb_slack=0):
+    E0, B0 = _fields(prob, seed)
+    xr, vr, Er, Br, nfb_o = _oracle(prob, scheme, steps, E0, B0)
+    xg, vg, Eg, Bg, fb, te, te0, energy = _gpu(prob, scheme, steps, E0, B0)
+    d = _diff(prob, (xr, vr, Er, Br), (xg, vg, Eg, Bg))
+    assert d["x"] <= TOL and d["v"] <= TOL and d["v_slow"] <= 1e-4, d
+    assert d["E"] <= TOL_F and d["B"] <= TOL_F, d
+    assert np.sum(np.abs(nfb_o - fb)) <= fb_slack, (nfb_o, fb)
+    if fb.sum() == 0:
+        assert np.max(np.abs(te - te0)) / te0 <= 1e-11
+    assert abs(energy[3] - te[-1]) <= 1e-12 * te0
+    return d
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("order", [1, 2])
+def test_weibel_parity_mixed(scheme, order):
+    prob = W.weibel(nx=32, ny=24, ppc=8, L=6.4, order=order, vth_par=0.1, seed=1)
+    _check(prob, scheme, fb_slack=2 if scheme == 1 else 0)
+
+
+def test_ragged_marker_count_mixed():
+    prob = W.weibel(nx=16, ny=16, ppc=8, L=3.2, vth_par=0.2, seed=2)
+    s = prob.species[0]
+    keep = 16 * 16 * 8 - 77
+    s.x, s.y, s.vx, s.vy, s.vz = s.x[:keep], s.y[:keep], s.vx[:keep], s.vy[:keep], s.vz[:keep]
+    _check(prob, 2, seed=3)
+
+
+def test_weibel_full_size_mixed():
+    """The 128 x 128, 64-per-cell Weibel workload (1,048,576 markers), 3 steps,
+    against the oracle on the same markers."""
+    _check(W.weibel(seed=4), 2, steps=3, seed=5)
+
+
+def test_mixed_follows_fp64_form_full_size():
+    """The mixed form against the FP64 form on the GPU, same workload, 5 steps."""
+    prob = W.weibel(seed=6)
+    E0, B0 = _fields(prob, 7)
+    a = _gpu(prob, 2, 5, E0, B0, precision=0)
+    b = _gpu(prob, 2, 5, E0, B0)
+    d = _diff(prob, a[:4], b[:4])
+    assert d["x"] <= TOL and d["v"] <= TOL and d["v_slow"] <= 1e-4, d
+    assert d["E"] <= TOL_F and d["B"] <= TOL_F, d
+    assert np.max(np.abs(a[5] - b[5])) / a[6] <= 1e-6
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_mixed_energy_conservation_long(order):
+    prob = W.weibel(nx=32, ny=32, ppc=16, L=6.4, vth_par=0.1, order=order, seed=8)
+    E0, B0 = _fields(prob, 9)
+    _, _, _, _, fb, te, te0, _ = _gpu(prob, 2, 300, E0, B0)
+    assert fb.sum() == 0
+    assert np.max(np.abs(te - te0)) / te0 <= 1e-11
+
+
+def test_mixed_uniform_b_rotation():
+    """E = 0, uniform Bz, one zero-weight marker: the rotation angle of the
+    exact scheme, -2 atan((q/m) B dt / 2) per step, to the FP32 rounding of
+    gather #1, and |v| kept to the float pairs' precision (B does no work)."""
+    prob = W.weibel(nx=8, ny=8, ppc=1, L=4.0, seed=10)
+    s = prob.species[0]
+    s.x, s.y = np.array([1.1]), np.array([2.3])
+    s.vx, s.vy, s.vz = np.array([0.3]), np.array([-0.4]), np.array([0.25])
+    s.w0 = 0.0
+    prob.dt = 0.1
+    B0 = np.zeros((3, 8, 8))
+    B0[2] = 1.7
+    x, v, *_ = _gpu(prob, 2, 50, np.zeros((3, 8, 8)), B0)
+    th = -2.0 * math.atan(-1.0 * 1.7 * 0.1 / 2) * 50
+    ref = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]]) @ np.array([0.3, -0.4])
+    assert np.max(np.abs(v[:2, 0] - ref)) <= 2e-6
+    assert abs(np.sum(v[:, 0] ** 2) / (0.3 ** 2 + 0.4 ** 2 + 0.25 ** 2) - 1.0) <= 1e-13
+
+
+def test_mixed_state_changes():
+    """pic_set_fields keeps the markers; pic_set_particles replaces them; both
+    continue like an oracle started from the new state."""
+    from paper_2411_09605_gb300 import pic
+    prob = W.weibel(nx=16, ny=16, ppc=8, L=3.2, vth_par=0.1, seed=11)
+    other = W.weibel(nx=16, ny=16, ppc=8, L=3.2, vth_par=0.1, seed=12)
+    E0, B0 = _fields(prob, 13)
+    sim = pic.Simulation2D(prob, E0=E0, B0=B0, precision=MIXED)
+    try:
+        sim.step(3)
+        s = other.species[0]
+        pic.pic_set_particles(sim.h, 0, np.ascontiguousarray(np.stack([s.x, s.y])),
+                              np.ascontiguousarray(np.stack([s.vx, s.vy, s.vz])))
+        pic.pic_set_fields(sim.h, E0, B0)
+        sim.step(5)
+        xg, vg = sim.particles(0)
+        Eg, Bg = sim.fields()
+    finally:
+        sim.close()
+    xr, vr, Er, Br, _ = _oracle(other, 2, 5, E0, B0)
+    d = _diff(other, (xr, vr, Er, Br), (xg, vg, Eg, Bg))
+    assert d["x"] <= TOL and d["v"] <= TOL and d["E"] <= TOL_F and d["B"] <= TOL_F, d
+
+
+def test_mixed_restrictions():
+    from paper_2411_09605_gb300 import pic
+    prob = W.weibel(nx=16, ny=16, ppc=4, L=3.2, seed=14)
+    prob.Ly = 2.4
+    prob.species[0].y *= 0.75
+    with pytest.raises(pic.PicError) as ei:
+        pic.Simulation2D(prob, precision=MIXED)
+    assert ei.value.code == -7
+    prob = W.weibel(nx=16, ny=16, ppc=4, L=3.2, seed=15)
+    prob.species.append(W.weibel(nx=16, ny=16, ppc=2, L=3.2, seed=16).species[0])
+    with pytest.raises(pic.PicError) as ei:
+        pic.Simulation2D(prob, precision=MIXED)
+    assert ei.value.code == -7
