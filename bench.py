@@ -590,9 +590,11 @@ def run_weibel2d(args):
                 if name == "fp64":
                     kern[kname]["fp64_ginst_s"] = round(EM2D_FP64_INST_PER_MARKER[kind] * n / t / 1e9, 1)
                     kern[kname]["frac_fp64"] = round(kern[kname]["fp64_ginst_s"] / fp64_peak, 4)
-        dom = max(("pass_c", "pass_e"), key=lambda k: kern[k]["avg_us"])
+        dom = max(("pass_c", "pass_e"), key=lambda k: kern[k]["avg_us"]) if "pass_e" in kern else None
         dk = 1 if dom == "pass_e" else 0
-        if name == "fp64":
+        if dom is None:
+            roof = None                       # no profiled steps
+        elif name == "fp64":
             roof = {"bound": "alu", "kernel": dom, "achieved": kern[dom]["fp64_ginst_s"],
                     "peak": round(fp64_peak, 1), "unit": "Ginst/s (FP64 pipe)",
                     "frac": kern[dom]["frac_fp64"], "traffic": EM2D_TRAFFIC[(name, dk)],
