@@ -65,7 +65,7 @@ class _Species(C.Structure):
 class _EmCfg(C.Structure):
     _fields_ = [("nx", C.c_long), ("ny", C.c_long), ("Lx", C.c_double), ("Ly", C.c_double),
                 ("order", C.c_int), ("dt", C.c_double), ("c", C.c_double), ("scheme", C.c_int),
-                ("gamma_on", C.c_int)]
+                ("gamma_on", C.c_int), ("charge_conserving", C.c_int)]
 
 
 class _Species2d(C.Structure):
@@ -105,6 +105,8 @@ def _declare(L):
     L.orc_em2d_step.restype = C.c_int
     L.orc_em2d_energy.argtypes = [C.POINTER(_EmCfg), C.POINTER(_Species2d), C.c_int, _dp, _dp,
                                   _dp, _dp, _dp]
+    L.orc_em2d_gauss_residual.argtypes = [C.POINTER(_EmCfg), C.POINTER(_Species2d), C.c_int,
+                                          _dp, _dp, _dp]
     L.orc_binomial_filter.argtypes = [C.c_long, _dp, _dp]
     L.orc_std_field.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, C.c_int, _dp]
     L.orc_std_start.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, C.c_int, _dp]
@@ -305,10 +307,11 @@ class EM2DConfig:
     c: float = 1.0
     scheme: int = 2
     gamma_on: bool = True
+    charge_conserving: bool = False    # Sec. 3.5: mixed-degree shapes, path pieces
 
     def _c(self):
         return _EmCfg(self.nx, self.ny, self.Lx, self.Ly, self.order, self.dt, self.c,
-                      self.scheme, int(self.gamma_on))
+                      self.scheme, int(self.gamma_on), int(self.charge_conserving))
 
 
 @dataclass
@@ -368,6 +371,16 @@ def em2d_step(cfg: EM2DConfig, species: Sequence[Species2D], E: np.ndarray, B: n
                              _ptr(B), nfb)
     assert rc == 0
     return list(nfb)
+
+
+def em2d_gauss_residual(cfg: EM2DConfig, species: Sequence[Species2D], E):
+    """(rho, div_h E - rho) on the nodes, each [ny, nx]; rho with the bilinear shape."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    rho = np.zeros((cfg.ny, cfg.nx))
+    r = np.zeros((cfg.ny, cfg.nx))
+    lib().orc_em2d_gauss_residual(C.byref(cfg._c()), _sp2_array(species), len(species), _ptr(E),
+                                  _ptr(rho), _ptr(r))
+    return rho, r
 
 
 def em2d_energy(cfg: EM2DConfig, species: Sequence[Species2D], E, B):

@@ -44,11 +44,19 @@ static long imod(long a, long n) {
  * next B-spline, an extension the paper allows but does not test) -> nodes
  * i0-1, i0, i0+1 with i0 = floor(xi + 1/2), d = xi - i0 and weights
  * (1/2 (1/2 - d)^2, 3/4 - d^2, 1/2 (1/2 + d)^2).
+ * order 0: the box B0 -> node floor(xi + 1/2) with weight 1 (the shape of
+ * the charge-conserving current on a half-node axis, Sec. 3.5).
  * Returns the number of nodes (order + 1); idx is reduced modulo nc.
  * Pinned: partition of unity, linear-field reproduction, symmetry, and the
  * B-spline as the convolution of tents (test_oracle_shapes.py).
  */
 int orc_shape_weights(int order, double xi, long nc, long *idx, double *wt) {
+  if (order == 0) {
+    /* the box B0: weight 1 at the nearest node floor(xi + 1/2) */
+    idx[0] = imod((long)floor(xi + 0.5), nc);
+    wt[0] = 1.0;
+    return 1;
+  }
   if (order == 1) {
     double fl = floor(xi);
     double f = xi - fl;
@@ -809,6 +817,7 @@ typedef struct {
   int scheme;  /* 1 = ESEC1-type v*, 2 = the j^{n,*} / E* stage of Eq.
                   (EMleapfrog) */
   int gamma_on;
+  int charge_conserving;  /* 1: the shapes and path segments below (order 1) */
 } orc_em2d_cfg;
 
 typedef struct {
@@ -823,14 +832,25 @@ typedef struct {
 static const double OFFX_E[3] = {0.5, 0.0, 0.0}, OFFY_E[3] = {0.0, 0.5, 0.0};
 static const double OFFX_B[3] = {0.0, 0.5, 0.5}, OFFY_B[3] = {0.5, 0.0, 0.5};
 
-/* Tensor-product weights of component with offsets (ox, oy). */
+/*
+ * Tensor-product weights of component with offsets (ox, oy).  Charge-
+ * conserving option (Sec. 3.5): the charge uses the bilinear shape (degree 1
+ * in x and y, on the nodes (i, j)); for Eq. (detbal) to hold the current
+ * component along an axis needs the derivative of that shape, a degree-0 box
+ * on the half nodes, so each component takes degree 0 on the axes where it
+ * sits on half nodes and degree 1 where it sits on integer nodes: Jx, Ex
+ * B0(x) B1(y); Jy, Ey B1(x) B0(y); Jz, Ez B1(x) B1(y) (the B components by the
+ * same rule, which no conservation property involves).
+ */
 static int shape2d(const orc_em2d_cfg *g, double x, double y, double ox,
                    double oy, long *idx, double *wt) {
   long ix[3], iy[3];
   double wx[3], wy[3];
   double hx = g->Lx / (double)g->nx, hy = g->Ly / (double)g->ny;
-  int kx = orc_shape_weights(g->order, x / hx - ox, g->nx, ix, wx);
-  int ky = orc_shape_weights(g->order, y / hy - oy, g->ny, iy, wy);
+  int degx = g->charge_conserving ? (ox == 0.5 ? 0 : 1) : g->order;
+  int degy = g->charge_conserving ? (oy == 0.5 ? 0 : 1) : g->order;
+  int kx = orc_shape_weights(degx, x / hx - ox, g->nx, ix, wx);
+  int ky = orc_shape_weights(degy, y / hy - oy, g->ny, iy, wy);
   int k = 0;
   for (int b = 0; b < ky; b++)
     for (int a = 0; a < kx; a++) {
@@ -905,6 +925,80 @@ static void gather3(const orc_em2d_cfg *g, const double *F, const double *ox,
   }
 }
 
+static int cmp_double(const void *a, const void *b) {
+  double u = *(const double *)a, v = *(const double *)b;
+  return (u > v) - (u < v);
+}
+
+/*
+ * The straight path from (x0, y0) to (x0 + dx, y0 + dy) (not wrapped) cut at
+ * every grid line x = i hx and y = j hy it crosses (Sec. 3.5: the charge shape
+ * is then quadratic along each piece, so Eq. (detbal) holds piece by piece).
+ * Returns the number of pieces K and, in *s (malloc'd, K + 1 entries), the
+ * path parameters 0 = s_0 <= s_1 <= ... <= s_K = 1 of the cuts.
+ */
+static int path_cuts(const orc_em2d_cfg *g, double x0, double y0, double dx, double dy,
+                     double **s) {
+  double hx = g->Lx / (double)g->nx, hy = g->Ly / (double)g->ny;
+  long ax0 = (long)floor(x0 / hx), ax1 = (long)floor((x0 + dx) / hx);
+  long ay0 = (long)floor(y0 / hy), ay1 = (long)floor((y0 + dy) / hy);
+  long nxc = labs(ax1 - ax0), nyc = labs(ay1 - ay0);
+  double *t = (double *)malloc(sizeof(double) * (size_t)(nxc + nyc + 2));
+  long k = 0;
+  t[k++] = 0.0;
+  /* the lines between the start and end cells: i = ax0 + 1 .. ax1 moving up,
+     i = ax0 .. ax1 + 1 moving down */
+  for (long m = 1; m <= nxc; m++) {
+    long line = ax1 > ax0 ? ax0 + m : ax0 - m + 1;
+    t[k++] = (line * hx - x0) / dx;
+  }
+  for (long m = 1; m <= nyc; m++) {
+    long line = ay1 > ay0 ? ay0 + m : ay0 - m + 1;
+    t[k++] = (line * hy - y0) / dy;
+  }
+  qsort(t + 1, (size_t)(k - 1), sizeof(double), cmp_double);
+  t[k] = 1.0;
+  *s = t;
+  return (int)k;
+}
+
+/*
+ * Charge-conserving deposit of j^{*,n+1/2} for one marker moving from
+ * (x0, y0) by (dx, dy) = dt v*: the sum over the path's pieces of the piece's
+ * fraction times the shape at the piece's midpoint.
+ */
+static void deposit_path(const orc_em2d_cfg *g, double coef, const double u[3], double x0,
+                         double y0, double dx, double dy, double *J) {
+  long ncell = g->nx * g->ny;
+  double *s;
+  int K = path_cuts(g, x0, y0, dx, dy, &s);
+  for (int k = 0; k < K; k++) {
+    double tau = s[k + 1] - s[k], mid = 0.5 * (s[k] + s[k + 1]);
+    double mx = wrap(x0 + mid * dx, g->Lx), my = wrap(y0 + mid * dy, g->Ly);
+    for (int c = 0; c < 3; c++) {
+      long idx[9];
+      double wt[9];
+      int n = shape2d(g, mx, my, OFFX_E[c], OFFY_E[c], idx, wt);
+      for (int a = 0; a < n; a++) J[c * ncell + idx[a]] += coef * u[c] * tau * wt[a];
+    }
+  }
+  free(s);
+}
+
+/* The matching gather of E at the same pieces: sum_k tau_k E(midpoint_k). */
+static void gather_path(const orc_em2d_cfg *g, const double *F, double x0, double y0,
+                        double dx, double dy, double out[3]) {
+  double *s;
+  int K = path_cuts(g, x0, y0, dx, dy, &s);
+  out[0] = out[1] = out[2] = 0.0;
+  for (int k = 0; k < K; k++) {
+    double tau = s[k + 1] - s[k], mid = 0.5 * (s[k] + s[k + 1]), e[3];
+    gather3(g, F, OFFX_E, OFFY_E, wrap(x0 + mid * dx, g->Lx), wrap(y0 + mid * dy, g->Ly), e);
+    for (int c = 0; c < 3; c++) out[c] += tau * e[c];
+  }
+  free(s);
+}
+
 static void cross(const double a[3], const double b[3], double r[3]) {
   r[0] = a[1] * b[2] - a[2] * b[1];
   r[1] = a[2] * b[0] - a[0] * b[2];
@@ -938,7 +1032,10 @@ void orc_vstar_solve(const double u[3], const double t[3], double out[3]) {
  *   v^dag       = v^n + dt (q/m)(E^{n+1/2}_p + v* x B^{n+1/2}_p)
  *   v^{n+1}     = Gamma v^dag  (Eq. opt_solution; fallback Gamma := 1)
  * The B in v^dag is gathered at x^{n+1/2}, as in the electromagnetic
- * schemes of Secs. 3.4 and 4.1.  E (3 x ncell) and B (3 x ncell, holding
+ * schemes of Secs. 3.4 and 4.1.  With charge_conserving the deposit of
+ * j^{*,n+1/2} and the gather of E^{n+1/2} run over the pieces of the path
+ * x^n -> x^{n+1} (deposit_path, gather_path) with the same fractions and
+ * shapes, so the pairing of Eq. (exp_econs_simple) still holds.  E (3 x ncell) and B (3 x ncell, holding
  * B^{n-1/2} on entry and B^{n+1/2} on exit) are updated in place.
  */
 int orc_em2d_step(const orc_em2d_cfg *g, orc_species2d *sp, int nsp, double *E,
@@ -1014,7 +1111,16 @@ int orc_em2d_step(const orc_em2d_cfg *g, orc_species2d *sp, int nsp, double *E,
       xh[s][p] = wrap(S->x[p] + 0.5 * dt * vst[0], g->Lx);
       yh[s][p] = wrap(S->y[p] + 0.5 * dt * vst[1], g->Ly);
     }
-    deposit_em(g, S, n, xh[s], yh[s], vsx[s], vsy[s], vsz[s], J);
+    if (g->charge_conserving) {
+      double area = hx * hy;
+      for (long p = 0; p < n; p++) {
+        const double vst[3] = {vsx[s][p], vsy[s][p], vsz[s][p]};
+        deposit_path(g, S->q * wt2d(S, p) / area, vst, S->x[p], S->y[p], dt * vst[0],
+                     dt * vst[1], J);
+      }
+    } else {
+      deposit_em(g, S, n, xh[s], yh[s], vsx[s], vsy[s], vsz[s], J);
+    }
   }
   for (long a = 0; a < 3 * ncell; a++) {
     En[a] = E[a] + dt * (c2 * cB[a] - J[a]);
@@ -1027,7 +1133,10 @@ int orc_em2d_step(const orc_em2d_cfg *g, orc_species2d *sp, int nsp, double *E,
     long count = 0;
     for (long p = 0; p < S->n; p++) {
       double Ep[3], Bp[3], vxb[3], vdag[3];
-      gather3(g, Eh, OFFX_E, OFFY_E, xh[s][p], yh[s][p], Ep);
+      if (g->charge_conserving)
+        gather_path(g, Eh, S->x[p], S->y[p], dt * vsx[s][p], dt * vsy[s][p], Ep);
+      else
+        gather3(g, Eh, OFFX_E, OFFY_E, xh[s][p], yh[s][p], Ep);
       gather3(g, Bh, OFFX_B, OFFY_B, xh[s][p], yh[s][p], Bp);
       const double vn[3] = {S->vx[p], S->vy[p], S->vz[p]};
       const double vst[3] = {vsx[s][p], vsy[s][p], vsz[s][p]};
@@ -1105,6 +1214,37 @@ void orc_em2d_energy(const orc_em2d_cfg *g, const orc_species2d *sp, int nsp,
   for (long a = 0; a < 3 * ncell; a++) wb += (B[a] - g->dt * cE[a]) * B[a];
   *WB = 0.5 * g->c * g->c * area * wb;
   free(cE);
+}
+
+/*
+ * Charge density on the nodes (i, j) with the bilinear shape of the
+ * charge-conserving option: rho = sum_p q w B1(x/hx - i) B1(y/hy - j) / |h|,
+ * and the Gauss's-law residual r = div_h E - rho with the Yee divergence
+ * (Ex(i+1/2,j) - Ex(i-1/2,j)) / hx + (Ey(i,j+1/2) - Ey(i,j-1/2)) / hy.  With
+ * exact charge conservation (Sec. 3.5) r keeps its initial value.
+ */
+void orc_em2d_gauss_residual(const orc_em2d_cfg *g, const orc_species2d *sp, int nsp,
+                             const double *E, double *rho, double *r) {
+  long nx = g->nx, ny = g->ny, ncell = nx * ny;
+  double hx = g->Lx / (double)nx, hy = g->Ly / (double)ny, area = hx * hy;
+  for (long a = 0; a < ncell; a++) rho[a] = 0.0;
+  for (int s = 0; s < nsp; s++)
+    for (long p = 0; p < sp[s].n; p++) {
+      long ix[2], iy[2];
+      double wx[2], wy[2];
+      orc_shape_weights(1, sp[s].x[p] / hx, nx, ix, wx);
+      orc_shape_weights(1, sp[s].y[p] / hy, ny, iy, wy);
+      for (int b = 0; b < 2; b++)
+        for (int a = 0; a < 2; a++)
+          rho[iy[b] * nx + ix[a]] += sp[s].q * wt2d(&sp[s], p) * wx[a] * wy[b] / area;
+    }
+  const double *Ex = E, *Ey = E + ncell;
+  for (long j = 0; j < ny; j++)
+    for (long i = 0; i < nx; i++) {
+      long im = imod(i - 1, nx), jm = imod(j - 1, ny);
+      double div = (Ex[j * nx + i] - Ex[j * nx + im]) / hx + (Ey[j * nx + i] - Ey[jm * nx + i]) / hy;
+      r[j * nx + i] = div - rho[j * nx + i];
+    }
 }
 
 /* ------------------------------------------------------------------------ */
