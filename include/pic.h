@@ -151,6 +151,18 @@ typedef struct {
                             /* Gauss field is that of F rho.  Other solvers,  */
                             /* the mixed form and the no-alloc entry point:   */
                             /* must be 0.                                     */
+  int charge_conserving;    /* Yee solver, FP64, shape_order 1: 1 = exact     */
+                            /* charge conservation (Sec. 3.5, Eq. detbal).    */
+                            /* With the bilinear charge shape rho, each J/E   */
+                            /* component takes the tent on its integer-node   */
+                            /* axes and the degree-0 box on its half-node     */
+                            /* axes, and the deposit of j^{*,n+1/2} and the   */
+                            /* gather of E^{n+1/2} run over the pieces of the */
+                            /* path x^n -> x^{n+1} between grid lines; then   */
+                            /* div_h E - rho keeps its initial value and the  */
+                            /* energy identity is unchanged.  0 = the point   */
+                            /* shapes of shape_order.  Other solvers or forms */
+                            /* with 1: PIC_ERR_UNSUPPORTED.                   */
 } pic_config;
 
 typedef struct pic_handle pic_handle;

@@ -19,6 +19,15 @@
 //               (c^2/2)|h| sum Bp . B^{n+3/2} (the energy of the new state)
 // Fields stay in global memory (0.8 MB at 128 x 128, L2-resident); the
 // current is accumulated with FP64 global atomics.
+//
+// Charge-conserving option (Sec. 3.5, Eq. detbal; order 1): with the bilinear
+// charge shape, each component takes the tent on the axes where it sits on
+// integer nodes and the degree-0 box on the axes where it sits on half nodes
+// (Jx, Ex: box x tent; Jy, Ey: tent x box; Jz, Ez: tent x tent), and the
+// deposit of j^{*,n+1/2} and the gather of E^{n+1/2} sum, over the pieces of
+// the path x^n -> x^{n+1} between grid lines, the piece's fraction times the
+// shape at its midpoint.  The continuity equation then holds exactly with the
+// Yee divergence, and the energy pairing is unchanged.
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -38,12 +47,16 @@ __device__ __forceinline__ double wrapd(double y, double L, unsigned *err) {
 }
 
 // 1D B-spline weights of coordinate xi (cell units) on nodes i0 .. i0+ORDER
+// (ORDER 0: the box, weight 1 at the nearest node)
 template <int ORDER>
 struct W1 {
   int i0;
   double w[ORDER + 1];
   __device__ __forceinline__ void set(double xi) {
-    if (ORDER == 1) {
+    if (ORDER == 0) {
+      i0 = (int)floor(__dadd_rn(xi, 0.5));
+      w[0] = 1.0;
+    } else if (ORDER == 1) {
       double fl = floor(xi);
       double f = __dadd_rn(xi, -fl);
       i0 = (int)fl;
@@ -61,10 +74,12 @@ struct W1 {
   }
 };
 
-// Weights of a point for integer-node (I) and half-node (H) components in x, y.
-template <int ORDER>
+// Weights of a point for integer-node (I) and half-node (H) components in x,
+// y: order OI on integer-node axes, OH on half-node axes.
+template <int OI, int OH>
 struct Shape2 {
-  W1<ORDER> xI, xH, yI, yH;
+  W1<OI> xI, yI;
+  W1<OH> xH, yH;
   __device__ __forceinline__ Shape2(const Em2dConst &c, double x, double y) {
     const double xi = __dmul_rn(x, c.inv_hx), yi = __dmul_rn(y, c.inv_hy);
     xI.set(xi);
@@ -74,55 +89,104 @@ struct Shape2 {
   }
 };
 
-template <int ORDER>
-__device__ __forceinline__ double gather_c(const double *F, int nx, int ny, const W1<ORDER> &wx,
-                                           const W1<ORDER> &wy) {
+template <int OX, int OY>
+__device__ __forceinline__ double gather_c(const double *F, int nx, int ny, const W1<OX> &wx,
+                                           const W1<OY> &wy) {
   double s = 0.0;
 #pragma unroll
-  for (int b = 0; b <= ORDER; b++) {
+  for (int b = 0; b <= OY; b++) {
     const int row = wrapi(wy.i0 + b, ny) * nx;
     double r = 0.0;
 #pragma unroll
-    for (int a = 0; a <= ORDER; a++) r = fma(__ldg(&F[row + wrapi(wx.i0 + a, nx)]), wx.w[a], r);
+    for (int a = 0; a <= OX; a++) r = fma(__ldg(&F[row + wrapi(wx.i0 + a, nx)]), wx.w[a], r);
     s = fma(r, wy.w[b], s);
   }
   return s;
 }
 
-template <int ORDER>
-__device__ __forceinline__ void deposit_c(double *J, int nx, int ny, const W1<ORDER> &wx,
-                                          const W1<ORDER> &wy, double coef) {
+template <int OX, int OY>
+__device__ __forceinline__ void deposit_c(double *J, int nx, int ny, const W1<OX> &wx,
+                                          const W1<OY> &wy, double coef) {
 #pragma unroll
-  for (int b = 0; b <= ORDER; b++) {
+  for (int b = 0; b <= OY; b++) {
     const int row = wrapi(wy.i0 + b, ny) * nx;
     const double cb = coef * wy.w[b];
 #pragma unroll
-    for (int a = 0; a <= ORDER; a++) atomicAdd(&J[row + wrapi(wx.i0 + a, nx)], cb * wx.w[a]);
+    for (int a = 0; a <= OX; a++) atomicAdd(&J[row + wrapi(wx.i0 + a, nx)], cb * wx.w[a]);
   }
 }
 
 // E (Ex: H,I; Ey: I,H; Ez: I,I) and B (Bx: I,H; By: H,I; Bz: H,H) at a point
-template <int ORDER>
+template <int OI, int OH>
 __device__ __forceinline__ void gather_eb(const Em2dConst &c, const double *E, const double *B,
-                                          const Shape2<ORDER> &S, double e[3], double bb[3]) {
+                                          const Shape2<OI, OH> &S, double e[3], double bb[3]) {
   const int nx = c.nx, ny = c.ny, nc = c.nx * c.ny;
   if (E) {
-    e[0] = gather_c<ORDER>(E, nx, ny, S.xH, S.yI);
-    e[1] = gather_c<ORDER>(E + nc, nx, ny, S.xI, S.yH);
-    e[2] = gather_c<ORDER>(E + 2 * nc, nx, ny, S.xI, S.yI);
+    e[0] = gather_c<OH, OI>(E, nx, ny, S.xH, S.yI);
+    e[1] = gather_c<OI, OH>(E + nc, nx, ny, S.xI, S.yH);
+    e[2] = gather_c<OI, OI>(E + 2 * nc, nx, ny, S.xI, S.yI);
   }
-  bb[0] = gather_c<ORDER>(B, nx, ny, S.xI, S.yH);
-  bb[1] = gather_c<ORDER>(B + nc, nx, ny, S.xH, S.yI);
-  bb[2] = gather_c<ORDER>(B + 2 * nc, nx, ny, S.xH, S.yH);
+  if (B) {
+    bb[0] = gather_c<OI, OH>(B, nx, ny, S.xI, S.yH);
+    bb[1] = gather_c<OH, OI>(B + nc, nx, ny, S.xH, S.yI);
+    bb[2] = gather_c<OH, OH>(B + 2 * nc, nx, ny, S.xH, S.yH);
+  }
 }
 
-template <int ORDER>
-__device__ __forceinline__ void deposit_j(const Em2dConst &c, double *J, const Shape2<ORDER> &S,
+template <int OI, int OH>
+__device__ __forceinline__ void deposit_j(const Em2dConst &c, double *J, const Shape2<OI, OH> &S,
                                           double coef, const double u[3]) {
   const int nx = c.nx, ny = c.ny, nc = c.nx * c.ny;
-  deposit_c<ORDER>(J, nx, ny, S.xH, S.yI, coef * u[0]);
-  deposit_c<ORDER>(J + nc, nx, ny, S.xI, S.yH, coef * u[1]);
-  deposit_c<ORDER>(J + 2 * nc, nx, ny, S.xI, S.yI, coef * u[2]);
+  deposit_c<OH, OI>(J, nx, ny, S.xH, S.yI, coef * u[0]);
+  deposit_c<OI, OH>(J + nc, nx, ny, S.xI, S.yH, coef * u[1]);
+  deposit_c<OI, OI>(J + 2 * nc, nx, ny, S.xI, S.yI, coef * u[2]);
+}
+
+// Shape orders of a form: the order on both axis kinds, or for the
+// charge-conserving form the tent on integer-node and the box on half-node axes
+template <int ORDER, bool CC>
+struct Orders {
+  static constexpr int I = CC ? 1 : ORDER;
+  static constexpr int H = CC ? 0 : ORDER;
+};
+
+// The pieces of the straight path from (x0, y0) by (dx, dy) between the grid
+// lines x = i hx and y = j hy, in path order: f(tau, xm, ym) with the piece's
+// fraction of the path and its (wrapped) midpoint.  The lines of each axis are
+// met in order, so the two sequences of crossing parameters are merged; there
+// are 1 + (lines crossed) pieces.
+template <class F>
+__device__ __forceinline__ void for_pieces(const Em2dConst &c, double x0, double y0, double dx,
+                                           double dy, unsigned *err, F f) {
+  const double ax = x0 * c.inv_hx, bx = (x0 + dx) * c.inv_hx;   // in cells
+  const double ay = y0 * c.inv_hy, by = (y0 + dy) * c.inv_hy;
+  const double fx0 = floor(ax), fx1 = floor(bx), fy0 = floor(ay), fy1 = floor(by);
+  const int nxc = (int)fabs(fx1 - fx0), nyc = (int)fabs(fy1 - fy0);
+  const double stx = fx1 > fx0 ? 1.0 : -1.0, sty = fy1 > fy0 ? 1.0 : -1.0;
+  double lx = fx1 > fx0 ? fx0 + 1.0 : fx0;   // next line to cross on each axis
+  double ly = fy1 > fy0 ? fy0 + 1.0 : fy0;
+  int kx = 0, ky = 0;
+  double s0 = 0.0;
+  for (int it = 0; it <= nxc + nyc; it++) {
+    const double tx = kx < nxc ? (lx - ax) / (bx - ax) : 2.0;
+    const double ty = ky < nyc ? (ly - ay) / (by - ay) : 2.0;
+    double s1;
+    if (it == nxc + nyc) {
+      s1 = 1.0;
+    } else if (tx <= ty) {
+      s1 = fmin(tx, 1.0);
+      kx++;
+      lx += stx;
+    } else {
+      s1 = fmin(ty, 1.0);
+      ky++;
+      ly += sty;
+    }
+    s1 = fmax(s1, s0);
+    const double mid = 0.5 * (s0 + s1);
+    f(s1 - s0, wrapd(x0 + mid * dx, c.Lx, err), wrapd(y0 + mid * dy, c.Ly, err));
+    s0 = s1;
+  }
 }
 
 __device__ __forceinline__ int species_of2(const Em2dConst &c, int64_t p) {
@@ -131,17 +195,17 @@ __device__ __forceinline__ int species_of2(const Em2dConst &c, int64_t p) {
   return s;
 }
 
-// x*, E**, B at x*, v* and x^{n+1/2}, bit for bit the same in K2 and K4.
-template <int ORDER>
+// x*, E**, B at x*, v* and x^{n+1/2}.
+template <int OI, int OH>
 __device__ __forceinline__ void half_push_em(const Em2dConst &c, const Em2dBufs &b, int s,
                                              double x, double y, const double v[3], double vs[3],
                                              double &xh, double &yh) {
   const double hdt = 0.5 * c.dt;
   const double xs = wrapd(__fma_rn(hdt, v[0], x), c.Lx, b.err);
   const double ys = wrapd(__fma_rn(hdt, v[1], y), c.Ly, b.err);
-  Shape2<ORDER> S(c, xs, ys);
+  Shape2<OI, OH> S(c, xs, ys);
   double e[3], bb[3];
-  gather_eb<ORDER>(c, b.Es, b.Bp, S, e, bb);
+  gather_eb<OI, OH>(c, b.Es, b.Bp, S, e, bb);
   const double k = __dmul_rn(hdt, c.qm[s]);
   double u[3], t[3];
 #pragma unroll
@@ -208,24 +272,35 @@ __global__ void __launch_bounds__(256) em_k5_kernel(Em2dConst c, Em2dBufs b) {
   if (threadIdx.x == 0) b.wf_part[2 * blockIdx.x + 1] = t;
 }
 
-template <int ORDER>
+template <int ORDER, bool CC>
 __global__ void __launch_bounds__(256) em_pass_c_kernel(Em2dConst c, Em2dBufs b) {
+  constexpr int OI = Orders<ORDER, CC>::I, OH = Orders<ORDER, CC>::H;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n_total;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int s = species_of2(c, p);
+    const double x = b.x[p], y = b.y[p];
     const double v[3] = {b.vx[p], b.vy[p], b.vz[p]};
     double vs[3], xh, yh;
-    half_push_em<ORDER>(c, b, s, b.x[p], b.y[p], v, vs, xh, yh);
+    half_push_em<OI, OH>(c, b, s, x, y, v, vs, xh, yh);
     b.vsx[p] = vs[0];   // pass E forms x^{n+1/2} from v* with the same rounding
     b.vsy[p] = vs[1];
     b.vsz[p] = vs[2];
-    Shape2<ORDER> S(c, xh, yh);
-    deposit_j<ORDER>(c, b.J2, S, b.w ? c.q_a[s] * b.w[p] : c.qw_a[s], vs);
+    const double coef = b.w ? c.q_a[s] * b.w[p] : c.qw_a[s];
+    if (CC) {
+      for_pieces(c, x, y, c.dt * vs[0], c.dt * vs[1], b.err, [&](double tau, double xm, double ym) {
+        const Shape2<OI, OH> S(c, xm, ym);
+        deposit_j<OI, OH>(c, b.J2, S, coef * tau, vs);
+      });
+    } else {
+      const Shape2<OI, OH> S(c, xh, yh);
+      deposit_j<OI, OH>(c, b.J2, S, coef, vs);
+    }
   }
 }
 
-template <int ORDER>
+template <int ORDER, bool CC>
 __global__ void __launch_bounds__(256) em_pass_e_kernel(Em2dConst c, Em2dBufs b, int slot) {
+  constexpr int OI = Orders<ORDER, CC>::I, OH = Orders<ORDER, CC>::H;
   __shared__ double red[33];
   double ke = 0.0;
   unsigned nfb = 0;
@@ -238,9 +313,22 @@ __global__ void __launch_bounds__(256) em_pass_e_kernel(Em2dConst c, Em2dBufs b,
     const double hdt = 0.5 * c.dt;
     const double xh = wrapd(__fma_rn(hdt, vs[0], x), c.Lx, b.err);
     const double yh = wrapd(__fma_rn(hdt, vs[1], y), c.Ly, b.err);
-    Shape2<ORDER> S(c, xh, yh);
+    Shape2<OI, OH> S(c, xh, yh);
     double e[3], bb[3];
-    gather_eb<ORDER>(c, b.Eh, b.Bp, S, e, bb);
+    if (CC) {
+      // E^{n+1/2} over the path's pieces with the deposit's fractions and shapes
+      gather_eb<OI, OH>(c, nullptr, b.Bp, S, e, bb);
+      e[0] = e[1] = e[2] = 0.0;
+      for_pieces(c, x, y, c.dt * vs[0], c.dt * vs[1], b.err, [&](double tau, double xm, double ym) {
+        const Shape2<OI, OH> Sm(c, xm, ym);
+        double ek[3];
+        gather_eb<OI, OH>(c, b.Eh, nullptr, Sm, ek, nullptr);
+#pragma unroll
+        for (int d = 0; d < 3; d++) e[d] += tau * ek[d];
+      });
+    } else {
+      gather_eb<OI, OH>(c, b.Eh, b.Bp, S, e, bb);
+    }
     const double k = c.dt * c.qm[s];
     const double vxb[3] = {vs[1] * bb[2] - vs[2] * bb[1], vs[2] * bb[0] - vs[0] * bb[2],
                            vs[0] * bb[1] - vs[1] * bb[0]};
@@ -267,8 +355,8 @@ __global__ void __launch_bounds__(256) em_pass_e_kernel(Em2dConst c, Em2dBufs b,
     if (c.scheme == 2) {
       const double xs2 = wrapd(xn + 0.5 * c.dt * vn[0], c.Lx, b.err);
       const double ys2 = wrapd(yn + 0.5 * c.dt * vn[1], c.Ly, b.err);
-      Shape2<ORDER> S2(c, xs2, ys2);
-      deposit_j<ORDER>(c, b.J1, S2, b.w ? c.q_a[s] * wp : c.qw_a[s], vn);
+      Shape2<OI, OH> S2(c, xs2, ys2);
+      deposit_j<OI, OH>(c, b.J1, S2, b.w ? c.q_a[s] * wp : c.qw_a[s], vn);
     }
     b.x[p] = xn;
     b.y[p] = yn;
@@ -284,16 +372,17 @@ __global__ void __launch_bounds__(256) em_pass_e_kernel(Em2dConst c, Em2dBufs b,
 }
 
 // j^{n,*} of the current state (start-up and after a state change)
-template <int ORDER>
+template <int ORDER, bool CC>
 __global__ void __launch_bounds__(256) em_deposit_initial_kernel(Em2dConst c, Em2dBufs b) {
+  constexpr int OI = Orders<ORDER, CC>::I, OH = Orders<ORDER, CC>::H;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n_total;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int s = species_of2(c, p);
     const double v[3] = {b.vx[p], b.vy[p], b.vz[p]};
     const double xs = wrapd(b.x[p] + 0.5 * c.dt * v[0], c.Lx, b.err);
     const double ys = wrapd(b.y[p] + 0.5 * c.dt * v[1], c.Ly, b.err);
-    Shape2<ORDER> S(c, xs, ys);
-    deposit_j<ORDER>(c, b.J1, S, b.w ? c.q_a[s] * b.w[p] : c.qw_a[s], v);
+    Shape2<OI, OH> S(c, xs, ys);
+    deposit_j<OI, OH>(c, b.J1, S, b.w ? c.q_a[s] * b.w[p] : c.qw_a[s], v);
   }
 }
 
@@ -347,10 +436,12 @@ void em2d_k1(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t
 }
 
 void em2d_pass_c(const Em2dConst &c, const Em2dBufs &b, LaunchShape lp, cudaStream_t st) {
-  if (c.order == 1)
-    em_pass_c_kernel<1><<<lp.grid, lp.block, 0, st>>>(c, b);
+  if (c.cc)
+    em_pass_c_kernel<1, true><<<lp.grid, lp.block, 0, st>>>(c, b);
+  else if (c.order == 1)
+    em_pass_c_kernel<1, false><<<lp.grid, lp.block, 0, st>>>(c, b);
   else
-    em_pass_c_kernel<2><<<lp.grid, lp.block, 0, st>>>(c, b);
+    em_pass_c_kernel<2, false><<<lp.grid, lp.block, 0, st>>>(c, b);
 }
 
 void em2d_k3(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st) {
@@ -359,10 +450,12 @@ void em2d_k3(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t
 
 void em2d_pass_e(const Em2dConst &c, const Em2dBufs &b, int slot, LaunchShape lp,
                  cudaStream_t st) {
-  if (c.order == 1)
-    em_pass_e_kernel<1><<<lp.grid, lp.block, 0, st>>>(c, b, slot);
+  if (c.cc)
+    em_pass_e_kernel<1, true><<<lp.grid, lp.block, 0, st>>>(c, b, slot);
+  else if (c.order == 1)
+    em_pass_e_kernel<1, false><<<lp.grid, lp.block, 0, st>>>(c, b, slot);
   else
-    em_pass_e_kernel<2><<<lp.grid, lp.block, 0, st>>>(c, b, slot);
+    em_pass_e_kernel<2, false><<<lp.grid, lp.block, 0, st>>>(c, b, slot);
 }
 
 void em2d_k5(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st) {
@@ -387,10 +480,12 @@ __global__ void em2d_validate_kernel(const double *x, const double *y, const dou
 
 void em2d_fp64_deposit_initial(const Em2dConst &c, const Em2dBufs &b, LaunchShape lp,
                                cudaStream_t st) {
-  if (c.order == 1)
-    em_deposit_initial_kernel<1><<<lp.grid, lp.block, 0, st>>>(c, b);
+  if (c.cc)
+    em_deposit_initial_kernel<1, true><<<lp.grid, lp.block, 0, st>>>(c, b);
+  else if (c.order == 1)
+    em_deposit_initial_kernel<1, false><<<lp.grid, lp.block, 0, st>>>(c, b);
   else
-    em_deposit_initial_kernel<2><<<lp.grid, lp.block, 0, st>>>(c, b);
+    em_deposit_initial_kernel<2, false><<<lp.grid, lp.block, 0, st>>>(c, b);
 }
 
 void em2d_fp64_bhalf(const Em2dConst &c, const double *B, const double *E, double *Bp,

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(512) pass_c_kernel(Es1dConst c, Es1dFp64Bufs b
     double x = b.x[p], v = b.v[p];
     double vs, xh;
     half_push<ORDER>(c, Es, x, v, c.qm[s], b.err, vs, xh);
-    b.vs[p] = vs;   // pass E forms x^{n+1/2} from it with the same rounding
+    if (b.vs) b.vs[p] = vs;   // pass E forms x^{n+1/2} from it with the same rounding
     double coef = (b.w ? c.q_h[s] * b.w[p] : c.qw_h[s]) * vs;
     Shape64<ORDER> S(__dmul_rn(xh, c.inv_h), c.nc);
     S.deposit(Jt, coef);
@@ -224,9 +224,16 @@ __global__ void __launch_bounds__(512) pass_e_kernel(Es1dConst c, Es1dFp64Bufs b
     int s = species_of(c, p);
     double x = b.x[p], v = b.v[p];
     double qm = c.qm[s];
-    // v* from pass C; x^{n+1/2} with the rounding half_push used for the deposit
-    const double vs = b.vs[p];
-    const double xh = wrap_periodic(__fma_rn(hdt, vs, x), c.L, b.err);
+    // v* from pass C and x^{n+1/2} with the rounding half_push used for the
+    // deposit; without the v* array (the entry point without allocation),
+    // half_push again on the same E* table, which gives the same bits
+    double vs, xh;
+    if (b.vs) {
+      vs = b.vs[p];
+      xh = wrap_periodic(__fma_rn(hdt, vs, x), c.L, b.err);
+    } else {
+      half_push<ORDER>(c, Es, x, v, qm, b.err, vs, xh);
+    }
     Shape64<ORDER> Sh(__dmul_rn(xh, c.inv_h), c.nc);
     double Ep = Sh.gather(Eh);
     double vd = v + c.dt * qm * Ep;

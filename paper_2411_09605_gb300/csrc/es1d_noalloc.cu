@@ -29,7 +29,9 @@ namespace {
 
 // Scratch layout (bytes): E_alt, J1[2], J2[2] (8192 doubles each), block
 // partials (1024 doubles), per-step energies (1024 doubles), W_E (1 double),
-// per-step fallback counters (1024 x u64), device error flags.
+// per-step fallback counters (1024 x u64), device error flags.  v* is not
+// kept between the passes (that would take N doubles): the buffer's v* array
+// stays null and pass E recomputes v* from the same E* table.
 constexpr int kNoallocMaxNodes = kMaxNodes1D;
 constexpr int kNoallocMaxSteps = 1024;
 constexpr int kNoallocMaxBlocks = 1024;
@@ -82,10 +84,10 @@ extern "C" int pic_es1d_step_noalloc(const pic_config *cfg, double q, double m, 
                                      int64_t *nfallback_per_step, double *te_per_step) {
   if (!cfg) return noalloc_fail(PIC_ERR_ARG, "pic_es1d_step_noalloc: cfg is NULL");
   if (cfg->solver != PIC_SOLVER_AMPERE_ES || cfg->grid.dim_x != 1 || cfg->grid.dim_v != 1 ||
-      cfg->precision != PIC_PREC_FP64 || cfg->binomial_passes != 0)
+      cfg->precision != PIC_PREC_FP64 || cfg->binomial_passes != 0 || cfg->charge_conserving != 0)
     return noalloc_fail(PIC_ERR_ARG,
                         "pic_es1d_step_noalloc: needs the 1D1V Ampere solver in FP64 form, "
-                        "without filtering (binomial_passes = 0)");
+                        "without filtering (binomial_passes = 0, charge_conserving = 0)");
   const int64_t nc = cfg->grid.n[0];
   if (nc < 4 || nc > kNoallocMaxNodes)
     return noalloc_fail(PIC_ERR_ARG, "pic_es1d_step_noalloc: grid must have 4..8192 nodes "

@@ -704,6 +704,7 @@ int init_em2d(pic_handle *h, const pic_species *species, const double *E0, const
   c.nx = (int)cfg.grid.n[0];
   c.ny = (int)cfg.grid.n[1];
   c.order = cfg.shape_order;
+  c.cc = cfg.charge_conserving;
   c.scheme = cfg.scheme;
   c.gamma_on = cfg.gamma_on;
   c.nsp = h->nsp;
@@ -1000,6 +1001,13 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
     return fail(PIC_ERR_ARG, "pic_init: unknown precision");
   if (cfg->binomial_passes < 0 || cfg->binomial_passes > 8)
     return fail(PIC_ERR_ARG, "pic_init: binomial_passes must be in [0, 8]");
+  if (cfg->charge_conserving != 0 && cfg->charge_conserving != 1)
+    return fail(PIC_ERR_ARG, "pic_init: charge_conserving must be 0 or 1");
+  if (cfg->charge_conserving &&
+      (cfg->solver != PIC_SOLVER_YEE_LEAPFROG || cfg->precision != PIC_PREC_FP64 ||
+       cfg->shape_order != 1))
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: charge_conserving runs the Yee solver in the FP64 "
+                                     "form with shape_order 1");
   if (cfg->binomial_passes != 0 &&
       !(cfg->solver == PIC_SOLVER_STANDARD_LEAPFROG ||
         (cfg->solver == PIC_SOLVER_AMPERE_ES && cfg->precision == PIC_PREC_FP64)))

@@ -112,6 +112,7 @@ struct Es1dMixBufs {
 struct Em2dConst {
   int nx, ny;
   int order;
+  int cc;          // charge-conserving shapes and path pieces (order 1)
   int scheme;
   int gamma_on;
   int nsp;
@@ -258,7 +259,8 @@ struct Em2dMixBufs {
 // Everything the 1D FP64 kernels touch.
 struct Es1dFp64Bufs {
   double *x, *v, *w;        // [N] SoA (w may be null)
-  double *vs;               // [N] v* of the current step (pass C -> pass E)
+  double *vs;               // [N] v* of the current step (pass C -> pass E), or null:
+                            // pass E then recomputes it (the same bits)
   double *E[2];             // ping-pong E^n / E^{n+1}
   double *J1[2];            // j^{n,*} (ESEC2), indexed by step parity
   double *J2[2];            // j^{*,n+1/2}

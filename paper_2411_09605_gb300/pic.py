@@ -59,7 +59,8 @@ class pic_config(C.Structure):
                 ("c", C.c_double), ("solver", C.c_int), ("scheme", C.c_int),
                 ("precision", C.c_int), ("sort_period", C.c_int), ("remove_mean", C.c_int),
                 ("gamma_on", C.c_int), ("ptr_on_device", C.c_int), ("cuda_stream", C.c_void_p),
-                ("skip_ids", C.c_int), ("binomial_passes", C.c_int)]
+                ("skip_ids", C.c_int), ("binomial_passes", C.c_int),
+                ("charge_conserving", C.c_int)]
 
 
 _lib = None
@@ -137,11 +138,11 @@ def _addr(a) -> Optional[int]:
 def make_config(nc, L, dt, order=1, scheme=PIC_SCHEME_ESEC2, precision=PIC_PREC_FP64,
                 solver=PIC_SOLVER_AMPERE_ES, dim_x=1, dim_v=1, ny=0, Ly=0.0, c=1.0,
                 sort_period=0, remove_mean=1, gamma_on=1, ptr_on_device=0, stream=None,
-                skip_ids=0, binomial_passes=0):
+                skip_ids=0, binomial_passes=0, charge_conserving=0):
     g = pic_grid(dim_x, dim_v, (C.c_int64 * 2)(nc, ny), (C.c_double * 2)(L, Ly))
     return pic_config(g, order, dt, c, solver, scheme, precision, sort_period, int(remove_mean),
                       int(gamma_on), int(ptr_on_device), stream, int(skip_ids),
-                      int(binomial_passes))
+                      int(binomial_passes), int(charge_conserving))
 
 
 def pic_init(cfg: pic_config, species: Sequence[dict], E0=None, B0=None) -> int:
@@ -301,11 +302,12 @@ class Simulation2D:
     """Owner of one Yee-solver handle built from a ``workloads.Problem2D``."""
 
     def __init__(self, prob, scheme=PIC_SCHEME_ESEC2, E0=None, B0=None, gamma_on=True,
-                 precision=PIC_PREC_FP64):
+                 precision=PIC_PREC_FP64, charge_conserving=False):
         self.prob = prob
         self.cfg = make_config(prob.nx, prob.Lx, prob.dt, prob.order, scheme, precision,
                                solver=PIC_SOLVER_YEE_LEAPFROG, dim_x=2, dim_v=3, ny=prob.ny,
-                               Ly=prob.Ly, c=prob.c, gamma_on=gamma_on)
+                               Ly=prob.Ly, c=prob.c, gamma_on=gamma_on,
+                               charge_conserving=charge_conserving)
         self.species = []
         for s in prob.species:
             x = np.ascontiguousarray(np.stack([s.x, s.y]), dtype=np.float64)
