@@ -448,6 +448,66 @@ __device__ __forceinline__ ff correct_velocity(float vh, float vl, int Vs, ff d,
   return ff_add(vd, p);
 }
 
+// gather_kick for two markers at once (lane x: S0, lane y: S1), packed FP32
+template <int ORDER, int RE>
+__device__ __forceinline__ ff2 gather_kick2(const float2 *El, const ShapeMix<ORDER> &S0,
+                                            const ShapeMix<ORDER> &S1) {
+  float2 ph[ORDER + 1], pl = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int k = 0; k <= ORDER; k++) {
+    const float2 e0 = El[(S0.p + k) * RE], e1 = El[(S1.p + k) * RE];
+    const float2 w = make_float2(S0.w[k], S1.w[k]);
+    const ff2 p = two_prod2(make_float2(e0.x, e1.x), w);
+    ph[k] = p.hi;
+    pl = add2(pl, fma2(make_float2(e0.y, e1.y), w, p.lo));
+  }
+  ff2 Ep = two_sum2(ph[0], ph[1]);
+  pl = add2(pl, Ep.lo);
+  if (ORDER == 2) {
+    Ep = two_sum2(Ep.hi, ph[ORDER]);
+    pl = add2(pl, Ep.lo);
+  }
+  return fast_two_sum2(Ep.hi, pl);
+}
+
+// correct_velocity for two markers at once.  The packed path covers the
+// common case, both markers corrected with |t| < 2^-8; any other pair runs
+// correct_velocity per marker, so each lane gets exactly the scalar result.
+__device__ __forceinline__ ff2 correct_velocity2(float2 vh, float2 vl, int Vs0, int Vs1, ff2 d,
+                                                 bool on0, bool on1, unsigned &nfb) {
+  const ff2 vd = ff_add2(ff2{vh, vl}, d);
+  bool packed = on0 && on1;
+  float2 gm = make_float2(0.0f, 0.0f);
+  if (packed) {
+    const int ih0 = __float2int_rn(vh.x), ih1 = __float2int_rn(vh.y);
+    const float2 fr = sub2(vh, make_float2(__int2float_rn(ih0), __int2float_rn(ih1)));
+    const ff2 q = two_sum2(make_float2(__int2float_rn(Vs0 - ih0), __int2float_rn(Vs1 - ih1)),
+                           mul2(splat2(-0.5f), d.hi));
+    const float2 small = sub2(sub2(sub2(q.lo, fr), vl), mul2(splat2(0.5f), d.lo));
+    const float2 bq = add2(q.hi, small);
+    // t = a / b by div_rcp_residual, lane by lane
+    const float2 a = mul2(add2(d.hi, d.hi), bq), b = mul2(vd.hi, vd.hi);
+    float2 r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r.x) : "f"(b.x));
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r.y) : "f"(b.y));
+    const float2 q0 = mul2(a, r);
+    const float2 t = fma2(fma2(neg2(q0), b, a), r, q0);
+    packed = fabsf(t.x) < 0.00390625f && fabsf(t.y) < 0.00390625f;
+    if (packed)
+      gm = mul2(t, fma2(t, fma2(t, fma2(t, splat2(-0.0390625f), splat2(0.0625f)), splat2(-0.125f)),
+                        splat2(0.5f)));
+  }
+  if (!packed) {
+    const ff v0 = correct_velocity(vh.x, vl.x, Vs0, ff{d.hi.x, d.lo.x}, on0, nfb);
+    const ff v1 = correct_velocity(vh.y, vl.y, Vs1, ff{d.hi.y, d.lo.y}, on1, nfb);
+    return ff2{make_float2(v0.hi, v1.hi), make_float2(v0.lo, v1.lo)};
+  }
+  ff2 p = two_prod2(vd.hi, gm);
+  p.lo = fma2(vd.lo, gm, p.lo);
+  const ff2 s = fast_two_sum2(vd.hi, p.hi);
+  return fast_two_sum2(s.hi, add2(s.lo, add2(vd.lo, p.lo)));
+}
+
 // Adds a 64-bit padded tile to J[node stride] with one global atomic per node
 // and, when total is not null, the tile's sum to *total.
 template <int ORDER>
@@ -706,56 +766,69 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
   const unsigned lane = threadIdx.x & 31u;
   unsigned *Jl = Jt + (lane & (RT - 1));
   const float2 *El = Eh2 + (lane & (RE - 1));
-  float ke_hi = 0.0f, ke_lo = 0.0f;
+  // kinetic sums of the even (x) and odd (y) markers of each group
+  float2 ke2h = make_float2(0.0f, 0.0f), ke2l = make_float2(0.0f, 0.0f);
   unsigned nfb = 0, bad = 0;
   constexpr int G = kGroupE;
+  static_assert(G % 2 == 0, "markers are processed in pairs");
   for_groups<G, true, !AGG && kPrefetchE>(b, c.n, P, [&](auto check, int64_t g, const MarkerGroup<G> &m, int64_t end) {
     constexpr bool CHECK = decltype(check)::value;
     const bool gv = !CHECK || g < end;
     MarkerGroup<G> o;
     DepositWindow<ORDER> win;
 #pragma unroll
-    for (int j = 0; j < G; j++) {
-      const uint32_t X = m.X[j];
-      const float vh = m.vh[j], vl = m.vl[j];
-      const int Vs = m.V[j];
-      const bool valid = !CHECK || (gv && G * g + j < c.n);
-      const uint32_t hs = half_shift(Vs, c);
-      // gather #2 at x^{n+1/2}: d = dt (q/m) E^{n+1/2}_p in V units
-      const ShapeMix<ORDER> Sh(X + hs, c.nc);
-      const ff d = gather_kick<ORDER, RE>(El, Sh);
-      const ff vn = correct_velocity(vh, vl, Vs, d, c.gamma_on && valid, nfb);
-      if (valid) {
-        ff s2 = two_prod(vn.hi, vn.hi);
-        s2.lo = __fmaf_rn(__fadd_rn(vn.hi, vn.hi), vn.lo, s2.lo);
-        const ff acc = two_sum(ke_hi, s2.hi);
-        ke_hi = acc.hi;
-        ke_lo = __fadd_rn(ke_lo, __fadd_rn(acc.lo, s2.lo));
+    for (int j = 0; j < G; j += 2) {
+      const bool valid0 = !CHECK || (gv && G * g + j < c.n);
+      const bool valid1 = !CHECK || (gv && G * g + j + 1 < c.n);
+      const uint32_t hs0 = half_shift(m.V[j], c), hs1 = half_shift(m.V[j + 1], c);
+      // gather #2 at x^{n+1/2}: d = dt (q/m) E^{n+1/2}_p in V units, two markers at once
+      const ShapeMix<ORDER> Sh0(m.X[j] + hs0, c.nc), Sh1(m.X[j + 1] + hs1, c.nc);
+      const ff2 d = gather_kick2<ORDER, RE>(El, Sh0, Sh1);
+      const ff2 vn2 = correct_velocity2(make_float2(m.vh[j], m.vh[j + 1]),
+                                        make_float2(m.vl[j], m.vl[j + 1]), m.V[j], m.V[j + 1], d,
+                                        c.gamma_on && valid0, c.gamma_on && valid1, nfb);
+      {
+        // |v^{n+1}|^2 in float pairs into the two lanes' sums (0 for a marker past the end)
+        const float2 h = make_float2(valid0 ? vn2.hi.x : 0.0f, valid1 ? vn2.hi.y : 0.0f);
+        const float2 l = make_float2(valid0 ? vn2.lo.x : 0.0f, valid1 ? vn2.lo.y : 0.0f);
+        ff2 s2 = two_prod2(h, h);
+        s2.lo = fma2(add2(h, h), l, s2.lo);
+        const ff2 acc = two_sum2(ke2h, s2.hi);
+        ke2h = acc.hi;
+        ke2l = add2(ke2l, add2(acc.lo, s2.lo));
       }
-      const uint32_t Xn = X + 2u * hs;
-      if (SCHEME == 2) {
-        const int Vn1 = to_fixed(vn.hi, bad);
-        const ShapeMix<ORDER> S1(Xn + half_shift(Vn1, c), c.nc);
-        if (AGG) {
-          if (j == 0) win.start(S1.p, valid, npad);
-          win.add(Jt, S1, Vn1, c, valid);
-        } else if (valid) {
-          deposit_direct<ORDER, RT>(Jl, S1, Vn1, c);
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const int jj = j + u;
+        const uint32_t X = m.X[jj];
+        const int Vs = m.V[jj];
+        const bool valid = u ? valid1 : valid0;
+        const ff vn = u ? ff{vn2.hi.y, vn2.lo.y} : ff{vn2.hi.x, vn2.lo.x};
+        const uint32_t Xn = X + 2u * (u ? hs1 : hs0);
+        if (SCHEME == 2) {
+          const int Vn1 = to_fixed(vn.hi, bad);
+          const ShapeMix<ORDER> S1(Xn + half_shift(Vn1, c), c.nc);
+          if (AGG) {
+            if (jj == 0) win.start(S1.p, valid, npad);
+            win.add(Jt, S1, Vn1, c, valid);
+          } else if (valid) {
+            deposit_direct<ORDER, RT>(Jl, S1, Vn1, c);
+          }
         }
-      }
-      if (MODE == 2) {
-        // sort on write: the marker's slot in key order, from pass C's counts
-        const uint32_t dst = warp_rank(off, sort_key(Xn, Vs, c.nc), valid);
-        if (valid) {
-          b.Xo[dst] = Xn;
-          b.vho[dst] = vn.hi;
-          b.vlo[dst] = vn.lo;
-          if (b.ids) b.ido[dst] = b.ids[G * g + j];
+        if (MODE == 2) {
+          // sort on write: the marker's slot in key order, from pass C's counts
+          const uint32_t dst = warp_rank(off, sort_key(Xn, Vs, c.nc), valid);
+          if (valid) {
+            b.Xo[dst] = Xn;
+            b.vho[dst] = vn.hi;
+            b.vlo[dst] = vn.lo;
+            if (b.ids) b.ido[dst] = b.ids[G * g + jj];
+          }
         }
+        o.X[jj] = valid ? Xn : X;
+        o.vh[jj] = valid ? vn.hi : m.vh[jj];
+        o.vl[jj] = valid ? vn.lo : m.vl[jj];
       }
-      o.X[j] = valid ? Xn : X;
-      o.vh[j] = valid ? vn.hi : vh;
-      o.vl[j] = valid ? vn.lo : vl;
     }
     if (AGG && SCHEME == 2) win.flush(Jt);
     if (MODE != 2 && gv) {
@@ -788,7 +861,9 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
       for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     if (threadIdx.x == 0) b.we_part[P.rb] = w;
   }
-  // a non-finite v^{n+1} leaves the thread's kinetic sum non-finite
+  // the two lanes' kinetic sums; a non-finite v^{n+1} leaves them non-finite
+  const ff ke_t = ff_add(ff{ke2h.x, ke2l.x}, ff{ke2h.y, ke2l.y});
+  const float ke_hi = ke_t.hi, ke_lo = ke_t.lo;
   if (!isfinite(ke_hi) || !isfinite(ke_lo)) bad |= kErrNonfinite;
   report_flags(bad, b.err);
   nfb = __reduce_add_sync(0xffffffffu, nfb);
