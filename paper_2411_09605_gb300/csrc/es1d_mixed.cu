@@ -81,6 +81,7 @@ struct ShapeMix {
   int p;
   float w[ORDER + 1];
   int s[ORDER + 1];
+  ShapeMix() = default;
   __device__ __forceinline__ ShapeMix(uint32_t X, int nc) {
     // xi (+ 1/2 for order 2) in 32.32 fixed point
     const uint64_t P = (uint64_t)X * (uint32_t)nc + (ORDER == 2 ? 0x80000000ull : 0ull);
@@ -106,6 +107,51 @@ struct ShapeMix {
     }
   }
 };
+
+// The shapes of two markers at once: the integer parts per marker, the float
+// weights in packed FP32 with the constructor's operations, lane by lane (the
+// same bits).
+template <int ORDER>
+__device__ __forceinline__ void shape_mix_pair(uint32_t X0, uint32_t X1, int nc,
+                                               ShapeMix<ORDER> &S0, ShapeMix<ORDER> &S1) {
+  const uint64_t P0 = (uint64_t)X0 * (uint32_t)nc + (ORDER == 2 ? 0x80000000ull : 0ull);
+  const uint64_t P1 = (uint64_t)X1 * (uint32_t)nc + (ORDER == 2 ? 0x80000000ull : 0ull);
+  S0.p = (int)(P0 >> 32);
+  S1.p = (int)(P1 >> 32);
+  const uint32_t g0 = (uint32_t)P0 >> 9, g1 = (uint32_t)P1 >> 9;
+  const float2 one = splat2(1.0f);
+  const float2 f = sub2(make_float2(__uint_as_float(0x3F800000u | g0),
+                                    __uint_as_float(0x3F800000u | g1)), one);
+  if (ORDER == 1) {
+    const float2 w0 = sub2(one, f);
+    S0.w[0] = w0.x;
+    S1.w[0] = w0.y;
+    S0.w[1] = f.x;
+    S1.w[1] = f.y;
+    S0.s[0] = (1 << 23) - (int)g0;
+    S1.s[0] = (1 << 23) - (int)g1;
+    S0.s[1] = (int)g0;
+    S1.s[1] = (int)g1;
+  } else {
+    const float2 a = sub2(one, f);
+    const float2 q0 = fma2(mul2(splat2(0.5f), a), a, one);
+    const float2 q2 = fma2(mul2(splat2(0.5f), f), f, one);
+    const float2 w0 = sub2(q0, one), w2 = sub2(q2, one);
+    const float2 w1 = sub2(sub2(one, w0), w2);
+    S0.w[0] = w0.x;
+    S1.w[0] = w0.y;
+    S0.w[1] = w1.x;
+    S1.w[1] = w1.y;
+    S0.w[ORDER] = w2.x;
+    S1.w[ORDER] = w2.y;
+    S0.s[0] = __float_as_int(q0.x) & 0x7FFFFF;
+    S1.s[0] = __float_as_int(q0.y) & 0x7FFFFF;
+    S0.s[ORDER] = __float_as_int(q2.x) & 0x7FFFFF;
+    S1.s[ORDER] = __float_as_int(q2.y) & 0x7FFFFF;
+    S0.s[1] = (1 << 23) - S0.s[0] - S0.s[ORDER];
+    S1.s[1] = (1 << 23) - S1.s[0] - S1.s[ORDER];
+  }
+}
 
 __device__ __forceinline__ long long deposit_term(int V, int s, const Es1dMixConst &c) {
   return ((long long)V * (long long)s + c.rnd) >> c.rshift;
@@ -673,27 +719,39 @@ __device__ __forceinline__ void pass_c_body(const Es1dMixConst &c, const Es1dMix
     const bool gv = !CHECK || g < end;
     int Vout[G];
     DepositWindow<ORDER> win;
+    static_assert(G % 2 == 0, "markers are processed in pairs");
 #pragma unroll
-    for (int j = 0; j < G; j++) {
-      const uint32_t X = m.X[j];
-      const float vh = m.vh[j], vl = m.vl[j];
-      const bool valid = !CHECK || (gv && G * g + j < c.n);
-      const int Vn = to_fixed(vh, bad);
-      const ShapeMix<ORDER> Sx(X + half_shift(Vn, c), c.nc);
-      float e = 0.0f;
+    for (int j = 0; j < G; j += 2) {
+      // gather #1 at x* and v* of two markers, the float work in packed FP32
+      ShapeMix<ORDER> Sx0, Sx1;
+      shape_mix_pair<ORDER>(m.X[j] + half_shift(to_fixed(m.vh[j], bad), c),
+                            m.X[j + 1] + half_shift(to_fixed(m.vh[j + 1], bad), c), c.nc, Sx0, Sx1);
+      float2 e = make_float2(0.0f, 0.0f);
 #pragma unroll
-      for (int k = 0; k <= ORDER; k++) e = __fmaf_rn(Sx.w[k], El[(Sx.p + k) * RE], e);
-      const int Vs = vstar_fixed(vh, vl, e, bad);
-      const uint32_t hs = half_shift(Vs, c);
-      const ShapeMix<ORDER> Sh(X + hs, c.nc);
-      if (AGG) {
-        if (j == 0) win.start(Sh.p, valid, npad);
-        win.add(Jt, Sh, Vs, c, valid);
-      } else if (valid) {
-        deposit_direct<ORDER, RT>(Jl, Sh, Vs, c);
+      for (int k = 0; k <= ORDER; k++)
+        e = fma2(make_float2(Sx0.w[k], Sx1.w[k]),
+                 make_float2(El[(Sx0.p + k) * RE], El[(Sx1.p + k) * RE]), e);
+      int Vs2[2];
+      vstar_fixed2(make_float2(m.vh[j], m.vh[j + 1]), make_float2(m.vl[j], m.vl[j + 1]), e, bad,
+                   Vs2);
+      const uint32_t hs0 = half_shift(Vs2[0], c), hs1 = half_shift(Vs2[1], c);
+      ShapeMix<ORDER> Sh0, Sh1;
+      shape_mix_pair<ORDER>(m.X[j] + hs0, m.X[j + 1] + hs1, c.nc, Sh0, Sh1);
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const int jj = j + u;
+        const bool valid = !CHECK || (gv && G * g + jj < c.n);
+        const int Vs = Vs2[u];
+        const ShapeMix<ORDER> &Sh = u ? Sh1 : Sh0;
+        if (AGG) {
+          if (jj == 0) win.start(Sh.p, valid, npad);
+          win.add(Jt, Sh, Vs, c, valid);
+        } else if (valid) {
+          deposit_direct<ORDER, RT>(Jl, Sh, Vs, c);
+        }
+        if (MODE == 2) warp_rank(hist, sort_key(m.X[jj] + 2u * (u ? hs1 : hs0), Vs, c.nc), valid);
+        Vout[jj] = Vs;
       }
-      if (MODE == 2) warp_rank(hist, sort_key(X + 2u * hs, Vs, c.nc), valid);
-      Vout[j] = Vs;
     }
     if (AGG) win.flush(Jt);
     if (gv) store_vec<G>(b.Vs, g, Vout);
@@ -782,7 +840,8 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
       const bool valid1 = !CHECK || (gv && G * g + j + 1 < c.n);
       const uint32_t hs0 = half_shift(m.V[j], c), hs1 = half_shift(m.V[j + 1], c);
       // gather #2 at x^{n+1/2}: d = dt (q/m) E^{n+1/2}_p in V units, two markers at once
-      const ShapeMix<ORDER> Sh0(m.X[j] + hs0, c.nc), Sh1(m.X[j + 1] + hs1, c.nc);
+      ShapeMix<ORDER> Sh0, Sh1;
+      shape_mix_pair<ORDER>(m.X[j] + hs0, m.X[j + 1] + hs1, c.nc, Sh0, Sh1);
       const ff2 d = gather_kick2<ORDER, RE>(El, Sh0, Sh1);
       const ff2 vn2 = correct_velocity2(make_float2(m.vh[j], m.vh[j + 1]),
                                         make_float2(m.vl[j], m.vl[j + 1]), m.V[j], m.V[j + 1], d,
@@ -797,6 +856,16 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
         ke2h = acc.hi;
         ke2l = add2(ke2l, add2(acc.lo, s2.lo));
       }
+      const uint32_t Xn0 = m.X[j] + 2u * hs0, Xn1 = m.X[j + 1] + 2u * hs1;
+      // x* of the next step and its shapes (ESEC2's j^{n+1,*} deposit)
+      int Vn1s[2] = {0, 0};
+      ShapeMix<ORDER> S10, S11;
+      if (SCHEME == 2) {
+        Vn1s[0] = to_fixed(vn2.hi.x, bad);
+        Vn1s[1] = to_fixed(vn2.hi.y, bad);
+        shape_mix_pair<ORDER>(Xn0 + half_shift(Vn1s[0], c), Xn1 + half_shift(Vn1s[1], c), c.nc,
+                              S10, S11);
+      }
 #pragma unroll
       for (int u = 0; u < 2; u++) {
         const int jj = j + u;
@@ -804,10 +873,10 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
         const int Vs = m.V[jj];
         const bool valid = u ? valid1 : valid0;
         const ff vn = u ? ff{vn2.hi.y, vn2.lo.y} : ff{vn2.hi.x, vn2.lo.x};
-        const uint32_t Xn = X + 2u * (u ? hs1 : hs0);
+        const uint32_t Xn = u ? Xn1 : Xn0;
         if (SCHEME == 2) {
-          const int Vn1 = to_fixed(vn.hi, bad);
-          const ShapeMix<ORDER> S1(Xn + half_shift(Vn1, c), c.nc);
+          const int Vn1 = Vn1s[u];
+          const ShapeMix<ORDER> &S1 = u ? S11 : S10;
           if (AGG) {
             if (jj == 0) win.start(S1.p, valid, npad);
             win.add(Jt, S1, Vn1, c, valid);

@@ -27,6 +27,18 @@ __device__ __forceinline__ int vstar_fixed(float vh, float vl, float e, unsigned
   return vi + __float2int_rn(rem);
 }
 
+// vstar_fixed for two markers (lanes x, y), the float work in packed FP32
+// with the same operations lane by lane.
+__device__ __forceinline__ void vstar_fixed2(float2 vh, float2 vl, float2 e, unsigned &bad,
+                                             int (&out)[2]) {
+  const ff2 s = two_sum2(vh, e);
+  const int v0 = to_fixed(s.hi.x, bad), v1 = to_fixed(s.hi.y, bad);
+  const float2 rem =
+      add2(add2(sub2(s.hi, make_float2((float)v0, (float)v1)), s.lo), vl);
+  out[0] = v0 + __float2int_rn(rem.x);
+  out[1] = v1 + __float2int_rn(rem.y);
+}
+
 // a / b by one correction of the hardware reciprocal estimate r with the
 // exact FMA residual (Markstein's FMA division): q0 = a r, e = a - q0 b,
 // q = q0 + e r.  Before its final rounding q is within about 2^-44 |a/b| of
