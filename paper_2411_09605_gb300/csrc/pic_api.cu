@@ -1001,6 +1001,11 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
     return fail(PIC_ERR_ARG, "pic_init: unknown precision");
   if (cfg->binomial_passes < 0 || cfg->binomial_passes > 8)
     return fail(PIC_ERR_ARG, "pic_init: binomial_passes must be in [0, 8]");
+  if (cfg->sort_period < 0) return fail(PIC_ERR_ARG, "pic_init: sort_period must be >= 0");
+  if (cfg->sort_period > 0 &&
+      (cfg->solver != PIC_SOLVER_AMPERE_ES || cfg->precision != PIC_PREC_MIXED))
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: sort_period is an option of the mixed form of "
+                                     "the Ampere solver");
   if (cfg->charge_conserving != 0 && cfg->charge_conserving != 1)
     return fail(PIC_ERR_ARG, "pic_init: charge_conserving must be 0 or 1");
   if (cfg->charge_conserving &&

@@ -78,6 +78,17 @@ def test_argument_errors_are_status_codes(lib):
     with pytest.raises(pic.PicError) as ei:
         pic.pic_init(pic.make_config(64, 1.0, 0.1, binomial_passes=9), sp)
     assert ei.value.code == -1
+    for kw in ({"sort_period": 4},                                  # sorting: mixed 1D form only
+               {"sort_period": 4, "solver": pic.PIC_SOLVER_YEE_LEAPFROG, "dim_x": 2, "dim_v": 3,
+                "ny": 64, "Ly": 1.0, "precision": pic.PIC_PREC_MIXED},
+               {"charge_conserving": 1}):                           # Yee solver only
+        with pytest.raises(pic.PicError) as ei:
+            pic.pic_init(pic.make_config(64, 1.0, 0.1, **kw), sp)
+        assert ei.value.code == -7
+    for kw in ({"sort_period": -1}, {"charge_conserving": 2}):
+        with pytest.raises(pic.PicError) as ei:
+            pic.pic_init(pic.make_config(64, 1.0, 0.1, **kw), sp)
+        assert ei.value.code == -1
     with pytest.raises(pic.PicError) as ei:   # its field follows from the charge
         pic.pic_init(pic.make_config(64, 1.0, 0.1, solver=pic.PIC_SOLVER_STANDARD_LEAPFROG), sp,
                      np.zeros(64))
