@@ -401,11 +401,12 @@ __global__ void __launch_bounds__(256) mix2_deposit_initial_kernel(Em2dMixConst 
 
 __global__ void mix2_from_fp64_kernel(Em2dMixConst c, Em2dMixBufs mb, Em2dBufs b) {
   const double *v[3] = {b.vx, b.vy, b.vz};
+  const double scale = 4294967296.0 / c.L;   // one multiply per coordinate, no divide
   unsigned bad = 0;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n;
        p += (int64_t)gridDim.x * blockDim.x) {
-    mb.X[p] = (uint32_t)((unsigned long long)llrint(b.x[p] / c.L * 4294967296.0) & 0xFFFFFFFFull);
-    mb.Y[p] = (uint32_t)((unsigned long long)llrint(b.y[p] / c.L * 4294967296.0) & 0xFFFFFFFFull);
+    mb.X[p] = (uint32_t)((unsigned long long)llrint(b.x[p] * scale) & 0xFFFFFFFFull);
+    mb.Y[p] = (uint32_t)((unsigned long long)llrint(b.y[p] * scale) & 0xFFFFFFFFull);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       const double vv = v[d][p] * c.cxk;

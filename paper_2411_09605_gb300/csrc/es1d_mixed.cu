@@ -1101,13 +1101,16 @@ __global__ void mix_finalize_kernel(Es1dMixBufs b, double h, int slot, int nbloc
 // FP64 (x, v) <-> (X, vh, vl) with v stored in V units (v * cxk)
 __global__ void to_mix_kernel(const double *x, const double *v, int64_t n, double L, double cxk,
                               uint32_t *X, float *vh, float *vl, unsigned *err) {
+  // x 2^32 / L with one multiply per marker (the FP64 divide is many FP64
+  // instructions); X is the rounded product, within a rounding of x / L 2^32
+  const double scale = 4294967296.0 / L;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     double xx = x[p], vv = v[p] * cxk;
     if (!(xx >= 0.0 && xx < L)) atomicOr(err, kErrBounds);
     if (!isfinite(vv)) atomicOr(err, kErrNonfinite);
     if (!(fabs(vv) < 2147483520.0)) atomicOr(err, kErrVelocityRange);
-    double u = xx / L * 4294967296.0;
+    double u = xx * scale;
     unsigned long long q = (unsigned long long)llrint(u);
     X[p] = (uint32_t)(q & 0xFFFFFFFFull);
     float h = (float)vv;
@@ -1432,12 +1435,25 @@ void es1d_batch_gather_stats(const Es1dMixBufs *bs, int nruns, int n, unsigned l
 
 void es1d_mix_from_fp64(const Es1dMixConst &c, const double *x, const double *v, Es1dMixBufs &b,
                         LaunchShape ls, cudaStream_t st) {
-  to_mix_kernel<<<ls.grid, 256, 0, st>>>(x, v, c.n, c.L, c.cxk, b.X, b.vh, b.vl, b.err);
+  es1d_mix_from_fp64_part(c, x, v, b, 0, c.n, ls, st);
 }
 
 void es1d_mix_to_fp64(const Es1dMixConst &c, const Es1dMixBufs &b, double *x, double *v,
                       LaunchShape ls, cudaStream_t st) {
-  from_mix_kernel<<<ls.grid, 256, 0, st>>>(b.X, b.vh, b.vl, c.n, c.L, 1.0 / c.cxk, x, v);
+  es1d_mix_to_fp64_part(c, b, x, v, 0, c.n, ls, st);
+}
+
+void es1d_mix_from_fp64_part(const Es1dMixConst &c, const double *x, const double *v,
+                             Es1dMixBufs &b, int64_t begin, int64_t count, LaunchShape ls,
+                             cudaStream_t st) {
+  to_mix_kernel<<<ls.grid, 256, 0, st>>>(x + begin, v + begin, count, c.L, c.cxk, b.X + begin,
+                                         b.vh + begin, b.vl + begin, b.err);
+}
+
+void es1d_mix_to_fp64_part(const Es1dMixConst &c, const Es1dMixBufs &b, double *x, double *v,
+                           int64_t begin, int64_t count, LaunchShape ls, cudaStream_t st) {
+  from_mix_kernel<<<ls.grid, 256, 0, st>>>(b.X + begin, b.vh + begin, b.vl + begin, count, c.L,
+                                           1.0 / c.cxk, x + begin, v + begin);
 }
 
 void es1d_mix_kinetic(const Es1dMixConst &c, const Es1dMixBufs &b, double *part, int nblocks,

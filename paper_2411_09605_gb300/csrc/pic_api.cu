@@ -40,6 +40,7 @@ int fail(int code, const char *fmt, ...) {
   } while (0)
 
 constexpr int kStepsCap = 1024;  // per-step stats slots per chunk of pic_step
+constexpr int kXferChunks = 8;   // pieces of a pipelined host transfer of the markers
 constexpr int kProfKinds = 8;    // 0 pass C, 1 pass E, 2 stats finalize, 3 sort, 4 field
 
 // ids[p] = p for one species' slots (marker ids after pic_set_particles).
@@ -142,7 +143,14 @@ struct pic_handle {
     *p = (T *)q;
     return PIC_OK;
   }
+  // chunked host transfers of the mixed 1D markers: a copy stream and one
+  // event per chunk (plus one), made on first use
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t chunk_ev[kXferChunks + 1] = {};
   ~pic_handle() {
+    if (copy_st) cudaStreamDestroy(copy_st);
+    for (cudaEvent_t e : chunk_ev)
+      if (e) cudaEventDestroy(e);
     for (Timed &t : timed) {
       cudaEventDestroy(t.a);
       cudaEventDestroy(t.b);
@@ -186,6 +194,65 @@ struct pic_handle {
 };
 
 namespace {
+
+// The copy stream and its events, made on first use.
+cudaError_t ensure_copy_stream(pic_handle *h) {
+  if (h->copy_st) return cudaSuccess;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking);
+  for (int k = 0; e == cudaSuccess && k <= kXferChunks; k++)
+    e = cudaEventCreateWithFlags(&h->chunk_ev[k], cudaEventDisableTiming);
+  return e;
+}
+
+// pic_set_particles of the mixed 1D form: the markers go into the FP64
+// staging arrays in kXferChunks pieces on the copy stream, and each piece is
+// turned into the mixed state on the handle's stream as soon as it has
+// arrived, so the conversion overlaps the transfer of the next piece.
+cudaError_t upload_mixed_1d(pic_handle *h, const double *x, const double *v) {
+  cudaError_t e = ensure_copy_stream(h);
+  Es1dFp64Bufs &b = h->b1;
+  const int64_t n = h->N, chunk = (n + kXferChunks - 1) / kXferChunks;
+  // earlier work on the handle's stream may still read the staging arrays
+  if (e == cudaSuccess) e = cudaEventRecord(h->chunk_ev[kXferChunks], h->st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_st, h->chunk_ev[kXferChunks], 0);
+  for (int k = 0; e == cudaSuccess && k < kXferChunks && k * chunk < n; k++) {
+    const int64_t b0 = k * chunk, cnt = std::min(chunk, n - b0);
+    e = cudaMemcpyAsync(b.x + b0, x + b0, sizeof(double) * cnt, cudaMemcpyDefault, h->copy_st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b.v + b0, v + b0, sizeof(double) * cnt, cudaMemcpyDefault, h->copy_st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->chunk_ev[k], h->copy_st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st, h->chunk_ev[k], 0);
+    if (e == cudaSuccess) {
+      es1d_mix_from_fp64_part(h->cm, b.x, b.v, h->bm, b0, cnt, h->ls, h->st);
+      e = cudaGetLastError();
+    }
+  }
+  return e;
+}
+
+// pic_get_particles of the mixed 1D form: each piece is converted to FP64 on
+// the handle's stream and copied out on the copy stream while the next piece
+// converts; returns after the last copy.
+cudaError_t download_mixed_1d(pic_handle *h, double *x, double *v) {
+  cudaError_t e = ensure_copy_stream(h);
+  Es1dFp64Bufs &b = h->b1;
+  const int64_t n = h->N, chunk = (n + kXferChunks - 1) / kXferChunks;
+  for (int k = 0; e == cudaSuccess && k < kXferChunks && k * chunk < n; k++) {
+    const int64_t b0 = k * chunk, cnt = std::min(chunk, n - b0);
+    es1d_mix_to_fp64_part(h->cm, h->bm, b.x, b.v, b0, cnt, h->ls, h->st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(h->chunk_ev[k], h->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_st, h->chunk_ev[k], 0);
+    if (e == cudaSuccess && x)
+      e = cudaMemcpyAsync(x + b0, b.x + b0, sizeof(double) * cnt, cudaMemcpyDefault, h->copy_st);
+    if (e == cudaSuccess && v)
+      e = cudaMemcpyAsync(v + b0, b.v + b0, sizeof(double) * cnt, cudaMemcpyDefault, h->copy_st);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h->chunk_ev[kXferChunks], h->copy_st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st, h->chunk_ev[kXferChunks], 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  return e;
+}
 
 // Marker ids 0..n-1 of species S, set on the device (no host array).
 cudaError_t reset_ids(pic_handle *h, const SpeciesInfo &S) {
@@ -1463,9 +1530,9 @@ int pic_get_particles(pic_handle *h, int s, double *x, double *v) {
     CUDA_TRY(cudaStreamSynchronize(h->st));
     return PIC_OK;
   }
-  if (h->mixed) {
-    es1d_mix_to_fp64(h->cm, h->bm, h->b1.x, h->b1.v, h->ls, h->st);
-    CUDA_TRY(cudaGetLastError());
+  if (h->mixed) {   // one species: the pieces cover the species
+    CUDA_TRY(download_mixed_1d(h, x, v));
+    return PIC_OK;
   }
   if (x) CUDA_TRY(cudaMemcpyAsync(x, h->b1.x + S.offset, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
   if (v) CUDA_TRY(cudaMemcpyAsync(v, h->b1.v + S.offset, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
@@ -1510,6 +1577,11 @@ int pic_set_particles(pic_handle *h, int s, const double *x, const double *v) {
                                cudaMemcpyDefault, h->st));
     CUDA_TRY(reset_ids(h, S));
     return restart_em2d(h);
+  }
+  if (h->mixed) {   // one species; the pieces are converted as they arrive
+    CUDA_TRY(upload_mixed_1d(h, x, v));
+    CUDA_TRY(reset_ids(h, S));
+    return restart_es1d(h, false);
   }
   CUDA_TRY(cudaMemcpyAsync(h->b1.x + S.offset, x, sizeof(double) * S.n, cudaMemcpyDefault, h->st));
   CUDA_TRY(cudaMemcpyAsync(h->b1.v + S.offset, v, sizeof(double) * S.n, cudaMemcpyDefault, h->st));

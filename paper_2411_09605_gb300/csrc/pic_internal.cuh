@@ -414,6 +414,13 @@ void es1d_mix_from_fp64(const Es1dMixConst &c, const double *x, const double *v,
                         LaunchShape ls, cudaStream_t st);
 void es1d_mix_to_fp64(const Es1dMixConst &c, const Es1dMixBufs &b, double *x, double *v,
                       LaunchShape ls, cudaStream_t st);
+// the same for markers [begin, begin + count) (x, v and the mixed arrays
+// indexed from the first marker)
+void es1d_mix_from_fp64_part(const Es1dMixConst &c, const double *x, const double *v,
+                             Es1dMixBufs &b, int64_t begin, int64_t count, LaunchShape ls,
+                             cudaStream_t st);
+void es1d_mix_to_fp64_part(const Es1dMixConst &c, const Es1dMixBufs &b, double *x, double *v,
+                           int64_t begin, int64_t count, LaunchShape ls, cudaStream_t st);
 void es1d_mix_kinetic(const Es1dMixConst &c, const Es1dMixBufs &b, double *part, int nblocks,
                       cudaStream_t st);
 void es1d_absmax(const double *v, int64_t n, unsigned long long *out, LaunchShape ls,
