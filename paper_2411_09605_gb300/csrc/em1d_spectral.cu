@@ -30,6 +30,18 @@
 // (a power of two, 4 <= n <= 1024) in shared memory, with its twiddles and
 // the PSATD per-mode coefficients tabulated once at set-up.
 //
+// Mixed form (Em1dMixConst / Em1dMixBufs): the same two passes and the same
+// FP64 field solve, with the per-marker work of the 1D1V mixed form: y as a
+// 32-bit fixed-point word, (vx, vy) as float pairs in V units, v* as the
+// integers (V*x, V*y), quantised shape weights, and the currents as exact
+// integer sums (split 32-bit counters in per-lane tile copies, one int64
+// global atomic per node and block); the last block hands the field solve
+// jscale times those sums.  Gather #1 (E*, B* at y*) runs in FP32; gather #2
+// reads the E of v^dag as float pairs with error-free weight products, and the
+// magnetic part dt (q/m) (V*y Bz, -V*x Bz) is formed in float pairs of the
+// exact V*, so it does no work; Gamma from the exact bracket
+// Delta . (V* - v^n - Delta/2), as in the 1D1V mixed form.
+//
 // Deposits: each lane of a block adds into its own copy of the block's
 // current tile (rt copies, laid out [node][component][copy], rt up to 32 as
 // shared memory allows), so FP64 shared atomics rarely meet; the flush sums
@@ -39,6 +51,8 @@
 #include <cuda_runtime.h>
 
 #include "es1d_fp64_common.cuh"
+#include "ff.cuh"
+#include "mixed_common.cuh"
 #include "pic_internal.cuh"
 #include "spectral_common.cuh"
 
@@ -451,6 +465,371 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_energy_kernel(Em1dConst c, E
   }
 }
 
+// ------------------------------------------------------------ mixed form
+
+// V units -> position units for half a step (kv >= 1)
+__device__ __forceinline__ uint32_t half_shift1(int V, const Em1dMixConst &m) {
+  return (uint32_t)((V + m.hround) >> m.kv);
+}
+
+// Split tile of the mixed passes: [padded node][component][half][copy], the
+// low 16 bits of each term (unsigned) and the signed rest, so a node's value
+// is rest 2^16 + low; lane l adds into copy l mod rt.
+template <int ORDER>
+__device__ __forceinline__ void mix_tile_deposit(unsigned *Jl, int rt, const ShapeMix<ORDER> &S,
+                                                 int Vx, int Vy, const Em1dMixConst &m) {
+#pragma unroll
+  for (int k = 0; k <= ORDER; k++) {
+    unsigned *q = Jl + (S.p + k) * 4 * rt;
+    const SplitTerm tx = split_term(Vx, S.s[k], m.rshift, m.rnd);
+    const SplitTerm ty = split_term(Vy, S.s[k], m.rshift, m.rnd);
+    atomicAdd(q, tx.lo);
+    atomicAdd(q + rt, (unsigned)tx.hi);
+    atomicAdd(q + 2 * rt, ty.lo);
+    atomicAdd(q + 3 * rt, (unsigned)ty.hi);
+  }
+}
+
+// Sums each (padded node, component)'s copies and adds the non-zero totals to
+// J [2][n] with one int64 atomic (ghost nodes add to the node they stand for).
+template <int ORDER>
+__device__ void mix_flush_tile(const unsigned *Jt, int rt, long long *J, int n) {
+  for (int i = threadIdx.x; i < 2 * npad_of(n); i += blockDim.x) {
+    const int q = i >> 1, comp = i & 1;
+    const unsigned *lo = Jt + (size_t)(q * 2 + comp) * 2 * rt, *hi = lo + rt;
+    unsigned long long sl = 0;
+    long long sh = 0;
+    for (int r = 0; r < rt; r++) {
+      const int k = (r + i) & (rt - 1);
+      sl += lo[k];
+      sh += (int)hi[k];
+    }
+    const long long a = sh * 65536 + (long long)sl;
+    if (a != 0)
+      atomicAdd((unsigned long long *)&J[comp * n + wrap_node(q - Pad<ORDER>::kPad, n)],
+                (unsigned long long)a);
+  }
+}
+
+// jscale times an integer current into slice 0 of an FP64 sliced current
+// (the field solve's input; the other slices stay zero); the block's threads.
+__device__ __forceinline__ void mix_current_to_fp64(const long long *Ji, double *J, int n,
+                                                    double jscale) {
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) J[i] = jscale * (double)__ldcg(Ji + i);
+}
+
+__device__ __forceinline__ void clear_words(unsigned *a, int len) {
+  for (int i = threadIdx.x; i < len; i += blockDim.x) a[i] = 0u;
+}
+
+// v^dag = v^n + Delta and v^{n+1} = Gamma v^dag for the pair (vx, vy) of one
+// marker, the components in the two lanes (x, y) of packed float pairs:
+// b = V* - v^n - Delta/2 from the exact differences, a = Delta . b, and
+// Gamma - 1 from t = 2a / |v^dag|^2 as in the 1D1V mixed form.
+__device__ __forceinline__ ff2 correct_velocity_xy(float2 vh, float2 vl, int Vx, int Vy, ff2 D,
+                                                   bool on, unsigned &nfb) {
+  const ff2 vd = ff_add2(ff2{vh, vl}, D);
+  if (!on) return vd;
+  const int ihx = __float2int_rn(vh.x), ihy = __float2int_rn(vh.y);
+  const float2 fr = sub2(vh, make_float2(__int2float_rn(ihx), __int2float_rn(ihy)));
+  const ff2 q = two_sum2(make_float2(__int2float_rn(Vx - ihx), __int2float_rn(Vy - ihy)),
+                         mul2(splat2(-0.5f), D.hi));
+  const float2 bq = add2(q.hi, sub2(sub2(sub2(q.lo, fr), vl), mul2(splat2(0.5f), D.lo)));
+  const float2 db = mul2(add2(D.hi, D.hi), bq);
+  const float2 v2 = mul2(vd.hi, vd.hi);
+  const float t = div_rcp_residual(__fadd_rn(db.x, db.y), __fadd_rn(v2.x, v2.y));
+  float gm;
+  if (fabsf(t) < 0.00390625f) {
+    gm = __fmul_rn(
+        t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, -0.0390625f, 0.0625f), -0.125f), 0.5f));
+  } else if (!(t >= -1.0f && t < 1e30f)) {
+    nfb++;
+    return vd;
+  } else {
+    gm = __fdiv_rn(t, __fadd_rn(1.0f, __fsqrt_rn(__fadd_rn(1.0f, t))));
+  }
+  ff2 p = two_prod2(vd.hi, splat2(gm));
+  p.lo = fma2(vd.lo, splat2(gm), p.lo);
+  return ff_add2(vd, p);
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kEm1Threads) em1m_pass_c_kernel(Em1dConst c, Em1dBufs b,
+                                                                   Em1dMixConst m,
+                                                                   Em1dMixBufs mb) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int PAD = Pad<ORDER>::kPad;
+  const int n = c.n, npad = npad_of(n), rt = m.rt;
+  unsigned *Jt = (unsigned *)smraw;                      // [npad][2][2][rt]
+  float4 *T = (float4 *)(Jt + 4 * rt * npad);            // e_half E*x, e_half E*y, t_half B*z
+  clear_words(Jt, 4 * rt * npad);
+  for (int q = threadIdx.x; q < npad; q += blockDim.x) {
+    const int i = wrap_node(q - PAD, n);
+    T[q] = make_float4((float)(m.e_half * b.Es[i]), (float)(m.e_half * b.Es[n + i]),
+                       (float)(m.t_half * b.Bs[i]), 0.0f);
+  }
+  __syncthreads();
+  unsigned *Jl = Jt + (threadIdx.x & (rt - 1));
+  unsigned bad = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m.N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t Y = mb.Y[p];
+    const float vxh = mb.vh[0][p], vxl = mb.vl[0][p], vyh = mb.vh[1][p], vyl = mb.vl[1][p];
+    // gather #1 at y* = y^n + dt/2 vy^n: e_half E*, t = t_half B*z
+    const ShapeMix<ORDER> S1(Y + half_shift1(to_fixed(vyh, bad), m), n);
+    float ex = 0.0f, ey = 0.0f, t = 0.0f;
+#pragma unroll
+    for (int k = 0; k <= ORDER; k++) {
+      const float4 f = T[S1.p + k];
+      ex = __fmaf_rn(S1.w[k], f.x, ex);
+      ey = __fmaf_rn(S1.w[k], f.y, ey);
+      t = __fmaf_rn(S1.w[k], f.z, t);
+    }
+    // v* = (ux + t uy, uy - t ux) / (1 + t^2), u = v^n + e: v* = u + correction
+    const float ux = __fadd_rn(vxh, ex), uy = __fadd_rn(vyh, ey);
+    const float tt = __fmul_rn(t, t), inv = __frcp_rn(__fadd_rn(1.0f, tt));
+    const float cx = __fmul_rn(__fmaf_rn(t, uy, -__fmul_rn(tt, ux)), inv);
+    const float cy = __fmul_rn(__fmaf_rn(-t, ux, -__fmul_rn(tt, uy)), inv);
+    const int Vx = vstar_fixed(vxh, vxl, __fadd_rn(ex, cx), bad);
+    const int Vy = vstar_fixed(vyh, vyl, __fadd_rn(ey, cy), bad);
+    const ShapeMix<ORDER> Sh(Y + half_shift1(Vy, m), n);
+    mix_tile_deposit<ORDER>(Jl, rt, Sh, Vx, Vy, m);
+    mb.Vs[0][p] = Vx;
+    mb.Vs[1][p] = Vy;
+  }
+  if (bad) atomicOr(b.err, bad);
+  __syncthreads();
+  mix_flush_tile<ORDER>(Jt, rt, mb.J2, n);
+  if (arrive_last(b.done)) {
+    mix_current_to_fp64(mb.J2, b.J2, n, m.jscale);
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) mb.J1[i] = 0;
+    __syncthreads();
+    double2 *Z = (double2 *)smraw;
+    field_advance(c, c.solver == 2, c.dt, b.coef, b.tw, b.E, b.B, b.J2, b.En, b.Bn, b.Ea, b.Bh, Z);
+  }
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kEm1Threads) em1m_pass_e_kernel(Em1dConst c, Em1dBufs b,
+                                                                   Em1dMixConst m,
+                                                                   Em1dMixBufs mb, int slot) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[33];
+  constexpr int PAD = Pad<ORDER>::kPad;
+  const int n = c.n, npad = npad_of(n), rt = m.rt;
+  unsigned *Jt = (unsigned *)smraw;                      // [npad][2][2][rt]
+  float4 *Ta = (float4 *)(Jt + 4 * rt * npad);           // kick Ea as pairs (x hi, x lo, y hi, y lo)
+  float *Tb = (float *)(Ta + npad);                      // m_full B^{n+1/2}
+  clear_words(Jt, 4 * rt * npad);
+  for (int q = threadIdx.x; q < npad; q += blockDim.x) {
+    const int i = wrap_node(q - PAD, n);
+    const ff ax = ff_from_double(m.kick * b.Ea[i]), ay = ff_from_double(m.kick * b.Ea[n + i]);
+    Ta[q] = make_float4(ax.hi, ax.lo, ay.hi, ay.lo);
+    Tb[q] = (float)(m.m_full * b.Bh[i]);
+  }
+  __syncthreads();
+  unsigned *Jl = Jt + (threadIdx.x & (rt - 1));
+  float2 keh = make_float2(0.0f, 0.0f), kel = make_float2(0.0f, 0.0f);
+  unsigned nfb = 0, bad = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m.N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t Y = mb.Y[p];
+    const float2 vh = make_float2(mb.vh[0][p], mb.vh[1][p]);
+    const float2 vl = make_float2(mb.vl[0][p], mb.vl[1][p]);
+    const int Vx = mb.Vs[0][p], Vy = mb.Vs[1][p];
+    const uint32_t hs = half_shift1(Vy, m);
+    const ShapeMix<ORDER> S(Y + hs, n);
+    // gather #2 at y^{n+1/2}: kick E as float pairs (lane x: Ex, lane y: Ey)
+    float2 ph[ORDER + 1], pl = make_float2(0.0f, 0.0f);
+    float bz = 0.0f;
+#pragma unroll
+    for (int k = 0; k <= ORDER; k++) {
+      const float4 e = Ta[S.p + k];
+      const float2 w = splat2(S.w[k]);
+      const ff2 pr = two_prod2(make_float2(e.x, e.z), w);
+      ph[k] = pr.hi;
+      pl = add2(pl, fma2(make_float2(e.y, e.w), w, pr.lo));
+      bz = __fmaf_rn(S.w[k], Tb[S.p + k], bz);
+    }
+    ff2 Ep = two_sum2(ph[0], ph[1]);
+    pl = add2(pl, Ep.lo);
+    if (ORDER == 2) {
+      Ep = two_sum2(Ep.hi, ph[ORDER]);
+      pl = add2(pl, Ep.lo);
+    }
+    // Delta = d + dt (q/m) (V*y Bz, -V*x Bz), the products in float pairs of the exact V*
+    const float fx = __int2float_rn(Vx), fy = __int2float_rn(Vy);
+    const ff2 vs{make_float2(fy, fx), make_float2(__int2float_rn(Vy - __float2int_rn(fy)),
+                                                  __int2float_rn(Vx - __float2int_rn(fx)))};
+    ff2 mu = two_prod2(vs.hi, splat2(bz));
+    mu.lo = fma2(vs.lo, splat2(bz), mu.lo);
+    mu = fast_two_sum2(mu.hi, mu.lo);
+    mu.hi.y = -mu.hi.y;
+    mu.lo.y = -mu.lo.y;
+    const ff2 D = ff_add2(fast_two_sum2(Ep.hi, pl), mu);
+    const ff2 vn = correct_velocity_xy(vh, vl, Vx, Vy, D, c.gamma_on != 0, nfb);
+    {
+      ff2 s2 = two_prod2(vn.hi, vn.hi);
+      s2.lo = fma2(add2(vn.hi, vn.hi), vn.lo, s2.lo);
+      const ff2 acc = two_sum2(keh, s2.hi);
+      keh = acc.hi;
+      kel = add2(kel, add2(acc.lo, s2.lo));
+    }
+    const uint32_t Y1 = Y + 2u * hs;
+    if (c.scheme == 2) {
+      const int V1x = to_fixed(vn.hi.x, bad), V1y = to_fixed(vn.hi.y, bad);
+      const ShapeMix<ORDER> S1(Y1 + half_shift1(V1y, m), n);
+      mix_tile_deposit<ORDER>(Jl, rt, S1, V1x, V1y, m);
+    }
+    mb.Y[p] = Y1;
+    mb.vh[0][p] = vn.hi.x;
+    mb.vl[0][p] = vn.lo.x;
+    mb.vh[1][p] = vn.hi.y;
+    mb.vl[1][p] = vn.lo.y;
+  }
+  const ff kt = ff_add(ff{keh.x, kel.x}, ff{keh.y, kel.y});
+  if (!isfinite(kt.hi) || !isfinite(kt.lo)) bad |= kErrNonfinite;
+  if (bad) atomicOr(b.err, bad);
+  const unsigned fbw = __reduce_add_sync(0xffffffffu, nfb);
+  if ((threadIdx.x & 31) == 0 && fbw) atomicAdd(&b.fallback[slot], (unsigned long long)fbw);
+  const double kb = block_sum_d((double)kt.hi + (double)kt.lo, red);
+  if (threadIdx.x == 0) b.ke_part[blockIdx.x] = m.ke_scale * kb;
+  __syncthreads();
+  if (c.scheme == 2) mix_flush_tile<ORDER>(Jt, rt, mb.J1, n);
+  if (arrive_last(b.done + 1)) {
+    // TE of the new state: KE from the block partials in block order, W_E + W_B
+    double wf = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double ex = __ldcg(b.En + i), ey = __ldcg(b.En + n + i), bz = __ldcg(b.Bn + i);
+      wf += 0.5 * c.h * (ex * ex + ey * ey) + 0.5 * c.c2 * c.h * bz * bz;
+    }
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) wf += __ldcg(b.ke_part + i);
+    const double tsum = block_sum_d(wf, red);
+    if (threadIdx.x == 0) b.te[slot] = tsum;
+    double2 *Z = (double2 *)smraw;
+    if (c.scheme == 2) {
+      mix_current_to_fp64(mb.J1, b.J1, n, m.jscale);
+      __syncthreads();
+      field_advance(c, c.solver == 2, 0.5 * c.dt, b.coef + kEm1Coef * (n / 2 + 1), b.tw, b.En,
+                    b.Bn, b.J1, b.Es, b.Bs, nullptr, nullptr, Z);
+    } else {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        b.Es[i] = __ldcg(b.En + i);
+        b.Es[n + i] = __ldcg(b.En + n + i);
+        b.Bs[i] = __ldcg(b.Bn + i);
+      }
+    }
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) mb.J2[i] = 0;
+  }
+}
+
+// j^{0,*} of the current state (ESEC2): V^n at y^n + dt/2 vy^n into mb.J1.
+template <int ORDER>
+__global__ void __launch_bounds__(kEm1Threads) em1m_deposit_initial_kernel(Em1dConst c,
+                                                                            Em1dMixConst m,
+                                                                            Em1dMixBufs mb,
+                                                                            unsigned *err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int n = c.n, rt = m.rt;
+  unsigned *Jt = (unsigned *)smraw;
+  clear_words(Jt, 4 * rt * npad_of(n));
+  __syncthreads();
+  unsigned *Jl = Jt + (threadIdx.x & (rt - 1));
+  unsigned bad = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m.N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int Vx = to_fixed(mb.vh[0][p], bad), Vy = to_fixed(mb.vh[1][p], bad);
+    const ShapeMix<ORDER> S(mb.Y[p] + half_shift1(Vy, m), n);
+    mix_tile_deposit<ORDER>(Jl, rt, S, Vx, Vy, m);
+  }
+  if (bad) atomicOr(err, bad);
+  __syncthreads();
+  mix_flush_tile<ORDER>(Jt, rt, mb.J1, n);
+}
+
+__global__ void em1m_j1_to_fp64_kernel(Em1dConst c, Em1dBufs b, Em1dMixConst m,
+                                       Em1dMixBufs mb) {
+  mix_current_to_fp64(mb.J1, b.J1, c.n, m.jscale);
+}
+
+__global__ void em1m_from_fp64_kernel(Em1dBufs b, Em1dMixConst m, Em1dMixBufs mb) {
+  const double scale = 4294967296.0 / m.L;   // one multiply per marker, no divide
+  const double *v[2] = {b.vx, b.vy};
+  unsigned bad = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m.N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    mb.Y[p] = (uint32_t)((unsigned long long)llrint(b.y[p] * scale) & 0xFFFFFFFFull);
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+      const double vv = v[d][p] * m.cxk;
+      if (!isfinite(vv)) bad |= kErrNonfinite;
+      if (!(fabs(vv) < 2147483520.0)) bad |= kErrVelocityRange;
+      const float hi = (float)vv;
+      mb.vh[d][p] = hi;
+      mb.vl[d][p] = (float)(vv - (double)hi);
+    }
+  }
+  if (bad) atomicOr(b.err, bad);
+}
+
+__global__ void em1m_to_fp64_kernel(Em1dBufs b, Em1dMixConst m, Em1dMixBufs mb) {
+  double *v[2] = {b.vx, b.vy};
+  const double inv = 1.0 / m.cxk;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m.N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    b.y[p] = (double)mb.Y[p] * (m.L / 4294967296.0);
+#pragma unroll
+    for (int d = 0; d < 2; d++) v[d][p] = ((double)mb.vh[d][p] + (double)mb.vl[d][p]) * inv;
+  }
+}
+
+__global__ void __launch_bounds__(kEm1Threads) em1m_energy_kernel(Em1dConst c, Em1dBufs b,
+                                                                   Em1dMixConst m,
+                                                                   Em1dMixBufs mb, double *ke_out,
+                                                                   double *wf) {
+  __shared__ double red[33];
+  double acc = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m.N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const double vx = (double)mb.vh[0][p] + (double)mb.vl[0][p];
+    const double vy = (double)mb.vh[1][p] + (double)mb.vl[1][p];
+    acc = fma(vx, vx, fma(vy, vy, acc));
+  }
+  const double t = block_sum_d(acc, red);
+  if (threadIdx.x == 0) ke_out[blockIdx.x] = m.ke_scale * t;
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    double we = 0.0, wb = 0.0;
+    for (int i = threadIdx.x; i < c.n; i += blockDim.x) {
+      we = fma(b.E[i], b.E[i], fma(b.E[c.n + i], b.E[c.n + i], we));
+      wb = fma(b.B[i], b.B[i], wb);
+    }
+    const double a = block_sum_d(we, red);
+    const double d = block_sum_d(wb, red);
+    if (threadIdx.x == 0) {
+      wf[0] = 0.5 * c.h * a;
+      wf[1] = 0.5 * c.c2 * c.h * d;
+    }
+  }
+}
+
+__global__ void em1m_absmax_kernel(Em1dBufs b, int64_t n, unsigned long long *out) {
+  double mx = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x)
+    mx = fmax(mx, fmax(fabs(b.vx[p]), fabs(b.vy[p])));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+// the mixed passes' tile and tables, or the field solve's 9n + 8 doubles
+size_t mix_smem(const Em1dConst &c, const Em1dMixConst &m) {
+  const size_t npad = (size_t)c.n + 3;
+  const size_t a = 4 * sizeof(unsigned) * m.rt * npad + (sizeof(float4) + sizeof(float)) * npad;
+  const size_t f = sizeof(double) * (9 * (size_t)c.n + 8);
+  return a > f ? a : f;
+}
+
 // the passes' tables and tile copies, or the field solve's 9n + 8 doubles
 size_t pass_smem(const Em1dConst &c) {
   const size_t a = (6 + 2 * (size_t)c.rt) * c.n, f = 9 * (size_t)c.n + 8;
@@ -528,6 +907,85 @@ void em1d_start(const Em1dConst &c, const Em1dBufs &b, LaunchShape lp, cudaStrea
 void em1d_energy(const Em1dConst &c, const Em1dBufs &b, double *ke_out, double *wf,
                  LaunchShape lp, cudaStream_t st) {
   em1d_energy_kernel<<<lp.grid, kEm1Threads, 0, st>>>(c, b, ke_out, wf);
+}
+
+int em1m_tile_copies(int n) {
+  const size_t npad = (size_t)n + 3;
+  int rt = 32;
+  while (rt > 1 && 4 * sizeof(unsigned) * rt * npad + (sizeof(float4) + sizeof(float)) * npad >
+                       kEm1TileBudget)
+    rt >>= 1;
+  return rt;
+}
+
+cudaError_t em1m_prepare(const Em1dConst &c, const Em1dMixConst &m) {
+  const size_t sm = mix_smem(c, m);
+  cudaError_t e = cudaSuccess;
+  if (c.order == 1) {
+    if ((e = allow_smem(em1m_pass_c_kernel<1>, sm))) return e;
+    if ((e = allow_smem(em1m_pass_e_kernel<1>, sm))) return e;
+    if ((e = allow_smem(em1m_deposit_initial_kernel<1>, sm))) return e;
+  } else {
+    if ((e = allow_smem(em1m_pass_c_kernel<2>, sm))) return e;
+    if ((e = allow_smem(em1m_pass_e_kernel<2>, sm))) return e;
+    if ((e = allow_smem(em1m_deposit_initial_kernel<2>, sm))) return e;
+  }
+  return allow_smem(em1d_half_kernel, pass_smem(c) > sm ? pass_smem(c) : sm);
+}
+
+void em1m_pass_c(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
+                 const Em1dMixBufs &mb, LaunchShape lp, cudaStream_t st) {
+  const size_t sm = mix_smem(c, m);
+  if (c.order == 1)
+    em1m_pass_c_kernel<1><<<lp.grid, kEm1Threads, sm, st>>>(c, b, m, mb);
+  else
+    em1m_pass_c_kernel<2><<<lp.grid, kEm1Threads, sm, st>>>(c, b, m, mb);
+}
+
+void em1m_pass_e(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
+                 const Em1dMixBufs &mb, int slot, LaunchShape lp, cudaStream_t st) {
+  const size_t sm = mix_smem(c, m);
+  if (c.order == 1)
+    em1m_pass_e_kernel<1><<<lp.grid, kEm1Threads, sm, st>>>(c, b, m, mb, slot);
+  else
+    em1m_pass_e_kernel<2><<<lp.grid, kEm1Threads, sm, st>>>(c, b, m, mb, slot);
+}
+
+void em1m_start(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
+                const Em1dMixBufs &mb, LaunchShape lp, cudaStream_t st) {
+  const size_t sm = mix_smem(c, m);
+  if (c.scheme == 2) {
+    if (c.order == 1)
+      em1m_deposit_initial_kernel<1><<<lp.grid, kEm1Threads, sm, st>>>(c, m, mb, b.err);
+    else
+      em1m_deposit_initial_kernel<2><<<lp.grid, kEm1Threads, sm, st>>>(c, m, mb, b.err);
+    em1m_j1_to_fp64_kernel<<<1, kEm1Threads, 0, st>>>(c, b, m, mb);
+  }
+  const size_t hs = pass_smem(c) > sm ? pass_smem(c) : sm;
+  em1d_half_kernel<<<1, kEm1Threads, hs, st>>>(c, b);
+}
+
+void em1m_from_fp64(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
+                    const Em1dMixBufs &mb, LaunchShape lp, cudaStream_t st) {
+  (void)c;
+  em1m_from_fp64_kernel<<<lp.grid, kEm1Threads, 0, st>>>(b, m, mb);
+}
+
+void em1m_to_fp64(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
+                  const Em1dMixBufs &mb, LaunchShape lp, cudaStream_t st) {
+  (void)c;
+  em1m_to_fp64_kernel<<<lp.grid, kEm1Threads, 0, st>>>(b, m, mb);
+}
+
+void em1m_energy(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
+                 const Em1dMixBufs &mb, double *ke_out, double *wf, LaunchShape lp,
+                 cudaStream_t st) {
+  em1m_energy_kernel<<<lp.grid, kEm1Threads, 0, st>>>(c, b, m, mb, ke_out, wf);
+}
+
+void em1m_absmax(const Em1dBufs &b, int64_t n, unsigned long long *out, LaunchShape lp,
+                 cudaStream_t st) {
+  em1m_absmax_kernel<<<lp.grid, kEm1Threads, 0, st>>>(b, n, out);
 }
 
 }  // namespace pic

@@ -11,6 +11,116 @@
 namespace pic {
 namespace {
 
+// Padded node indices.  The shared-memory field tables and current tiles carry
+// ghost nodes so that the nodes of a marker's shape are consecutive with no
+// periodic wrap: nc + 3 padded nodes, padded node q standing for grid node
+// (q - kPad) mod nc with kPad = 1 for order 2 (nodes i0 - 1 .. i0 + 1, i0 in
+// [0, nc]) and 0 for order 1 (nodes i, i + 1, i in [0, nc)).
+template <int ORDER>
+struct Pad {
+  static constexpr int kPad = ORDER == 2 ? 1 : 0;
+};
+__device__ __forceinline__ int npad_of(int nc) { return nc + 3; }
+__device__ __forceinline__ int wrap_node(int i, int nc) {
+  return i < 0 ? i + nc : (i >= nc ? i - nc : i);
+}
+
+// Shape of a marker at X: first padded node p and the weights.  The weights
+// are quantised B-spline values, multiples of 2^-23, available both as floats
+// (w, for the gathers) and as integers (s = w 2^23, for the deposits); gather
+// and deposit at the same X therefore use exactly the same numbers and sum to
+// 1 exactly.  Order 1: w = (1 - f, f).  Order 2: with f = xi - i0 + 1/2 in
+// [0, 1), w = (1/2 (1 - f)^2, 1 - w0 - w2, 1/2 f^2) at nodes i0 - 1, i0, i0 + 1.
+template <int ORDER>
+struct ShapeMix {
+  int p;
+  float w[ORDER + 1];
+  int s[ORDER + 1];
+  ShapeMix() = default;
+  __device__ __forceinline__ ShapeMix(uint32_t X, int nc) {
+    // xi (+ 1/2 for order 2) in 32.32 fixed point
+    const uint64_t P = (uint64_t)X * (uint32_t)nc + (ORDER == 2 ? 0x80000000ull : 0ull);
+    p = (int)(P >> 32);
+    const uint32_t f23 = (uint32_t)P >> 9;
+    const float f = __fsub_rn(__uint_as_float(0x3F800000u | f23), 1.0f);  // exact
+    if (ORDER == 1) {
+      w[0] = __fsub_rn(1.0f, f);
+      w[1] = f;
+      s[0] = (1 << 23) - (int)f23;
+      s[1] = (int)f23;
+    } else {
+      const float a = __fsub_rn(1.0f, f);
+      // 1 + w0 and 1 + w2 in [1, 1.5]: rounding to float puts w on the 2^-23 grid
+      const float q0 = __fmaf_rn(__fmul_rn(0.5f, a), a, 1.0f);
+      const float q2 = __fmaf_rn(__fmul_rn(0.5f, f), f, 1.0f);
+      w[0] = __fsub_rn(q0, 1.0f);
+      w[ORDER] = __fsub_rn(q2, 1.0f);
+      w[1] = __fsub_rn(__fsub_rn(1.0f, w[0]), w[ORDER]);
+      s[0] = __float_as_int(q0) & 0x7FFFFF;
+      s[ORDER] = __float_as_int(q2) & 0x7FFFFF;
+      s[1] = (1 << 23) - s[0] - s[ORDER];
+    }
+  }
+};
+
+// The shapes of two markers at once: the integer parts per marker, the float
+// weights in packed FP32 with the constructor's operations, lane by lane (the
+// same bits).
+template <int ORDER>
+__device__ __forceinline__ void shape_mix_pair(uint32_t X0, uint32_t X1, int nc,
+                                               ShapeMix<ORDER> &S0, ShapeMix<ORDER> &S1) {
+  const uint64_t P0 = (uint64_t)X0 * (uint32_t)nc + (ORDER == 2 ? 0x80000000ull : 0ull);
+  const uint64_t P1 = (uint64_t)X1 * (uint32_t)nc + (ORDER == 2 ? 0x80000000ull : 0ull);
+  S0.p = (int)(P0 >> 32);
+  S1.p = (int)(P1 >> 32);
+  const uint32_t g0 = (uint32_t)P0 >> 9, g1 = (uint32_t)P1 >> 9;
+  const float2 one = splat2(1.0f);
+  const float2 f = sub2(make_float2(__uint_as_float(0x3F800000u | g0),
+                                    __uint_as_float(0x3F800000u | g1)), one);
+  if (ORDER == 1) {
+    const float2 w0 = sub2(one, f);
+    S0.w[0] = w0.x;
+    S1.w[0] = w0.y;
+    S0.w[1] = f.x;
+    S1.w[1] = f.y;
+    S0.s[0] = (1 << 23) - (int)g0;
+    S1.s[0] = (1 << 23) - (int)g1;
+    S0.s[1] = (int)g0;
+    S1.s[1] = (int)g1;
+  } else {
+    const float2 a = sub2(one, f);
+    const float2 q0 = fma2(mul2(splat2(0.5f), a), a, one);
+    const float2 q2 = fma2(mul2(splat2(0.5f), f), f, one);
+    const float2 w0 = sub2(q0, one), w2 = sub2(q2, one);
+    const float2 w1 = sub2(sub2(one, w0), w2);
+    S0.w[0] = w0.x;
+    S1.w[0] = w0.y;
+    S0.w[1] = w1.x;
+    S1.w[1] = w1.y;
+    S0.w[ORDER] = w2.x;
+    S1.w[ORDER] = w2.y;
+    S0.s[0] = __float_as_int(q0.x) & 0x7FFFFF;
+    S1.s[0] = __float_as_int(q0.y) & 0x7FFFFF;
+    S0.s[ORDER] = __float_as_int(q2.x) & 0x7FFFFF;
+    S1.s[ORDER] = __float_as_int(q2.y) & 0x7FFFFF;
+    S0.s[1] = (1 << 23) - S0.s[0] - S0.s[ORDER];
+    S1.s[1] = (1 << 23) - S1.s[0] - S1.s[ORDER];
+  }
+}
+
+// The two tile counters' shares of round(V s / 2^r), r in [17, 31] (rnd =
+// 2^(r-1)): bits [r, r + 16) of P = V s + rnd (unsigned) and P >> (r + 16)
+// (signed); a node's value is (signed share) 2^16 + (unsigned share).
+struct SplitTerm {
+  unsigned lo;
+  int hi;
+};
+__device__ __forceinline__ SplitTerm split_term(int V, int s, int rshift, long long rnd) {
+  const long long P = (long long)V * (long long)s + rnd;
+  const unsigned plo = (unsigned)P, phi = (unsigned)(P >> 32);
+  return {__funnelshift_r(plo, phi, rshift) & 0xFFFFu, (int)phi >> (rshift - 16)};
+}
+
 // rint(y) with a range flag: |y| must stay below the largest float under 2^31
 __device__ __forceinline__ int to_fixed(float y, unsigned &bad) {
   if (!(fabsf(y) < 2147483520.0f)) bad |= kErrVelocityRange;

@@ -104,6 +104,8 @@ struct pic_handle {
   bool em = false;
   Em2dConst ce{};
   Em2dBufs be{};
+  Em1dMixConst c1m{};   // mixed form of the 1D2V path (em1 && mixed)
+  Em1dMixBufs b1m{};
   Em2dMixConst cme{};   // mixed form of the 2D3V path (em && mixed)
   Em2dMixBufs bme{};
   LaunchShape lp{1, 256}, lg{1, 256};
@@ -940,18 +942,103 @@ int init_std(pic_handle *h, const pic_species *species) {
 }
 
 // 1D2V spectral state change: validate markers, j^{n,*} and the half step.
-int restart_em1d(pic_handle *h) {
+// 1D2V state change: validate markers, j^{n,*} and the half step (E*, B*).
+// The mixed form takes its markers from the FP64 staging arrays only when
+// they changed.
+int restart_em1d(pic_handle *h, bool markers_changed = true) {
   Em1dBufs &b = h->b1e;
   const int n = h->c1e.n;
-  em1d_validate_kernel<<<h->le.grid, 256, 0, h->st>>>(b.y, b.vx, b.vy, h->N, h->c1e.L, b.err);
-  CUDA_TRY(cudaGetLastError());
+  if (markers_changed || !h->mixed) {
+    em1d_validate_kernel<<<h->le.grid, 256, 0, h->st>>>(b.y, b.vx, b.vy, h->N, h->c1e.L, b.err);
+    CUDA_TRY(cudaGetLastError());
+  }
   CUDA_TRY(cudaMemsetAsync(b.J1, 0, sizeof(double) * kJSlices * 2 * n, h->st));
   CUDA_TRY(cudaMemsetAsync(b.J2, 0, sizeof(double) * kJSlices * 2 * n, h->st));
   CUDA_TRY(cudaMemsetAsync(b.done, 0, sizeof(unsigned) * 2, h->st));
-  em1d_start(h->c1e, b, h->le, h->st);
+  if (h->mixed) {
+    const Em1dMixBufs &mb = h->b1m;
+    CUDA_TRY(cudaMemsetAsync(mb.J1, 0, sizeof(long long) * 2 * n, h->st));
+    CUDA_TRY(cudaMemsetAsync(mb.J2, 0, sizeof(long long) * 2 * n, h->st));
+    if (markers_changed) em1m_from_fp64(h->c1e, b, h->c1m, mb, h->le, h->st);
+    em1m_start(h->c1e, b, h->c1m, mb, h->le, h->st);
+    h->launches += 1 + (markers_changed ? 2 : 1) + 2 * (h->c1e.scheme == 2);
+  } else {
+    em1d_start(h->c1e, b, h->le, h->st);
+    h->launches += 2 + (h->c1e.scheme == 2);
+  }
   CUDA_TRY(cudaGetLastError());
-  h->launches += 2 + (h->c1e.scheme == 2);
   return check_flags(h, "pic_init/pic_set_*");
+}
+
+// Mixed form of the 1D2V path: the velocity scale from the largest initial
+// speed, the deposit shift from the markers per tile copy, the per-marker
+// state (the FP64 staging arrays hold the initial markers).
+int init_em1d_mixed(pic_handle *h) {
+  const Em1dConst &c = h->c1e;
+  const SpeciesInfo &S = h->sp[0];
+  Em1dMixConst &m = h->c1m;
+  Em1dMixBufs &mb = h->b1m;
+  m.n = c.n;
+  m.order = c.order;
+  m.scheme = c.scheme;
+  m.gamma_on = c.gamma_on;
+  m.rt = em1m_tile_copies(c.n);
+  m.N = h->N;
+  m.L = c.L;
+  m.dt = c.dt;
+  unsigned long long *mx = nullptr;
+  int rc;
+  if ((rc = h->alloc(&mx, 1))) return rc;
+  CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), h->st));
+  em1m_absmax(h->b1e, h->N, mx, h->le, h->st);
+  CUDA_TRY(cudaGetLastError());
+  unsigned long long bits = 0;
+  CUDA_TRY(cudaMemcpyAsync(&bits, mx, sizeof bits, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  double vmax;
+  memcpy(&vmax, &bits, sizeof vmax);
+  // V units of (dt 2^31 / L) 2^kv, with room for 8x the largest initial speed
+  // inside the 31-bit range; kv >= 1 keeps the half-step shift a rounded shift
+  const double cx = c.dt * 2147483648.0 / c.L;
+  const double vcap = std::max(8.0 * vmax, 1e-6 * c.L / c.dt);
+  const int kv = (int)std::floor(std::log2(1073741824.0 / (cx * vcap)));
+  m.kv = std::min(24, std::max(1, kv));
+  m.hround = 1 << (m.kv - 1);
+  m.cxk = std::ldexp(cx, m.kv);
+  // Terms round(V* s / 2^r) are below 2^T = 2^(54 - r).  pcnt markers add into
+  // one tile copy (the threads that share it, each over its grid-stride
+  // trips): its split counters need pcnt 2^16 < 2^32 and pcnt 2^(T-16) < 2^31,
+  // so T = 47 - ceil(log2 pcnt); the int64 sums need N 2^T < 2^63.
+  const int64_t threads = (int64_t)h->le.grid * 256;
+  const int64_t trips = (h->N + threads - 1) / threads;
+  const int64_t pcnt = std::max<int64_t>(1, trips * (256 / m.rt));
+  int lg = 0;
+  while (((int64_t)1 << lg) < pcnt) lg++;
+  int bitlen = 0;
+  while (bitlen < 62 && ((int64_t)1 << bitlen) <= h->N) bitlen++;
+  const int T = std::min(37, std::min(47 - lg, 62 - bitlen));
+  m.rshift = 54 - T;
+  if (m.rshift < 17 || m.rshift > 31)
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: %lld markers need a deposit shift of %d (17..31)",
+                (long long)h->N, m.rshift);
+  m.rnd = 1ll << (m.rshift - 1);
+  const double qm = S.q / S.m;
+  m.jscale = S.q * S.w0 * std::ldexp(1.0, m.rshift) / (c.h * m.cxk * 8388608.0);
+  m.ke_scale = 0.5 * S.m * S.w0 / (m.cxk * m.cxk);
+  m.e_half = 0.5 * c.dt * qm * m.cxk;
+  m.t_half = 0.5 * c.dt * qm;
+  m.kick = c.dt * qm * m.cxk;
+  m.m_full = c.dt * qm;
+  const size_t N = (size_t)h->N;
+  if ((rc = h->alloc(&mb.Y, N)) || (rc = h->alloc(&mb.J1, 2 * (size_t)c.n)) ||
+      (rc = h->alloc(&mb.J2, 2 * (size_t)c.n)))
+    return rc;
+  for (int d = 0; d < 2; d++)
+    if ((rc = h->alloc(&mb.vh[d], N)) || (rc = h->alloc(&mb.vl[d], N)) ||
+        (rc = h->alloc(&mb.Vs[d], N)))
+      return rc;
+  CUDA_TRY(em1m_prepare(c, m));
+  return PIC_OK;
 }
 
 // 1D2V with a spectral field solve: constants, SoA markers (y, vx, vy), fields.
@@ -989,9 +1076,9 @@ int init_em1d(pic_handle *h, const pic_species *species, const double *E0, const
   h->le.grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->N + 255) / 256, (int64_t)h->nsm * 2));
   const size_t n = (size_t)c.n;
   int rc;
-  if ((rc = h->alloc(&b.y, h->N)) || (rc = h->alloc(&b.vx, h->N)) || (rc = h->alloc(&b.vy, h->N)) ||
-      (rc = h->alloc(&b.vsx, h->N)) || (rc = h->alloc(&b.vsy, h->N)))
+  if ((rc = h->alloc(&b.y, h->N)) || (rc = h->alloc(&b.vx, h->N)) || (rc = h->alloc(&b.vy, h->N)))
     return rc;
+  if (!h->mixed && ((rc = h->alloc(&b.vsx, h->N)) || (rc = h->alloc(&b.vsy, h->N)))) return rc;
   b.w = nullptr;
   if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;
   double **e2[] = {&b.E, &b.En, &b.Es, &b.Ea};
@@ -1041,6 +1128,7 @@ int init_em1d(pic_handle *h, const pic_species *species, const double *E0, const
   if (E0) CUDA_TRY(cudaMemcpyAsync(b.E, E0, sizeof(double) * 2 * n, cudaMemcpyDefault, h->st));
   if (B0) CUDA_TRY(cudaMemcpyAsync(b.B, B0, sizeof(double) * n, cudaMemcpyDefault, h->st));
   CUDA_TRY(cudaStreamSynchronize(h->st));
+  if (h->mixed && (rc = init_em1d_mixed(h))) return rc;
   return restart_em1d(h);
 }
 
@@ -1114,8 +1202,7 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
                   kSpecMaxNodes);
     if (!(cfg->grid.L[0] > 0.0) || !(cfg->c > 0.0) || !std::isfinite(cfg->c))
       return fail(PIC_ERR_ARG, "pic_init: the spectral solvers need L > 0 and c > 0");
-    if (cfg->precision == PIC_PREC_MIXED)
-      return fail(PIC_ERR_UNSUPPORTED, "pic_init: the spectral solvers run in the FP64 form");
+
   } else if (cfg->solver == PIC_SOLVER_YEE_LEAPFROG) {
     if (cfg->grid.dim_x != 2 || cfg->grid.dim_v != 3)
       return fail(PIC_ERR_ARG, "pic_init: the Yee solver runs 2D3V (dim_x = 2, dim_v = 3)");
@@ -1211,8 +1298,15 @@ int pic_step_async(pic_handle *h, int nsteps) {
   for (int k = 0; k < nsteps && h->em1; k++) {
     Em1dBufs &e = h->b1e;
     const int slot = h->pending;
-    CUDA_TRY(h->timed_launch(0, [&] { em1d_pass_c(h->c1e, e, h->le, h->st); }));
-    CUDA_TRY(h->timed_launch(1, [&] { em1d_pass_e(h->c1e, e, slot, h->le, h->st); }));
+    if (h->mixed) {
+      CUDA_TRY(h->timed_launch(0, [&] { em1m_pass_c(h->c1e, e, h->c1m, h->b1m, h->le, h->st); }));
+      CUDA_TRY(h->timed_launch(1, [&] {
+        em1m_pass_e(h->c1e, e, h->c1m, h->b1m, slot, h->le, h->st);
+      }));
+    } else {
+      CUDA_TRY(h->timed_launch(0, [&] { em1d_pass_c(h->c1e, e, h->le, h->st); }));
+      CUDA_TRY(h->timed_launch(1, [&] { em1d_pass_e(h->c1e, e, slot, h->le, h->st); }));
+    }
     h->launches += 2;
     std::swap(e.E, e.En);
     std::swap(e.B, e.Bn);
@@ -1399,7 +1493,10 @@ static int energy_em2d(pic_handle *h, double *KE_per_species, double *W_E, doubl
 static int energy_em1d(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, double *TE) {
   const int nb = h->le.grid;
   double *ke = h->e1_part, *wf = h->e1_part + (size_t)nb * h->nsp;
-  em1d_energy(h->c1e, h->b1e, ke, wf, h->le, h->st);
+  if (h->mixed)
+    em1m_energy(h->c1e, h->b1e, h->c1m, h->b1m, ke, wf, h->le, h->st);
+  else
+    em1d_energy(h->c1e, h->b1e, ke, wf, h->le, h->st);
   CUDA_TRY(cudaGetLastError());
   h->launches += 1;
   std::vector<double> part((size_t)nb * h->nsp + 2);
@@ -1504,6 +1601,10 @@ int pic_get_particles(pic_handle *h, int s, double *x, double *v) {
     return PIC_OK;
   }
   if (h->em1) {
+    if (h->mixed) {
+      em1m_to_fp64(h->c1e, h->b1e, h->c1m, h->b1m, h->le, h->st);
+      CUDA_TRY(cudaGetLastError());
+    }
     if (x) CUDA_TRY(cudaMemcpyAsync(x, h->b1e.y + S.offset, sizeof(double) * S.n, cudaMemcpyDefault,
                                     h->st));
     if (v) {
@@ -1630,7 +1731,7 @@ int pic_set_fields(pic_handle *h, const double *E, const double *B) {
     CUDA_TRY(cudaMemcpyAsync(h->b1e.E, E, sizeof(double) * 2 * n, cudaMemcpyDefault, h->st));
     CUDA_TRY(cudaMemcpyAsync(h->b1e.B, B, sizeof(double) * n, cudaMemcpyDefault, h->st));
     CUDA_TRY(cudaStreamSynchronize(h->st));
-    return restart_em1d(h);
+    return restart_em1d(h, false);
   }
   if (h->em) {
     if (!B) return fail(PIC_ERR_ARG, "pic_set_fields: the Yee solver needs B^{n-1/2}");

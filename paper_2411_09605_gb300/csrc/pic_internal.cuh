@@ -220,6 +220,36 @@ struct StdBufs {
   unsigned *err;
 };
 
+// Mixed form of the 1D2V spectral path (one species, uniform weight): y as
+// 32-bit fixed point (y = Y L / 2^32), (vx, vy) as float pairs in V units
+// (v cxk, one V unit moves a marker 2^-kv position units in half a step), v*
+// as integers, the currents (jx, jy) as exact integer sums of round(V* s /
+// 2^rshift) through per-lane split tiles; the fields and the field solve stay
+// FP64 (Em1dBufs), fed with jscale times the integer sums.
+struct Em1dMixConst {
+  int n, order, scheme, gamma_on;
+  int rt;              // copies of the shared current tile
+  int kv, hround;      // V units -> half-step position shift: (V + hround) >> kv
+  int rshift;          // current term = round(V* s / 2^rshift), rshift in [17, 31]
+  long long rnd;       // 2^(rshift - 1)
+  int64_t N;
+  double L, dt;
+  double cxk;          // (dt 2^31 / L) 2^kv
+  double jscale;       // J = jscale * (integer node sum)
+  double ke_scale;     // (m w / 2) / cxk^2
+  double e_half;       // dt/2 (q/m) cxk: E* -> V units
+  double t_half;       // dt/2 (q/m): Bz* -> the rotation t of v*
+  double kick;         // dt (q/m) cxk: the E of v^dag -> V units
+  double m_full;       // dt (q/m): V* x B^{n+1/2} -> V units
+};
+
+struct Em1dMixBufs {
+  uint32_t *Y;                // [N]
+  float *vh[2], *vl[2];       // [N] (vx, vy) pairs in V units
+  int *Vs[2];                 // [N] V* (pass C -> pass E)
+  long long *J1, *J2;         // [2][n] integer sums of j^{n,*} and j^{*,n+1/2}
+};
+
 // Mixed form of the 2D3V Yee path (one species, uniform weight, square
 // domain): positions X, Y as 32-bit fixed point (x = X L / 2^32), velocities as
 // float pairs in V units (v cxk; one V unit moves a marker 2^-kv position units
@@ -366,6 +396,32 @@ void em2dm_kinetic(const Em2dMixConst &m, const Em2dMixBufs &mb, double *out, La
 // largest |v| component of the FP64 staging velocities (bits of a double)
 void em2dm_absmax(const Em2dBufs &b, int64_t n, unsigned long long *out, LaunchShape lp,
                   cudaStream_t st);
+
+// 1D2V spectral path, mixed form (em1d_spectral.cu): the FP64 field side of
+// Em1dBufs, the markers of Em1dMixBufs
+void em1m_pass_c(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
+                 const Em1dMixBufs &mb, LaunchShape lp, cudaStream_t st);
+void em1m_pass_e(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
+                 const Em1dMixBufs &mb, int slot, LaunchShape lp, cudaStream_t st);
+// j^{0,*} (ESEC2) and the first half step (E*, B*) of the current state
+void em1m_start(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
+                const Em1dMixBufs &mb, LaunchShape lp, cudaStream_t st);
+// FP64 staging (y, vx, vy of Em1dBufs) <-> the mixed markers
+void em1m_from_fp64(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
+                    const Em1dMixBufs &mb, LaunchShape lp, cudaStream_t st);
+void em1m_to_fp64(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
+                  const Em1dMixBufs &mb, LaunchShape lp, cudaStream_t st);
+// kinetic energy block partials of the mixed markers, and W_E, W_B (em1d_energy's layout)
+void em1m_energy(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
+                 const Em1dMixBufs &mb, double *ke_out, double *wf, LaunchShape lp,
+                 cudaStream_t st);
+// largest |v| component of the FP64 staging velocities (bits of a double)
+void em1m_absmax(const Em1dBufs &b, int64_t n, unsigned long long *out, LaunchShape lp,
+                 cudaStream_t st);
+// tile copies of the mixed passes: the largest power of two <= 32 whose tile
+// and tables fit the budget
+int em1m_tile_copies(int n);
+cudaError_t em1m_prepare(const Em1dConst &c, const Em1dMixConst &m);
 
 // 1D2V spectral path (em1d_spectral.cu)
 // shared-memory opt-in and the twiddle / coefficient tables (b.tw, b.coef)

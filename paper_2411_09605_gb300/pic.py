@@ -357,9 +357,9 @@ class Simulation1D2V:
     a ``workloads.Problem1D2V``."""
 
     def __init__(self, prob, solver=PIC_SOLVER_PSATD, scheme=PIC_SCHEME_ESEC2, E0=None, B0=None,
-                 gamma_on=True, stream=None):
+                 gamma_on=True, stream=None, precision=PIC_PREC_FP64):
         self.prob = prob
-        self.cfg = make_config(prob.n, prob.L, prob.dt, prob.order, scheme, PIC_PREC_FP64,
+        self.cfg = make_config(prob.n, prob.L, prob.dt, prob.order, scheme, precision,
                                solver=solver, dim_x=1, dim_v=2, c=prob.c, gamma_on=gamma_on,
                                stream=stream)
         self.species = []

@@ -67,9 +67,9 @@ def test_argument_errors_are_status_codes(lib):
     with pytest.raises(pic.PicError) as ei:
         pic.pic_init(pic.make_config(64, 1.0, 0.1), [])
     assert ei.value.code == -1
-    with pytest.raises(pic.PicError) as ei:   # the spectral solvers have no mixed form
+    with pytest.raises(pic.PicError) as ei:   # the mixed forms run one species
         pic.pic_init(pic.make_config(64, 1.0, 0.1, precision=pic.PIC_PREC_MIXED,
-                                     solver=pic.PIC_SOLVER_PSATD, dim_v=2), sp)
+                                     solver=pic.PIC_SOLVER_PSATD, dim_v=2), sp * 2)
     assert ei.value.code == -7
     with pytest.raises(pic.PicError) as ei:   # no filtering in the mixed form
         pic.pic_init(pic.make_config(64, 1.0, 0.1, binomial_passes=1,
