@@ -644,14 +644,104 @@ EM1D_ALGO_BYTES = {0: 40, 1: 64}          # pass C also writes v*, pass E reads 
 EM1D_FP64_INST_PER_MARKER = {0: 54.45, 1: 85.35}
 # DRAM bytes per launch at 2^23 markers (dram__bytes_read.sum + dram__bytes_write.sum)
 EM1D_TRAFFIC = {0: None, 1: 487232768}
+# the mixed form: y (u32) and two float pairs; pass C writes V* (2 x i32),
+# pass E reads it and writes y and the pairs
+EM1D_MIX_ALGO_BYTES = {0: 28, 1: 48}
+EM1D_MIX_TRAFFIC = {0: None, 1: None}
+
+
+def _weibel1d_form(W, pic, torch, solver, precision, args, stream, flush, peak, long_steps):
+    """One solver in one form: the paper's size over a long run (energy) and
+    2^23 markers with per-step events and an L2 flush before each (throughput)."""
+    res = {}
+    # the paper's size: state 2.5 MB, L2-resident; chunks of <= 1000 steps
+    prob = W.weibel_1d2v(seed=0)
+    sim = pic.Simulation1D2V(prob, solver=solver, stream=stream.cuda_stream, precision=precision)
+    try:
+        te0 = sim.energy()[3]
+        fbs, tes, ms = [], [], 0.0
+        left = long_steps
+        while left:
+            k = min(left, 1000)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            pic.pic_step_async(sim.h, k)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+            fb, te = pic.pic_read_stats(sim.h)
+            fbs.append(fb)
+            tes.append(te)
+            left -= k
+        fb, te = np.concatenate(fbs), np.concatenate(tes)
+        WE = sim.energy()
+    finally:
+        sim.close()
+    res["paper_size"] = {
+        "markers": prob.n_markers, "steps": long_steps, "t_end": long_steps * prob.dt,
+        "value": prob.n_markers * long_steps / (ms / 1e3), "us_per_step": 1e3 * ms / long_steps,
+        "max_rel_dTE": float(np.max(np.abs(te - te0)) / te0), "fallbacks": int(fb.sum()),
+        "W_B_end": WE[2], "l2": "resident (2.5 MB state), not flushed"}
+    big = W.weibel_1d2v(ppc=(1 << 23) // 32, seed=1)
+    sim = pic.Simulation1D2V(big, solver=solver, stream=stream.cuda_stream, precision=precision)
+    try:
+        te0 = sim.energy()[3]
+        pic.pic_step_async(sim.h, max(3, args.warmup))
+        pic.pic_read_stats(sim.h)
+        evs = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pic.pic_step_async(sim.h, 1)
+            b.record(stream)
+            evs.append((a, b))
+        fb, te = pic.pic_read_stats(sim.h)
+        torch.cuda.synchronize()
+        step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+        pic.pic_set_profiling(sim.h, True)
+        for _ in range(args.profile_steps):
+            flush.zero_()
+            pic.pic_step_async(sim.h, 1)
+        pic.pic_read_stats(sim.h)
+        kern = {}
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        fp64_peak = FP64_LANES_PER_SM_CLK * nsm * 2070.0e6 / 1e9   # Ginst/s
+        for kind, kname in ((0, "pass_c"), (1, "pass_e")):
+            n, tot = pic.pic_profile(sim.h, kind)
+            if n:
+                avg = 1e3 * tot / n
+                algo = (EM1D_MIX_ALGO_BYTES if precision else EM1D_ALGO_BYTES)[kind]
+                ach = algo * big.n_markers / (avg * 1e-6) / 1e9
+                kern[kname] = {"avg_us": avg, "launches": n, "achieved_GBs": round(ach, 1),
+                               "frac_hbm": round(ach / peak, 4)}
+                if not precision:
+                    inst = EM1D_FP64_INST_PER_MARKER[kind] * big.n_markers / (avg * 1e-6) / 1e9
+                    kern[kname].update({"fp64_ginst_s": round(inst, 1),
+                                        "fp64_peak": round(fp64_peak, 1),
+                                        "frac_fp64": round(inst / fp64_peak, 4)})
+        pic.pic_set_profiling(sim.h, False)
+    finally:
+        sim.close()
+    res["2p23"] = {"markers": big.n_markers, "steps": args.steps,
+                   "value": big.n_markers * args.steps / (step_ms.sum() / 1e3),
+                   "us_per_step": 1e3 * float(step_ms.mean()),
+                   "max_rel_dTE": float(np.max(np.abs(te - te0)) / te0),
+                   "fallbacks": int(fb.sum()), "kernels": kern,
+                   "l2": "flushed (512 MiB write) before every timed step"}
+    return res
 
 
 def run_weibel1d(args):
     """The 1D2V Weibel test of Sec. 5 (32 cells, beta 0.01, beams +-0.3, b 0.001,
-    k0 0.2, dt 0.1, c 1) with both spectral field solves: the paper's size
-    (3200 markers per cell, 102,400 markers) over a long run for the energy
-    error, and 2^23 markers (262,144 per cell) for throughput and the HBM
-    roofline of the passes."""
+    k0 0.2, dt 0.1, c 1) with both spectral field solves, each in the FP64 and
+    the mixed form: the paper's size (3200 markers per cell, 102,400 markers)
+    over a long run for the energy error, and 2^23 markers (262,144 per cell)
+    for throughput and the roofline of the passes.  The headline is PSATD in
+    the mixed form at 2^23 markers."""
     import torch
     from paper_2411_09605_gb300 import build as B, pic, workloads as W
     B.build()
@@ -664,104 +754,27 @@ def run_weibel1d(args):
     out = {}
     with ClockSampler(0, enabled=not args.no_clocks) as clk:
         for name, solver in (("cn", pic.PIC_SOLVER_CN_SPECTRAL), ("psatd", pic.PIC_SOLVER_PSATD)):
-            res = {}
-            # the paper's size: state 2.5 MB, L2-resident; chunks of <= 1000 steps
-            prob = W.weibel_1d2v(seed=0)
-            sim = pic.Simulation1D2V(prob, solver=solver, stream=stream.cuda_stream)
-            try:
-                te0 = sim.energy()[3]
-                fbs, tes, ms = [], [], 0.0
-                left = long_steps
-                while left:
-                    k = min(left, 1000)
-                    a = torch.cuda.Event(enable_timing=True)
-                    b = torch.cuda.Event(enable_timing=True)
-                    torch.cuda.synchronize()
-                    a.record(stream)
-                    pic.pic_step_async(sim.h, k)
-                    b.record(stream)
-                    torch.cuda.synchronize()
-                    ms += a.elapsed_time(b)
-                    fb, te = pic.pic_read_stats(sim.h)
-                    fbs.append(fb)
-                    tes.append(te)
-                    left -= k
-                fb, te = np.concatenate(fbs), np.concatenate(tes)
-                WE = sim.energy()
-            finally:
-                sim.close()
-            res["paper_size"] = {
-                "markers": prob.n_markers, "steps": long_steps, "t_end": long_steps * prob.dt,
-                "value": prob.n_markers * long_steps / (ms / 1e3), "us_per_step": 1e3 * ms / long_steps,
-                "max_rel_dTE": float(np.max(np.abs(te - te0)) / te0), "fallbacks": int(fb.sum()),
-                "W_B_end": WE[2], "l2": "resident (2.5 MB state), not flushed"}
-            # 2^23 markers: per-step events, L2 flushed between steps
-            big = W.weibel_1d2v(ppc=(1 << 23) // 32, seed=1)
-            sim = pic.Simulation1D2V(big, solver=solver, stream=stream.cuda_stream)
-            try:
-                te0 = sim.energy()[3]
-                pic.pic_step_async(sim.h, max(3, args.warmup))
-                pic.pic_read_stats(sim.h)
-                evs = []
-                for _ in range(args.steps):
-                    flush.zero_()
-                    a = torch.cuda.Event(enable_timing=True)
-                    b = torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
-                    pic.pic_step_async(sim.h, 1)
-                    b.record(stream)
-                    evs.append((a, b))
-                fb, te = pic.pic_read_stats(sim.h)
-                torch.cuda.synchronize()
-                step_ms = np.array([a.elapsed_time(b) for a, b in evs])
-                pic.pic_set_profiling(sim.h, True)
-                for _ in range(args.profile_steps):
-                    flush.zero_()
-                    pic.pic_step_async(sim.h, 1)
-                pic.pic_read_stats(sim.h)
-                kern = {}
-                nsm = torch.cuda.get_device_properties(0).multi_processor_count
-                fp64_peak = FP64_LANES_PER_SM_CLK * nsm * 2070.0e6 / 1e9   # Ginst/s
-                for kind, kname in ((0, "pass_c"), (1, "pass_e")):
-                    n, tot = pic.pic_profile(sim.h, kind)
-                    if n:
-                        avg = 1e3 * tot / n
-                        ach = EM1D_ALGO_BYTES[kind] * big.n_markers / (avg * 1e-6) / 1e9
-                        inst = EM1D_FP64_INST_PER_MARKER[kind] * big.n_markers / (avg * 1e-6) / 1e9
-                        kern[kname] = {"avg_us": avg, "launches": n, "achieved_GBs": round(ach, 1),
-                                       "frac_hbm": round(ach / peak, 4),
-                                       "fp64_ginst_s": round(inst, 1), "fp64_peak": round(fp64_peak, 1),
-                                       "frac_fp64": round(inst / fp64_peak, 4)}
-                pic.pic_set_profiling(sim.h, False)
-            finally:
-                sim.close()
-            res["2p23"] = {"markers": big.n_markers, "steps": args.steps,
-                           "value": big.n_markers * args.steps / (step_ms.sum() / 1e3),
-                           "us_per_step": 1e3 * float(step_ms.mean()),
-                           "max_rel_dTE": float(np.max(np.abs(te - te0)) / te0),
-                           "fallbacks": int(fb.sum()), "kernels": kern,
-                           "l2": "flushed (512 MiB write) before every timed step"}
-            out[name] = res
-    head = out["psatd"]["2p23"]
+            for form, precision in (("fp64", 0), ("mixed", 1)):
+                out[f"{name}_{form}"] = _weibel1d_form(W, pic, torch, solver, precision, args,
+                                                       stream, flush, peak, long_steps)
+    head = out["psatd_mixed"]["2p23"]
     dom = max(head["kernels"].items(), key=lambda kv: kv[1]["avg_us"])
     line = {
         "metric": "particle-steps/s, 1D2V Weibel with spectral EM field solves",
         "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": head["us_per_step"] / 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+i32+i64 (fields, field solve and energy in f64)",
         "data": "synthetic (seeded Weibel markers, quiet start in y)",
         "config": {"workload": "weibel_1d2v", "cells": 32, "dt": 0.1, "c": 1.0, "shape_order": 1,
-                   "scheme": "ESEC2", "value_from": "PSATD at 2^23 markers"},
-        "roofline": {"bound": "alu", "kernel": dom[0], "achieved": dom[1]["fp64_ginst_s"],
-                     "peak": dom[1]["fp64_peak"], "unit": "Ginst/s (FP64 pipe)",
-                     "frac": dom[1]["frac_fp64"],
-                     "traffic": EM1D_TRAFFIC[0 if dom[0] == "pass_c" else 1],
-                     "peak_source": f"{FP64_LANES_PER_SM_CLK} FP64 lanes/SM/clk x SMs x 2070 MHz",
-                     "hbm_frac": dom[1]["frac_hbm"]},
+                   "scheme": "ESEC2", "value_from": "PSATD, mixed form, at 2^23 markers"},
+        "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": dom[1]["achieved_GBs"],
+                     "peak": peak, "unit": "GB/s", "frac": dom[1]["frac_hbm"],
+                     "traffic": EM1D_MIX_TRAFFIC[0 if dom[0] == "pass_c" else 1],
+                     "peak_source": peak_src},
         "solvers": out, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
-
 
 def run_grad(args):
     """Reverse mode of the FP64 form on the bump-on-tail workload (2^20 weighted

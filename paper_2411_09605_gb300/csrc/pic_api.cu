@@ -1073,7 +1073,11 @@ int init_em1d(pic_handle *h, const pic_species *species, const double *E0, const
   }
   for (int s = h->nsp; s < kMaxSpecies; s++) c.sp_end[s] = h->N;
   h->le.block = 256;
-  h->le.grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->N + 255) / 256, (int64_t)h->nsm * 2));
+  // the FP64 passes are bound by the FP64 pipe (two blocks per SM keep it
+  // busy); the mixed passes need the latency hiding of four (at 64 registers
+  // a thread, four 256-thread blocks fill an SM's register file)
+  const int64_t per_sm = h->mixed ? 4 : 2;
+  h->le.grid = (int)std::max<int64_t>(1, std::min<int64_t>((h->N + 255) / 256, (int64_t)h->nsm * per_sm));
   const size_t n = (size_t)c.n;
   int rc;
   if ((rc = h->alloc(&b.y, h->N)) || (rc = h->alloc(&b.vx, h->N)) || (rc = h->alloc(&b.vy, h->N)))
