@@ -102,10 +102,11 @@ typedef enum { PIC_SCHEME_ESEC1 = 1, PIC_SCHEME_ESEC2 = 2 } pic_scheme;
  * FP32, current accumulated exactly in 64-bit integers, Gamma from an exact
  * difference; energy reductions in double.  Conserves energy to the same
  * bound (the pairing of Eq. exp_econs_simple is exact by construction).
- * Runs the Ampere solver (1D1V) and the Yee solver (2D3V, square domain
- * L[0] == L[1], where the fields stay FP64 on the grid and the magnetic force
- * V* x B is formed in float pairs from the integer v*, so it does no work);
- * one species with a uniform weight, else PIC_ERR_UNSUPPORTED. */
+ * Runs the Ampere solver (1D1V), the Yee solver (2D3V, square domain
+ * L[0] == L[1]) and the spectral solvers (1D2V); in the electromagnetic
+ * solvers the fields and their update stay FP64 and the magnetic force
+ * V* x B is formed in float pairs from the integer v*, so it does no work.
+ * One species with a uniform weight, else PIC_ERR_UNSUPPORTED. */
 typedef enum { PIC_PREC_FP64 = 0, PIC_PREC_MIXED = 1 } pic_precision;
 
 typedef struct {
