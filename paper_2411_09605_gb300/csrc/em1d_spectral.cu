@@ -554,7 +554,7 @@ __device__ __forceinline__ ff2 correct_velocity_xy(float2 vh, float2 vl, int Vx,
 }
 
 template <int ORDER>
-__global__ void __launch_bounds__(kEm1Threads) em1m_pass_c_kernel(Em1dConst c, Em1dBufs b,
+__global__ void __launch_bounds__(kEm1Threads, 4) em1m_pass_c_kernel(Em1dConst c, Em1dBufs b,
                                                                    Em1dMixConst m,
                                                                    Em1dMixBufs mb) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -571,31 +571,51 @@ __global__ void __launch_bounds__(kEm1Threads) em1m_pass_c_kernel(Em1dConst c, E
   __syncthreads();
   unsigned *Jl = Jt + (threadIdx.x & (rt - 1));
   unsigned bad = 0;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m.N;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t Y = mb.Y[p];
-    const float vxh = mb.vh[0][p], vxl = mb.vl[0][p], vyh = mb.vh[1][p], vyl = mb.vl[1][p];
-    // gather #1 at y* = y^n + dt/2 vy^n: e_half E*, t = t_half B*z
-    const ShapeMix<ORDER> S1(Y + half_shift1(to_fixed(vyh, bad), m), n);
-    float ex = 0.0f, ey = 0.0f, t = 0.0f;
+  // four consecutive markers per thread and trip, loaded 16 bytes at a time
+  // (the arrays are padded to a multiple of four)
+  const int64_t ngroups = (m.N + 3) / 4;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 Yq = reinterpret_cast<const uint4 *>(mb.Y)[g];
+    const float4 xh4 = reinterpret_cast<const float4 *>(mb.vh[0])[g];
+    const float4 xl4 = reinterpret_cast<const float4 *>(mb.vl[0])[g];
+    const float4 yh4 = reinterpret_cast<const float4 *>(mb.vh[1])[g];
+    const float4 yl4 = reinterpret_cast<const float4 *>(mb.vl[1])[g];
+    const uint32_t Ya[4] = {Yq.x, Yq.y, Yq.z, Yq.w};
+    const float xha[4] = {xh4.x, xh4.y, xh4.z, xh4.w}, xla[4] = {xl4.x, xl4.y, xl4.z, xl4.w};
+    const float yha[4] = {yh4.x, yh4.y, yh4.z, yh4.w}, yla[4] = {yl4.x, yl4.y, yl4.z, yl4.w};
+    int Vxa[4], Vya[4];
 #pragma unroll
-    for (int k = 0; k <= ORDER; k++) {
-      const float4 f = T[S1.p + k];
-      ex = __fmaf_rn(S1.w[k], f.x, ex);
-      ey = __fmaf_rn(S1.w[k], f.y, ey);
-      t = __fmaf_rn(S1.w[k], f.z, t);
+    for (int j = 0; j < 4; j++) {
+      const bool valid = 4 * g + j < m.N;
+      const uint32_t Y = Ya[j];
+      const float vxh = xha[j], vxl = xla[j], vyh = yha[j], vyl = yla[j];
+      unsigned flags = 0;
+      // gather #1 at y* = y^n + dt/2 vy^n: e_half E*, t = t_half B*z
+      const ShapeMix<ORDER> S1(Y + half_shift1(to_fixed(vyh, flags), m), n);
+      float ex = 0.0f, ey = 0.0f, t = 0.0f;
+#pragma unroll
+      for (int k = 0; k <= ORDER; k++) {
+        const float4 f = T[S1.p + k];
+        ex = __fmaf_rn(S1.w[k], f.x, ex);
+        ey = __fmaf_rn(S1.w[k], f.y, ey);
+        t = __fmaf_rn(S1.w[k], f.z, t);
+      }
+      // v* = (ux + t uy, uy - t ux) / (1 + t^2), u = v^n + e: v* = u + correction
+      const float ux = __fadd_rn(vxh, ex), uy = __fadd_rn(vyh, ey);
+      const float tt = __fmul_rn(t, t), inv = __frcp_rn(__fadd_rn(1.0f, tt));
+      const float cx = __fmul_rn(__fmaf_rn(t, uy, -__fmul_rn(tt, ux)), inv);
+      const float cy = __fmul_rn(__fmaf_rn(-t, ux, -__fmul_rn(tt, uy)), inv);
+      Vxa[j] = vstar_fixed(vxh, vxl, __fadd_rn(ex, cx), flags);
+      Vya[j] = vstar_fixed(vyh, vyl, __fadd_rn(ey, cy), flags);
+      if (valid) {
+        bad |= flags;
+        const ShapeMix<ORDER> Sh(Y + half_shift1(Vya[j], m), n);
+        mix_tile_deposit<ORDER>(Jl, rt, Sh, Vxa[j], Vya[j], m);
+      }
     }
-    // v* = (ux + t uy, uy - t ux) / (1 + t^2), u = v^n + e: v* = u + correction
-    const float ux = __fadd_rn(vxh, ex), uy = __fadd_rn(vyh, ey);
-    const float tt = __fmul_rn(t, t), inv = __frcp_rn(__fadd_rn(1.0f, tt));
-    const float cx = __fmul_rn(__fmaf_rn(t, uy, -__fmul_rn(tt, ux)), inv);
-    const float cy = __fmul_rn(__fmaf_rn(-t, ux, -__fmul_rn(tt, uy)), inv);
-    const int Vx = vstar_fixed(vxh, vxl, __fadd_rn(ex, cx), bad);
-    const int Vy = vstar_fixed(vyh, vyl, __fadd_rn(ey, cy), bad);
-    const ShapeMix<ORDER> Sh(Y + half_shift1(Vy, m), n);
-    mix_tile_deposit<ORDER>(Jl, rt, Sh, Vx, Vy, m);
-    mb.Vs[0][p] = Vx;
-    mb.Vs[1][p] = Vy;
+    reinterpret_cast<int4 *>(mb.Vs[0])[g] = make_int4(Vxa[0], Vxa[1], Vxa[2], Vxa[3]);
+    reinterpret_cast<int4 *>(mb.Vs[1])[g] = make_int4(Vya[0], Vya[1], Vya[2], Vya[3]);
   }
   if (bad) atomicOr(b.err, bad);
   __syncthreads();
@@ -610,7 +630,7 @@ __global__ void __launch_bounds__(kEm1Threads) em1m_pass_c_kernel(Em1dConst c, E
 }
 
 template <int ORDER>
-__global__ void __launch_bounds__(kEm1Threads) em1m_pass_e_kernel(Em1dConst c, Em1dBufs b,
+__global__ void __launch_bounds__(kEm1Threads, 4) em1m_pass_e_kernel(Em1dConst c, Em1dBufs b,
                                                                    Em1dMixConst m,
                                                                    Em1dMixBufs mb, int slot) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -631,61 +651,84 @@ __global__ void __launch_bounds__(kEm1Threads) em1m_pass_e_kernel(Em1dConst c, E
   unsigned *Jl = Jt + (threadIdx.x & (rt - 1));
   float2 keh = make_float2(0.0f, 0.0f), kel = make_float2(0.0f, 0.0f);
   unsigned nfb = 0, bad = 0;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m.N;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t Y = mb.Y[p];
-    const float2 vh = make_float2(mb.vh[0][p], mb.vh[1][p]);
-    const float2 vl = make_float2(mb.vl[0][p], mb.vl[1][p]);
-    const int Vx = mb.Vs[0][p], Vy = mb.Vs[1][p];
-    const uint32_t hs = half_shift1(Vy, m);
-    const ShapeMix<ORDER> S(Y + hs, n);
-    // gather #2 at y^{n+1/2}: kick E as float pairs (lane x: Ex, lane y: Ey)
-    float2 ph[ORDER + 1], pl = make_float2(0.0f, 0.0f);
-    float bz = 0.0f;
+  // four consecutive markers per thread and trip, loaded and stored 16 bytes
+  // at a time (the arrays are padded to a multiple of four)
+  const int64_t ngroups = (m.N + 3) / 4;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 Yq = reinterpret_cast<const uint4 *>(mb.Y)[g];
+    const float4 xh4 = reinterpret_cast<const float4 *>(mb.vh[0])[g];
+    const float4 xl4 = reinterpret_cast<const float4 *>(mb.vl[0])[g];
+    const float4 yh4 = reinterpret_cast<const float4 *>(mb.vh[1])[g];
+    const float4 yl4 = reinterpret_cast<const float4 *>(mb.vl[1])[g];
+    const int4 vx4 = reinterpret_cast<const int4 *>(mb.Vs[0])[g];
+    const int4 vy4 = reinterpret_cast<const int4 *>(mb.Vs[1])[g];
+    uint32_t Ya[4] = {Yq.x, Yq.y, Yq.z, Yq.w};
+    float xha[4] = {xh4.x, xh4.y, xh4.z, xh4.w}, xla[4] = {xl4.x, xl4.y, xl4.z, xl4.w};
+    float yha[4] = {yh4.x, yh4.y, yh4.z, yh4.w}, yla[4] = {yl4.x, yl4.y, yl4.z, yl4.w};
+    const int Vxa[4] = {vx4.x, vx4.y, vx4.z, vx4.w}, Vya[4] = {vy4.x, vy4.y, vy4.z, vy4.w};
 #pragma unroll
-    for (int k = 0; k <= ORDER; k++) {
-      const float4 e = Ta[S.p + k];
-      const float2 w = splat2(S.w[k]);
-      const ff2 pr = two_prod2(make_float2(e.x, e.z), w);
-      ph[k] = pr.hi;
-      pl = add2(pl, fma2(make_float2(e.y, e.w), w, pr.lo));
-      bz = __fmaf_rn(S.w[k], Tb[S.p + k], bz);
-    }
-    ff2 Ep = two_sum2(ph[0], ph[1]);
-    pl = add2(pl, Ep.lo);
-    if (ORDER == 2) {
-      Ep = two_sum2(Ep.hi, ph[ORDER]);
+    for (int j = 0; j < 4; j++) {
+      const bool valid = 4 * g + j < m.N;
+      const uint32_t Y = Ya[j];
+      const float2 vh = make_float2(xha[j], yha[j]), vl = make_float2(xla[j], yla[j]);
+      const int Vx = Vxa[j], Vy = Vya[j];
+      const uint32_t hs = half_shift1(Vy, m);
+      const ShapeMix<ORDER> S(Y + hs, n);
+      // gather #2 at y^{n+1/2}: kick E as float pairs (lane x: Ex, lane y: Ey)
+      float2 ph[ORDER + 1], pl = make_float2(0.0f, 0.0f);
+      float bz = 0.0f;
+#pragma unroll
+      for (int k = 0; k <= ORDER; k++) {
+        const float4 e = Ta[S.p + k];
+        const float2 w = splat2(S.w[k]);
+        const ff2 pr = two_prod2(make_float2(e.x, e.z), w);
+        ph[k] = pr.hi;
+        pl = add2(pl, fma2(make_float2(e.y, e.w), w, pr.lo));
+        bz = __fmaf_rn(S.w[k], Tb[S.p + k], bz);
+      }
+      ff2 Ep = two_sum2(ph[0], ph[1]);
       pl = add2(pl, Ep.lo);
+      if (ORDER == 2) {
+        Ep = two_sum2(Ep.hi, ph[ORDER]);
+        pl = add2(pl, Ep.lo);
+      }
+      // Delta = d + dt (q/m) (V*y Bz, -V*x Bz), the products in float pairs of the exact V*
+      const float fx = __int2float_rn(Vx), fy = __int2float_rn(Vy);
+      const ff2 vs{make_float2(fy, fx), make_float2(__int2float_rn(Vy - __float2int_rn(fy)),
+                                                    __int2float_rn(Vx - __float2int_rn(fx)))};
+      ff2 mu = two_prod2(vs.hi, splat2(bz));
+      mu.lo = fma2(vs.lo, splat2(bz), mu.lo);
+      mu = fast_two_sum2(mu.hi, mu.lo);
+      mu.hi.y = -mu.hi.y;
+      mu.lo.y = -mu.lo.y;
+      const ff2 D = ff_add2(fast_two_sum2(Ep.hi, pl), mu);
+      const ff2 vn = correct_velocity_xy(vh, vl, Vx, Vy, D, c.gamma_on != 0 && valid, nfb);
+      if (!valid) continue;
+      {
+        ff2 s2 = two_prod2(vn.hi, vn.hi);
+        s2.lo = fma2(add2(vn.hi, vn.hi), vn.lo, s2.lo);
+        const ff2 acc = two_sum2(keh, s2.hi);
+        keh = acc.hi;
+        kel = add2(kel, add2(acc.lo, s2.lo));
+      }
+      const uint32_t Y1 = Y + 2u * hs;
+      if (c.scheme == 2) {
+        const int V1x = to_fixed(vn.hi.x, bad), V1y = to_fixed(vn.hi.y, bad);
+        const ShapeMix<ORDER> S1(Y1 + half_shift1(V1y, m), n);
+        mix_tile_deposit<ORDER>(Jl, rt, S1, V1x, V1y, m);
+      }
+      Ya[j] = Y1;
+      xha[j] = vn.hi.x;
+      xla[j] = vn.lo.x;
+      yha[j] = vn.hi.y;
+      yla[j] = vn.lo.y;
     }
-    // Delta = d + dt (q/m) (V*y Bz, -V*x Bz), the products in float pairs of the exact V*
-    const float fx = __int2float_rn(Vx), fy = __int2float_rn(Vy);
-    const ff2 vs{make_float2(fy, fx), make_float2(__int2float_rn(Vy - __float2int_rn(fy)),
-                                                  __int2float_rn(Vx - __float2int_rn(fx)))};
-    ff2 mu = two_prod2(vs.hi, splat2(bz));
-    mu.lo = fma2(vs.lo, splat2(bz), mu.lo);
-    mu = fast_two_sum2(mu.hi, mu.lo);
-    mu.hi.y = -mu.hi.y;
-    mu.lo.y = -mu.lo.y;
-    const ff2 D = ff_add2(fast_two_sum2(Ep.hi, pl), mu);
-    const ff2 vn = correct_velocity_xy(vh, vl, Vx, Vy, D, c.gamma_on != 0, nfb);
-    {
-      ff2 s2 = two_prod2(vn.hi, vn.hi);
-      s2.lo = fma2(add2(vn.hi, vn.hi), vn.lo, s2.lo);
-      const ff2 acc = two_sum2(keh, s2.hi);
-      keh = acc.hi;
-      kel = add2(kel, add2(acc.lo, s2.lo));
-    }
-    const uint32_t Y1 = Y + 2u * hs;
-    if (c.scheme == 2) {
-      const int V1x = to_fixed(vn.hi.x, bad), V1y = to_fixed(vn.hi.y, bad);
-      const ShapeMix<ORDER> S1(Y1 + half_shift1(V1y, m), n);
-      mix_tile_deposit<ORDER>(Jl, rt, S1, V1x, V1y, m);
-    }
-    mb.Y[p] = Y1;
-    mb.vh[0][p] = vn.hi.x;
-    mb.vl[0][p] = vn.lo.x;
-    mb.vh[1][p] = vn.hi.y;
-    mb.vl[1][p] = vn.lo.y;
+    reinterpret_cast<uint4 *>(mb.Y)[g] = make_uint4(Ya[0], Ya[1], Ya[2], Ya[3]);
+    reinterpret_cast<float4 *>(mb.vh[0])[g] = make_float4(xha[0], xha[1], xha[2], xha[3]);
+    reinterpret_cast<float4 *>(mb.vl[0])[g] = make_float4(xla[0], xla[1], xla[2], xla[3]);
+    reinterpret_cast<float4 *>(mb.vh[1])[g] = make_float4(yha[0], yha[1], yha[2], yha[3]);
+    reinterpret_cast<float4 *>(mb.vl[1])[g] = make_float4(yla[0], yla[1], yla[2], yla[3]);
   }
   const ff kt = ff_add(ff{keh.x, kel.x}, ff{keh.y, kel.y});
   if (!isfinite(kt.hi) || !isfinite(kt.lo)) bad |= kErrNonfinite;

@@ -1010,8 +1010,8 @@ int init_em1d_mixed(pic_handle *h) {
   // trips): its split counters need pcnt 2^16 < 2^32 and pcnt 2^(T-16) < 2^31,
   // so T = 47 - ceil(log2 pcnt); the int64 sums need N 2^T < 2^63.
   const int64_t threads = (int64_t)h->le.grid * 256;
-  const int64_t trips = (h->N + threads - 1) / threads;
-  const int64_t pcnt = std::max<int64_t>(1, trips * (256 / m.rt));
+  const int64_t trips = ((h->N + 3) / 4 + threads - 1) / threads;   // 4 markers a trip
+  const int64_t pcnt = std::max<int64_t>(1, 4 * trips * (256 / m.rt));
   int lg = 0;
   while (((int64_t)1 << lg) < pcnt) lg++;
   int bitlen = 0;
@@ -1029,7 +1029,7 @@ int init_em1d_mixed(pic_handle *h) {
   m.t_half = 0.5 * c.dt * qm;
   m.kick = c.dt * qm * m.cxk;
   m.m_full = c.dt * qm;
-  const size_t N = (size_t)h->N;
+  const size_t N = (size_t)(h->N + 3) / 4 * 4;   // padded: the passes move 4 markers at a time
   if ((rc = h->alloc(&mb.Y, N)) || (rc = h->alloc(&mb.J1, 2 * (size_t)c.n)) ||
       (rc = h->alloc(&mb.J2, 2 * (size_t)c.n)))
     return rc;
