@@ -330,26 +330,6 @@ __device__ __forceinline__ void store_copies(T *row, T v) {
   }
 }
 
-// dt (q/m) cxk E^{n+1/2}_p as a float pair: error-free products of the pair
-// table with the quantised weights, the high parts summed with two-sums.
-template <int ORDER, int RE>
-__device__ __forceinline__ ff gather_kick(const float2 *El, const ShapeMix<ORDER> &S) {
-  float ph[ORDER + 1], pl = 0.0f;
-#pragma unroll
-  for (int k = 0; k <= ORDER; k++) {
-    const float2 eh = El[(S.p + k) * RE];
-    const ff p = two_prod(eh.x, S.w[k]);
-    ph[k] = p.hi;
-    pl = __fadd_rn(pl, __fmaf_rn(eh.y, S.w[k], p.lo));
-  }
-  ff Ep = two_sum(ph[0], ph[1]);
-  pl = __fadd_rn(pl, Ep.lo);
-  if (ORDER == 2) {
-    Ep = two_sum(Ep.hi, ph[ORDER]);
-    pl = __fadd_rn(pl, Ep.lo);
-  }
-  return fast_two_sum(Ep.hi, pl);
-}
 
 // v^dag = v^n + d and v^{n+1} = Gamma v^dag (Eq. opt_solution) in float pairs.
 // With R = |v^n|^2 + 2 v* . (v^dag - v^n), R - |v^dag|^2 = 2a and
@@ -392,7 +372,9 @@ __device__ __forceinline__ ff correct_velocity(float vh, float vl, int Vs, ff d,
   return ff_add(vd, p);
 }
 
-// gather_kick for two markers at once (lane x: S0, lane y: S1), packed FP32
+// dt (q/m) cxk E^{n+1/2}_p of two markers (lane x: S0, lane y: S1) as float
+// pairs: error-free products of the pair table with the quantised weights,
+// the high parts summed with two-sums, in packed FP32
 template <int ORDER, int RE>
 __device__ __forceinline__ ff2 gather_kick2(const float2 *El, const ShapeMix<ORDER> &S0,
                                             const ShapeMix<ORDER> &S1) {
