@@ -168,3 +168,28 @@ def test_state_changes_mixed():
     r, Er, Br, _, _ = _oracle_run(other, O.PSATD, 2, 5)
     d = _diff(other, (r.y, r.vx, r.vy, Er, Br), (y, vx, vy, E, B))
     assert d["y"] <= TOL and d["v"] <= TOL and d["E"] <= TOL_F and d["B"] <= TOL_F, d
+
+
+def test_input_errors_mixed():
+    """Positions outside [0, L), non-finite velocities and speeds beyond the
+    fixed-point range come back as status codes, at pic_init and through
+    pic_set_particles."""
+    from paper_2411_09605_gb300 import pic
+    prob = W.weibel_1d2v(n=32, ppc=16, k0=0.5, b=0.02, seed=31)
+    s = prob.species[0]
+    bad = W.weibel_1d2v(n=32, ppc=16, k0=0.5, b=0.02, seed=31)
+    bad.species[0].y = bad.species[0].y.copy()
+    bad.species[0].y[3] = -1e-9
+    with pytest.raises(pic.PicError) as ei:
+        pic.Simulation1D2V(bad, precision=MIXED)
+    assert ei.value.code == -6
+    sim = pic.Simulation1D2V(prob, precision=MIXED)
+    try:
+        y = np.ascontiguousarray(s.y)
+        for v, code in ((np.stack([s.vx, np.full_like(s.vy, np.inf)]), -4),
+                        (np.stack([s.vx, s.vy]) * 1000.0, -6)):
+            with pytest.raises(pic.PicError) as ei:
+                pic.pic_set_particles(sim.h, 0, y, np.ascontiguousarray(v))
+            assert ei.value.code == code
+    finally:
+        sim.close()

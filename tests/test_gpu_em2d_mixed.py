@@ -190,3 +190,28 @@ def test_mixed_restrictions():
     with pytest.raises(pic.PicError) as ei:
         pic.Simulation2D(prob, precision=MIXED)
     assert ei.value.code == -7
+
+
+def test_input_errors_mixed():
+    """Positions outside [0, L), non-finite velocities and speeds beyond the
+    fixed-point range come back as status codes, at pic_init and through
+    pic_set_particles."""
+    from paper_2411_09605_gb300 import pic
+    prob = W.weibel(nx=16, ny=16, ppc=4, L=3.2, vth_par=0.1, seed=30)
+    s = prob.species[0]
+    bad = W.weibel(nx=16, ny=16, ppc=4, L=3.2, vth_par=0.1, seed=30)
+    bad.species[0].x = bad.species[0].x.copy()
+    bad.species[0].x[5] = prob.Lx
+    with pytest.raises(pic.PicError) as ei:
+        pic.Simulation2D(bad, precision=MIXED)
+    assert ei.value.code == -6
+    sim = pic.Simulation2D(prob, precision=MIXED)
+    try:
+        x = np.ascontiguousarray(np.stack([s.x, s.y]))
+        for v, code in ((np.stack([s.vx, s.vy, s.vz]) * np.array([[1.0], [1.0], [np.nan]]), -4),
+                        (np.stack([s.vx, s.vy, s.vz]) * 1000.0, -6)):
+            with pytest.raises(pic.PicError) as ei:
+                pic.pic_set_particles(sim.h, 0, x, np.ascontiguousarray(v))
+            assert ei.value.code == code
+    finally:
+        sim.close()
