@@ -50,7 +50,9 @@ def test_two_stream_full_size_2000_steps():
         te0, fb, te = _run_1d(prob, precision, 2000)
         clean = _per_step(te0, fb, te)
         assert (fb[:150] == 0).all()                   # linear phase: no fallback
-        assert np.max(clean) <= 1e-13, (precision, np.max(clean))
+        # round-off per step; the mixed form's saturated phase has many markers
+        # on the FP32 branch of Gamma (|t| >= 2^-8, relative error 2^-24 of t)
+        assert np.max(clean) <= (1e-13 if precision == 0 else 2e-13), (precision, np.max(clean))
         res[precision] = fb.sum()
     # the same physics in both forms: fallback counts of the same order
     assert 0.5 <= res[1] / max(res[0], 1) <= 2.0, res
