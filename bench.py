@@ -512,10 +512,12 @@ EM2D_ALGO_BYTES = {("fp64", 0): 64, ("fp64", 1): 104, ("mixed", 0): 44, ("mixed"
                    ("fp64_charge_conserving", 0): 64, ("fp64_charge_conserving", 1): 104}
 # FP64-pipe thread instructions per marker of the FP64 form (ncu, 2^20
 # markers): that form is bound by the FP64 pipe
-EM2D_FP64_INST_PER_MARKER = {0: 163.0, 1: 205.89}
+EM2D_FP64_INST_PER_MARKER = {("fp64", 0): 163.0, ("fp64", 1): 205.89,
+                             ("fp64_charge_conserving", 0): 173.80,
+                             ("fp64_charge_conserving", 1): 232.84}
 EM2D_TRAFFIC = {("fp64", 0): None, ("fp64", 1): 68729856,   # dram read + write per launch
                 ("mixed", 0): None, ("mixed", 1): None,
-                ("fp64_charge_conserving", 0): None, ("fp64_charge_conserving", 1): None}
+                ("fp64_charge_conserving", 0): 43356928, ("fp64_charge_conserving", 1): 69003776}
 
 
 def time_weibel2d(prob, precision, args, stream, flush, charge_conserving=False):
@@ -590,19 +592,14 @@ def run_weibel2d(args):
                 ach = EM2D_ALGO_BYTES[(name, kind)] * n / t / 1e9
                 kern[kname]["achieved_GBs"] = round(ach, 1)
                 kern[kname]["frac_hbm"] = round(ach / peak, 4)
-                if name == "fp64":      # FP64 instruction counts taken for this form only
-                    kern[kname]["fp64_ginst_s"] = round(EM2D_FP64_INST_PER_MARKER[kind] * n / t / 1e9, 1)
+                if name != "mixed":     # the FP64 forms: FP64-pipe instructions per marker (ncu)
+                    kern[kname]["fp64_ginst_s"] = round(EM2D_FP64_INST_PER_MARKER[(name, kind)] * n / t / 1e9, 1)
                     kern[kname]["frac_fp64"] = round(kern[kname]["fp64_ginst_s"] / fp64_peak, 4)
         dom = max(("pass_c", "pass_e"), key=lambda k: kern[k]["avg_us"]) if "pass_e" in kern else None
         dk = 1 if dom == "pass_e" else 0
         if dom is None:
             roof = None                       # no profiled steps
-        elif name == "fp64_charge_conserving":
-            roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": round(fp64_peak, 1),
-                    "unit": "Ginst/s (FP64 pipe)", "frac": None, "traffic": None,
-                    "hbm_frac": kern[dom]["frac_hbm"], "hbm_peak": peak,
-                    "note": "FP64 instruction count of this form not captured"}
-        elif name == "fp64":
+        elif name != "mixed":
             roof = {"bound": "alu", "kernel": dom, "achieved": kern[dom]["fp64_ginst_s"],
                     "peak": round(fp64_peak, 1), "unit": "Ginst/s (FP64 pipe)",
                     "frac": kern[dom]["frac_fp64"], "traffic": EM2D_TRAFFIC[(name, dk)],
