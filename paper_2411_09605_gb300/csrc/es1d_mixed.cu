@@ -256,43 +256,25 @@ __device__ __forceinline__ void flush_tile(const unsigned *Jt, long long *J, lon
   }
 }
 
-// Sum over the block of one double per thread: warp sums only in warps that
-// hold nonzero values, then warp 0 (the FP64 pipe is narrow on this part).
-// The result is valid in thread 0.
-__device__ __forceinline__ double block_sum_sparse(double v, int nactive) {
-  __shared__ double wred[32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp * 32 < nactive) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) wred[warp] = v;
-  }
-  __syncthreads();
-  double t = 0.0;
-  if (warp == 0) {
-    t = lane * 32 < nactive ? wred[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  }
-  return t;
-}
-
 // TE of a finished step from the blocks' partials of the kinetic energy and
-// of sum E^2 (pass E); first = this thread's first pair, loaded early by the
-// caller so that its latency overlaps other work.
-__device__ __forceinline__ void finalize_stats_mix(const Es1dMixBufs &b, double h, int slot,
-                                                   int nblocks, double first) {
-  double s = first;
-  for (int i = threadIdx.x + blockDim.x; i < nblocks; i += blockDim.x)
-    s += b.ke_part[i] + 0.5 * h * b.we_part[i];
-  const double t = block_sum_sparse(s, nblocks < (int)blockDim.x ? nblocks : (int)blockDim.x);
-  if (threadIdx.x == 0) {
-    b.te[slot] = t;
-    if (!isfinite(t)) atomicOr(b.err, kErrNonfinite);
+// of sum E^2 (pass E), by one warp: lane l sums the partials l, l + 32, ...,
+// then the lanes are summed by a butterfly.  Lane 0 stores TE.  The passes run
+// it in one warp before that warp's markers, off the path between launches.
+__device__ __forceinline__ void finalize_stats_warp(const Es1dMixBufs &b, double h, int slot,
+                                                    int nblocks) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+#pragma unroll 4
+  for (int i = lane; i < nblocks; i += 32) s += b.ke_part[i] + 0.5 * h * b.we_part[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    b.te[slot] = s;
+    if (!isfinite(s)) atomicOr(b.err, kErrNonfinite);
   }
 }
 
-__device__ __forceinline__ double finalize_first(const Es1dMixBufs &b, double h, int nblocks) {
-  return (int)threadIdx.x < nblocks ? b.ke_part[threadIdx.x] + 0.5 * h * b.we_part[threadIdx.x]
-                                    : 0.0;
+__device__ __forceinline__ bool last_warp() {
+  return (threadIdx.x >> 5) == (blockDim.x >> 5) - 1;
 }
 
 // Programmatic dependent launch: the passes are launched so that a kernel may
@@ -593,6 +575,9 @@ __device__ __forceinline__ void pass_c_body(const Es1dMixConst &c, const Es1dMix
   unsigned *Jl = Jt + (lane & (RT - 1));
   const float *El = Es + (lane & (RE - 1));
   unsigned bad = 0;
+  // TE of the previous step (its pass E partials are complete after the wait)
+  if (P.rb == 0 && prev_slot >= 0 && last_warp())
+    finalize_stats_warp(b, c.h, prev_slot, prev_nblocks);
   constexpr int G = kGroupC;
   for_groups<G, false, !AGG && kPrefetchC>(b, c.n, P, [&](auto check, int64_t g, const MarkerGroup<G> &m, int64_t end) {
     constexpr bool CHECK = decltype(check)::value;
@@ -638,9 +623,6 @@ __device__ __forceinline__ void pass_c_body(const Es1dMixConst &c, const Es1dMix
   });
   griddep_launch_dependents();
   report_flags(bad, b.err);
-  // TE of the previous step from pass E's block partials
-  if (P.rb == 0 && prev_slot >= 0)
-    finalize_stats_mix(b, c.h, prev_slot, prev_nblocks, finalize_first(b, c.h, prev_nblocks));
   __syncthreads();
   flush_tile<ORDER, RT>(Jt, PSEL(b.J2, par), b.Jtot + 2 + par, c.nc);
   if (MODE == 2)
@@ -701,6 +683,32 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
   }
   __syncthreads();
 
+  // E^{n+1} = E^n - dt (jscale J2 - jscale <J2>) in FP64 on the nodes
+  // [b nc / grid, (b + 1) nc / grid) by the last warp of block b, before its
+  // markers (with a block's groups not a multiple of its threads, the last
+  // warp has one trip fewer): the field, its float-pair table for the next
+  // step, the cleared J2 of the next step and this block's part of
+  // sum (E^{n+1})^2.  Nothing in this pass reads what it writes.
+  if (last_warp()) {
+    const unsigned lane = threadIdx.x & 31u;
+    const double *E = PSEL(b.E, par);
+    const double mean_e = c.remove_mean ? (double)b.Jtot[2 + par] * c.jscale / c.nc : 0.0;
+    if (P.rb == 0 && lane == 0) b.Jtot[2 + (par ^ 1)] = 0;
+    const int n0 = (int)((int64_t)c.nc * P.rb / P.nb);
+    const int n1 = (int)((int64_t)c.nc * (P.rb + 1) / P.nb);
+    double w = 0.0;
+    for (int i = n0 + (int)lane; i < n1; i += 32) {
+      const double en = E[i] - c.dt * ((double)J2[i * kJStride] * c.jscale - mean_e);
+      PSEL(b.E, par ^ 1)[i] = en;
+      const ff k = ff_from_double(c.kick * en);
+      PSEL(b.Ek, par ^ 1)[i] = make_float2(k.hi, k.lo);
+      PSEL(b.J2, par ^ 1)[i * kJStride] = 0;
+      w = fma(en, en, w);
+    }
+    if (n1 > n0)
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (lane == 0) b.we_part[P.rb] = w;
+  }
   const unsigned lane = threadIdx.x & 31u;
   unsigned *Jl = Jt + (lane & (RT - 1));
   const float2 *El = Eh2 + (lane & (RE - 1));
@@ -787,29 +795,6 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
     }
   });
   griddep_launch_dependents();
-  // E^{n+1} = E^n - dt (jscale J2 - jscale <J2>) in FP64 on the nodes
-  // [b nc / grid, (b + 1) nc / grid) by warp 0 of block b: the field, its
-  // float-pair table for the next step, the cleared J2 of the next step and
-  // this block's part of sum (E^{n+1})^2
-  if (threadIdx.x < 32) {
-    const double *E = PSEL(b.E, par);
-    const double mean_e = c.remove_mean ? (double)b.Jtot[2 + par] * c.jscale / c.nc : 0.0;
-    if (P.rb == 0 && threadIdx.x == 0) b.Jtot[2 + (par ^ 1)] = 0;
-    const int n0 = (int)((int64_t)c.nc * P.rb / P.nb);
-    const int n1 = (int)((int64_t)c.nc * (P.rb + 1) / P.nb);
-    double w = 0.0;
-    for (int i = n0 + (int)threadIdx.x; i < n1; i += 32) {
-      const double en = E[i] - c.dt * ((double)J2[i * kJStride] * c.jscale - mean_e);
-      PSEL(b.E, par ^ 1)[i] = en;
-      const ff k = ff_from_double(c.kick * en);
-      PSEL(b.Ek, par ^ 1)[i] = make_float2(k.hi, k.lo);
-      PSEL(b.J2, par ^ 1)[i * kJStride] = 0;
-      w = fma(en, en, w);
-    }
-    if (n1 > n0)
-      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    if (threadIdx.x == 0) b.we_part[P.rb] = w;
-  }
   // the two lanes' kinetic sums; a non-finite v^{n+1} leaves them non-finite
   const ff ke_t = ff_add(ff{ke2h.x, ke2l.x}, ff{ke2h.y, ke2l.y});
   const float ke_hi = ke_t.hi, ke_lo = ke_t.lo;
@@ -946,13 +931,12 @@ __global__ void __launch_bounds__(1024, 1)
     pass_e_body<2, SCHEME, 0, 32, 16>(c, b, par, slot, P);
 }
 
-// TE of step `slot` of every run (one block per run).
+// TE of step `slot` of every run (one warp per run).
 __global__ void mix_batch_finalize_kernel(const Es1dMixConst *cs, const Es1dMixBufs *bs,
                                           const int *nblocks, int slot) {
   const Es1dMixBufs &b = bs[blockIdx.x];
   const double h = cs[blockIdx.x].h;
-  const int nb = nblocks[blockIdx.x];
-  finalize_stats_mix(b, h, slot, nb, finalize_first(b, h, nb));
+  finalize_stats_warp(b, h, slot, nblocks[blockIdx.x]);
 }
 
 // Copies the first n per-step counts and energies of every run into one
@@ -975,7 +959,7 @@ __global__ void mix_set_ek_kernel(const double *E, float2 *Ek, int nc, double ki
 }
 
 __global__ void mix_finalize_kernel(Es1dMixBufs b, double h, int slot, int nblocks) {
-  finalize_stats_mix(b, h, slot, nblocks, finalize_first(b, h, nblocks));
+  finalize_stats_warp(b, h, slot, nblocks);
 }
 
 // FP64 (x, v) <-> (X, vh, vl) with v stored in V units (v * cxk)
@@ -1259,7 +1243,7 @@ void es1d_mix_charge(const Es1dMixConst &c, const Es1dMixBufs &b, long long *cou
 
 void es1d_mix_finalize(const Es1dMixConst &c, const Es1dMixBufs &b, int slot, int nblocks,
                        cudaStream_t st) {
-  mix_finalize_kernel<<<1, 1024, 0, st>>>(b, c.h, slot, nblocks);
+  mix_finalize_kernel<<<1, 32, 0, st>>>(b, c.h, slot, nblocks);
 }
 
 void es1d_mix_set_ek(const Es1dMixConst &c, const Es1dMixBufs &b, int parity, cudaStream_t st) {
@@ -1305,7 +1289,7 @@ void es1d_batch_pass_e(const Es1dMixConst *cs, const Es1dMixBufs *bs, const Batc
 
 void es1d_batch_finalize(const Es1dMixConst *cs, const Es1dMixBufs *bs, const int *nblocks,
                          int nruns, int slot, cudaStream_t st) {
-  mix_batch_finalize_kernel<<<nruns, 1024, 0, st>>>(cs, bs, nblocks, slot);
+  mix_batch_finalize_kernel<<<nruns, 32, 0, st>>>(cs, bs, nblocks, slot);
 }
 
 void es1d_batch_gather_stats(const Es1dMixBufs *bs, int nruns, int n, unsigned long long *fb,
