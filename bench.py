@@ -51,7 +51,7 @@ FP64_LANES_PER_SM_CLK = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu capture of the current kernels on this workload (2^23 markers); None where
 # the kernel changed since it was taken.
-TRAFFIC = {("mixed", 0): 111648000, ("mixed", 1): 178000896,
+TRAFFIC = {("mixed", 0): 111117312, ("mixed", 1): 174521600,
            ("fp64", 0): None, ("fp64", 1): 304729600, ("standard", 1): 207165440}
 
 
