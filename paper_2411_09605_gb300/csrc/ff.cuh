@@ -57,9 +57,9 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float f) {
 
 // Two float pairs side by side, lane x for one marker and lane y for
 // another, with the packed two-lane FP32 add / multiply / FMA of sm_100 and
-// later: each lane rounds as the scalar instruction does, so every function
-// below gives, lane by lane, the bits of its scalar namesake above.  a - b is
-// the add of -b (the IEEE definition of subtraction).
+// later: each lane rounds as the scalar instruction does, and every function
+// below performs, lane by lane, the operations of its scalar namesake above.
+// a - b is the add of -b (the IEEE definition of subtraction).
 struct ff2 {
   float2 hi, lo;
 };
