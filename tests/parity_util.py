@@ -2,9 +2,26 @@
 compare them (used by the -m gpu parity tests and by smoke())."""
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 from oracle import oracle as O
+
+GOLDEN_PAPER = os.path.join(os.path.dirname(__file__), "golden", "paper_tests.txt")
+
+
+def paper_values(path: str = GOLDEN_PAPER) -> dict:
+    """The values of tests/golden/paper_tests.txt (key = value, '#' comments):
+    the parameters and outcomes the paper prints for its tests."""
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                key, val = (t.strip() for t in line.split("=", 1))
+                vals[key] = float(val)
+    return vals
 
 
 def oracle_run(prob, scheme=2, steps=10, remove_mean=True, gamma_on=True, E0=None):

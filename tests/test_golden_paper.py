@@ -11,29 +11,14 @@ component passes through zero far more often than |v| does in 2D, and Gamma
 is imaginary only near v^dag = 0, so ESEC1 is held only to the orderings the
 paper reports (more fallbacks and a larger error than ESEC2, growing with the
 time step).  Sec. 5.3 is the paper's own 1D2V geometry and runs at its size."""
-import os
-
 import numpy as np
 import pytest
 
 from oracle import oracle as O
 from paper_2411_09605_gb300 import workloads as W
+from tests.parity_util import paper_values
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tests.txt")
-
-
-def _load():
-    vals = {}
-    with open(GOLDEN) as f:
-        for line in f:
-            line = line.split("#", 1)[0].strip()
-            if line:
-                key, val = (t.strip() for t in line.split("=", 1))
-                vals[key] = float(val)
-    return vals
-
-
-P = _load()
+P = paper_values()
 
 
 def _es_run(prob, scheme, steps, dt):
