@@ -518,6 +518,20 @@ __device__ __forceinline__ void mix_current_to_fp64(const long long *Ji, double 
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) J[i] = jscale * (double)__ldcg(Ji + i);
 }
 
+// 16-byte asynchronous global -> shared copy (L2 only), its commit and the
+// wait for all of this thread's copies
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ float4 __uint_as_float4(uint4 u) {
+  return make_float4(__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z),
+                     __uint_as_float(u.w));
+}
+
 __device__ __forceinline__ void clear_words(unsigned *a, int len) {
   for (int i = threadIdx.x; i < len; i += blockDim.x) a[i] = 0u;
 }
@@ -562,25 +576,43 @@ __global__ void __launch_bounds__(kEm1Threads, 4) em1m_pass_c_kernel(Em1dConst c
   const int n = c.n, npad = npad_of(n), rt = m.rt;
   unsigned *Jt = (unsigned *)smraw;                      // [npad][2][2][rt]
   float4 *T = (float4 *)(Jt + 4 * rt * npad);            // e_half E*x, e_half E*y, t_half B*z
+  uint4 *stage = (uint4 *)(T + npad);                    // [5][blockDim]: next group's words
   clear_words(Jt, 4 * rt * npad);
   for (int q = threadIdx.x; q < npad; q += blockDim.x) {
     const int i = wrap_node(q - PAD, n);
     T[q] = make_float4((float)(m.e_half * b.Es[i]), (float)(m.e_half * b.Es[n + i]),
                        (float)(m.t_half * b.Bs[i]), 0.0f);
   }
-  __syncthreads();
   unsigned *Jl = Jt + (threadIdx.x & (rt - 1));
   unsigned bad = 0;
-  // four consecutive markers per thread and trip, loaded 16 bytes at a time
-  // (the arrays are padded to a multiple of four)
+  // four consecutive markers per thread and trip, 16 bytes per array (the
+  // arrays are padded to a multiple of four).  Each thread copies its next
+  // group into its own five stage slots with asynchronous copies while it
+  // works on the current one; it reads only its own slots, so the wait is on
+  // its own copies and needs no block barrier.
   const int64_t ngroups = (m.N + 3) / 4;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 Yq = reinterpret_cast<const uint4 *>(mb.Y)[g];
-    const float4 xh4 = reinterpret_cast<const float4 *>(mb.vh[0])[g];
-    const float4 xl4 = reinterpret_cast<const float4 *>(mb.vl[0])[g];
-    const float4 yh4 = reinterpret_cast<const float4 *>(mb.vh[1])[g];
-    const float4 yl4 = reinterpret_cast<const float4 *>(mb.vl[1])[g];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const unsigned slot0 = (unsigned)__cvta_generic_to_shared(stage + threadIdx.x);
+  const unsigned sstep = 16u * blockDim.x;
+  const auto fetch = [&](int64_t gg) {
+    cp_async16(slot0, reinterpret_cast<const uint4 *>(mb.Y) + gg);
+    cp_async16(slot0 + sstep, reinterpret_cast<const uint4 *>(mb.vh[0]) + gg);
+    cp_async16(slot0 + 2 * sstep, reinterpret_cast<const uint4 *>(mb.vl[0]) + gg);
+    cp_async16(slot0 + 3 * sstep, reinterpret_cast<const uint4 *>(mb.vh[1]) + gg);
+    cp_async16(slot0 + 4 * sstep, reinterpret_cast<const uint4 *>(mb.vl[1]) + gg);
+    cp_async_commit();
+  };
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g < ngroups) fetch(g);
+  __syncthreads();
+  for (; g < ngroups; g += stride) {
+    cp_async_wait_all();
+    const uint4 Yq = stage[threadIdx.x];
+    const float4 xh4 = __uint_as_float4(stage[blockDim.x + threadIdx.x]);
+    const float4 xl4 = __uint_as_float4(stage[2 * blockDim.x + threadIdx.x]);
+    const float4 yh4 = __uint_as_float4(stage[3 * blockDim.x + threadIdx.x]);
+    const float4 yl4 = __uint_as_float4(stage[4 * blockDim.x + threadIdx.x]);
+    if (g + stride < ngroups) fetch(g + stride);
     const uint32_t Ya[4] = {Yq.x, Yq.y, Yq.z, Yq.w};
     const float xha[4] = {xh4.x, xh4.y, xh4.z, xh4.w}, xla[4] = {xl4.x, xl4.y, xl4.z, xl4.w};
     const float yha[4] = {yh4.x, yh4.y, yh4.z, yh4.w}, yla[4] = {yl4.x, yl4.y, yl4.z, yl4.w};
@@ -873,6 +905,16 @@ size_t mix_smem(const Em1dConst &c, const Em1dMixConst &m) {
   return a > f ? a : f;
 }
 
+// pass C: tile copies, its table and the stage of the next groups (five
+// 16-byte words a thread), or the field solve
+size_t mix_smem_c(const Em1dConst &c, const Em1dMixConst &m) {
+  const size_t npad = (size_t)c.n + 3;
+  const size_t a = 4 * sizeof(unsigned) * m.rt * npad + sizeof(float4) * npad +
+                   5 * sizeof(uint4) * kEm1Threads;
+  const size_t f = sizeof(double) * (9 * (size_t)c.n + 8);
+  return a > f ? a : f;
+}
+
 // the passes' tables and tile copies, or the field solve's 9n + 8 doubles
 size_t pass_smem(const Em1dConst &c) {
   const size_t a = (6 + 2 * (size_t)c.rt) * c.n, f = 9 * (size_t)c.n + 8;
@@ -964,12 +1006,13 @@ int em1m_tile_copies(int n) {
 cudaError_t em1m_prepare(const Em1dConst &c, const Em1dMixConst &m) {
   const size_t sm = mix_smem(c, m);
   cudaError_t e = cudaSuccess;
+  const size_t smc = mix_smem_c(c, m);
   if (c.order == 1) {
-    if ((e = allow_smem(em1m_pass_c_kernel<1>, sm))) return e;
+    if ((e = allow_smem(em1m_pass_c_kernel<1>, smc))) return e;
     if ((e = allow_smem(em1m_pass_e_kernel<1>, sm))) return e;
     if ((e = allow_smem(em1m_deposit_initial_kernel<1>, sm))) return e;
   } else {
-    if ((e = allow_smem(em1m_pass_c_kernel<2>, sm))) return e;
+    if ((e = allow_smem(em1m_pass_c_kernel<2>, smc))) return e;
     if ((e = allow_smem(em1m_pass_e_kernel<2>, sm))) return e;
     if ((e = allow_smem(em1m_deposit_initial_kernel<2>, sm))) return e;
   }
@@ -978,7 +1021,7 @@ cudaError_t em1m_prepare(const Em1dConst &c, const Em1dMixConst &m) {
 
 void em1m_pass_c(const Em1dConst &c, const Em1dBufs &b, const Em1dMixConst &m,
                  const Em1dMixBufs &mb, LaunchShape lp, cudaStream_t st) {
-  const size_t sm = mix_smem(c, m);
+  const size_t sm = mix_smem_c(c, m);
   if (c.order == 1)
     em1m_pass_c_kernel<1><<<lp.grid, kEm1Threads, sm, st>>>(c, b, m, mb);
   else
