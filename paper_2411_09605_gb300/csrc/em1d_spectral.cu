@@ -518,20 +518,6 @@ __device__ __forceinline__ void mix_current_to_fp64(const long long *Ji, double 
   for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) J[i] = jscale * (double)__ldcg(Ji + i);
 }
 
-// 16-byte asynchronous global -> shared copy (L2 only), its commit and the
-// wait for all of this thread's copies
-__device__ __forceinline__ void cp_async16(unsigned dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
-__device__ __forceinline__ float4 __uint_as_float4(uint4 u) {
-  return make_float4(__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z),
-                     __uint_as_float(u.w));
-}
-
 __device__ __forceinline__ void clear_words(unsigned *a, int len) {
   for (int i = threadIdx.x; i < len; i += blockDim.x) a[i] = 0u;
 }
@@ -608,10 +594,10 @@ __global__ void __launch_bounds__(kEm1Threads, 4) em1m_pass_c_kernel(Em1dConst c
   for (; g < ngroups; g += stride) {
     cp_async_wait_all();
     const uint4 Yq = stage[threadIdx.x];
-    const float4 xh4 = __uint_as_float4(stage[blockDim.x + threadIdx.x]);
-    const float4 xl4 = __uint_as_float4(stage[2 * blockDim.x + threadIdx.x]);
-    const float4 yh4 = __uint_as_float4(stage[3 * blockDim.x + threadIdx.x]);
-    const float4 yl4 = __uint_as_float4(stage[4 * blockDim.x + threadIdx.x]);
+    const float4 xh4 = uint_as_float4(stage[blockDim.x + threadIdx.x]);
+    const float4 xl4 = uint_as_float4(stage[2 * blockDim.x + threadIdx.x]);
+    const float4 yh4 = uint_as_float4(stage[3 * blockDim.x + threadIdx.x]);
+    const float4 yl4 = uint_as_float4(stage[4 * blockDim.x + threadIdx.x]);
     if (g + stride < ngroups) fetch(g + stride);
     const uint32_t Ya[4] = {Yq.x, Yq.y, Yq.z, Yq.w};
     const float xha[4] = {xh4.x, xh4.y, xh4.z, xh4.w}, xla[4] = {xl4.x, xl4.y, xl4.z, xl4.w};

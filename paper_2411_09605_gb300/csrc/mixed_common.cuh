@@ -121,6 +121,24 @@ __device__ __forceinline__ SplitTerm split_term(int V, int s, int rshift, long l
   return {__funnelshift_r(plo, phi, rshift) & 0xFFFFu, (int)phi >> (rshift - 16)};
 }
 
+// 16-byte asynchronous global -> shared copy (L2 only), its commit and the
+// wait for all of this thread's copies: the passes stage a thread's next
+// marker words in shared-memory slots of its own while it works on the
+// current ones.
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ float4 uint_as_float4(uint4 u) {
+  return make_float4(__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z),
+                     __uint_as_float(u.w));
+}
+
 // rint(y) with a range flag: |y| must stay below the largest float under 2^31
 __device__ __forceinline__ int to_fixed(float y, unsigned &bad) {
   if (!(fabsf(y) < 2147483520.0f)) bad |= kErrVelocityRange;
