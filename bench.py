@@ -644,7 +644,7 @@ EM1D_TRAFFIC = {0: None, 1: 487232768}
 # the mixed form: y (u32) and two float pairs; pass C writes V* (2 x i32),
 # pass E reads it and writes y and the pairs
 EM1D_MIX_ALGO_BYTES = {0: 28, 1: 48}
-EM1D_MIX_TRAFFIC = {0: None, 1: 342160384}   # dram read + write per launch, 2^23 markers (None: changed since)
+EM1D_MIX_TRAFFIC = {0: 206697216, 1: 342160384}   # dram read + write per launch, 2^23 markers
 
 
 def _weibel1d_form(W, pic, torch, solver, precision, args, stream, flush, peak, long_steps):
