@@ -91,6 +91,19 @@ def test_parity_mixed(solver, scheme, order):
     _check(prob, solver, scheme, fb_slack=2 if scheme == 1 else 0)
 
 
+@pytest.mark.parametrize("drop", [1, 2, 3])
+def test_ragged_marker_count_mixed(drop):
+    """Marker counts that are not a multiple of four: the last group of four
+    holds one to three markers and the padding (the passes move four markers a
+    thread, and pass C stages them in shared memory), against the oracle."""
+    prob = W.weibel_1d2v(n=32, ppc=401, k0=0.5, b=0.02, order=2, seed=9 + drop)
+    s = prob.species[0]
+    keep = len(s.y) - drop
+    s.y, s.vx, s.vy = s.y[:keep], s.vx[:keep], s.vy[:keep]
+    for solver in (O.CN, O.PSATD):
+        _check(prob, solver, 2, steps=6)
+
+
 @pytest.mark.parametrize("n", [4, 1024])
 def test_grid_size_limits_mixed(n):
     prob = W.weibel_1d2v(n=n, ppc=max(8, 4096 // n), k0=0.5, b=0.02, order=2, seed=5)
