@@ -607,9 +607,14 @@ def run_weibel2d(args):
                     "hbm_frac": kern[dom]["frac_hbm"], "hbm_peak": peak,
                     "hbm_peak_source": peak_src}
         else:
+            # the HBM fraction of the algorithmic bytes, reported for reference:
+            # these passes are bound by L2 requests (the integer current's
+            # global atomics), see the note
             roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_GBs"],
                     "peak": peak, "unit": "GB/s", "frac": kern[dom]["frac_hbm"],
-                    "traffic": EM2D_TRAFFIC[(name, dk)], "peak_source": peak_src}
+                    "traffic": EM2D_TRAFFIC[(name, dk)], "peak_source": peak_src,
+                    "note": "bound by L2 requests (64-bit global atomics of the integer "
+                            "current; ncu: L2 tag lookups near 70% of peak), not by HBM"}
         out[name] = {"value": n * args.steps / (f["step_ms"].sum() / 1e3),
                      "ms_per_step": float(f["step_ms"].mean()),
                      "energy": {"max_rel_dTE": f["max_rel_dTE"], "fallbacks": f["fallbacks"]},
