@@ -255,8 +255,12 @@ int pic_set_fields(pic_handle *h, const double *E, const double *B);
  * per call, else PIC_ERR_ARG.  Its scratch is one static device array of
  * 352,576 bytes that every GPU which loads the library holds until exit; all
  * calls on a device share it, so calls that overlap on the GPU race and must
- * be serialised.  The first call on a device looks the array up
- * (cudaGetSymbolAddress): make it before any stream capture.
+ * be serialised.  Every call looks up the array's address on the current
+ * device (cudaGetSymbolAddress); no address is kept between calls.  The inputs
+ * are checked before the first step: a position outside [0, L) returns
+ * PIC_ERR_BOUNDS and a non-finite velocity or field value PIC_ERR_NONFINITE,
+ * with x, v and E left as passed.  The call returns after its work on
+ * cfg->cuda_stream has completed.
  */
 int pic_es1d_step_noalloc(const pic_config *cfg, double q, double m, double w0, int64_t n,
                           double *x, double *v, double *E, int nsteps,

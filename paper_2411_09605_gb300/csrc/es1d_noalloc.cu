@@ -15,11 +15,16 @@
 // device shares it (the contents of the last call remain; what must start at
 // zero is cleared at the start of each call).  Calls that overlap on the GPU
 // (two streams, or two host threads) race on it and must be serialised by the
-// caller.  The first call on a device looks up the array's device address with
-// cudaGetSymbolAddress; make that first call before any stream capture.
+// caller.  Host code cannot use the array's name as a device address, so every
+// call looks the address up (cudaGetSymbolAddress) on the current device; no
+// address is kept between calls, so a call made after the device's context was
+// reset sees the array of the new context.
+//
+// The inputs are checked before any step runs: a position outside [0, L) or a
+// non-finite velocity or field value returns an error with x, v and E as the
+// caller passed them.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "pic_internal.cuh"
@@ -41,10 +46,6 @@ constexpr size_t kNoallocScratchBytes =
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
-
 int noalloc_fail(int code, const char *msg, cudaError_t e = cudaSuccess) {
   std::string m = msg;
   if (e != cudaSuccess) {
@@ -55,14 +56,19 @@ int noalloc_fail(int code, const char *msg, cudaError_t e = cudaSuccess) {
   return code;
 }
 
-__global__ void noalloc_validate_kernel(const double *x, const double *v, int64_t n, double L,
-                                        unsigned *err) {
+// Flags positions outside [0, L) and non-finite velocities and field values.
+__global__ void noalloc_validate_kernel(const double *x, const double *v, int64_t n,
+                                        const double *E, int nc, double L, unsigned *err) {
+  unsigned bad = 0;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     double a = x[p], b = v[p];
-    if (!(a >= 0.0 && a < L)) atomicOr(err, kErrBounds);
-    if (!isfinite(b)) atomicOr(err, kErrNonfinite);
+    if (!(a >= 0.0 && a < L)) bad |= kErrBounds;
+    if (!isfinite(b)) bad |= kErrNonfinite;
   }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+    if (!isfinite(E[i])) bad |= kErrNonfinite;
+  if (bad) atomicOr(err, bad);
 }
 
 bool is_device_pointer(const void *p) {
@@ -111,20 +117,13 @@ extern "C" int pic_es1d_step_noalloc(const pic_config *cfg, double q, double m, 
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return noalloc_fail(PIC_ERR_CUDA, "pic_es1d_step_noalloc: device query", e);
-  if (dev < 0 || dev >= kMaxDevices)
-    return noalloc_fail(PIC_ERR_ARG, "pic_es1d_step_noalloc: device index above 63");
-  unsigned char *base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-      void *ptr = nullptr;
-      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-      if (e != cudaSuccess || !ptr)
-        return noalloc_fail(PIC_ERR_CUDA, "pic_es1d_step_noalloc: cudaGetSymbolAddress", e);
-      g_scratch_addr[dev] = ptr;
-    }
-    base = (unsigned char *)g_scratch_addr[dev];
-  }
+  // the array's address in the current device's context, looked up on every
+  // call (nothing is cached across calls or devices)
+  void *ptr = nullptr;
+  e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr)
+    return noalloc_fail(PIC_ERR_CUDA, "pic_es1d_step_noalloc: cudaGetSymbolAddress", e);
+  unsigned char *base = (unsigned char *)ptr;
 
   Es1dConst c{};
   c.nc = (int)nc;
@@ -177,7 +176,20 @@ extern "C" int pic_es1d_step_noalloc(const pic_config *cfg, double q, double m, 
     e = cudaMemsetAsync(b.fallback, 0, sizeof(unsigned long long) * kNoallocMaxSteps, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.err, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return noalloc_fail(PIC_ERR_CUDA, "pic_es1d_step_noalloc: clear scratch", e);
-  if (n > 0) noalloc_validate_kernel<<<ls.grid, 256, 0, st>>>(x, v, n, c.L, b.err);
+  // validate before stepping: a bad input returns with x, v and E untouched
+  {
+    noalloc_validate_kernel<<<ls.grid, 256, 0, st>>>(x, v, n, E, (int)nc, c.L, b.err);
+    unsigned pre = 0;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&pre, b.err, sizeof pre, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return noalloc_fail(PIC_ERR_CUDA, "pic_es1d_step_noalloc: validation", e);
+    if (pre & kErrNonfinite)
+      return noalloc_fail(PIC_ERR_NONFINITE,
+                          "pic_es1d_step_noalloc: non-finite velocity or field on input");
+    if (pre & kErrBounds)
+      return noalloc_fail(PIC_ERR_BOUNDS, "pic_es1d_step_noalloc: a position is outside [0, L)");
+  }
   if (c.scheme == 2) es1d_fp64_deposit_initial(c, b, 0, ls, st);
   for (int k = 0; k < nsteps; k++) {
     es1d_fp64_pass_c(c, b, k, k, ls, st);

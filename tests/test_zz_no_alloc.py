@@ -87,3 +87,30 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         pic.pic_es1d_step_noalloc(cfg, -1.0, 1.0, 0.1, 8, np.full(8, 0.5), np.zeros(8),
                                   np.zeros(16), 1)
     assert ei.value.code == -1
+
+
+def test_noalloc_bad_input_leaves_buffers_untouched():
+    """A position outside [0, L) or a non-finite velocity or field is reported before
+    any step runs, so the caller's x, v and E come back exactly as passed."""
+    import torch
+    from paper_2411_09605_gb300 import pic
+    dev = torch.device("cuda", 0)
+    prob = W.two_stream(n=1000, nc=64, seed=22)
+    s = prob.species[0]
+    cfg = pic.make_config(prob.nc, prob.L, prob.dt, prob.order, 2)
+    E0 = np.linspace(-0.1, 0.1, prob.nc)
+    cases = [("x", 17, prob.L, -6), ("x", 3, -1e-12, -6), ("v", 5, np.inf, -4),
+             ("E", 9, np.nan, -4)]
+    for which, idx, bad, code in cases:
+        xs, vs, Es = s.x.copy(), s.v.copy(), E0.copy()
+        {"x": xs, "v": vs, "E": Es}[which][idx] = bad
+        x = torch.from_numpy(xs).to(dev)
+        v = torch.from_numpy(vs).to(dev)
+        E = torch.from_numpy(Es).to(dev)
+        with pytest.raises(pic.PicError) as ei:
+            pic.pic_es1d_step_noalloc(cfg, s.q, s.m, s.w0, len(xs), x, v, E, 3)
+        assert ei.value.code == code, (which, ei.value)
+        torch.cuda.synchronize()
+        assert np.array_equal(x.cpu().numpy(), xs, equal_nan=True)
+        assert np.array_equal(v.cpu().numpy(), vs, equal_nan=True)
+        assert np.array_equal(E.cpu().numpy(), Es, equal_nan=True)
