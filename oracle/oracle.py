@@ -47,6 +47,40 @@ def lib():
     return _lib
 
 
+_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source with -fopenmp: orc_es1d_step's particle loops run on all
+    host cores (per-thread private current sums).  Used only to time the CPU
+    baseline; the tests check against the single-threaded build."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = (not os.path.exists(_OMP_PATH)) or (
+        os.path.getmtime(_OMP_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _OMP_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _OMP_PATH)
+    return _OMP_PATH
+
+
+def lib_omp():
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = C.CDLL(build_omp())
+        _declare(_lib_omp)
+    return _lib_omp
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP build runs with (its omp_get_max_threads())."""
+    f = lib_omp().omp_get_max_threads
+    f.restype = C.c_int
+    return int(f())
+
+
 _dp = C.POINTER(C.c_double)
 _lp = C.POINTER(C.c_long)
 
@@ -91,6 +125,8 @@ def _declare(L):
     L.orc_es1d_step.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp, _lp,
                                 C.POINTER(_dp)]
     L.orc_es1d_step.restype = C.c_int
+    L.orc_es1d_charge_diag.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp,
+                                       _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_es1d_energy.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp, _dp, _dp]
     L.orc_es1d_run.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp, C.c_long,
                                _dp, _dp, _lp]
@@ -190,8 +226,10 @@ def gather_1d(order, nc, L, x, E):
     return Ep
 
 
-def es1d_step(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray, want_gamma=False):
-    """One step; returns (fallback counts per species, Gamma arrays or None)."""
+def es1d_step(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray, want_gamma=False,
+              threaded: bool = False):
+    """One step; returns (fallback counts per species, Gamma arrays or None).
+    threaded=True runs the OpenMP build (CPU-baseline timing only)."""
     sp = _sp_array(species)
     nfb = (C.c_long * len(species))()
     gam = None
@@ -200,7 +238,8 @@ def es1d_step(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray, want_g
         gam = [np.zeros(len(s.x)) for s in species]
         garr = (_dp * len(species))(*[_ptr(g) for g in gam])
         gptr = C.cast(garr, C.POINTER(_dp))
-    rc = lib().orc_es1d_step(C.byref(cfg._c()), sp, len(species), _ptr(E), nfb, gptr)
+    L = lib_omp() if threaded else lib()
+    rc = L.orc_es1d_step(C.byref(cfg._c()), sp, len(species), _ptr(E), nfb, gptr)
     assert rc == 0
     return list(nfb), gam
 
@@ -242,6 +281,19 @@ def es1d_grad(cfg: ES1DConfig, species: Sequence[Species], E0: np.ndarray, nstep
                              nsteps, _ptr(Eb), arr(xb), arr(vb), arr(wb))
     assert rc == 0
     return Eb, xb, vb, wb
+
+
+def es1d_charge_diag(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray):
+    """Charge diagnostics of the state: dict with Q_markers, Q_grid, gauss_l2,
+    rho_l2 and the real-space residual r and filtered charge rhot ([nc])."""
+    nc = cfg.nc
+    qm, qg, g, pl = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    r, rt = np.zeros(nc), np.zeros(nc)
+    lib().orc_es1d_charge_diag(C.byref(cfg._c()), _sp_array(species), len(species),
+                               _ptr(np.ascontiguousarray(E, dtype=np.float64)), C.byref(qm),
+                               C.byref(qg), C.byref(g), C.byref(pl), _ptr(r), _ptr(rt))
+    return dict(Q_markers=qm.value, Q_grid=qg.value, gauss_l2=g.value, rho_l2=pl.value, r=r,
+                rhot=rt)
 
 
 def poisson_e0_1d(cfg: ES1DConfig, species: Sequence[Species]):

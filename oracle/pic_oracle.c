@@ -21,12 +21,22 @@
  *
  * Parity status of each function is stated next to it; the pins live in
  * tests/test_oracle_*.py.
+ *
+ * The checker is built single-threaded (no -fopenmp): every loop then runs in
+ * the order written.  The same source built with -fopenmp is used only to
+ * time the CPU baseline on all host cores: orc_es1d_step's particle loops are
+ * then split over threads, and each thread deposits its markers into a
+ * private array that is added to the grid afterwards (a different order of
+ * the same sums).  Tests never load that build.
  */
 #include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------ */
 /* Shape functions (Sec. 2.2: B-spline shapes; tent S(z) = max(0, 1-|z|/h)) */
@@ -177,6 +187,47 @@ static void ampere_update(const orc_es1d_cfg *cfg, const double *Ein,
   for (long i = 0; i < cfg->nc; i++) Eout[i] = Ein[i] - tau * (J[i] - mean);
 }
 
+/* Particle loops split over threads in the OpenMP timing build only (see the
+ * header); empty in the checker build. */
+#ifdef _OPENMP
+#define ORC_PARALLEL_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORC_PARALLEL_FOR
+#endif
+
+/* J += (1/h) sum_p q w_p u_p S(x_h - X_p) over the markers of species s at
+ * positions X with velocities U (Sec. 2.2).  Checker build: one loop in marker
+ * order.  OpenMP timing build: per-thread private sums, added afterwards. */
+static void deposit_current(const orc_es1d_cfg *cfg, const orc_species *s, const double *X,
+                            const double *U, double h, double *J) {
+  long nc = cfg->nc;
+#ifdef _OPENMP
+#pragma omp parallel
+  {
+    double *Jp = (double *)calloc((size_t)nc, sizeof(double));
+#pragma omp for schedule(static)
+    for (long p = 0; p < s->n; p++) {
+      long idx[3];
+      double wt[3];
+      int k = orc_shape_weights(cfg->order, X[p] / h, nc, idx, wt);
+      double c = s->q * weight_of(s, p) * U[p];
+      for (int j = 0; j < k; j++) Jp[idx[j]] += c * wt[j] / h;
+    }
+#pragma omp critical
+    for (long i = 0; i < nc; i++) J[i] += Jp[i];
+    free(Jp);
+  }
+#else
+  for (long p = 0; p < s->n; p++) {
+    long idx[3];
+    double wt[3];
+    int k = orc_shape_weights(cfg->order, X[p] / h, nc, idx, wt);
+    double c = s->q * weight_of(s, p) * U[p];
+    for (int j = 0; j < k; j++) J[idx[j]] += c * wt[j] / h;
+  }
+#endif
+}
+
 /*
  * One time step of ESEC1 / ESEC2 (1D1V, B = 0), in the paper's order:
  *
@@ -227,21 +278,16 @@ int orc_es1d_step(const orc_es1d_cfg *cfg, orc_species *sp, int nsp,
   }
 
   /* x* = x^n + dt/2 v^n */
-  for (int s = 0; s < nsp; s++)
+  for (int s = 0; s < nsp; s++) {
+    ORC_PARALLEL_FOR
     for (long p = 0; p < sp[s].n; p++)
       xs[s][p] = wrap(sp[s].x[p] + 0.5 * dt * sp[s].v[p], L);
+  }
 
   if (cfg->scheme == 2) {
     /* j^{n,*}: v^n deposited at x*, then E* = E^n - dt/2 j^{n,*} */
     for (long i = 0; i < nc; i++) J[i] = 0.0;
-    for (int s = 0; s < nsp; s++)
-      for (long p = 0; p < sp[s].n; p++) {
-        long idx[3];
-        double wt[3];
-        int k = orc_shape_weights(cfg->order, xs[s][p] / h, nc, idx, wt);
-        double c = sp[s].q * weight_of(&sp[s], p) * sp[s].v[p];
-        for (int j = 0; j < k; j++) J[idx[j]] += c * wt[j] / h;
-      }
+    for (int s = 0; s < nsp; s++) deposit_current(cfg, &sp[s], xs[s], sp[s].v, h, J);
     filter_passes(nc, J, cfg->passes);
     ampere_update(cfg, E, J, 0.5 * dt, Estar);
   } else {
@@ -252,6 +298,7 @@ int orc_es1d_step(const orc_es1d_cfg *cfg, orc_species *sp, int nsp,
   /* v* from the field gathered at x*; then x^{n+1/2} */
   for (int s = 0; s < nsp; s++) {
     double qm = sp[s].q / sp[s].m;
+    ORC_PARALLEL_FOR
     for (long p = 0; p < sp[s].n; p++) {
       long idx[3];
       double wt[3];
@@ -265,14 +312,7 @@ int orc_es1d_step(const orc_es1d_cfg *cfg, orc_species *sp, int nsp,
 
   /* j^{*,n+1/2}: v* deposited at x^{n+1/2}; E^{n+1}, E^{n+1/2} */
   for (long i = 0; i < nc; i++) J[i] = 0.0;
-  for (int s = 0; s < nsp; s++)
-    for (long p = 0; p < sp[s].n; p++) {
-      long idx[3];
-      double wt[3];
-      int k = orc_shape_weights(cfg->order, xh[s][p] / h, nc, idx, wt);
-      double c = sp[s].q * weight_of(&sp[s], p) * vs[s][p];
-      for (int j = 0; j < k; j++) J[idx[j]] += c * wt[j] / h;
-    }
+  for (int s = 0; s < nsp; s++) deposit_current(cfg, &sp[s], xh[s], vs[s], h, J);
   filter_passes(nc, J, cfg->passes);
   ampere_update(cfg, E, J, dt, Enew);
   for (long i = 0; i < nc; i++) Ehalf[i] = 0.5 * (E[i] + Enew[i]);
@@ -282,6 +322,9 @@ int orc_es1d_step(const orc_es1d_cfg *cfg, orc_species *sp, int nsp,
   for (int s = 0; s < nsp; s++) {
     double qm = sp[s].q / sp[s].m;
     long count = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : count)
+#endif
     for (long p = 0; p < sp[s].n; p++) {
       long idx[3];
       double wt[3];
@@ -687,6 +730,73 @@ void orc_poisson_e0_1d(const orc_es1d_cfg *cfg, const orc_species *sp,
   deposit_charge(cfg, sp, nsp, rho);
   poisson_spectral(nc, cfg->L, rho, E);
   free(rho);
+}
+
+/*
+ * Charge diagnostics of a 1D1V state (Sec. 2.1: Gauss's law dE/dx = rho - 1 in
+ * the paper's units, kept in time by continuity, d rho/dt + dj/dx = 0):
+ *   rho_h     = (1/h) sum_p q w_p S(x_h - x_p), the deposit's own shape;
+ *   Q_grid    = h sum_h rho_h,   Q_markers = sum_p q w_p;
+ *   r         = D E - (rho - <rho>): the residual of Gauss's law with the
+ *               spectral derivative D of the initial Poisson solve, on the
+ *               Fourier modes m = 1 .. (nc - 1) / 2 (k = 0, the neutralising
+ *               background, and the Nyquist mode, which D does not represent,
+ *               left out): r_m = i kappa_m E_m - rho_m, kappa_m = 2 pi m / L,
+ *               F_m = sum_j F_j exp(-2 pi i m j / nc), and in real space
+ *               r_j = (2 / nc) sum_m Re(r_m exp(2 pi i m j / nc));
+ *   gauss_l2  = sqrt(h sum_j r_j^2),  rho_l2 = sqrt(h sum_j rhot_j^2) with
+ *               rhot the same modes of rho.
+ * r and rhot: [nc] or NULL.  Plain O(nc^2) transforms.
+ * Pinned (test_oracle_charge1d.py): the residual against numpy's FFT, a single
+ * field mode in closed form, zero for the field of the Poisson solve, the
+ * charge totals against the markers' charge.
+ */
+void orc_es1d_charge_diag(const orc_es1d_cfg *cfg, const orc_species *sp, int nsp,
+                          const double *E, double *Q_markers, double *Q_grid,
+                          double *gauss_l2, double *rho_l2, double *r, double *rhot) {
+  const double twopi = 6.283185307179586476925286766559;
+  long nc = cfg->nc, M = (nc - 1) / 2;
+  double h = cfg->L / (double)nc;
+  double *rho = (double *)calloc((size_t)nc, sizeof(double));
+  double *rr = (double *)calloc((size_t)nc, sizeof(double));
+  double *rt = (double *)calloc((size_t)nc, sizeof(double));
+  deposit_charge(cfg, sp, nsp, rho);
+  double qm = 0.0, qg = 0.0;
+  for (int s = 0; s < nsp; s++)
+    for (long p = 0; p < sp[s].n; p++) qm += sp[s].q * weight_of(&sp[s], p);
+  for (long j = 0; j < nc; j++) qg += h * rho[j];
+  for (long m = 1; m <= M; m++) {
+    double er = 0.0, ei = 0.0, pr = 0.0, pi = 0.0;
+    for (long j = 0; j < nc; j++) {
+      double ang = -twopi * (double)((j * m) % nc) / (double)nc;
+      er += E[j] * cos(ang);
+      ei += E[j] * sin(ang);
+      pr += rho[j] * cos(ang);
+      pi += rho[j] * sin(ang);
+    }
+    double kappa = twopi * (double)m / cfg->L;
+    /* r_m = i kappa E_m - rho_m */
+    double rre = -kappa * ei - pr, rim = kappa * er - pi;
+    for (long j = 0; j < nc; j++) {
+      double ang = twopi * (double)((j * m) % nc) / (double)nc;
+      rr[j] += 2.0 * (rre * cos(ang) - rim * sin(ang)) / (double)nc;
+      rt[j] += 2.0 * (pr * cos(ang) - pi * sin(ang)) / (double)nc;
+    }
+  }
+  double g2 = 0.0, p2 = 0.0;
+  for (long j = 0; j < nc; j++) {
+    g2 += rr[j] * rr[j];
+    p2 += rt[j] * rt[j];
+  }
+  if (Q_markers) *Q_markers = qm;
+  if (Q_grid) *Q_grid = qg;
+  if (gauss_l2) *gauss_l2 = sqrt(h * g2);
+  if (rho_l2) *rho_l2 = sqrt(h * p2);
+  if (r) memcpy(r, rr, sizeof(double) * (size_t)nc);
+  if (rhot) memcpy(rhot, rt, sizeof(double) * (size_t)nc);
+  free(rho);
+  free(rr);
+  free(rt);
 }
 
 /* E from dE/dx = rho - <rho> as above (k = 0 and the Nyquist mode zeroed). */
