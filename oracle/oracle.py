@@ -125,6 +125,9 @@ def _declare(L):
     L.orc_es1d_step.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp, _lp,
                                 C.POINTER(_dp)]
     L.orc_es1d_step.restype = C.c_int
+    L.orc_es1d_step_radicand.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp,
+                                         _lp, C.POINTER(_dp), C.POINTER(_dp)]
+    L.orc_es1d_step_radicand.restype = C.c_int
     L.orc_es1d_charge_diag.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp,
                                        _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_es1d_energy.argtypes = [C.POINTER(_EsCfg), C.POINTER(_Species), C.c_int, _dp, _dp, _dp]
@@ -242,6 +245,19 @@ def es1d_step(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray, want_g
     rc = L.orc_es1d_step(C.byref(cfg._c()), sp, len(species), _ptr(E), nfb, gptr)
     assert rc == 0
     return list(nfb), gam
+
+
+def es1d_step_radicand(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray):
+    """One step; returns (fallback counts per species, R / |v^dag|^2 per marker of
+    each species: negative where Gamma would be imaginary)."""
+    sp = _sp_array(species)
+    nfb = (C.c_long * len(species))()
+    rad = [np.zeros(len(s.x)) for s in species]
+    rarr = (_dp * len(species))(*[_ptr(g) for g in rad])
+    rc = lib().orc_es1d_step_radicand(C.byref(cfg._c()), sp, len(species), _ptr(E), nfb,
+                                      C.cast(None, C.POINTER(_dp)), C.cast(rarr, C.POINTER(_dp)))
+    assert rc == 0
+    return list(nfb), rad
 
 
 def es1d_energy(cfg: ES1DConfig, species: Sequence[Species], E: np.ndarray):

@@ -259,8 +259,21 @@ static void deposit_current(const orc_es1d_cfg *cfg, const orc_species *s, const
  * Gamma = 1 + O(dt^3) / O(dt^4), cold plasma frequency, Landau and
  * two-stream rates, brute force (test_oracle_es1d.py).
  */
+int orc_es1d_step_radicand(const orc_es1d_cfg *cfg, orc_species *sp, int nsp, double *E,
+                           long *nfallback, double *const *gamma_out,
+                           double *const *radicand_out);
+
 int orc_es1d_step(const orc_es1d_cfg *cfg, orc_species *sp, int nsp,
                   double *E, long *nfallback, double *const *gamma_out) {
+  return orc_es1d_step_radicand(cfg, sp, nsp, E, nfallback, gamma_out, NULL);
+}
+
+/* orc_es1d_step with one more optional output: radicand_out (NULL, or nsp
+ * pointers, each NULL or [n]) receives R / |v^dag|^2 of every marker, the
+ * scale-free radicand whose sign decides the fallback (NaN where v^dag = 0). */
+int orc_es1d_step_radicand(const orc_es1d_cfg *cfg, orc_species *sp, int nsp, double *E,
+                           long *nfallback, double *const *gamma_out,
+                           double *const *radicand_out) {
   if (nsp <= 0 || cfg->nc <= 0) return -1;
   long nc = cfg->nc;
   double L = cfg->L, dt = cfg->dt, h = L / (double)nc;
@@ -345,6 +358,7 @@ int orc_es1d_step(const orc_es1d_cfg *cfg, orc_species *sp, int nsp,
         }
       }
       if (gamma_out && gamma_out[s]) gamma_out[s][p] = gamma;
+      if (radicand_out && radicand_out[s]) radicand_out[s][p] = vd2 > 0.0 ? R / vd2 : NAN;
       sp[s].v[p] = gamma == 1.0 ? vdag : vdag * gamma;
       sp[s].x[p] = wrap(sp[s].x[p] + dt * vstar, L);
     }
