@@ -164,6 +164,20 @@ typedef struct {
                             /* energy identity is unchanged.  0 = the point   */
                             /* shapes of shape_order.  Other solvers or forms */
                             /* with 1: PIC_ERR_UNSUPPORTED.                   */
+  int gamma_fp64;           /* mixed 1D1V form, sort_period 0: 1 = the        */
+                            /* correction (t, the R < 0 test and Gamma) in    */
+                            /* FP64 for every marker; 0 = FP64 only where     */
+                            /* |Gamma - 1| >= 2^-9 or R may be negative, an   */
+                            /* FP32 series elsewhere.  The FP64 form computes */
+                            /* everything in FP64 (the flag changes nothing); */
+                            /* other mixed forms with 1: PIC_ERR_UNSUPPORTED. */
+  int separate_passes;      /* mixed 1D1V form, ESEC1, sort_period 0: 0 = one */
+                            /* launch per step, the update of step n fused    */
+                            /* with the push and deposit of step n+1 (ESEC1  */
+                            /* needs no j^{n,*}, so nothing global lies       */
+                            /* between them); 1 = two launches per step, as   */
+                            /* ESEC2 runs.  Both give the same results bit    */
+                            /* for bit.  Other forms: ignored.                */
 } pic_config;
 
 typedef struct pic_handle pic_handle;
@@ -214,7 +228,8 @@ int pic_launch_count(pic_handle *h, int64_t *launches);
  * 0 = pass C (gather at x*, push to v*, deposit of j^{*,n+1/2}),
  * 1 = pass E (gather at x^{n+1/2}, Gamma, state update, next j^{n,*}),
  * 2 = per-step energy/fallback finalisation, 3 = cell sort,
- * 4 = grid field updates (Yee solver).
+ * 4 = grid field updates (Yee solver), 5 = the fused ESEC1 pass (pass E of a
+ * step with pass C of the next, see separate_passes).
  */
 int pic_set_profiling(pic_handle *h, int on);
 int pic_profile(pic_handle *h, int kind, int64_t *launches, double *total_ms);
@@ -227,6 +242,45 @@ int pic_profile(pic_handle *h, int kind, int64_t *launches, double *total_ms);
  * Any output may be NULL.  Always host pointers.
  */
 int pic_energy(pic_handle *h, double *KE_per_species, double *W_E, double *W_B, double *TE);
+
+/*
+ * Charge diagnostics of the current state (Sec. 2.1: Gauss's law, kept in time
+ * by continuity when the deposit conserves charge, Sec. 3.5), reduced in FP64
+ * on the device:
+ *   Q_markers = sum_p q w_p over all species; Q_grid = |h| sum rho_h, with rho
+ *   the charge density deposited on the nodes (equal to Q_markers up to
+ *   rounding: the shapes are a partition of unity);
+ *   the residual r of Gauss's law with the neutralising background:
+ *   - Ampere solver (1D): rho with the scheme's own shape (the mixed form's
+ *     quantised weights), r = D E^n - (rho - <rho>) with the spectral
+ *     derivative D of the initial Poisson solve, on the Fourier modes
+ *     1 .. (nodes - 1) / 2 (k = 0 is the background; D does not represent the
+ *     Nyquist mode); zero to rounding right after pic_init with E0 = NULL;
+ *   - Yee solver (2D): rho with the bilinear shape on the nodes (i, j),
+ *     r = div_h E^n - (rho - <rho>) with the Yee divergence
+ *     (Ex(i+1/2,j) - Ex(i-1/2,j)) / hx + (Ey(i,j+1/2) - Ey(i,j-1/2)) / hy; with
+ *     charge_conserving = 1, r keeps its initial value (Eq. detbal);
+ *   gauss_l2 = sqrt(|h| sum r^2); rho_l2 = sqrt(|h| sum (rho - <rho>)^2) over
+ *   the same modes (1D) or nodes (2D), its scale.
+ * residual: [nodes] (1D) or [ny][nx] (2D), host or device as the handle's
+ * pointers, or NULL.  Any output may be NULL.  The spectral solvers and the
+ * standard comparator: PIC_ERR_UNSUPPORTED.  The first call allocates the
+ * diagnostic's device buffers.
+ */
+int pic_charge(pic_handle *h, double *Q_markers, double *Q_grid, double *gauss_l2, double *rho_l2,
+               double *residual);
+
+/*
+ * Resolution of a mixed-form handle (precision PIC_PREC_MIXED, any solver;
+ * else PIC_ERR_UNSUPPORTED): *dx = L / 2^32, the step of the fixed-point
+ * positions; *dv = the velocity of one unit of the integer v* (the float-pair
+ * velocities resolve about 2^-48 of their value in the same units); and
+ * *deposit_bits = T: every marker's deposit adds an integer below 2^T, the
+ * product of its v* and shape weights rounded to 2^-T of its largest value,
+ * so T bounds the relative rounding of each deposited term (the current, and
+ * through it the field work of Eq. exp_econs_simple).  Any output may be NULL.
+ */
+int pic_mixed_resolution(pic_handle *h, double *dx, double *dv, int *deposit_bits);
 
 /* Copies species s out as FP64 SoA ([dim_x][n] positions, [dim_v][n]
  * velocities).  Marker order is the library's current (possibly sorted)

@@ -481,8 +481,8 @@ __device__ __forceinline__ void mix_tile_deposit(unsigned *Jl, int rt, const Sha
 #pragma unroll
   for (int k = 0; k <= ORDER; k++) {
     unsigned *q = Jl + (S.p + k) * 4 * rt;
-    const SplitTerm tx = split_term(Vx, S.s[k], m.rshift, m.rnd);
-    const SplitTerm ty = split_term(Vy, S.s[k], m.rshift, m.rnd);
+    const SplitTerm tx = split_term(Vx, S.s[k], m.rshift, m.rnd, 0xFFFFu, m.rshift - 16);
+    const SplitTerm ty = split_term(Vy, S.s[k], m.rshift, m.rnd, 0xFFFFu, m.rshift - 16);
     atomicAdd(q, tx.lo);
     atomicAdd(q + rt, (unsigned)tx.hi);
     atomicAdd(q + 2 * rt, ty.lo);
@@ -522,10 +522,29 @@ __device__ __forceinline__ void clear_words(unsigned *a, int len) {
   for (int i = threadIdx.x; i < len; i += blockDim.x) a[i] = 0u;
 }
 
+// The non-series path of correct_velocity_xy: the R < 0 test and Gamma - 1 in
+// FP64 (mixed_common.cuh).
+__device__ __noinline__ ff2 correct_velocity_xy_fp64(float2 vh, float2 vl, int Vx, int Vy, ff2 D,
+                                                     ff2 vd, unsigned &nfb) {
+  const ff Dx{D.hi.x, D.lo.x}, Dy{D.hi.y, D.lo.y};
+  const ff vx{vd.hi.x, vd.lo.x}, vy{vd.hi.y, vd.lo.y};
+  const double a = ff_to_double(Dx) * bracket_fp64(vh.x, vl.x, Vx, Dx) +
+                   ff_to_double(Dy) * bracket_fp64(vh.y, vl.y, Vy, Dy);
+  const double ux = ff_to_double(vx), uy = ff_to_double(vy);
+  double g;
+  if (!gamma_minus_one_fp64(a, ux * ux + uy * uy, g)) {
+    nfb++;
+    return vd;
+  }
+  const ff nx = scale_by_gamma_fp64(vx, g), ny = scale_by_gamma_fp64(vy, g);
+  return ff2{make_float2(nx.hi, ny.hi), make_float2(nx.lo, ny.lo)};
+}
+
 // v^dag = v^n + Delta and v^{n+1} = Gamma v^dag for the pair (vx, vy) of one
 // marker, the components in the two lanes (x, y) of packed float pairs:
 // b = V* - v^n - Delta/2 from the exact differences, a = Delta . b, and
-// Gamma - 1 from t = 2a / |v^dag|^2 as in the 1D1V mixed form.
+// Gamma - 1 from t = 2a / |v^dag|^2 as in the 1D1V mixed form: the FP32
+// series for |t| < 2^-8, else the R < 0 test and Gamma in FP64.
 __device__ __forceinline__ ff2 correct_velocity_xy(float2 vh, float2 vl, int Vx, int Vy, ff2 D,
                                                    bool on, unsigned &nfb) {
   const ff2 vd = ff_add2(ff2{vh, vl}, D);
@@ -538,16 +557,9 @@ __device__ __forceinline__ ff2 correct_velocity_xy(float2 vh, float2 vl, int Vx,
   const float2 db = mul2(add2(D.hi, D.hi), bq);
   const float2 v2 = mul2(vd.hi, vd.hi);
   const float t = div_rcp_residual(__fadd_rn(db.x, db.y), __fadd_rn(v2.x, v2.y));
-  float gm;
-  if (fabsf(t) < 0.00390625f) {
-    gm = __fmul_rn(
-        t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, -0.0390625f, 0.0625f), -0.125f), 0.5f));
-  } else if (!(t >= -1.0f && t < 1e30f)) {
-    nfb++;
-    return vd;
-  } else {
-    gm = __fdiv_rn(t, __fadd_rn(1.0f, __fsqrt_rn(__fadd_rn(1.0f, t))));
-  }
+  if (!(fabsf(t) < 0.00390625f)) return correct_velocity_xy_fp64(vh, vl, Vx, Vy, D, vd, nfb);
+  const float gm = __fmul_rn(
+      t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, -0.0390625f, 0.0625f), -0.125f), 0.5f));
   ff2 p = two_prod2(vd.hi, splat2(gm));
   p.lo = fma2(vd.lo, splat2(gm), p.lo);
   return ff_add2(vd, p);

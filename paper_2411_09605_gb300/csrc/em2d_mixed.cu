@@ -190,13 +190,27 @@ __device__ __forceinline__ ff ff_from_int(int V) {
   return {hi, __int2float_rn(V - __float2int_rn(hi))};
 }
 
+// The non-series path of correct_velocity3: the R < 0 test and Gamma - 1 in
+// FP64 (mixed_common.cuh); returns false for the fallback.
+__device__ __noinline__ bool gamma3_fp64(float vh0, float vh1, float vh2, float vl0, float vl1,
+                                         float vl2, int V0, int V1, int V2, ff D0, ff D1, ff D2,
+                                         ff u0, ff u1, ff u2, double &g) {
+  const double a = ff_to_double(D0) * bracket_fp64(vh0, vl0, V0, D0) +
+                   ff_to_double(D1) * bracket_fp64(vh1, vl1, V1, D1) +
+                   ff_to_double(D2) * bracket_fp64(vh2, vl2, V2, D2);
+  const double x = ff_to_double(u0), y = ff_to_double(u1), z = ff_to_double(u2);
+  return gamma_minus_one_fp64(a, x * x + y * y + z * z, g);
+}
+
 // v^dag = v^n + Delta and v^{n+1} = Gamma v^dag (Eq. opt_solution) in float
 // pairs, three components.  R - |v^dag|^2 = 2a with a = Delta . b and
 // b = V* - v^n - Delta/2: each b_i is formed from the exact difference
 // V*_i - rint(vh_i) and the exact remainders, the small product in FP32.
 // Gamma - 1 = t / (1 + sqrt(1 + t)), t = 2a / |v^dag|^2; for |t| < 2^-8 the
-// series t/2 - t^2/8 + t^3/16 - 5t^4/128 (relative error < 2^-33).  R < 0
-// (t < -1) and v^dag = 0 (t not finite) fall back to Gamma = 1, counted.
+// series t/2 - t^2/8 + t^3/16 - 5t^4/128 (relative error < 2^-33); every
+// other marker, among them every candidate for the fallback, takes
+// gamma3_fp64: R < 0 (t < -1) and v^dag = 0 (t not finite) fall back to
+// Gamma = 1, counted.
 __device__ __forceinline__ void correct_velocity3(const float vh[3], const float vl[3],
                                                   const int Vs[3], const ff D[3], bool on,
                                                   unsigned &nfb, ff vn[3]) {
@@ -221,10 +235,16 @@ __device__ __forceinline__ void correct_velocity3(const float vh[3], const float
     if (fabsf(t) < 0.00390625f) {
       gm = __fmul_rn(
           t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, -0.0390625f, 0.0625f), -0.125f), 0.5f));
-    } else if (!(t >= -1.0f && t < 1e30f)) {
-      nfb++;
     } else {
-      gm = __fdiv_rn(t, __fadd_rn(1.0f, __fsqrt_rn(__fadd_rn(1.0f, t))));
+      double g;
+      if (!gamma3_fp64(vh[0], vh[1], vh[2], vl[0], vl[1], vl[2], Vs[0], Vs[1], Vs[2], D[0], D[1],
+                       D[2], vd[0], vd[1], vd[2], g)) {
+        nfb++;
+      } else {
+#pragma unroll
+        for (int d = 0; d < 3; d++) vn[d] = scale_by_gamma_fp64(vd[d], g);
+        return;
+      }
     }
   }
 #pragma unroll

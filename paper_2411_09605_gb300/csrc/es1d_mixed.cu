@@ -60,7 +60,7 @@ __device__ __forceinline__ int cell_of(uint32_t X, int nc) {
 
 
 __device__ __forceinline__ SplitTerm deposit_split(int V, int s, const Es1dMixConst &c) {
-  return split_term(V, s, c.rshift, c.rnd);
+  return split_term(V, s, c.rshift, c.rnd, c.lomask, c.hishift);
 }
 
 __device__ __forceinline__ long long deposit_term(int V, int s, const Es1dMixConst &c) {
@@ -74,18 +74,19 @@ __device__ __forceinline__ uint32_t half_shift(int V, const Es1dMixConst &c) {
 }
 
 // Shared-memory current tile.  Every padded node holds two 32-bit counters per
-// copy: the low 16 bits of each added amount (unsigned) and the signed rest;
-// an amount A is added exactly as (A & 0xFFFF, A >> 16) and the node's value is
-// rest 2^16 + low.  Two 32-bit shared atomics run faster than one 64-bit one,
-// and the rounding shift r is chosen so that no counter can overflow for the
-// markers that add into it.  The tile is laid out [node][half][copy] with RT
+// copy: the low b = c.split bits of each added amount (unsigned) and the
+// signed rest; an amount A is added exactly as (A mod 2^b, A >> b) and the
+// node's value is rest 2^b + low.  Two 32-bit shared atomics run faster than
+// one 64-bit one.  With at most 2^(32-b) amounts per copy in a launch the low
+// counter cannot overflow, and the rounding shift r is chosen so that the
+// signed rest cannot either.  The tile is laid out [node][half][copy] with RT
 // copies; lane l of every warp adds into copy l mod RT (Jl = tile + l mod RT).
 // With RT = 32 the lanes of a warp always address 32 different banks, so the
 // random-address atomics of unsorted markers never conflict.
 template <int RT>
-__device__ __forceinline__ void tile_add(unsigned *Jl, int q, long long a) {
-  atomicAdd(&Jl[q * 2 * RT], (unsigned)a & 0xFFFFu);
-  atomicAdd(&Jl[q * 2 * RT + RT], (unsigned)(int)(a >> 16));
+__device__ __forceinline__ void tile_add(unsigned *Jl, int q, long long a, int b) {
+  atomicAdd(&Jl[q * 2 * RT], (unsigned)a & ((1u << b) - 1u));
+  atomicAdd(&Jl[q * 2 * RT + RT], (unsigned)(int)(a >> b));
 }
 
 template <int ORDER, int RT>
@@ -137,17 +138,17 @@ struct DepositWindow {
       }
     } else {
 #pragma unroll
-      for (int k = 0; k <= ORDER; k++) tile_add<1>(Jt, S.p + k, t[k]);
+      for (int k = 0; k <= ORDER; k++) tile_add<1>(Jt, S.p + k, t[k], c.split);
     }
   }
-  __device__ __forceinline__ void flush(unsigned *Jt) {
+  __device__ __forceinline__ void flush(unsigned *Jt, int b) {
     const bool lead = (threadIdx.x & 31u) == 0u;
 #pragma unroll
     for (int w = 0; w < kWin; w++) {
       if (__any_sync(0xffffffffu, acc[w] != 0)) {
         const int hs = __reduce_add_sync(0xffffffffu, (int)(acc[w] >> 20));
         const int ls = __reduce_add_sync(0xffffffffu, (int)(acc[w] & 0xFFFFF));
-        if (lead) tile_add<1>(Jt, base + w, ((long long)hs << 20) + (long long)ls);
+        if (lead) tile_add<1>(Jt, base + w, ((long long)hs << 20) + (long long)ls, b);
       }
     }
   }
@@ -226,7 +227,7 @@ __device__ __forceinline__ void clear_tile(unsigned *Jt, int npad) {
 // integers, so the grid total does not depend on the order of the blocks).
 template <int ORDER, int RT>
 __device__ __forceinline__ void flush_tile(const unsigned *Jt, long long *J, long long *total,
-                                           int nc) {
+                                           int nc, int b) {
   __shared__ long long tred[32];
   const int npad = npad_of(nc);
   long long mine = 0;
@@ -240,7 +241,7 @@ __device__ __forceinline__ void flush_tile(const unsigned *Jt, long long *J, lon
       lo += Jt[q * 2 * RT + kk];
       hi += (int)Jt[q * 2 * RT + RT + kk];
     }
-    const long long a = hi * 65536ll + lo;
+    const long long a = hi * (1ll << b) + lo;
     mine += a;
     if (a != 0)
       atomicAdd((unsigned long long *)&J[wrap_node(q - Pad<ORDER>::kPad, nc) * kJStride],
@@ -313,22 +314,36 @@ __device__ __forceinline__ void store_copies(T *row, T v) {
 }
 
 
+// The correction of Eq. opt_solution in FP64 from the float-pair state
+// (bracket_fp64, gamma_minus_one_fp64): the R < 0 test and Gamma - 1 in FP64;
+// a fallback keeps v^dag and is counted (Sec. 3.2, Sec. 5.1).
+__device__ __forceinline__ ff correct_velocity_fp64(float vh, float vl, int Vs, ff d, ff vd,
+                                                 unsigned &nfb) {
+  const double vdd = ff_to_double(vd);
+  double g;
+  if (!gamma_minus_one_fp64(ff_to_double(d) * bracket_fp64(vh, vl, Vs, d), vdd * vdd, g)) {
+    nfb++;
+    return vd;
+  }
+  return scale_by_gamma_fp64(vd, g);
+}
+
 // v^dag = v^n + d and v^{n+1} = Gamma v^dag (Eq. opt_solution) in float pairs.
-// With R = |v^n|^2 + 2 v* . (v^dag - v^n), R - |v^dag|^2 = 2a and
-// a = d (v* - v^n - d/2); the bracket is formed from the exact difference
-// V* - v^n, so t = 2a / |v^dag|^2 keeps its relative precision however small it
-// is, and Gamma - 1 = sqrt(1 + t) - 1 = t / (1 + sqrt(1 + t)).  For |t| < 2^-8
-// the series t/2 - t^2/8 + t^3/16 - 5t^4/128 (relative error < 2^-33) replaces
-// the correctly rounded sqrt and divide.  R < 0 is t < -1; that and v^dag = 0
-// (t not finite) fall back to Gamma = 1 and are counted.
+// t = 2a / |v^dag|^2 (see correct_velocity_fp64) is first formed in FP32 from
+// the same exact pieces: V* - v^n = (V* - ih) - fr - vl with V* - ih a small
+// exact integer, its sum with -d/2 split exactly by a two-sum and only the
+// small terms rounded.  For |t| < 2^-8 (|Gamma - 1| < 2^-9: every marker whose
+// speed is not small against its kick) Gamma - 1 is the series t/2 - t^2/8 +
+// t^3/16 - 5t^4/128 in FP32 (relative error below 2^-22, so Gamma is within
+// 2^-31 of its value); every other marker, among them every candidate for
+// the fallback, takes correct_velocity_fp64, which decides R < 0 and forms
+// Gamma in FP64.  With G64 every marker takes correct_velocity_fp64.
+template <bool G64>
 __device__ __forceinline__ ff correct_velocity(float vh, float vl, int Vs, ff d, bool on,
                                                unsigned &nfb) {
   const ff vd = ff_add(ff{vh, vl}, d);
   if (!on) return vd;
-  // b = v* - v^n - d/2 with v* = V*: vh = ih + fr with ih = rint(vh) (an int,
-  // |vh| < 2^31) and fr exact, so V* - v^n = (V* - ih) - fr - vl where V* - ih
-  // is a small exact integer; its sum with -d/2 is split exactly by a two-sum
-  // and only the small terms are rounded.
+  if (G64) return correct_velocity_fp64(vh, vl, Vs, d, vd, nfb);
   const int ih = __float2int_rn(vh);
   const float fr = __fsub_rn(vh, __int2float_rn(ih));
   const ff q = two_sum(__int2float_rn(Vs - ih), __fmul_rn(-0.5f, d.hi));
@@ -344,14 +359,7 @@ __device__ __forceinline__ ff correct_velocity(float vh, float vl, int Vs, ff d,
     const ff s = fast_two_sum(vd.hi, p.hi);
     return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(vd.lo, p.lo)));
   }
-  if (!(t >= -1.0f && t < 1e30f)) {
-    nfb++;
-    return vd;
-  }
-  const float gm = __fdiv_rn(t, __fadd_rn(1.0f, __fsqrt_rn(__fadd_rn(1.0f, t))));
-  ff p = two_prod(vd.hi, gm);
-  p.lo = __fmaf_rn(vd.lo, gm, p.lo);
-  return ff_add(vd, p);
+  return correct_velocity_fp64(vh, vl, Vs, d, vd, nfb);
 }
 
 // dt (q/m) cxk E^{n+1/2}_p of two markers (lane x: S0, lane y: S1) as float
@@ -381,8 +389,14 @@ __device__ __forceinline__ ff2 gather_kick2(const float2 *El, const ShapeMix<ORD
 // correct_velocity for two markers at once.  The packed path covers the
 // common case, both markers corrected with |t| < 2^-8; any other pair runs
 // correct_velocity per marker, so each lane gets exactly the scalar result.
+template <bool G64>
 __device__ __forceinline__ ff2 correct_velocity2(float2 vh, float2 vl, int Vs0, int Vs1, ff2 d,
                                                  bool on0, bool on1, unsigned &nfb) {
+  if (G64) {
+    const ff v0 = correct_velocity<true>(vh.x, vl.x, Vs0, ff{d.hi.x, d.lo.x}, on0, nfb);
+    const ff v1 = correct_velocity<true>(vh.y, vl.y, Vs1, ff{d.hi.y, d.lo.y}, on1, nfb);
+    return ff2{make_float2(v0.hi, v1.hi), make_float2(v0.lo, v1.lo)};
+  }
   const ff2 vd = ff_add2(ff2{vh, vl}, d);
   bool packed = on0 && on1;
   float2 gm = make_float2(0.0f, 0.0f);
@@ -406,8 +420,8 @@ __device__ __forceinline__ ff2 correct_velocity2(float2 vh, float2 vl, int Vs0, 
                         splat2(0.5f)));
   }
   if (!packed) {
-    const ff v0 = correct_velocity(vh.x, vl.x, Vs0, ff{d.hi.x, d.lo.x}, on0, nfb);
-    const ff v1 = correct_velocity(vh.y, vl.y, Vs1, ff{d.hi.y, d.lo.y}, on1, nfb);
+    const ff v0 = correct_velocity<false>(vh.x, vl.x, Vs0, ff{d.hi.x, d.lo.x}, on0, nfb);
+    const ff v1 = correct_velocity<false>(vh.y, vl.y, Vs1, ff{d.hi.y, d.lo.y}, on1, nfb);
     return ff2{make_float2(v0.hi, v1.hi), make_float2(v0.lo, v1.lo)};
   }
   ff2 p = two_prod2(vd.hi, gm);
@@ -618,13 +632,13 @@ __device__ __forceinline__ void pass_c_body(const Es1dMixConst &c, const Es1dMix
         Vout[jj] = Vs;
       }
     }
-    if (AGG) win.flush(Jt);
+    if (AGG) win.flush(Jt, c.split);
     if (gv) store_vec<G>(b.Vs, g, Vout);
   });
   griddep_launch_dependents();
   report_flags(bad, b.err);
   __syncthreads();
-  flush_tile<ORDER, RT>(Jt, PSEL(b.J2, par), b.Jtot + 2 + par, c.nc);
+  flush_tile<ORDER, RT>(Jt, PSEL(b.J2, par), b.Jtot + 2 + par, c.nc, c.split);
   if (MODE == 2)
     for (int i = threadIdx.x; i < 2 * c.nc; i += blockDim.x)
       b.H[(int64_t)i * P.nb + P.rb] = hist[i];
@@ -639,7 +653,7 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
 // pass E: E^{n+1} and dt (q/m) cxk E^{n+1/2} (float pairs) in the prologue; per
 // marker the gather at x^{n+1/2} = X + [V*], v^dag, Gamma, x^{n+1}, v^{n+1},
 // the kinetic energy and (ESEC2) the next step's x* and j^{n+1,*} deposit.
-template <int ORDER, int SCHEME, int MODE, int RT, int RE>
+template <int ORDER, int SCHEME, int MODE, int RT, int RE, bool G64 = false>
 __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMixBufs &b, int par,
                                             int slot, BlockPlace P) {
   constexpr bool AGG = MODE > 0;
@@ -731,7 +745,7 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
       ShapeMix<ORDER> Sh0, Sh1;
       shape_mix_pair<ORDER>(m.X[j] + hs0, m.X[j + 1] + hs1, c.nc, Sh0, Sh1);
       const ff2 d = gather_kick2<ORDER, RE>(El, Sh0, Sh1);
-      const ff2 vn2 = correct_velocity2(make_float2(m.vh[j], m.vh[j + 1]),
+      const ff2 vn2 = correct_velocity2<G64>(make_float2(m.vh[j], m.vh[j + 1]),
                                         make_float2(m.vl[j], m.vl[j + 1]), m.V[j], m.V[j + 1], d,
                                         c.gamma_on && valid0, c.gamma_on && valid1, nfb);
       {
@@ -787,7 +801,7 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
         o.vl[jj] = valid ? vn.lo : m.vl[jj];
       }
     }
-    if (AGG && SCHEME == 2) win.flush(Jt);
+    if (AGG && SCHEME == 2) win.flush(Jt, c.split);
     if (MODE != 2 && gv) {
       store_vec<G>(b.X, g, o.X);
       store_vec<G>(b.vh, g, o.vh);
@@ -818,13 +832,173 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
       if (lane == 0) b.ke_part[P.rb] = c.ke_scale * ((double)k.hi + (double)k.lo);
     }
   }
-  if (SCHEME == 2) flush_tile<ORDER, RT>(Jt, PSEL(b.J1, par ^ 1), b.Jtot + (par ^ 1), c.nc);
+  if (SCHEME == 2) flush_tile<ORDER, RT>(Jt, PSEL(b.J1, par ^ 1), b.Jtot + (par ^ 1), c.nc, c.split);
 }
 
-template <int ORDER, int SCHEME, int MODE, int RT, int RE>
+template <int ORDER, int SCHEME, int MODE, int RT, int RE, bool G64>
 __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
     mix_pass_e_kernel(Es1dMixConst c, Es1dMixBufs b, int par, int slot) {
-  pass_e_body<ORDER, SCHEME, MODE, RT, RE>(c, b, par, slot, grid_place());
+  pass_e_body<ORDER, SCHEME, MODE, RT, RE, G64>(c, b, par, slot, grid_place());
+}
+
+// ESEC1 in one pass per step (Eq. naivetranslation with the correction of Eq.
+// PICmodification).  ESEC1 has no j^{n,*}: the only grid quantity a step
+// needs before its first gather is E^n, so the update of step n (pass E: the
+// gather at x^{n+1/2}, Gamma, x^{n+1}, v^{n+1}) and the push of step n+1
+// (pass C: the gather of E^{n+1} at x*, v*, the deposit of j^{*,n+3/2}) run
+// on each marker in one visit: 16 bytes read and 16 written per
+// particle-step.  The block prologue builds both tables from the same inputs
+// the two separate passes use (kick E^{n+1/2} in float pairs; e_scale E^{n+1}
+// in FP32 from the FP64 E^{n+1} that the last warp also writes back), so the
+// results are those of the two-launch form bit for bit.  Currents rotate
+// through three buffers (RingIO): this launch reads j^{*,n+1/2}, deposits
+// j^{*,n+3/2} and clears the one the previous launch read.
+template <int ORDER, int RT, int RE, int RE1>
+__global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
+    mix_pass_ec_kernel(Es1dMixConst c, Es1dMixBufs b, RingIO io, int par, int slot,
+                       int prev_slot, int prev_nblocks) {
+  constexpr int PAD = Pad<ORDER>::kPad;
+  const BlockPlace P = grid_place();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int npad = npad_of(c.nc);
+  unsigned *Jt = (unsigned *)smraw;              // [npad][2][RT]
+  float2 *Eh2 = (float2 *)(Jt + 2 * RT * npad);  // [npad][RE]: kick E^{n+1/2}
+  float *Es = (float *)(Eh2 + RE * npad);         // [npad][RE1]: e_scale E^{n+1}
+  clear_tile<RT>(Jt, npad);  // needs nothing from the previous kernel
+  griddep_wait();
+  const double mean_e = c.remove_mean ? (double)(*io.Tr) * c.jscale / c.nc : 0.0;
+  {
+    const float2 *Ek = PSEL(b.Ek, par);
+    const double *E = PSEL(b.E, par);
+    const ff meanj = c.remove_mean ? mean_of_total(*io.Tr, c) : ff{0.0f, 0.0f};
+    for (int q = threadIdx.x; q < npad; q += blockDim.x) {
+      const int i = wrap_node(q - PAD, c.nc);
+      const float2 ek = Ek[i];
+      const long long j2 = io.Jr[i * kJStride];
+      const ff dj = ff_sub(ff_from_i64(j2), meanj);
+      const ff eh = ff_sub(ff{ek.x, ek.y}, ff_mul(c.kick_jhalf, dj));
+      store_copies<RE>(Eh2 + q * RE, make_float2(eh.hi, eh.lo));
+      const double en = E[i] - c.dt * ((double)j2 * c.jscale - mean_e);
+      const ff k = ff_from_double(c.kick * en);
+      store_copies<RE1>(Es + q * RE1, __fmul_rn(0.5f, __fadd_rn(k.hi, k.lo)));
+    }
+  }
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31u;
+  if (last_warp()) {
+    // TE of the previous step from its partials (io.ke_prev, io.we_prev)
+    if (P.rb == 0 && prev_slot >= 0) {
+      Es1dMixBufs bp = b;
+      bp.ke_part = const_cast<double *>(io.ke_prev);
+      bp.we_part = const_cast<double *>(io.we_prev);
+      finalize_stats_warp(bp, c.h, prev_slot, prev_nblocks);
+    }
+    // E^{n+1} on this block's slice of nodes, its float-pair table, the
+    // cleared current buffer of step n+2 and this block's part of sum E^2
+    const double *E = PSEL(b.E, par);
+    if (P.rb == 0 && lane == 0) *io.Tc = 0;
+    const int n0 = (int)((int64_t)c.nc * P.rb / P.nb);
+    const int n1 = (int)((int64_t)c.nc * (P.rb + 1) / P.nb);
+    double w = 0.0;
+    for (int i = n0 + (int)lane; i < n1; i += 32) {
+      const double en = E[i] - c.dt * ((double)io.Jr[i * kJStride] * c.jscale - mean_e);
+      PSEL(b.E, par ^ 1)[i] = en;
+      const ff k = ff_from_double(c.kick * en);
+      PSEL(b.Ek, par ^ 1)[i] = make_float2(k.hi, k.lo);
+      io.Jc[i * kJStride] = 0;
+      w = fma(en, en, w);
+    }
+    if (n1 > n0)
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (lane == 0) io.we_out[P.rb] = w;
+  }
+  unsigned *Jl = Jt + (lane & (RT - 1));
+  const float2 *El = Eh2 + (lane & (RE - 1));
+  const float *Ex = Es + (lane & (RE1 - 1));
+  float2 ke2h = make_float2(0.0f, 0.0f), ke2l = make_float2(0.0f, 0.0f);
+  unsigned nfb = 0, bad = 0;
+  constexpr int G = kGroupE;
+  for_groups<G, true, false>(b, c.n, P, [&](auto check, int64_t g, const MarkerGroup<G> &m, int64_t end) {
+    constexpr bool CHECK = decltype(check)::value;
+    const bool gv = !CHECK || g < end;
+    MarkerGroup<G> o;
+#pragma unroll
+    for (int j = 0; j < G; j += 2) {
+      const bool valid0 = !CHECK || (gv && G * g + j < c.n);
+      const bool valid1 = !CHECK || (gv && G * g + j + 1 < c.n);
+      // step n: gather #2 at x^{n+1/2} = X + [V*], Gamma, x^{n+1}, v^{n+1}
+      const uint32_t hs0 = half_shift(m.V[j], c), hs1 = half_shift(m.V[j + 1], c);
+      ShapeMix<ORDER> Sh0, Sh1;
+      shape_mix_pair<ORDER>(m.X[j] + hs0, m.X[j + 1] + hs1, c.nc, Sh0, Sh1);
+      const ff2 d = gather_kick2<ORDER, RE>(El, Sh0, Sh1);
+      const ff2 vn2 = correct_velocity2<false>(make_float2(m.vh[j], m.vh[j + 1]),
+                                               make_float2(m.vl[j], m.vl[j + 1]), m.V[j],
+                                               m.V[j + 1], d, c.gamma_on && valid0,
+                                               c.gamma_on && valid1, nfb);
+      {
+        const float2 h = make_float2(valid0 ? vn2.hi.x : 0.0f, valid1 ? vn2.hi.y : 0.0f);
+        const float2 l = make_float2(valid0 ? vn2.lo.x : 0.0f, valid1 ? vn2.lo.y : 0.0f);
+        ff2 s2 = two_prod2(h, h);
+        s2.lo = fma2(add2(h, h), l, s2.lo);
+        const ff2 acc = two_sum2(ke2h, s2.hi);
+        ke2h = acc.hi;
+        ke2l = add2(ke2l, add2(acc.lo, s2.lo));
+      }
+      const uint32_t Xn0 = m.X[j] + 2u * hs0, Xn1 = m.X[j + 1] + 2u * hs1;
+      // step n+1: gather #1 of E^{n+1} at x* = x^{n+1} + dt/2 v^{n+1}, V*,
+      // x^{n+3/2} and the deposit of j^{*,n+3/2}
+      ShapeMix<ORDER> Sx0, Sx1;
+      shape_mix_pair<ORDER>(Xn0 + half_shift(to_fixed(vn2.hi.x, bad), c),
+                            Xn1 + half_shift(to_fixed(vn2.hi.y, bad), c), c.nc, Sx0, Sx1);
+      float2 e = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int k = 0; k <= ORDER; k++)
+        e = fma2(make_float2(Sx0.w[k], Sx1.w[k]),
+                 make_float2(Ex[(Sx0.p + k) * RE1], Ex[(Sx1.p + k) * RE1]), e);
+      int Vs2[2];
+      vstar_fixed2(vn2.hi, vn2.lo, e, bad, Vs2);
+      const uint32_t h20 = half_shift(Vs2[0], c), h21 = half_shift(Vs2[1], c);
+      ShapeMix<ORDER> S20, S21;
+      shape_mix_pair<ORDER>(Xn0 + h20, Xn1 + h21, c.nc, S20, S21);
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const int jj = j + u;
+        const bool valid = u ? valid1 : valid0;
+        if (valid) deposit_direct<ORDER, RT>(Jl, u ? S21 : S20, Vs2[u], c);
+        o.X[jj] = valid ? (u ? Xn1 : Xn0) : m.X[jj];
+        o.vh[jj] = valid ? (u ? vn2.hi.y : vn2.hi.x) : m.vh[jj];
+        o.vl[jj] = valid ? (u ? vn2.lo.y : vn2.lo.x) : m.vl[jj];
+        o.V[jj] = valid ? Vs2[u] : m.V[jj];
+      }
+    }
+    if (gv) {
+      store_vec<G>(b.X, g, o.X);
+      store_vec<G>(b.vh, g, o.vh);
+      store_vec<G>(b.vl, g, o.vl);
+      store_vec<G>(b.Vs, g, o.V);
+    }
+  });
+  griddep_launch_dependents();
+  const ff ke_t = ff_add(ff{ke2h.x, ke2l.x}, ff{ke2h.y, ke2l.y});
+  if (!isfinite(ke_t.hi) || !isfinite(ke_t.lo)) bad |= kErrNonfinite;
+  report_flags(bad, b.err);
+  nfb = __reduce_add_sync(0xffffffffu, nfb);
+  if (lane == 0 && nfb) atomicAdd(&b.fallback[slot], (unsigned long long)nfb);
+  {
+    __shared__ float2 kred[32];
+    ff k = ke_t;
+    for (int o = 16; o > 0; o >>= 1)
+      k = ff_add(k, ff{__shfl_xor_sync(0xffffffffu, k.hi, o), __shfl_xor_sync(0xffffffffu, k.lo, o)});
+    if (lane == 0) kred[threadIdx.x >> 5] = make_float2(k.hi, k.lo);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      k = threadIdx.x < (blockDim.x >> 5) ? ff{kred[lane].x, kred[lane].y} : ff{0.0f, 0.0f};
+      for (int o = 16; o > 0; o >>= 1)
+        k = ff_add(k, ff{__shfl_xor_sync(0xffffffffu, k.hi, o), __shfl_xor_sync(0xffffffffu, k.lo, o)});
+      if (lane == 0) io.ke_out[P.rb] = c.ke_scale * ((double)k.hi + (double)k.lo);
+    }
+  }
+  flush_tile<ORDER, RT>(Jt, io.Jw, io.Tw, c.nc, c.split);
 }
 
 template <int ORDER>
@@ -873,7 +1047,7 @@ __global__ void __launch_bounds__(1024, 1)
   }
   if (bad) atomicOr(b.err, bad);
   __syncthreads();
-  flush_tile<ORDER, RT>(Jt, PSEL(b.J1, par), b.Jtot + par, c.nc);
+  flush_tile<ORDER, RT>(Jt, PSEL(b.J1, par), b.Jtot + par, c.nc, c.split);
 }
 
 // Charge of the markers for the initial Poisson solve: the integer weights
@@ -1126,11 +1300,16 @@ void dispatch_mix(const Es1dMixConst &c, F f) {
   using R1 = std::integral_constant<int, 1>;
   using R16 = std::integral_constant<int, 16>;
   using R32 = std::integral_constant<int, 32>;
+  using G0 = std::false_type;
+  using G1 = std::true_type;
+  // the FP64 correction for every marker (gamma64) is built for the unsorted mode
   auto go = [&](auto O, auto S) {
-    if (c.mode == 0 && c.wide) f(O, S, M0(), R32(), R16());
-    if (c.mode == 0 && !c.wide) f(O, S, M0(), R1(), R1());
-    if (c.mode == 1) f(O, S, M1(), R1(), R1());
-    if (c.mode == 2) f(O, S, M2(), R1(), R1());
+    if (c.mode == 0 && c.wide && !c.gamma64) f(O, S, M0(), R32(), R16(), G0());
+    if (c.mode == 0 && c.wide && c.gamma64) f(O, S, M0(), R32(), R16(), G1());
+    if (c.mode == 0 && !c.wide && !c.gamma64) f(O, S, M0(), R1(), R1(), G0());
+    if (c.mode == 0 && !c.wide && c.gamma64) f(O, S, M0(), R1(), R1(), G1());
+    if (c.mode == 1) f(O, S, M1(), R1(), R1(), G0());
+    if (c.mode == 2) f(O, S, M2(), R1(), R1(), G0());
   };
   if (c.order == 1 && c.scheme == 1) go(I1(), I1());
   if (c.order == 1 && c.scheme == 2) go(I1(), I2());
@@ -1147,18 +1326,43 @@ size_t smem_c(const Es1dMixConst &c) {
 size_t smem_e(const Es1dMixConst &c) {
   return npad_host(c) * (8 * tile_copies(c) + 8 * table_copies(c)) + (c.mode == 2 ? 8 * c.nc : 0);
 }
+// the fused ESEC1 pass: the tile, the float-pair table and an FP32 table with
+// half the copies (the three fit 227 KB at 512 nodes)
+int fused_table_copies(const Es1dMixConst &c) { return c.wide ? 8 : 1; }
+size_t smem_ec(const Es1dMixConst &c) {
+  return npad_host(c) * (8 * tile_copies(c) + 8 * table_copies(c) + 4 * fused_table_copies(c));
+}
+
+template <typename F>
+void dispatch_fused(const Es1dMixConst &c, F f) {
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  using R1 = std::integral_constant<int, 1>;
+  using R8 = std::integral_constant<int, 8>;
+  using R16 = std::integral_constant<int, 16>;
+  using R32 = std::integral_constant<int, 32>;
+  auto go = [&](auto O) {
+    if (c.wide)
+      f(O, R32(), R16(), R8());
+    else
+      f(O, R1(), R1(), R1());
+  };
+  if (c.order == 1) go(I1());
+  if (c.order == 2) go(I2());
+}
 
 }  // namespace
 
 cudaError_t es1d_mix_prepare(const Es1dMixConst &c) {
   cudaError_t e = cudaSuccess;
-  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE) {
+  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE, auto G) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
     constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
+    constexpr bool G64 = decltype(G)::value;
     e = cudaFuncSetAttribute(mix_pass_c_kernel<ORDER, SCHEME, MODE, NT, NE>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c(c));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE>,
+      e = cudaFuncSetAttribute(mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE, G64>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e(c));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mix_deposit_initial_kernel<ORDER>,
@@ -1171,6 +1375,12 @@ cudaError_t es1d_mix_prepare(const Es1dMixConst &c) {
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(2 * 32 * 4 * npad_host(c)));
   });
+  if (e == cudaSuccess && c.scheme == 1 && c.mode == 0)
+    dispatch_fused(c, [&](auto O, auto RT, auto RE, auto RE1) {
+      e = cudaFuncSetAttribute(mix_pass_ec_kernel<decltype(O)::value, decltype(RT)::value,
+                                                  decltype(RE)::value, decltype(RE1)::value>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ec(c));
+    });
   return e;
 }
 
@@ -1196,7 +1406,7 @@ void launch_dependent(void (*kern)(P...), LaunchShape ls, size_t smem, cudaStrea
 void es1d_mix_pass_c(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_index, int slot,
                      LaunchShape ls, cudaStream_t st) {
   int par = (int)(step_index & 1);
-  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE) {
+  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE, auto) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
     constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
     launch_dependent(mix_pass_c_kernel<ORDER, SCHEME, MODE, NT, NE>, ls, smem_c(c), st, c, b, par,
@@ -1207,11 +1417,21 @@ void es1d_mix_pass_c(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_i
 void es1d_mix_pass_e(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_index, int slot,
                      LaunchShape ls, cudaStream_t st) {
   int par = (int)(step_index & 1);
-  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE) {
+  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE, auto G) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
     constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
-    launch_dependent(mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE>, ls, smem_e(c), st, c, b, par,
-                     slot);
+    launch_dependent(mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE, decltype(G)::value>, ls,
+                     smem_e(c), st, c, b, par, slot);
+  });
+}
+
+void es1d_mix_pass_ec(const Es1dMixConst &c, const Es1dMixBufs &b, const RingIO &io,
+                      int64_t step_index, int slot, LaunchShape ls, cudaStream_t st) {
+  const int par = (int)(step_index & 1);
+  dispatch_fused(c, [&](auto O, auto RT, auto RE, auto RE1) {
+    launch_dependent(mix_pass_ec_kernel<decltype(O)::value, decltype(RT)::value,
+                                        decltype(RE)::value, decltype(RE1)::value>,
+                     ls, smem_ec(c), st, c, b, io, par, slot, slot - 1, ls.grid);
   });
 }
 

@@ -108,17 +108,21 @@ __device__ __forceinline__ void shape_mix_pair(uint32_t X0, uint32_t X1, int nc,
   }
 }
 
-// The two tile counters' shares of round(V s / 2^r), r in [17, 31] (rnd =
-// 2^(r-1)): bits [r, r + 16) of P = V s + rnd (unsigned) and P >> (r + 16)
-// (signed); a node's value is (signed share) 2^16 + (unsigned share).
+// The two tile counters' shares of round(V s / 2^r) (rnd = 2^(r-1)) with a
+// low counter of b bits: bits [r, r + b) of P = V s + rnd (unsigned) and
+// P >> (r + b) (signed); a node's value is (signed share) 2^b + (unsigned
+// share).  Needs r <= 31 and r + b >= 32 (the signed share comes from the high
+// word of P alone).
 struct SplitTerm {
   unsigned lo;
   int hi;
 };
-__device__ __forceinline__ SplitTerm split_term(int V, int s, int rshift, long long rnd) {
+__device__ __forceinline__ SplitTerm split_term(int V, int s, int rshift, long long rnd,
+                                                unsigned lomask, int hishift) {
+  // lomask = 2^b - 1, hishift = r + b - 32
   const long long P = (long long)V * (long long)s + rnd;
   const unsigned plo = (unsigned)P, phi = (unsigned)(P >> 32);
-  return {__funnelshift_r(plo, phi, rshift) & 0xFFFFu, (int)phi >> (rshift - 16)};
+  return {__funnelshift_r(plo, phi, rshift) & lomask, (int)phi >> hishift};
 }
 
 // 16-byte asynchronous global -> shared copy (L2 only), its commit and the
@@ -179,6 +183,34 @@ __device__ __forceinline__ float div_rcp_residual(float a, float b) {
   const float q0 = __fmul_rn(a, r);
   const float e = __fmaf_rn(-q0, b, a);
   return __fmaf_rn(e, r, q0);
+}
+
+// The correction of Eq. opt_solution in FP64, shared by the mixed forms.  With
+// R = |v^n|^2 + 2 v* . (v^dag - v^n) and Delta = v^dag - v^n, R - |v^dag|^2 =
+// 2a, a = sum_i Delta_i b_i, b_i = V*_i - v^n_i - Delta_i / 2.  bracket_fp64
+// forms b_i from its exact pieces (V*_i - ih an integer, fr = vh - ih, vl, and
+// the float pair Delta_i), so a and t = 2a / |v^dag|^2 keep FP64's relative
+// precision however small they are.
+__device__ __forceinline__ double bracket_fp64(float vh, float vl, int Vs, ff D) {
+  const int ih = __float2int_rn(vh);
+  const double fr = (double)__fsub_rn(vh, __int2float_rn(ih));
+  return (((double)(Vs - ih) - 0.5 * (double)D.hi) - fr) - (double)vl - 0.5 * (double)D.lo;
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// Gamma - 1 = t / (1 + sqrt(1 + t)), t = 2a / v2 (v2 = |v^dag|^2), in FP64.
+// Returns false for the fallback of Sec. 3.2: R < 0 (t < -1) or v^dag = 0 (t
+// not finite); R = 0 gives Gamma = 0.
+__device__ __forceinline__ bool gamma_minus_one_fp64(double a, double v2, double &g) {
+  const double t = 2.0 * a / v2;
+  if (!(t >= -1.0 && t < 1e300)) return false;
+  g = t / (1.0 + sqrt(1.0 + t));
+  return true;
+}
+
+// v^dag_i + g v^dag_i: the product rounded once in FP64, added as a float pair
+__device__ __forceinline__ ff scale_by_gamma_fp64(ff vd, double g) {
+  return ff_add(vd, ff_from_double(g * ff_to_double(vd)));
 }
 
 }  // namespace

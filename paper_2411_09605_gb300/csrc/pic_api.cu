@@ -41,7 +41,7 @@ int fail(int code, const char *fmt, ...) {
 
 constexpr int kStepsCap = 1024;  // per-step stats slots per chunk of pic_step
 constexpr int kXferChunks = 8;   // pieces of a pipelined host transfer of the markers
-constexpr int kProfKinds = 8;    // 0 pass C, 1 pass E, 2 stats finalize, 3 sort, 4 field
+constexpr int kProfKinds = 8;    // 0 pass C, 1 pass E, 2 stats finalize, 3 sort, 4 field, 5 fused ESEC1 pass
 
 // ids[p] = p for one species' slots (marker ids after pic_set_particles).
 __global__ void iota_ids_kernel(int64_t *ids, int64_t n) {
@@ -120,6 +120,11 @@ struct pic_handle {
   uint32_t *sort_hist = nullptr;
   int sort_blocks = 0;
   int nsm = 0;
+  // fused ESEC1 (mixed, unsorted): pass C of the next step already ran (its V*
+  // and current are in place); the energy partials alternate between two buffers
+  bool fused = false, primed = false;
+  double *ke_alt = nullptr, *we_alt = nullptr;
+  long long *jtot_base = nullptr;  // [8]; bm.Jtot = jtot_base + 4
   int64_t *ids = nullptr;
   // reverse mode (pic_grad_forward / pic_grad_backward), FP64 1D form
   struct Grad {
@@ -132,6 +137,16 @@ struct pic_handle {
     double *mk = nullptr;     // [5][N] x_bar, v_bar, w_bar and marker scratch
     size_t ckpt_cap = 0, seg_cap = 0;
   } grad;
+  // charge diagnostics (pic_charge), allocated on first use
+  struct Diag {
+    double *rho = nullptr;      // [nodes] charge density
+    double2 *tw = nullptr;      // [nc] exp(2 pi i t / nc) (1D)
+    double2 *rm = nullptr, *pm = nullptr;  // [(nc - 1) / 2] modes of r and rho (1D)
+    double *r = nullptr;        // [nodes] residual of Gauss's law
+    double *part = nullptr;     // [3 x blocks] block partials; weight sums
+    long long *cnt = nullptr;   // [nc] integer charge of the mixed 1D form
+    int blocks = 0;
+  } diag;
   std::vector<void *> allocs;
 
   template <typename T>
@@ -391,6 +406,7 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   m.hround = 1 << (m.kv - 1);
   m.cxk = std::ldexp(cx, m.kv);
   m.mode = h->cfg.sort_period == 1 ? 2 : (h->cfg.sort_period > 1 ? 1 : 0);
+  m.gamma64 = h->cfg.gamma_fp64;
   m.wide = m.mode == 0 && c.nc <= kWideMaxNodes;
   const int64_t ngroups = (h->N + 3) / 4;
   if (m.wide) {
@@ -402,35 +418,50 @@ int init_mixed(pic_handle *h, bool solve_e0) {
     h->lmix = h->ls;
   }
   // Terms round(V* s / 2^r) are below 2^T = 2^(54 - r).  At most pcnt markers
-  // add into one tile copy of a block; its split counters need pcnt 2^16 <
-  // 2^32 (low halves) and pcnt 2^(T-16) < 2^31 (signed rest), so T = 47 -
-  // ceil(log2 pcnt); the int64 grid sums need N 2^T < 2^63.  pcnt is the
-  // markers of a 512-thread block of the single-copy launch (at least 2048);
-  // a copy of the wide tile (4 markers per trip from each of 32 threads) is
-  // held to the same count, and one r for every mode keeps the results
-  // independent of the marker order.
-  const int64_t threads = (int64_t)h->ls.grid * 512;
-  const int64_t trips = (ngroups + threads - 1) / threads;
-  const int64_t pcnt = std::max<int64_t>(1, trips * 512 * 4);
-  if (m.wide) {
-    const int64_t wthreads = (int64_t)h->lmix.grid * 1024;
-    const int64_t wtrips = (ngroups + wthreads - 1) / wthreads;
-    if (wtrips * 128 > pcnt) {
-      const int64_t grid = (ngroups * 128 + pcnt * 1024 - 1) / (pcnt * 1024);
-      h->lmix.grid = (int)std::max<int64_t>(h->lmix.grid, grid);
+  // add into one tile copy of a block in a launch.  Its split counters hold the
+  // low b = 32 - lg bits of each term (lg = ceil(log2 pcnt): pcnt 2^b <= 2^32)
+  // and the signed rest (pcnt 2^(T-b) <= 2^31), so T <= 63 - 2 lg; the signed
+  // share comes from the high word of V* s (r + b >= 32: T <= 22 + b); the
+  // sorted modes' warp sums take 4 terms a lane in 20-bit halves (T <= 44);
+  // the int64 grid sums need N 2^T < 2^62.  Every launch of a handle keeps to
+  // the same pcnt: on grids of up to kWideMaxNodes nodes 2048 (the wide
+  // launch has 32 copies and enough blocks; the batched launch at most 16
+  // trips of 128 markers a copy; the sorted modes' single-copy launch one trip
+  // of 2048 markers a block), on larger grids the markers of a 512-thread
+  // block of the single-copy launch.  One r and b for every mode keep the
+  // results independent of the marker order.
+  int64_t pcnt;
+  if (c.nc <= kWideMaxNodes) {
+    pcnt = 2048;
+    if (m.wide) {
+      const int64_t wthreads = (int64_t)h->lmix.grid * 1024;
+      const int64_t wtrips = (ngroups + wthreads - 1) / wthreads;
+      if (wtrips * 128 > pcnt) {
+        const int64_t grid = (ngroups * 128 + pcnt * 1024 - 1) / (pcnt * 1024);
+        h->lmix.grid = (int)std::max<int64_t>(h->lmix.grid, grid);
+      }
     }
+  } else {
+    const int64_t threads = (int64_t)h->ls.grid * 512;
+    const int64_t trips = (ngroups + threads - 1) / threads;
+    pcnt = std::max<int64_t>(2048, trips * 512 * 4);
   }
+  if (!m.wide && h->lmix.grid * (int64_t)2048 < 4 * ngroups && c.nc <= kWideMaxNodes)
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: internal launch size for the sorted modes");
   int lg = 0;
   while (((int64_t)1 << lg) < pcnt) lg++;
-  int T = std::min(37, 47 - lg);
+  m.split = 32 - lg;
+  int T = std::min(std::min(63 - 2 * lg, 22 + m.split), 44);
   int bitlen = 0;
   while (bitlen < 62 && ((int64_t)1 << bitlen) <= h->N) bitlen++;
   T = std::min(T, 62 - bitlen);
   m.rshift = 54 - T;
-  if (m.rshift < 17 || m.rshift > 31)
-    return fail(PIC_ERR_UNSUPPORTED, "pic_init: %lld markers need a deposit shift of %d (17..31)",
+  if (m.rshift > 31 || m.rshift + m.split < 32)
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: %lld markers need a deposit shift of %d",
                 (long long)h->N, m.rshift);
   m.rnd = 1ll << (m.rshift - 1);
+  m.lomask = (1u << m.split) - 1u;
+  m.hishift = m.rshift + m.split - 32;
   m.jscale = S.q * S.w0 * std::ldexp(1.0, m.rshift) / (c.h * m.cxk * 8388608.0);
   m.ke_scale = 0.5 * S.m * S.w0 / (m.cxk * m.cxk);
   m.e_scale = 0.5 * c.dt * S.q / S.m * m.cxk;
@@ -461,8 +492,16 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   bm.fallback = b.fallback;
   bm.te = b.te;
   bm.we = b.we;
-  if ((rc = h->alloc(&bm.Jtot, 4))) return rc;
-  CUDA_TRY(cudaMemsetAsync(bm.Jtot, 0, sizeof(long long) * 4, h->st));
+  // grid totals: [4] for J1[0], J1[1], J2[0], J2[1], with room on either side
+  // (a fused ESEC1 step addresses the totals of its three current buffers)
+  if ((rc = h->alloc(&h->jtot_base, 8))) return rc;
+  CUDA_TRY(cudaMemsetAsync(h->jtot_base, 0, sizeof(long long) * 8, h->st));
+  bm.Jtot = h->jtot_base + 4;
+  h->fused = m.scheme == 1 && m.mode == 0 && !h->cfg.separate_passes;
+  h->primed = false;
+  if (h->fused && ((rc = h->alloc(&h->ke_alt, (size_t)h->ls.grid)) ||
+                   (rc = h->alloc(&h->we_alt, (size_t)h->ls.grid))))
+    return rc;
   if ((rc = h->alloc(&bm.we_part, (size_t)h->ls.grid))) return rc;
   CUDA_TRY(cudaMemsetAsync(bm.we_part, 0, sizeof(double) * h->ls.grid, h->st));
   bm.err = b.err;
@@ -653,7 +692,8 @@ int restart_es1d(pic_handle *h, bool particles_changed) {
       CUDA_TRY(cudaMemsetAsync(bm.J1[k], 0, sizeof(long long) * h->cm.nc * kJStride, h->st));
       CUDA_TRY(cudaMemsetAsync(bm.J2[k], 0, sizeof(long long) * h->cm.nc * kJStride, h->st));
     }
-    CUDA_TRY(cudaMemsetAsync(bm.Jtot, 0, sizeof(long long) * 4, h->st));
+    CUDA_TRY(cudaMemsetAsync(h->jtot_base, 0, sizeof(long long) * 8, h->st));
+    h->primed = false;
     // the FP64 staging arrays hold the new markers only after pic_set_particles
     if (particles_changed) es1d_mix_from_fp64(h->cm, b.x, b.v, bm, h->ls, h->st);
     es1d_mix_set_ek(h->cm, bm, par, h->st);
@@ -1167,6 +1207,14 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
                                      "the Ampere solver");
   if (cfg->charge_conserving != 0 && cfg->charge_conserving != 1)
     return fail(PIC_ERR_ARG, "pic_init: charge_conserving must be 0 or 1");
+  if (cfg->gamma_fp64 != 0 && cfg->gamma_fp64 != 1)
+    return fail(PIC_ERR_ARG, "pic_init: gamma_fp64 must be 0 or 1");
+  if (cfg->separate_passes != 0 && cfg->separate_passes != 1)
+    return fail(PIC_ERR_ARG, "pic_init: separate_passes must be 0 or 1");
+  if (cfg->gamma_fp64 && cfg->precision == PIC_PREC_MIXED &&
+      (cfg->solver != PIC_SOLVER_AMPERE_ES || cfg->sort_period != 0))
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: gamma_fp64 is built for the mixed form of the "
+                                     "Ampere solver with sort_period 0");
   if (cfg->charge_conserving &&
       (cfg->solver != PIC_SOLVER_YEE_LEAPFROG || cfg->precision != PIC_PREC_FP64 ||
        cfg->shape_order != 1))
@@ -1263,6 +1311,11 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
     // the bound the split integer tile is sized for
     const int64_t need = ((N + 3) / 4 + 512 * 16 - 1) / (512 * 16);
     h->ls.grid = (int)std::max<int64_t>(h->ls.grid, need);
+    // the sorted 1D modes on grids of up to kWideMaxNodes nodes: one trip of
+    // 2048 markers per 512-thread block (the tile bound of that grid size)
+    if (cfg->solver == PIC_SOLVER_AMPERE_ES && cfg->sort_period > 0 &&
+        cfg->grid.n[0] <= kWideMaxNodes)
+      h->ls.grid = (int)std::max<int64_t>(h->ls.grid, ((N + 3) / 4 + 511) / 512);
   }
   h->nsm = nsm;
   h->em = cfg->solver == PIC_SOLVER_YEE_LEAPFROG;
@@ -1348,6 +1401,38 @@ int pic_step_async(pic_handle *h, int nsteps) {
       if (h->cm.mode == 1 && h->steps_done > 0 && h->steps_done % h->cfg.sort_period == 0) {
         int rc = sort_mixed(h);
         if (rc) return rc;
+      }
+      if (h->fused) {
+        // ESEC1 in one launch per step.  The currents rotate through J2[0],
+        // J2[1], J1[0] (ESEC1 has no j^{n,*}): step n reads buffer n mod 3.
+        Es1dMixBufs &bm = h->bm;
+        long long *ring[3] = {bm.J2[0], bm.J2[1], bm.J1[0]};
+        long long *tot[3] = {bm.Jtot + 2, bm.Jtot + 3, bm.Jtot + 0};
+        const int64_t n = h->steps_done;
+        const int r0 = (int)(n % 3), r1 = (int)((n + 1) % 3), r2 = (int)((n + 2) % 3);
+        if (!h->primed) {
+          // pass C of step n alone, depositing into buffer n mod 3
+          Es1dMixBufs bp = bm;
+          const int par = (int)(n & 1);
+          if (par) bp.J2[1] = ring[r0]; else bp.J2[0] = ring[r0];
+          bp.Jtot = tot[r0] - 2 - par;
+          CUDA_TRY(h->timed_launch(0, [&] {
+            es1d_mix_pass_c(h->cm, bp, n, h->pending, h->lmix, h->st);
+          }));
+          h->launches += 1;
+          h->primed = true;
+        }
+        const RingIO io{ring[r0], tot[r0], ring[r1], tot[r1], ring[r2], tot[r2],
+                        bm.ke_part, bm.we_part, h->ke_alt, h->we_alt};
+        CUDA_TRY(h->timed_launch(5, [&] {
+          es1d_mix_pass_ec(h->cm, bm, io, n, h->pending, h->lmix, h->st);
+        }));
+        std::swap(bm.ke_part, h->ke_alt);
+        std::swap(bm.we_part, h->we_alt);
+        h->launches += 1;
+        h->steps_done++;
+        h->pending++;
+        continue;
       }
       CUDA_TRY(h->timed_launch(0, [&] {
         es1d_mix_pass_c(h->cm, h->bm, h->steps_done, h->pending, h->lmix, h->st);
@@ -1869,6 +1954,131 @@ int pic_grad_backward(pic_handle *h, const double *Ebar, const double *xbar, con
   return check_flags(h, "pic_grad_backward");
 }
 
+// Sum over the species of q sum_p w_p (uniform species: q w0 n; weighted ones
+// through a device reduction of their weights).
+static int markers_charge(pic_handle *h, const double *w, double *Q) {
+  double q = 0.0;
+  for (int s = 0; s < h->nsp; s++) {
+    const SpeciesInfo &S = h->sp[s];
+    if (!S.weighted || !w) {
+      q += S.q * S.w0 * (double)S.n;
+      continue;
+    }
+    const int nb = std::max(1, std::min(h->diag.blocks, (int)((S.n + 255) / 256)));
+    diag_sum_range(w + S.offset, S.n, h->diag.part, nb, h->st);
+    CUDA_TRY(cudaGetLastError());
+    std::vector<double> part(nb);
+    CUDA_TRY(cudaMemcpyAsync(part.data(), h->diag.part, sizeof(double) * nb,
+                             cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    double sw = 0.0;
+    for (double v : part) sw += v;
+    q += S.q * sw;
+  }
+  *Q = q;
+  return PIC_OK;
+}
+
+int pic_charge(pic_handle *h, double *Q_markers, double *Q_grid, double *gauss_l2, double *rho_l2,
+               double *residual) {
+  if (!h) return fail(PIC_ERR_ARG, "pic_charge: NULL handle");
+  if (h->stdp || h->em1)
+    return fail(PIC_ERR_UNSUPPORTED, "pic_charge: built for the Ampere and Yee solvers");
+  int rc;
+  const int nodes = h->em ? h->ce.nx * h->ce.ny : h->c1.nc;
+  auto &D = h->diag;
+  if (!D.rho) {
+    D.blocks = std::max(diag_blocks(nodes), 1024);
+    if ((rc = h->alloc(&D.rho, (size_t)nodes)) || (rc = h->alloc(&D.r, (size_t)nodes)) ||
+        (rc = h->alloc(&D.part, 3 * (size_t)D.blocks)))
+      return rc;
+    if (!h->em) {
+      const int nc = h->c1.nc, M = std::max(1, (nc - 1) / 2);
+      if ((rc = h->alloc(&D.tw, (size_t)nc)) || (rc = h->alloc(&D.rm, (size_t)M)) ||
+          (rc = h->alloc(&D.pm, (size_t)M)) || (rc = h->alloc(&D.cnt, (size_t)nc)))
+        return rc;
+      std::vector<double2> tw(nc);
+      const double twopi = 6.283185307179586476925286766559;
+      for (int t = 0; t < nc; t++) tw[t] = make_double2(cos(twopi * t / nc), sin(twopi * t / nc));
+      CUDA_TRY(cudaMemcpyAsync(D.tw, tw.data(), sizeof(double2) * nc, cudaMemcpyHostToDevice, h->st));
+    }
+  }
+  double qm = 0.0, area = 0.0, mean = 0.0;
+  const double *E = nullptr;
+  if (h->em) {
+    const Em2dConst &c = h->ce;
+    if (h->mixed) {
+      em2dm_to_fp64(h->cme, h->bme, h->be, h->lp, h->st);
+      CUDA_TRY(cudaGetLastError());
+    }
+    if ((rc = markers_charge(h, h->be.w, &qm))) return rc;
+    area = (c.Lx / c.nx) * (c.Ly / c.ny);
+    mean = qm / (c.Lx * c.Ly);
+    CUDA_TRY(cudaMemsetAsync(D.rho, 0, sizeof(double) * nodes, h->st));
+    diag_em2d_charge(c, h->be.x, h->be.y, h->be.w, D.rho, h->lp, h->st);
+    diag_em2d_gauss(c, h->be.E, D.rho, mean, D.r, D.part, h->st);
+  } else {
+    const Es1dConst &c = h->c1;
+    area = c.h;
+    if ((rc = markers_charge(h, h->b1.w, &qm))) return rc;
+    if (h->mixed) {
+      // the mixed form's own charge: its quantised weights summed exactly
+      CUDA_TRY(cudaMemsetAsync(D.cnt, 0, sizeof(long long) * c.nc, h->st));
+      es1d_mix_charge(h->cm, h->bm, D.cnt, h->ls, h->st);
+      const SpeciesInfo &S = h->sp[0];
+      diag_rho_from_counts(D.cnt, c.nc, S.q * S.w0 / c.h * std::ldexp(1.0, -23), D.rho, h->st);
+    } else {
+      CUDA_TRY(cudaMemsetAsync(D.rho, 0, sizeof(double) * nodes, h->st));
+      es1d_fp64_charge(c, h->b1.x, h->b1.w, D.rho, h->ls, h->st);
+    }
+    E = h->b1.E[h->steps_done & 1];
+    diag_gauss1d(E, D.rho, c.nc, c.L, D.tw, D.rm, D.pm, D.r, D.part, h->st);
+  }
+  CUDA_TRY(cudaGetLastError());
+  const int nb = diag_blocks(nodes);
+  std::vector<double> part(3 * (size_t)nb);
+  CUDA_TRY(cudaMemcpyAsync(part.data(), D.part, sizeof(double) * part.size(),
+                           cudaMemcpyDeviceToHost, h->st));
+  if (residual)
+    CUDA_TRY(cudaMemcpyAsync(residual, D.r, sizeof(double) * nodes, cudaMemcpyDefault, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  double r2 = 0.0, p2 = 0.0, rs = 0.0;
+  for (int b = 0; b < nb; b++) {
+    r2 += part[3 * b];
+    p2 += part[3 * b + 1];
+    rs += part[3 * b + 2];
+  }
+  if (Q_markers) *Q_markers = qm;
+  if (Q_grid) *Q_grid = area * rs;
+  if (gauss_l2) *gauss_l2 = std::sqrt(area * r2);
+  if (rho_l2) *rho_l2 = std::sqrt(area * p2);
+  return PIC_OK;
+}
+
+int pic_mixed_resolution(pic_handle *h, double *dx, double *dv, int *deposit_bits) {
+  if (!h) return fail(PIC_ERR_ARG, "pic_mixed_resolution: NULL handle");
+  if (!h->mixed) return fail(PIC_ERR_UNSUPPORTED, "pic_mixed_resolution: not a mixed-form handle");
+  double L, cxk;
+  int T;
+  if (h->em) {
+    L = h->cme.L;
+    cxk = h->cme.cxk;
+    T = 77 - h->cme.rshift;   // V* (31 bits) times two 23-bit weights
+  } else if (h->em1) {
+    L = h->c1m.L;
+    cxk = h->c1m.cxk;
+    T = 54 - h->c1m.rshift;
+  } else {
+    L = h->cm.L;
+    cxk = h->cm.cxk;
+    T = 54 - h->cm.rshift;
+  }
+  if (dx) *dx = L / 4294967296.0;
+  if (dv) *dv = 1.0 / cxk;
+  if (deposit_bits) *deposit_bits = T;
+  return PIC_OK;
+}
+
 int pic_step_count(pic_handle *h, int64_t *steps) {
   if (!h || !steps) return fail(PIC_ERR_ARG, "pic_step_count: bad arguments");
   *steps = h->steps_done;
@@ -1971,10 +2181,10 @@ int pic_batch_init(const pic_config *cfgs, const pic_species *species, int nruns
     const pic_config &c = cfgs[r];
     if (c.solver != PIC_SOLVER_AMPERE_ES || c.precision != PIC_PREC_MIXED || c.sort_period != 0 ||
         c.grid.n[0] > kWideMaxNodes || c.scheme != cfgs[0].scheme ||
-        c.cuda_stream != cfgs[0].cuda_stream)
+        c.cuda_stream != cfgs[0].cuda_stream || c.gamma_fp64 != 0)
       return fail(PIC_ERR_UNSUPPORTED,
                   "pic_batch_init: run %d: batches take unsorted mixed-form 1D runs with at most "
-                  "%d nodes, one scheme and one stream", r, kWideMaxNodes);
+                  "%d nodes, one scheme, one stream and gamma_fp64 = 0", r, kWideMaxNodes);
   }
   pic_batch *b = new pic_batch();
   b->scheme = cfgs[0].scheme;

@@ -55,10 +55,14 @@ struct Es1dMixConst {
   int remove_mean;
   int gamma_on;
   int rshift;          // deposit term = round(V* s_k / 2^rshift)
+  int split;           // bits b of the low counter of the split current tiles
+  unsigned lomask;     // 2^b - 1
+  int hishift;         // rshift + b - 32: the signed share from the high word
   int kv;              // one V unit = 2^-kv position units per half step
   int mode;            // 0 unsorted, 1 periodic counting sort, 2 sorted on write every step
   int wide;            // unsorted with nc <= kWideMaxNodes: per-lane tile copies, 1024-thread blocks
   int hround;          // 2^(kv - 1), kv >= 1
+  int gamma64;         // 1: the correction in FP64 for every marker (unsorted mode)
   long long rnd;       // 2^(rshift - 1)
   int64_t n;
   double L, h, dt;
@@ -85,6 +89,19 @@ constexpr int kWideMaxNodes = 512;
 // Mixed-form integer node sums J1, J2 hold node i at [i * kJStride]: one node
 // per 128-byte line, so the blocks' global atomics spread over the L2 slices.
 constexpr int kJStride = 16;
+
+// Buffers of one fused ESEC1 launch (es1d_mix_pass_ec): the current sums and
+// grid total it reads (j^{*,n+1/2}), the ones it deposits (j^{*,n+3/2}) and
+// the ones it clears (read by the previous launch, written by the next), and
+// the block partials of the previous step's energy (for its TE) and of this
+// step's.
+struct RingIO {
+  const long long *Jr, *Tr;
+  long long *Jw, *Tw;
+  long long *Jc, *Tc;
+  const double *ke_prev, *we_prev;
+  double *ke_out, *we_out;
+};
 
 struct Es1dMixBufs {
   uint32_t *X;              // [N padded to 4] positions, x = X L / 2^32
@@ -446,6 +463,9 @@ void es1d_mix_pass_e(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_i
                      LaunchShape ls, cudaStream_t st);
 void es1d_mix_deposit_initial(const Es1dMixConst &c, const Es1dMixBufs &b, int parity,
                               LaunchShape ls, cudaStream_t st);
+// ESEC1, unsorted: pass E of step step_index fused with pass C of the next step
+void es1d_mix_pass_ec(const Es1dMixConst &c, const Es1dMixBufs &b, const RingIO &io,
+                      int64_t step_index, int slot, LaunchShape ls, cudaStream_t st);
 void es1d_mix_finalize(const Es1dMixConst &c, const Es1dMixBufs &b, int slot, int nblocks,
                        cudaStream_t st);
 void es1d_mix_set_ek(const Es1dMixConst &c, const Es1dMixBufs &b, int parity, cudaStream_t st);
@@ -486,5 +506,18 @@ void es1d_mix_fused_scan(const Es1dMixConst &c, const Es1dMixBufs &b, int G, cud
 cudaError_t es1d_mix_sort(const Es1dMixConst &c, const Es1dMixBufs &src, const Es1dMixBufs &dst,
                           const int64_t *ids_in, int64_t *ids_out, uint32_t *H, int G,
                           cudaStream_t st);
+
+// charge diagnostics (charge_diag.cu): 1D spectral Gauss residual and the 2D
+// Yee one; part receives 3 doubles per block (sum r^2, sum rhot^2, sum rho)
+int diag_blocks(int nodes);
+void diag_rho_from_counts(const long long *cnt, int nc, double scale, double *rho,
+                          cudaStream_t st);
+void diag_gauss1d(const double *E, const double *rho, int nc, double L, const double2 *tw,
+                  double2 *rm, double2 *pm, double *r, double *part, cudaStream_t st);
+void diag_sum_range(const double *a, int64_t n, double *part, int blocks, cudaStream_t st);
+void diag_em2d_charge(const Em2dConst &c, const double *x, const double *y, const double *w,
+                      double *rho, LaunchShape lp, cudaStream_t st);
+void diag_em2d_gauss(const Em2dConst &c, const double *E, const double *rho, double mean,
+                     double *r, double *part, cudaStream_t st);
 
 }  // namespace pic

@@ -35,7 +35,7 @@ EXPORTS = ["pic_init", "pic_step", "pic_step_async", "pic_read_stats", "pic_laun
            "pic_last_error", "pic_version", "pic_es1d_step_noalloc",
            "pic_batch_init", "pic_batch_step", "pic_batch_set_graph", "pic_batch_read_stats",
            "pic_batch_run", "pic_batch_info", "pic_batch_free", "pic_batch_autotune",
-           "pic_grad_forward", "pic_grad_backward"]
+           "pic_grad_forward", "pic_grad_backward", "pic_mixed_resolution", "pic_charge"]
 
 
 class PicError(RuntimeError):
@@ -60,7 +60,8 @@ class pic_config(C.Structure):
                 ("precision", C.c_int), ("sort_period", C.c_int), ("remove_mean", C.c_int),
                 ("gamma_on", C.c_int), ("ptr_on_device", C.c_int), ("cuda_stream", C.c_void_p),
                 ("skip_ids", C.c_int), ("binomial_passes", C.c_int),
-                ("charge_conserving", C.c_int)]
+                ("charge_conserving", C.c_int), ("gamma_fp64", C.c_int),
+                ("separate_passes", C.c_int)]
 
 
 _lib = None
@@ -90,6 +91,10 @@ def lib() -> C.CDLL:
         L.pic_get_fields.argtypes = [vp, vp, vp]
         L.pic_set_fields.argtypes = [vp, vp, vp]
         L.pic_step_count.argtypes = [vp, i64p]
+        L.pic_mixed_resolution.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                           C.POINTER(C.c_int)]
+        dblp = C.POINTER(C.c_double)
+        L.pic_charge.argtypes = [vp, dblp, dblp, dblp, dblp, vp]
         L.pic_es1d_step_noalloc.argtypes = [C.POINTER(pic_config), C.c_double, C.c_double,
                                              C.c_double, C.c_int64, vp, vp, vp, C.c_int, vp, vp]
         L.pic_grad_forward.argtypes = [vp, C.c_int, C.c_int]
@@ -138,11 +143,13 @@ def _addr(a) -> Optional[int]:
 def make_config(nc, L, dt, order=1, scheme=PIC_SCHEME_ESEC2, precision=PIC_PREC_FP64,
                 solver=PIC_SOLVER_AMPERE_ES, dim_x=1, dim_v=1, ny=0, Ly=0.0, c=1.0,
                 sort_period=0, remove_mean=1, gamma_on=1, ptr_on_device=0, stream=None,
-                skip_ids=0, binomial_passes=0, charge_conserving=0):
+                skip_ids=0, binomial_passes=0, charge_conserving=0, gamma_fp64=0,
+                separate_passes=0):
     g = pic_grid(dim_x, dim_v, (C.c_int64 * 2)(nc, ny), (C.c_double * 2)(L, Ly))
     return pic_config(g, order, dt, c, solver, scheme, precision, sort_period, int(remove_mean),
                       int(gamma_on), int(ptr_on_device), stream, int(skip_ids),
-                      int(binomial_passes), int(charge_conserving))
+                      int(binomial_passes), int(charge_conserving), int(gamma_fp64),
+                      int(separate_passes))
 
 
 def pic_init(cfg: pic_config, species: Sequence[dict], E0=None, B0=None) -> int:
@@ -222,6 +229,22 @@ def pic_set_fields(h: int, E, B=None):
     _check(lib().pic_set_fields(h, _addr(E), _addr(B)))
 
 
+def pic_charge(h: int, residual=None):
+    """Charge diagnostics (see pic.h): dict with Q_markers, Q_grid, gauss_l2,
+    rho_l2; residual (optional array of the grid's nodes) receives r."""
+    q, g, l2, p2 = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    _check(lib().pic_charge(h, C.byref(q), C.byref(g), C.byref(l2), C.byref(p2),
+                            _addr(residual)))
+    return dict(Q_markers=q.value, Q_grid=g.value, gauss_l2=l2.value, rho_l2=p2.value)
+
+
+def pic_mixed_resolution(h: int):
+    """(dx, dv, deposit_bits) of a mixed-form handle (see pic.h)."""
+    dx, dv, T = C.c_double(), C.c_double(), C.c_int()
+    _check(lib().pic_mixed_resolution(h, C.byref(dx), C.byref(dv), C.byref(T)))
+    return dx.value, dv.value, T.value
+
+
 def pic_step_count(h: int) -> int:
     n = C.c_int64()
     _check(lib().pic_step_count(h, C.byref(n)))
@@ -248,14 +271,16 @@ class Simulation:
 
     def __init__(self, prob, scheme=PIC_SCHEME_ESEC2, precision=PIC_PREC_FP64, E0=None,
                  sort_period=0, remove_mean=True, gamma_on=True, stream=None,
-                 solver=PIC_SOLVER_AMPERE_ES, binomial_passes=0):
+                 solver=PIC_SOLVER_AMPERE_ES, binomial_passes=0, gamma_fp64=False,
+                 separate_passes=False):
         """solver PIC_SOLVER_STANDARD_LEAPFROG selects the standard-PIC comparator
         (its particles() then returns v^{n-1/2})."""
         self.prob = prob
         self.cfg = make_config(prob.nc, prob.L, prob.dt, prob.order, scheme, precision,
                                sort_period=sort_period, remove_mean=remove_mean,
                                gamma_on=gamma_on, stream=stream, solver=solver,
-                               binomial_passes=binomial_passes)
+                               binomial_passes=binomial_passes, gamma_fp64=gamma_fp64,
+                               separate_passes=separate_passes)
         self.species = [dict(q=s.q, m=s.m, x=np.ascontiguousarray(s.x, dtype=np.float64),
                              v=np.ascontiguousarray(s.v, dtype=np.float64),
                              w=None if s.w is None else np.ascontiguousarray(s.w, np.float64),

@@ -225,15 +225,20 @@ class Problem2D:
 
 def weibel(nx: int = 128, ny: int = 128, ppc: int = 64, L: float = 12.8, vth_par: float = 0.05,
            t_ratio: float = 10.0, c: float = 1.0, cfl: float = 0.5, steps: int = 4000,
-           order: int = 1, seed: int = 0, quiet: bool = False) -> Problem2D:
+           order: int = 1, seed: int = 0, quiet: bool = False,
+           mirrored: bool = False) -> Problem2D:
     """2D3V Weibel instability: uniform electrons, bi-Maxwellian with vth_par along x
-    and sqrt(t_ratio) vth_par along y and z; dt from c dt sqrt(hx^-2 + hy^-2) = cfl."""
+    and sqrt(t_ratio) vth_par along y and z; dt from c dt sqrt(hx^-2 + hy^-2) = cfl.
+    quiet: positions on a lattice of about ppc points per cell.  mirrored (with
+    quiet): the markers come in eights at one point with the eight sign patterns
+    of one drawn velocity, so no cell carries current at the start."""
     rng = np.random.default_rng(seed)
     n = nx * ny * ppc
     hx, hy = L / nx, L / ny
     dt = cfl / (c * np.sqrt(hx ** -2 + hy ** -2))
     if quiet:
-        side = int(round(np.sqrt(ppc)))
+        per = ppc // 8 if mirrored else ppc
+        side = int(round(np.sqrt(per)))
         gx = (np.arange(nx * side) + 0.5) * (L / (nx * side))
         gy = (np.arange(ny * side) + 0.5) * (L / (ny * side))
         X, Y = np.meshgrid(gx, gy)
@@ -246,6 +251,14 @@ def weibel(nx: int = 128, ny: int = 128, ppc: int = 64, L: float = 12.8, vth_par
     vx = rng.standard_normal(n) * vth_par
     vy = rng.standard_normal(n) * vperp
     vz = rng.standard_normal(n) * vperp
+    if quiet and mirrored:
+        sx, sy, sz = (np.array([(k >> b & 1) * -2 + 1 for k in range(8)], dtype=float)
+                      for b in range(3))
+        x, y = np.repeat(x, 8), np.repeat(y, 8)
+        vx = (vx[:, None] * sx).ravel()
+        vy = (vy[:, None] * sy).ravel()
+        vz = (vz[:, None] * sz).ravel()
+        n = len(x)
     return Problem2D("weibel", nx, ny, L, L, order, dt, c, steps,
                      [Markers2D(-1.0, 1.0, x, y, vx, vy, vz, None, L * L / n)])
 
