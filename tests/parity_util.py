@@ -51,10 +51,11 @@ def gpu_run(prob, scheme=2, steps=10, precision=0, remove_mean=True, gamma_on=Tr
             vs.append(v)
         E = sim.field()
         ke, we, wb, te_now = sim.energy()
+        res = pic.pic_mixed_resolution(sim.h) if precision == 1 else None
     finally:
         sim.close()
     return dict(x=xs, v=vs, E=E, nfb=fb, te=np.concatenate([[te0], te]), E0=E_init,
-                te_now=te_now)
+                te_now=te_now, resolution=res)
 
 
 def periodic_dist(a, b, L):
@@ -72,3 +73,33 @@ def compare(prob, ref, got):
     En = np.linalg.norm(ref["E"]) or 1.0
     out["E"] = np.linalg.norm(ref["E"] - got["E"]) / En
     return out
+
+
+def mixed_bars(ref_v, got_v, pos_err, h, dx, dv, dt, qm, Emax, steps):
+    """The mixed forms against the FP64 oracle after `steps` steps, in units of
+    their own quanta (pic_mixed_resolution: dx = L / 2^32 the position step,
+    dv the velocity of one unit of the integer v*).  Returns the ratios
+    error / bar (each must be <= 1):
+
+    positions: 1e-6 h (the gathers' FP32 weights and tables, relative 2^-23)
+      plus 4 dx per step (x^{n+1/2} and x^{n+1} are rounded to dx, and the
+      rounded v* moves a marker by up to one dx more per step);
+    velocities, marker by marker: 4 dv per step times (1 + kick / |v|), kick =
+      dt |q/m| max|E|.  Each step rounds v* to one unit (+-dv/2) and the
+      fixed-point position perturbs the gathered kick; through Gamma
+      (Eq. opt_solution) a change of v* moves v^{n+1} by about
+      |v^dag - v^n| / |v^dag| times itself, the 1 / |v| growth of slow markers.
+
+    ref_v, got_v: [K][N] velocity components; pos_err: [D][N] periodic
+    position differences; h: cell size (per axis, the smallest is used)."""
+    ref_v = np.atleast_2d(ref_v)
+    got_v = np.atleast_2d(got_v)
+    speed = np.sqrt(np.sum(ref_v ** 2, axis=0))
+    kick = dt * abs(qm) * Emax
+    vbar = 4.0 * steps * dv * (1.0 + kick / np.maximum(speed, 1e-300))
+    verr = np.max(np.abs(got_v - ref_v), axis=0)
+    xbar = 1e-6 * np.min(np.atleast_1d(h)) + 4.0 * steps * dx
+    xerr = np.max(np.abs(np.atleast_2d(pos_err)), axis=0)
+    return {"x": float(np.max(xerr, initial=0.0) / xbar),
+            "v": float(np.max(verr / vbar, initial=0.0)),
+            "x_over_h": float(np.max(xerr, initial=0.0) / np.min(np.atleast_1d(h)))}

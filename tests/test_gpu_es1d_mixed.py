@@ -1,26 +1,28 @@
 """Parity of the mixed-precision 1D1V form with the oracle and with the FP64 form.
 
-The mixed form stores positions as 32-bit fixed point (L / 2^32), v* as a
-fixed-point integer (1 / cxk, cxk = 2^kv dt 2^31 / L), shape weights as
-integers of 2^-23 and gathers #1 in FP32, so its states follow the FP64 oracle
-to about 1e-7 of the scale per step, not to 1e-11.  Bar (derived from those quanta over
-10 steps): positions / L, velocities / max|v| and the field (2-norm, relative)
-within 1e-6 (3e-6 for the field, which integrates the weight quanta of every
-deposit).  Gamma - 1 = t / (1 + sqrt(1 + t)) with t ~ 2 d (v* - v - d/2) / |v^dag|^2 is
-as sensitive to v* as 1 / |v^dag|^2, so for the few markers with |v| below 1% of
-the largest speed a one-unit difference in the fixed-point v* shows up as up to
-1e-4 of max|v|; those are held to 1e-4.  Energy is the quantity it conserves to the FP64 bound: every step
-without an imaginary-Gamma fallback changes TE by round-off only, and runs
-without fallbacks stay within max_n |TE^n - TE^0| / TE^0 <= 1e-11."""
+The mixed form stores positions as 32-bit fixed point (dx = L / 2^32), v* as an
+integer (one unit is dv = 1 / cxk, cxk = 2^kv dt 2^31 / L), shape weights as
+integers of 2^-23 and runs gather #1 in FP32, so its states follow the FP64
+oracle to its quanta, not to 1e-11.  The bars are derived from those quanta
+(pic_mixed_resolution reports dx and dv; tests/parity_util.mixed_bars states
+the derivation): over `steps` steps each marker's position within 1e-6 h +
+4 steps dx, and its velocity within 4 steps dv (1 + kick / |v|), the last
+factor being Gamma's sensitivity to v* (the 1 / |v| growth of slow markers);
+the field (2-norm, relative) within 3e-6, since it integrates the 2^-23 weight
+quanta of every deposit.  Fallback counts equal the oracle's exactly: the
+R < 0 test is taken in FP64 (Sec. 3.2).  Energy is the quantity it conserves
+to the FP64 bound: every step without an imaginary-Gamma fallback changes TE
+by round-off only, and runs without fallbacks stay within
+max_n |TE^n - TE^0| / TE^0 <= 1e-11."""
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2411_09605_gb300 import workloads as W
-from tests.parity_util import compare, gpu_run, oracle_run
+from tests.parity_util import compare, gpu_run, mixed_bars, oracle_run, periodic_dist
 
 pytestmark = pytest.mark.gpu
-TOL = 1e-6
-TOL_E = 3e-6   # the field integrates the 2^-24 weight quanta of every deposit
+TOL_E = 3e-6   # the field integrates the 2^-23 weight quanta of every deposit
 MIXED = 1
 
 
@@ -30,16 +32,19 @@ def _built():
     build.build()
 
 
-def _check(prob, scheme=2, steps=10, fb_slack=0, **kw):
+def _check(prob, scheme=2, steps=10, **kw):
     ref = oracle_run(prob, scheme, steps, **kw)
     got = gpu_run(prob, scheme, steps, precision=MIXED, **kw)
+    dx, dv, _ = got["resolution"]
+    Emax = max(np.max(np.abs(ref["E0"])), np.max(np.abs(ref["E"])))
+    h = prob.L / prob.nc
+    for sref, r_x, g_x, r_v, g_v in zip(prob.species, ref["x"], got["x"], ref["v"], got["v"]):
+        b = mixed_bars(r_v, g_v, periodic_dist(r_x, g_x, prob.L), h, dx, dv, prob.dt,
+                       sref.q / sref.m, Emax, steps)
+        assert b["x"] <= 1.0 and b["v"] <= 1.0, b
     d = compare(prob, ref, got)
-    vmax = max(np.max(np.abs(r)) for r in ref["v"])
-    slow = [np.abs(r) < 0.01 * vmax for r in ref["v"]]
-    d["v"] = max(np.max(np.abs(r - g)[~m], initial=0.0) for r, g, m in zip(ref["v"], got["v"], slow)) / vmax
-    d["v_slow"] = max(np.max(np.abs(r - g)[m], initial=0.0) for r, g, m in zip(ref["v"], got["v"], slow)) / vmax
-    assert d["x"] <= TOL and d["v"] <= TOL and d["E"] <= TOL_E and d["v_slow"] <= 1e-4, d
-    assert np.sum(np.abs(ref["nfb"] - got["nfb"])) <= fb_slack, (ref["nfb"], got["nfb"])
+    assert d["E"] <= TOL_E, d
+    assert np.array_equal(ref["nfb"], got["nfb"]), (ref["nfb"], got["nfb"])
     te = got["te"]
     assert np.max(np.abs(te - te[0])) / te[0] <= 1e-11 or got["nfb"].sum() > 0
     return ref, got
@@ -48,7 +53,7 @@ def _check(prob, scheme=2, steps=10, fb_slack=0, **kw):
 @pytest.mark.parametrize("scheme", [1, 2])
 @pytest.mark.parametrize("order", [1, 2])
 def test_landau_parity_mixed(scheme, order):
-    _check(W.landau(n=20_000, order=order, seed=1), scheme, fb_slack=2 if scheme == 1 else 0)
+    _check(W.landau(n=20_000, order=order, seed=1), scheme)
 
 
 def test_two_stream_ragged_mixed():
@@ -61,11 +66,19 @@ def test_two_stream_full_size_mixed():
 
 
 def test_mixed_follows_fp64_form_full_size():
+    """The two forms of the library on the 2^23-marker two-stream workload, 10 steps:
+    the mixed form follows the FP64 form within the same quanta-derived bars."""
     prob = W.two_stream(seed=3)
     a = gpu_run(prob, 2, 10, precision=0)
     b = gpu_run(prob, 2, 10, precision=MIXED)
-    d = compare(prob, a, b)
-    assert max(d.values()) <= TOL, d
+    dx, dv, _ = b["resolution"]
+    s = prob.species[0]
+    Emax = max(np.max(np.abs(a["E0"])), np.max(np.abs(a["E"])))
+    bars = mixed_bars(a["v"][0], b["v"][0], periodic_dist(a["x"][0], b["x"][0], prob.L),
+                      prob.L / prob.nc, dx, dv, prob.dt, s.q / s.m, Emax, 10)
+    assert bars["x"] <= 1.0 and bars["v"] <= 1.0, bars
+    assert compare(prob, a, b)["E"] <= TOL_E
+    assert np.array_equal(a["nfb"], b["nfb"])
 
 
 def test_mixed_energy_conservation_landau():
@@ -193,3 +206,35 @@ def test_sort_on_write_keeps_key_order():
     assert np.all(np.diff(cells) >= 0)
     key = 2 * cells + (v > 0)
     assert np.mean(np.diff(key) >= 0) > 0.999
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_esec1_fallback_counts_step_by_step(order):
+    """ESEC1 Landau damping (20,000 markers, dt = 0.1), where Gamma is imaginary for a
+    few markers every step.  Each step the GPU starts from the oracle's state
+    (positions rounded to L 2^-32, velocities to float pairs), so the two sides
+    decide the fallback (R < 0, Sec. 3.2) on the same inputs.  The oracle reports
+    every marker's radicand R / |v^dag|^2; on a step whose markers all keep it
+    at least 1e-3 away from zero (far beyond the inputs' rounding) the counts
+    must be equal, and at least 8 of the 10 steps must be of that kind."""
+    from paper_2411_09605_gb300 import pic
+    prob = W.landau(n=20_000, order=order, seed=1)
+    s = prob.species[0]
+    cfg = O.ES1DConfig(nc=prob.nc, L=prob.L, order=order, dt=prob.dt, scheme=1)
+    sp = [O.Species(s.q, s.m, s.x.copy(), s.v.copy(), None, s.w0)]
+    E = O.poisson_e0_1d(cfg, sp)
+    sim = pic.Simulation(prob, scheme=1, precision=MIXED, E0=E)
+    checked, total = 0, 0
+    try:
+        for k in range(10):
+            pic.pic_set_particles(sim.h, 0, sp[0].x.copy(), sp[0].v.copy())
+            pic.pic_set_fields(sim.h, E.copy())
+            fb, _ = sim.step(1)
+            nfb, rad = O.es1d_step_radicand(cfg, sp, E)
+            total += nfb[0]
+            if np.nanmin(np.abs(rad[0])) >= 1e-3:
+                assert fb[0] == nfb[0], (k, fb[0], nfb[0])
+                checked += 1
+    finally:
+        sim.close()
+    assert checked >= 8 and total >= 10, (checked, total)
