@@ -40,6 +40,11 @@ L2_FLUSH_BYTES = 512 << 20          # > 2x the 126.5 MB L2
 ALGO_BYTES = {  # (form, kernel kind) -> bytes per marker
     ("fp64", 0): 24, ("fp64", 1): 40,    # pass C also writes v*, pass E reads it
     ("mixed", 0): 16, ("mixed", 1): 28,
+    ("mixed_g64", 0): 16, ("mixed_g64", 1): 28,   # the mixed form, Gamma in FP64 for every marker
+    # ESEC1, mixed form: one fused launch per step reads and writes X, vh, vl, V*
+    # (32 bytes per particle-step); two launches: 16 + 28 as ESEC2
+    ("mixed_esec1", 0): 16, ("mixed_esec1", 5): 32,
+    ("mixed_esec1_2l", 0): 16, ("mixed_esec1_2l", 1): 28,
     ("standard", 1): 32,     # the comparator's one pass reads and writes x, v
 }
 # The FP64 form is bound by the FP64 pipe (2 thread-instructions per SM and
@@ -51,7 +56,7 @@ FP64_LANES_PER_SM_CLK = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu capture of the current kernels on this workload (2^23 markers); None where
 # the kernel changed since it was taken.
-TRAFFIC = {("mixed", 0): 111117312, ("mixed", 1): 174521600,
+TRAFFIC = {("mixed", 0): 111284224, ("mixed", 1): 178933760,
            ("fp64", 0): None, ("fp64", 1): 304729600, ("standard", 1): 207165440}
 
 
@@ -68,6 +73,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--full-run", action=argparse.BooleanOptionalAction, default=True,
+                    help="also run the workload's whole length per form, untimed, for its "
+                         "energy error and fallbacks")
     ap.add_argument("--sort-period", type=int, default=0,
                     help="cell sort of the mixed form every this many steps (0 = never)")
     ap.add_argument("--weibel2d", action="store_true",
@@ -224,7 +232,9 @@ def time_form(prob, precision_name: str, steps: int, warmup: int, profile_steps:
     """Device-timed throughput of one library form on the resident workload."""
     import torch
     from paper_2411_09605_gb300 import pic
-    prec = pic.PIC_PREC_MIXED if precision_name == "mixed" else pic.PIC_PREC_FP64
+    mixed = precision_name.startswith("mixed")
+    prec = pic.PIC_PREC_MIXED if mixed else pic.PIC_PREC_FP64
+    scheme = pic.PIC_SCHEME_ESEC1 if "esec1" in precision_name else pic.PIC_SCHEME_ESEC2
     s = prob.species[0]
     dev = torch.device("cuda", torch.cuda.current_device())
     x_d = torch.from_numpy(s.x).to(dev)
@@ -232,11 +242,13 @@ def time_form(prob, precision_name: str, steps: int, warmup: int, profile_steps:
     # "standard": the comparison scheme of Sec. 5 (leapfrog Vlasov-Poisson, one
     # binomial filter pass on the charge) on the same workload
     std = precision_name == "standard"
-    cfg = pic.make_config(prob.nc, prob.L, prob.dt, prob.order, pic.PIC_SCHEME_ESEC2, prec,
+    cfg = pic.make_config(prob.nc, prob.L, prob.dt, prob.order, scheme, prec,
                           ptr_on_device=1, stream=stream.cuda_stream,
                           sort_period=sort_period if precision_name == "mixed" else 0,
                           solver=pic.PIC_SOLVER_STANDARD_LEAPFROG if std else
-                          pic.PIC_SOLVER_AMPERE_ES, binomial_passes=1 if std else 0)
+                          pic.PIC_SOLVER_AMPERE_ES, binomial_passes=1 if std else 0,
+                          gamma_fp64=1 if precision_name == "mixed_g64" else 0,
+                          separate_passes=1 if precision_name == "mixed_esec1_2l" else 0)
     torch.cuda.synchronize()
     h = pic.pic_init(cfg, [dict(q=s.q, m=s.m, x=x_d, v=v_d, w=None, w0=s.w0)])
     del x_d, v_d
@@ -277,7 +289,8 @@ def time_form(prob, precision_name: str, steps: int, warmup: int, profile_steps:
             pic.pic_step_async(h, 1)
         pic.pic_read_stats(h)
         kern = {}
-        for kind, name in ((0, "pass_c"), (1, "pass_e"), (2, "finalize"), (3, "sort")):
+        for kind, name in ((0, "pass_c"), (1, "pass_e"), (2, "finalize"), (3, "sort"),
+                           (5, "pass_ec")):
             n, ms = pic.pic_profile(h, kind)
             if n:
                 kern[name] = {"kind": kind, "launches": n, "avg_us": 1e3 * ms / n}
@@ -385,6 +398,34 @@ def cpu_baseline_oracle(markers: int, seed: int, budget_s: float = 10.0, max_ste
                                         "the single-threaded checker build)"}}
 
 
+def full_run(prob, form: str, steps: int):
+    """The workload's whole run, untimed: energy error over the run (max over the
+    steps of |TE^n - TE^0| / TE^0), the largest change of one step without a
+    fallback (relative to TE^0), and the fallbacks (Sec. 5.1)."""
+    from paper_2411_09605_gb300 import pic
+    mixed = form.startswith("mixed")
+    sim = pic.Simulation(prob, scheme=1 if "esec1" in form else 2,
+                         precision=pic.PIC_PREC_MIXED if mixed else pic.PIC_PREC_FP64,
+                         gamma_fp64=form == "mixed_g64")
+    try:
+        te0 = sim.energy()[3]
+        fbs, tes = [], []
+        for k in range(0, steps, 1000):
+            fb, te = sim.step(min(1000, steps - k))
+            fbs.append(fb)
+            tes.append(te)
+    finally:
+        sim.close()
+    fb, te = np.concatenate(fbs), np.concatenate(tes)
+    d = np.abs(np.diff(np.concatenate([[te0], te]))) / abs(te0)
+    first = int(np.argmax(fb > 0)) if fb.any() else -1
+    return {"steps": steps, "max_rel_dTE": float(np.max(np.abs(te - te0)) / abs(te0)),
+            "max_step_dTE_without_fallback": float(np.max(d[fb == 0], initial=0.0)),
+            "fallbacks": int(fb.sum()), "first_fallback_step": first,
+            "max_rel_dTE_before_first_fallback":
+                float(np.max(np.abs(te[:first] - te0)) / abs(te0)) if first > 0 else None}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -453,7 +494,7 @@ def run_ours(args):
         "metric": METRIC, "value": hf["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": hf["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+i32+i64 (energy in f64)" if head == "mixed" else "f64",
+        "dtype": "f32+i32+i64 (energy in f64)" if head.startswith("mixed") else "f64",
         "data": "synthetic (seeded two-stream markers)",
         "config": config_dict(prob, {"form": head, "parallelism": f"replicas{world}",
                                      "sort_period": args.sort_period if head == "mixed" else 0}),
@@ -468,6 +509,10 @@ def run_ours(args):
         t = max_over_ranks(e["s_per_step"], world, dev)
         line["e2e"] = {"value": sum_over_ranks(prob.n_markers, world, dev) / t, "unit": UNIT,
                        "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"]}
+    if rank == 0 and world == 1 and args.full_run:
+        # the configuration's whole run (2000 steps) per form, untimed
+        line["full_run"] = {name: full_run(prob, name, prob.steps)
+                            for name in avail if name != "standard"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(1 << 21, 0)
     line["wall_s_timed_forms"] = round(wall, 2)
