@@ -609,12 +609,15 @@ EM2D_TRAFFIC = {("fp64", 0): None, ("fp64", 1): 68729856,   # dram read + write 
                 ("fp64_charge_conserving", 0): 43356928, ("fp64_charge_conserving", 1): 69003776}
 
 
-def time_weibel2d(prob, precision, args, stream, flush, charge_conserving=False):
+def time_weibel2d(prob, precision, args, stream, flush, charge_conserving=False,
+                  sort_period=0):
     """Warm-up, timed steps (one event pair per step, L2 flushed before each)
-    and a profiled run of one form of the 2D3V Yee step."""
+    and a profiled run of one form of the 2D3V Yee step.  With sort_period P
+    the timed steps include the sorts that fall in them."""
     import torch
     from paper_2411_09605_gb300 import pic
-    sim = pic.Simulation2D(prob, precision=precision, charge_conserving=charge_conserving)
+    sim = pic.Simulation2D(prob, precision=precision, charge_conserving=charge_conserving,
+                           sort_period=sort_period)
     try:
         te0 = sim.energy()[3]
         pic.pic_step_async(sim.h, max(3, args.warmup))
@@ -639,7 +642,8 @@ def time_weibel2d(prob, precision, args, stream, flush, charge_conserving=False)
             pic.pic_step_async(sim.h, 1)
         pic.pic_read_stats(sim.h)
         kern = {}
-        for kind, kname in ((0, "pass_c"), (1, "pass_e"), (2, "finalize"), (4, "field")):
+        for kind, kname in ((0, "pass_c"), (1, "pass_e"), (2, "finalize"), (4, "field"),
+                            (3, "sort")):
             n, tot = pic.pic_profile(sim.h, kind)
             if n:
                 kern[kname] = {"launches": n, "avg_us": 1e3 * tot / n}
@@ -669,26 +673,30 @@ def run_weibel2d(args):
     fp64_peak = FP64_LANES_PER_SM_CLK * nsm * 2070.0e6 / 1e9
     forms = {}
     with ClockSampler(0, enabled=not args.no_clocks) as clk:
-        for name, precision, cc in (("mixed", 1, False), ("fp64", 0, False),
-                                    ("fp64_charge_conserving", 0, True)):
-            forms[name] = time_weibel2d(prob, precision, args, stream, flush, cc)
+        for name, precision, cc, sp in (("mixed", 1, False, args.sort_period),
+                                        ("mixed_unsorted", 1, False, 0),
+                                        ("fp64", 0, False, 0),
+                                        ("fp64_charge_conserving", 0, True, 0)):
+            if name == "mixed_unsorted" and args.sort_period == 0:
+                continue
+            forms[name] = time_weibel2d(prob, precision, args, stream, flush, cc, sp)
     out = {}
     for name, f in forms.items():
         kern = f["kernels"]
         for kind, kname in ((0, "pass_c"), (1, "pass_e")):
             if kname in kern:
                 t = kern[kname]["avg_us"] * 1e-6
-                ach = EM2D_ALGO_BYTES[(name, kind)] * n / t / 1e9
+                ach = EM2D_ALGO_BYTES[("mixed" if name.startswith("mixed") else name, kind)] * n / t / 1e9
                 kern[kname]["achieved_GBs"] = round(ach, 1)
                 kern[kname]["frac_hbm"] = round(ach / peak, 4)
-                if name != "mixed":     # the FP64 forms: FP64-pipe instructions per marker (ncu)
+                if not name.startswith("mixed"):  # the FP64 forms: FP64-pipe instructions per marker (ncu)
                     kern[kname]["fp64_ginst_s"] = round(EM2D_FP64_INST_PER_MARKER[(name, kind)] * n / t / 1e9, 1)
                     kern[kname]["frac_fp64"] = round(kern[kname]["fp64_ginst_s"] / fp64_peak, 4)
         dom = max(("pass_c", "pass_e"), key=lambda k: kern[k]["avg_us"]) if "pass_e" in kern else None
         dk = 1 if dom == "pass_e" else 0
         if dom is None:
             roof = None                       # no profiled steps
-        elif name != "mixed":
+        elif not name.startswith("mixed"):
             roof = {"bound": "alu", "kernel": dom, "achieved": kern[dom]["fp64_ginst_s"],
                     "peak": round(fp64_peak, 1), "unit": "Ginst/s (FP64 pipe)",
                     "frac": kern[dom]["frac_fp64"], "traffic": EM2D_TRAFFIC[(name, dk)],
@@ -701,7 +709,7 @@ def run_weibel2d(args):
             # global atomics), see the note
             roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_GBs"],
                     "peak": peak, "unit": "GB/s", "frac": kern[dom]["frac_hbm"],
-                    "traffic": EM2D_TRAFFIC[(name, dk)], "peak_source": peak_src,
+                    "traffic": EM2D_TRAFFIC.get((name, dk)), "peak_source": peak_src,
                     "note": "bound by L2 requests (64-bit global atomics of the integer "
                             "current; ncu: L2 tag lookups near 70% of peak), not by HBM"}
         out[name] = {"value": n * args.steps / (f["step_ms"].sum() / 1e3),
@@ -719,6 +727,7 @@ def run_weibel2d(args):
         "config": {"workload": "weibel_2d3v_yee", "cells": [prob.nx, prob.ny],
                    "markers": n, "dt": prob.dt, "c": prob.c, "scheme": "ESEC2",
                    "shape_order": prob.order, "form": "mixed",
+                   "sort_period": args.sort_period,
                    "l2": "flushed (512 MiB write) before every timed step"},
         "energy": hf["energy"], "gpu_launches": hf["gpu_launches"],
         "kernels": hf["kernels"], "clocks": clk.summary(), "roofline": hf["roofline"],

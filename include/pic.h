@@ -134,10 +134,14 @@ typedef struct {
   pic_scheme scheme;
   pic_precision precision;
   int sort_period;          /* mixed form: 0 = markers never reordered;       */
-                            /* 1 = kept sorted by (cell, sign of v) every     */
-                            /* step, written in key order by the update pass; */
-                            /* P > 1 = counting sort by cell every P steps.   */
-                            /* Sorting only reorders markers.                 */
+                            /* Ampere solver: 1 = kept sorted by (cell, sign  */
+                            /* of v) every step, written in key order by the  */
+                            /* update pass; P > 1 = counting sort by cell     */
+                            /* every P steps.  Yee solver: P >= 1 = counting  */
+                            /* sort by quarter cell every P steps, and each   */
+                            /* warp's deposits summed over its lanes' equal   */
+                            /* stencils before the atomics.  Sorting only     */
+                            /* reorders markers (pic_get_ids maps them).      */
   int remove_mean;          /* ES: 1 -> E -= dt (J - <J>), 0 -> E -= dt J     */
   int gamma_on;             /* 1 = energy correction; 0 = naive scheme        */
   int ptr_on_device;        /* see Conventions                                */

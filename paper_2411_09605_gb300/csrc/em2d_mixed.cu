@@ -179,6 +179,70 @@ __device__ __forceinline__ void deposit_j(const Em2dMixConst &c, long long *J,
   deposit_c<ORDER>(J + 2 * nc, nx, S.xI, S.yI, V[2], c);
 }
 
+// Segments of a warp's lanes for one current component: neighbouring lanes
+// with equal keys (the component's first stencil node) form a segment.  With
+// the markers sorted by quarter cell, the lanes of a warp hold a few segments,
+// and each segment's deposits can be summed over its lanes before one atomic
+// per node: exact integer sums, so the result is the per-marker atomics' bit
+// for bit, whatever the order (an unsorted warp only gets shorter segments).
+struct WarpSegments {
+  int start;  // first lane of this lane's segment
+  bool tail;  // this lane ends its segment
+  __device__ __forceinline__ explicit WarpSegments(int key) {
+    const unsigned lane = threadIdx.x & 31u;
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0u || key != prev);
+    start = 31 - __clz(heads & (0xffffffffu >> (31u - lane)));
+    tail = lane == 31u || ((heads >> (lane + 1u)) & 1u);
+  }
+  // inclusive sum of v over the lanes of the segment up to this one
+  __device__ __forceinline__ long long scan(long long v) const {
+    const int lane = (int)(threadIdx.x & 31u);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long t = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane - d >= start) v += t;
+    }
+    return v;
+  }
+};
+
+// deposit_c for cell-sorted markers, called by every lane of the warp
+// (valid = the lane holds a marker): the segment's sums, added by its last lane
+template <int ORDER>
+__device__ __forceinline__ void deposit_c_seg(long long *J, int nx, const AxisMix<ORDER> &ax,
+                                              const AxisMix<ORDER> &ay, int V, bool valid,
+                                              const Em2dMixConst &c) {
+  const WarpSegments seg(valid ? ax.k[0] + nx * ay.k[0] : -1 - (int)(threadIdx.x & 31u));
+  const bool neg = V < 0;
+  const uint32_t mag = neg ? 0u - (uint32_t)V : (uint32_t)V;
+#pragma unroll
+  for (int b = 0; b <= ORDER; b++) {
+    const uint64_t m = (uint64_t)mag * ay.s[b];
+    long long *row = J + ay.k[b] * nx;
+#pragma unroll
+    for (int a = 0; a <= ORDER; a++) {
+      const long long sum = seg.scan(valid ? deposit_term(m, ax.s[a], neg, c) : 0ll);
+      if (seg.tail && valid && sum != 0)
+        atomicAdd((unsigned long long *)(row + ax.k[a]), (unsigned long long)sum);
+    }
+  }
+}
+
+template <int ORDER, bool SORTED>
+__device__ __forceinline__ void deposit_j_any(const Em2dMixConst &c, long long *J,
+                                              const Shape2Mix<ORDER> &S, const int V[3],
+                                              bool valid) {
+  if (SORTED) {
+    const int nx = c.nx, nc = c.nx * c.ny;
+    deposit_c_seg<ORDER>(J, nx, S.xH, S.yI, V[0], valid, c);
+    deposit_c_seg<ORDER>(J + nc, nx, S.xI, S.yH, V[1], valid, c);
+    deposit_c_seg<ORDER>(J + 2 * nc, nx, S.xI, S.yI, V[2], valid, c);
+  } else if (valid) {
+    deposit_j<ORDER>(c, J, S, V);
+  }
+}
+
 __device__ __forceinline__ void report_bad(unsigned bad, unsigned *err) {
   bad = __reduce_or_sync(0xffffffffu, bad);
   if ((threadIdx.x & 31u) == 0u && bad) atomicOr(err, bad);
@@ -286,18 +350,23 @@ __global__ void mix2_k3_kernel(Em2dConst c, Em2dMixConst m, Em2dMixBufs mb, Em2d
 }
 
 // Pass C: x*, E* and B at x*, v* (integer V*), x^{n+1/2}, deposit of j^{*,n+1/2}
-template <int ORDER>
+template <int ORDER, bool SORTED>
 __global__ void __launch_bounds__(256) mix2_pass_c_kernel(Em2dMixConst c, Em2dMixBufs b) {
   const int nx = c.nx, nc = c.nx * c.ny;
   unsigned bad = 0;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t X = b.X[p], Y = b.Y[p];
+  // every lane of a warp runs the same trips (the sorted deposit sums over the warp)
+  for (int64_t pw = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); pw < c.n;
+       pw += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = pw + (threadIdx.x & 31u);
+    const bool valid = p < c.n;
+    if (!SORTED && !valid) break;
+    const int64_t q = valid ? p : c.n - 1;
+    const uint32_t X = b.X[q], Y = b.Y[q];
     float vh[3], vl[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-      vh[d] = b.vh[d][p];
-      vl[d] = b.vl[d][p];
+      vh[d] = b.vh[d][q];
+      vl[d] = b.vl[d][q];
     }
     const Shape2Mix<ORDER> S1(X + half_shift(to_fixed(vh[0], bad), c),
                               Y + half_shift(to_fixed(vh[1], bad), c), c.nx, c.ny);
@@ -326,32 +395,37 @@ __global__ void __launch_bounds__(256) mix2_pass_c_kernel(Em2dMixConst c, Em2dMi
       Vs[d] = vstar_fixed(vh[d], vl[d], __fadd_rn(e[d], corr), bad);
     }
     const Shape2Mix<ORDER> Sh(X + half_shift(Vs[0], c), Y + half_shift(Vs[1], c), c.nx, c.ny);
-    deposit_j<ORDER>(c, b.J2, Sh, Vs);
+    deposit_j_any<ORDER, SORTED>(c, b.J2, Sh, Vs, valid);
+    if (valid)
 #pragma unroll
-    for (int d = 0; d < 3; d++) b.Vs[d][p] = Vs[d];
+      for (int d = 0; d < 3; d++) b.Vs[d][p] = Vs[d];
   }
   report_bad(bad, b.err);
 }
 
 // Pass E: gather at x^{n+1/2} = X + [V*], v^dag, Gamma, x^{n+1}, v^{n+1}, the
 // kinetic energy and (ESEC2) the next step's j^{n+1,*}
-template <int ORDER>
+template <int ORDER, bool SORTED>
 __global__ void __launch_bounds__(256) mix2_pass_e_kernel(Em2dMixConst c, Em2dMixBufs b,
                                                           int slot) {
   __shared__ double red[33];
   const int nx = c.nx, nc = c.nx * c.ny;
   float ke_hi = 0.0f, ke_lo = 0.0f;
   unsigned nfb = 0, bad = 0;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t X = b.X[p], Y = b.Y[p];
+  for (int64_t pw = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); pw < c.n;
+       pw += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = pw + (threadIdx.x & 31u);
+    const bool valid = p < c.n;
+    if (!SORTED && !valid) break;
+    const int64_t q = valid ? p : c.n - 1;
+    const uint32_t X = b.X[q], Y = b.Y[q];
     float vh[3], vl[3];
     int Vs[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-      vh[d] = b.vh[d][p];
-      vl[d] = b.vl[d][p];
-      Vs[d] = b.Vs[d][p];
+      vh[d] = b.vh[d][q];
+      vl[d] = b.vl[d][q];
+      Vs[d] = b.Vs[d][q];
     }
     const uint32_t hx = half_shift(Vs[0], c), hy = half_shift(Vs[1], c);
     const Shape2Mix<ORDER> S(X + hx, Y + hy, c.nx, c.ny);
@@ -368,7 +442,10 @@ __global__ void __launch_bounds__(256) mix2_pass_e_kernel(Em2dMixConst c, Em2dMi
     D[1] = ff_add(D[1], ff_sub(ff_mul_f(vs[2], bb[0]), ff_mul_f(vs[0], bb[2])));
     D[2] = ff_add(D[2], ff_sub(ff_mul_f(vs[0], bb[1]), ff_mul_f(vs[1], bb[0])));
     ff vn[3];
-    correct_velocity3(vh, vl, Vs, D, c.gamma_on != 0, nfb, vn);
+    correct_velocity3(vh, vl, Vs, D, c.gamma_on != 0 && valid, nfb, vn);
+    if (!valid)
+#pragma unroll
+      for (int d = 0; d < 3; d++) vn[d] = ff{0.0f, 0.0f};
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       ff s2 = two_prod(vn[d].hi, vn[d].hi);
@@ -383,15 +460,17 @@ __global__ void __launch_bounds__(256) mix2_pass_e_kernel(Em2dMixConst c, Em2dMi
                           to_fixed(vn[2].hi, bad)};
       const Shape2Mix<ORDER> S1(Xn + half_shift(Vn1[0], c), Yn + half_shift(Vn1[1], c), c.nx,
                                 c.ny);
-      deposit_j<ORDER>(c, b.J1, S1, Vn1);
+      deposit_j_any<ORDER, SORTED>(c, b.J1, S1, Vn1, valid);
     }
-    b.X[p] = Xn;
-    b.Y[p] = Yn;
+    if (valid) {
+      b.X[p] = Xn;
+      b.Y[p] = Yn;
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-      b.vh[d][p] = vn[d].hi;
-      b.vl[d][p] = vn[d].lo;
-      if (!isfinite(vn[d].hi)) bad |= kErrNonfinite;
+      for (int d = 0; d < 3; d++) {
+        b.vh[d][p] = vn[d].hi;
+        b.vl[d][p] = vn[d].lo;
+        if (!isfinite(vn[d].hi)) bad |= kErrNonfinite;
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
@@ -479,7 +558,78 @@ __global__ void mix2_absmax_kernel(Em2dBufs b, int64_t n, unsigned long long *ou
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
+// ------------------------------------------------------------ quarter-cell sort
+// The markers in the order of their quarter cell floor(2x / hx) + 2 nx
+// floor(2y / hy): within a quarter cell every current component's stencil
+// starts at the same node (order 1 and 2, integer and half nodes), so a
+// warp's deposits form few segments.  Counting sort: counts, their exclusive
+// scan, then each marker (and its id) to the next free slot of its key; the
+// order within a key is not fixed, which changes no result (the currents are
+// exact integer sums).
+__device__ __forceinline__ int quarter_key(uint32_t X, uint32_t Y, int nx, int ny) {
+  const int qx = (int)(((uint64_t)X * (uint32_t)(2 * nx)) >> 32);
+  const int qy = (int)(((uint64_t)Y * (uint32_t)(2 * ny)) >> 32);
+  return qx + 2 * nx * qy;
+}
+
+__global__ void mix2_sort_count_kernel(const uint32_t *X, const uint32_t *Y, int64_t n, int nx,
+                                       int ny, unsigned *cnt) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[quarter_key(X[p], Y[p], nx, ny)], 1u);
+}
+
+// Exclusive scan of cnt[0 .. nk) into off[] by one block of 1024 threads.
+__global__ void __launch_bounds__(1024) mix2_sort_scan_kernel(const unsigned *cnt, unsigned *off,
+                                                              int nk) {
+  __shared__ unsigned part[1024];
+  const int per = (nk + blockDim.x - 1) / blockDim.x;
+  const int beg = threadIdx.x * per, end = beg + per < nk ? beg + per : nk;
+  unsigned sum = 0;
+  for (int i = beg; i < end; i++) sum += cnt[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const unsigned v = (int)threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned run = part[threadIdx.x] - sum;
+  for (int i = beg; i < end; i++) {
+    off[i] = run;
+    run += cnt[i];
+  }
+}
+
+__global__ void mix2_sort_move_kernel(Em2dMixBufs src, Em2dMixBufs dst, const int64_t *ids_in,
+                                      int64_t *ids_out, int64_t n, int nx, int ny, unsigned *off) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t X = src.X[p], Y = src.Y[p];
+    const unsigned slot = atomicAdd(&off[quarter_key(X, Y, nx, ny)], 1u);
+    dst.X[slot] = X;
+    dst.Y[slot] = Y;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      dst.vh[d][slot] = src.vh[d][p];
+      dst.vl[d][slot] = src.vl[d][p];
+    }
+    if (ids_in) ids_out[slot] = ids_in[p];
+  }
+}
+
 }  // namespace
+
+void em2dm_sort(const Em2dMixConst &m, const Em2dMixBufs &src, const Em2dMixBufs &dst,
+                const int64_t *ids_in, int64_t *ids_out, unsigned *cnt, unsigned *off,
+                LaunchShape lp, cudaStream_t st) {
+  const int nk = 4 * m.nx * m.ny;
+  cudaMemsetAsync(cnt, 0, sizeof(unsigned) * nk, st);
+  mix2_sort_count_kernel<<<lp.grid, 256, 0, st>>>(src.X, src.Y, m.n, m.nx, m.ny, cnt);
+  mix2_sort_scan_kernel<<<1, 1024, 0, st>>>(cnt, off, nk);
+  mix2_sort_move_kernel<<<lp.grid, 256, 0, st>>>(src, dst, ids_in, ids_out, m.n, m.nx, m.ny, off);
+}
 
 void em2dm_k1(const Em2dConst &c, const Em2dMixConst &m, const Em2dMixBufs &mb,
               const Em2dBufs &b, LaunchShape lg, cudaStream_t st) {
@@ -492,18 +642,18 @@ void em2dm_k3(const Em2dConst &c, const Em2dMixConst &m, const Em2dMixBufs &mb,
 }
 
 void em2dm_pass_c(const Em2dMixConst &m, const Em2dMixBufs &mb, LaunchShape lp, cudaStream_t st) {
-  if (m.order == 1)
-    mix2_pass_c_kernel<1><<<lp.grid, 256, 0, st>>>(m, mb);
-  else
-    mix2_pass_c_kernel<2><<<lp.grid, 256, 0, st>>>(m, mb);
+  if (m.order == 1 && !m.sorted) mix2_pass_c_kernel<1, false><<<lp.grid, 256, 0, st>>>(m, mb);
+  if (m.order == 1 && m.sorted) mix2_pass_c_kernel<1, true><<<lp.grid, 256, 0, st>>>(m, mb);
+  if (m.order == 2 && !m.sorted) mix2_pass_c_kernel<2, false><<<lp.grid, 256, 0, st>>>(m, mb);
+  if (m.order == 2 && m.sorted) mix2_pass_c_kernel<2, true><<<lp.grid, 256, 0, st>>>(m, mb);
 }
 
 void em2dm_pass_e(const Em2dMixConst &m, const Em2dMixBufs &mb, int slot, LaunchShape lp,
                   cudaStream_t st) {
-  if (m.order == 1)
-    mix2_pass_e_kernel<1><<<lp.grid, 256, 0, st>>>(m, mb, slot);
-  else
-    mix2_pass_e_kernel<2><<<lp.grid, 256, 0, st>>>(m, mb, slot);
+  if (m.order == 1 && !m.sorted) mix2_pass_e_kernel<1, false><<<lp.grid, 256, 0, st>>>(m, mb, slot);
+  if (m.order == 1 && m.sorted) mix2_pass_e_kernel<1, true><<<lp.grid, 256, 0, st>>>(m, mb, slot);
+  if (m.order == 2 && !m.sorted) mix2_pass_e_kernel<2, false><<<lp.grid, 256, 0, st>>>(m, mb, slot);
+  if (m.order == 2 && m.sorted) mix2_pass_e_kernel<2, true><<<lp.grid, 256, 0, st>>>(m, mb, slot);
 }
 
 void em2dm_from_fp64(const Em2dMixConst &m, const Em2dMixBufs &mb, const Em2dBufs &b,

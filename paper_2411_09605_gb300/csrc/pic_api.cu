@@ -108,6 +108,9 @@ struct pic_handle {
   Em1dMixBufs b1m{};
   Em2dMixConst cme{};   // mixed form of the 2D3V path (em && mixed)
   Em2dMixBufs bme{};
+  Em2dMixBufs bme_alt{};          // the quarter-cell sort's destination markers
+  unsigned *sort2_cnt = nullptr;  // [4 nx ny] counts and offsets of the sort
+  unsigned *sort2_off = nullptr;
   LaunchShape lp{1, 256}, lg{1, 256};
   // 1D mixed-precision state
   bool mixed = false;
@@ -368,6 +371,17 @@ void swap_sorted_output(pic_handle *h) {
   (void)bm;
 }
 
+// Markers a tile copy of the mixed 1D passes takes in one launch on grids of up
+// to kWideMaxNodes nodes: those of one wave of the wide launch (one
+// 1024-thread block per SM, 32 copies a block, 4 markers per thread and
+// trip), at least 2048.  Every launch of such a handle keeps to it.
+int64_t mixed_wide_pcnt(int64_t N, int nsm) {
+  const int64_t ngroups = (N + 3) / 4;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((ngroups + 1023) / 1024, nsm));
+  const int64_t trips = (ngroups + grid * 1024 - 1) / (grid * 1024);
+  return std::max<int64_t>(2048, trips * 128);
+}
+
 // Mixed form: constants, integer/float-pair state converted from the FP64
 // staging arrays, j^{n,*} of the initial state.
 int init_mixed(pic_handle *h, bool solve_e0) {
@@ -424,30 +438,27 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   // share comes from the high word of V* s (r + b >= 32: T <= 22 + b); the
   // sorted modes' warp sums take 4 terms a lane in 20-bit halves (T <= 44);
   // the int64 grid sums need N 2^T < 2^62.  Every launch of a handle keeps to
-  // the same pcnt: on grids of up to kWideMaxNodes nodes 2048 (the wide
-  // launch has 32 copies and enough blocks; the batched launch at most 16
-  // trips of 128 markers a copy; the sorted modes' single-copy launch one trip
-  // of 2048 markers a block), on larger grids the markers of a 512-thread
-  // block of the single-copy launch.  One r and b for every mode keep the
-  // results independent of the marker order.
+  // the same pcnt: on grids of up to kWideMaxNodes nodes the markers a copy
+  // takes in one wave of the wide launch (mixed_wide_pcnt, at least 2048; the
+  // batched launch takes at most 16 trips of 128 markers a copy, the sorted
+  // modes' single-copy launch pcnt markers a 512-thread block), on larger
+  // grids the markers of a 512-thread block of the single-copy launch.  One r
+  // and b for every mode keep the results independent of the marker order.
   int64_t pcnt;
   if (c.nc <= kWideMaxNodes) {
-    pcnt = 2048;
-    if (m.wide) {
-      const int64_t wthreads = (int64_t)h->lmix.grid * 1024;
-      const int64_t wtrips = (ngroups + wthreads - 1) / wthreads;
-      if (wtrips * 128 > pcnt) {
-        const int64_t grid = (ngroups * 128 + pcnt * 1024 - 1) / (pcnt * 1024);
-        h->lmix.grid = (int)std::max<int64_t>(h->lmix.grid, grid);
-      }
-    }
+    pcnt = mixed_wide_pcnt(h->N, h->nsm);
   } else {
     const int64_t threads = (int64_t)h->ls.grid * 512;
     const int64_t trips = (ngroups + threads - 1) / threads;
     pcnt = std::max<int64_t>(2048, trips * 512 * 4);
   }
-  if (!m.wide && h->lmix.grid * (int64_t)2048 < 4 * ngroups && c.nc <= kWideMaxNodes)
+  if (m.wide) {
+    const int64_t wthreads = (int64_t)h->lmix.grid * 1024;
+    if (((ngroups + wthreads - 1) / wthreads) * 128 > pcnt)
+      return fail(PIC_ERR_UNSUPPORTED, "pic_init: internal launch size of the wide passes");
+  } else if (c.nc <= kWideMaxNodes && h->lmix.grid * pcnt < 4 * ngroups) {
     return fail(PIC_ERR_UNSUPPORTED, "pic_init: internal launch size for the sorted modes");
+  }
   int lg = 0;
   while (((int64_t)1 << lg) < pcnt) lg++;
   m.split = 32 - lg;
@@ -801,6 +812,39 @@ int init_em2d_mixed(pic_handle *h) {
   mb.ke_part = h->be.ke_part;
   mb.fallback = h->be.fallback;
   mb.err = h->be.err;
+  m.sorted = h->cfg.sort_period > 0;
+  if (m.sorted) {
+    // markers in quarter-cell order every sort_period steps (ids follow them)
+    Em2dMixBufs &alt = h->bme_alt;
+    alt = mb;
+    if ((rc = h->alloc(&alt.X, n)) || (rc = h->alloc(&alt.Y, n)) ||
+        (rc = h->alloc(&h->ids_alt, n)) ||
+        (rc = h->alloc(&h->sort2_cnt, 4 * (size_t)c.nx * c.ny)) ||
+        (rc = h->alloc(&h->sort2_off, 4 * (size_t)c.nx * c.ny)))
+      return rc;
+    for (int d = 0; d < 3; d++)
+      if ((rc = h->alloc(&alt.vh[d], n)) || (rc = h->alloc(&alt.vl[d], n))) return rc;
+  }
+  return PIC_OK;
+}
+
+// Sorts the mixed 2D markers (and their ids) by quarter cell into the
+// alternate arrays and swaps them in.
+int sort_em2d_mixed(pic_handle *h) {
+  const bool ids = !h->cfg.skip_ids;
+  CUDA_TRY(h->timed_launch(3, [&] {
+    em2dm_sort(h->cme, h->bme, h->bme_alt, ids ? h->ids : nullptr, ids ? h->ids_alt : nullptr,
+               h->sort2_cnt, h->sort2_off, h->lp, h->st);
+  }));
+  h->launches += 3;
+  Em2dMixBufs &a = h->bme, &b = h->bme_alt;
+  std::swap(a.X, b.X);
+  std::swap(a.Y, b.Y);
+  for (int d = 0; d < 3; d++) {
+    std::swap(a.vh[d], b.vh[d]);
+    std::swap(a.vl[d], b.vl[d]);
+  }
+  if (ids) std::swap(h->ids, h->ids_alt);
   return PIC_OK;
 }
 
@@ -1202,9 +1246,10 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
     return fail(PIC_ERR_ARG, "pic_init: binomial_passes must be in [0, 8]");
   if (cfg->sort_period < 0) return fail(PIC_ERR_ARG, "pic_init: sort_period must be >= 0");
   if (cfg->sort_period > 0 &&
-      (cfg->solver != PIC_SOLVER_AMPERE_ES || cfg->precision != PIC_PREC_MIXED))
+      ((cfg->solver != PIC_SOLVER_AMPERE_ES && cfg->solver != PIC_SOLVER_YEE_LEAPFROG) ||
+       cfg->precision != PIC_PREC_MIXED))
     return fail(PIC_ERR_UNSUPPORTED, "pic_init: sort_period is an option of the mixed form of "
-                                     "the Ampere solver");
+                                     "the Ampere and Yee solvers");
   if (cfg->charge_conserving != 0 && cfg->charge_conserving != 1)
     return fail(PIC_ERR_ARG, "pic_init: charge_conserving must be 0 or 1");
   if (cfg->gamma_fp64 != 0 && cfg->gamma_fp64 != 1)
@@ -1311,11 +1356,14 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
     // the bound the split integer tile is sized for
     const int64_t need = ((N + 3) / 4 + 512 * 16 - 1) / (512 * 16);
     h->ls.grid = (int)std::max<int64_t>(h->ls.grid, need);
-    // the sorted 1D modes on grids of up to kWideMaxNodes nodes: one trip of
-    // 2048 markers per 512-thread block (the tile bound of that grid size)
+    // the sorted 1D modes on grids of up to kWideMaxNodes nodes: at most the
+    // wide launch's per-copy count of markers per 512-thread block (the tile
+    // bound of that grid size)
     if (cfg->solver == PIC_SOLVER_AMPERE_ES && cfg->sort_period > 0 &&
-        cfg->grid.n[0] <= kWideMaxNodes)
-      h->ls.grid = (int)std::max<int64_t>(h->ls.grid, ((N + 3) / 4 + 511) / 512);
+        cfg->grid.n[0] <= kWideMaxNodes) {
+      const int64_t pc = mixed_wide_pcnt(N, nsm);
+      h->ls.grid = (int)std::max<int64_t>(h->ls.grid, (4 * ((N + 3) / 4) + pc - 1) / pc);
+    }
   }
   h->nsm = nsm;
   h->em = cfg->solver == PIC_SOLVER_YEE_LEAPFROG;
@@ -1374,6 +1422,10 @@ int pic_step_async(pic_handle *h, int nsteps) {
     Em2dBufs &e = h->be;
     const int slot = h->pending;
     if (h->mixed) {
+      if (h->cme.sorted && h->steps_done % h->cfg.sort_period == 0) {
+        const int rc = sort_em2d_mixed(h);
+        if (rc) return rc;
+      }
       const Em2dMixBufs &mb = h->bme;
       CUDA_TRY(h->timed_launch(4, [&] { em2dm_k1(h->ce, h->cme, mb, e, h->lg, h->st); }));
       CUDA_TRY(h->timed_launch(0, [&] { em2dm_pass_c(h->cme, mb, h->lp, h->st); }));

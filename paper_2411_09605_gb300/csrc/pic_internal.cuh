@@ -288,6 +288,7 @@ struct Em2dMixConst {
   double t_half;       // dt/2 (q/m): B -> the rotation vector t of v*
   double kick;         // dt (q/m) cxk: E^{n+1/2} -> V units
   double m_full;       // dt (q/m): (V* x B) -> V units
+  int sorted;          // markers kept in quarter-cell order: segmented warp deposits
 };
 
 struct Em2dMixBufs {
@@ -399,6 +400,11 @@ void em2dm_k3(const Em2dConst &c, const Em2dMixConst &m, const Em2dMixBufs &mb,
 void em2dm_pass_c(const Em2dMixConst &m, const Em2dMixBufs &mb, LaunchShape lp, cudaStream_t st);
 void em2dm_pass_e(const Em2dMixConst &m, const Em2dMixBufs &mb, int slot, LaunchShape lp,
                   cudaStream_t st);
+// quarter-cell counting sort of the mixed 2D markers (and ids) from src into
+// dst; cnt, off: [4 nx ny] scratch
+void em2dm_sort(const Em2dMixConst &m, const Em2dMixBufs &src, const Em2dMixBufs &dst,
+                const int64_t *ids_in, int64_t *ids_out, unsigned *cnt, unsigned *off,
+                LaunchShape lp, cudaStream_t st);
 // FP64 staging (x, y, vx, vy, vz) <-> the mixed state
 void em2dm_from_fp64(const Em2dMixConst &m, const Em2dMixBufs &mb, const Em2dBufs &b,
                      LaunchShape lp, cudaStream_t st);

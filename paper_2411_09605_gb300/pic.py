@@ -327,12 +327,12 @@ class Simulation2D:
     """Owner of one Yee-solver handle built from a ``workloads.Problem2D``."""
 
     def __init__(self, prob, scheme=PIC_SCHEME_ESEC2, E0=None, B0=None, gamma_on=True,
-                 precision=PIC_PREC_FP64, charge_conserving=False):
+                 precision=PIC_PREC_FP64, charge_conserving=False, sort_period=0):
         self.prob = prob
         self.cfg = make_config(prob.nx, prob.Lx, prob.dt, prob.order, scheme, precision,
                                solver=PIC_SOLVER_YEE_LEAPFROG, dim_x=2, dim_v=3, ny=prob.ny,
                                Ly=prob.Ly, c=prob.c, gamma_on=gamma_on,
-                               charge_conserving=charge_conserving)
+                               charge_conserving=charge_conserving, sort_period=sort_period)
         self.species = []
         for s in prob.species:
             x = np.ascontiguousarray(np.stack([s.x, s.y]), dtype=np.float64)
@@ -351,10 +351,15 @@ class Simulation2D:
         return fb, te
 
     def particles(self, s: int = 0):
+        """(x [2, n], v [3, n]) of species s in the order the markers were given."""
         n = self.species[s]["n"]
         x, v = np.zeros((2, n)), np.zeros((3, n))
         pic_get_particles(self.h, s, x, v)
-        return x, v
+        ids = np.zeros(n, dtype=np.int64)
+        pic_get_ids(self.h, s, ids)
+        xo, vo = np.zeros_like(x), np.zeros_like(v)
+        xo[:, ids], vo[:, ids] = x, v
+        return xo, vo
 
     def fields(self):
         shape = (3, self.prob.ny, self.prob.nx)

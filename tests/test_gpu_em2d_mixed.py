@@ -231,3 +231,72 @@ def test_input_errors_mixed():
             assert ei.value.code == code
     finally:
         sim.close()
+
+
+@pytest.mark.parametrize("order,scheme,period", [(1, 2, 1), (1, 1, 3), (2, 2, 2), (2, 2, 5)])
+def test_quarter_cell_sort_does_not_change_the_physics(order, scheme, period):
+    """The markers kept in quarter-cell order every `period` steps, with each
+    warp's deposits summed over its lanes' equal stencils before the atomics:
+    the currents are exact integer sums, so the run equals the unsorted one bit
+    for bit (markers compared through their ids), over 12 steps."""
+    from paper_2411_09605_gb300 import pic
+    prob = W.weibel(nx=32, ny=32, ppc=16, L=6.4, vth_par=0.1, order=order, seed=21)
+    E0, B0 = _fields(prob, 22)
+    res = []
+    for sp in (0, period):
+        sim = pic.Simulation2D(prob, scheme=scheme, E0=E0, B0=B0, precision=MIXED,
+                               sort_period=sp)
+        try:
+            fb, te = sim.step(12)
+            x, v = sim.particles(0)
+            E, B = sim.fields()
+        finally:
+            sim.close()
+        res.append((x, v, E, B, fb, te))
+    a, b = res
+    for u, w in zip(a[:5], b[:5]):
+        assert np.array_equal(u, w)
+    assert np.max(np.abs(a[5] - b[5])) <= 1e-14 * abs(a[5][0])
+
+
+def test_quarter_cell_order_after_a_sort():
+    """Right after a sort the slots run in quarter-cell order and the ids are a
+    permutation (bit-exact integer work)."""
+    from paper_2411_09605_gb300 import pic
+    # nearly cold markers: one step moves almost none of them into another
+    # quarter cell, so the slots after the step show the order of the sort
+    prob = W.weibel(nx=16, ny=16, ppc=8, L=3.2, vth_par=1e-4, seed=23)
+    sim = pic.Simulation2D(prob, precision=MIXED, sort_period=4)
+    n = prob.n_markers
+    try:
+        sim.step(1)   # sorted at the start of step 0, then moved by one step
+        x, v = np.zeros((2, n)), np.zeros((3, n))
+        pic.pic_get_particles(sim.h, 0, x, v)
+        ids = np.zeros(n, dtype=np.int64)
+        pic.pic_get_ids(sim.h, 0, ids)
+    finally:
+        sim.close()
+    assert np.array_equal(np.sort(ids), np.arange(n))
+    q = np.floor(2 * x[0] / (prob.Lx / 16)).astype(int) + 32 * np.floor(2 * x[1] / (prob.Ly / 16)).astype(int)
+    assert np.mean(np.diff(q) >= 0) > 0.999
+
+
+def test_sorted_mixed_against_oracle():
+    """The sorted mode at the mixed bars against the oracle (orders 1 and 2)."""
+    for order in (1, 2):
+        prob = W.weibel(nx=32, ny=32, ppc=8, L=6.4, order=order, vth_par=0.1, seed=24)
+        E0, B0 = _fields(prob, 25)
+        xr, vr, Er, Br, nfb_o = _oracle(prob, 2, 10, E0, B0)
+        from paper_2411_09605_gb300 import pic
+        sim = pic.Simulation2D(prob, E0=E0, B0=B0, precision=MIXED, sort_period=2)
+        try:
+            fb, te = sim.step(10)
+            xg, vg = sim.particles(0)
+            Eg, Bg = sim.fields()
+            res = pic.pic_mixed_resolution(sim.h)
+        finally:
+            sim.close()
+        _bars(prob, (xr, vr, Er, Br), (xg, vg), E0, B0, res, 10)
+        d = _diff(prob, (xr, vr, Er, Br), (xg, vg, Eg, Bg))
+        assert d["E"] <= TOL_F and d["B"] <= TOL_F, d
+        assert np.array_equal(nfb_o, fb)
