@@ -76,8 +76,9 @@ def parse():
     ap.add_argument("--full-run", action=argparse.BooleanOptionalAction, default=True,
                     help="also run the workload's whole length per form, untimed, for its "
                          "energy error and fallbacks")
-    ap.add_argument("--sort-period", type=int, default=0,
-                    help="cell sort of the mixed form every this many steps (0 = never)")
+    ap.add_argument("--sort-period", type=int, default=None,
+                    help="sort of the mixed form's markers every this many steps (0 = never; "
+                         "default: 0 on the 1D workloads, 2 on the 2D3V Weibel workload)")
     ap.add_argument("--weibel2d", action="store_true",
                     help="time the 2D3V Yee/leapfrog path on the 128 x 128 Weibel workload "
                          "instead (not the default line)")
@@ -90,7 +91,13 @@ def parse():
     ap.add_argument("--ensemble", type=int, default=0,
                     help="time a batch of this many independent runs instead (not the default "
                          "line): batched launches vs the same runs stepped one by one")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.sort_period is None:
+        # the fastest setting measured per workload: unsorted markers on the 1D
+        # grids (the tile copies sit in shared memory), a quarter-cell sort every
+        # second step on the 2D3V grid (the deposit's runs need sorted markers)
+        args.sort_period = 2 if args.weibel2d else 0
+    return args
 
 
 def dist_env():

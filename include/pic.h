@@ -137,10 +137,12 @@ typedef struct {
                             /* Ampere solver: 1 = kept sorted by (cell, sign  */
                             /* of v) every step, written in key order by the  */
                             /* update pass; P > 1 = counting sort by cell     */
-                            /* every P steps.  Yee solver: P >= 1 = counting  */
-                            /* sort by quarter cell every P steps, and each   */
-                            /* warp's deposits summed over its lanes' equal   */
-                            /* stencils before the atomics.  Sorting only     */
+                            /* every P steps.  Yee solver: P >= 1 = the       */
+                            /* update pass of every P-th step writes them in  */
+                            /* quarter-cell order, and each thread's run of   */
+                            /* consecutive markers in one quarter cell sums   */
+                            /* its deposits in registers, the runs over the   */
+                            /* warp, before the atomics.  Sorting only        */
                             /* reorders markers (pic_get_ids maps them).      */
   int remove_mean;          /* ES: 1 -> E -= dt (J - <J>), 0 -> E -= dt J     */
   int gamma_on;             /* 1 = energy correction; 0 = naive scheme        */

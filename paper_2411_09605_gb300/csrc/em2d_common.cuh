@@ -1,6 +1,7 @@
 // Grid helpers shared by the FP64 and mixed forms of the 2D3V Yee step
 // (Sec. 4.1, Eq. EMleapfrog): periodic index wrap, the discrete curls on the
-// staggered lattice, and a block sum.  Both forms advance the fields with the
+// staggered lattice, a block sum, the B update with the field energies (K5)
+// and the step's total energy.  Both forms advance the fields with the
 // same FP64 curls, so their field energies are computed the same way.
 #pragma once
 
@@ -48,6 +49,44 @@ __device__ __forceinline__ double curl_e(const Em2dConst &c, const double *E, in
   if (d == 0) return (Ez[jp * nx + i] - Ez[j * nx + i]) * c.inv_hy;
   if (d == 1) return -(Ez[j * nx + ip] - Ez[j * nx + i]) * c.inv_hx;
   return (Ey[j * nx + ip] - Ey[j * nx + i]) * c.inv_hx - (Ex[jp * nx + i] - Ex[j * nx + i]) * c.inv_hy;
+}
+
+// K5 as block blk of nblk: B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1} and the
+// block's partials of W_E and W_B (wf_part[2 blk], wf_part[2 blk + 1])
+__device__ __forceinline__ void k5_block(const Em2dConst &c, const Em2dBufs &b, int blk, int nblk,
+                                         double *red) {
+  const int nc = c.nx * c.ny;
+  double we = 0.0, wb = 0.0;
+  for (int a = blk * blockDim.x + threadIdx.x; a < 3 * nc; a += nblk * blockDim.x) {
+    const int d = a / nc, ij = a % nc, i = ij % c.nx, j = ij / c.nx;
+    const double bpp = b.Bp[a] - c.dt * curl_e(c, b.En, i, j, d);
+    b.Bpp[a] = bpp;
+    we += b.En[a] * b.En[a];
+    wb += b.Bp[a] * bpp;
+  }
+  double t = block_sum2(we, red);
+  if (threadIdx.x == 0) b.wf_part[2 * blk] = t;
+  t = block_sum2(wb, red);
+  if (threadIdx.x == 0) b.wf_part[2 * blk + 1] = t;
+}
+
+// TE of the step in slot from its nkb kinetic and nfb field partials (one block)
+__device__ __forceinline__ void finalize_block(const Em2dConst &c, const Em2dBufs &b, int slot,
+                                               int nkb, int nfb, double *red) {
+  double ke = 0.0, we = 0.0, wb = 0.0;
+  for (int i = threadIdx.x; i < nkb; i += blockDim.x) ke += b.ke_part[i];
+  for (int i = threadIdx.x; i < nfb; i += blockDim.x) {
+    we += b.wf_part[2 * i];
+    wb += b.wf_part[2 * i + 1];
+  }
+  const double k = block_sum2(ke, red);
+  const double e = block_sum2(we, red);
+  const double m = block_sum2(wb, red);
+  if (threadIdx.x == 0) {
+    const double te = k + 0.5 * c.area * e + 0.5 * c.c2 * c.area * m;
+    b.te[slot] = te;
+    if (!isfinite(te)) atomicOr(b.err, kErrNonfinite);
+  }
 }
 
 }  // namespace

@@ -33,6 +33,7 @@
 #include <type_traits>
 
 #include "em2d_common.cuh"
+#include "pdl.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -257,19 +258,9 @@ __global__ void em_k3_kernel(Em2dConst c, Em2dBufs b) {
 // K5: B^{n+3/2} = Bp - dt curl E^{n+1}, block partials of W_E and W_B
 __global__ void __launch_bounds__(256) em_k5_kernel(Em2dConst c, Em2dBufs b) {
   __shared__ double red[33];
-  const int nc = c.nx * c.ny;
-  double we = 0.0, wb = 0.0;
-  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < 3 * nc; a += gridDim.x * blockDim.x) {
-    const int d = a / nc, ij = a % nc, i = ij % c.nx, j = ij / c.nx;
-    const double bpp = b.Bp[a] - c.dt * curl_e(c, b.En, i, j, d);
-    b.Bpp[a] = bpp;
-    we += b.En[a] * b.En[a];
-    wb += b.Bp[a] * bpp;
-  }
-  double t = block_sum2(we, red);
-  if (threadIdx.x == 0) b.wf_part[2 * blockIdx.x] = t;
-  t = block_sum2(wb, red);
-  if (threadIdx.x == 0) b.wf_part[2 * blockIdx.x + 1] = t;
+  griddep_wait();
+  griddep_launch_dependents();
+  k5_block(c, b, blockIdx.x, gridDim.x, red);
 }
 
 template <int ORDER, bool CC>
@@ -396,23 +387,11 @@ __global__ void em_bhalf_kernel(Em2dConst c, const double *B, const double *E, d
 }
 
 // TE of the step in slot: KE partials + field partials
-__global__ void em_finalize_kernel(Em2dBufs b, int slot, int nkb, int nfb, double we_scale,
-                                   double wb_scale) {
+__global__ void em_finalize_kernel(Em2dConst c, Em2dBufs b, int slot, int nkb, int nfb) {
   __shared__ double red[33];
-  double ke = 0.0, we = 0.0, wb = 0.0;
-  for (int i = threadIdx.x; i < nkb; i += blockDim.x) ke += b.ke_part[i];
-  for (int i = threadIdx.x; i < nfb; i += blockDim.x) {
-    we += b.wf_part[2 * i];
-    wb += b.wf_part[2 * i + 1];
-  }
-  double k = block_sum2(ke, red);
-  double e = block_sum2(we, red);
-  double m = block_sum2(wb, red);
-  if (threadIdx.x == 0) {
-    double te = k + we_scale * e + wb_scale * m;
-    b.te[slot] = te;
-    if (!isfinite(te)) atomicOr(b.err, kErrNonfinite);
-  }
+  griddep_wait();
+  griddep_launch_dependents();
+  finalize_block(c, b, slot, nkb, nfb, red);
 }
 
 __global__ void __launch_bounds__(256) em_kinetic_kernel(Em2dConst c, Em2dBufs b, double *out) {
@@ -458,14 +437,14 @@ void em2d_pass_e(const Em2dConst &c, const Em2dBufs &b, int slot, LaunchShape lp
     em_pass_e_kernel<2, false><<<lp.grid, lp.block, 0, st>>>(c, b, slot);
 }
 
-void em2d_k5(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st) {
-  em_k5_kernel<<<lg.grid, 256, 0, st>>>(c, b);
+void em2d_k5(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st, bool pdl) {
+  launch_dependent(em_k5_kernel, LaunchShape{lg.grid, 256}, 0, st, pdl, c, b);
 }
 
 void em2d_finalize(const Em2dConst &c, const Em2dBufs &b, int slot, LaunchShape lp,
-                   LaunchShape lg, cudaStream_t st) {
-  em_finalize_kernel<<<1, 256, 0, st>>>(b, slot, lp.grid, lg.grid, 0.5 * c.area,
-                                        0.5 * c.c2 * c.area);
+                   LaunchShape lg, cudaStream_t st, bool pdl) {
+  launch_dependent(em_finalize_kernel, LaunchShape{1, 256}, 0, st, pdl, c, b, slot, lp.grid,
+                   lg.grid);
 }
 
 __global__ void em2d_validate_kernel(const double *x, const double *y, const double *vx,

@@ -17,7 +17,10 @@
 //     integers s_x s_y, as Eq. exp_econs_simple requires.
 //   * current: each marker adds round(V*_c s_x s_y / 2^r) (r >= 32, so no
 //     node sum overflows) to the int64 node sums with global atomics: exact
-//     integer sums, independent of the marker order.
+//     integer sums, independent of the marker order.  With sort_period P the
+//     markers are kept in quarter-cell order (written so by pass E every P
+//     steps), and the terms of a thread's consecutive markers in one quarter
+//     cell are summed in registers and then over the warp before the atomics.
 //   * gather #1 (E*, B at x*) only shapes v*: FP32 tables and FP32 weights;
 //     v* = (u + u x t + (u.t) t) / (1 + |t|^2) as u plus an FP32 correction.
 //   * gather #2: kick E^{n+1/2} as float pairs with error-free products, so
@@ -35,6 +38,7 @@
 #include "em2d_common.cuh"
 #include "ff.cuh"
 #include "mixed_common.cuh"
+#include "pdl.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -207,41 +211,98 @@ struct WarpSegments {
   }
 };
 
-// deposit_c for cell-sorted markers, called by every lane of the warp
-// (valid = the lane holds a marker): the segment's sums, added by its last lane
-template <int ORDER>
-__device__ __forceinline__ void deposit_c_seg(long long *J, int nx, const AxisMix<ORDER> &ax,
-                                              const AxisMix<ORDER> &ay, int V, bool valid,
-                                              const Em2dMixConst &c) {
-  const WarpSegments seg(valid ? ax.k[0] + nx * ay.k[0] : -1 - (int)(threadIdx.x & 31u));
-  const bool neg = V < 0;
-  const uint32_t mag = neg ? 0u - (uint32_t)V : (uint32_t)V;
-#pragma unroll
-  for (int b = 0; b <= ORDER; b++) {
-    const uint64_t m = (uint64_t)mag * ay.s[b];
-    long long *row = J + ay.k[b] * nx;
-#pragma unroll
-    for (int a = 0; a <= ORDER; a++) {
-      const long long sum = seg.scan(valid ? deposit_term(m, ax.s[a], neg, c) : 0ll);
-      if (seg.tail && valid && sum != 0)
-        atomicAdd((unsigned long long *)(row + ax.k[a]), (unsigned long long)sum);
-    }
-  }
+// The quarter cell floor(2x / hx) + 2 nx floor(2y / hy) of a point: within a
+// quarter cell every current component's stencil starts at the same node
+// (order 1 and 2, integer and half nodes).
+__device__ __forceinline__ int quarter_key(uint32_t X, uint32_t Y, int nx, int ny) {
+  const int qx = (int)(((uint64_t)X * (uint32_t)(2 * nx)) >> 32);
+  const int qy = (int)(((uint64_t)Y * (uint32_t)(2 * ny)) >> 32);
+  return qx + 2 * nx * qy;
 }
 
-template <int ORDER, bool SORTED>
-__device__ __forceinline__ void deposit_j_any(const Em2dMixConst &c, long long *J,
-                                              const Shape2Mix<ORDER> &S, const int V[3],
-                                              bool valid) {
-  if (SORTED) {
-    const int nx = c.nx, nc = c.nx * c.ny;
-    deposit_c_seg<ORDER>(J, nx, S.xH, S.yI, V[0], valid, c);
-    deposit_c_seg<ORDER>(J + nc, nx, S.xI, S.yH, V[1], valid, c);
-    deposit_c_seg<ORDER>(J + 2 * nc, nx, S.xI, S.yI, V[2], valid, c);
-  } else if (valid) {
-    deposit_j<ORDER>(c, J, S, V);
+// The deposits of a thread's consecutive markers (sorted by quarter cell),
+// summed in registers while they fall in one quarter cell: a marker in
+// another quarter cell first sends the run's sums to the grid, and the last
+// run of each thread goes through the warp's segmented sums (flush_warp), one
+// atomic per segment and node.  The sums are exact integers, so the grid gets
+// the per-marker atomics' result bit for bit, in any order.
+template <int ORDER>
+struct DepositRun {
+  static constexpr int K = (ORDER + 1) * (ORDER + 1);
+  long long s[3][K];  // Jx, Jy, Jz terms, node (a, b) at b (ORDER + 1) + a
+  int key;            // quarter cell of the run, or -1 - lane while empty
+  uint32_t X, Y;      // a deposit point of the run
+
+  __device__ __forceinline__ explicit DepositRun(unsigned lane)
+      : key(-1 - (int)lane), X(0u), Y(0u) {
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+      for (int t = 0; t < K; t++) s[d][t] = 0;
   }
-}
+
+  __device__ __forceinline__ static void add_terms(const AxisMix<ORDER> &ax,
+                                                   const AxisMix<ORDER> &ay, int V,
+                                                   const Em2dMixConst &c, long long *t) {
+    const bool neg = V < 0;
+    const uint32_t mag = neg ? 0u - (uint32_t)V : (uint32_t)V;
+#pragma unroll
+    for (int b = 0; b <= ORDER; b++) {
+      const uint64_t m = (uint64_t)mag * ay.s[b];
+#pragma unroll
+      for (int a = 0; a <= ORDER; a++) t[b * (ORDER + 1) + a] += deposit_term(m, ax.s[a], neg, c);
+    }
+  }
+
+  // sums v[d][t] into the nodes of the run's stencil (zero sums skipped)
+  template <typename F>
+  __device__ __forceinline__ void to_grid(const Em2dMixConst &c, long long *J, F &&sum) const {
+    const int nx = c.nx, nc = c.nx * c.ny;
+    const Shape2Mix<ORDER> S(X, Y, c.nx, c.ny);
+    const AxisMix<ORDER> *ax[3] = {&S.xH, &S.xI, &S.xI}, *ay[3] = {&S.yI, &S.yH, &S.yI};
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+      for (int b = 0; b <= ORDER; b++)
+#pragma unroll
+        for (int a = 0; a <= ORDER; a++) {
+          const long long v = sum(d, b * (ORDER + 1) + a);
+          if (v != 0)
+            atomicAdd((unsigned long long *)(J + d * nc + ay[d]->k[b] * nx + ax[d]->k[a]),
+                      (unsigned long long)v);
+        }
+  }
+
+  // one marker with deposit point (Xd, Yd), shape S there and velocity V
+  __device__ __forceinline__ void add(const Em2dMixConst &c, long long *J, uint32_t Xd,
+                                      uint32_t Yd, const Shape2Mix<ORDER> &S, const int V[3]) {
+    const int k = quarter_key(Xd, Yd, c.nx, c.ny);
+    if (k != key) {
+      if (key >= 0) to_grid(c, J, [&](int d, int i) { return s[d][i]; });
+      key = k;
+      X = Xd;
+      Y = Yd;
+#pragma unroll
+      for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int i = 0; i < K; i++) s[d][i] = 0;
+    }
+    add_terms(S.xH, S.yI, V[0], c, s[0]);
+    add_terms(S.xI, S.yH, V[1], c, s[1]);
+    add_terms(S.xI, S.yI, V[2], c, s[2]);
+  }
+
+  // called by every lane of the warp: the last lane of each segment of equal
+  // keys adds the segment's sums
+  __device__ __forceinline__ void flush_warp(const Em2dMixConst &c, long long *J) {
+    const WarpSegments seg(key);
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+      for (int i = 0; i < K; i++) s[d][i] = seg.scan(s[d][i]);
+    if (seg.tail && key >= 0) to_grid(c, J, [&](int d, int i) { return s[d][i]; });
+  }
+};
 
 __device__ __forceinline__ void report_bad(unsigned bad, unsigned *err) {
   bad = __reduce_or_sync(0xffffffffu, bad);
@@ -256,7 +317,7 @@ __device__ __forceinline__ ff ff_from_int(int V) {
 
 // The non-series path of correct_velocity3: the R < 0 test and Gamma - 1 in
 // FP64 (mixed_common.cuh); returns false for the fallback.
-__device__ __noinline__ bool gamma3_fp64(float vh0, float vh1, float vh2, float vl0, float vl1,
+__device__ __forceinline__ bool gamma3_fp64(float vh0, float vh1, float vh2, float vl0, float vl1,
                                          float vl2, int V0, int V1, int V2, ff D0, ff D1, ff D2,
                                          ff u0, ff u1, ff u2, double &g) {
   const double a = ff_to_double(D0) * bracket_fp64(vh0, vl0, V0, D0) +
@@ -320,10 +381,21 @@ __device__ __forceinline__ void correct_velocity3(const float vh[3], const float
 }
 
 // K1: e_half E* (ESEC2: E^n + dt/2 (c^2 curl B^{n+1/2} - j^{n,*}); ESEC1: E^n)
-// and t_half B^{n+1/2} as FP32 tables; clear J2
-__global__ void mix2_k1_kernel(Em2dConst c, Em2dMixConst m, Em2dMixBufs mb, Em2dBufs b) {
+// and t_half B^{n+1/2} as FP32 tables; clear J2.  One more block may reduce
+// the previous step's total energy (its partials are complete).
+__global__ void mix2_k1_kernel(Em2dConst c, Em2dMixConst m, Em2dMixBufs mb, Em2dBufs b,
+                               int fin_slot, int nkb, int nfb) {
+  griddep_wait();
+  griddep_launch_dependents();
+  // with fin_slot >= 0 the last block reduces the previous step's TE instead
+  const int nb = fin_slot >= 0 ? (int)gridDim.x - 1 : (int)gridDim.x;
+  if ((int)blockIdx.x == nb) {
+    __shared__ double red[33];
+    finalize_block(c, b, fin_slot, nkb, nfb, red);
+    return;
+  }
   const int nc = c.nx * c.ny;
-  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < 3 * nc; a += gridDim.x * blockDim.x) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < 3 * nc; a += nb * blockDim.x) {
     const int d = a / nc, ij = a % nc, i = ij % c.nx, j = ij / c.nx;
     double es = b.E[a];
     if (m.scheme == 2)
@@ -336,6 +408,8 @@ __global__ void mix2_k1_kernel(Em2dConst c, Em2dMixConst m, Em2dMixBufs mb, Em2d
 
 // K3: E^{n+1} (FP64), kick E^{n+1/2} as float pairs, m_full B^{n+1/2}; clear J1
 __global__ void mix2_k3_kernel(Em2dConst c, Em2dMixConst m, Em2dMixBufs mb, Em2dBufs b) {
+  griddep_wait();
+  griddep_launch_dependents();
   const int nc = c.nx * c.ny;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < 3 * nc; a += gridDim.x * blockDim.x) {
     const int d = a / nc, ij = a % nc, i = ij % c.nx, j = ij / c.nx;
@@ -349,128 +423,251 @@ __global__ void mix2_k3_kernel(Em2dConst c, Em2dMixConst m, Em2dMixBufs mb, Em2d
   }
 }
 
-// Pass C: x*, E* and B at x*, v* (integer V*), x^{n+1/2}, deposit of j^{*,n+1/2}
-template <int ORDER, bool SORTED>
-__global__ void __launch_bounds__(256) mix2_pass_c_kernel(Em2dMixConst c, Em2dMixBufs b) {
+// Pass C for marker p up to v*: x*, E* and B at x*, the integer V* (stored)
+// and the deposit point x^{n+1/2} = (Xd, Yd)
+template <int ORDER>
+__device__ __forceinline__ void pass_c_marker(const Em2dMixConst &c, const Em2dMixBufs &b,
+                                              int64_t p, unsigned &bad, int Vs[3],
+                                              uint32_t &Xd, uint32_t &Yd) {
   const int nx = c.nx, nc = c.nx * c.ny;
+  const uint32_t X = b.X[p], Y = b.Y[p];
+  float vh[3], vl[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    vh[d] = b.vh[d][p];
+    vl[d] = b.vl[d][p];
+  }
+  const Shape2Mix<ORDER> S1(X + half_shift(to_fixed(vh[0], bad), c),
+                            Y + half_shift(to_fixed(vh[1], bad), c), c.nx, c.ny);
+  const float *T = b.T1;
+  float e[3], t[3];
+  e[0] = gather_f<ORDER>(T, nx, S1.xH, S1.yI);
+  e[1] = gather_f<ORDER>(T + nc, nx, S1.xI, S1.yH);
+  e[2] = gather_f<ORDER>(T + 2 * nc, nx, S1.xI, S1.yI);
+  t[0] = gather_f<ORDER>(T + 3 * nc, nx, S1.xI, S1.yH);
+  t[1] = gather_f<ORDER>(T + 4 * nc, nx, S1.xH, S1.yI);
+  t[2] = gather_f<ORDER>(T + 5 * nc, nx, S1.xH, S1.yH);
+  // v* - v* x t = u = v^n + e: v* = u + (u x t + (u.t) t - |t|^2 u) / (1 + |t|^2)
+  float u[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) u[d] = __fadd_rn(vh[d], e[d]);
+  const float ut = __fmaf_rn(u[2], t[2], __fmaf_rn(u[1], t[1], __fmul_rn(u[0], t[0])));
+  const float tt = __fmaf_rn(t[2], t[2], __fmaf_rn(t[1], t[1], __fmul_rn(t[0], t[0])));
+  const float inv = __frcp_rn(__fadd_rn(1.0f, tt));
+  const float r[3] = {__fsub_rn(__fmul_rn(u[1], t[2]), __fmul_rn(u[2], t[1])),
+                      __fsub_rn(__fmul_rn(u[2], t[0]), __fmul_rn(u[0], t[2])),
+                      __fsub_rn(__fmul_rn(u[0], t[1]), __fmul_rn(u[1], t[0]))};
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    const float corr = __fmul_rn(__fmaf_rn(ut, t[d], __fmaf_rn(-tt, u[d], r[d])), inv);
+    Vs[d] = vstar_fixed(vh[d], vl[d], __fadd_rn(e[d], corr), bad);
+  }
+  Xd = X + half_shift(Vs[0], c);
+  Yd = Y + half_shift(Vs[1], c);
+}
+
+// The lanes of a warp with equal keys (a match over the warp) take their
+// slots in cnt[key] with one atomic: each lane gets the old count plus its
+// rank among them.  Called by all 32 lanes; a lane with key < 0 has no
+// marker (its key is -1 - lane, so it matches no other lane).
+__device__ __forceinline__ unsigned warp_slot(unsigned *cnt, int key) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned grp = __match_any_sync(0xffffffffu, key);
+  const int leader = __ffs(grp) - 1;
+  unsigned base = 0u;
+  if (key >= 0 && lane == (unsigned)leader) base = atomicAdd(&cnt[key], (unsigned)__popc(grp));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return base + (unsigned)__popc(grp & ((1u << lane) - 1u));
+}
+
+// Markers a thread takes in a row on sorted markers, their deposits summed in
+// a DepositRun: each warp takes 32 kRunMarkers consecutive markers, lane l
+// those from kRunMarkers l on (every lane the same trips).  Unsorted markers:
+// one per thread and trip, per-marker atomics.
+constexpr int kRunMarkers = 4;
+
+// Pass C: x*, E* and B at x*, v* (integer V*), x^{n+1/2}, deposit of j^{*,n+1/2};
+// on sorted markers, with cnt set (the step that ends a sort period), the
+// count of each quarter cell of x^{n+1} = X + 2 [V*]
+template <int ORDER, bool SORTED>
+__global__ void __launch_bounds__(256, SORTED ? (ORDER == 1 ? 3 : 2) : 0)
+    mix2_pass_c_kernel(Em2dMixConst c, Em2dMixBufs b, unsigned *cnt) {
+  griddep_wait();
+  griddep_launch_dependents();
+  const unsigned lane = threadIdx.x & 31u;
   unsigned bad = 0;
-  // every lane of a warp runs the same trips (the sorted deposit sums over the warp)
-  for (int64_t pw = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); pw < c.n;
-       pw += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = pw + (threadIdx.x & 31u);
-    const bool valid = p < c.n;
-    if (!SORTED && !valid) break;
-    const int64_t q = valid ? p : c.n - 1;
-    const uint32_t X = b.X[q], Y = b.Y[q];
-    float vh[3], vl[3];
+  if constexpr (SORTED) {
+    constexpr int M = kRunMarkers;
+    for (int64_t pw = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u)) * M; pw < c.n;
+         pw += (int64_t)gridDim.x * blockDim.x * M) {
+      DepositRun<ORDER> run(lane);
+#pragma unroll 1
+      for (int j = 0; j < M; j++) {
+        const int64_t p = pw + (int64_t)lane * M + j;
+        int key = -1 - (int)lane;
+        if (p < c.n) {
+          int Vs[3];
+          uint32_t Xd, Yd;
+          pass_c_marker<ORDER>(c, b, p, bad, Vs, Xd, Yd);
+          run.add(c, b.J2, Xd, Yd, Shape2Mix<ORDER>(Xd, Yd, c.nx, c.ny), Vs);
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-      vh[d] = b.vh[d][q];
-      vl[d] = b.vl[d][q];
+          for (int d = 0; d < 3; d++) b.Vs[d][p] = Vs[d];
+          key = quarter_key(Xd + half_shift(Vs[0], c), Yd + half_shift(Vs[1], c), c.nx, c.ny);
+        }
+        if (cnt) warp_slot(cnt, key);
+      }
+      run.flush_warp(c, b.J2);
     }
-    const Shape2Mix<ORDER> S1(X + half_shift(to_fixed(vh[0], bad), c),
-                              Y + half_shift(to_fixed(vh[1], bad), c), c.nx, c.ny);
-    const float *T = b.T1;
-    float e[3], t[3];
-    e[0] = gather_f<ORDER>(T, nx, S1.xH, S1.yI);
-    e[1] = gather_f<ORDER>(T + nc, nx, S1.xI, S1.yH);
-    e[2] = gather_f<ORDER>(T + 2 * nc, nx, S1.xI, S1.yI);
-    t[0] = gather_f<ORDER>(T + 3 * nc, nx, S1.xI, S1.yH);
-    t[1] = gather_f<ORDER>(T + 4 * nc, nx, S1.xH, S1.yI);
-    t[2] = gather_f<ORDER>(T + 5 * nc, nx, S1.xH, S1.yH);
-    // v* - v* x t = u = v^n + e: v* = u + (u x t + (u.t) t - |t|^2 u) / (1 + |t|^2)
-    float u[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) u[d] = __fadd_rn(vh[d], e[d]);
-    const float ut = __fmaf_rn(u[2], t[2], __fmaf_rn(u[1], t[1], __fmul_rn(u[0], t[0])));
-    const float tt = __fmaf_rn(t[2], t[2], __fmaf_rn(t[1], t[1], __fmul_rn(t[0], t[0])));
-    const float inv = __frcp_rn(__fadd_rn(1.0f, tt));
-    const float r[3] = {__fsub_rn(__fmul_rn(u[1], t[2]), __fmul_rn(u[2], t[1])),
-                        __fsub_rn(__fmul_rn(u[2], t[0]), __fmul_rn(u[0], t[2])),
-                        __fsub_rn(__fmul_rn(u[0], t[1]), __fmul_rn(u[1], t[0]))};
-    int Vs[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-      const float corr = __fmul_rn(__fmaf_rn(ut, t[d], __fmaf_rn(-tt, u[d], r[d])), inv);
-      Vs[d] = vstar_fixed(vh[d], vl[d], __fadd_rn(e[d], corr), bad);
-    }
-    const Shape2Mix<ORDER> Sh(X + half_shift(Vs[0], c), Y + half_shift(Vs[1], c), c.nx, c.ny);
-    deposit_j_any<ORDER, SORTED>(c, b.J2, Sh, Vs, valid);
-    if (valid)
+  } else {
+    for (int64_t pw = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); pw < c.n;
+         pw += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t p = pw + lane;
+      if (p >= c.n) break;
+      int Vs[3];
+      uint32_t Xd, Yd;
+      pass_c_marker<ORDER>(c, b, p, bad, Vs, Xd, Yd);
+      deposit_j<ORDER>(c, b.J2, Shape2Mix<ORDER>(Xd, Yd, c.nx, c.ny), Vs);
 #pragma unroll
       for (int d = 0; d < 3; d++) b.Vs[d][p] = Vs[d];
+    }
   }
   report_bad(bad, b.err);
 }
 
-// Pass E: gather at x^{n+1/2} = X + [V*], v^dag, Gamma, x^{n+1}, v^{n+1}, the
-// kinetic energy and (ESEC2) the next step's j^{n+1,*}
-template <int ORDER, bool SORTED>
-__global__ void __launch_bounds__(256) mix2_pass_e_kernel(Em2dMixConst c, Em2dMixBufs b,
-                                                          int slot) {
-  __shared__ double red[33];
+// Pass E for marker p: the gather at x^{n+1/2} = X + [V*], v^dag, Gamma,
+// the kinetic energy; returns x^{n+1} = (Xn, Yn), v^{n+1} = vn and (ESEC2)
+// the next step's deposit point (Xd, Yd) and V* estimate Vn1
+template <int ORDER>
+__device__ __forceinline__ void pass_e_marker(const Em2dMixConst &c, const Em2dMixBufs &b,
+                                              int64_t p, unsigned &bad, unsigned &nfb,
+                                              float &ke_hi, float &ke_lo, int Vn1[3],
+                                              uint32_t &Xd, uint32_t &Yd, uint32_t &Xn,
+                                              uint32_t &Yn, ff vn[3]) {
   const int nx = c.nx, nc = c.nx * c.ny;
+  const uint32_t X = b.X[p], Y = b.Y[p];
+  float vh[3], vl[3];
+  int Vs[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    vh[d] = b.vh[d][p];
+    vl[d] = b.vl[d][p];
+    Vs[d] = b.Vs[d][p];
+  }
+  const uint32_t hx = half_shift(Vs[0], c), hy = half_shift(Vs[1], c);
+  const Shape2Mix<ORDER> S(X + hx, Y + hy, c.nx, c.ny);
+  ff D[3];
+  D[0] = gather_ff<ORDER>(b.T2, nx, S.xH, S.yI);
+  D[1] = gather_ff<ORDER>(b.T2 + nc, nx, S.xI, S.yH);
+  D[2] = gather_ff<ORDER>(b.T2 + 2 * nc, nx, S.xI, S.yI);
+  const float bb[3] = {gather_f<ORDER>(b.B2, nx, S.xI, S.yH),
+                       gather_f<ORDER>(b.B2 + nc, nx, S.xH, S.yI),
+                       gather_f<ORDER>(b.B2 + 2 * nc, nx, S.xH, S.yH)};
+  // Delta = d + dt (q/m) V* x B, the cross product in float pairs of the exact V*
+  const ff vs[3] = {ff_from_int(Vs[0]), ff_from_int(Vs[1]), ff_from_int(Vs[2])};
+  D[0] = ff_add(D[0], ff_sub(ff_mul_f(vs[1], bb[2]), ff_mul_f(vs[2], bb[1])));
+  D[1] = ff_add(D[1], ff_sub(ff_mul_f(vs[2], bb[0]), ff_mul_f(vs[0], bb[2])));
+  D[2] = ff_add(D[2], ff_sub(ff_mul_f(vs[0], bb[1]), ff_mul_f(vs[1], bb[0])));
+  correct_velocity3(vh, vl, Vs, D, c.gamma_on != 0, nfb, vn);
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    ff s2 = two_prod(vn[d].hi, vn[d].hi);
+    s2.lo = __fmaf_rn(__fadd_rn(vn[d].hi, vn[d].hi), vn[d].lo, s2.lo);
+    const ff acc = two_sum(ke_hi, s2.hi);
+    ke_hi = acc.hi;
+    ke_lo = __fadd_rn(ke_lo, __fadd_rn(acc.lo, s2.lo));
+  }
+  Xn = X + 2u * hx;
+  Yn = Y + 2u * hy;
+  if (c.scheme == 2) {
+#pragma unroll
+    for (int d = 0; d < 3; d++) Vn1[d] = to_fixed(vn[d].hi, bad);
+    Xd = Xn + half_shift(Vn1[0], c);
+    Yd = Yn + half_shift(Vn1[1], c);
+  }
+#pragma unroll
+  for (int d = 0; d < 3; d++)
+    if (!isfinite(vn[d].hi)) bad |= kErrNonfinite;
+}
+
+__device__ __forceinline__ void store_marker(const Em2dMixBufs &b, int64_t q, uint32_t Xn,
+                                             uint32_t Yn, const ff vn[3]) {
+  b.X[q] = Xn;
+  b.Y[q] = Yn;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    b.vh[d][q] = vn[d].hi;
+    b.vl[d][q] = vn[d].lo;
+  }
+}
+
+// Pass E: gather at x^{n+1/2} = X + [V*], v^dag, Gamma, x^{n+1}, v^{n+1}, the
+// kinetic energy and (ESEC2) the next step's j^{n+1,*}.  On sorted markers
+// with so.off set (the step that ends a sort period) each marker goes to the
+// next free slot of its quarter cell in so.dst (its id with it), else back to
+// its own slot.
+//
+// The last nk5 blocks run K5 on the FP64 fields (fc, fb) instead: it reads
+// E^{n+1} and B^{n+1/2} and writes B^{n+3/2} and the field energies, nothing
+// the markers touch.
+template <int ORDER, bool SORTED>
+__global__ void __launch_bounds__(256, SORTED ? 2 : 0)
+    mix2_pass_e_kernel(Em2dMixConst c, Em2dMixBufs b, int slot, Em2dSortIO so, Em2dConst fc,
+                       Em2dBufs fb, int nk5) {
+  __shared__ double red[33];
+  griddep_wait();
+  griddep_launch_dependents();
+  const int npass = (int)gridDim.x - nk5;
+  if ((int)blockIdx.x >= npass) {
+    k5_block(fc, fb, (int)blockIdx.x - npass, nk5, red);
+    return;
+  }
+  const unsigned lane = threadIdx.x & 31u;
   float ke_hi = 0.0f, ke_lo = 0.0f;
   unsigned nfb = 0, bad = 0;
-  for (int64_t pw = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); pw < c.n;
-       pw += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = pw + (threadIdx.x & 31u);
-    const bool valid = p < c.n;
-    if (!SORTED && !valid) break;
-    const int64_t q = valid ? p : c.n - 1;
-    const uint32_t X = b.X[q], Y = b.Y[q];
-    float vh[3], vl[3];
-    int Vs[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-      vh[d] = b.vh[d][q];
-      vl[d] = b.vl[d][q];
-      Vs[d] = b.Vs[d][q];
-    }
-    const uint32_t hx = half_shift(Vs[0], c), hy = half_shift(Vs[1], c);
-    const Shape2Mix<ORDER> S(X + hx, Y + hy, c.nx, c.ny);
-    ff D[3];
-    D[0] = gather_ff<ORDER>(b.T2, nx, S.xH, S.yI);
-    D[1] = gather_ff<ORDER>(b.T2 + nc, nx, S.xI, S.yH);
-    D[2] = gather_ff<ORDER>(b.T2 + 2 * nc, nx, S.xI, S.yI);
-    const float bb[3] = {gather_f<ORDER>(b.B2, nx, S.xI, S.yH),
-                         gather_f<ORDER>(b.B2 + nc, nx, S.xH, S.yI),
-                         gather_f<ORDER>(b.B2 + 2 * nc, nx, S.xH, S.yH)};
-    // Delta = d + dt (q/m) V* x B, the cross product in float pairs of the exact V*
-    const ff vs[3] = {ff_from_int(Vs[0]), ff_from_int(Vs[1]), ff_from_int(Vs[2])};
-    D[0] = ff_add(D[0], ff_sub(ff_mul_f(vs[1], bb[2]), ff_mul_f(vs[2], bb[1])));
-    D[1] = ff_add(D[1], ff_sub(ff_mul_f(vs[2], bb[0]), ff_mul_f(vs[0], bb[2])));
-    D[2] = ff_add(D[2], ff_sub(ff_mul_f(vs[0], bb[1]), ff_mul_f(vs[1], bb[0])));
-    ff vn[3];
-    correct_velocity3(vh, vl, Vs, D, c.gamma_on != 0 && valid, nfb, vn);
-    if (!valid)
-#pragma unroll
-      for (int d = 0; d < 3; d++) vn[d] = ff{0.0f, 0.0f};
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-      ff s2 = two_prod(vn[d].hi, vn[d].hi);
-      s2.lo = __fmaf_rn(__fadd_rn(vn[d].hi, vn[d].hi), vn[d].lo, s2.lo);
-      const ff acc = two_sum(ke_hi, s2.hi);
-      ke_hi = acc.hi;
-      ke_lo = __fadd_rn(ke_lo, __fadd_rn(acc.lo, s2.lo));
-    }
-    const uint32_t Xn = X + 2u * hx, Yn = Y + 2u * hy;
-    if (c.scheme == 2) {
-      const int Vn1[3] = {to_fixed(vn[0].hi, bad), to_fixed(vn[1].hi, bad),
-                          to_fixed(vn[2].hi, bad)};
-      const Shape2Mix<ORDER> S1(Xn + half_shift(Vn1[0], c), Yn + half_shift(Vn1[1], c), c.nx,
-                                c.ny);
-      deposit_j_any<ORDER, SORTED>(c, b.J1, S1, Vn1, valid);
-    }
-    if (valid) {
-      b.X[p] = Xn;
-      b.Y[p] = Yn;
-#pragma unroll
-      for (int d = 0; d < 3; d++) {
-        b.vh[d][p] = vn[d].hi;
-        b.vl[d][p] = vn[d].lo;
-        if (!isfinite(vn[d].hi)) bad |= kErrNonfinite;
+  if constexpr (SORTED) {
+    constexpr int M = kRunMarkers;
+    for (int64_t pw = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u)) * M; pw < c.n;
+         pw += (int64_t)npass * blockDim.x * M) {
+      DepositRun<ORDER> run(lane);
+#pragma unroll 1
+      for (int j = 0; j < M; j++) {
+        const int64_t p = pw + (int64_t)lane * M + j;
+        const bool valid = p < c.n;
+        int key = -1 - (int)lane;
+        uint32_t Xn = 0u, Yn = 0u;
+        ff vn[3];
+        int Vn1[3];
+        uint32_t Xd = 0u, Yd = 0u;
+        if (valid) {
+          pass_e_marker<ORDER>(c, b, p, bad, nfb, ke_hi, ke_lo, Vn1, Xd, Yd, Xn, Yn, vn);
+          if (so.off)
+            key = quarter_key(Xn, Yn, c.nx, c.ny);
+          else
+            store_marker(b, p, Xn, Yn, vn);
+        }
+        if (so.off) {
+          const unsigned q = warp_slot(so.off, key);
+          if (valid) {
+            store_marker(so.dst, q, Xn, Yn, vn);
+            if (so.ids_in) so.ids_out[q] = so.ids_in[p];
+          }
+        }
+        if (valid && c.scheme == 2)
+          run.add(c, b.J1, Xd, Yd, Shape2Mix<ORDER>(Xd, Yd, c.nx, c.ny), Vn1);
       }
+      if (c.scheme == 2) run.flush_warp(c, b.J1);
+    }
+  } else {
+    for (int64_t pw = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); pw < c.n;
+         pw += (int64_t)npass * blockDim.x) {
+      const int64_t p = pw + lane;
+      if (p >= c.n) break;
+      int Vn1[3];
+      uint32_t Xd, Yd, Xn, Yn;
+      ff vn[3];
+      pass_e_marker<ORDER>(c, b, p, bad, nfb, ke_hi, ke_lo, Vn1, Xd, Yd, Xn, Yn, vn);
+      store_marker(b, p, Xn, Yn, vn);
+      if (c.scheme == 2) deposit_j<ORDER>(c, b.J1, Shape2Mix<ORDER>(Xd, Yd, c.nx, c.ny), Vn1);
     }
   }
   for (int o = 16; o > 0; o >>= 1) nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
@@ -559,101 +756,124 @@ __global__ void mix2_absmax_kernel(Em2dBufs b, int64_t n, unsigned long long *ou
 }
 
 // ------------------------------------------------------------ quarter-cell sort
-// The markers in the order of their quarter cell floor(2x / hx) + 2 nx
-// floor(2y / hy): within a quarter cell every current component's stencil
-// starts at the same node (order 1 and 2, integer and half nodes), so a
-// warp's deposits form few segments.  Counting sort: counts, their exclusive
-// scan, then each marker (and its id) to the next free slot of its key; the
-// order within a key is not fixed, which changes no result (the currents are
-// exact integer sums).
-__device__ __forceinline__ int quarter_key(uint32_t X, uint32_t Y, int nx, int ny) {
-  const int qx = (int)(((uint64_t)X * (uint32_t)(2 * nx)) >> 32);
-  const int qy = (int)(((uint64_t)Y * (uint32_t)(2 * ny)) >> 32);
-  return qx + 2 * nx * qy;
-}
+// The markers in the order of their quarter cell (quarter_key), written so by
+// pass E of the step that ends a sort period: pass C counts the quarter cells
+// of x^{n+1} (known once V* is), the scan below turns the counts into
+// offsets, and pass E puts each marker (and its id) at the next free slot of
+// its quarter cell.  The order within a quarter cell is not fixed, which
+// changes no result (the currents are exact integer sums).
+//
+// Exclusive scan of cnt[0 .. nk) into off[] (nk a multiple of 4) in tiles of
+// 4096 keys, a block of 1024 threads per tile, 4 keys a thread: the tiles'
+// totals first, then each tile's scan from the sum of the totals before it.
+// The second kernel leaves the counts zero for the next sort.
+constexpr int kScanThreads = 1024, kScanTile = 4 * kScanThreads;
 
-__global__ void mix2_sort_count_kernel(const uint32_t *X, const uint32_t *Y, int64_t n, int nx,
-                                       int ny, unsigned *cnt) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&cnt[quarter_key(X[p], Y[p], nx, ny)], 1u);
-}
-
-// Exclusive scan of cnt[0 .. nk) into off[] by one block of 1024 threads.
-__global__ void __launch_bounds__(1024) mix2_sort_scan_kernel(const unsigned *cnt, unsigned *off,
-                                                              int nk) {
-  __shared__ unsigned part[1024];
-  const int per = (nk + blockDim.x - 1) / blockDim.x;
-  const int beg = threadIdx.x * per, end = beg + per < nk ? beg + per : nk;
-  unsigned sum = 0;
-  for (int i = beg; i < end; i++) sum += cnt[i];
-  part[threadIdx.x] = sum;
+__device__ __forceinline__ unsigned block_sum_u(unsigned v, unsigned *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31u) == 0u) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-    const unsigned v = (int)threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  unsigned run = part[threadIdx.x] - sum;
-  for (int i = beg; i < end; i++) {
-    off[i] = run;
-    run += cnt[i];
-  }
+  unsigned t = 0;
+  for (int w = 0; w < kScanThreads / 32; w++) t += red[w];
+  return t;
 }
 
-__global__ void mix2_sort_move_kernel(Em2dMixBufs src, Em2dMixBufs dst, const int64_t *ids_in,
-                                      int64_t *ids_out, int64_t n, int nx, int ny, unsigned *off) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t X = src.X[p], Y = src.Y[p];
-    const unsigned slot = atomicAdd(&off[quarter_key(X, Y, nx, ny)], 1u);
-    dst.X[slot] = X;
-    dst.Y[slot] = Y;
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-      dst.vh[d][slot] = src.vh[d][p];
-      dst.vl[d][slot] = src.vl[d][p];
-    }
-    if (ids_in) ids_out[slot] = ids_in[p];
+__global__ void __launch_bounds__(kScanThreads) mix2_sort_tilesum_kernel(const unsigned *cnt,
+                                                                        int nk, unsigned *tsum) {
+  __shared__ unsigned red[kScanThreads / 32];
+  griddep_wait();
+  griddep_launch_dependents();
+  const int i = blockIdx.x * kScanTile + 4 * (int)threadIdx.x;
+  unsigned v = 0;
+  if (i < nk) {
+    const uint4 q = *(const uint4 *)(cnt + i);
+    v = q.x + q.y + q.z + q.w;
+  }
+  v = block_sum_u(v, red);
+  if (threadIdx.x == 0) tsum[blockIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) mix2_sort_offsets_kernel(unsigned *cnt, int nk,
+                                                                        const unsigned *tsum,
+                                                                        unsigned *off) {
+  __shared__ unsigned red[kScanThreads / 32];
+  __shared__ unsigned wsum[kScanThreads / 32];
+  griddep_wait();
+  griddep_launch_dependents();
+  unsigned before = 0;
+  for (int t = threadIdx.x; t < (int)blockIdx.x; t += kScanThreads) before += tsum[t];
+  before = block_sum_u(before, red);
+  const int i = blockIdx.x * kScanTile + 4 * (int)threadIdx.x;
+  uint4 q = make_uint4(0u, 0u, 0u, 0u);
+  if (i < nk) {
+    q = *(const uint4 *)(cnt + i);
+    *(uint4 *)(cnt + i) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  const unsigned mine = q.x + q.y + q.z + q.w;
+  // inclusive scan of the threads' totals: over the warp, then over the warps
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  unsigned inc = mine;
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned t = __shfl_up_sync(0xffffffffu, inc, d);
+    if ((int)lane >= d) inc += t;
+  }
+  if (lane == 31u) wsum[warp] = inc;
+  __syncthreads();
+  unsigned wbefore = 0;
+  for (unsigned w = 0; w < warp; w++) wbefore += wsum[w];
+  if (i < nk) {
+    const unsigned o = before + wbefore + inc - mine;
+    *(uint4 *)(off + i) = make_uint4(o, o + q.x, o + q.x + q.y, o + q.x + q.y + q.z);
   }
 }
 
 }  // namespace
 
-void em2dm_sort(const Em2dMixConst &m, const Em2dMixBufs &src, const Em2dMixBufs &dst,
-                const int64_t *ids_in, int64_t *ids_out, unsigned *cnt, unsigned *off,
-                LaunchShape lp, cudaStream_t st) {
-  const int nk = 4 * m.nx * m.ny;
-  cudaMemsetAsync(cnt, 0, sizeof(unsigned) * nk, st);
-  mix2_sort_count_kernel<<<lp.grid, 256, 0, st>>>(src.X, src.Y, m.n, m.nx, m.ny, cnt);
-  mix2_sort_scan_kernel<<<1, 1024, 0, st>>>(cnt, off, nk);
-  mix2_sort_move_kernel<<<lp.grid, 256, 0, st>>>(src, dst, ids_in, ids_out, m.n, m.nx, m.ny, off);
+LaunchShape em2dm_pass_shape(int64_t n, bool sorted, LaunchShape lp) {
+  if (!sorted) return lp;
+  const int64_t per_block = 256 * (int64_t)kRunMarkers;
+  return {(int)std::max<int64_t>(1, (n + per_block - 1) / per_block), 256};
+}
+
+size_t em2dm_sort_count_words(int nx, int ny) {
+  const size_t nk = 4 * (size_t)nx * ny;
+  return nk + (nk + kScanTile - 1) / kScanTile;
+}
+
+void em2dm_sort_scan(const Em2dMixConst &m, unsigned *cnt, unsigned *off, cudaStream_t st) {
+  const int nk = 4 * m.nx * m.ny, tiles = (nk + kScanTile - 1) / kScanTile;
+  unsigned *tsum = cnt + nk;  // [tiles] after the counts
+  launch_dependent(mix2_sort_tilesum_kernel, LaunchShape{tiles, kScanThreads}, 0, st, true, cnt,
+                   nk, tsum);
+  launch_dependent(mix2_sort_offsets_kernel, LaunchShape{tiles, kScanThreads}, 0, st, true, cnt,
+                   nk, (const unsigned *)tsum, off);
 }
 
 void em2dm_k1(const Em2dConst &c, const Em2dMixConst &m, const Em2dMixBufs &mb,
-              const Em2dBufs &b, LaunchShape lg, cudaStream_t st) {
-  mix2_k1_kernel<<<lg.grid, lg.block, 0, st>>>(c, m, mb, b);
+              const Em2dBufs &b, int fin_slot, LaunchShape lp, LaunchShape lg, cudaStream_t st) {
+  const LaunchShape ls{lg.grid + (fin_slot >= 0 ? 1 : 0), lg.block};
+  launch_dependent(mix2_k1_kernel, ls, 0, st, true, c, m, mb, b, fin_slot, lp.grid, lg.grid);
 }
 
 void em2dm_k3(const Em2dConst &c, const Em2dMixConst &m, const Em2dMixBufs &mb,
               const Em2dBufs &b, LaunchShape lg, cudaStream_t st) {
-  mix2_k3_kernel<<<lg.grid, lg.block, 0, st>>>(c, m, mb, b);
+  launch_dependent(mix2_k3_kernel, lg, 0, st, true, c, m, mb, b);
 }
 
-void em2dm_pass_c(const Em2dMixConst &m, const Em2dMixBufs &mb, LaunchShape lp, cudaStream_t st) {
-  if (m.order == 1 && !m.sorted) mix2_pass_c_kernel<1, false><<<lp.grid, 256, 0, st>>>(m, mb);
-  if (m.order == 1 && m.sorted) mix2_pass_c_kernel<1, true><<<lp.grid, 256, 0, st>>>(m, mb);
-  if (m.order == 2 && !m.sorted) mix2_pass_c_kernel<2, false><<<lp.grid, 256, 0, st>>>(m, mb);
-  if (m.order == 2 && m.sorted) mix2_pass_c_kernel<2, true><<<lp.grid, 256, 0, st>>>(m, mb);
-}
-
-void em2dm_pass_e(const Em2dMixConst &m, const Em2dMixBufs &mb, int slot, LaunchShape lp,
+void em2dm_pass_c(const Em2dMixConst &m, const Em2dMixBufs &mb, unsigned *cnt, LaunchShape lp,
                   cudaStream_t st) {
-  if (m.order == 1 && !m.sorted) mix2_pass_e_kernel<1, false><<<lp.grid, 256, 0, st>>>(m, mb, slot);
-  if (m.order == 1 && m.sorted) mix2_pass_e_kernel<1, true><<<lp.grid, 256, 0, st>>>(m, mb, slot);
-  if (m.order == 2 && !m.sorted) mix2_pass_e_kernel<2, false><<<lp.grid, 256, 0, st>>>(m, mb, slot);
-  if (m.order == 2 && m.sorted) mix2_pass_e_kernel<2, true><<<lp.grid, 256, 0, st>>>(m, mb, slot);
+  auto k = m.order == 1 ? (m.sorted ? mix2_pass_c_kernel<1, true> : mix2_pass_c_kernel<1, false>)
+                        : (m.sorted ? mix2_pass_c_kernel<2, true> : mix2_pass_c_kernel<2, false>);
+  launch_dependent(k, LaunchShape{lp.grid, 256}, 0, st, true, m, mb, cnt);
+}
+
+void em2dm_pass_e(const Em2dMixConst &m, const Em2dMixBufs &mb, int slot, const Em2dSortIO &so,
+                  const Em2dConst &c, const Em2dBufs &b, LaunchShape lp, LaunchShape lg,
+                  cudaStream_t st) {
+  auto k = m.order == 1 ? (m.sorted ? mix2_pass_e_kernel<1, true> : mix2_pass_e_kernel<1, false>)
+                        : (m.sorted ? mix2_pass_e_kernel<2, true> : mix2_pass_e_kernel<2, false>);
+  launch_dependent(k, LaunchShape{lp.grid + lg.grid, 256}, 0, st, true, m, mb, slot, so, c, b,
+                   lg.grid);
 }
 
 void em2dm_from_fp64(const Em2dMixConst &m, const Em2dMixBufs &mb, const Em2dBufs &b,

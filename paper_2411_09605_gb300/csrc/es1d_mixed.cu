@@ -43,6 +43,7 @@
 
 #include "ff.cuh"
 #include "mixed_common.cuh"
+#include "pdl.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -278,14 +279,8 @@ __device__ __forceinline__ bool last_warp() {
   return (threadIdx.x >> 5) == (blockDim.x >> 5) - 1;
 }
 
-// Programmatic dependent launch: the passes are launched so that a kernel may
-// start while the previous one finishes; griddepcontrol.wait blocks until the
-// previous kernel has completed and its writes are visible, and
-// launch_dependents lets the next kernel be scheduled early.
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void griddep_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// The passes are launched as programmatic dependent launches (pdl.cuh): each
+// one sets up its shared memory before griddep_wait().
 
 // Ors the flags of a warp's lanes into the error word (one atomic per warp).
 __device__ __forceinline__ void report_flags(unsigned bad, unsigned *err) {
@@ -1384,33 +1379,14 @@ cudaError_t es1d_mix_prepare(const Es1dMixConst &c) {
   return e;
 }
 
-// Launch with programmatic stream serialization: the kernel may begin (its
-// shared-memory set-up) while the previous kernel in the stream finishes; it
-// waits in griddep_wait() before touching that kernel's results.
-template <typename... P, typename... A>
-void launch_dependent(void (*kern)(P...), LaunchShape ls, size_t smem, cudaStream_t st,
-                      A... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(ls.grid);
-  cfg.blockDim = dim3(ls.block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, args...);  // errors surface in cudaGetLastError
-}
-
 void es1d_mix_pass_c(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_index, int slot,
                      LaunchShape ls, cudaStream_t st) {
   int par = (int)(step_index & 1);
   dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE, auto) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
     constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
-    launch_dependent(mix_pass_c_kernel<ORDER, SCHEME, MODE, NT, NE>, ls, smem_c(c), st, c, b, par,
-                     slot - 1, ls.grid);
+    launch_dependent(mix_pass_c_kernel<ORDER, SCHEME, MODE, NT, NE>, ls, smem_c(c), st, true, c,
+                     b, par, slot - 1, ls.grid);
   });
 }
 
@@ -1421,7 +1397,7 @@ void es1d_mix_pass_e(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_i
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
     constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
     launch_dependent(mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE, decltype(G)::value>, ls,
-                     smem_e(c), st, c, b, par, slot);
+                     smem_e(c), st, true, c, b, par, slot);
   });
 }
 
@@ -1431,7 +1407,7 @@ void es1d_mix_pass_ec(const Es1dMixConst &c, const Es1dMixBufs &b, const RingIO 
   dispatch_fused(c, [&](auto O, auto RT, auto RE, auto RE1) {
     launch_dependent(mix_pass_ec_kernel<decltype(O)::value, decltype(RT)::value,
                                         decltype(RE)::value, decltype(RE1)::value>,
-                     ls, smem_ec(c), st, c, b, io, par, slot, slot - 1, ls.grid);
+                     ls, smem_ec(c), st, true, c, b, io, par, slot, slot - 1, ls.grid);
   });
 }
 
@@ -1491,9 +1467,11 @@ void es1d_batch_pass_c(const Es1dMixConst *cs, const Es1dMixBufs *bs, const Batc
   const int par = (int)(step_index & 1);
   const LaunchShape ls{nitems, 1024};
   if (scheme == 1)
-    launch_dependent(mix_batch_pass_c_kernel<1>, ls, smem, st, cs, bs, items, par, prev_slot);
+    launch_dependent(mix_batch_pass_c_kernel<1>, ls, smem, st, true, cs, bs, items, par,
+                     prev_slot);
   else
-    launch_dependent(mix_batch_pass_c_kernel<2>, ls, smem, st, cs, bs, items, par, prev_slot);
+    launch_dependent(mix_batch_pass_c_kernel<2>, ls, smem, st, true, cs, bs, items, par,
+                     prev_slot);
 }
 
 void es1d_batch_pass_e(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,
@@ -1502,9 +1480,9 @@ void es1d_batch_pass_e(const Es1dMixConst *cs, const Es1dMixBufs *bs, const Batc
   const int par = (int)(step_index & 1);
   const LaunchShape ls{nitems, 1024};
   if (scheme == 1)
-    launch_dependent(mix_batch_pass_e_kernel<1>, ls, smem, st, cs, bs, items, par, slot);
+    launch_dependent(mix_batch_pass_e_kernel<1>, ls, smem, st, true, cs, bs, items, par, slot);
   else
-    launch_dependent(mix_batch_pass_e_kernel<2>, ls, smem, st, cs, bs, items, par, slot);
+    launch_dependent(mix_batch_pass_e_kernel<2>, ls, smem, st, true, cs, bs, items, par, slot);
 }
 
 void es1d_batch_finalize(const Es1dMixConst *cs, const Es1dMixBufs *bs, const int *nblocks,

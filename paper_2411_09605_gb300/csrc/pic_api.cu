@@ -76,6 +76,7 @@ struct pic_handle {
   int64_t N = 0;
   int64_t steps_done = 0;
   int pending = 0;          // asynchronous steps whose stats are not read yet
+  bool te_open = false;     // mixed 2D3V: the last pending step's TE is not reduced yet
   int64_t launches = 0;     // kernels launched on behalf of this handle
   bool weighted = false;
   // optional per-launch timing (pic_set_profiling): events around each launch
@@ -112,6 +113,7 @@ struct pic_handle {
   unsigned *sort2_cnt = nullptr;  // [4 nx ny] counts and offsets of the sort
   unsigned *sort2_off = nullptr;
   LaunchShape lp{1, 256}, lg{1, 256};
+  LaunchShape lpm{1, 256};  // passes C and E of the mixed 2D3V form
   // 1D mixed-precision state
   bool mixed = false;
   Es1dMixConst cm{};
@@ -814,29 +816,25 @@ int init_em2d_mixed(pic_handle *h) {
   mb.err = h->be.err;
   m.sorted = h->cfg.sort_period > 0;
   if (m.sorted) {
-    // markers in quarter-cell order every sort_period steps (ids follow them)
+    // markers written in quarter-cell order every sort_period steps (ids
+    // follow them); the counts stay zero between sorts
     Em2dMixBufs &alt = h->bme_alt;
     alt = mb;
+    const size_t ncnt = em2dm_sort_count_words(c.nx, c.ny);
     if ((rc = h->alloc(&alt.X, n)) || (rc = h->alloc(&alt.Y, n)) ||
-        (rc = h->alloc(&h->ids_alt, n)) ||
-        (rc = h->alloc(&h->sort2_cnt, 4 * (size_t)c.nx * c.ny)) ||
+        (rc = h->alloc(&h->ids_alt, n)) || (rc = h->alloc(&h->sort2_cnt, ncnt)) ||
         (rc = h->alloc(&h->sort2_off, 4 * (size_t)c.nx * c.ny)))
       return rc;
     for (int d = 0; d < 3; d++)
       if ((rc = h->alloc(&alt.vh[d], n)) || (rc = h->alloc(&alt.vl[d], n))) return rc;
+    CUDA_TRY(cudaMemsetAsync(h->sort2_cnt, 0, sizeof(unsigned) * ncnt, h->st));
   }
   return PIC_OK;
 }
 
-// Sorts the mixed 2D markers (and their ids) by quarter cell into the
-// alternate arrays and swaps them in.
-int sort_em2d_mixed(pic_handle *h) {
-  const bool ids = !h->cfg.skip_ids;
-  CUDA_TRY(h->timed_launch(3, [&] {
-    em2dm_sort(h->cme, h->bme, h->bme_alt, ids ? h->ids : nullptr, ids ? h->ids_alt : nullptr,
-               h->sort2_cnt, h->sort2_off, h->lp, h->st);
-  }));
-  h->launches += 3;
+// After pass E wrote the mixed 2D markers (and their ids) in quarter-cell
+// order into the alternate arrays: swaps them in.
+void swap_em2d_sorted(pic_handle *h) {
   Em2dMixBufs &a = h->bme, &b = h->bme_alt;
   std::swap(a.X, b.X);
   std::swap(a.Y, b.Y);
@@ -844,10 +842,8 @@ int sort_em2d_mixed(pic_handle *h) {
     std::swap(a.vh[d], b.vh[d]);
     std::swap(a.vl[d], b.vl[d]);
   }
-  if (ids) std::swap(h->ids, h->ids_alt);
-  return PIC_OK;
+  if (!h->cfg.skip_ids) std::swap(h->ids, h->ids_alt);
 }
-
 
 // 2D3V Yee: constants, SoA markers, fields E^0, B^{-1/2} and B^{1/2}, j^{0,*}.
 int init_em2d(pic_handle *h, const pic_species *species, const double *E0, const double *B0) {
@@ -896,7 +892,11 @@ int init_em2d(pic_handle *h, const pic_species *species, const double *E0, const
   double **fields[] = {&b.E, &b.En, &b.Eh, &b.Es, &b.B, &b.Bp, &b.Bpp, &b.J1, &b.J2};
   for (double **f : fields)
     if ((rc = h->alloc(f, nc3))) return rc;
-  if ((rc = h->alloc(&b.ke_part, (size_t)h->lp.grid * kMaxSpecies)) ||
+  // the mixed passes on sorted markers launch a block per 256 runs of markers
+  h->lpm = h->mixed ? em2dm_pass_shape(h->N, cfg.sort_period > 0, h->lp) : h->lp;
+  const size_t nke = std::max((size_t)h->lp.grid * kMaxSpecies, (size_t)h->lpm.grid);
+  if ((rc = h->alloc(&b.ke_part, nke)) ||
+      (rc = h->alloc(&h->energy_part, (size_t)h->lp.grid * kMaxSpecies)) ||
       (rc = h->alloc(&b.wf_part, 2 * (size_t)h->lg.grid)) || (rc = h->alloc(&b.fallback, kStepsCap)) ||
       (rc = h->alloc(&b.te, kStepsCap)) || (rc = h->alloc(&b.err, 1)) ||
       (rc = h->alloc(&h->ids, h->N)))
@@ -1422,24 +1422,48 @@ int pic_step_async(pic_handle *h, int nsteps) {
     Em2dBufs &e = h->be;
     const int slot = h->pending;
     if (h->mixed) {
-      if (h->cme.sorted && h->steps_done % h->cfg.sort_period == 0) {
-        const int rc = sort_em2d_mixed(h);
-        if (rc) return rc;
-      }
+      // sorted markers: pass E of every sort_period-th step writes them in
+      // quarter-cell order (from pass C's counts and their scan)
+      const bool sort_now = h->cme.sorted && (h->steps_done + 1) % h->cfg.sort_period == 0;
       const Em2dMixBufs &mb = h->bme;
-      CUDA_TRY(h->timed_launch(4, [&] { em2dm_k1(h->ce, h->cme, mb, e, h->lg, h->st); }));
-      CUDA_TRY(h->timed_launch(0, [&] { em2dm_pass_c(h->cme, mb, h->lp, h->st); }));
+      Em2dSortIO so{};
+      if (sort_now) {
+        so.off = h->sort2_off;
+        so.dst = h->bme_alt;
+        so.ids_in = h->cfg.skip_ids ? nullptr : h->ids;
+        so.ids_out = h->cfg.skip_ids ? nullptr : h->ids_alt;
+      }
+      unsigned *cnt = sort_now ? h->sort2_cnt : nullptr;
+      // K1 also reduces the previous step's TE; pass E also runs K5
+      const int fin = (h->te_open && slot > 0) ? slot - 1 : -1;
+      CUDA_TRY(h->timed_launch(4, [&] {
+        em2dm_k1(h->ce, h->cme, mb, e, fin, h->lpm, h->lg, h->st);
+      }));
+      CUDA_TRY(h->timed_launch(0, [&] { em2dm_pass_c(h->cme, mb, cnt, h->lpm, h->st); }));
+      if (sort_now) {
+        CUDA_TRY(h->timed_launch(3, [&] {
+          em2dm_sort_scan(h->cme, h->sort2_cnt, h->sort2_off, h->st);
+        }));
+        h->launches += 2;
+      }
       CUDA_TRY(h->timed_launch(4, [&] { em2dm_k3(h->ce, h->cme, mb, e, h->lg, h->st); }));
-      CUDA_TRY(h->timed_launch(1, [&] { em2dm_pass_e(h->cme, mb, slot, h->lp, h->st); }));
+      CUDA_TRY(h->timed_launch(1, [&] {
+        em2dm_pass_e(h->cme, mb, slot, so, h->ce, e, h->lpm, h->lg, h->st);
+      }));
+      if (sort_now) swap_em2d_sorted(h);
+      h->te_open = true;
+      h->launches += 4;
     } else {
       CUDA_TRY(h->timed_launch(4, [&] { em2d_k1(h->ce, e, h->lg, h->st); }));
       CUDA_TRY(h->timed_launch(0, [&] { em2d_pass_c(h->ce, e, h->lp, h->st); }));
       CUDA_TRY(h->timed_launch(4, [&] { em2d_k3(h->ce, e, h->lg, h->st); }));
       CUDA_TRY(h->timed_launch(1, [&] { em2d_pass_e(h->ce, e, slot, h->lp, h->st); }));
+      CUDA_TRY(h->timed_launch(4, [&] { em2d_k5(h->ce, e, h->lg, h->st, false); }));
+      CUDA_TRY(h->timed_launch(2, [&] {
+        em2d_finalize(h->ce, e, slot, h->lp, h->lg, h->st, false);
+      }));
+      h->launches += 6;
     }
-    CUDA_TRY(h->timed_launch(4, [&] { em2d_k5(h->ce, e, h->lg, h->st); }));
-    CUDA_TRY(h->timed_launch(2, [&] { em2d_finalize(h->ce, e, slot, h->lp, h->lg, h->st); }));
-    h->launches += 6;
     std::swap(e.E, e.En);
     double *old = e.B;
     e.B = e.Bp;
@@ -1521,6 +1545,13 @@ int pic_read_stats(pic_handle *h, int capacity, int64_t *nfallback_per_step, dou
   if ((nfallback_per_step || te_per_step) && capacity < n)
     return fail(PIC_ERR_ARG, "pic_read_stats: %d steps pending, capacity %d", n, capacity);
   Es1dFp64Bufs &b = h->b1;
+  if (h->em && h->mixed && h->te_open) {
+    CUDA_TRY(h->timed_launch(2, [&] {
+      em2d_finalize(h->ce, h->be, n - 1, h->lpm, h->lg, h->st, false);
+    }));
+    h->launches += 1;
+  }
+  h->te_open = false;
   if (!h->em && !h->em1 && !h->stdp) {
     CUDA_TRY(h->timed_launch(2, [&] {
       if (h->mixed)
@@ -1596,14 +1627,17 @@ static int energy_em2d(pic_handle *h, double *KE_per_species, double *W_E, doubl
   const Em2dConst &c = h->ce;
   Em2dBufs &b = h->be;
   const int nb = h->lp.grid;
+  // own partials: the mixed form keeps the last step's in ke_part until the
+  // next step (or pic_read_stats) has reduced them
+  double *part_d = h->energy_part;
   if (h->mixed)
-    em2dm_kinetic(h->cme, h->bme, b.ke_part, h->lp, h->st);
+    em2dm_kinetic(h->cme, h->bme, part_d, h->lp, h->st);
   else
-    em2d_fp64_kinetic(c, b, b.ke_part, nb, h->st);
+    em2d_fp64_kinetic(c, b, part_d, nb, h->st);
   CUDA_TRY(cudaGetLastError());
   const size_t nc3 = 3 * (size_t)c.nx * c.ny;
   std::vector<double> part((size_t)nb * h->nsp), e(nc3), bo(nc3), bp(nc3);
-  CUDA_TRY(cudaMemcpyAsync(part.data(), b.ke_part, sizeof(double) * part.size(),
+  CUDA_TRY(cudaMemcpyAsync(part.data(), part_d, sizeof(double) * part.size(),
                            cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(cudaMemcpyAsync(e.data(), b.E, sizeof(double) * nc3, cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(cudaMemcpyAsync(bo.data(), b.B, sizeof(double) * nc3, cudaMemcpyDeviceToHost, h->st));

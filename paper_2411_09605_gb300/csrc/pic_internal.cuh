@@ -304,6 +304,15 @@ struct Em2dMixBufs {
   unsigned *err;
 };
 
+// The quarter-cell sort of the mixed 2D3V markers, written by pass E of the
+// step that ends a sort period (off set; null on every other step).
+struct Em2dSortIO {
+  unsigned *off;            // [4 nx ny] first free slot of each quarter cell
+  Em2dMixBufs dst;          // X, Y, vh, vl of the sorted markers
+  const int64_t *ids_in;    // [N] marker ids, or null (not carried)
+  int64_t *ids_out;         // [N] the ids in the sorted order
+};
+
 // Everything the 1D FP64 kernels touch.
 struct Es1dFp64Bufs {
   double *x, *v, *w;        // [N] SoA (w may be null)
@@ -368,9 +377,11 @@ void em2d_k1(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t
 void em2d_pass_c(const Em2dConst &c, const Em2dBufs &b, LaunchShape lp, cudaStream_t st);
 void em2d_k3(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st);
 void em2d_pass_e(const Em2dConst &c, const Em2dBufs &b, int slot, LaunchShape lp, cudaStream_t st);
-void em2d_k5(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st);
+// k5 and the finalize kernel wait for the previous kernel with griddep_wait():
+// pdl launches them as programmatic dependent launches (the mixed form's chain)
+void em2d_k5(const Em2dConst &c, const Em2dBufs &b, LaunchShape lg, cudaStream_t st, bool pdl);
 void em2d_finalize(const Em2dConst &c, const Em2dBufs &b, int slot, LaunchShape lp,
-                   LaunchShape lg, cudaStream_t st);
+                   LaunchShape lg, cudaStream_t st, bool pdl);
 void em2d_fp64_deposit_initial(const Em2dConst &c, const Em2dBufs &b, LaunchShape lp,
                                cudaStream_t st);
 void em2d_fp64_bhalf(const Em2dConst &c, const double *B, const double *E, double *Bp,
@@ -393,18 +404,30 @@ void std_energy(const StdConst &c, const StdBufs &b, double *ke_out, double *we,
 
 // 2D3V Yee path, mixed form (em2d_mixed.cu); the FP64 fields live in Em2dBufs
 // and K5 / the finalize kernel of the FP64 form are shared.
+// K1 of the mixed form; with fin_slot >= 0 one more block reduces the total
+// energy of the step in fin_slot (lp: the passes' shape, lg: the grid's)
 void em2dm_k1(const Em2dConst &c, const Em2dMixConst &m, const Em2dMixBufs &mb,
-              const Em2dBufs &b, LaunchShape lg, cudaStream_t st);
+              const Em2dBufs &b, int fin_slot, LaunchShape lp, LaunchShape lg, cudaStream_t st);
 void em2dm_k3(const Em2dConst &c, const Em2dMixConst &m, const Em2dMixBufs &mb,
               const Em2dBufs &b, LaunchShape lg, cudaStream_t st);
-void em2dm_pass_c(const Em2dMixConst &m, const Em2dMixBufs &mb, LaunchShape lp, cudaStream_t st);
-void em2dm_pass_e(const Em2dMixConst &m, const Em2dMixBufs &mb, int slot, LaunchShape lp,
+// pass C; cnt: [4 nx ny] counts of the quarter cells of x^{n+1} (sorted
+// markers, the step that ends a sort period) or null
+void em2dm_pass_c(const Em2dMixConst &m, const Em2dMixBufs &mb, unsigned *cnt, LaunchShape lp,
                   cudaStream_t st);
-// quarter-cell counting sort of the mixed 2D markers (and ids) from src into
-// dst; cnt, off: [4 nx ny] scratch
-void em2dm_sort(const Em2dMixConst &m, const Em2dMixBufs &src, const Em2dMixBufs &dst,
-                const int64_t *ids_in, int64_t *ids_out, unsigned *cnt, unsigned *off,
-                LaunchShape lp, cudaStream_t st);
+// pass E, and K5 of the FP64 fields (c, b) in lg.grid more blocks
+void em2dm_pass_e(const Em2dMixConst &m, const Em2dMixBufs &mb, int slot, const Em2dSortIO &so,
+                  const Em2dConst &c, const Em2dBufs &b, LaunchShape lp, LaunchShape lg,
+                  cudaStream_t st);
+// Launch shape of the mixed 2D3V passes C and E (and so the number of kinetic
+// partials pass E writes): lp on unsorted markers; on sorted ones one block per
+// 256 threads' runs of consecutive markers, so every warp makes one trip.
+LaunchShape em2dm_pass_shape(int64_t n, bool sorted, LaunchShape lp);
+// Words of the sort's count array: a count per quarter cell, then the totals
+// of the scan's tiles.
+size_t em2dm_sort_count_words(int nx, int ny);
+// offsets off[] of the quarter cells from pass C's counts cnt[], which it
+// leaves zero for the next sort
+void em2dm_sort_scan(const Em2dMixConst &m, unsigned *cnt, unsigned *off, cudaStream_t st);
 // FP64 staging (x, y, vx, vy, vz) <-> the mixed state
 void em2dm_from_fp64(const Em2dMixConst &m, const Em2dMixBufs &mb, const Em2dBufs &b,
                      LaunchShape lp, cudaStream_t st);

@@ -78,9 +78,11 @@ def test_argument_errors_are_status_codes(lib):
     with pytest.raises(pic.PicError) as ei:
         pic.pic_init(pic.make_config(64, 1.0, 0.1, binomial_passes=9), sp)
     assert ei.value.code == -1
-    for kw in ({"sort_period": 4},                                  # sorting: mixed 1D form only
+    for kw in ({"sort_period": 4},          # sorting: mixed forms of the Ampere and Yee solvers
                {"sort_period": 4, "solver": pic.PIC_SOLVER_YEE_LEAPFROG, "dim_x": 2, "dim_v": 3,
-                "ny": 64, "Ly": 1.0, "precision": pic.PIC_PREC_MIXED},
+                "ny": 64, "Ly": 1.0},
+               {"sort_period": 4, "solver": pic.PIC_SOLVER_PSATD, "dim_v": 2,
+                "precision": pic.PIC_PREC_MIXED},
                {"charge_conserving": 1}):                           # Yee solver only
         with pytest.raises(pic.PicError) as ei:
             pic.pic_init(pic.make_config(64, 1.0, 0.1, **kw), sp)

@@ -235,9 +235,10 @@ def test_input_errors_mixed():
 
 @pytest.mark.parametrize("order,scheme,period", [(1, 2, 1), (1, 1, 3), (2, 2, 2), (2, 2, 5)])
 def test_quarter_cell_sort_does_not_change_the_physics(order, scheme, period):
-    """The markers kept in quarter-cell order every `period` steps, with each
-    warp's deposits summed over its lanes' equal stencils before the atomics:
-    the currents are exact integer sums, so the run equals the unsorted one bit
+    """The markers written in quarter-cell order by pass E every `period`
+    steps, each thread's run of consecutive markers in one quarter cell summed
+    in registers and the runs over the warp's lanes before the atomics: the
+    currents are exact integer sums, so the run equals the unsorted one bit
     for bit (markers compared through their ids), over 12 steps."""
     from paper_2411_09605_gb300 import pic
     prob = W.weibel(nx=32, ny=32, ppc=16, L=6.4, vth_par=0.1, order=order, seed=21)
@@ -263,13 +264,11 @@ def test_quarter_cell_order_after_a_sort():
     """Right after a sort the slots run in quarter-cell order and the ids are a
     permutation (bit-exact integer work)."""
     from paper_2411_09605_gb300 import pic
-    # nearly cold markers: one step moves almost none of them into another
-    # quarter cell, so the slots after the step show the order of the sort
-    prob = W.weibel(nx=16, ny=16, ppc=8, L=3.2, vth_par=1e-4, seed=23)
+    prob = W.weibel(nx=16, ny=16, ppc=8, L=3.2, vth_par=0.05, seed=23)
     sim = pic.Simulation2D(prob, precision=MIXED, sort_period=4)
     n = prob.n_markers
     try:
-        sim.step(1)   # sorted at the start of step 0, then moved by one step
+        sim.step(4)   # pass E of the 4th step writes the markers in the order of x^4
         x, v = np.zeros((2, n)), np.zeros((3, n))
         pic.pic_get_particles(sim.h, 0, x, v)
         ids = np.zeros(n, dtype=np.int64)
