@@ -62,10 +62,15 @@ struct AxisMix {
     const uint64_t P = (uint64_t)X * (uint32_t)n + ((uint64_t)(uint32_t)n << 32) +
                        (ORDER == 2 ? 0x80000000ull : 0ull) - (half ? 0x80000000ull : 0ull);
     const int i0 = (int)(P >> 32) - n - (ORDER == 2 ? 1 : 0);
+    // i0 lies in [0, n - 1] (order 1, integer nodes), [-1, n - 2] (order 2,
+    // half nodes) or [-1, n - 1]: node i0 + a can fall below 0 only for a = 0
+    // and i0 < 0 possible, and reach n only for a >= 1 (a = 2 when i0 <= n - 2)
 #pragma unroll
     for (int a = 0; a <= ORDER; a++) {
       const int i = i0 + a;
-      k[a] = i < 0 ? i + n : (i >= n ? i - n : i);
+      const bool low = a == 0 && (half || ORDER == 2);
+      const bool high = a >= ((half && ORDER == 2) ? 2 : 1);
+      k[a] = low ? (i < 0 ? i + n : i) : (high ? (i >= n ? i - n : i) : i);
     }
     const uint32_t f23 = (uint32_t)P >> 9;
     const float f = __fsub_rn(__uint_as_float(0x3F800000u | f23), 1.0f);  // exact
@@ -145,14 +150,16 @@ __device__ __forceinline__ ff gather_ff(const float2 *T, int nx, const AxisMix<O
   return acc;
 }
 
-// round(V s_a s_b / 2^r) for r >= 32, given m = |V| s_b (|V| < 2^31, s <= 2^23,
-// so the product is below 2^77): with m = mh 2^32 + ml,
-// (m s_a + 2^(r-1)) >> r = (mh s_a + ((ml s_a + 2^(r-1)) >> 32)) >> (r - 32).
-__device__ __forceinline__ long long deposit_term(uint64_t m, uint32_t sa, bool neg,
+// floor(V s_a s_b / 2^r + 1/2) (the nearest integer, ties up) for r >= 32,
+// given m = V s_b (|V| < 2^31, s <= 2^23, so |V s_a s_b| < 2^77): with m =
+// mh 2^32 + ml (mh signed, ml unsigned), m s_a + 2^(r-1) = (mh s_a + ((ml s_a +
+// 2^(r-1)) >> 32)) 2^32 + the low word, and the floor of its quotient by 2^r is
+// the arithmetic shift of the first factor by r - 32.
+__device__ __forceinline__ long long deposit_term(long long m, uint32_t sa,
                                                   const Em2dMixConst &c) {
   const uint64_t lo = (uint64_t)(uint32_t)m * sa + (uint64_t)c.rnd;
-  const uint64_t q = ((uint64_t)(uint32_t)(m >> 32) * sa + (lo >> 32)) >> (c.rshift - 32);
-  return neg ? -(long long)q : (long long)q;
+  const long long hi = (long long)(int)(m >> 32) * (long long)sa + (long long)(lo >> 32);
+  return hi >> (c.rshift - 32);
 }
 
 template <int ORDER>
@@ -160,16 +167,14 @@ __device__ __forceinline__ void deposit_c(long long *J, int nx, const AxisMix<OR
                                           const AxisMix<ORDER> &ay, int V,
                                           const Em2dMixConst &c) {
   if (V == 0) return;
-  const bool neg = V < 0;
-  const uint32_t mag = neg ? 0u - (uint32_t)V : (uint32_t)V;
 #pragma unroll
   for (int b = 0; b <= ORDER; b++) {
-    const uint64_t m = (uint64_t)mag * ay.s[b];
+    const long long m = (long long)V * ay.s[b];
     long long *row = J + ay.k[b] * nx;
 #pragma unroll
     for (int a = 0; a <= ORDER; a++)
       atomicAdd((unsigned long long *)(row + ax.k[a]),
-                (unsigned long long)deposit_term(m, ax.s[a], neg, c));
+                (unsigned long long)deposit_term(m, ax.s[a], c));
   }
 }
 
@@ -244,13 +249,11 @@ struct DepositRun {
   __device__ __forceinline__ static void add_terms(const AxisMix<ORDER> &ax,
                                                    const AxisMix<ORDER> &ay, int V,
                                                    const Em2dMixConst &c, long long *t) {
-    const bool neg = V < 0;
-    const uint32_t mag = neg ? 0u - (uint32_t)V : (uint32_t)V;
 #pragma unroll
     for (int b = 0; b <= ORDER; b++) {
-      const uint64_t m = (uint64_t)mag * ay.s[b];
+      const long long m = (long long)V * ay.s[b];
 #pragma unroll
-      for (int a = 0; a <= ORDER; a++) t[b * (ORDER + 1) + a] += deposit_term(m, ax.s[a], neg, c);
+      for (int a = 0; a <= ORDER; a++) t[b * (ORDER + 1) + a] += deposit_term(m, ax.s[a], c);
     }
   }
 

@@ -327,12 +327,14 @@ class Simulation2D:
     """Owner of one Yee-solver handle built from a ``workloads.Problem2D``."""
 
     def __init__(self, prob, scheme=PIC_SCHEME_ESEC2, E0=None, B0=None, gamma_on=True,
-                 precision=PIC_PREC_FP64, charge_conserving=False, sort_period=0):
+                 precision=PIC_PREC_FP64, charge_conserving=False, sort_period=0,
+                 skip_ids=False):
         self.prob = prob
         self.cfg = make_config(prob.nx, prob.Lx, prob.dt, prob.order, scheme, precision,
                                solver=PIC_SOLVER_YEE_LEAPFROG, dim_x=2, dim_v=3, ny=prob.ny,
                                Ly=prob.Ly, c=prob.c, gamma_on=gamma_on,
-                               charge_conserving=charge_conserving, sort_period=sort_period)
+                               charge_conserving=charge_conserving, sort_period=sort_period,
+                               skip_ids=int(skip_ids))
         self.species = []
         for s in prob.species:
             x = np.ascontiguousarray(np.stack([s.x, s.y]), dtype=np.float64)

@@ -299,3 +299,128 @@ def test_sorted_mixed_against_oracle():
         d = _diff(prob, (xr, vr, Er, Br), (xg, vg, Eg, Bg))
         assert d["E"] <= TOL_F and d["B"] <= TOL_F, d
         assert np.array_equal(nfb_o, fb)
+
+
+def _truncated(prob, n):
+    import dataclasses
+    s = prob.species[0]
+    part = dataclasses.replace(s, x=s.x[:n].copy(), y=s.y[:n].copy(), vx=s.vx[:n].copy(),
+                               vy=s.vy[:n].copy(), vz=s.vz[:n].copy())
+    return dataclasses.replace(prob, species=[part])
+
+
+@pytest.mark.parametrize("n", [1, 5, 1037, 2047])
+def test_sorted_mode_ragged_counts(n):
+    """Marker counts that fill no warp, block or run of four evenly: the sorted
+    mode's partial last runs and lanes without markers still give the unsorted
+    run bit for bit (sorts every step and every third step)."""
+    from paper_2411_09605_gb300 import pic
+    prob = _truncated(W.weibel(nx=16, ny=16, ppc=8, L=3.2, vth_par=0.1, seed=31), n)
+    E0, B0 = _fields(prob, 32)
+    res = {}
+    for sp in (0, 1, 3):
+        sim = pic.Simulation2D(prob, E0=E0, B0=B0, precision=MIXED, sort_period=sp)
+        try:
+            fb, te = sim.step(7)
+            x, v = sim.particles(0)
+            E, B = sim.fields()
+        finally:
+            sim.close()
+        res[sp] = (x, v, E, B, fb, te)
+    for sp in (1, 3):
+        for u, w in zip(res[0][:5], res[sp][:5]):
+            assert np.array_equal(u, w), sp
+        assert np.max(np.abs(res[0][5] - res[sp][5])) <= 1e-14 * abs(res[0][5][0])
+
+
+def test_sorted_mode_without_ids():
+    """skip_ids: the sort moves the markers without their ids (pic_get_ids then
+    fails); fields, fallback counts and the set of marker states are the
+    unsorted run's bit for bit."""
+    from paper_2411_09605_gb300 import pic
+    prob = W.weibel(nx=16, ny=16, ppc=8, L=3.2, vth_par=0.1, seed=33)
+    E0, B0 = _fields(prob, 34)
+    n = prob.n_markers
+    out = []
+    for sp, skip in ((0, False), (2, True)):
+        sim = pic.Simulation2D(prob, E0=E0, B0=B0, precision=MIXED, sort_period=sp,
+                               skip_ids=skip)
+        try:
+            fb, te = sim.step(6)
+            x, v = np.zeros((2, n)), np.zeros((3, n))
+            pic.pic_get_particles(sim.h, 0, x, v)
+            E, B = sim.fields()
+            if skip:
+                with pytest.raises(pic.PicError):
+                    pic.pic_get_ids(sim.h, 0, np.zeros(n, dtype=np.int64))
+        finally:
+            sim.close()
+        rows = np.concatenate([x, v])
+        out.append((rows[:, np.lexsort(rows[::-1])], E, B, fb))
+    for u, w in zip(*out):
+        assert np.array_equal(u, w)
+
+
+def test_async_steps_with_energy_calls_between():
+    """The mixed form reduces each step's total energy in the next step's first
+    kernel (the last one when the stats are read): asynchronous steps with
+    pic_energy calls in between (which use partials of their own) give the same
+    per-step TE and fallbacks as one synchronous run: bit for bit on unsorted
+    markers; to the float-pair kinetic sums' round-off when sorting, whose order
+    within a quarter cell is not fixed."""
+    from paper_2411_09605_gb300 import pic
+    prob = W.weibel(nx=16, ny=16, ppc=8, L=3.2, vth_par=0.1, seed=35)
+    E0, B0 = _fields(prob, 36)
+    for sp in (0, 2):
+        sim = pic.Simulation2D(prob, E0=E0, B0=B0, precision=MIXED, sort_period=sp)
+        try:
+            fb_ref, te_ref = sim.step(7)
+        finally:
+            sim.close()
+        sim = pic.Simulation2D(prob, E0=E0, B0=B0, precision=MIXED, sort_period=sp)
+        try:
+            pic.pic_step_async(sim.h, 3)
+            e_mid = sim.energy()
+            pic.pic_step_async(sim.h, 1)
+            sim.energy()
+            pic.pic_step_async(sim.h, 3)
+            fb, te = pic.pic_read_stats(sim.h)
+        finally:
+            sim.close()
+        assert np.array_equal(fb, fb_ref), sp
+        if sp == 0:
+            assert np.array_equal(te, te_ref)
+        else:
+            assert np.max(np.abs(te - te_ref)) <= 1e-14 * abs(te_ref[0])
+        # pic_energy recomputes TE from the state: step 3's, to round-off
+        assert abs(e_mid[3] - te_ref[2]) <= 1e-13 * abs(te_ref[2])
+
+
+def test_state_change_in_a_sorted_run():
+    """pic_set_particles between steps of a sorted run (the markers arrive in
+    the caller's order, the ids restart from it): the run goes on as the
+    unsorted run given the same states does, bit for bit."""
+    from paper_2411_09605_gb300 import pic
+    prob = W.weibel(nx=16, ny=16, ppc=8, L=3.2, vth_par=0.1, seed=37)
+    E0, B0 = _fields(prob, 38)
+    rng = np.random.default_rng(39)
+    res = []
+    for sp in (0, 3):
+        sim = pic.Simulation2D(prob, E0=E0, B0=B0, precision=MIXED, sort_period=sp)
+        try:
+            sim.step(4)
+            x, v = sim.particles(0)
+            # a new state in a fixed order (the same for both runs): shuffled and kicked
+            order = rng.permutation(x.shape[1]) if not res else res[0][0]
+            x2 = np.ascontiguousarray(x[:, order])
+            v2 = np.ascontiguousarray(1.01 * v[:, order])
+            pic.pic_set_particles(sim.h, 0, x2, v2)
+            fb, te = sim.step(5)
+            xa, va = sim.particles(0)
+            E, B = sim.fields()
+        finally:
+            sim.close()
+        res.append((order, xa, va, E, B, fb, te))
+    for u, w in zip(res[0][1:6], res[1][1:6]):
+        assert np.array_equal(u, w)
+    assert np.max(np.abs(res[0][6] - res[1][6])) <= 1e-14 * abs(res[0][6][0])
