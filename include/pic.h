@@ -290,10 +290,15 @@ int pic_mixed_resolution(pic_handle *h, double *dx, double *dv, int *deposit_bit
 
 /* Copies species s out as FP64 SoA ([dim_x][n] positions, [dim_v][n]
  * velocities).  Marker order is the library's current (possibly sorted)
- * order; pic_get_ids returns, for each slot, the marker's index at init. */
+ * order; pic_get_ids returns, for each slot, the marker's index at init.
+ * Both return after the data is in place. */
 int pic_get_particles(pic_handle *h, int s, double *x, double *v);
 int pic_get_ids(pic_handle *h, int s, int64_t *ids);
-/* Replaces species s (same n; resets its ids to 0..n-1). */
+/* Replaces species s (same n; resets its ids to 0..n-1); returns after the
+ * buffers have been read.  The mixed 1D1V form converts buffers that the
+ * device can address (device memory, pinned host memory) in one kernel
+ * reading them in place, and stages others (pageable host memory) through
+ * cudaMemcpy; pic_get_particles writes the same way. */
 int pic_set_particles(pic_handle *h, int s, const double *x, const double *v);
 /* Fields: E^n and (Yee) B^{n-1/2}; B may be NULL for the ES solver and is
  * required by pic_set_fields for the Yee solver (B^{n+1/2} is then rebuilt as

@@ -226,11 +226,35 @@ cudaError_t ensure_copy_stream(pic_handle *h) {
   return e;
 }
 
-// pic_set_particles of the mixed 1D form: the markers go into the FP64
-// staging arrays in kXferChunks pieces on the copy stream, and each piece is
-// turned into the mixed state on the handle's stream as soon as it has
+// p as the device addresses it: device or managed memory, or host memory that
+// is pinned and mapped into the device's address space (kernels then read or
+// write it over the host link directly, at the link's rate); null for other
+// host memory (pageable), which goes through cudaMemcpy.
+template <typename T>
+T *device_view(T *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // an unknown pointer is not an error here
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
+      a.type == cudaMemoryTypeHost)
+    return static_cast<T *>(a.devicePointer);
+  return nullptr;
+}
+
+// pic_set_particles of the mixed 1D form.  Markers the device can address
+// (device memory, pinned host memory) are turned into the mixed state by one
+// kernel that reads them where they are.  Other host memory goes into the
+// FP64 staging arrays in kXferChunks pieces on the copy stream, and each piece
+// is turned into the mixed state on the handle's stream as soon as it has
 // arrived, so the conversion overlaps the transfer of the next piece.
 cudaError_t upload_mixed_1d(pic_handle *h, const double *x, const double *v) {
+  const double *xd = device_view(x), *vd = device_view(v);
+  if (xd && vd) {
+    es1d_mix_from_fp64_part(h->cm, xd, vd, h->bm, 0, h->N, h->ls, h->st);
+    return cudaGetLastError();
+  }
   cudaError_t e = ensure_copy_stream(h);
   Es1dFp64Bufs &b = h->b1;
   const int64_t n = h->N, chunk = (n + kXferChunks - 1) / kXferChunks;
@@ -252,10 +276,17 @@ cudaError_t upload_mixed_1d(pic_handle *h, const double *x, const double *v) {
   return e;
 }
 
-// pic_get_particles of the mixed 1D form: each piece is converted to FP64 on
+// pic_get_particles of the mixed 1D form: written by one kernel straight into
+// memory the device can address; otherwise each piece is converted to FP64 on
 // the handle's stream and copied out on the copy stream while the next piece
-// converts; returns after the last copy.
+// converts.  Returns after the last write.
 cudaError_t download_mixed_1d(pic_handle *h, double *x, double *v) {
+  double *xd = x ? device_view(x) : nullptr, *vd = v ? device_view(v) : nullptr;
+  if (x && v && xd && vd) {
+    es1d_mix_to_fp64_part(h->cm, h->bm, xd, vd, 0, h->N, h->ls, h->st);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? cudaStreamSynchronize(h->st) : e;
+  }
   cudaError_t e = ensure_copy_stream(h);
   Es1dFp64Bufs &b = h->b1;
   const int64_t n = h->N, chunk = (n + kXferChunks - 1) / kXferChunks;

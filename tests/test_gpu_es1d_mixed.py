@@ -238,3 +238,51 @@ def test_esec1_fallback_counts_step_by_step(order):
     finally:
         sim.close()
     assert checked >= 8 and total >= 10, (checked, total)
+
+
+def test_particle_buffers_pinned_and_on_device():
+    """pic_set_particles / pic_get_particles of the mixed form read and write
+    buffers the device can address (pinned host memory, device memory) in
+    place, pageable ones through cudaMemcpy staging: the three give the same
+    states bit for bit, and a bad position in a pinned buffer is still
+    reported."""
+    import torch
+    from paper_2411_09605_gb300 import pic
+    prob = W.two_stream(n=3 * (1 << 14) + 5, nc=256, seed=41)
+    n = prob.n_markers
+    res = {}
+    for kind in ("pageable", "pinned", "device"):
+        sim = pic.Simulation(prob, precision=MIXED)
+        try:
+            sim.step(3)
+            if kind == "pageable":
+                x, v = np.zeros(n), np.zeros(n)
+            elif kind == "pinned":
+                x = torch.zeros(n, dtype=torch.float64).pin_memory()
+                v = torch.zeros(n, dtype=torch.float64).pin_memory()
+            else:
+                x = torch.zeros(n, dtype=torch.float64, device="cuda")
+                v = torch.zeros(n, dtype=torch.float64, device="cuda")
+            pic.pic_get_particles(sim.h, 0, x, v)
+            got = tuple(a.copy() if kind == "pageable" else a.cpu().numpy().copy()
+                        for a in (x, v))
+            v.mul_(1.001) if kind != "pageable" else np.multiply(v, 1.001, out=v)
+            pic.pic_set_particles(sim.h, 0, x, v)
+            fb, te = sim.step(3)
+            x2, v2 = sim.particles(0)
+        finally:
+            sim.close()
+        res[kind] = (*got, x2, v2, fb, te)
+    for kind in ("pinned", "device"):
+        for a, b in zip(res["pageable"], res[kind]):
+            assert np.array_equal(a, b), kind
+    sim = pic.Simulation(prob, precision=MIXED)
+    try:
+        x = torch.from_numpy(prob.species[0].x.copy()).pin_memory()
+        v = torch.from_numpy(prob.species[0].v.copy()).pin_memory()
+        x[7] = prob.L
+        with pytest.raises(pic.PicError) as ei:
+            pic.pic_set_particles(sim.h, 0, x, v)
+        assert ei.value.code == -6
+    finally:
+        sim.close()
