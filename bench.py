@@ -91,6 +91,10 @@ def parse():
     ap.add_argument("--ensemble", type=int, default=0,
                     help="time a batch of this many independent runs instead (not the default "
                          "line): batched launches vs the same runs stepped one by one")
+    ap.add_argument("--ensemble-markers", default="1e4:1e6",
+                    help="MIN:MAX of the log-uniform marker counts of the ensemble's runs")
+    ap.add_argument("--ensemble-cells", default="32:512",
+                    help="MIN:MAX of the uniform cell counts of the ensemble's runs")
     args = ap.parse_args()
     if args.sort_period is None:
         # the fastest setting measured per workload: unsorted markers on the 1D
@@ -539,7 +543,10 @@ def run_ensemble(args):
     B.build()
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()             # every run and every event on one stream
-    probs = W.ensemble(args.ensemble, seed=0)
+    n_min, n_max = (float(a) for a in args.ensemble_markers.split(":"))
+    nc_min, nc_max = (int(a) for a in args.ensemble_cells.split(":"))
+    probs = W.ensemble(args.ensemble, seed=0, n_min=n_min, n_max=n_max, nc_min=nc_min,
+                       nc_max=nc_max)
     markers = sum(p.n_markers for p in probs)
     steps = max(2, min(args.steps, 100))
 
@@ -588,7 +595,8 @@ def run_ensemble(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32+i64 (energy in f64)",
         "data": "synthetic (seeded Landau and two-stream runs)",
         "config": {"workload": "ensemble_1d1v", "runs": len(probs), "markers": markers,
-                   "cells": "U{32..512}", "markers_per_run": "log-uniform [1e4, 1e6]",
+                   "cells": f"U{{{nc_min}..{nc_max}}}",
+                   "markers_per_run": f"log-uniform [{n_min:g}, {n_max:g}]",
                    "blocks_per_pass": nblocks, "trips_per_block (autotuned)": trips,
                    "l2": "not flushed: the batch state (%.0f MB) is larger than L2"
                          % (16e-6 * markers)},

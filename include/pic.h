@@ -151,13 +151,14 @@ typedef struct {
   int skip_ids;             /* 1: do not carry marker ids through sorts       */
                             /* (pic_get_ids then fails); 0: keep them         */
   int binomial_passes;      /* 1-2-1 filter passes, 0..8.  Standard solver: on */
-                            /* the charge.  Ampere solver, FP64 form: inside  */
+                            /* the charge.  Ampere solver, both forms: inside */
                             /* the scheme, energy-consistently (Ampere uses   */
                             /* F j, the gathers F E; F is symmetric, so the   */
                             /* energy identity stays exact), and the initial  */
-                            /* Gauss field is that of F rho.  Other solvers,  */
-                            /* the mixed form and the no-alloc entry point:   */
-                            /* must be 0.                                     */
+                            /* Gauss field is that of F rho (ESEC1 then runs  */
+                            /* two launches per step).  Other solvers,        */
+                            /* batches and the no-alloc entry point: must be  */
+                            /* 0.                                             */
   int charge_conserving;    /* Yee solver, FP64, shape_order 1: 1 = exact     */
                             /* charge conservation (Sec. 3.5, Eq. detbal).    */
                             /* With the bilinear charge shape rho, each J/E   */

@@ -211,6 +211,76 @@ __device__ __forceinline__ ff mean_of_total(long long total, const Es1dMixConst 
   return ff_mul(ff_from_i64(total), c.inv_nc);
 }
 
+// The binomial filter F (the periodic 1-2-1 stencil, p passes) inside the
+// scheme, put in energy-consistently: both Ampere updates use F j and both
+// gathers read F E* and F E^{n+1/2}; F is symmetric and keeps the mean, so
+// sum E (F j) = sum (F E) j.  A table entry is a stencil over the unfiltered
+// grid: F E* = F E^n - dt/2 (F^2 j1 - <j1>), with F^p's weights C(2p, p + k) /
+// 4^p and F^2p's (b.filt).  Node i + k of the periodic grid, any k:
+__device__ __forceinline__ int node_at(int i, int k, int nc) {
+  const int j = (i + k) % nc;
+  return j < 0 ? j + nc : j;
+}
+
+// The filtered tables are built out of line (noinline), so that the kernels
+// without the filter keep their code.  e_scale F E* on the padded nodes in
+// FP32 (gather #1 only shapes v*), RE copies each:
+template <int SCHEME, int RE, int PAD>
+__device__ __noinline__ void estar_table_filtered(int nc, int p, float c_jstar, const float2 *filt,
+                                                  const float2 *Ek, const long long *J1,
+                                                  float mean, float *Es, int npad) {
+  const float2 *f2 = filt + 2 * p + 1;
+  for (int q = threadIdx.x; q < npad; q += blockDim.x) {
+    const int i = wrap_node(q - PAD, nc);
+    float e = 0.0f;
+    for (int k = -p; k <= p; k++) {
+      const float2 ek = Ek[node_at(i, k, nc)];
+      e = __fmaf_rn(filt[k + p].x, __fmul_rn(0.5f, __fadd_rn(ek.x, ek.y)), e);
+    }
+    if (SCHEME == 2) {
+      float j = 0.0f;
+      for (int k = -2 * p; k <= 2 * p; k++)
+        j = __fmaf_rn(f2[k + 2 * p].x, __ll2float_rn(J1[node_at(i, k, nc) * kJStride]), j);
+      e = __fmaf_rn(-c_jstar, __fsub_rn(j, mean), e);
+    }
+    for (int k = 0; k < RE; k++) Es[q * RE + k] = e;
+  }
+}
+
+// kick F E^{n+1/2} = kick F E^n - kick dt/2 jscale (F^2 j2 - <j2>) on the
+// padded nodes in float pairs, RE copies each
+template <int RE, int PAD>
+__device__ __noinline__ void ehalf_table_filtered(int nc, int p, ff kick_jhalf, const float2 *filt,
+                                                  const float2 *Ek, const long long *J2, ff mean,
+                                                  float2 *Eh2, int npad) {
+  const float2 *f2 = filt + 2 * p + 1;
+  for (int q = threadIdx.x; q < npad; q += blockDim.x) {
+    const int i = wrap_node(q - PAD, nc);
+    ff e{0.0f, 0.0f}, j{0.0f, 0.0f};
+    for (int k = -p; k <= p; k++) {
+      const float2 ek = Ek[node_at(i, k, nc)], f = filt[k + p];
+      e = ff_add(e, ff_mul(ff{f.x, f.y}, ff{ek.x, ek.y}));
+    }
+    for (int k = -2 * p; k <= 2 * p; k++) {
+      const float2 f = f2[k + 2 * p];
+      j = ff_add(j, ff_mul(ff{f.x, f.y}, ff_from_i64(J2[node_at(i, k, nc) * kJStride])));
+    }
+    const ff eh = ff_sub(e, ff_mul(kick_jhalf, ff_sub(j, mean)));
+    for (int k = 0; k < RE; k++) Eh2[q * RE + k] = make_float2(eh.hi, eh.lo);
+  }
+}
+
+// (F^p j2)_i in FP64, as the state's Ampere update uses it
+__device__ __noinline__ double filtered_j(int nc, int p, const float2 *filt, const long long *J2,
+                                          int i) {
+  double j = 0.0;
+  for (int k = -p; k <= p; k++) {
+    const float2 f = filt[k + p];
+    j = fma((double)f.x + (double)f.y, (double)J2[node_at(i, k, nc) * kJStride], j);
+  }
+  return j;
+}
+
 // Zeroes 2 RT npad counters (RT > 1: the count is a multiple of 4, 16-byte aligned).
 template <int RT>
 __device__ __forceinline__ void clear_tile(unsigned *Jt, int npad) {
@@ -536,10 +606,13 @@ constexpr int kGroupE = 4;
 constexpr bool kPrefetchC = true;
 constexpr bool kPrefetchE = false;
 
-template <int ORDER, int SCHEME, int MODE, int RT, int RE>
+// FILT: the unsorted kernels are built with and without the filter's table
+// code (the sorted ones test c.passes at run time)
+template <int ORDER, int SCHEME, int MODE, int RT, int RE, bool FILT = false>
 __device__ __forceinline__ void pass_c_body(const Es1dMixConst &c, const Es1dMixBufs &b, int par,
                                             int prev_slot, int prev_nblocks, BlockPlace P) {
   constexpr bool AGG = MODE > 0;
+  constexpr bool kFilterCode = FILT || MODE > 0;
   constexpr int PAD = Pad<ORDER>::kPad;
   static_assert(!AGG || RT == 1, "sorted modes use a single tile copy");
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -563,16 +636,21 @@ __device__ __forceinline__ void pass_c_body(const Es1dMixConst &c, const Es1dMix
     const float2 E0 = has0 ? Ek[i0] : make_float2(0.0f, 0.0f);
     const long long J0 = (SCHEME == 2 && has0) ? J1[i0 * kJStride] : 0;
     const float mean = (SCHEME == 2 && c.remove_mean) ? mean_of_total(b.Jtot[par], c).hi : 0.0f;
-    for (int q = threadIdx.x; q < npad; q += blockDim.x) {
-      const int i = wrap_node(q - PAD, c.nc);
-      const bool first = q == (int)threadIdx.x;
-      const float2 ek = first ? E0 : Ek[i];
-      float e = __fmul_rn(0.5f, __fadd_rn(ek.x, ek.y));
-      if (SCHEME == 2) {
-        const float dj = __fsub_rn(__ll2float_rn(first ? J0 : J1[i * kJStride]), mean);
-        e = __fmaf_rn(-c.c_jstar, dj, e);
+    if (kFilterCode && c.passes > 0) {
+      estar_table_filtered<SCHEME, RE, PAD>(c.nc, c.passes, c.c_jstar, b.filt, Ek, J1, mean, Es,
+                                            npad);
+    } else {
+      for (int q = threadIdx.x; q < npad; q += blockDim.x) {
+        const int i = wrap_node(q - PAD, c.nc);
+        const bool first = q == (int)threadIdx.x;
+        const float2 ek = first ? E0 : Ek[i];
+        float e = __fmul_rn(0.5f, __fadd_rn(ek.x, ek.y));
+        if (SCHEME == 2) {
+          const float dj = __fsub_rn(__ll2float_rn(first ? J0 : J1[i * kJStride]), mean);
+          e = __fmaf_rn(-c.c_jstar, dj, e);
+        }
+        store_copies<RE>(Es + q * RE, e);
       }
-      store_copies<RE>(Es + q * RE, e);
     }
   }
   if (P.rb == 0 && SCHEME == 2) {
@@ -639,19 +717,20 @@ __device__ __forceinline__ void pass_c_body(const Es1dMixConst &c, const Es1dMix
       b.H[(int64_t)i * P.nb + P.rb] = hist[i];
 }
 
-template <int ORDER, int SCHEME, int MODE, int RT, int RE>
+template <int ORDER, int SCHEME, int MODE, int RT, int RE, bool FILT>
 __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
     mix_pass_c_kernel(Es1dMixConst c, Es1dMixBufs b, int par, int prev_slot, int prev_nblocks) {
-  pass_c_body<ORDER, SCHEME, MODE, RT, RE>(c, b, par, prev_slot, prev_nblocks, grid_place());
+  pass_c_body<ORDER, SCHEME, MODE, RT, RE, FILT>(c, b, par, prev_slot, prev_nblocks, grid_place());
 }
 
 // pass E: E^{n+1} and dt (q/m) cxk E^{n+1/2} (float pairs) in the prologue; per
 // marker the gather at x^{n+1/2} = X + [V*], v^dag, Gamma, x^{n+1}, v^{n+1},
 // the kinetic energy and (ESEC2) the next step's x* and j^{n+1,*} deposit.
-template <int ORDER, int SCHEME, int MODE, int RT, int RE, bool G64 = false>
+template <int ORDER, int SCHEME, int MODE, int RT, int RE, bool G64 = false, bool FILT = false>
 __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMixBufs &b, int par,
                                             int slot, BlockPlace P) {
   constexpr bool AGG = MODE > 0;
+  constexpr bool kFilterCode = FILT || MODE > 0;
   constexpr int PAD = Pad<ORDER>::kPad;
   static_assert(!AGG || RT == 1, "sorted modes use a single tile copy");
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -681,23 +760,29 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
     const float2 E0 = has0 ? Ek[i0] : make_float2(0.0f, 0.0f);
     const long long J0 = has0 ? J2[i0 * kJStride] : 0;
     if (c.remove_mean) mean2.j = mean_of_total(b.Jtot[2 + par], c);
-    for (int q = threadIdx.x; q < npad; q += blockDim.x) {
-      const int i = wrap_node(q - PAD, c.nc);
-      const bool first = q == (int)threadIdx.x;
-      const float2 ek = first ? E0 : Ek[i];
-      const ff dj = ff_sub(ff_from_i64(first ? J0 : J2[i * kJStride]), mean2.j);
-      const ff eh = ff_sub(ff{ek.x, ek.y}, ff_mul(c.kick_jhalf, dj));
-      store_copies<RE>(Eh2 + q * RE, make_float2(eh.hi, eh.lo));
+    if (kFilterCode && c.passes > 0) {
+      ehalf_table_filtered<RE, PAD>(c.nc, c.passes, c.kick_jhalf, b.filt, Ek, J2, mean2.j, Eh2,
+                                    npad);
+    } else {
+      for (int q = threadIdx.x; q < npad; q += blockDim.x) {
+        const int i = wrap_node(q - PAD, c.nc);
+        const bool first = q == (int)threadIdx.x;
+        const float2 ek = first ? E0 : Ek[i];
+        const ff dj = ff_sub(ff_from_i64(first ? J0 : J2[i * kJStride]), mean2.j);
+        const ff eh = ff_sub(ff{ek.x, ek.y}, ff_mul(c.kick_jhalf, dj));
+        store_copies<RE>(Eh2 + q * RE, make_float2(eh.hi, eh.lo));
+      }
     }
   }
   __syncthreads();
 
-  // E^{n+1} = E^n - dt (jscale J2 - jscale <J2>) in FP64 on the nodes
-  // [b nc / grid, (b + 1) nc / grid) by the last warp of block b, before its
-  // markers (with a block's groups not a multiple of its threads, the last
-  // warp has one trip fewer): the field, its float-pair table for the next
-  // step, the cleared J2 of the next step and this block's part of
-  // sum (E^{n+1})^2.  Nothing in this pass reads what it writes.
+  // E^{n+1} = E^n - dt (jscale J2 - jscale <J2>) (F^p J2 with the filter) in
+  // FP64 on the nodes [b nc / grid, (b + 1) nc / grid) by the last warp of
+  // block b, before its markers (with a block's groups not a multiple of its
+  // threads, the last warp has one trip fewer): the field, its float-pair
+  // table for the next step, the cleared J2 of the next step and this
+  // block's part of sum (E^{n+1})^2.  Nothing in this pass reads what it
+  // writes.
   if (last_warp()) {
     const unsigned lane = threadIdx.x & 31u;
     const double *E = PSEL(b.E, par);
@@ -707,7 +792,9 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
     const int n1 = (int)((int64_t)c.nc * (P.rb + 1) / P.nb);
     double w = 0.0;
     for (int i = n0 + (int)lane; i < n1; i += 32) {
-      const double en = E[i] - c.dt * ((double)J2[i * kJStride] * c.jscale - mean_e);
+      const double j = kFilterCode && c.passes > 0 ? filtered_j(c.nc, c.passes, b.filt, J2, i)
+                                                   : (double)J2[i * kJStride];
+      const double en = E[i] - c.dt * (j * c.jscale - mean_e);
       PSEL(b.E, par ^ 1)[i] = en;
       const ff k = ff_from_double(c.kick * en);
       PSEL(b.Ek, par ^ 1)[i] = make_float2(k.hi, k.lo);
@@ -830,10 +917,10 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
   if (SCHEME == 2) flush_tile<ORDER, RT>(Jt, PSEL(b.J1, par ^ 1), b.Jtot + (par ^ 1), c.nc, c.split);
 }
 
-template <int ORDER, int SCHEME, int MODE, int RT, int RE, bool G64>
+template <int ORDER, int SCHEME, int MODE, int RT, int RE, bool G64, bool FILT>
 __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
     mix_pass_e_kernel(Es1dMixConst c, Es1dMixBufs b, int par, int slot) {
-  pass_e_body<ORDER, SCHEME, MODE, RT, RE, G64>(c, b, par, slot, grid_place());
+  pass_e_body<ORDER, SCHEME, MODE, RT, RE, G64, FILT>(c, b, par, slot, grid_place());
 }
 
 // ESEC1 in one pass per step (Eq. naivetranslation with the correction of Eq.
@@ -1297,14 +1384,21 @@ void dispatch_mix(const Es1dMixConst &c, F f) {
   using R32 = std::integral_constant<int, 32>;
   using G0 = std::false_type;
   using G1 = std::true_type;
-  // the FP64 correction for every marker (gamma64) is built for the unsorted mode
+  using F0 = std::false_type;
+  using F1 = std::true_type;
+  // the FP64 correction for every marker (gamma64) is built for the unsorted
+  // mode without the filter; the unsorted kernels with the filter (F1) are
+  // separate instantiations, the sorted ones test c.passes at run time
+  const bool filt = c.passes > 0;
   auto go = [&](auto O, auto S) {
-    if (c.mode == 0 && c.wide && !c.gamma64) f(O, S, M0(), R32(), R16(), G0());
-    if (c.mode == 0 && c.wide && c.gamma64) f(O, S, M0(), R32(), R16(), G1());
-    if (c.mode == 0 && !c.wide && !c.gamma64) f(O, S, M0(), R1(), R1(), G0());
-    if (c.mode == 0 && !c.wide && c.gamma64) f(O, S, M0(), R1(), R1(), G1());
-    if (c.mode == 1) f(O, S, M1(), R1(), R1(), G0());
-    if (c.mode == 2) f(O, S, M2(), R1(), R1(), G0());
+    if (c.mode == 0 && c.wide && !c.gamma64 && !filt) f(O, S, M0(), R32(), R16(), G0(), F0());
+    if (c.mode == 0 && c.wide && !c.gamma64 && filt) f(O, S, M0(), R32(), R16(), G0(), F1());
+    if (c.mode == 0 && c.wide && c.gamma64) f(O, S, M0(), R32(), R16(), G1(), F0());
+    if (c.mode == 0 && !c.wide && !c.gamma64 && !filt) f(O, S, M0(), R1(), R1(), G0(), F0());
+    if (c.mode == 0 && !c.wide && !c.gamma64 && filt) f(O, S, M0(), R1(), R1(), G0(), F1());
+    if (c.mode == 0 && !c.wide && c.gamma64) f(O, S, M0(), R1(), R1(), G1(), F0());
+    if (c.mode == 1) f(O, S, M1(), R1(), R1(), G0(), F0());
+    if (c.mode == 2) f(O, S, M2(), R1(), R1(), G0(), F0());
   };
   if (c.order == 1 && c.scheme == 1) go(I1(), I1());
   if (c.order == 1 && c.scheme == 2) go(I1(), I2());
@@ -1350,14 +1444,14 @@ void dispatch_fused(const Es1dMixConst &c, F f) {
 
 cudaError_t es1d_mix_prepare(const Es1dMixConst &c) {
   cudaError_t e = cudaSuccess;
-  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE, auto G) {
+  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE, auto G, auto F) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
     constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
-    constexpr bool G64 = decltype(G)::value;
-    e = cudaFuncSetAttribute(mix_pass_c_kernel<ORDER, SCHEME, MODE, NT, NE>,
+    constexpr bool G64 = decltype(G)::value, FILT = decltype(F)::value;
+    e = cudaFuncSetAttribute(mix_pass_c_kernel<ORDER, SCHEME, MODE, NT, NE, FILT>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c(c));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE, G64>,
+      e = cudaFuncSetAttribute(mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE, G64, FILT>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e(c));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mix_deposit_initial_kernel<ORDER>,
@@ -1382,22 +1476,23 @@ cudaError_t es1d_mix_prepare(const Es1dMixConst &c) {
 void es1d_mix_pass_c(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_index, int slot,
                      LaunchShape ls, cudaStream_t st) {
   int par = (int)(step_index & 1);
-  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE, auto) {
+  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE, auto, auto F) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
     constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
-    launch_dependent(mix_pass_c_kernel<ORDER, SCHEME, MODE, NT, NE>, ls, smem_c(c), st, true, c,
-                     b, par, slot - 1, ls.grid);
+    launch_dependent(mix_pass_c_kernel<ORDER, SCHEME, MODE, NT, NE, decltype(F)::value>, ls,
+                     smem_c(c), st, true, c, b, par, slot - 1, ls.grid);
   });
 }
 
 void es1d_mix_pass_e(const Es1dMixConst &c, const Es1dMixBufs &b, int64_t step_index, int slot,
                      LaunchShape ls, cudaStream_t st) {
   int par = (int)(step_index & 1);
-  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE, auto G) {
+  dispatch_mix(c, [&](auto O, auto S, auto M, auto RT, auto RE, auto G, auto F) {
     constexpr int ORDER = decltype(O)::value, SCHEME = decltype(S)::value;
     constexpr int MODE = decltype(M)::value, NT = decltype(RT)::value, NE = decltype(RE)::value;
-    launch_dependent(mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE, decltype(G)::value>, ls,
-                     smem_e(c), st, true, c, b, par, slot);
+    launch_dependent(
+        mix_pass_e_kernel<ORDER, SCHEME, MODE, NT, NE, decltype(G)::value, decltype(F)::value>,
+        ls, smem_e(c), st, true, c, b, par, slot);
   });
 }
 

@@ -513,8 +513,30 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   m.kick_jhalf = ff_from_double(m.kick * 0.5 * c.dt * m.jscale);
   m.inv_nc = ff_from_double(1.0 / c.nc);
   m.c_jstar = (float)(m.e_scale * 0.5 * c.dt * m.jscale);
+  m.passes = c.passes;
   CUDA_TRY(es1d_mix_prepare(m));
   Es1dMixBufs &bm = h->bm;
+  bm.filt = nullptr;
+  if (m.passes > 0) {
+    // the stencils of F^p and F^2p: C(2p, p + k) / 4^p, C(4p, 2p + k) / 16^p
+    // (exact doubles, exact float pairs)
+    std::vector<float2> w;
+    for (int n : {2 * m.passes, 4 * m.passes}) {
+      double cnk = 1.0;
+      const double scale = std::ldexp(1.0, -n);
+      for (int k = 0; k <= n; k++) {
+        const ff f = ff_from_double(cnk * scale);
+        w.push_back(make_float2(f.hi, f.lo));
+        cnk = cnk * (n - k) / (k + 1);
+      }
+    }
+    float2 *filt = nullptr;
+    if ((rc = h->alloc(&filt, w.size()))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(filt, w.data(), sizeof(float2) * w.size(), cudaMemcpyHostToDevice,
+                             h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    bm.filt = filt;
+  }
   size_t npad = (size_t)((h->N + 3) / 4 * 4);
   if ((rc = h->alloc(&bm.X, npad)) || (rc = h->alloc(&bm.vh, npad)) || (rc = h->alloc(&bm.vl, npad)) ||
       (rc = h->alloc(&bm.Vs, npad)))
@@ -541,7 +563,7 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   if ((rc = h->alloc(&h->jtot_base, 8))) return rc;
   CUDA_TRY(cudaMemsetAsync(h->jtot_base, 0, sizeof(long long) * 8, h->st));
   bm.Jtot = h->jtot_base + 4;
-  h->fused = m.scheme == 1 && m.mode == 0 && !h->cfg.separate_passes;
+  h->fused = m.scheme == 1 && m.mode == 0 && !h->cfg.separate_passes && m.passes == 0;
   h->primed = false;
   if (h->fused && ((rc = h->alloc(&h->ke_alt, (size_t)h->ls.grid)) ||
                    (rc = h->alloc(&h->we_alt, (size_t)h->ls.grid))))
@@ -578,8 +600,14 @@ int init_mixed(pic_handle *h, bool solve_e0) {
     std::vector<long long> ci(c.nc);
     CUDA_TRY(cudaMemcpyAsync(ci.data(), cnt, sizeof(long long) * c.nc, cudaMemcpyDeviceToHost, h->st));
     CUDA_TRY(cudaStreamSynchronize(h->st));
-    std::vector<double> r(c.nc), e;
+    std::vector<double> r(c.nc), e, t(c.nc);
     for (int i = 0; i < c.nc; i++) r[i] = S.q * S.w0 / c.h * std::ldexp((double)ci[i], -23);
+    // with the filter inside the scheme, Gauss's law of the filtered charge
+    for (int k = 0; k < m.passes; k++) {
+      for (int i = 0; i < c.nc; i++)
+        t[i] = 0.25 * (r[(i + c.nc - 1) % c.nc] + 2.0 * r[i] + r[(i + 1) % c.nc]);
+      r.swap(t);
+    }
     poisson_1d_host(r, c.L, e);
     CUDA_TRY(cudaMemcpyAsync(b.E[0], e.data(), sizeof(double) * c.nc, cudaMemcpyHostToDevice, h->st));
     CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(long long) * c.nc, h->st));
@@ -1288,19 +1316,18 @@ int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, co
   if (cfg->separate_passes != 0 && cfg->separate_passes != 1)
     return fail(PIC_ERR_ARG, "pic_init: separate_passes must be 0 or 1");
   if (cfg->gamma_fp64 && cfg->precision == PIC_PREC_MIXED &&
-      (cfg->solver != PIC_SOLVER_AMPERE_ES || cfg->sort_period != 0))
+      (cfg->solver != PIC_SOLVER_AMPERE_ES || cfg->sort_period != 0 || cfg->binomial_passes != 0))
     return fail(PIC_ERR_UNSUPPORTED, "pic_init: gamma_fp64 is built for the mixed form of the "
-                                     "Ampere solver with sort_period 0");
+                                     "Ampere solver with sort_period 0 and no filter");
   if (cfg->charge_conserving &&
       (cfg->solver != PIC_SOLVER_YEE_LEAPFROG || cfg->precision != PIC_PREC_FP64 ||
        cfg->shape_order != 1))
     return fail(PIC_ERR_UNSUPPORTED, "pic_init: charge_conserving runs the Yee solver in the FP64 "
                                      "form with shape_order 1");
   if (cfg->binomial_passes != 0 &&
-      !(cfg->solver == PIC_SOLVER_STANDARD_LEAPFROG ||
-        (cfg->solver == PIC_SOLVER_AMPERE_ES && cfg->precision == PIC_PREC_FP64)))
-    return fail(PIC_ERR_UNSUPPORTED, "pic_init: binomial_passes is for the standard solver and "
-                                     "the FP64 form of the Ampere solver");
+      !(cfg->solver == PIC_SOLVER_STANDARD_LEAPFROG || cfg->solver == PIC_SOLVER_AMPERE_ES))
+    return fail(PIC_ERR_UNSUPPORTED, "pic_init: binomial_passes is for the standard and the "
+                                     "Ampere solvers");
   if (cfg->solver == PIC_SOLVER_AMPERE_ES) {
     if (cfg->grid.dim_x != 1 || cfg->grid.dim_v != 1)
       return fail(PIC_ERR_ARG, "pic_init: the Ampere solver runs 1D1V (dim_x = dim_v = 1)");
@@ -2298,10 +2325,11 @@ int pic_batch_init(const pic_config *cfgs, const pic_species *species, int nruns
     const pic_config &c = cfgs[r];
     if (c.solver != PIC_SOLVER_AMPERE_ES || c.precision != PIC_PREC_MIXED || c.sort_period != 0 ||
         c.grid.n[0] > kWideMaxNodes || c.scheme != cfgs[0].scheme ||
-        c.cuda_stream != cfgs[0].cuda_stream || c.gamma_fp64 != 0)
+        c.cuda_stream != cfgs[0].cuda_stream || c.gamma_fp64 != 0 || c.binomial_passes != 0)
       return fail(PIC_ERR_UNSUPPORTED,
                   "pic_batch_init: run %d: batches take unsorted mixed-form 1D runs with at most "
-                  "%d nodes, one scheme, one stream and gamma_fp64 = 0", r, kWideMaxNodes);
+                  "%d nodes, one scheme, one stream, gamma_fp64 = 0 and no filter", r,
+                  kWideMaxNodes);
   }
   pic_batch *b = new pic_batch();
   b->scheme = cfgs[0].scheme;

@@ -74,6 +74,7 @@ struct Es1dMixConst {
   ff kick_jhalf;       // kick dt/2 jscale as a float pair: J units -> kick E units
   ff inv_nc;           // 1 / nc as a float pair
   float c_jstar;       // e_scale dt/2 jscale: J units -> kick-table units of E*
+  int passes;          // p passes of the binomial filter inside the scheme (0: none)
 };
 
 // One block of a batched launch over several independent runs: block rb of the
@@ -123,6 +124,9 @@ struct Es1dMixBufs {
   double *we;
   double *we_part;          // [grid] per-block W_E partials of the newest field
   unsigned *err;
+  // passes > 0: the stencils of F^p (2p + 1 weights) and of F^2p (4p + 1) as
+  // float pairs (exact: binomial coefficients over powers of 4)
+  const float2 *filt;
 };
 
 // Per-launch constants of the 2D3V Yee kernels (FP64 form).

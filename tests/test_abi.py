@@ -71,9 +71,11 @@ def test_argument_errors_are_status_codes(lib):
         pic.pic_init(pic.make_config(64, 1.0, 0.1, precision=pic.PIC_PREC_MIXED,
                                      solver=pic.PIC_SOLVER_PSATD, dim_v=2), sp * 2)
     assert ei.value.code == -7
-    with pytest.raises(pic.PicError) as ei:   # no filtering in the mixed form
+    with pytest.raises(pic.PicError) as ei:   # no filtering in the Yee solver
         pic.pic_init(pic.make_config(64, 1.0, 0.1, binomial_passes=1,
-                                     precision=pic.PIC_PREC_MIXED), sp)
+                                     precision=pic.PIC_PREC_MIXED,
+                                     solver=pic.PIC_SOLVER_YEE_LEAPFROG, dim_x=2, dim_v=3,
+                                     ny=64, Ly=1.0), sp)
     assert ei.value.code == -7
     with pytest.raises(pic.PicError) as ei:
         pic.pic_init(pic.make_config(64, 1.0, 0.1, binomial_passes=9), sp)
@@ -105,9 +107,10 @@ def test_batch_argument_errors_are_status_codes(lib):
     x = np.array([0.5])
     v = np.array([0.1])
     sp = [dict(q=-1.0, m=1.0, x=x, v=v, w=None, w0=1.0)]
-    # not batchable: FP64 form, sorted markers, more than 512 nodes, mixed schemes
+    # not batchable: FP64 form, sorted markers, the filter, more than 512 nodes, mixed schemes
     for cfgs in ([pic.make_config(64, 1.0, 0.1)],
                  [pic.make_config(64, 1.0, 0.1, precision=pic.PIC_PREC_MIXED, sort_period=4)],
+                 [pic.make_config(64, 1.0, 0.1, precision=pic.PIC_PREC_MIXED, binomial_passes=1)],
                  [pic.make_config(1024, 1.0, 0.1, precision=pic.PIC_PREC_MIXED)],
                  [pic.make_config(64, 1.0, 0.1, precision=pic.PIC_PREC_MIXED),
                   pic.make_config(64, 1.0, 0.1, scheme=pic.PIC_SCHEME_ESEC1,

@@ -1,13 +1,14 @@
-"""GPU parity of the energy-conserving FP64 1D scheme with binomial filtering
-inside it (binomial_passes > 0: Ampere uses F j, the gathers F E), against the
-oracle, and its energy conservation.  The initial field is Gauss's law of the
-filtered charge on both sides."""
+"""GPU parity of the energy-conserving 1D scheme with binomial filtering inside
+it (binomial_passes > 0: Ampere uses F j, the gathers F E), against the
+oracle, and its energy conservation, in the FP64 form (to 1e-11) and in the
+mixed form (to its quanta, tests/parity_util.mixed_bars).  The initial field
+is Gauss's law of the filtered charge on both sides."""
 import numpy as np
 import pytest
 
 from oracle import oracle as O
 from paper_2411_09605_gb300 import workloads as W
-from tests.parity_util import compare
+from tests.parity_util import compare, mixed_bars, periodic_dist
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
@@ -87,3 +88,71 @@ def test_filter_declined_where_not_built():
         assert ei.value.code == -7
     finally:
         sim.close()
+
+
+def _mixed(prob, scheme, passes, steps, E0=None, sort_period=0):
+    from paper_2411_09605_gb300 import pic
+    sim = pic.Simulation(prob, scheme=scheme, precision=1, binomial_passes=passes, E0=E0,
+                         sort_period=sort_period)
+    try:
+        E_init = sim.field()
+        te0 = sim.energy()[3]
+        fb, te = sim.step(steps)
+        x, v = sim.particles(0)
+        E = sim.field()
+        res = pic.pic_mixed_resolution(sim.h)
+    finally:
+        sim.close()
+    return dict(x=[x], v=[v], E=E, nfb=fb, te=np.concatenate([[te0], te]), E0=E_init,
+                resolution=res)
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("order", [1, 2])
+def test_filtered_mixed_parity(order, scheme, passes):
+    """The mixed form with the filter against the oracle's filtered scheme from
+    the same initial field: markers within the mixed bars, E within 3e-6,
+    fallback counts equal; TE kept to round-off on steps without fallbacks."""
+    prob = W.two_stream(n=40_009, nc=128, order=order, seed=order + 2 * scheme + 5 * passes)
+    ref = _oracle(prob, scheme, passes, 10)
+    got = _mixed(prob, scheme, passes, 10, E0=ref["E0"])
+    dx, dv, _ = got["resolution"]
+    s = prob.species[0]
+    Emax = max(np.max(np.abs(ref["E0"])), np.max(np.abs(ref["E"])))
+    b = mixed_bars(ref["v"][0], got["v"][0], periodic_dist(ref["x"][0], got["x"][0], prob.L),
+                   prob.L / prob.nc, dx, dv, prob.dt, s.q / s.m, Emax, 10)
+    assert b["x"] <= 1.0 and b["v"] <= 1.0, b
+    assert compare(prob, ref, got)["E"] <= 3e-6
+    assert np.array_equal(got["nfb"], ref["nfb"])
+    d = np.abs(np.diff(got["te"])) / got["te"][0]
+    assert np.all(d[got["nfb"] == 0] <= 1e-13), d
+
+
+def test_filtered_mixed_initial_field():
+    """Without E0 the mixed form solves Gauss's law of the filtered charge of
+    its own quantised weights: the oracle's filtered field to the weights'
+    2^-23."""
+    prob = W.two_stream(n=40_009, nc=128, order=2, seed=11)
+    for passes in (1, 3):
+        ref = _oracle(prob, 2, passes, 0)
+        got = _mixed(prob, 2, passes, 1)
+        assert np.linalg.norm(got["E0"] - ref["E0"]) <= 1e-6 * np.linalg.norm(ref["E0"])
+
+
+def test_filtered_mixed_energy_long_and_sorted():
+    """1e6 markers, 300 steps with two filter passes: per-step TE changes on
+    steps without fallbacks at round-off; the cell-sorted modes give the
+    unsorted run bit for bit (exact integer currents)."""
+    prob = W.two_stream(n=1 << 20, nc=512, seed=13)
+    res = {}
+    for sp in (0, 1, 4):
+        got = _mixed(prob, 2, 2, 300 if sp == 0 else 20, sort_period=sp)
+        res[sp] = got
+    d = np.abs(np.diff(res[0]["te"])) / res[0]["te"][0]
+    assert np.all(d[res[0]["nfb"] == 0] <= 1e-13), np.max(d)
+    short = _mixed(prob, 2, 2, 20)
+    for sp in (1, 4):
+        for key in ("x", "v"):
+            assert np.array_equal(short[key][0], res[sp][key][0]), (sp, key)
+        assert np.array_equal(short["E"], res[sp]["E"]) and np.array_equal(short["nfb"], res[sp]["nfb"])
