@@ -410,9 +410,12 @@ def cpu_baseline_oracle(markers: int, seed: int, budget_s: float = 10.0, max_ste
 
 
 def full_run(prob, form: str, steps: int):
-    """The workload's whole run, untimed: energy error over the run (max over the
-    steps of |TE^n - TE^0| / TE^0), the largest change of one step without a
-    fallback (relative to TE^0), and the fallbacks (Sec. 5.1)."""
+    """The workload's whole run: energy error over the run (max over the steps
+    of |TE^n - TE^0| / TE^0), the largest change of one step without a
+    fallback (relative to TE^0), the fallbacks (Sec. 5.1), and the run's own
+    throughput (wall clock around all steps, the stats read every 1000 steps,
+    no L2 flush: the saturated phase, where the correction's FP64 path is
+    taken, is inside it)."""
     from paper_2411_09605_gb300 import pic
     mixed = form.startswith("mixed")
     sim = pic.Simulation(prob, scheme=1 if "esec1" in form else 2,
@@ -421,16 +424,19 @@ def full_run(prob, form: str, steps: int):
     try:
         te0 = sim.energy()[3]
         fbs, tes = [], []
+        t0 = time.perf_counter()
         for k in range(0, steps, 1000):
             fb, te = sim.step(min(1000, steps - k))
             fbs.append(fb)
             tes.append(te)
+        wall = time.perf_counter() - t0
     finally:
         sim.close()
     fb, te = np.concatenate(fbs), np.concatenate(tes)
     d = np.abs(np.diff(np.concatenate([[te0], te]))) / abs(te0)
     first = int(np.argmax(fb > 0)) if fb.any() else -1
-    return {"steps": steps, "max_rel_dTE": float(np.max(np.abs(te - te0)) / abs(te0)),
+    return {"steps": steps, "particle_steps_per_s": prob.n_markers * steps / wall,
+            "max_rel_dTE": float(np.max(np.abs(te - te0)) / abs(te0)),
             "max_step_dTE_without_fallback": float(np.max(d[fb == 0], initial=0.0)),
             "fallbacks": int(fb.sum()), "first_fallback_step": first,
             "max_rel_dTE_before_first_fallback":
