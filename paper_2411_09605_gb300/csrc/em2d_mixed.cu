@@ -15,8 +15,8 @@
 //   * weights: quantised B-spline values (multiples of 2^-23) per axis; the
 //     gather of E^{n+1/2} and the deposit of j^{*,n+1/2} use the same
 //     integers s_x s_y, as Eq. exp_econs_simple requires.
-//   * current: each marker adds round(V*_c s_x s_y / 2^r) (r >= 32, so no
-//     node sum overflows) to the int64 node sums with global atomics: exact
+//   * current: each marker adds floor(V*_c s_x s_y / 2^r + 1/2) (r >= 32, so
+//     no node sum overflows) to the int64 node sums with global atomics: exact
 //     integer sums, independent of the marker order.  With sort_period P the
 //     markers are kept in quarter-cell order (written so by pass E every P
 //     steps), and the terms of a thread's consecutive markers in one quarter
@@ -30,8 +30,10 @@
 //     (whatever rounding the B table had).
 //   * Gamma (Eq. opt_solution): with Delta = v^dag - v^n = d + mu,
 //     |v^{n+1}|^2 - |v^dag|^2 = 2 Delta . (V* - v^n - Delta/2), the bracket
-//     from the exact difference V* - v^n per component, then
-//     Gamma - 1 = t / (1 + sqrt(1 + t)), t = 2a / |v^dag|^2, in float pairs.
+//     from the exact difference V* - v^n per component, t = 2a / |v^dag|^2,
+//     and Gamma - 1 = t / (1 + sqrt(1 + t)): a 4-term FP32 series for
+//     |t| < 2^-8, FP64 otherwise (every candidate for the fallback among
+//     them).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -188,12 +190,12 @@ __device__ __forceinline__ void deposit_j(const Em2dMixConst &c, long long *J,
   deposit_c<ORDER>(J + 2 * nc, nx, S.xI, S.yI, V[2], c);
 }
 
-// Segments of a warp's lanes for one current component: neighbouring lanes
-// with equal keys (the component's first stencil node) form a segment.  With
-// the markers sorted by quarter cell, the lanes of a warp hold a few segments,
-// and each segment's deposits can be summed over its lanes before one atomic
-// per node: exact integer sums, so the result is the per-marker atomics' bit
-// for bit, whatever the order (an unsorted warp only gets shorter segments).
+// Segments of a warp's lanes: neighbouring lanes with equal keys (the quarter
+// cell of their deposit runs) form a segment.  With the markers sorted by
+// quarter cell, the lanes of a warp hold a few segments, and each segment's
+// deposits can be summed over its lanes before one atomic per node: exact
+// integer sums, so the result is the per-marker atomics' bit for bit, whatever
+// the order (an unsorted warp only gets shorter segments).
 struct WarpSegments {
   int start;  // first lane of this lane's segment
   bool tail;  // this lane ends its segment
@@ -257,7 +259,8 @@ struct DepositRun {
     }
   }
 
-  // sums v[d][t] into the nodes of the run's stencil (zero sums skipped)
+  // adds sum(d, i) to node i of component d's stencil at the run's point (zero
+  // sums skipped)
   template <typename F>
   __device__ __forceinline__ void to_grid(const Em2dMixConst &c, long long *J, F &&sum) const {
     const int nx = c.nx, nc = c.nx * c.ny;
