@@ -385,8 +385,10 @@ typedef struct pic_batch pic_batch;
 /* Creates nruns runs, run r from cfgs[r] and the single species species[r],
  * as pic_init would (E0 from the Poisson solve).  Every run must use
  * PIC_SOLVER_AMPERE_ES, PIC_PREC_MIXED, sort_period 0, at most 512 nodes, the
- * same scheme and the same cuda_stream, else PIC_ERR_UNSUPPORTED.  The batch
- * owns the runs and frees them in pic_batch_free. */
+ * same scheme, the same cuda_stream, gamma_fp64 0 and binomial_passes 0, else
+ * PIC_ERR_UNSUPPORTED.  A batch whose runs all have at most 2^15 markers runs
+ * blocks of 256 threads, others blocks of 1024.  The batch owns the runs and
+ * frees them in pic_batch_free. */
 int pic_batch_init(const pic_config *cfgs, const pic_species *species, int nruns,
                    pic_batch **out);
 

@@ -1159,32 +1159,45 @@ __global__ void __launch_bounds__(512) mix_charge_kernel(Es1dMixConst c, Es1dMix
 // buffers (read-only arrays, read before the dependency wait) and the same
 // pass bodies as a single-run launch; the kernel boundaries remain the only
 // barriers between the passes.
-template <int SCHEME>
-__global__ void __launch_bounds__(1024, 1)
+// Batch blocks of NT threads: 1024 (32 tile copies, 16 table copies, one
+// block per SM) for runs of many markers, 256 (8 and 8, up to eight blocks per
+// SM) for batches of small runs, where a 1024-thread block would sit mostly
+// idle.  A copy takes at most 2048 markers a launch in both (16 trips).
+template <int NT>
+struct BatchLayout {
+  static constexpr int RT = NT == 1024 ? 32 : 8;
+  static constexpr int RE = NT == 1024 ? 16 : 8;
+  static constexpr int kMinBlocks = NT == 1024 ? 1 : 3;
+};
+
+template <int SCHEME, int NT>
+__global__ void __launch_bounds__(NT, BatchLayout<NT>::kMinBlocks)
     mix_batch_pass_c_kernel(const Es1dMixConst *__restrict__ cs, const Es1dMixBufs *__restrict__ bs,
                             const BatchItem *__restrict__ items, int par, int prev_slot) {
+  constexpr int RT = BatchLayout<NT>::RT, RE = BatchLayout<NT>::RE;
   const BatchItem it = items[blockIdx.x];
   const Es1dMixConst &c = cs[it.run];
   const Es1dMixBufs &b = bs[it.run];
   const BlockPlace P{it.rb, it.nb};
   if (c.order == 1)
-    pass_c_body<1, SCHEME, 0, 32, 16>(c, b, par, prev_slot, it.nb, P);
+    pass_c_body<1, SCHEME, 0, RT, RE>(c, b, par, prev_slot, it.nb, P);
   else
-    pass_c_body<2, SCHEME, 0, 32, 16>(c, b, par, prev_slot, it.nb, P);
+    pass_c_body<2, SCHEME, 0, RT, RE>(c, b, par, prev_slot, it.nb, P);
 }
 
-template <int SCHEME>
-__global__ void __launch_bounds__(1024, 1)
+template <int SCHEME, int NT>
+__global__ void __launch_bounds__(NT, BatchLayout<NT>::kMinBlocks)
     mix_batch_pass_e_kernel(const Es1dMixConst *__restrict__ cs, const Es1dMixBufs *__restrict__ bs,
                             const BatchItem *__restrict__ items, int par, int slot) {
+  constexpr int RT = BatchLayout<NT>::RT, RE = BatchLayout<NT>::RE;
   const BatchItem it = items[blockIdx.x];
   const Es1dMixConst &c = cs[it.run];
   const Es1dMixBufs &b = bs[it.run];
   const BlockPlace P{it.rb, it.nb};
   if (c.order == 1)
-    pass_e_body<1, SCHEME, 0, 32, 16>(c, b, par, slot, P);
+    pass_e_body<1, SCHEME, 0, RT, RE>(c, b, par, slot, P);
   else
-    pass_e_body<2, SCHEME, 0, 32, 16>(c, b, par, slot, P);
+    pass_e_body<2, SCHEME, 0, RT, RE>(c, b, par, slot, P);
 }
 
 // TE of step `slot` of every run (one warp per run).
@@ -1542,10 +1555,17 @@ void es1d_mix_set_ek(const Es1dMixConst &c, const Es1dMixBufs &b, int parity, cu
                                                          c.kick);
 }
 
-cudaError_t es1d_batch_prepare(size_t smem) {
+cudaError_t es1d_batch_prepare(size_t smem, int threads) {
   cudaError_t e = cudaSuccess;
-  for (auto k : {(const void *)mix_batch_pass_c_kernel<1>, (const void *)mix_batch_pass_c_kernel<2>,
-                 (const void *)mix_batch_pass_e_kernel<1>, (const void *)mix_batch_pass_e_kernel<2>})
+  const void *ks[4] = {(const void *)mix_batch_pass_c_kernel<1, 1024>,
+                       (const void *)mix_batch_pass_c_kernel<2, 1024>,
+                       (const void *)mix_batch_pass_e_kernel<1, 1024>,
+                       (const void *)mix_batch_pass_e_kernel<2, 1024>};
+  const void *ks_small[4] = {(const void *)mix_batch_pass_c_kernel<1, 256>,
+                             (const void *)mix_batch_pass_c_kernel<2, 256>,
+                             (const void *)mix_batch_pass_e_kernel<1, 256>,
+                             (const void *)mix_batch_pass_e_kernel<2, 256>};
+  for (const void *k : threads == 1024 ? ks : ks_small)
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return e;
@@ -1556,28 +1576,34 @@ size_t es1d_mix_smem_max(const Es1dMixConst &c) {
   return a > b ? a : b;
 }
 
+size_t es1d_batch_smem(const Es1dMixConst &c, int threads) {
+  if (threads == 1024) return es1d_mix_smem_max(c);
+  constexpr int RT = BatchLayout<256>::RT, RE = BatchLayout<256>::RE;
+  return npad_host(c) * (8 * RT + 8 * RE);  // pass E's (pass C's table is FP32)
+}
+
 void es1d_batch_pass_c(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,
-                       int nitems, int scheme, size_t smem, int64_t step_index, int prev_slot,
-                       cudaStream_t st) {
+                       int nitems, int scheme, int threads, size_t smem, int64_t step_index,
+                       int prev_slot, cudaStream_t st) {
   const int par = (int)(step_index & 1);
-  const LaunchShape ls{nitems, 1024};
-  if (scheme == 1)
-    launch_dependent(mix_batch_pass_c_kernel<1>, ls, smem, st, true, cs, bs, items, par,
-                     prev_slot);
-  else
-    launch_dependent(mix_batch_pass_c_kernel<2>, ls, smem, st, true, cs, bs, items, par,
-                     prev_slot);
+  const LaunchShape ls{nitems, threads};
+  auto k = threads == 1024 ? (scheme == 1 ? mix_batch_pass_c_kernel<1, 1024>
+                                          : mix_batch_pass_c_kernel<2, 1024>)
+                           : (scheme == 1 ? mix_batch_pass_c_kernel<1, 256>
+                                          : mix_batch_pass_c_kernel<2, 256>);
+  launch_dependent(k, ls, smem, st, true, cs, bs, items, par, prev_slot);
 }
 
 void es1d_batch_pass_e(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,
-                       int nitems, int scheme, size_t smem, int64_t step_index, int slot,
-                       cudaStream_t st) {
+                       int nitems, int scheme, int threads, size_t smem, int64_t step_index,
+                       int slot, cudaStream_t st) {
   const int par = (int)(step_index & 1);
-  const LaunchShape ls{nitems, 1024};
-  if (scheme == 1)
-    launch_dependent(mix_batch_pass_e_kernel<1>, ls, smem, st, true, cs, bs, items, par, slot);
-  else
-    launch_dependent(mix_batch_pass_e_kernel<2>, ls, smem, st, true, cs, bs, items, par, slot);
+  const LaunchShape ls{nitems, threads};
+  auto k = threads == 1024 ? (scheme == 1 ? mix_batch_pass_e_kernel<1, 1024>
+                                          : mix_batch_pass_e_kernel<2, 1024>)
+                           : (scheme == 1 ? mix_batch_pass_e_kernel<1, 256>
+                                          : mix_batch_pass_e_kernel<2, 256>);
+  launch_dependent(k, ls, smem, st, true, cs, bs, items, par, slot);
 }
 
 void es1d_batch_finalize(const Es1dMixConst *cs, const Es1dMixBufs *bs, const int *nblocks,

@@ -2250,7 +2250,8 @@ struct pic_batch {
   int scheme = 2;
   size_t smem = 0;
   int nitems = 0;
-  int trips = 8;  // target 4-marker trips per 1024-thread block of a run
+  int trips = 8;  // target 4-marker trips per block of a run
+  int threads = 1024;  // block size of the passes (256 for batches of small runs)
   bool prev_closed = false;  // the last pending step's TE was reduced already
   Es1dMixConst *d_c = nullptr;
   Es1dMixBufs *d_b = nullptr;
@@ -2281,29 +2282,38 @@ struct pic_batch {
     for (int k = 0; k < nsteps; k++) {
       const int64_t step = steps_done + k;
       const int prev = (k == 0 && prev_closed) ? -1 : first_slot + k - 1;
-      es1d_batch_pass_c(d_c, d_b, d_items, nitems, scheme, smem, step, prev, st);
-      es1d_batch_pass_e(d_c, d_b, d_items, nitems, scheme, smem, step, first_slot + k, st);
+      es1d_batch_pass_c(d_c, d_b, d_items, nitems, scheme, threads, smem, step, prev, st);
+      es1d_batch_pass_e(d_c, d_b, d_items, nitems, scheme, threads, smem, step, first_slot + k,
+                        st);
     }
     if (nsteps > 0) prev_closed = false;
   }
 };
 
 namespace {
-// Blocks of 1024 threads per run: about `trips` 4-marker trips each (at most
-// 16, the bound the runs' integer tiles are sized for).
+// Blocks per run: about `trips` 4-marker trips each (at most 16, the bound the
+// runs' integer tiles are sized for).
 constexpr int kBatchTrips = 8;
+// A batch whose runs all have at most this many markers runs 256-thread blocks.
+constexpr int64_t kBatchSmallRun = 1 << 15;
+
+// trips of a run of ngroups 4-marker groups over nb blocks of `threads`
+int64_t batch_trips(int64_t ngroups, int nb, int threads) {
+  return (ngroups + (int64_t)nb * threads - 1) / ((int64_t)nb * threads);
+}
 
 // Work list of a batch for a trip target; returns the blocks per run.
-std::vector<int> batch_items(const std::vector<pic_handle *> &runs, int trips,
+std::vector<int> batch_items(const std::vector<pic_handle *> &runs, int trips, int threads,
                              std::vector<BatchItem> &items) {
   std::vector<int> nbs;
   items.clear();
   for (int r = 0; r < (int)runs.size(); r++) {
     const pic_handle *h = runs[r];
     const int64_t ngroups = (h->N + 3) / 4;
-    int nb = (int)std::max<int64_t>(1, (ngroups + 1024 * trips - 1) / (1024 * trips));
+    int nb = (int)std::max<int64_t>(1, (ngroups + (int64_t)threads * trips - 1) /
+                                           ((int64_t)threads * trips));
     nb = std::min(nb, h->ls.grid);  // the run's per-block partials hold ls.grid entries
-    while ((ngroups + (int64_t)nb * 1024 - 1) / ((int64_t)nb * 1024) > 16 && nb < h->ls.grid) nb++;
+    while (batch_trips(ngroups, nb, threads) > 16 && nb < h->ls.grid) nb++;
     nbs.push_back(nb);
     for (int k = 0; k < nb; k++) items.push_back(BatchItem{r, k, nb});
   }
@@ -2333,6 +2343,9 @@ int pic_batch_init(const pic_config *cfgs, const pic_species *species, int nruns
   }
   pic_batch *b = new pic_batch();
   b->scheme = cfgs[0].scheme;
+  b->threads = 256;
+  for (int r = 0; r < nruns; r++)
+    if (species[r].n > kBatchSmallRun) b->threads = 1024;
   std::vector<Es1dMixConst> hc(nruns);
   std::vector<Es1dMixBufs> hb(nruns);
   std::vector<BatchItem> items;
@@ -2353,13 +2366,13 @@ int pic_batch_init(const pic_config *cfgs, const pic_species *species, int nruns
     b->st = h->st;
     hc[r] = h->cm;
     hb[r] = h->bm;
-    b->smem = std::max(b->smem, es1d_mix_smem_max(h->cm));
+    b->smem = std::max(b->smem, es1d_batch_smem(h->cm, b->threads));
   }
   b->trips = kBatchTrips;
-  nbs = batch_items(b->runs, b->trips, items);
+  nbs = batch_items(b->runs, b->trips, b->threads, items);
   for (int r = 0; r < nruns; r++) {
     const int64_t ngroups = (b->runs[r]->N + 3) / 4;
-    if ((ngroups + (int64_t)nbs[r] * 1024 - 1) / ((int64_t)nbs[r] * 1024) > 16) {
+    if (batch_trips(ngroups, nbs[r], b->threads) > 16) {
       delete b;
       return fail(PIC_ERR_UNSUPPORTED, "pic_batch_init: run %d is too large for a batch", r);
     }
@@ -2389,7 +2402,7 @@ int pic_batch_init(const pic_config *cfgs, const pic_species *species, int nruns
   if (e == cudaSuccess) e = up(&b->d_nb, nbs);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_fb, sizeof(unsigned long long) * kStepsCap * nruns);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_te, sizeof(double) * kStepsCap * nruns);
-  if (e == cudaSuccess) e = es1d_batch_prepare(b->smem);
+  if (e == cudaSuccess) e = es1d_batch_prepare(b->smem, b->threads);
   for (int r = 0; r < nruns && e == cudaSuccess; r++)
     e = cudaMemsetAsync(hb[r].fallback, 0, sizeof(unsigned long long) * kStepsCap, b->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
@@ -2406,10 +2419,10 @@ int pic_batch_init(const pic_config *cfgs, const pic_species *species, int nruns
 // old list are dropped).
 static int batch_retarget(pic_batch *b, int trips) {
   std::vector<BatchItem> items;
-  std::vector<int> nbs = batch_items(b->runs, trips, items);
+  std::vector<int> nbs = batch_items(b->runs, trips, b->threads, items);
   for (int r = 0; r < (int)b->runs.size(); r++) {
     const int64_t ngroups = (b->runs[r]->N + 3) / 4;
-    if ((ngroups + (int64_t)nbs[r] * 1024 - 1) / ((int64_t)nbs[r] * 1024) > 16) return PIC_OK;
+    if (batch_trips(ngroups, nbs[r], b->threads) > 16) return PIC_OK;
   }
   CUDA_TRY(cudaStreamSynchronize(b->st));
   if (b->pending && !b->prev_closed) {

@@ -503,15 +503,18 @@ void es1d_mix_finalize(const Es1dMixConst &c, const Es1dMixBufs &b, int slot, in
                        cudaStream_t st);
 void es1d_mix_set_ek(const Es1dMixConst &c, const Es1dMixBufs &b, int parity, cudaStream_t st);
 // batched runs (unsorted, nc <= kWideMaxNodes, one scheme): device arrays of the
-// runs' constants and buffers and the work list of nitems blocks
-cudaError_t es1d_batch_prepare(size_t smem);
+// runs' constants and buffers and the work list of nitems blocks of `threads`
+// (1024, or 256 for batches of small runs)
+cudaError_t es1d_batch_prepare(size_t smem, int threads);
+// dynamic shared memory of a batch block of `threads` for a run
+size_t es1d_batch_smem(const Es1dMixConst &c, int threads);
 // prev_slot: stats slot of the previous step to reduce (TE), or -1
 void es1d_batch_pass_c(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,
-                       int nitems, int scheme, size_t smem, int64_t step_index, int prev_slot,
-                       cudaStream_t st);
+                       int nitems, int scheme, int threads, size_t smem, int64_t step_index,
+                       int prev_slot, cudaStream_t st);
 void es1d_batch_pass_e(const Es1dMixConst *cs, const Es1dMixBufs *bs, const BatchItem *items,
-                       int nitems, int scheme, size_t smem, int64_t step_index, int slot,
-                       cudaStream_t st);
+                       int nitems, int scheme, int threads, size_t smem, int64_t step_index,
+                       int slot, cudaStream_t st);
 void es1d_batch_finalize(const Es1dMixConst *cs, const Es1dMixBufs *bs, const int *nblocks,
                          int nruns, int slot, cudaStream_t st);
 void es1d_batch_gather_stats(const Es1dMixBufs *bs, int nruns, int n, unsigned long long *fb,
