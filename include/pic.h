@@ -65,8 +65,10 @@ enum {
   PIC_ERR_CUDA = -2,       /* a CUDA runtime call failed                    */
   PIC_ERR_OOM = -3,        /* device allocation failed                      */
   PIC_ERR_NONFINITE = -4,  /* a non-finite value reached the state          */
-  PIC_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up            */
-  PIC_ERR_BOUNDS = -6,     /* an input position lies outside [0, L)         */
+  PIC_ERR_TIMEOUT = -5,    /* reserved: no kernel waits on another, so this */
+                           /* version never returns it                      */
+  PIC_ERR_BOUNDS = -6,     /* an input position lies outside [0, L); in the */
+                           /* debug-bounds build also a failed index check  */
   PIC_ERR_UNSUPPORTED = -7 /* a valid combination this build does not run   */
 };
 
@@ -369,8 +371,26 @@ void pic_free(pic_handle *h);
 /* Message for the last nonzero status returned on this thread. */
 const char *pic_last_error(void);
 
-/* Library version string. */
+/* Library version string ("..., debug-bounds)" for the debug-bounds build). */
 const char *pic_version(void);
+
+/* The debug-bounds build.  A library compiled with PIC_DEBUG_BOUNDS checks the
+ * index arithmetic of the mixed forms where an index is formed (the first
+ * node of a marker's shape, the periodic node indices of the 2D shapes, sort
+ * keys and sort-on-write slots, the grid nodes a current tile is flushed to):
+ * an index outside its range is replaced by 0, so that the access stays in
+ * bounds, and recorded; the next call that checks the state's flags
+ * (pic_read_stats, pic_step, pic_set_*, pic_batch_read_stats) then returns
+ * PIC_ERR_BOUNDS with the check's file and line in pic_last_error().  The
+ * records are per process, not per handle.  Results of a run with no failed
+ * check are those of the normal build.
+ *
+ * pic_debug_bounds runs one such check on the device for (index, extent):
+ * *flagged = 1 when index lies outside [0, extent) and the check recorded it,
+ * 0 when it passed (the record is cleared either way); PIC_ERR_CUDA if the
+ * check did not behave so.  In the normal build it returns
+ * PIC_ERR_UNSUPPORTED and sets *flagged = -1. */
+int pic_debug_bounds(int64_t index, int64_t extent, int *flagged);
 
 /* ---------------------------------------------------------------- batches
  * Many independent 1D runs stepped together (a parameter scan or an ensemble

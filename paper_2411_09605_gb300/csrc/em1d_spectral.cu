@@ -927,6 +927,8 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 
 }  // namespace
 
+PIC_BOUNDS_READER(bounds_site_em1d_spectral)
+
 int em1d_tile_copies(int n) {
   int rt = 32;
   while (rt > 1 && sizeof(double) * (6 + 2 * (size_t)rt) * n > kEm1TileBudget) rt >>= 1;

@@ -72,7 +72,7 @@ struct AxisMix {
       const int i = i0 + a;
       const bool low = a == 0 && (half || ORDER == 2);
       const bool high = a >= ((half && ORDER == 2) ? 2 : 1);
-      k[a] = low ? (i < 0 ? i + n : i) : (high ? (i >= n ? i - n : i) : i);
+      k[a] = PIC_INDEX(low ? (i < 0 ? i + n : i) : (high ? (i >= n ? i - n : i) : i), n);
     }
     const uint32_t f23 = (uint32_t)P >> 9;
     const float f = __fsub_rn(__uint_as_float(0x3F800000u | f23), 1.0f);  // exact
@@ -224,7 +224,7 @@ struct WarpSegments {
 __device__ __forceinline__ int quarter_key(uint32_t X, uint32_t Y, int nx, int ny) {
   const int qx = (int)(((uint64_t)X * (uint32_t)(2 * nx)) >> 32);
   const int qy = (int)(((uint64_t)Y * (uint32_t)(2 * ny)) >> 32);
-  return qx + 2 * nx * qy;
+  return PIC_INDEX(qx + 2 * nx * qy, 4 * nx * ny);
 }
 
 // The deposits of a thread's consecutive markers (sorted by quarter cell),
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(256, SORTED ? 2 : 0)
             store_marker(b, p, Xn, Yn, vn);
         }
         if (so.off) {
-          const unsigned q = warp_slot(so.off, key);
+          const unsigned q = PIC_INDEX(warp_slot(so.off, key), c.n);
           if (valid) {
             store_marker(so.dst, q, Xn, Yn, vn);
             if (so.ids_in) so.ids_out[q] = so.ids_in[p];
@@ -834,6 +834,8 @@ __global__ void __launch_bounds__(kScanThreads) mix2_sort_offsets_kernel(unsigne
 }
 
 }  // namespace
+
+PIC_BOUNDS_READER(bounds_site_em2d_mixed)
 
 LaunchShape em2dm_pass_shape(int64_t n, bool sorted, LaunchShape lp) {
   if (!sorted) return lp;

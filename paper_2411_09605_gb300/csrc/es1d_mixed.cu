@@ -160,7 +160,7 @@ __device__ void block_exclusive_scan(const uint32_t *T, uint32_t *base, int nc, 
 // Sort key of a marker after the step: its cell and the sign of its velocity
 // (counter-streaming markers of one cell then sit in separate runs).
 __device__ __forceinline__ int sort_key(uint32_t X, int V, int nc) {
-  return 2 * cell_of(X, nc) + (V > 0 ? 1 : 0);
+  return PIC_INDEX(2 * cell_of(X, nc) + (V > 0 ? 1 : 0), 2 * nc);
 }
 
 // Warp-aggregated increment of a shared counter array: returns this lane's
@@ -315,7 +315,8 @@ __device__ __forceinline__ void flush_tile(const unsigned *Jt, long long *J, lon
     const long long a = hi * (1ll << b) + lo;
     mine += a;
     if (a != 0)
-      atomicAdd((unsigned long long *)&J[wrap_node(q - Pad<ORDER>::kPad, nc) * kJStride],
+      atomicAdd((unsigned long long *)&J[PIC_INDEX(wrap_node(q - Pad<ORDER>::kPad, nc), nc) *
+                                         kJStride],
                 (unsigned long long)a);
   }
   for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
@@ -505,7 +506,8 @@ __device__ __forceinline__ void flush_tile_i64(const long long *Jt, long long *J
     const long long a = Jt[q];
     mine += a;
     if (a != 0)
-      atomicAdd((unsigned long long *)&J[wrap_node(q - Pad<ORDER>::kPad, nc) * stride],
+      atomicAdd((unsigned long long *)&J[PIC_INDEX(wrap_node(q - Pad<ORDER>::kPad, nc), nc) *
+                                         stride],
                 (unsigned long long)a);
   }
   if (total) {
@@ -870,7 +872,7 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
         }
         if (MODE == 2) {
           // sort on write: the marker's slot in key order, from pass C's counts
-          const uint32_t dst = warp_rank(off, sort_key(Xn, Vs, c.nc), valid);
+          const uint32_t dst = PIC_INDEX(warp_rank(off, sort_key(Xn, Vs, c.nc), valid), c.n);
           if (valid) {
             b.Xo[dst] = Xn;
             b.vho[dst] = vn.hi;
@@ -1375,7 +1377,7 @@ __global__ void __launch_bounds__(512) sort_move_kernel(Es1dMixBufs src, Es1dMix
     bool valid = p < end;
     uint32_t X = valid ? src.X[p] : 0u;
     int key = valid ? cell_of(X, nc) : -1;
-    const uint32_t dest = warp_rank(off, key, valid);
+    const uint32_t dest = PIC_INDEX(warp_rank(off, key, valid), n);
     if (valid) {
       dst.X[dest] = X;
       dst.vh[dest] = src.vh[p];
@@ -1454,6 +1456,8 @@ void dispatch_fused(const Es1dMixConst &c, F f) {
 }
 
 }  // namespace
+
+PIC_BOUNDS_READER(bounds_site_es1d_mixed)
 
 cudaError_t es1d_mix_prepare(const Es1dMixConst &c) {
   cudaError_t e = cudaSuccess;

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include "debug_bounds.cuh"
 #include "ff.cuh"
 #include "pic_internal.cuh"
 
@@ -25,7 +26,8 @@ __device__ __forceinline__ int wrap_node(int i, int nc) {
   return i < 0 ? i + nc : (i >= nc ? i - nc : i);
 }
 
-// Shape of a marker at X: first padded node p and the weights.  The weights
+// Shape of a marker at X: first padded node p (in [0, nc + ORDER - 1) for
+// any 32-bit X) and the weights.  The weights
 // are quantised B-spline values, multiples of 2^-23, available both as floats
 // (w, for the gathers) and as integers (s = w 2^23, for the deposits); gather
 // and deposit at the same X therefore use exactly the same numbers and sum to
@@ -40,7 +42,7 @@ struct ShapeMix {
   __device__ __forceinline__ ShapeMix(uint32_t X, int nc) {
     // xi (+ 1/2 for order 2) in 32.32 fixed point
     const uint64_t P = (uint64_t)X * (uint32_t)nc + (ORDER == 2 ? 0x80000000ull : 0ull);
-    p = (int)(P >> 32);
+    p = PIC_INDEX((int)(P >> 32), nc + ORDER - 1);
     const uint32_t f23 = (uint32_t)P >> 9;
     const float f = __fsub_rn(__uint_as_float(0x3F800000u | f23), 1.0f);  // exact
     if (ORDER == 1) {
@@ -71,8 +73,8 @@ __device__ __forceinline__ void shape_mix_pair(uint32_t X0, uint32_t X1, int nc,
                                                ShapeMix<ORDER> &S0, ShapeMix<ORDER> &S1) {
   const uint64_t P0 = (uint64_t)X0 * (uint32_t)nc + (ORDER == 2 ? 0x80000000ull : 0ull);
   const uint64_t P1 = (uint64_t)X1 * (uint32_t)nc + (ORDER == 2 ? 0x80000000ull : 0ull);
-  S0.p = (int)(P0 >> 32);
-  S1.p = (int)(P1 >> 32);
+  S0.p = PIC_INDEX((int)(P0 >> 32), nc + ORDER - 1);
+  S1.p = PIC_INDEX((int)(P1 >> 32), nc + ORDER - 1);
   const uint32_t g0 = (uint32_t)P0 >> 9, g1 = (uint32_t)P1 >> 9;
   const float2 one = splat2(1.0f);
   const float2 f = sub2(make_float2(__uint_as_float(0x3F800000u | g0),

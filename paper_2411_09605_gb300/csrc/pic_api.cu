@@ -12,9 +12,16 @@
 #include <string>
 #include <vector>
 
+#include "debug_bounds.cuh"
 #include "pic_internal.cuh"
 
 using namespace pic;
+
+#ifdef PIC_DEBUG_BOUNDS
+namespace pic {
+PIC_BOUNDS_READER(bounds_site_pic_api)
+}  // namespace pic
+#endif
 
 namespace {
 
@@ -320,13 +327,28 @@ int check_flags(pic_handle *h, const char *where) {
   unsigned flags = 0;
   CUDA_TRY(cudaMemcpyAsync(&flags, h->b1.err, sizeof flags, cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(cudaStreamSynchronize(h->st));
+#ifdef PIC_DEBUG_BOUNDS
+  // a failed index check comes first: the flags after it may be its effects
+  // (the records are per process, not per handle)
+  const struct {
+    unsigned (*read)();
+    const char *unit;
+  } units[] = {{bounds_site_es1d_mixed, "es1d_mixed.cu"},
+               {bounds_site_em2d_mixed, "em2d_mixed.cu"},
+               {bounds_site_em1d_spectral, "em1d_spectral.cu"}};
+  for (const auto &u : units)
+    if (const unsigned site = u.read()) {
+      if (flags) CUDA_TRY(cudaMemsetAsync(h->b1.err, 0, sizeof(unsigned), h->st));
+      return fail(PIC_ERR_BOUNDS, "%s: index check failed at %s:%u (a kernel of %s)", where,
+                  bounds_file_name(site), site & 0xFFFFu, u.unit);
+    }
+#endif
   if (flags) {
     CUDA_TRY(cudaMemsetAsync(h->b1.err, 0, sizeof(unsigned), h->st));
     if (flags & kErrNonfinite) return fail(PIC_ERR_NONFINITE, "%s: non-finite value in the state", where);
     if (flags & kErrBounds)
       return fail(PIC_ERR_BOUNDS, "%s: a position left [0, L) (input out of range, or a "
                                   "particle crossed more than one period in a step)", where);
-    if (flags & kErrTimeout) return fail(PIC_ERR_TIMEOUT, "%s: device wait timed out", where);
     if (flags & kErrVelocityRange)
       return fail(PIC_ERR_BOUNDS, "%s: a velocity left the mixed form's fixed-point range "
                                   "(8 times the largest initial speed)", where);
@@ -1279,13 +1301,52 @@ int init_em1d(pic_handle *h, const pic_species *species, const double *E0, const
   return restart_em1d(h);
 }
 
+#ifdef PIC_DEBUG_BOUNDS
+// one index check of the debug-bounds build, run on the device
+__global__ void bounds_probe_kernel(long long i, long long n, long long *out) {
+  *out = PIC_INDEX(i, n);
+}
+#endif
+
 }  // namespace
 
 extern "C" {
 
 const char *pic_last_error(void) { return g_last_error.c_str(); }
 
+#ifdef PIC_DEBUG_BOUNDS
+const char *pic_version(void) { return "gb300-ecpic 0.1 (sm_103a, debug-bounds)"; }
+#else
 const char *pic_version(void) { return "gb300-ecpic 0.1 (sm_103a)"; }
+#endif
+
+int pic_debug_bounds(int64_t index, int64_t extent, int *flagged) {
+  if (!flagged) return fail(PIC_ERR_ARG, "pic_debug_bounds: flagged is NULL");
+  *flagged = -1;
+#ifdef PIC_DEBUG_BOUNDS
+  long long *d = nullptr, got = -1;
+  cudaError_t e = cudaMalloc(&d, sizeof *d);
+  if (e == cudaSuccess) {
+    bounds_probe_kernel<<<1, 1>>>((long long)index, (long long)extent, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&got, d, sizeof got, cudaMemcpyDeviceToHost);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) return fail(PIC_ERR_CUDA, "pic_debug_bounds: %s", cudaGetErrorString(e));
+  const unsigned site = bounds_site_pic_api();
+  const bool in_range = index >= 0 && index < extent;
+  // the check yields the index when it passes, 0 when it records a failure
+  if ((site != 0) == in_range || got != (in_range ? (long long)index : 0ll))
+    return fail(PIC_ERR_CUDA, "pic_debug_bounds: check of %lld in [0, %lld) gave %lld, record 0x%x",
+                (long long)index, (long long)extent, got, site);
+  *flagged = site != 0;
+  return PIC_OK;
+#else
+  (void)index;
+  (void)extent;
+  return fail(PIC_ERR_UNSUPPORTED, "pic_debug_bounds: library built without PIC_DEBUG_BOUNDS");
+#endif
+}
 
 int pic_init(const pic_config *cfg, const pic_species *species, int nspecies, const double *E0,
              const double *B0, pic_handle **out) {

@@ -17,7 +17,19 @@ constexpr int kMaxSpecies = 8;
 constexpr int kMaxNodes1D = 8192;   // 1D grid held whole in shared memory
 
 // Device-side error flags (bit set by kernels, read by the host after a call).
-enum : unsigned { kErrNonfinite = 1u, kErrBounds = 2u, kErrVelocityRange = 4u, kErrTimeout = 8u };
+// No kernel of the library waits on another block or launch (every ordering
+// is a stream's or a kernel boundary's), so none has a wait that could time
+// out: PIC_ERR_TIMEOUT has no flag.
+enum : unsigned { kErrNonfinite = 1u, kErrBounds = 2u, kErrVelocityRange = 4u };
+
+#ifdef PIC_DEBUG_BOUNDS
+// Records of the index checks of the debug-bounds build, one per translation
+// unit with checks: file code << 16 | line of the first failed check, 0 if
+// none; each call clears its record.
+unsigned bounds_site_es1d_mixed();
+unsigned bounds_site_em2d_mixed();
+unsigned bounds_site_em1d_spectral();
+#endif
 
 struct SpeciesInfo {
   double q, m, w0;

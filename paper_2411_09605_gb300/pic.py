@@ -3,7 +3,9 @@
 Every function here forwards to the function of the same name in libpic.so;
 all arithmetic of the method runs in the library's CUDA kernels.  The library
 must have been built (``paper_2411_09605_gb300.build.build()``); importing this
-module without it raises, there is no fallback.
+module without it raises, there is no fallback.  With PIC_DEBUG_BOUNDS=1 in the
+environment the debug-bounds build libpic_debug.so is loaded instead
+(``build(debug_bounds=True)``).
 
 Arrays may be numpy float64 arrays (host) or, with ``ptr_on_device=1`` in the
 config, torch CUDA tensors (their ``data_ptr()`` is passed through).
@@ -18,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpic.so")
+DEBUG_LIB_PATH = os.path.join(_HERE, "libpic_debug.so")
 
 PIC_OK = 0
 ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_OOM", -4: "PIC_ERR_NONFINITE",
@@ -35,7 +38,8 @@ EXPORTS = ["pic_init", "pic_step", "pic_step_async", "pic_read_stats", "pic_laun
            "pic_last_error", "pic_version", "pic_es1d_step_noalloc",
            "pic_batch_init", "pic_batch_step", "pic_batch_set_graph", "pic_batch_read_stats",
            "pic_batch_run", "pic_batch_info", "pic_batch_free", "pic_batch_autotune",
-           "pic_grad_forward", "pic_grad_backward", "pic_mixed_resolution", "pic_charge"]
+           "pic_grad_forward", "pic_grad_backward", "pic_mixed_resolution", "pic_charge",
+           "pic_debug_bounds"]
 
 
 class PicError(RuntimeError):
@@ -71,10 +75,13 @@ def lib() -> C.CDLL:
     """Loads libpic.so (raises if it has not been built)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise ImportError(f"{LIB_PATH} is missing: build it with "
-                              "paper_2411_09605_gb300.build.build() (needs nvcc)")
-        L = C.CDLL(LIB_PATH)
+        debug = os.environ.get("PIC_DEBUG_BOUNDS") == "1"
+        path = DEBUG_LIB_PATH if debug else LIB_PATH
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with "
+                              "paper_2411_09605_gb300.build.build("
+                              f"{'debug_bounds=True' if debug else ''}) (needs nvcc)")
+        L = C.CDLL(path)
         vp, i64p, dp = C.c_void_p, C.POINTER(C.c_int64), C.c_void_p
         L.pic_init.argtypes = [C.POINTER(pic_config), C.POINTER(pic_species), C.c_int, dp, dp,
                                C.POINTER(vp)]
@@ -99,6 +106,7 @@ def lib() -> C.CDLL:
                                              C.c_double, C.c_int64, vp, vp, vp, C.c_int, vp, vp]
         L.pic_grad_forward.argtypes = [vp, C.c_int, C.c_int]
         L.pic_grad_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.pic_debug_bounds.argtypes = [C.c_int64, C.c_int64, C.POINTER(C.c_int)]
         L.pic_free.argtypes = [vp]
         L.pic_free.restype = None
         L.pic_batch_init.argtypes = [C.POINTER(pic_config), C.POINTER(pic_species), C.c_int,
@@ -264,6 +272,14 @@ def pic_es1d_step_noalloc(cfg: pic_config, q: float, m: float, w0: float, n: int
 
 def pic_version() -> str:
     return lib().pic_version().decode()
+
+
+def pic_debug_bounds(index: int, extent: int) -> int:
+    """One device-side index check of the debug-bounds build: 1 if it flagged
+    index outside [0, extent), 0 if it passed."""
+    flagged = C.c_int()
+    _check(lib().pic_debug_bounds(index, extent, C.byref(flagged)))
+    return flagged.value
 
 
 class Simulation:

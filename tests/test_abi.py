@@ -36,6 +36,20 @@ def test_version_string(lib):
     assert "sm_103a" in pic.pic_version()
 
 
+def test_debug_bounds_probe_unsupported_in_normal_build(lib):
+    """The index checks exist only in the PIC_DEBUG_BOUNDS build; the normal
+    library says so without touching the device."""
+    import ctypes as C
+    if os.environ.get("PIC_DEBUG_BOUNDS") == "1":
+        pytest.skip("the debug-bounds library is loaded")
+    flagged = C.c_int(7)
+    assert lib.pic_debug_bounds(3, 10, C.byref(flagged)) == -7
+    assert flagged.value == -1
+    assert b"PIC_DEBUG_BOUNDS" in lib.pic_last_error()
+    assert lib.pic_debug_bounds(3, 10, None) == -1
+    assert "debug-bounds" not in lib.pic_version().decode()
+
+
 def test_argument_errors_are_status_codes(lib):
     from paper_2411_09605_gb300 import pic
     x = np.array([0.5])
