@@ -211,6 +211,62 @@ __device__ __forceinline__ ff mean_of_total(long long total, const Es1dMixConst 
   return ff_mul(ff_from_i64(total), c.inv_nc);
 }
 
+// Stores one table value into RE consecutive copies (RE = 16: 16-byte stores).
+template <int RE, typename T>
+__device__ __forceinline__ void store_copies(T *row, T v) {
+  if (RE == 1) {
+    row[0] = v;
+  } else {
+    static_assert(16 % sizeof(T) == 0, "copies are written 16 bytes at a time");
+    constexpr int kPer = 16 / sizeof(T);
+    union {
+      T t[kPer];
+      uint4 u;
+    } pk;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) pk.t[k] = v;
+    uint4 *r4 = reinterpret_cast<uint4 *>(row);
+#pragma unroll
+    for (int k = 0; k < RE / kPer; k++) r4[k] = pk.u;
+  }
+}
+
+// The RE copies of the 32 nodes q of a warp's lanes (lane l holds the value v
+// of node q = q0 + l; called by all 32 lanes, node q written when q < npad),
+// the warp together: its CPN = 16 RE / sizeof(T) stores of 16 bytes per lane
+// cover consecutive 512-byte spans of the table, so no two lanes of a quarter
+// warp address the same banks.  (Each lane writing its own node's copies puts
+// the lanes 16 RE bytes apart, all on the same four banks.)
+template <int RE, typename T>
+__device__ __forceinline__ void store_copies_warp(T *table, int q, T v, int npad) {
+  constexpr int kPer = 16 / sizeof(T);
+  if constexpr (RE < kPer || RE % kPer != 0) {
+    if (q < npad) store_copies<RE>(table + q * RE, v);
+  } else {
+    constexpr int CPN = RE / kPer;  // 16-byte chunks per node
+    const int lane = (int)(threadIdx.x & 31u), q0 = q - lane;
+    uint4 *base = reinterpret_cast<uint4 *>(table + q0 * RE);
+#pragma unroll
+    for (int s = 0; s < CPN; s++) {
+      const int src = (32 * s + lane) / CPN;  // the lane whose node this chunk is
+      union {
+        T t[kPer];
+        uint4 u;
+      } pk;
+      T w;
+      static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte table entries");
+      if constexpr (sizeof(T) == 4) {
+        w = __int_as_float(__shfl_sync(0xffffffffu, __float_as_int(v), src));
+      } else {
+        w = make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+      }
+#pragma unroll
+      for (int k = 0; k < kPer; k++) pk.t[k] = w;
+      if (q0 + src < npad) base[32 * s + lane] = pk.u;
+    }
+  }
+}
+
 // The binomial filter F (the periodic 1-2-1 stencil, p passes) inside the
 // scheme, put in energy-consistently: both Ampere updates use F j and both
 // gathers read F E* and F E^{n+1/2}; F is symmetric and keeps the mean, so
@@ -230,20 +286,23 @@ __device__ __noinline__ void estar_table_filtered(int nc, int p, float c_jstar, 
                                                   const float2 *Ek, const long long *J1,
                                                   float mean, float *Es, int npad) {
   const float2 *f2 = filt + 2 * p + 1;
-  for (int q = threadIdx.x; q < npad; q += blockDim.x) {
-    const int i = wrap_node(q - PAD, nc);
+  // whole warps in every trip (the copies are written by the warp together)
+  for (int q = threadIdx.x; q - (int)(threadIdx.x & 31u) < npad; q += blockDim.x) {
     float e = 0.0f;
-    for (int k = -p; k <= p; k++) {
-      const float2 ek = Ek[node_at(i, k, nc)];
-      e = __fmaf_rn(filt[k + p].x, __fmul_rn(0.5f, __fadd_rn(ek.x, ek.y)), e);
+    if (q < npad) {
+      const int i = wrap_node(q - PAD, nc);
+      for (int k = -p; k <= p; k++) {
+        const float2 ek = Ek[node_at(i, k, nc)];
+        e = __fmaf_rn(filt[k + p].x, __fmul_rn(0.5f, __fadd_rn(ek.x, ek.y)), e);
+      }
+      if (SCHEME == 2) {
+        float j = 0.0f;
+        for (int k = -2 * p; k <= 2 * p; k++)
+          j = __fmaf_rn(f2[k + 2 * p].x, __ll2float_rn(J1[node_at(i, k, nc) * kJStride]), j);
+        e = __fmaf_rn(-c_jstar, __fsub_rn(j, mean), e);
+      }
     }
-    if (SCHEME == 2) {
-      float j = 0.0f;
-      for (int k = -2 * p; k <= 2 * p; k++)
-        j = __fmaf_rn(f2[k + 2 * p].x, __ll2float_rn(J1[node_at(i, k, nc) * kJStride]), j);
-      e = __fmaf_rn(-c_jstar, __fsub_rn(j, mean), e);
-    }
-    for (int k = 0; k < RE; k++) Es[q * RE + k] = e;
+    store_copies_warp<RE>(Es, q, e, npad);
   }
 }
 
@@ -254,19 +313,24 @@ __device__ __noinline__ void ehalf_table_filtered(int nc, int p, ff kick_jhalf, 
                                                   const float2 *Ek, const long long *J2, ff mean,
                                                   float2 *Eh2, int npad) {
   const float2 *f2 = filt + 2 * p + 1;
-  for (int q = threadIdx.x; q < npad; q += blockDim.x) {
-    const int i = wrap_node(q - PAD, nc);
-    ff e{0.0f, 0.0f}, j{0.0f, 0.0f};
-    for (int k = -p; k <= p; k++) {
-      const float2 ek = Ek[node_at(i, k, nc)], f = filt[k + p];
-      e = ff_add(e, ff_mul(ff{f.x, f.y}, ff{ek.x, ek.y}));
+  // whole warps in every trip (the copies are written by the warp together)
+  for (int q = threadIdx.x; q - (int)(threadIdx.x & 31u) < npad; q += blockDim.x) {
+    float2 v = make_float2(0.0f, 0.0f);
+    if (q < npad) {
+      const int i = wrap_node(q - PAD, nc);
+      ff e{0.0f, 0.0f}, j{0.0f, 0.0f};
+      for (int k = -p; k <= p; k++) {
+        const float2 ek = Ek[node_at(i, k, nc)], f = filt[k + p];
+        e = ff_add(e, ff_mul(ff{f.x, f.y}, ff{ek.x, ek.y}));
+      }
+      for (int k = -2 * p; k <= 2 * p; k++) {
+        const float2 f = f2[k + 2 * p];
+        j = ff_add(j, ff_mul(ff{f.x, f.y}, ff_from_i64(J2[node_at(i, k, nc) * kJStride])));
+      }
+      const ff eh = ff_sub(e, ff_mul(kick_jhalf, ff_sub(j, mean)));
+      v = make_float2(eh.hi, eh.lo);
     }
-    for (int k = -2 * p; k <= 2 * p; k++) {
-      const float2 f = f2[k + 2 * p];
-      j = ff_add(j, ff_mul(ff{f.x, f.y}, ff_from_i64(J2[node_at(i, k, nc) * kJStride])));
-    }
-    const ff eh = ff_sub(e, ff_mul(kick_jhalf, ff_sub(j, mean)));
-    for (int k = 0; k < RE; k++) Eh2[q * RE + k] = make_float2(eh.hi, eh.lo);
+    store_copies_warp<RE>(Eh2, q, v, npad);
   }
 }
 
@@ -359,25 +423,6 @@ __device__ __forceinline__ void report_flags(unsigned bad, unsigned *err) {
   if ((threadIdx.x & 31u) == 0u && bad) atomicOr(err, bad);
 }
 
-// Stores one table value into RE consecutive copies (RE = 16: 16-byte stores).
-template <int RE, typename T>
-__device__ __forceinline__ void store_copies(T *row, T v) {
-  if (RE == 1) {
-    row[0] = v;
-  } else {
-    static_assert(16 % sizeof(T) == 0, "copies are written 16 bytes at a time");
-    constexpr int kPer = 16 / sizeof(T);
-    union {
-      T t[kPer];
-      uint4 u;
-    } pk;
-#pragma unroll
-    for (int k = 0; k < kPer; k++) pk.t[k] = v;
-    uint4 *r4 = reinterpret_cast<uint4 *>(row);
-#pragma unroll
-    for (int k = 0; k < RE / kPer; k++) r4[k] = pk.u;
-  }
-}
 
 
 // The correction of Eq. opt_solution in FP64 from the float-pair state
@@ -642,16 +687,20 @@ __device__ __forceinline__ void pass_c_body(const Es1dMixConst &c, const Es1dMix
       estar_table_filtered<SCHEME, RE, PAD>(c.nc, c.passes, c.c_jstar, b.filt, Ek, J1, mean, Es,
                                             npad);
     } else {
-      for (int q = threadIdx.x; q < npad; q += blockDim.x) {
-        const int i = wrap_node(q - PAD, c.nc);
-        const bool first = q == (int)threadIdx.x;
-        const float2 ek = first ? E0 : Ek[i];
-        float e = __fmul_rn(0.5f, __fadd_rn(ek.x, ek.y));
-        if (SCHEME == 2) {
-          const float dj = __fsub_rn(__ll2float_rn(first ? J0 : J1[i * kJStride]), mean);
-          e = __fmaf_rn(-c.c_jstar, dj, e);
+      // whole warps in every trip (the copies are written by the warp together)
+      for (int q = threadIdx.x; q - (int)(threadIdx.x & 31u) < npad; q += blockDim.x) {
+        float e = 0.0f;
+        if (q < npad) {
+          const int i = wrap_node(q - PAD, c.nc);
+          const bool first = q == (int)threadIdx.x;
+          const float2 ek = first ? E0 : Ek[i];
+          e = __fmul_rn(0.5f, __fadd_rn(ek.x, ek.y));
+          if (SCHEME == 2) {
+            const float dj = __fsub_rn(__ll2float_rn(first ? J0 : J1[i * kJStride]), mean);
+            e = __fmaf_rn(-c.c_jstar, dj, e);
+          }
         }
-        store_copies<RE>(Es + q * RE, e);
+        store_copies_warp<RE>(Es, q, e, npad);
       }
     }
   }
@@ -766,13 +815,18 @@ __device__ __forceinline__ void pass_e_body(const Es1dMixConst &c, const Es1dMix
       ehalf_table_filtered<RE, PAD>(c.nc, c.passes, c.kick_jhalf, b.filt, Ek, J2, mean2.j, Eh2,
                                     npad);
     } else {
-      for (int q = threadIdx.x; q < npad; q += blockDim.x) {
-        const int i = wrap_node(q - PAD, c.nc);
-        const bool first = q == (int)threadIdx.x;
-        const float2 ek = first ? E0 : Ek[i];
-        const ff dj = ff_sub(ff_from_i64(first ? J0 : J2[i * kJStride]), mean2.j);
-        const ff eh = ff_sub(ff{ek.x, ek.y}, ff_mul(c.kick_jhalf, dj));
-        store_copies<RE>(Eh2 + q * RE, make_float2(eh.hi, eh.lo));
+      // whole warps in every trip (the copies are written by the warp together)
+      for (int q = threadIdx.x; q - (int)(threadIdx.x & 31u) < npad; q += blockDim.x) {
+        float2 v = make_float2(0.0f, 0.0f);
+        if (q < npad) {
+          const int i = wrap_node(q - PAD, c.nc);
+          const bool first = q == (int)threadIdx.x;
+          const float2 ek = first ? E0 : Ek[i];
+          const ff dj = ff_sub(ff_from_i64(first ? J0 : J2[i * kJStride]), mean2.j);
+          const ff eh = ff_sub(ff{ek.x, ek.y}, ff_mul(c.kick_jhalf, dj));
+          v = make_float2(eh.hi, eh.lo);
+        }
+        store_copies_warp<RE>(Eh2, q, v, npad);
       }
     }
   }
@@ -955,16 +1009,23 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
     const float2 *Ek = PSEL(b.Ek, par);
     const double *E = PSEL(b.E, par);
     const ff meanj = c.remove_mean ? mean_of_total(*io.Tr, c) : ff{0.0f, 0.0f};
-    for (int q = threadIdx.x; q < npad; q += blockDim.x) {
-      const int i = wrap_node(q - PAD, c.nc);
-      const float2 ek = Ek[i];
-      const long long j2 = io.Jr[i * kJStride];
-      const ff dj = ff_sub(ff_from_i64(j2), meanj);
-      const ff eh = ff_sub(ff{ek.x, ek.y}, ff_mul(c.kick_jhalf, dj));
-      store_copies<RE>(Eh2 + q * RE, make_float2(eh.hi, eh.lo));
-      const double en = E[i] - c.dt * ((double)j2 * c.jscale - mean_e);
-      const ff k = ff_from_double(c.kick * en);
-      store_copies<RE1>(Es + q * RE1, __fmul_rn(0.5f, __fadd_rn(k.hi, k.lo)));
+    // whole warps in every trip (the copies are written by the warp together)
+    for (int q = threadIdx.x; q - (int)(threadIdx.x & 31u) < npad; q += blockDim.x) {
+      float2 vh = make_float2(0.0f, 0.0f);
+      float vs = 0.0f;
+      if (q < npad) {
+        const int i = wrap_node(q - PAD, c.nc);
+        const float2 ek = Ek[i];
+        const long long j2 = io.Jr[i * kJStride];
+        const ff dj = ff_sub(ff_from_i64(j2), meanj);
+        const ff eh = ff_sub(ff{ek.x, ek.y}, ff_mul(c.kick_jhalf, dj));
+        vh = make_float2(eh.hi, eh.lo);
+        const double en = E[i] - c.dt * ((double)j2 * c.jscale - mean_e);
+        const ff k = ff_from_double(c.kick * en);
+        vs = __fmul_rn(0.5f, __fadd_rn(k.hi, k.lo));
+      }
+      store_copies_warp<RE>(Eh2, q, vh, npad);
+      store_copies_warp<RE1>(Es, q, vs, npad);
     }
   }
   __syncthreads();
