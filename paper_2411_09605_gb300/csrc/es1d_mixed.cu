@@ -992,7 +992,7 @@ __global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
 // through three buffers (RingIO): this launch reads j^{*,n+1/2}, deposits
 // j^{*,n+3/2} and clears the one the previous launch read.
 template <int ORDER, int RT, int RE, int RE1>
-__global__ void __launch_bounds__(RT > 1 ? 1024 : 512, RT > 1 ? 1 : 2)
+__global__ void __launch_bounds__(RT > 1 ? kFusedThreads : 512, RT > 1 ? 1 : 2)
     mix_pass_ec_kernel(Es1dMixConst c, Es1dMixBufs b, RingIO io, int par, int slot,
                        int prev_slot, int prev_nblocks) {
   constexpr int PAD = Pad<ORDER>::kPad;

@@ -125,6 +125,7 @@ struct pic_handle {
   bool mixed = false;
   Es1dMixConst cm{};
   LaunchShape lmix{1, 512};  // passes C and E of the mixed form
+  LaunchShape lmix_ec{1, 512};  // the fused ESEC1 pass (same grid)
   double *energy_part = nullptr;  // pic_energy's kinetic partials (ke_part may be in use)
   Es1dMixBufs bm{};
   Es1dMixBufs bm_alt{};     // the counting sort's destination (swapped after a sort)
@@ -429,12 +430,15 @@ void swap_sorted_output(pic_handle *h) {
 // Markers a tile copy of the mixed 1D passes takes in one launch on grids of up
 // to kWideMaxNodes nodes: those of one wave of the wide launch (one
 // 1024-thread block per SM, 32 copies a block, 4 markers per thread and
-// trip), at least 2048.  Every launch of such a handle keeps to it.
+// trip, or kFusedThreads-thread blocks for the fused ESEC1 pass on the same
+// grid, whichever is more), at least 2048.  Every launch of such a handle
+// keeps to it, whatever its scheme, so that all modes round alike.
 int64_t mixed_wide_pcnt(int64_t N, int nsm) {
   const int64_t ngroups = (N + 3) / 4;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((ngroups + 1023) / 1024, nsm));
   const int64_t trips = (ngroups + grid * 1024 - 1) / (grid * 1024);
-  return std::max<int64_t>(2048, trips * 128);
+  const int64_t trips_ec = (ngroups + grid * kFusedThreads - 1) / (grid * kFusedThreads);
+  return std::max<int64_t>(2048, std::max(trips * 128, trips_ec * (kFusedThreads / 8)));
 }
 
 // Mixed form: constants, integer/float-pair state converted from the FP64
@@ -483,9 +487,13 @@ int init_mixed(pic_handle *h, bool solve_e0) {
     // checked against the counters' bound below)
     const int64_t want = std::min<int64_t>((ngroups + 1023) / 1024, h->nsm);
     h->lmix = LaunchShape{(int)std::max<int64_t>(1, want), 1024};
+    h->lmix_ec = LaunchShape{h->lmix.grid, kFusedThreads};
   } else {
     h->lmix = h->ls;
+    h->lmix_ec = h->ls;
   }
+  // ESEC1 in one launch per step (the fused pass) on this handle
+  const bool fused = m.scheme == 1 && m.mode == 0 && !h->cfg.separate_passes && c.passes == 0;
   // Terms round(V* s / 2^r) are below 2^T = 2^(54 - r).  At most pcnt markers
   // add into one tile copy of a block in a launch.  Its split counters hold the
   // low b = 32 - lg bits of each term (lg = ceil(log2 pcnt): pcnt 2^b <= 2^32)
@@ -509,7 +517,9 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   }
   if (m.wide) {
     const int64_t wthreads = (int64_t)h->lmix.grid * 1024;
-    if (((ngroups + wthreads - 1) / wthreads) * 128 > pcnt)
+    const int64_t ethreads = (int64_t)h->lmix_ec.grid * kFusedThreads;
+    if (((ngroups + wthreads - 1) / wthreads) * 128 > pcnt ||
+        ((ngroups + ethreads - 1) / ethreads) * (kFusedThreads / 8) > pcnt)
       return fail(PIC_ERR_UNSUPPORTED, "pic_init: internal launch size of the wide passes");
   } else if (c.nc <= kWideMaxNodes && h->lmix.grid * pcnt < 4 * ngroups) {
     return fail(PIC_ERR_UNSUPPORTED, "pic_init: internal launch size for the sorted modes");
@@ -585,7 +595,7 @@ int init_mixed(pic_handle *h, bool solve_e0) {
   if ((rc = h->alloc(&h->jtot_base, 8))) return rc;
   CUDA_TRY(cudaMemsetAsync(h->jtot_base, 0, sizeof(long long) * 8, h->st));
   bm.Jtot = h->jtot_base + 4;
-  h->fused = m.scheme == 1 && m.mode == 0 && !h->cfg.separate_passes && m.passes == 0;
+  h->fused = fused;
   h->primed = false;
   if (h->fused && ((rc = h->alloc(&h->ke_alt, (size_t)h->ls.grid)) ||
                    (rc = h->alloc(&h->we_alt, (size_t)h->ls.grid))))
@@ -1620,7 +1630,7 @@ int pic_step_async(pic_handle *h, int nsteps) {
         const RingIO io{ring[r0], tot[r0], ring[r1], tot[r1], ring[r2], tot[r2],
                         bm.ke_part, bm.we_part, h->ke_alt, h->we_alt};
         CUDA_TRY(h->timed_launch(5, [&] {
-          es1d_mix_pass_ec(h->cm, bm, io, n, h->pending, h->lmix, h->st);
+          es1d_mix_pass_ec(h->cm, bm, io, n, h->pending, h->lmix_ec, h->st);
         }));
         std::swap(bm.ke_part, h->ke_alt);
         std::swap(bm.we_part, h->we_alt);

@@ -99,6 +99,10 @@ struct BatchItem {
 // current tile and 16 of the field tables per block (one 1024-thread block per
 // SM); larger grids one copy (512-thread blocks).
 constexpr int kWideMaxNodes = 512;
+// Block size of the fused ESEC1 pass in that layout: 768 threads, one block per
+// SM.  The fused pass keeps both tables and both shapes of a marker live; at
+// 1024 threads its 64 registers spill, at 768 it has 80 and none.
+constexpr int kFusedThreads = 768;
 // Mixed-form integer node sums J1, J2 hold node i at [i * kJStride]: one node
 // per 128-byte line, so the blocks' global atomics spread over the L2 slices.
 constexpr int kJStride = 16;
