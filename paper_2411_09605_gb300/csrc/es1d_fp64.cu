@@ -241,10 +241,13 @@ __global__ void __launch_bounds__(512) pass_e_kernel(Es1dConst c, Es1dFp64Bufs b
     double vd2 = vd * vd;
     double vn = vd;
     if (c.gamma_on) {
+      // v^{n+1} = Gamma v^dag with Gamma = sqrt(R) / |v^dag| (Eq. opt_solution):
+      // in 1D that is sqrt(R) with the sign of v^dag (one square root, no
+      // division)
       if (R < 0.0 || vd2 == 0.0)
         nfb++;
       else
-        vn = vd * (sqrt(R) / sqrt(vd2));
+        vn = copysign(sqrt(R), vd);
     }
     double xn = wrap_periodic(x + c.dt * vs, c.L, b.err);
     double wp = b.w ? b.w[p] : 1.0;
