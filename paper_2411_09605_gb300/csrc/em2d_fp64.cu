@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256) em_pass_e_kernel(Em2dConst c, Em2dBufs b,
       if (R < 0.0 || vd2 == 0.0)
         nfb++;
       else
-        g = sqrt(R) / sqrt(vd2);
+        g = sqrt(R / vd2);  // Gamma = sqrt(R) / |v^dag| (one root)
     }
     double vn[3];
 #pragma unroll
