@@ -425,18 +425,21 @@ __device__ __forceinline__ void report_flags(unsigned bad, unsigned *err) {
 
 
 
-// The correction of Eq. opt_solution in FP64 from the float-pair state
-// (bracket_fp64, gamma_minus_one_fp64): the R < 0 test and Gamma - 1 in FP64;
-// a fallback keeps v^dag and is counted (Sec. 3.2, Sec. 5.1).
+// The correction of Eq. opt_solution in FP64 from the float-pair state: R =
+// |v^dag|^2 + 2a (a from bracket_fp64), the R < 0 test, and in 1D v^{n+1} =
+// Gamma v^dag = sqrt(R) with the sign of v^dag (one root, no quotient; v^dag
+// is exact in FP64, so R carries FP64's precision), rounded to a float pair;
+// a fallback (R < 0 or v^dag = 0) keeps v^dag and is counted (Sec. 3.2,
+// Sec. 5.1).
 __device__ __forceinline__ ff correct_velocity_fp64(float vh, float vl, int Vs, ff d, ff vd,
                                                  unsigned &nfb) {
   const double vdd = ff_to_double(vd);
-  double g;
-  if (!gamma_minus_one_fp64(ff_to_double(d) * bracket_fp64(vh, vl, Vs, d), vdd * vdd, g)) {
+  const double R = fma(vdd, vdd, 2.0 * (ff_to_double(d) * bracket_fp64(vh, vl, Vs, d)));
+  if (!(R >= 0.0) || vdd == 0.0) {
     nfb++;
     return vd;
   }
-  return scale_by_gamma_fp64(vd, g);
+  return ff_from_double(copysign(sqrt(R), vdd));
 }
 
 // v^dag = v^n + d and v^{n+1} = Gamma v^dag (Eq. opt_solution) in float pairs.
