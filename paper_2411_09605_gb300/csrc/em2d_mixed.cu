@@ -31,9 +31,8 @@
 //   * Gamma (Eq. opt_solution): with Delta = v^dag - v^n = d + mu,
 //     |v^{n+1}|^2 - |v^dag|^2 = 2 Delta . (V* - v^n - Delta/2), the bracket
 //     from the exact difference V* - v^n per component, t = 2a / |v^dag|^2,
-//     and Gamma - 1 = t / (1 + sqrt(1 + t)): a 4-term FP32 series for
-//     |t| < 2^-8, FP64 otherwise (every candidate for the fallback among
-//     them).
+//     and Gamma - 1 = sqrt(1 + t) - 1: a 4-term FP32 series for |t| < 2^-8,
+//     FP64 otherwise (every candidate for the fallback among them).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -337,7 +336,7 @@ __device__ __forceinline__ bool gamma3_fp64(float vh0, float vh1, float vh2, flo
 // pairs, three components.  R - |v^dag|^2 = 2a with a = Delta . b and
 // b = V* - v^n - Delta/2: each b_i is formed from the exact difference
 // V*_i - rint(vh_i) and the exact remainders, the small product in FP32.
-// Gamma - 1 = t / (1 + sqrt(1 + t)), t = 2a / |v^dag|^2; for |t| < 2^-8 the
+// Gamma - 1 = sqrt(1 + t) - 1, t = 2a / |v^dag|^2; for |t| < 2^-8 the
 // series t/2 - t^2/8 + t^3/16 - 5t^4/128 (relative error < 2^-33); every
 // other marker, among them every candidate for the fallback, takes
 // gamma3_fp64: R < 0 (t < -1) and v^dag = 0 (t not finite) fall back to

@@ -29,8 +29,10 @@
 //   * Gamma (Eq. opt_solution) from the exact difference
 //     |v^{n+1}|^2 - |v^dag|^2 = 2a, a = d (v* - v^n - d/2) (float pairs for
 //     the cancelling subtraction, FP32 for the small product):
-//     g = Gamma - 1 = t / (1 + sqrt(1 + t)), t = 2a/|v^dag|^2, and
-//     v^{n+1} = v^dag + g v^dag in float pairs.  R < 0 is 1 + t < 0.
+//     g = Gamma - 1, t = 2a/|v^dag|^2: for |t| < 2^-8 an FP32 series of
+//     sqrt(1 + t) - 1 and v^{n+1} = v^dag + g v^dag in float pairs; every
+//     other marker takes FP64, R = |v^dag|^2 + 2a and v^{n+1} = sqrt(R) with
+//     the sign of v^dag.  R < 0 is 1 + t < 0.
 //   * energies: per-thread float-pair sums of v^2, block sums in FP64.
 // Gather #1 and deposit #1 only shape v* (not the conservation), so they use
 // plain FP32 weights and the same integer deposit.

@@ -200,13 +200,15 @@ __device__ __forceinline__ double bracket_fp64(float vh, float vl, int Vs, ff D)
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
-// Gamma - 1 = t / (1 + sqrt(1 + t)), t = 2a / v2 (v2 = |v^dag|^2), in FP64.
-// Returns false for the fallback of Sec. 3.2: R < 0 (t < -1) or v^dag = 0 (t
-// not finite); R = 0 gives Gamma = 0.
+// Gamma - 1 = sqrt(1 + t) - 1, t = 2a / v2 (v2 = |v^dag|^2), in FP64 (one
+// quotient, one root).  Its absolute error is about 2^-53, and v^{n+1} =
+// v^dag + (Gamma - 1) v^dag needs no more: the float-pair velocity holds 48
+// bits.  Returns false for the fallback of Sec. 3.2: R < 0 (t < -1) or v^dag =
+// 0 (t not finite); R = 0 gives Gamma = 0.
 __device__ __forceinline__ bool gamma_minus_one_fp64(double a, double v2, double &g) {
   const double t = 2.0 * a / v2;
   if (!(t >= -1.0 && t < 1e300)) return false;
-  g = t / (1.0 + sqrt(1.0 + t));
+  g = sqrt(1.0 + t) - 1.0;
   return true;
 }
 
