@@ -63,6 +63,22 @@ def test_fused_equals_two_launches(order, nc):
     assert b[6] < a[6]
 
 
+def test_fused_marker_bound_of_both_block_sizes():
+    """At 9,806,432 markers on 152 SMs a tile copy of a 768-thread block takes
+    22 trips of 96 markers (2112), more than a 1024-thread block's 16 trips of
+    128 (2048): the handle's bound covers both block sizes (one more bit in
+    the counters' split), and the fused and two-launch forms still agree."""
+    import torch
+    if torch.cuda.get_device_properties(0).multi_processor_count != 152:
+        pytest.skip("the marker count is chosen for 152 SMs")
+    prob = W.two_stream(n=9_806_432, nc=512, order=2, seed=33)
+    a = _run(prob, True, [2, 1])
+    b = _run(prob, False, [2, 1])
+    for u, w in zip(a[:4], b[:4]):
+        assert np.array_equal(u, w)
+    assert _same_energies(a[4], b[4])
+
+
 def test_fused_restart_and_async():
     """A restart drops the pending push of the next step and redoes it; the
     asynchronous interface reads the same stats."""
