@@ -56,7 +56,7 @@ FP64_LANES_PER_SM_CLK = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu capture of the current kernels on this workload (2^23 markers); None where
 # the kernel changed since it was taken.
-TRAFFIC = {("mixed", 0): 111684352, ("mixed", 1): 178928896, ("mixed_esec1", 5): 208356864,
+TRAFFIC = {("mixed", 0): 111384320, ("mixed", 1): 177644544, ("mixed_esec1", 5): 208671488,
            ("fp64", 0): None, ("fp64", 1): 301577216, ("standard", 1): 207165440}
 
 
