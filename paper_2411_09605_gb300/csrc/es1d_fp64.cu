@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(512) pass_c_kernel(Es1dConst c, Es1dFp64Bufs b
     double coef = (b.w ? c.q_h[s] * b.w[p] : c.qw_h[s]) * vs;
     Shape64<ORDER> S(__dmul_rn(xh, c.inv_h), c.nc);
     S.deposit(Jt, coef);
+    if (b.sw) S.store(b.sw, b.si, p, c.n_total);  // pass E gathers with it
   }
   __syncthreads();
   flush_tile(Jt, b.J2[par], c.nc);
@@ -224,17 +225,25 @@ __global__ void __launch_bounds__(512) pass_e_kernel(Es1dConst c, Es1dFp64Bufs b
     int s = species_of(c, p);
     double x = b.x[p], v = b.v[p];
     double qm = c.qm[s];
-    // v* from pass C and x^{n+1/2} with the rounding half_push used for the
-    // deposit; without the v* array (the entry point without allocation),
-    // half_push again on the same E* table, which gives the same bits
-    double vs, xh;
-    if (b.vs) {
+    // v* and the shape at x^{n+1/2} that pass C deposited with (loaded: on
+    // this FP64-bound pass bytes are cheaper than the shape's arithmetic);
+    // without those arrays (the entry point without allocation), half_push
+    // again on the same E* table, which gives the same bits
+    double vs;
+    Shape64<ORDER> Sh;
+    if (b.vs && b.sw) {
       vs = b.vs[p];
-      xh = wrap_periodic(__fma_rn(hdt, vs, x), c.L, b.err);
+      Sh.load(b.sw, b.si, p, c.n_total, c.nc);
     } else {
-      half_push<ORDER>(c, Es, x, v, qm, b.err, vs, xh);
+      double xh;
+      if (b.vs) {
+        vs = b.vs[p];
+        xh = wrap_periodic(__fma_rn(hdt, vs, x), c.L, b.err);
+      } else {
+        half_push<ORDER>(c, Es, x, v, qm, b.err, vs, xh);
+      }
+      Sh = Shape64<ORDER>(__dmul_rn(xh, c.inv_h), c.nc);
     }
-    Shape64<ORDER> Sh(__dmul_rn(xh, c.inv_h), c.nc);
     double Ep = Sh.gather(Eh);
     double vd = v + c.dt * qm * Ep;
     double R = v * v + 2.0 * vs * (vd - v);

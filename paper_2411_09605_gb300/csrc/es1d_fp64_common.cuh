@@ -30,6 +30,27 @@ template <int ORDER>
 struct Shape64 {
   int idx[ORDER + 1];
   double w[ORDER + 1];
+  Shape64() = default;
+  // the shape a pass stored (store()), node i0 = idx[ORDER - 1]
+  __device__ __forceinline__ void load(const double *sw, const int *si, int64_t p, int64_t n,
+                                       int nc) {
+    const int i0 = si[p];
+    if (ORDER == 1) {
+      idx[0] = i0;
+      idx[1] = i0 + 1 == nc ? 0 : i0 + 1;
+    } else {
+      idx[0] = i0 - 1 < 0 ? i0 - 1 + nc : i0 - 1;
+      idx[1] = i0;
+      idx[ORDER] = i0 + 1 >= nc ? i0 + 1 - nc : i0 + 1;
+    }
+#pragma unroll
+    for (int k = 0; k <= ORDER; k++) w[k] = sw[k * n + p];
+  }
+  __device__ __forceinline__ void store(double *sw, int *si, int64_t p, int64_t n) const {
+    si[p] = idx[ORDER - 1];
+#pragma unroll
+    for (int k = 0; k <= ORDER; k++) sw[k * n + p] = w[k];
+  }
   __device__ __forceinline__ Shape64(double xi, int nc) {
     if (ORDER == 1) {
       double fl = floor(xi);

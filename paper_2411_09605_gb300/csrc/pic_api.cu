@@ -690,6 +690,11 @@ int init_es1d(pic_handle *h, const pic_species *species, const double *E0) {
   if ((rc = h->alloc(&b.x, h->N)) || (rc = h->alloc(&b.v, h->N)) ||
       (!h->mixed && (rc = h->alloc(&b.vs, h->N))))
     return rc;
+  b.sw = nullptr;
+  b.si = nullptr;
+  if (!h->mixed && ((rc = h->alloc(&b.sw, (size_t)(c.order + 1) * h->N)) ||
+                    (rc = h->alloc(&b.si, h->N))))
+    return rc;
   b.w = nullptr;
   if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;
   for (int k = 0; k < 2; k++)
