@@ -81,6 +81,39 @@ template <int OI, int OH>
 struct Shape2 {
   W1<OI> xI, yI;
   W1<OH> xH, yH;
+  static constexpr int kWeights = 2 * (OI + 1) + 2 * (OH + 1);
+  Shape2() = default;
+  // the four axes' first nodes and weights, as store() wrote them for marker p
+  __device__ __forceinline__ void load(const double *sw, const int *si, int64_t p, int64_t n) {
+    xI.i0 = si[p];
+    xH.i0 = si[n + p];
+    yI.i0 = si[2 * n + p];
+    yH.i0 = si[3 * n + p];
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a <= OI; a++) xI.w[a] = sw[(k++) * n + p];
+#pragma unroll
+    for (int a = 0; a <= OH; a++) xH.w[a] = sw[(k++) * n + p];
+#pragma unroll
+    for (int a = 0; a <= OI; a++) yI.w[a] = sw[(k++) * n + p];
+#pragma unroll
+    for (int a = 0; a <= OH; a++) yH.w[a] = sw[(k++) * n + p];
+  }
+  __device__ __forceinline__ void store(double *sw, int *si, int64_t p, int64_t n) const {
+    si[p] = xI.i0;
+    si[n + p] = xH.i0;
+    si[2 * n + p] = yI.i0;
+    si[3 * n + p] = yH.i0;
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a <= OI; a++) sw[(k++) * n + p] = xI.w[a];
+#pragma unroll
+    for (int a = 0; a <= OH; a++) sw[(k++) * n + p] = xH.w[a];
+#pragma unroll
+    for (int a = 0; a <= OI; a++) sw[(k++) * n + p] = yI.w[a];
+#pragma unroll
+    for (int a = 0; a <= OH; a++) sw[(k++) * n + p] = yH.w[a];
+  }
   __device__ __forceinline__ Shape2(const Em2dConst &c, double x, double y) {
     const double xi = __dmul_rn(x, c.inv_hx), yi = __dmul_rn(y, c.inv_hy);
     xI.set(xi);
@@ -285,6 +318,7 @@ __global__ void __launch_bounds__(256) em_pass_c_kernel(Em2dConst c, Em2dBufs b)
     } else {
       const Shape2<OI, OH> S(c, xh, yh);
       deposit_j<OI, OH>(c, b.J2, S, coef, vs);
+      if (b.sw) S.store(b.sw, b.si, p, c.n_total);  // pass E gathers with it
     }
   }
 }
@@ -301,10 +335,18 @@ __global__ void __launch_bounds__(256) em_pass_e_kernel(Em2dConst c, Em2dBufs b,
     const double x = b.x[p], y = b.y[p];
     const double v[3] = {b.vx[p], b.vy[p], b.vz[p]};
     const double vs[3] = {b.vsx[p], b.vsy[p], b.vsz[p]};
-    const double hdt = 0.5 * c.dt;
-    const double xh = wrapd(__fma_rn(hdt, vs[0], x), c.Lx, b.err);
-    const double yh = wrapd(__fma_rn(hdt, vs[1], y), c.Ly, b.err);
-    Shape2<OI, OH> S(c, xh, yh);
+    // the shape at x^{n+1/2} that pass C deposited with (point shapes, loaded:
+    // on this FP64-bound pass bytes are cheaper than its arithmetic), else
+    // formed again with pass C's rounding
+    Shape2<OI, OH> S;
+    if (!CC && b.sw) {
+      S.load(b.sw, b.si, p, c.n_total);
+    } else {
+      const double hdt = 0.5 * c.dt;
+      const double xh = wrapd(__fma_rn(hdt, vs[0], x), c.Lx, b.err);
+      const double yh = wrapd(__fma_rn(hdt, vs[1], y), c.Ly, b.err);
+      S = Shape2<OI, OH>(c, xh, yh);
+    }
     double e[3], bb[3];
     if (CC) {
       // E^{n+1/2} over the path's pieces with the deposit's fractions and shapes

@@ -983,6 +983,14 @@ int init_em2d(pic_handle *h, const pic_species *species, const double *E0, const
   if (!h->mixed && ((rc = h->alloc(&b.vsx, h->N)) || (rc = h->alloc(&b.vsy, h->N)) ||
                     (rc = h->alloc(&b.vsz, h->N))))
     return rc;
+  // the point-shape FP64 passes hand the shape at x^{n+1/2} from pass C to pass
+  // E: 4 first nodes and 4 (order + 1) weights a marker
+  b.sw = nullptr;
+  b.si = nullptr;
+  if (!h->mixed && !cfg.charge_conserving &&
+      ((rc = h->alloc(&b.sw, (size_t)4 * (cfg.shape_order + 1) * h->N)) ||
+       (rc = h->alloc(&b.si, (size_t)4 * h->N))))
+    return rc;
   b.w = nullptr;
   if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;
   double **fields[] = {&b.E, &b.En, &b.Eh, &b.Es, &b.B, &b.Bp, &b.Bpp, &b.J1, &b.J2};
