@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_c_kernel(Em1dConst c, E
     const Shape64<ORDER> S(__dmul_rn(yh, c.inv_h), n);
     const double qw = marker_qw(c, b, s, p);
     tile_deposit<ORDER>(Jt, c.rt, S, qw * vsx, qw * vsy);
+    if (b.sw) S.store(b.sw, b.si, p, c.n_total);  // pass E gathers with it
   }
   __syncthreads();
   flush_tile(Jt, c.rt, b.J2, n);
@@ -318,8 +319,16 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_e_kernel(Em1dConst c, E
     const double qm = c.qm[s];
     const double y = b.y[p], vx = b.vx[p], vy = b.vy[p];
     const double vsx = b.vsx[p], vsy = b.vsy[p];
-    const double yh = wrap_periodic(__fma_rn(hdt, vsy, y), c.L, b.err);
-    const Shape64<ORDER> S(__dmul_rn(yh, c.inv_h), n);
+    // the shape at y^{n+1/2} that pass C deposited with (loaded: on this
+    // FP64-bound pass bytes are cheaper than its arithmetic), else formed
+    // again with pass C's rounding
+    Shape64<ORDER> S;
+    if (b.sw) {
+      S.load(b.sw, b.si, p, c.n_total, n);
+    } else {
+      const double yh = wrap_periodic(__fma_rn(hdt, vsy, y), c.L, b.err);
+      S = Shape64<ORDER>(__dmul_rn(yh, c.inv_h), n);
+    }
     const double ex = S.gather(Eax), ey = S.gather(Eay), bz = S.gather(Bh);
     const double a = dt * qm;
     const double dx = fma(a, fma(vsy, bz, ex), vx);

@@ -212,6 +212,8 @@ struct Em1dConst {
 struct Em1dBufs {
   double *y, *vx, *vy, *w;   // [N] SoA (w may be null)
   double *vsx, *vsy;         // [N] v* of the current step (pass C -> pass E)
+  double *sw;                // [order + 1][N] shape weights at y^{n+1/2} and
+  int *si;                   // [N] its node (pass C -> pass E), or null (recomputed)
   double *E, *En;            // E^n, E^{n+1}: [2][n] (Ex, Ey); swapped after each step
   double *B, *Bn;            // Bz^n, Bz^{n+1}: [n]
   double *Es, *Bs;           // E*, B* of the half step
