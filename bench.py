@@ -51,13 +51,13 @@ ALGO_BYTES = {  # (form, kernel kind) -> bytes per marker
 # clock on this part), not by HBM: its roofline counts FP64-pipe thread
 # instructions per marker, measured once with ncu
 # (sm__thread_inst_executed_pipe_fp64_pred_on.sum / markers) on these kernels.
-FP64_INST_PER_MARKER = {("fp64", 0): 53.49, ("fp64", 1): 54.84, ("standard", 1): 45.39}
+FP64_INST_PER_MARKER = {("fp64", 0): 32.56, ("fp64", 1): 56.78, ("standard", 1): 45.39}
 FP64_LANES_PER_SM_CLK = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu capture of the current kernels on this workload (2^23 markers); None where
 # the kernel changed since it was taken.
 TRAFFIC = {("mixed", 0): 111384320, ("mixed", 1): 177644544, ("mixed_esec1", 5): 208671488,
-           ("fp64", 0): 378750464, ("fp64", 1): 542751488, ("standard", 1): 207165440}
+           ("fp64", 0): 631477504, ("fp64", 1): 754875648, ("standard", 1): 207165440}
 
 
 def parse():

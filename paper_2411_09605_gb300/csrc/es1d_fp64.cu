@@ -155,7 +155,15 @@ __global__ void __launch_bounds__(512) pass_c_kernel(Es1dConst c, Es1dFp64Bufs b
     int s = species_of(c, p);
     double x = b.x[p], v = b.v[p];
     double vs, xh;
-    half_push<ORDER>(c, Es, x, v, c.qm[s], b.err, vs, xh);
+    if (SCHEME == 2 && b.sws) {
+      // the shape at x* that the previous pass E (or the initial deposit)
+      // deposited j^{n,*} with, the same bits as forming it here
+      Shape64<ORDER> Sx;
+      Sx.load(b.sws, b.sis, p, c.n_total, c.nc);
+      half_push_at<ORDER>(c, Es, Sx, x, v, c.qm[s], b.err, vs, xh);
+    } else {
+      half_push<ORDER>(c, Es, x, v, c.qm[s], b.err, vs, xh);
+    }
     if (b.vs) b.vs[p] = vs;   // pass E forms x^{n+1/2} from it with the same rounding
     double coef = (b.w ? c.q_h[s] * b.w[p] : c.qw_h[s]) * vs;
     Shape64<ORDER> S(__dmul_rn(xh, c.inv_h), c.nc);
@@ -262,9 +270,9 @@ __global__ void __launch_bounds__(512) pass_e_kernel(Es1dConst c, Es1dFp64Bufs b
     double wp = b.w ? b.w[p] : 1.0;
     ke += (b.w ? c.half_m[s] * wp : c.half_mw[s]) * vn * vn;
     if (SCHEME == 2) {
-      double xs2 = wrap_periodic(xn + hdt * vn, c.L, b.err);
-      Shape64<ORDER> S2(xs2 * c.inv_h, c.nc);
+      Shape64<ORDER> S2(__dmul_rn(xstar(c, xn, vn, b.err), c.inv_h), c.nc);
       S2.deposit(Jt, (b.w ? c.q_h[s] * wp : c.qw_h[s]) * vn);
+      if (b.sws) S2.store(b.sws, b.sis, p, c.n_total);  // the next pass C gathers with it
     }
     b.x[p] = xn;
     b.v[p] = vn;
@@ -292,9 +300,9 @@ __global__ void __launch_bounds__(512) deposit_initial_kernel(Es1dConst c, Es1dF
        p += (int64_t)gridDim.x * blockDim.x) {
     int s = species_of(c, p);
     double x = b.x[p], v = b.v[p];
-    double xs = wrap_periodic(x + 0.5 * c.dt * v, c.L, b.err);
-    Shape64<ORDER> S(xs * c.inv_h, c.nc);
+    Shape64<ORDER> S(__dmul_rn(xstar(c, x, v, b.err), c.inv_h), c.nc);
     S.deposit(Jt, (b.w ? c.q_h[s] * b.w[p] : c.qw_h[s]) * v);
+    if (b.sws) S.store(b.sws, b.sis, p, c.n_total);  // pass C gathers with it
   }
   __syncthreads();
   flush_tile(Jt, b.J1[par], c.nc);

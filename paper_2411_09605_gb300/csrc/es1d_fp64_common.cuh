@@ -98,6 +98,24 @@ __device__ __forceinline__ int species_of(const Es1dConst &c, int64_t p) {
 // operations so that the two passes agree bit for bit (the deposit of pass C
 // and the gather of pass E must use the same x^{n+1/2} and v*, Eq.
 // exp_econs_simple).
+// x* = x + dt/2 v with the rounding every kernel of this form uses for it
+__device__ __forceinline__ double xstar(const Es1dConst &c, double x, double v, unsigned *err) {
+  return wrap_periodic(__fma_rn(0.5 * c.dt, v, x), c.L, err);
+}
+
+// E**_p, v*, x^{n+1/2} from the shape S at x*
+template <int ORDER>
+__device__ __forceinline__ void half_push_at(const Es1dConst &c, const double *Es,
+                                             const Shape64<ORDER> &S, double x, double v,
+                                             double qm, unsigned *err, double &vs, double &xh) {
+  double hdt = 0.5 * c.dt;
+  double Ess = __fma_rn(Es[S.idx[0]], S.w[0], 0.0);
+#pragma unroll
+  for (int k = 1; k <= ORDER; k++) Ess = __fma_rn(Es[S.idx[k]], S.w[k], Ess);
+  vs = __fma_rn(__dmul_rn(hdt, qm), Ess, v);
+  xh = wrap_periodic(__fma_rn(hdt, vs, x), c.L, err);
+}
+
 template <int ORDER>
 __device__ __forceinline__ void half_push(const Es1dConst &c, const double *Es, double x,
                                           double v, double qm, unsigned *err, double &vs,

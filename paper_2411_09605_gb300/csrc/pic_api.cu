@@ -692,8 +692,14 @@ int init_es1d(pic_handle *h, const pic_species *species, const double *E0) {
     return rc;
   b.sw = nullptr;
   b.si = nullptr;
+  b.sws = nullptr;
+  b.sis = nullptr;
   if (!h->mixed && ((rc = h->alloc(&b.sw, (size_t)(c.order + 1) * h->N)) ||
                     (rc = h->alloc(&b.si, h->N))))
+    return rc;
+  // ESEC2: the shape at x* from pass E (or the initial deposit) to pass C
+  if (!h->mixed && c.scheme == 2 &&
+      ((rc = h->alloc(&b.sws, (size_t)(c.order + 1) * h->N)) || (rc = h->alloc(&b.sis, h->N))))
     return rc;
   b.w = nullptr;
   if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;

@@ -344,6 +344,9 @@ struct Es1dFp64Bufs {
                             // pass E then recomputes it (the same bits)
   double *sw;               // [order + 1][N] shape weights at x^{n+1/2} and
   int *si;                  // [N] its node (pass C -> pass E), or null (recomputed)
+  double *sws;              // ESEC2: [order + 1][N] shape weights at the next step's
+  int *sis;                 // x* and its node (pass E or the initial deposit -> pass
+                            // C), or null (recomputed)
   double *E[2];             // ping-pong E^n / E^{n+1}
   double *J1[2];            // j^{n,*} (ESEC2), indexed by step parity
   double *J2[2];            // j^{*,n+1/2}
