@@ -622,12 +622,12 @@ EM2D_ALGO_BYTES = {("fp64", 0): 64, ("fp64", 1): 104, ("mixed", 0): 44, ("mixed"
                    ("fp64_charge_conserving", 0): 64, ("fp64_charge_conserving", 1): 104}
 # FP64-pipe thread instructions per marker of the FP64 form (ncu, 2^20
 # markers): that form is bound by the FP64 pipe
-EM2D_FP64_INST_PER_MARKER = {("fp64", 0): 162.15, ("fp64", 1): 160.74,
-                             ("fp64_charge_conserving", 0): 173.77,
+EM2D_FP64_INST_PER_MARKER = {("fp64", 0): 128.15, ("fp64", 1): 163.74,
+                             ("fp64_charge_conserving", 0): 174.77,
                              ("fp64_charge_conserving", 1): 224.81}
-EM2D_TRAFFIC = {("fp64", 0): 93685760, ("fp64", 1): 167203328,   # dram read + write per launch
+EM2D_TRAFFIC = {("fp64", 0): 192259840, ("fp64", 1): 226352640,   # dram read + write per launch
                 ("mixed", 0): None, ("mixed", 1): None,
-                ("fp64_charge_conserving", 0): 43222784, ("fp64_charge_conserving", 1): 68536576}
+                ("fp64_charge_conserving", 0): 45156096, ("fp64_charge_conserving", 1): 68527360}
 
 
 def time_weibel2d(prob, precision, args, stream, flush, charge_conserving=False,

@@ -229,15 +229,24 @@ __device__ __forceinline__ int species_of2(const Em2dConst &c, int64_t p) {
   return s;
 }
 
-// x*, E**, B at x*, v* and x^{n+1/2}.
+// The shape at x* = x + dt/2 v, with the rounding every kernel of this form
+// uses for it.
 template <int OI, int OH>
-__device__ __forceinline__ void half_push_em(const Em2dConst &c, const Em2dBufs &b, int s,
-                                             double x, double y, const double v[3], double vs[3],
-                                             double &xh, double &yh) {
+__device__ __forceinline__ Shape2<OI, OH> shape_at_xstar(const Em2dConst &c, const Em2dBufs &b,
+                                                         double x, double y, const double v[3]) {
   const double hdt = 0.5 * c.dt;
   const double xs = wrapd(__fma_rn(hdt, v[0], x), c.Lx, b.err);
   const double ys = wrapd(__fma_rn(hdt, v[1], y), c.Ly, b.err);
-  Shape2<OI, OH> S(c, xs, ys);
+  return Shape2<OI, OH>(c, xs, ys);
+}
+
+// E**, B at x* (shape S), v* and x^{n+1/2}.
+template <int OI, int OH>
+__device__ __forceinline__ void half_push_em(const Em2dConst &c, const Em2dBufs &b, int s,
+                                             const Shape2<OI, OH> &S, double x, double y,
+                                             const double v[3], double vs[3], double &xh,
+                                             double &yh) {
+  const double hdt = 0.5 * c.dt;
   double e[3], bb[3];
   gather_eb<OI, OH>(c, b.Es, b.Bp, S, e, bb);
   const double k = __dmul_rn(hdt, c.qm[s]);
@@ -305,7 +314,14 @@ __global__ void __launch_bounds__(256) em_pass_c_kernel(Em2dConst c, Em2dBufs b)
     const double x = b.x[p], y = b.y[p];
     const double v[3] = {b.vx[p], b.vy[p], b.vz[p]};
     double vs[3], xh, yh;
-    half_push_em<OI, OH>(c, b, s, x, y, v, vs, xh, yh);
+    // ESEC2, point shapes: the shape at x* that the previous pass E (or the
+    // initial deposit) deposited j^{n,*} with, the same bits as forming it
+    Shape2<OI, OH> Sx;
+    if (!CC && b.sws)
+      Sx.load(b.sws, b.sis, p, c.n_total);
+    else
+      Sx = shape_at_xstar<OI, OH>(c, b, x, y, v);
+    half_push_em<OI, OH>(c, b, s, Sx, x, y, v, vs, xh, yh);
     b.vsx[p] = vs[0];   // pass E forms x^{n+1/2} from v* with the same rounding
     b.vsy[p] = vs[1];
     b.vsz[p] = vs[2];
@@ -386,10 +402,9 @@ __global__ void __launch_bounds__(256) em_pass_e_kernel(Em2dConst c, Em2dBufs b,
     const double wp = b.w ? b.w[p] : 1.0;
     ke += (b.w ? c.half_m[s] * wp : c.half_mw[s]) * (vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
     if (c.scheme == 2) {
-      const double xs2 = wrapd(xn + 0.5 * c.dt * vn[0], c.Lx, b.err);
-      const double ys2 = wrapd(yn + 0.5 * c.dt * vn[1], c.Ly, b.err);
-      Shape2<OI, OH> S2(c, xs2, ys2);
+      const Shape2<OI, OH> S2 = shape_at_xstar<OI, OH>(c, b, xn, yn, vn);
       deposit_j<OI, OH>(c, b.J1, S2, b.w ? c.q_a[s] * wp : c.qw_a[s], vn);
+      if (!CC && b.sws) S2.store(b.sws, b.sis, p, c.n_total);  // the next pass C's
     }
     b.x[p] = xn;
     b.y[p] = yn;
@@ -412,10 +427,9 @@ __global__ void __launch_bounds__(256) em_deposit_initial_kernel(Em2dConst c, Em
        p += (int64_t)gridDim.x * blockDim.x) {
     const int s = species_of2(c, p);
     const double v[3] = {b.vx[p], b.vy[p], b.vz[p]};
-    const double xs = wrapd(b.x[p] + 0.5 * c.dt * v[0], c.Lx, b.err);
-    const double ys = wrapd(b.y[p] + 0.5 * c.dt * v[1], c.Ly, b.err);
-    Shape2<OI, OH> S(c, xs, ys);
+    const Shape2<OI, OH> S = shape_at_xstar<OI, OH>(c, b, b.x[p], b.y[p], v);
     deposit_j<OI, OH>(c, b.J1, S, b.w ? c.q_a[s] * b.w[p] : c.qw_a[s], v);
+    if (!CC && b.sws) S.store(b.sws, b.sis, p, c.n_total);  // pass C gathers with it
   }
 }
 

@@ -993,9 +993,16 @@ int init_em2d(pic_handle *h, const pic_species *species, const double *E0, const
   // E: 4 first nodes and 4 (order + 1) weights a marker
   b.sw = nullptr;
   b.si = nullptr;
+  b.sws = nullptr;
+  b.sis = nullptr;
   if (!h->mixed && !cfg.charge_conserving &&
       ((rc = h->alloc(&b.sw, (size_t)4 * (cfg.shape_order + 1) * h->N)) ||
        (rc = h->alloc(&b.si, (size_t)4 * h->N))))
+    return rc;
+  // ESEC2: the shape at x* from pass E (or the initial deposit) to pass C
+  if (!h->mixed && !cfg.charge_conserving && cfg.scheme == 2 &&
+      ((rc = h->alloc(&b.sws, (size_t)4 * (cfg.shape_order + 1) * h->N)) ||
+       (rc = h->alloc(&b.sis, (size_t)4 * h->N))))
     return rc;
   b.w = nullptr;
   if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;

@@ -177,6 +177,8 @@ struct Em2dBufs {
   double *vsx, *vsy, *vsz;     // [N] v* of the current step (pass C -> pass E)
   double *sw;     // [weights][N] shape at x^{n+1/2} (point shapes: pass C -> pass E),
   int *si;        // [4][N] its first nodes; both null: pass E forms it again
+  double *sws;    // ESEC2, point shapes: the shape at the next step's x* (pass E or
+  int *sis;       // the initial deposit -> pass C), as sw / si; null: formed again
   double *ke_part;             // [particle blocks]
   double *wf_part;             // [2 x grid blocks] W_E, W_B partials
   unsigned long long *fallback;
