@@ -762,9 +762,9 @@ EM1D_ALGO_BYTES = {0: 40, 1: 64}          # pass C also writes v*, pass E reads 
 # FP64-pipe thread instructions per marker of the 1D2V passes (ncu,
 # sm__thread_inst_executed_pipe_fp64_pred_on.sum / markers at 2^23 markers):
 # like the FP64 1D form these passes are bound by the FP64 pipe, not by HBM
-EM1D_FP64_INST_PER_MARKER = {0: 54.48, 1: 73.37}
+EM1D_FP64_INST_PER_MARKER = {0: 42.57, 1: 74.38}
 # DRAM bytes per launch at 2^23 markers (dram__bytes_read.sum + dram__bytes_write.sum)
-EM1D_TRAFFIC = {0: 446745600, 1: 668553216}
+EM1D_TRAFFIC = {0: 627530240, 1: 822075136}
 # the mixed form: y (u32) and two float pairs; pass C writes V* (2 x i32),
 # pass E reads it and writes y and the pairs
 EM1D_MIX_ALGO_BYTES = {0: 28, 1: 48}

@@ -69,14 +69,23 @@ __device__ __forceinline__ int species_of1(const Em1dConst &c, int64_t p) {
 
 // y*, E**, B**, v*, y^{n+1/2} with explicitly rounded operations: pass C
 // deposits at exactly the y^{n+1/2} and v* that pass E gathers at.
+// The shape at y* = y + dt/2 vy, with the rounding every kernel of this form
+// uses for it.
+template <int ORDER>
+__device__ __forceinline__ Shape64<ORDER> em1d_shape_at_ystar(const Em1dConst &c, double y,
+                                                              double vy, unsigned *err) {
+  const double ys = wrap_periodic(__fma_rn(0.5 * c.dt, vy, y), c.L, err);
+  return Shape64<ORDER>(__dmul_rn(ys, c.inv_h), c.n);
+}
+
+// E**, B**, v*, y^{n+1/2} from the shape S at y*
 template <int ORDER>
 __device__ __forceinline__ void em1d_half_push(const Em1dConst &c, const double *Esx,
-                                               const double *Esy, const double *Bs, double y,
-                                               double vx, double vy, double qm, unsigned *err,
-                                               double &vsx, double &vsy, double &yh) {
+                                               const double *Esy, const double *Bs,
+                                               const Shape64<ORDER> &S, double y, double vx,
+                                               double vy, double qm, unsigned *err, double &vsx,
+                                               double &vsy, double &yh) {
   const double hdt = 0.5 * c.dt;
-  const double ys = wrap_periodic(__fma_rn(hdt, vy, y), c.L, err);
-  const Shape64<ORDER> S(__dmul_rn(ys, c.inv_h), c.n);
   const double ex = S.gather(Esx), ey = S.gather(Esy), bz = S.gather(Bs);
   const double a = __dmul_rn(hdt, qm);
   const double ux = __fma_rn(a, ex, vx), uy = __fma_rn(a, ey, vy);
@@ -275,7 +284,15 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_c_kernel(Em1dConst c, E
        p += (int64_t)gridDim.x * blockDim.x) {
     const int s = species_of1(c, p);
     double vsx, vsy, yh;
-    em1d_half_push<ORDER>(c, Esx, Esy, Bs, b.y[p], b.vx[p], b.vy[p], c.qm[s], b.err, vsx, vsy, yh);
+    // ESEC2: the shape at y* that the previous pass E (or the initial deposit)
+    // deposited j^{n,*} with, the same bits as forming it here
+    Shape64<ORDER> Sy;
+    if (b.sws)
+      Sy.load(b.sws, b.sis, p, c.n_total, n);
+    else
+      Sy = em1d_shape_at_ystar<ORDER>(c, b.y[p], b.vy[p], b.err);
+    em1d_half_push<ORDER>(c, Esx, Esy, Bs, Sy, b.y[p], b.vx[p], b.vy[p], c.qm[s], b.err, vsx, vsy,
+                          yh);
     b.vsx[p] = vsx;   // pass E forms y^{n+1/2} from v* with the same rounding
     b.vsy[p] = vsy;
     const Shape64<ORDER> S(__dmul_rn(yh, c.inv_h), n);
@@ -350,10 +367,10 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_pass_e_kernel(Em1dConst c, E
     b.vy[p] = v1y;
     ke = fma(c.half_m[s] * (b.w ? b.w[p] : c.w0[s]), fma(v1x, v1x, v1y * v1y), ke);
     if (c.scheme == 2) {
-      const double ys = wrap_periodic(fma(hdt, v1y, y1), c.L, b.err);
-      const Shape64<ORDER> S2(ys * c.inv_h, n);
+      const Shape64<ORDER> S2 = em1d_shape_at_ystar<ORDER>(c, y1, v1y, b.err);
       const double qw = marker_qw(c, b, s, p);
       tile_deposit<ORDER>(Jt, c.rt, S2, qw * v1x, qw * v1y);
+      if (b.sws) S2.store(b.sws, b.sis, p, c.n_total);  // the next pass C gathers with it
     }
   }
   if (!isfinite(ke)) atomicOr(b.err, kErrNonfinite);
@@ -401,10 +418,10 @@ __global__ void __launch_bounds__(kEm1Threads) em1d_deposit_initial_kernel(Em1dC
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < c.n_total;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int s = species_of1(c, p);
-    const double ys = wrap_periodic(fma(0.5 * c.dt, b.vy[p], b.y[p]), c.L, b.err);
-    const Shape64<ORDER> S(ys * c.inv_h, c.n);
+    const Shape64<ORDER> S = em1d_shape_at_ystar<ORDER>(c, b.y[p], b.vy[p], b.err);
     const double qw = marker_qw(c, b, s, p);
     tile_deposit<ORDER>(Jt, c.rt, S, qw * b.vx[p], qw * b.vy[p]);
+    if (b.sws) S.store(b.sws, b.sis, p, c.n_total);  // pass C gathers with it
   }
   __syncthreads();
   flush_tile(Jt, c.rt, b.J1, c.n);

@@ -1284,11 +1284,18 @@ int init_em1d(pic_handle *h, const pic_species *species, const double *E0, const
   if ((rc = h->alloc(&b.y, h->N)) || (rc = h->alloc(&b.vx, h->N)) || (rc = h->alloc(&b.vy, h->N)))
     return rc;
   if (!h->mixed && ((rc = h->alloc(&b.vsx, h->N)) || (rc = h->alloc(&b.vsy, h->N)))) return rc;
-  // the FP64 passes hand the shape at y^{n+1/2} from pass C to pass E
+  // the FP64 passes hand the shape at y^{n+1/2} from pass C to pass E and,
+  // with ESEC2, the shape at the next y* from pass E to pass C
   b.sw = nullptr;
   b.si = nullptr;
+  b.sws = nullptr;
+  b.sis = nullptr;
   if (!h->mixed && ((rc = h->alloc(&b.sw, (size_t)(cfg.shape_order + 1) * h->N)) ||
                     (rc = h->alloc(&b.si, h->N))))
+    return rc;
+  if (!h->mixed && cfg.scheme == 2 &&
+      ((rc = h->alloc(&b.sws, (size_t)(cfg.shape_order + 1) * h->N)) ||
+       (rc = h->alloc(&b.sis, h->N))))
     return rc;
   b.w = nullptr;
   if (h->weighted && (rc = h->alloc(&b.w, h->N))) return rc;

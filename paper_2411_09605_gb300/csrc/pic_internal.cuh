@@ -216,6 +216,8 @@ struct Em1dBufs {
   double *vsx, *vsy;         // [N] v* of the current step (pass C -> pass E)
   double *sw;                // [order + 1][N] shape weights at y^{n+1/2} and
   int *si;                   // [N] its node (pass C -> pass E), or null (recomputed)
+  double *sws;               // ESEC2: the shape at the next step's y* (pass E or the
+  int *sis;                  // initial deposit -> pass C), as sw / si; null: formed again
   double *E, *En;            // E^n, E^{n+1}: [2][n] (Ex, Ey); swapped after each step
   double *B, *Bn;            // Bz^n, Bz^{n+1}: [n]
   double *Es, *Bs;           // E*, B* of the half step
